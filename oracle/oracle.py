@@ -1,0 +1,243 @@
+"""ctypes wrapper of the FP64 CPU oracle (splx_oracle.cpp).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the
+benchmark's CPU-baseline leg.  The product path never imports this module.
+
+Every function takes float64 copies of the parameters, so finite differences can
+perturb them in FP64; the FP32 binning specification rounds them to float itself.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "splx_oracle.cpp")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (-ffp-contract=off keeps the FP32 spec uncontracted)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32),
+                ("height", C.c_int32), ("near_plane", C.c_float)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("eps_T", C.c_double), ("eps_comp", C.c_double),
+                ("alpha_min", C.c_double), ("alpha_max", C.c_double), ("bg", C.c_double * 3),
+                ("amb_alpha", C.c_double), ("amb_power", C.c_double), ("amb_T", C.c_double),
+                ("amb_key", C.c_double)]
+
+
+_dp = C.POINTER(C.c_double)
+
+
+class Params(C.Structure):
+    _fields_ = [("means", _dp), ("log_scales", _dp), ("quats", _dp), ("opacity_logits", _dp),
+                ("sh", _dp), ("n", C.c_int64), ("sh_degree", C.c_int32)]
+
+
+class Grads(C.Structure):
+    _fields_ = [("means", _dp), ("log_scales", _dp), ("quats", _dp), ("opacity_logits", _dp),
+                ("sh", _dp)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            P = C.c_void_p
+            _lib.orc_exp_spec.restype = C.c_float
+            _lib.orc_exp_spec.argtypes = [C.c_float]
+            _lib.orc_exp_spec_n.argtypes = [P, P, C.c_int64]
+            _lib.orc_sh_basis.argtypes = [P, C.c_int64, P]
+            _lib.orc_sh_basis_grad.argtypes = [P, C.c_int64, P]
+            _lib.orc_bin.argtypes = [P, P, P, P, P]
+            _lib.orc_tile_lists.restype = C.c_int64
+            _lib.orc_tile_lists.argtypes = [P, P, C.c_int32, P, P, C.c_int64]
+            _lib.orc_project.argtypes = [P, P, P]
+            _lib.orc_render.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
+            _lib.orc_composite.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P, P, P]
+            _lib.orc_render_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P, P, P, P]
+            _lib.orc_backward_view.argtypes = [P, P, C.c_int32, P, P, P, P, P]
+            _lib.orc_adam.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_double,
+                                      C.c_double, C.c_int64]
+            _lib.orc_num_threads.restype = C.c_int
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+class _Keep:
+    """Holds float64 copies of a scene alive while C code reads them."""
+
+    def __init__(self, scene):
+        self.arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in scene.arrays()]
+        m, ls, q, o, sh = self.arrs
+        self.p = Params(m.ctypes.data_as(_dp), ls.ctypes.data_as(_dp), q.ctypes.data_as(_dp),
+                        o.ctypes.data_as(_dp), sh.ctypes.data_as(_dp), m.shape[0], scene.sh_degree)
+
+
+def camera(cam) -> Camera:
+    c = Camera()
+    c.R[:] = [float(x) for x in np.asarray(cam.R, np.float32).reshape(-1)]
+    c.t[:] = [float(x) for x in np.asarray(cam.t, np.float32).reshape(-1)]
+    c.fx, c.fy, c.cx, c.cy = cam.fx, cam.fy, cam.cx, cam.cy
+    c.width, c.height, c.near_plane = cam.width, cam.height, cam.near
+    return c
+
+
+def opts(tile=16, eps_T=1e-4, eps_comp=1e-4, alpha_min=1.0 / 255.0, alpha_max=0.99,
+         bg=(0.0, 0.0, 0.0), amb_alpha=2e-5, amb_power=1e-5, amb_T=3e-4, amb_key=1e-5) -> Opts:
+    o = Opts()
+    o.tile, o.eps_T, o.eps_comp, o.alpha_min, o.alpha_max = tile, eps_T, eps_comp, alpha_min, alpha_max
+    o.bg[:] = list(bg)
+    o.amb_alpha, o.amb_power, o.amb_T, o.amb_key = amb_alpha, amb_power, amb_T, amb_key
+    return o
+
+
+def exp_spec(x: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, np.float32)
+    y = np.empty_like(x)
+    lib().orc_exp_spec_n(_ptr(x), _ptr(y), x.size)
+    return y
+
+
+def sh_basis(dirs: np.ndarray, grad: bool = False) -> np.ndarray:
+    d = np.ascontiguousarray(dirs, np.float64).reshape(-1, 3)
+    if grad:
+        out = np.empty((d.shape[0], 16, 3))
+        lib().orc_sh_basis_grad(_ptr(d), d.shape[0], _ptr(out))
+    else:
+        out = np.empty((d.shape[0], 16))
+        lib().orc_sh_basis(_ptr(d), d.shape[0], _ptr(out))
+    return out
+
+
+def bin(scene, cam):
+    """FP32 binning spec: (visible[n], rect[n,4] x0,x1,y0,y1, depth_bits[n] uint32)."""
+    k = _Keep(scene)
+    n = scene.n
+    vis = np.empty(n, np.int32)
+    rect = np.empty((n, 4), np.int32)
+    db = np.empty(n, np.uint32)
+    c = camera(cam)
+    lib().orc_bin(C.byref(k.p), C.byref(c), _ptr(vis), _ptr(rect), _ptr(db))
+    return vis, rect, db
+
+
+def tile_lists(scene, cam, tile=16):
+    """Sorted per-tile Gaussian lists: (tile_start[ntiles+1] int64, list[int32])."""
+    k = _Keep(scene)
+    c = camera(cam)
+    nt = ((cam.width + tile - 1) // tile) * ((cam.height + tile - 1) // tile)
+    start = np.empty(nt + 1, np.int64)
+    total = lib().orc_tile_lists(C.byref(k.p), C.byref(c), tile, _ptr(start), None, 0)
+    lst = np.empty(max(total, 1), np.int32)
+    got = lib().orc_tile_lists(C.byref(k.p), C.byref(c), tile, _ptr(start), _ptr(lst), lst.size)
+    assert got == total
+    return start, lst[:total]
+
+
+def project(scene, cam) -> np.ndarray:
+    """FP64 projection [n,12]: u, v, A, B, C, o, r, g, b, depth, a, c (0 for culled)."""
+    k = _Keep(scene)
+    out = np.empty((scene.n, 12))
+    c = camera(cam)
+    lib().orc_project(C.byref(k.p), C.byref(c), _ptr(out))
+    return out
+
+
+def render(scene, cam, o: Opts | None = None, tile_mask=None):
+    """Local render of one subset: dict of C[3,H,W], T, D, last, ncontrib, amb, evaluated."""
+    o = o or opts()
+    k = _Keep(scene)
+    c = camera(cam)
+    H, W = cam.height, cam.width
+    Cc = np.zeros((3, H, W)); T = np.ones((H, W)); D = np.zeros((H, W))
+    last = np.full((H, W), -1, np.int32); nc = np.zeros((H, W), np.int32)
+    amb = np.zeros((H, W), np.uint8); st = np.zeros(1, np.int64)
+    tm = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8)
+    lib().orc_render(C.byref(k.p), C.byref(c), C.byref(o), _ptr(tm), _ptr(Cc), _ptr(T), _ptr(D),
+                     _ptr(last), _ptr(nc), _ptr(amb), _ptr(st))
+    return dict(C=Cc, T=T, D=D, last=last, ncontrib=nc, amb=amb, evaluated=int(st[0]))
+
+
+def composite(Cp, Tp, Dp, o: Opts | None = None):
+    """Eq. 5 over K partials (C[K,3,H,W], T[K,H,W], D[K,H,W]): image, T, nused, amb."""
+    o = o or opts()
+    Cp = np.ascontiguousarray(Cp, np.float64); Tp = np.ascontiguousarray(Tp, np.float64)
+    Dp = np.ascontiguousarray(Dp, np.float64)
+    K, _, H, W = Cp.shape
+    out = np.empty((3, H, W)); To = np.empty((H, W)); nu = np.empty((H, W), np.int32)
+    amb = np.zeros((H, W), np.uint8)
+    lib().orc_composite(K, H, W, _ptr(Cp), _ptr(Tp), _ptr(Dp), C.byref(o), _ptr(out), _ptr(To),
+                        _ptr(nu), _ptr(amb))
+    return dict(image=out, T=To, nused=nu, amb=amb)
+
+
+def render_view(scene, offsets, cam, o: Opts | None = None, tile_mask=None, separable=False):
+    """K contiguous subsets rendered and composited: dict(image, T, Cp, Tp, Dp, amb, sep)."""
+    o = o or opts()
+    k = _Keep(scene)
+    c = camera(cam)
+    off = np.ascontiguousarray(offsets, np.int64)
+    K = off.size - 1
+    H, W = cam.height, cam.width
+    out = np.zeros((3, H, W)); To = np.ones((H, W))
+    Cp = np.zeros((K, 3, H, W)); Tp = np.ones((K, H, W)); Dp = np.zeros((K, H, W))
+    amb = np.zeros((H, W), np.uint8)
+    sep = np.ones((H, W), np.uint8) if separable else None
+    st = np.zeros(1, np.int64)
+    tm = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8)
+    lib().orc_render_view(C.byref(k.p), _ptr(off), K, C.byref(c), C.byref(o), _ptr(tm), _ptr(out),
+                          _ptr(To), _ptr(Cp), _ptr(Tp), _ptr(Dp), _ptr(amb), _ptr(sep), _ptr(st))
+    return dict(image=out, T=To, Cp=Cp, Tp=Tp, Dp=Dp, amb=amb, sep=sep, evaluated=int(st[0]))
+
+
+def backward_view(scene, offsets, cam, dLdC, dLdT=None, o: Opts | None = None):
+    """Gradients (float64) of sum(dLdC*C) + sum(dLdT*T) w.r.t. every parameter array."""
+    o = o or opts()
+    k = _Keep(scene)
+    c = camera(cam)
+    off = np.ascontiguousarray(offsets, np.int64)
+    K = off.size - 1
+    g = [np.zeros(a.shape) for a in scene.arrays()]
+    gr = Grads(*(a.ctypes.data_as(_dp) for a in g))
+    dC = np.ascontiguousarray(dLdC, np.float64)
+    dT = None if dLdT is None else np.ascontiguousarray(dLdT, np.float64)
+    lib().orc_backward_view(C.byref(k.p), _ptr(off), K, C.byref(c), C.byref(o), _ptr(dC), _ptr(dT),
+                            C.byref(gr))
+    return g
+
+
+def adam(p, g, m, v, lr, b1, b2, eps, step):
+    """In-place FP64 Adam on float64 arrays."""
+    for a in (p, g, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib().orc_adam(p.size, _ptr(p), _ptr(g), _ptr(m), _ptr(v), lr, b1, b2, eps, step)
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())

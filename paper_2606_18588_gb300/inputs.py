@@ -1,0 +1,238 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle, the tests and the bench.
+
+This module only draws numbers and arranges them: Gaussian scenes, cameras, target
+images and the k-d split that forms the K convex subsets.  It holds none of the
+rendering arithmetic (projection, binning, blending, composition, gradients).
+
+Layouts (all float32, C-contiguous):
+  means [N,3], log_scales [N,3], quats [N,4] as (w,x,y,z), opacity_logits [N],
+  sh [N,(deg+1)^2,3]  (coefficient-major, RGB innermost).
+Camera: world->camera rotation R (3x3, rows = camera right, down, forward), t (3),
+pinhole fx, fy, cx, cy, width, height, near.  Camera space is x right, y down, z forward.
+
+The synthetic recipes stand in for the paper's MatrixCity scenes (Sec. 5), which are
+not available; the scene shapes follow the workloads it describes (Sec. 5, Sec. 8.1).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# Real spherical-harmonic DC normalisation Y_00 = 1/(2 sqrt(pi)).  Only used to turn
+# a drawn RGB into the DC coefficient that reproduces it (colour = Y_00*dc + 0.5).
+_INV_Y00 = 2.0 * math.sqrt(math.pi)
+
+
+@dataclasses.dataclass
+class Scene:
+    means: np.ndarray
+    log_scales: np.ndarray
+    quats: np.ndarray
+    opacity_logits: np.ndarray
+    sh: np.ndarray
+    sh_degree: int
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    def subset(self, lo: int, hi: int) -> "Scene":
+        return Scene(self.means[lo:hi], self.log_scales[lo:hi], self.quats[lo:hi],
+                     self.opacity_logits[lo:hi], self.sh[lo:hi], self.sh_degree)
+
+    def take(self, idx: np.ndarray) -> "Scene":
+        return Scene(*(np.ascontiguousarray(a[idx]) for a in
+                       (self.means, self.log_scales, self.quats, self.opacity_logits, self.sh)),
+                     self.sh_degree)
+
+    def arrays(self):
+        return (self.means, self.log_scales, self.quats, self.opacity_logits, self.sh)
+
+
+@dataclasses.dataclass
+class Camera:
+    R: np.ndarray          # (3,3) float32, world -> camera rotation
+    t: np.ndarray          # (3,)  float32
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    width: int
+    height: int
+    near: float = 0.01
+
+    @property
+    def eye(self) -> np.ndarray:
+        """Camera centre in world coordinates (float64)."""
+        return -(self.R.astype(np.float64).T @ self.t.astype(np.float64))
+
+
+def n_sh_coeffs(deg: int) -> int:
+    return (deg + 1) * (deg + 1)
+
+
+def look_at(eye, target, world_up=(0.0, -1.0, 0.0)):
+    """Rotation/translation of a camera at `eye` looking at `target` (x right, y down, z forward)."""
+    eye = np.asarray(eye, np.float64)
+    f = np.asarray(target, np.float64) - eye
+    f /= np.linalg.norm(f)
+    r = np.cross(f, np.asarray(world_up, np.float64))
+    r /= np.linalg.norm(r)
+    d = np.cross(f, r)
+    R = np.stack([r, d, f]).astype(np.float32)
+    t = (-(R.astype(np.float64) @ eye)).astype(np.float32)
+    return R, t
+
+
+def pinhole(width: int, height: int, fov_x_deg: float, eye, target, near=0.01,
+            world_up=(0.0, -1.0, 0.0)) -> Camera:
+    R, t = look_at(eye, target, world_up)
+    fx = 0.5 * width / math.tan(math.radians(fov_x_deg) * 0.5)
+    return Camera(R, t, float(np.float32(fx)), float(np.float32(fx)),
+                  0.5 * width, 0.5 * height, int(width), int(height), float(near))
+
+
+def _quats(rng, n):
+    q = rng.standard_normal((n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    return q.astype(np.float32)
+
+
+def _sh(rng, n, deg, rgb):
+    c = n_sh_coeffs(deg)
+    sh = np.zeros((n, c, 3), np.float32)
+    sh[:, 0, :] = (rgb - 0.5) * _INV_Y00
+    if c > 1:
+        sh[:, 1:, :] = rng.normal(0.0, 0.2, (n, c - 1, 3))
+    return sh
+
+
+def uniform_scene(n: int, seed: int, sh_degree: int = 0, log_scale_mu=-3.5,
+                  log_scale_sigma=0.5, extent=1.0) -> Scene:
+    """Means ~ U[-extent,extent]^3, log-scales ~ N(mu, sigma), unit quaternions uniform
+    on S^3, opacity = sigmoid(N(0,1)), RGB ~ U[0,1] (the 10k-Gaussian plain-forward case)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    means = rng.uniform(-extent, extent, (n, 3)).astype(np.float32)
+    log_scales = rng.normal(log_scale_mu, log_scale_sigma, (n, 3)).astype(np.float32)
+    quats = _quats(rng, n)
+    logits = rng.standard_normal(n).astype(np.float32)
+    rgb = rng.uniform(0.0, 1.0, (n, 3))
+    return Scene(means, log_scales, quats, logits, _sh(rng, n, sh_degree, rgb), sh_degree)
+
+
+def cluster_scene(n: int, seed: int, sh_degree: int = 3, n_clusters: int = 64,
+                  box: float = 20.0, sigma_range=(0.5, 2.0), log_scale_sigma=0.5) -> Scene:
+    """Means from an equal-weight mixture of isotropic clusters inside a cube of side
+    `box` centred at the origin (points outside are redrawn); log-scale mean chosen so
+    that a Gaussian's scale is about a third of the mean spacing (V_box/N)^(1/3)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    half = 0.5 * box
+    centres = rng.uniform(-half, half, (n_clusters, 3))
+    sig = rng.uniform(sigma_range[0], sigma_range[1], n_clusters)
+    lab = rng.integers(0, n_clusters, n)
+    means = centres[lab] + sig[lab, None] * rng.standard_normal((n, 3))
+    bad = np.any(np.abs(means) > half, axis=1)
+    while bad.any():
+        k = int(bad.sum())
+        means[bad] = centres[lab[bad]] + sig[lab[bad], None] * rng.standard_normal((k, 3))
+        bad = np.any(np.abs(means) > half, axis=1)
+    means = means.astype(np.float32)
+    mu = math.log(0.33 * (box ** 3 / n) ** (1.0 / 3.0))
+    log_scales = rng.normal(mu, log_scale_sigma, (n, 3)).astype(np.float32)
+    quats = _quats(rng, n)
+    logits = rng.standard_normal(n).astype(np.float32)
+    rgb = rng.uniform(0.0, 1.0, (n, 3))
+    return Scene(means, log_scales, quats, logits, _sh(rng, n, sh_degree, rgb), sh_degree)
+
+
+def kd_partition(means: np.ndarray, K: int, axes=(0, 2)):
+    """Recursive median split into K (a power of two) axis-aligned boxes.
+
+    At every node the split axis is the one of `axes` with the largest extent of the
+    node's means; the node's Gaussians are ordered by (coordinate, index) and the left
+    child takes the first floor(n/2) (Sec. 8.1, partition strategy).  Returns the
+    permutation that makes subsets contiguous, the K+1 subset offsets, and each subset's
+    (lo, hi) split-plane box (infinite on unsplit sides).
+    """
+    if K < 1 or (K & (K - 1)) != 0:
+        raise ValueError("K must be a power of two")
+    n = means.shape[0]
+    m = means.astype(np.float64)
+    groups = [(np.arange(n), np.full(3, -np.inf), np.full(3, np.inf))]
+    while len(groups) < K:
+        nxt = []
+        for idx, lo, hi in groups:
+            ext = [m[idx, a].max() - m[idx, a].min() if idx.size else 0.0 for a in axes]
+            ax = axes[int(np.argmax(ext))]
+            order = np.lexsort((idx, m[idx, ax]))
+            idx = idx[order]
+            h = idx.size // 2
+            left, right = idx[:h], idx[h:]
+            if left.size and right.size:
+                plane = 0.5 * (m[left[-1], ax] + m[right[0], ax])
+            else:
+                plane = 0.0
+            lhi = hi.copy(); lhi[ax] = plane
+            rlo = lo.copy(); rlo[ax] = plane
+            nxt.append((np.sort(left), lo, lhi))
+            nxt.append((np.sort(right), rlo, hi))
+        groups = nxt
+    perm = np.concatenate([g[0] for g in groups]).astype(np.int64)
+    offsets = np.zeros(K + 1, np.int64)
+    offsets[1:] = np.cumsum([g[0].size for g in groups])
+    boxes = np.stack([np.stack([g[1], g[2]]) for g in groups])
+    return perm, offsets, boxes
+
+
+def orbit_cameras(n_views: int, seed: int, sizes, radius=25.0, height=(2.0, 10.0),
+                  fov_x_deg=60.0, centre=(0.0, 0.0, 0.0), near=0.01):
+    """Cameras on a seeded orbit around `centre` (world up is -y), looking at it.
+    `sizes` is a list of (width, height) cycled over the views."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cams = []
+    c = np.asarray(centre, np.float64)
+    for i in range(n_views):
+        phi = rng.uniform(0.0, 2.0 * math.pi)
+        h = rng.uniform(height[0], height[1])
+        eye = c + np.array([radius * math.cos(phi), -h, radius * math.sin(phi)])
+        w, hh = sizes[i % len(sizes)]
+        cams.append(pinhole(w, hh, fov_x_deg, eye, c, near))
+    return cams
+
+
+def random_image(height: int, width: int, seed: int) -> np.ndarray:
+    """Target image ~ U[0,1], planar [3,H,W] float32."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(0.0, 1.0, (3, height, width)).astype(np.float32)
+
+
+def plain_forward_case(seed: int = 0, n: int = 10_000):
+    """10k Gaussians, SH degree 0, means U[-1,1]^3, 256x256, fov 60 deg, eye at distance 3
+    looking at the origin, near 0.01, one subset."""
+    scene = uniform_scene(n, seed, 0)
+    cam = pinhole(256, 256, 60.0, (0.0, 0.0, -3.0), (0.0, 0.0, 0.0), 0.01)
+    return scene, cam
+
+
+def cluster_case(n: int, seed: int, K: int, n_views: int, sizes, sh_degree: int = 3):
+    """A cluster scene reordered so its K k-d subsets (split on x/z) are contiguous,
+    plus orbit cameras.  Returns (scene, offsets, boxes, cameras)."""
+    scene = cluster_scene(n, seed, sh_degree)
+    perm, offsets, boxes = kd_partition(scene.means, K)
+    scene = scene.take(perm)
+    cams = orbit_cameras(n_views, seed + 1, sizes)
+    return scene, offsets, boxes, cams
+
+
+# Named workloads (sizes follow the five configurations the hot path is quoted on).
+WORKLOADS = {
+    "plain_fwd_10k": dict(n=10_000, sh_degree=0, K=1, sizes=[(256, 256)], views=1),
+    "fwdbwd_1m_k4": dict(n=1_000_000, sh_degree=3, K=4, sizes=[(1920, 1080)], views=1),
+    "batched_10m_k8": dict(n=10_000_000, sh_degree=3, K=8,
+                           sizes=[(1600, 1064), (1280, 720)], views=16),
+    "train_120m_k32": dict(n=120_000_000, sh_degree=3, K=32, sizes=[(1920, 1080)], views=8),
+    "serve_20m_k8": dict(n=20_000_000, sh_degree=3, K=8,
+                         sizes=[(512, 512), (1280, 720), (1920, 1080), (3840, 2160)], views=0),
+}

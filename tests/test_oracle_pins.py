@@ -1,0 +1,453 @@
+"""Pins of the FP64 oracle to things other than itself (CPU only).
+
+Each test fixes a part of the oracle against a closed form, a library routine, brute
+force or finite differences, chosen so that a dropped term, a wrong sign or index or a
+transposed operand in the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2606_18588_gb300 import inputs as I
+
+Y00 = 0.5 / math.sqrt(math.pi)
+
+
+def _scene(means, log_scales, quats, logits, rgb=None, sh=None, deg=0):
+    n = len(means)
+    if sh is None:
+        sh = np.zeros((n, I.n_sh_coeffs(deg), 3), np.float32)
+        sh[:, 0, :] = (np.asarray(rgb, np.float64) - 0.5) / Y00
+    return I.Scene(np.asarray(means, np.float32).reshape(n, 3),
+                   np.asarray(log_scales, np.float32).reshape(n, 3),
+                   np.asarray(quats, np.float32).reshape(n, 4),
+                   np.asarray(logits, np.float32).reshape(n),
+                   np.asarray(sh, np.float32), deg)
+
+
+def _cam(W=64, H=48, fov=60.0, eye=(0.0, 0.0, -3.0)):
+    return I.pinhole(W, H, fov, eye, (0.0, 0.0, 0.0), 0.01)
+
+
+def _logit(o):
+    return math.log(o / (1.0 - o))
+
+
+# --------------------------------------------------------------------------- exp spec
+def test_exp_spec_within_3_ulp_of_exp():
+    x = np.linspace(-20.0, 12.0, 200001).astype(np.float32)
+    y = O.exp_spec(x).astype(np.float64)
+    ref = np.exp(x.astype(np.float64))
+    ulp = np.spacing(ref.astype(np.float32)).astype(np.float64)
+    assert np.max(np.abs(y - ref) / ulp) <= 3.0
+    assert O.exp_spec(np.array([0.0], np.float32))[0] == 1.0
+
+
+# --------------------------------------------------------------------------- SH basis
+def test_sh_basis_matches_scipy_real_harmonics():
+    sp = pytest.importorskip("scipy.special")
+    rng = np.random.default_rng(3)
+    d = rng.standard_normal((200, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    theta = np.arccos(np.clip(d[:, 2], -1, 1))
+    phi = np.arctan2(d[:, 1], d[:, 0])
+    ref = []
+    for l in range(4):
+        for m in range(-l, l + 1):
+            Y = sp.sph_harm_y(l, abs(m), theta, phi)  # complex, Condon-Shortley phase
+            if m > 0:
+                ref.append(math.sqrt(2.0) * Y.real)
+            elif m < 0:
+                ref.append(math.sqrt(2.0) * Y.imag)
+            else:
+                ref.append(Y.real)
+    ref = np.stack(ref, axis=1)
+    got = O.sh_basis(d)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12)
+
+
+def test_sh_basis_gradient_matches_finite_differences():
+    rng = np.random.default_rng(4)
+    d = rng.standard_normal((20, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    g = O.sh_basis(d, grad=True)
+    h = 1e-6
+    for e in range(3):
+        dp = d.copy(); dp[:, e] += h
+        dm = d.copy(); dm[:, e] -= h
+        fd = (O.sh_basis(dp) - O.sh_basis(dm)) / (2 * h)
+        np.testing.assert_allclose(g[:, :, e], fd, atol=1e-7)
+
+
+# --------------------------------------------------------------------------- closed forms
+def _closed_form_image(cam, u, v, Sig, o, c, depth, r):
+    """alpha-blend of one Gaussian with 2-D covariance Sig: C = c*alpha, T = 1-alpha."""
+    H, W = cam.height, cam.width
+    Q = np.linalg.inv(Sig)
+    py, px = np.mgrid[0:H, 0:W]
+    dx = px + 0.5 - u
+    dy = py + 0.5 - v
+    power = -0.5 * (Q[0, 0] * dx * dx + 2 * Q[0, 1] * dx * dy + Q[1, 1] * dy * dy)
+    alpha = np.minimum(0.99, o * np.exp(power))
+    inside = (np.abs(px + 0.5 - u) <= r) & (np.abs(py + 0.5 - v) <= r)
+    alpha = np.where(inside & (alpha >= 1.0 / 255.0), alpha, 0.0)
+    return c[:, None, None] * alpha, 1.0 - alpha, depth * alpha
+
+
+@pytest.mark.parametrize("case", ["iso", "aniso_rot", "offaxis", "offaxis_xz"])
+def test_single_gaussian_closed_form(case):
+    cam = _cam(64, 48)
+    f = cam.fx
+    o = 0.8
+    rgb = np.array([0.9, 0.4, 0.1])
+    z = 3.0
+    if case == "iso":
+        s = np.array([0.05, 0.05, 0.05]); mean = [0.0, 0.0, 0.0]; th = 0.0
+    elif case == "aniso_rot":
+        s = np.array([0.08, 0.02, 0.05]); mean = [0.0, 0.0, 0.0]; th = 0.7
+    elif case == "offaxis":
+        s = np.array([0.04, 0.04, 0.04]); mean = [0.3, 0.0, 0.0]; th = 0.0
+    else:
+        s = np.array([0.15, 0.01, 0.01]); mean = [0.8, 0.0, 0.0]; th = 0.0
+    q = [math.cos(th / 2), 0.0, 0.0, math.sin(th / 2)]  # rotation about the optical axis
+    if case == "offaxis_xz":
+        q = [math.cos(math.pi / 8), 0.0, math.sin(math.pi / 8), 0.0]  # 45 deg about y
+    sc = _scene([mean], [np.log(s)], [q], [_logit(o)], rgb=[rgb])
+    sf = np.exp(np.asarray(sc.log_scales[0], np.float64))  # the exact stored scale
+    x = float(sc.means[0, 0])
+    # Sigma2D = J R diag(s^2) R^T J^T + 0.3 I; the camera axes are the world axes here.
+    Rz = np.array([[math.cos(th), -math.sin(th), 0], [math.sin(th), math.cos(th), 0], [0, 0, 1]])
+    if case == "offaxis_xz":
+        c4 = math.cos(math.pi / 4)
+        Rz = np.array([[c4, 0, c4], [0, 1, 0], [-c4, 0, c4]])
+    Sig3 = Rz @ np.diag(sf ** 2) @ Rz.T
+    J = np.array([[f / z, 0.0, -f * x / z ** 2], [0.0, f / z, 0.0]])
+    Sig = J @ Sig3 @ J.T + 0.3 * np.eye(2)
+    u = f * x / z + cam.cx
+    v = cam.cy
+    lam = 0.5 * (Sig[0, 0] + Sig[1, 1]) + math.sqrt(max(0.1, (0.5 * (Sig[0, 0] - Sig[1, 1])) ** 2
+                                                      + Sig[0, 1] ** 2))
+    r = math.ceil(3.0 * math.sqrt(lam))
+    C, T, D = _closed_form_image(cam, u, v, Sig, o, rgb, z, r)
+    got = O.render(sc, cam, O.opts(tile=16, eps_T=0.0, eps_comp=0.0))
+    np.testing.assert_allclose(got["C"], C, atol=1e-6)
+    np.testing.assert_allclose(got["T"], T, atol=1e-6)
+    np.testing.assert_allclose(got["D"], D, atol=1e-5)
+    # the FP64 projection itself (conic = Sigma2D^{-1}, mean, depth)
+    pr = O.project(sc, cam)[0]
+    Q = np.linalg.inv(Sig)
+    np.testing.assert_allclose(pr[[0, 1]], [u, v], rtol=1e-6)
+    np.testing.assert_allclose(pr[[2, 3, 4]], [Q[0, 0], Q[0, 1], Q[1, 1]], rtol=1e-5)
+    np.testing.assert_allclose(pr[9], z, rtol=1e-6)
+
+
+def test_colour_dc_only_is_y00_times_dc_plus_half():
+    cam = _cam()
+    rng = np.random.default_rng(0)
+    rgb = rng.uniform(0, 1, (5, 3))
+    sc = _scene(rng.uniform(-0.5, 0.5, (5, 3)), np.full((5, 3), -3.0), [[1, 0, 0, 0]] * 5,
+                np.zeros(5), rgb=rgb)
+    pr = O.project(sc, cam)
+    np.testing.assert_allclose(pr[:, 6:9], rgb, atol=1e-6)
+
+
+def test_colour_degree1_closed_form():
+    # degree-1 colour = Y00*dc + 0.5 + k1*(-y*c1 + z*c2 - x*c3) at the unit viewing direction
+    cam = _cam()
+    sh = np.zeros((1, 4, 3), np.float32)
+    sh[0, 1] = [0.3, 0.0, 0.0]; sh[0, 2] = [0.0, 0.2, 0.0]; sh[0, 3] = [0.0, 0.0, -0.25]
+    sc = _scene([[0.4, -0.3, 0.5]], [[-3, -3, -3]], [[1, 0, 0, 0]], [0.0], sh=sh, deg=1)
+    d = sc.means[0].astype(np.float64) - cam.eye
+    d /= np.linalg.norm(d)
+    k1 = math.sqrt(3.0 / (4.0 * math.pi))
+    want = 0.5 + np.array([-k1 * d[1] * 0.3, k1 * d[2] * 0.2, -k1 * d[0] * -0.25])
+    np.testing.assert_allclose(O.project(sc, cam)[0, 6:9], np.maximum(want, 0.0), atol=1e-7)
+
+
+# --------------------------------------------------------------------------- brute force
+def _brute_force(sc, cam, eps_T=1e-4, amin=1.0 / 255.0, amax=0.99):
+    """Per pixel: gather every visible Gaussian whose rectangle holds it, order by
+    (FP32 depth bits, index), blend literally.  No tiles, no per-tile lists."""
+    vis, rect, db = O.bin(sc, cam)
+    pr = O.project(sc, cam)
+    H, W = cam.height, cam.width
+    C = np.zeros((3, H, W)); T = np.ones((H, W)); D = np.zeros((H, W))
+    order = sorted([i for i in range(sc.n) if vis[i]], key=lambda i: (int(db[i]), i))
+    for py in range(H):
+        for px in range(W):
+            t = 1.0
+            for i in order:
+                x0, x1, y0, y1 = rect[i]
+                if not (x0 <= px <= x1 and y0 <= py <= y1):
+                    continue
+                u, v, A, B, Cc, o = pr[i, :6]
+                dx, dy = px + 0.5 - u, py + 0.5 - v
+                power = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy
+                if power > 0:
+                    continue
+                a = min(amax, o * math.exp(power))
+                if a < amin:
+                    continue
+                if t * (1 - a) < eps_T:
+                    break
+                C[:, py, px] += pr[i, 6:9] * a * t
+                D[py, px] += pr[i, 9] * a * t
+                t *= 1 - a
+            T[py, px] = t
+    return C, T, D
+
+
+@pytest.mark.parametrize("n,seed,tile", [(1, 0, 8), (5, 1, 8), (20, 2, 16), (20, 3, 8)])
+def test_render_matches_brute_force(n, seed, tile):
+    rng = np.random.default_rng(seed)
+    means = rng.uniform(-0.4, 0.4, (n, 3))
+    if n >= 5:
+        means[1] = means[0]            # equal depth: exercises the index tie-break
+    sc = _scene(means, rng.normal(-2.8, 0.4, (n, 3)), rng.standard_normal((n, 4)),
+                rng.normal(1.0, 1.0, n), rgb=rng.uniform(0, 1, (n, 3)))
+    cam = _cam(40, 32)
+    Cb, Tb, Db = _brute_force(sc, cam)
+    got = O.render(sc, cam, O.opts(tile=tile))
+    np.testing.assert_allclose(got["C"], Cb, atol=1e-12)
+    np.testing.assert_allclose(got["T"], Tb, atol=1e-12)
+    np.testing.assert_allclose(got["D"], Db, atol=1e-12)
+
+
+def test_tile_lists_invariants_and_tile_size_independence():
+    sc, cam = I.plain_forward_case(5, n=2000)
+    vis, rect, db = O.bin(sc, cam)
+    ref = None
+    for B in (8, 16, 32):
+        start, lst = O.tile_lists(sc, cam, B)
+        tw = (cam.width + B - 1) // B
+        expect = sum((r[1] // B - r[0] // B + 1) * (r[3] // B - r[2] // B + 1)
+                     for r, v in zip(rect, vis) if v)
+        assert lst.size == expect
+        for t in range(start.size - 1):
+            seg = lst[start[t]:start[t + 1]]
+            tx, ty = t % tw, t // tw
+            for g in seg:
+                x0, x1, y0, y1 = rect[g]
+                assert x0 // B <= tx <= x1 // B and y0 // B <= ty <= y1 // B
+            keys = [(int(db[g]), int(g)) for g in seg]
+            assert keys == sorted(keys)
+        out = O.render(sc, cam, O.opts(tile=B))
+        if ref is None:
+            ref = out
+        else:
+            for k in ("C", "T", "D", "last", "ncontrib"):
+                assert np.array_equal(out[k], ref[k]), k
+
+
+def test_blend_identity_sum_alpha_T_equals_one_minus_T():
+    # with every colour equal to 1, C = sum_i alpha_i T_i = 1 - T exactly (Eq. 2-4)
+    sc, cam = I.plain_forward_case(7, n=3000)
+    sc.sh[:, 0, :] = np.float32(0.5 / Y00)
+    out = O.render(sc, cam)
+    for ch in range(3):
+        np.testing.assert_allclose(out["C"][ch], 1.0 - out["T"], atol=1e-12)
+    assert out["T"].min() >= 0.0 and out["T"].max() <= 1.0
+
+
+def test_nearplane_and_degenerate_culls():
+    cam = _cam()
+    sc = _scene([[0, 0, -3.0 + 0.005], [0, 0, -3.0 + 0.02], [0, 0, 0.0], [5e3, 0, 0.0]],
+                [[-3] * 3, [-3] * 3, [-3] * 3, [-3] * 3],
+                [[1, 0, 0, 0], [1, 0, 0, 0], [0, 0, 0, 0], [1, 0, 0, 0]], [0, 0, 0, 0],
+                rgb=[[1, 1, 1]] * 4)
+    vis, rect, db = O.bin(sc, cam)
+    assert list(vis) == [0, 1, 0, 0]  # behind near, kept, zero quaternion, off-image
+
+
+# --------------------------------------------------------------------------- composite
+def _slab_scene(seed, K=3, per=40):
+    """K groups at disjoint depth slabs with a gap far above 3 sigma: separable pixels."""
+    rng = np.random.default_rng(seed)
+    means, ls = [], []
+    for k in range(K):
+        m = rng.uniform(-0.5, 0.5, (per, 3))
+        m[:, 2] = -0.8 + 0.8 * k + rng.uniform(-0.15, 0.15, per)
+        means.append(m)
+        ls.append(rng.normal(-3.2, 0.2, (per, 3)))
+    n = K * per
+    sc = _scene(np.concatenate(means), np.concatenate(ls), rng.standard_normal((n, 4)),
+                rng.normal(0.5, 1.0, n), rgb=rng.uniform(0, 1, (n, 3)))
+    offsets = np.arange(K + 1) * per
+    return sc, offsets
+
+
+def test_composite_equals_monolithic_on_separable_scene():
+    sc, off = _slab_scene(11)
+    cam = _cam(48, 40)
+    o = O.opts(eps_T=0.0, eps_comp=0.0)
+    comp = O.render_view(sc, off, cam, o)
+    mono = O.render_view(sc, np.array([0, sc.n]), cam, o)
+    np.testing.assert_allclose(comp["image"], mono["image"], atol=1e-12)
+    np.testing.assert_allclose(comp["T"], mono["T"], atol=1e-12)
+    # a shuffled subset order must give the same image: order comes from the depth keys
+    perm = [2, 0, 1]
+    idx = np.concatenate([np.arange(off[k], off[k + 1]) for k in perm])
+    sc2 = sc.take(idx)
+    comp2 = O.render_view(sc2, off, cam, o)
+    np.testing.assert_allclose(comp2["image"], mono["image"], atol=1e-12)
+
+
+def test_composite_termination_bound():
+    sc, off = _slab_scene(12)
+    sc.opacity_logits[:] = 3.0
+    cam = _cam(48, 40)
+    exact = O.render_view(sc, np.array([0, sc.n]), cam, O.opts(eps_T=0.0, eps_comp=0.0))
+    comp = O.render_view(sc, off, cam, O.opts(eps_T=1e-4, eps_comp=1e-4))
+    err = np.abs(comp["image"] - exact["image"]).max()
+    assert err <= 3e-4  # omitted light is at most about eps per cut, times max colour (<= 1)
+
+
+def test_composite_single_subset_is_identity_plus_background():
+    rng = np.random.default_rng(2)
+    Cp = rng.uniform(0, 0.5, (1, 3, 8, 8)); Tp = rng.uniform(0, 1, (1, 8, 8))
+    Dp = rng.uniform(1, 2, (1, 8, 8))
+    out = O.composite(Cp, Tp, Dp, O.opts(eps_comp=0.0, bg=(0.1, 0.2, 0.3)))
+    np.testing.assert_allclose(out["image"], Cp[0] + np.array([0.1, 0.2, 0.3])[:, None, None] * Tp[0])
+    np.testing.assert_allclose(out["T"], Tp[0])
+
+
+def test_composite_is_the_over_operator_in_key_order():
+    # (C,T) over (C',T') = (C + T C', T T'), applied in increasing D/(1-T); associative
+    rng = np.random.default_rng(5)
+    K, H, W = 4, 6, 7
+    Tp = rng.uniform(0.05, 0.95, (K, H, W))
+    Cp = rng.uniform(0, 1, (K, 3, H, W)) * (1 - Tp)[:, None]
+    z = rng.uniform(1, 10, (K, H, W))
+    Dp = z * (1 - Tp)
+    out = O.composite(Cp, Tp, Dp, O.opts(eps_comp=0.0))
+    order = np.argsort(z, axis=0, kind="stable")
+    for py in range(H):
+        for px in range(W):
+            ms = order[:, py, px]
+            # right fold
+            c, t = np.zeros(3), 1.0
+            for m in ms[::-1]:
+                c = Cp[m, :, py, px] + Tp[m, py, px] * c
+                t = Tp[m, py, px] * t
+            np.testing.assert_allclose(out["image"][:, py, px], c, atol=1e-12)
+            np.testing.assert_allclose(out["T"][py, px], t, atol=1e-12)
+
+
+def test_kd_partition_convex_boxes_and_balance():
+    sc = I.cluster_scene(4096, 3, 0)
+    perm, off, boxes = I.kd_partition(sc.means, 8)
+    assert sorted(perm.tolist()) == list(range(4096))
+    assert np.all(np.diff(off) == 512)
+    m = sc.means[perm].astype(np.float64)
+    for k in range(8):
+        seg = m[off[k]:off[k + 1]]
+        lo, hi = boxes[k]
+        assert np.all(seg >= lo - 1e-9) and np.all(seg <= hi + 1e-9)
+        assert np.all(np.isinf(lo[1])) and np.all(np.isinf(hi[1]))  # y is never split
+
+
+# --------------------------------------------------------------------------- finite differences
+def _signature(sc, off, cam, o):
+    vis, rect, db = O.bin(sc, cam)
+    parts = []
+    for k in range(len(off) - 1):
+        r = O.render(sc.subset(off[k], off[k + 1]), cam, o)
+        parts.append((r["last"].copy(), r["ncontrib"].copy()))
+    v = O.render_view(sc, off, cam, o)
+    key = np.where(v["Tp"] < 1, v["Dp"] / np.maximum(1 - v["Tp"], 1e-300), np.inf)
+    order = np.argsort(key, axis=0, kind="stable")
+    return (vis.tobytes(), rect.tobytes(), b"".join(a.tobytes() + b.tobytes() for a, b in parts),
+            order.tobytes())
+
+
+def _loss(sc, off, cam, o, wC, wT):
+    v = O.render_view(sc, off, cam, o)
+    return float(np.sum(wC * v["image"]) + np.sum(wT * v["T"]))
+
+
+@pytest.mark.parametrize("deg", [0, 3])
+def test_backward_matches_central_finite_differences(deg):
+    rng = np.random.default_rng(20 + deg)
+    n = 24
+    means = rng.uniform(-0.5, 0.5, (n, 3))
+    sh = np.zeros((n, I.n_sh_coeffs(deg), 3), np.float32)
+    sh[:, 0, :] = (rng.uniform(0.2, 0.8, (n, 3)) - 0.5) / Y00
+    if deg:
+        sh[:, 1:, :] = rng.normal(0, 0.2, (n, I.n_sh_coeffs(deg) - 1, 3))
+    sc = _scene(means, rng.normal(-2.6, 0.3, (n, 3)), rng.standard_normal((n, 4)),
+                rng.normal(0.0, 1.0, n), sh=sh, deg=deg)
+    perm, off, _ = I.kd_partition(sc.means, 2)
+    sc = sc.take(perm)
+    cam = I.pinhole(40, 36, 60.0, (0.3, -0.2, -2.2), (0.0, 0.0, 0.0), 0.01)
+    # a camera-axis clamp case: one Gaussian far to the side
+    o = O.opts(eps_T=1e-4, eps_comp=1e-4)
+    wC = rng.standard_normal((3, cam.height, cam.width))
+    wT = rng.standard_normal((cam.height, cam.width))
+    grads = O.backward_view(sc, off, cam, wC, wT, o)
+    base_sig = _signature(sc, off, cam, o)
+    arrays = list(sc.arrays())
+    checked = 0
+    for ai, (arr, g) in enumerate(zip(arrays, grads)):
+        flat = arr.reshape(-1)
+        gflat = g.reshape(-1)
+        idx = rng.choice(flat.size, size=min(flat.size, 40), replace=False)
+        for j in idx:
+            x0 = float(flat[j])
+            h = 1e-6 * max(1.0, abs(x0))
+            vals = []
+            ok = True
+            for sgn in (1, -1):
+                sc2 = I.Scene(*[a.astype(np.float64).copy() for a in arrays], sc.sh_degree)
+                sc2.arrays()[ai].reshape(-1)[j] = x0 + sgn * h
+                if _signature(sc2, off, cam, o) != base_sig:
+                    ok = False
+                    break
+                vals.append(_loss(sc2, off, cam, o, wC, wT))
+            if not ok:
+                continue
+            fd = (vals[0] - vals[1]) / (2 * h)
+            scale = max(1e-3, np.abs(gflat).max() * 1e-3)
+            assert abs(fd - gflat[j]) <= 1e-4 * max(abs(fd), scale), (ai, j, fd, gflat[j])
+            checked += 1
+    assert checked >= 100
+
+
+# --------------------------------------------------------------------------- Adam
+def test_adam_matches_torch_optim_adam():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(9)
+    p0 = rng.standard_normal(1000)
+    p = p0.copy(); m = np.zeros_like(p); v = np.zeros_like(p)
+    tp = torch.tensor(p0.copy(), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=1e-2, betas=(0.9, 0.999), eps=1e-15)
+    for step in range(1, 6):
+        g = rng.standard_normal(1000)
+        O.adam(p, g, m, v, 1e-2, 0.9, 0.999, 1e-15, step)
+        tp.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+    np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-13, atol=1e-15)
+
+
+# --------------------------------------------------------------------------- regression
+def test_oracle_regression_fixture():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_regression_small.json")
+    with open(path) as f:
+        g = json.load(f)
+    arr = g["inputs"]
+    sc = I.Scene(*(np.asarray(arr[k], np.float32) for k in
+                   ("means", "log_scales", "quats", "opacity_logits", "sh")), g["sh_degree"])
+    c = g["camera"]
+    cam = I.Camera(np.asarray(c["R"], np.float32), np.asarray(c["t"], np.float32), c["fx"],
+                   c["fy"], c["cx"], c["cy"], c["width"], c["height"], c["near"])
+    o = O.opts(tile=8)
+    view = O.render_view(sc, np.asarray(g["offsets"]), cam, o)
+    np.testing.assert_allclose(view["image"], np.asarray(g["image"]), atol=1e-12)
+    np.testing.assert_allclose(view["T"], np.asarray(g["T"]), atol=1e-12)
+    gr = O.backward_view(sc, np.asarray(g["offsets"]), cam, np.ones((3, cam.height, cam.width)),
+                         None, o)
+    np.testing.assert_allclose(gr[0], np.asarray(g["grad_means"]), rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(gr[3], np.asarray(g["grad_opacity_logits"]), rtol=1e-9, atol=1e-12)
