@@ -1,0 +1,258 @@
+/*
+ * splx.h - C ABI of the GB300-native Splaxel hot path (libsplx.so).
+ *
+ * The library renders K Gaussian subsets of a 3D Gaussian Splatting scene into partial
+ * pixel images (premultiplied colour C^m, transmittance T^m, alpha-weighted depth D^m;
+ * Sec. 4.1 "Local Rendering", Eq. 3-4), composites them per pixel in depth order into
+ * the final image (Sec. 4.1 "Global Composition", Eq. 5), back-propagates a pixel loss
+ * gradient through both steps to the Gaussian parameters (Sec. 4.1 "Backward
+ * Propagation", Eq. 6-7) and applies Adam (Sec. 2, step 4 "Parameter Optimization").
+ * The K subsets the paper places on K GPUs are all resident on one device here.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers are DEVICE pointers unless a comment says "host".  The caller owns every
+ *     buffer it passes (parameters, gradients, Adam moments, images, partials) and must
+ *     keep it alive until the stream work completes.  The library owns its scratch and
+ *     the opaque objects it returns.
+ *   - Every call is asynchronous on `stream` (NULL = legacy default stream) unless its
+ *     comment says it synchronises.  No call throws, aborts or traps; each returns a
+ *     status code below.  Errors detected on the device (capacity overflow, a bounded
+ *     wait that gave up) set a device status word read by splx_device_status().
+ *   - Gaussian parameters are FP32 structure-of-arrays: means [n][3], log_scales [n][3],
+ *     quats [n][4] as (w,x,y,z) (normalised on use), opacity_logits [n] (opacity =
+ *     sigmoid), sh [n][(deg+1)^2][3] real spherical-harmonic coefficients (colour =
+ *     max(0, SH(view direction) + 0.5)).  Theta_i = {mu, R, S, o, c} of Sec. 2.
+ *   - Images are planar FP32: rgb [3][H][W], T [H][W]; pixel (x, y) has centre
+ *     (x + 0.5, y + 0.5).  Camera space is x right, y down, z forward.
+ *   - Gradients are ACCUMULATED (+=) into the caller's arrays, so K subsets and many
+ *     views can share one gradient buffer; zero it before a step.
+ */
+#ifndef SPLX_H
+#define SPLX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------ */
+#define SPLX_OK 0
+#define SPLX_ERR_INVALID (-1)   /* bad argument (null pointer, size, alignment, option) */
+#define SPLX_ERR_BUDGET (-2)    /* the context's HBM budget would be exceeded */
+#define SPLX_ERR_CAPACITY (-3)  /* a pair buffer overflowed on the device; re-plan larger */
+#define SPLX_ERR_CUDA (-4)      /* a CUDA runtime call failed (see splx_last_cuda_error) */
+#define SPLX_ERR_TIMEOUT (-5)   /* a bounded device wait gave up */
+#define SPLX_ERR_STATE (-6)     /* object used in the wrong state (e.g. stale forward state) */
+
+typedef struct CUstream_st* splx_stream_t; /* a cudaStream_t */
+typedef struct splx_ctx_s* splx_ctx_t;     /* library-owned context (scratch pool, budget) */
+typedef struct splx_state_s* splx_state_t; /* forward state of one (view, subset) render */
+typedef struct splx_batch_s* splx_batch_t; /* planned batch of V views x K subsets */
+typedef struct splx_graph_s* splx_graph_t; /* captured CUDA graph of library calls */
+
+/* One Gaussian subset Q^m (read-only parameters). */
+typedef struct {
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* opacity_logits;
+  const float* sh;
+  int64_t n;          /* Gaussians in the subset, < 2^31 */
+  int32_t sh_degree;  /* 0..3 */
+} splx_gaussians;
+
+/* Mutable parameter arrays with the same layout: gradients (+=), Adam moments, or the
+ * parameters being optimised. */
+typedef struct {
+  float* means;
+  float* log_scales;
+  float* quats;
+  float* opacity_logits;
+  float* sh;
+  int64_t n;
+  int32_t sh_degree;
+} splx_params;
+
+/* Pinhole camera (host struct).  R is the world->camera rotation (row-major), t the
+ * translation: x_cam = R x_world + t.  fx, fy, cx, cy in pixels. */
+typedef struct {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t width, height; /* 1..16384 */
+  float near_plane;      /* Gaussians with camera depth <= near_plane are culled */
+} splx_camera;
+
+/* Rendering options (host struct). */
+typedef struct {
+  int32_t tile;    /* tile side: 8, 16 or 32; results do not depend on it */
+  float eps_T;     /* a pixel stops before the Gaussian that would take T below eps_T */
+  float eps_comp;  /* composition skips subsets once the prefix transmittance < eps_comp
+                      (the saturation threshold, 1e-4 in Sec. 5.4) */
+  float alpha_min; /* Gaussians with alpha < alpha_min are skipped (1/255) */
+  float alpha_max; /* alpha is clamped to alpha_max (0.99) */
+  float bg[3];     /* background colour added behind the composite */
+} splx_opts;
+
+/* Partial pixel image of one (view, subset): Eq. 3-4.  rgb = C^m premultiplied
+ * [3][H][W]; T = T^m [H][W]; depth = D^m = sum_i d_i alpha_i T_i [H][W] (Eq. 4 read with
+ * the alpha_i factor); last = position of the last blended entry in the subset's sorted
+ * tile list, -1 if none [H][W] (used by the backward to recompute the blend). */
+typedef struct {
+  float* rgb;
+  float* T;
+  float* depth;
+  int32_t* last;
+} splx_partial;
+
+/* Adam hyper-parameters (host struct); torch.optim.Adam semantics. */
+typedef struct {
+  float lr[6]; /* means, log_scales, quats, opacity_logits, sh degree-0, sh higher */
+  float beta1, beta2, eps;
+  int32_t zero_grad; /* nonzero: the gradient arrays are set to 0 after they are read */
+} splx_adam;
+
+/* ---- context ------------------------------------------------------------------ */
+
+/* Creates a context on CUDA device `device` whose scratch never exceeds
+ * `hbm_budget_bytes` (0 = no cap).  Scratch comes from a stream-ordered pool the
+ * context owns.  Returns SPLX_ERR_INVALID for a bad device. */
+int splx_create(splx_ctx_t* out, int device, size_t hbm_budget_bytes);
+/* Synchronises the device, frees all scratch and the context. */
+int splx_destroy(splx_ctx_t ctx);
+/* Scratch bytes currently held by the context (host value). */
+size_t splx_scratch_bytes(splx_ctx_t ctx);
+
+/* ---- per-view entry points (Sec. 4.1) ------------------------------------------- */
+
+/* Local rendering of one subset for one view (Sec. 4.1, Eq. 3-4; steps 1-3 of Sec. 2):
+ * projection with EWA covariance, SH colour, 16x16 (opts->tile) binning, radix sort by
+ * (tile, depth) with the Gaussian index as tie-break, front-to-back alpha blending into
+ * `out` (sized to cam->width x cam->height).  If state_out is non-NULL the projected
+ * records and sorted lists are kept for splx_backward and must be released with
+ * splx_state_release.  Synchronises once (to size the pair list). */
+int splx_render_partial(splx_ctx_t ctx, const splx_gaussians* subset, const splx_camera* cam,
+                        const splx_opts* opts, const splx_partial* out, splx_state_t* state_out,
+                        splx_stream_t stream);
+
+/* Global composition (Sec. 4.1, Eq. 5): per pixel, orders the K partials by the
+ * normalised depth D^m/(1-T^m) (ties to the lower index, empty subsets last) and
+ * accumulates C = sum_m C^m prod_{k before m} T^k + bg * prod T, skipping the rest once
+ * the prefix product falls below opts->eps_comp.  parts is a host array of K partials
+ * (device planes).  out_rgb [3][H][W]; out_T [H][W] (nullable) = prefix product. */
+int splx_composite(splx_ctx_t ctx, const splx_partial* parts, int32_t K, int32_t width,
+                   int32_t height, const splx_opts* opts, float* out_rgb, float* out_T,
+                   splx_stream_t stream);
+
+/* Backward of one view (Sec. 4.1, Eq. 6-7, then the chain through Eq. 1-4 and the
+ * projection): given dL/dC of the composited image [3][H][W] and optionally dL/dT of
+ * out_T [H][W] (nullable), adds dL/dtheta for every Gaussian of the K subsets into
+ * grads[k] (host array of K; device arrays sized like the subsets).  subsets, parts and
+ * states are the host arrays used in the forward. */
+int splx_backward(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
+                  const splx_camera* cam, const splx_partial* parts, const splx_state_t* states,
+                  const float* dL_drgb, const float* dL_dT, const splx_opts* opts,
+                  const splx_params* grads, splx_stream_t stream);
+
+/* Diagnostic export of a forward state (synchronises): the pair count and tile count
+ * (host, either nullable), then - for each non-NULL device buffer - the per-tile
+ * [start, end) ranges into the sorted list (ranges_out: n_tiles x 2 uint32), the sorted
+ * Gaussian indices (vals_out: n_pairs uint32) and the 64-byte projected records
+ * (rec_out: n x 16 floats: u, v, qa, qb | qc, opacity, depth, rect_x | r, g, b, rect_y |
+ * 0,0,0,0 where rect_x = x0 | x1 << 16 and rect_y = y0 | y1 << 16 as bit patterns and
+ * (qa, qb, qc) = -log2(e) * (A/2, B, C/2) for the conic (A, B, C); a culled Gaussian has
+ * x0 = 0xFFFF > x1).  Tiles are numbered row-major. */
+int splx_state_export(splx_ctx_t ctx, splx_state_t state, int64_t* n_pairs, int64_t* n_tiles,
+                      uint32_t* ranges_out, uint32_t* vals_out, float* rec_out,
+                      splx_stream_t stream);
+
+/* Releases a forward state (stream-ordered). */
+int splx_state_release(splx_ctx_t ctx, splx_state_t state, splx_stream_t stream);
+
+/* Adam step on one parameter set (Sec. 2 step 4; the paper names no optimiser, torch
+ * Adam semantics are used): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr * (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps), per-group lr. */
+int splx_step(splx_ctx_t ctx, const splx_params* p, const splx_params* g, const splx_params* m,
+              const splx_params* v, const splx_adam* hp, int64_t step, splx_stream_t stream);
+
+/* splx_step with the step number on the device: *step_dev (device int64) is incremented
+ * first and the update uses the new value, so a CUDA graph holding this call advances
+ * the bias correction on every replay. */
+int splx_step_device(splx_ctx_t ctx, const splx_params* p, const splx_params* g,
+                     const splx_params* m, const splx_params* v, const splx_adam* hp,
+                     int64_t* step_dev, splx_stream_t stream);
+
+/* L1 photometric loss (Sec. 2 step 4, the L_RGB term): loss_out[0] = mean |img - target|
+ * over n elements and dL_dimg = sign(img - target)/n (sign(0) = 0).  dL_dimg nullable.
+ * loss_out is a device float (overwritten). */
+int splx_loss_l1(splx_ctx_t ctx, const float* img, const float* target, int64_t n,
+                 float* loss_out, float* dL_dimg, splx_stream_t stream);
+
+/* ---- batched path: V views x K subsets per launch (conflict-free view consolidation
+ *      of Sec. 4.3 in spirit: many independent views run in the same kernels) ------- */
+
+/* Plans a batch.  subsets (host array of K) share one SH degree; cams (host array of
+ * V).  Each view keeps its resolution for the life of the batch; poses may change with
+ * splx_batch_set_cameras.  pair_capacity = max (Gaussian, tile) pairs the batch holds;
+ * 0 = measure once now (synchronises) and add 25% headroom.  The batch owns scratch for
+ * V*K partial images, the projected records and the pair lists; it reads parameters
+ * through the subset pointers on every run. */
+int splx_batch_create(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
+                      const splx_camera* cams, int32_t V, const splx_opts* opts,
+                      int64_t pair_capacity, splx_batch_t* out, splx_stream_t stream);
+/* Replaces the V camera poses (resolutions must be unchanged); host cams are copied
+ * through a pinned staging buffer, so the call is capturable. */
+int splx_batch_set_cameras(splx_batch_t b, const splx_camera* cams, int32_t V,
+                           splx_stream_t stream);
+/* Offsets (in floats) of view v's image inside the concatenated outputs: rgb at
+ * rgb_off[v] (3*H_v*W_v floats), T at pix_off[v]; host arrays of V+1 entries each. */
+int splx_batch_layout(splx_batch_t b, int64_t* rgb_off, int64_t* pix_off);
+/* Forward of all V views: local render of every (view, subset) then composition.
+ * out_rgb / out_T are the concatenated images (layout from splx_batch_layout).  Never
+ * synchronises; capturable once the batch exists. */
+int splx_batch_forward(splx_batch_t b, float* out_rgb, float* out_T, splx_stream_t stream);
+/* Backward of the last forward: dL_drgb / dL_dT (nullable) concatenated like the
+ * outputs; gradients added into grads[k] (host array of K).  Capturable. */
+int splx_batch_backward(splx_batch_t b, const float* dL_drgb, const float* dL_dT,
+                        const splx_params* grads, splx_stream_t stream);
+/* Total pairs of the last forward and the device status word (synchronises).  Returns
+ * SPLX_ERR_CAPACITY if the pair list overflowed (its forward output is invalid). */
+int splx_batch_status(splx_batch_t b, int64_t* pairs_out, splx_stream_t stream);
+int splx_batch_destroy(splx_batch_t b);
+/* Per-kernel timing (off by default).  When enabled the batch records CUDA events around
+ * each of its kernels; inside a captured graph they become event nodes, so every replay
+ * re-records them.  splx_batch_kernel_times waits for the last run's final event and
+ * writes 10 durations in ms (host array): project, scan, emit, sort, ranges, raster_fwd,
+ * composite, composite_bwd, raster_bwd, project_bwd. */
+int splx_batch_set_timing(splx_batch_t b, int enable);
+int splx_batch_kernel_times(splx_batch_t b, float* ms_out);
+/* Work counters of the last run (synchronises): out[0] = (Gaussian, tile) pairs,
+ * out[1] = list entries examined by the forward rasteriser over all pixels, out[2] =
+ * Gaussians blended, out[3] = list entries examined by the backward rasteriser. */
+int splx_batch_counters(splx_batch_t b, int64_t* out, splx_stream_t stream);
+
+/* ---- CUDA graphs of library calls --------------------------------------------- */
+/* Begins capturing `stream` (thread-local mode).  Any capturable splx_* calls issued
+ * until splx_graph_end become one graph. */
+int splx_graph_begin(splx_ctx_t ctx, splx_stream_t stream);
+int splx_graph_end(splx_ctx_t ctx, splx_stream_t stream, splx_graph_t* out);
+int splx_graph_launch(splx_graph_t g, splx_stream_t stream);
+int splx_graph_destroy(splx_graph_t g);
+
+/* ---- diagnostics ---------------------------------------------------------------- */
+/* Synchronises `stream`, returns and clears the context's device status word
+ * (SPLX_OK, SPLX_ERR_CAPACITY or SPLX_ERR_TIMEOUT). */
+int splx_device_status(splx_ctx_t ctx, splx_stream_t stream);
+/* Text of a status code (static storage). */
+const char* splx_strerror(int status);
+/* Last CUDA error string seen by the library in this thread (static storage). */
+const char* splx_last_cuda_error(void);
+/* Number of kernel launches issued by the library since the context was created. */
+int64_t splx_launch_count(splx_ctx_t ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPLX_H */

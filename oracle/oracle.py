@@ -78,7 +78,7 @@ def lib():
             _lib.orc_render.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
             _lib.orc_composite.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P, P, P]
             _lib.orc_render_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P, P, P, P]
-            _lib.orc_backward_view.argtypes = [P, P, C.c_int32, P, P, P, P, P]
+            _lib.orc_backward_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P]
             _lib.orc_adam.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_double,
                                       C.c_double, C.c_int64]
             _lib.orc_num_threads.restype = C.c_int
@@ -216,8 +216,9 @@ def render_view(scene, offsets, cam, o: Opts | None = None, tile_mask=None, sepa
     return dict(image=out, T=To, Cp=Cp, Tp=Tp, Dp=Dp, amb=amb, sep=sep, evaluated=int(st[0]))
 
 
-def backward_view(scene, offsets, cam, dLdC, dLdT=None, o: Opts | None = None):
-    """Gradients (float64) of sum(dLdC*C) + sum(dLdT*T) w.r.t. every parameter array."""
+def backward_view(scene, offsets, cam, dLdC, dLdT=None, o: Opts | None = None, tile_mask=None):
+    """Gradients (float64) of sum(dLdC*C) + sum(dLdT*T) w.r.t. every parameter array
+    (restricted to the pixels of tiles where tile_mask is nonzero, if given)."""
     o = o or opts()
     k = _Keep(scene)
     c = camera(cam)
@@ -227,8 +228,9 @@ def backward_view(scene, offsets, cam, dLdC, dLdT=None, o: Opts | None = None):
     gr = Grads(*(a.ctypes.data_as(_dp) for a in g))
     dC = np.ascontiguousarray(dLdC, np.float64)
     dT = None if dLdT is None else np.ascontiguousarray(dLdT, np.float64)
+    tm = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8)
     lib().orc_backward_view(C.byref(k.p), _ptr(off), K, C.byref(c), C.byref(o), _ptr(dC), _ptr(dT),
-                            C.byref(gr))
+                            _ptr(tm), C.byref(gr))
     return g
 
 

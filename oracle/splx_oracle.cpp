@@ -652,9 +652,11 @@ int orc_render_view(const orc_params* p, const int64_t* offsets, int32_t K, cons
 // Backward of one view [Eq. 6-7 and the chain through Eq. 1-4 and the projection].
 // dLdC [3][H][W] and dLdT [H][W] (nullable) are the loss gradients w.r.t. the composited
 // image and total transmittance.  Gradients are written (not accumulated) to g.
+// tile_mask (nullable) restricts the adjoint to pixels of tiles with a nonzero entry,
+// as if dLdC and dLdT were zero elsewhere.
 int orc_backward_view(const orc_params* p, const int64_t* offsets, int32_t K,
                       const orc_camera* cam, const orc_opts* o, const double* dLdC,
-                      const double* dLdT, const orc_grads* gr) {
+                      const double* dLdT, const uint8_t* tile_mask, const orc_grads* gr) {
   const int W = cam->width, H = cam->height, B = o->tile;
   const int64_t HW = (int64_t)W * H;
   const int nc = (p->sh_degree + 1) * (p->sh_degree + 1);
@@ -663,20 +665,20 @@ int orc_backward_view(const orc_params* p, const int64_t* offsets, int32_t K,
   for (int m = 0; m < K; ++m) {
     orc_params q = slice(*p, offsets[m], offsets[m + 1]);
     subs[m] = prepare(q, *cam, B);
-    orc_render(&q, cam, o, nullptr, C.data() + (size_t)m * 3 * HW, T.data() + (size_t)m * HW,
+    orc_render(&q, cam, o, tile_mask, C.data() + (size_t)m * 3 * HW, T.data() + (size_t)m * HW,
                D.data() + (size_t)m * HW, nullptr, nullptr, nullptr, nullptr);
   }
-  // per-Gaussian 2-D gradients: u, v, A, B, C, o, r, g, b
+  // per-Gaussian 2-D gradients: u, v, A, B, C, o, r, g, b (threads add atomically)
   std::vector<double> g2((size_t)p->n * 9, 0.0);
   const int tw = (W + B - 1) / B, th = (H + B - 1) / B;
 #pragma omp parallel
   {
-    std::vector<double> g2l((size_t)p->n * 9, 0.0);
     std::vector<Frag> fr;
     std::vector<double> Tm(K), Dm(K), gT(K), gC((size_t)K * 3), Pj(K + 1);
     std::vector<int> ord(K);
 #pragma omp for schedule(dynamic, 1)
     for (int t = 0; t < tw * th; ++t) {
+      if (tile_mask && !tile_mask[t]) continue;
       const int tx = t % tw, ty = t / tw;
       for (int py = ty * B; py < std::min(H, (ty + 1) * B); ++py)
         for (int px = tx * B; px < std::min(W, (tx + 1) * B); ++px) {
@@ -724,24 +726,27 @@ int orc_backward_view(const orc_params* p, const int64_t* offsets, int32_t K,
               for (int ch = 0; ch < 3; ++ch)
                 ga += gC[3 * m + ch] * (q.col[ch] * f.T - Bc[ch] / (1.0 - f.alpha));
               ga += gT[m] * (-Tf / (1.0 - f.alpha));
-              double* G = g2l.data() + (size_t)(offsets[m] + f.g) * 9;
-              for (int ch = 0; ch < 3; ++ch) G[6 + ch] += gC[3 * m + ch] * f.alpha * f.T;
+              double add[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+              for (int ch = 0; ch < 3; ++ch) add[6 + ch] = gC[3 * m + ch] * f.alpha * f.T;
               if (!f.clamped) {
-                G[5] += ga * f.ex;
+                add[5] = ga * f.ex;
                 const double gp = ga * f.alpha;
-                G[0] += (q.A * f.dx + q.B * f.dy) * gp;
-                G[1] += (q.C * f.dy + q.B * f.dx) * gp;
-                G[2] += -0.5 * f.dx * f.dx * gp;
-                G[3] += -f.dx * f.dy * gp;
-                G[4] += -0.5 * f.dy * f.dy * gp;
+                add[0] = (q.A * f.dx + q.B * f.dy) * gp;
+                add[1] = (q.C * f.dy + q.B * f.dx) * gp;
+                add[2] = -0.5 * f.dx * f.dx * gp;
+                add[3] = -f.dx * f.dy * gp;
+                add[4] = -0.5 * f.dy * f.dy * gp;
+              }
+              double* G = g2.data() + (size_t)(offsets[m] + f.g) * 9;
+              for (int e = 0; e < 9; ++e) {
+#pragma omp atomic
+                G[e] += add[e];
               }
               for (int ch = 0; ch < 3; ++ch) Bc[ch] += q.col[ch] * f.alpha * f.T;
             }
           }
         }
     }
-#pragma omp critical
-    for (size_t i = 0; i < g2.size(); ++i) g2[i] += g2l[i];
   }
   // projection adjoint per Gaussian
   double Rc[9];

@@ -1,0 +1,951 @@
+// C ABI of libsplx (declared in include/splx.h): context, per-view entry points, the
+// batched V x K plan, CUDA-graph helpers and diagnostics.  Host code only; every step
+// of the math runs in the kernels of project.cu, sort.cu, raster.cu, composite.cu and
+// project_bwd.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+
+namespace splx {
+thread_local int64_t* g_launch_counter = nullptr;
+}
+
+using namespace splx;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e, const char* what) {
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
+  return SPLX_ERR_CUDA;
+}
+
+#define CK(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+#define CK_LAUNCH()                                                     \
+  do {                                                                  \
+    cudaError_t e_ = cudaGetLastError();                                \
+    if (e_ != cudaSuccess) return cuda_fail(e_, "kernel launch");       \
+  } while (0)
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+// ---------------------------------------------------------------- context
+struct splx_ctx_s {
+  int device = 0;
+  size_t budget = 0;
+  size_t in_use = 0;
+  cudaMemPool_t pool = nullptr;
+  int* d_status = nullptr;
+  int64_t launches = 0;
+  std::mutex mu;
+  std::unordered_map<void*, size_t> sizes;
+};
+
+namespace {
+
+struct CtxScope {
+  int prev = -1;
+  explicit CtxScope(splx_ctx_t c) {
+    g_launch_counter = &c->launches;
+    cudaGetDevice(&prev);
+    if (prev != c->device) cudaSetDevice(c->device);
+  }
+  ~CtxScope() {
+    g_launch_counter = nullptr;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int ctx_alloc(splx_ctx_t c, void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->budget && c->in_use + bytes > c->budget) return SPLX_ERR_BUDGET;
+    c->in_use += bytes;
+  }
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, c->pool, s);
+  if (e != cudaSuccess) {
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->in_use -= bytes;
+    return cuda_fail(e, "cudaMallocFromPoolAsync");
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->sizes[*p] = bytes;
+  return SPLX_OK;
+}
+
+void ctx_free(splx_ctx_t c, void* p, cudaStream_t s) {
+  if (!p) return;
+  cudaFreeAsync(p, s);
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->sizes.find(p);
+  if (it != c->sizes.end()) {
+    c->in_use -= it->second;
+    c->sizes.erase(it);
+  }
+}
+
+template <typename T>
+int ctx_alloc_t(splx_ctx_t c, T** p, size_t count, cudaStream_t s) {
+  return ctx_alloc(c, reinterpret_cast<void**>(p), count * sizeof(T), s);
+}
+
+int check_opts(const splx_opts* o) {
+  if (!o) return SPLX_ERR_INVALID;
+  if (o->tile != 8 && o->tile != 16 && o->tile != 32) return SPLX_ERR_INVALID;
+  if (!(o->alpha_min >= 0.0f) || !(o->alpha_max > 0.0f) || !(o->alpha_max < 1.0f)) return SPLX_ERR_INVALID;
+  if (!(o->eps_T >= 0.0f) || !(o->eps_comp >= 0.0f)) return SPLX_ERR_INVALID;
+  return SPLX_OK;
+}
+
+int check_cam(const splx_camera* c) {
+  if (!c) return SPLX_ERR_INVALID;
+  if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384) return SPLX_ERR_INVALID;
+  if (!(c->fx > 0.0f) || !(c->fy > 0.0f)) return SPLX_ERR_INVALID;
+  return SPLX_OK;
+}
+
+int check_gaussians(const splx_gaussians* g) {
+  if (!g) return SPLX_ERR_INVALID;
+  if (g->n < 0 || g->n >= (int64_t(1) << 31)) return SPLX_ERR_INVALID;
+  if (g->sh_degree < 0 || g->sh_degree > 3) return SPLX_ERR_INVALID;
+  if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+    return SPLX_ERR_INVALID;
+  if (g->n > 0 && !aligned16(g->quats)) return SPLX_ERR_INVALID;
+  return SPLX_OK;
+}
+
+ViewDev make_view(const splx_camera& c, int tile) {
+  ViewDev v;
+  std::memcpy(v.R, c.R, sizeof(v.R));
+  std::memcpy(v.t, c.t, sizeof(v.t));
+  v.fx = c.fx; v.fy = c.fy; v.cx = c.cx; v.cy = c.cy; v.near_plane = c.near_plane;
+  // camera centre eye = -R^T t (double on the host, rounded once)
+  for (int k = 0; k < 3; ++k)
+    v.eye[k] = (float)(-((double)c.R[k] * c.t[0] + (double)c.R[3 + k] * c.t[1] +
+                         (double)c.R[6 + k] * c.t[2]));
+  v.W = c.width; v.H = c.height;
+  v.tiles_x = (c.width + tile - 1) / tile;
+  v.tiles_y = (c.height + tile - 1) / tile;
+  return v;
+}
+
+int bits_for(int64_t n) {
+  int b = 1;
+  while (b < 62 && (int64_t(1) << b) < n) ++b;
+  return b;
+}
+
+// A planned render of V views x K subsets.  The per-view entry points use V = 1 plans;
+// the batch API uses one plan for the whole batch.
+struct Plan {
+  splx_ctx_t ctx = nullptr;
+  int V = 0, K = 0, deg = 0, tile = 16;
+  int64_t N = 0;
+  std::vector<SubsetDev> subsets_h;
+  std::vector<ViewDev> views_h;
+  std::vector<ImgDev> imgs_h;
+  SubsetDev* subsets_d = nullptr;
+  ViewDev* views_d = nullptr;
+  ImgDev* imgs_d = nullptr;
+  Rec* rec = nullptr;
+  uint32_t* counts = nullptr;
+  uint64_t* offsets = nullptr;
+  uint64_t* keys[2] = {nullptr, nullptr};
+  uint32_t* vals[2] = {nullptr, nullptr};
+  uint2* ranges = nullptr;
+  float4* grad2d = nullptr;
+  unsigned long long* counters = nullptr;  // [4]: see BatchDev::counters
+  void* scan_temp = nullptr;
+  void* sort_temp = nullptr;
+  int64_t capacity = 0, n_tiles = 0, total_pixels = 0;
+  int sorted_alt = 0;  // which buffer holds the sorted pairs
+  splx_opts opts{};
+  std::vector<int64_t> tile_base, pix_off;
+  // per-kernel timing: events at the marks of Mark, recorded as graph event nodes when
+  // the stream is being captured
+  bool timing = false;
+  cudaEvent_t ev[12] = {};
+
+  void mark(int i, cudaStream_t s) {
+    if (timing && ev[i]) cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
+  }
+
+  void layout() {
+    tile_base.assign(V + 1, 0);
+    pix_off.assign(V + 1, 0);
+    for (int v = 0; v < V; ++v) {
+      tile_base[v + 1] = tile_base[v] + (int64_t)K * views_h[v].tiles_x * views_h[v].tiles_y;
+      pix_off[v + 1] = pix_off[v] + (int64_t)views_h[v].W * views_h[v].H;
+    }
+    n_tiles = tile_base[V];
+    total_pixels = pix_off[V];
+  }
+
+  BatchDev dev() const {
+    BatchDev b;
+    std::memset(&b, 0, sizeof(b));
+    b.V = V; b.K = K; b.sh_degree = deg; b.nc = n_sh(deg); b.N = N; b.tile = tile;
+    b.n_tiles = n_tiles;
+    b.tile_bits = bits_for(n_tiles + 1);
+    b.capacity = capacity;
+    b.eps_T = opts.eps_T; b.eps_comp = opts.eps_comp;
+    b.alpha_min = opts.alpha_min; b.alpha_max = opts.alpha_max;
+    for (int c = 0; c < 3; ++c) b.bg[c] = opts.bg[c];
+    b.subsets = subsets_d; b.views = views_d; b.imgs = imgs_d;
+    b.rec = rec; b.counts = counts; b.offsets = offsets;
+    b.keys = keys[0]; b.vals = vals[0]; b.ranges = ranges; b.grad2d = grad2d;
+    b.status = ctx->d_status;
+    b.counters = counters;
+    for (int k = 0; k <= K; ++k) b.goff[k] = k < K ? subsets_h[k].goff : N;
+    for (int v = 0; v <= V; ++v) { b.tile_base[v] = tile_base[v]; b.pix_off[v] = pix_off[v]; }
+    return b;
+  }
+
+  void release(cudaStream_t s) {
+    void* ps[] = {subsets_d, views_d, imgs_d, rec, counts, offsets, keys[0], keys[1],
+                  vals[0], vals[1], ranges, grad2d, scan_temp, sort_temp, counters};
+    for (void* p : ps) ctx_free(ctx, p, s);
+    counters = nullptr;
+    for (auto& e : ev)
+      if (e) { cudaEventDestroy(e); e = nullptr; }
+    subsets_d = nullptr; views_d = nullptr; imgs_d = nullptr; rec = nullptr; counts = nullptr;
+    offsets = nullptr; keys[0] = keys[1] = nullptr; vals[0] = vals[1] = nullptr;
+    ranges = nullptr; grad2d = nullptr; scan_temp = nullptr; sort_temp = nullptr;
+  }
+
+  // Project, scan and (if capacity > 0) emit, sort and build ranges.
+  int bin(cudaStream_t s) {
+    const BatchDev b = dev();
+    if (counters) CK(cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned long long), s));
+    mark(0, s);
+    launch_project(b, s);
+    CK_LAUNCH();
+    mark(1, s);
+    scan_u32_u64(counts, offsets, (int64_t)V * N, scan_temp, s);
+    CK_LAUNCH();
+    mark(2, s);
+    if (capacity <= 0) return SPLX_OK;
+    launch_emit(b, s);
+    CK_LAUNCH();
+    mark(3, s);
+    const int bits = 32 + b.tile_bits;
+    const uint64_t* n_dev = offsets + (int64_t)V * N;
+    sorted_alt = radix_sort_pairs(keys[0], vals[0], keys[1], vals[1], n_dev, capacity, bits,
+                                  sort_temp, s) ? 1 : 0;
+    CK_LAUNCH();
+    mark(4, s);
+    CK(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)std::max<int64_t>(n_tiles, 1), s));
+    BatchDev b2 = b;
+    b2.keys = keys[sorted_alt];
+    b2.vals = vals[sorted_alt];
+    launch_ranges(b2, keys[sorted_alt], s);
+    CK_LAUNCH();
+    mark(5, s);
+    return SPLX_OK;
+  }
+
+  int alloc_pairs(int64_t cap, cudaStream_t s) {
+    capacity = cap;
+    int r;
+    for (int i = 0; i < 2; ++i) {
+      if ((r = ctx_alloc_t(ctx, &keys[i], (size_t)std::max<int64_t>(cap, 1), s))) return r;
+      if ((r = ctx_alloc_t(ctx, &vals[i], (size_t)std::max<int64_t>(cap, 1), s))) return r;
+    }
+    if ((r = ctx_alloc(ctx, &sort_temp, radix_sort_temp_bytes(cap), s))) return r;
+    return SPLX_OK;
+  }
+
+  int alloc_common(cudaStream_t s) {
+    int r;
+    if ((r = ctx_alloc_t(ctx, &subsets_d, subsets_h.size(), s))) return r;
+    if ((r = ctx_alloc_t(ctx, &views_d, views_h.size(), s))) return r;
+    if ((r = ctx_alloc_t(ctx, &imgs_d, std::max<size_t>(imgs_h.size(), 1), s))) return r;
+    if ((r = ctx_alloc_t(ctx, &rec, (size_t)std::max<int64_t>((int64_t)V * N, 1), s))) return r;
+    if ((r = ctx_alloc_t(ctx, &counts, (size_t)std::max<int64_t>((int64_t)V * N, 1), s))) return r;
+    if ((r = ctx_alloc_t(ctx, &offsets, (size_t)V * N + 1, s))) return r;
+    if ((r = ctx_alloc(ctx, &scan_temp, scan_u32_u64_temp_bytes((int64_t)V * N), s))) return r;
+    if ((r = ctx_alloc_t(ctx, &ranges, (size_t)std::max<int64_t>(n_tiles, 1), s))) return r;
+    CK(cudaMemcpyAsync(subsets_d, subsets_h.data(), sizeof(SubsetDev) * subsets_h.size(),
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(views_d, views_h.data(), sizeof(ViewDev) * views_h.size(),
+                       cudaMemcpyHostToDevice, s));
+    if (!imgs_h.empty())
+      CK(cudaMemcpyAsync(imgs_d, imgs_h.data(), sizeof(ImgDev) * imgs_h.size(),
+                         cudaMemcpyHostToDevice, s));
+    return SPLX_OK;
+  }
+};
+
+SubsetDev make_subset(const splx_gaussians& g, int64_t goff) {
+  SubsetDev d;
+  std::memset(&d, 0, sizeof(d));
+  d.means = g.means; d.log_scales = g.log_scales; d.quats = g.quats;
+  d.opacity_logits = g.opacity_logits; d.sh = g.sh; d.n = g.n; d.goff = goff;
+  return d;
+}
+
+}  // namespace
+
+struct splx_state_s {
+  Plan plan;
+  bool has_grad2d = false;
+};
+
+struct splx_batch_s {
+  Plan plan;
+  splx_camera* pinned_cams = nullptr;
+  float4* gCT = nullptr;       // [K * total_pixels]
+  float* partial = nullptr;    // rgb [3 K P], T [K P], D [K P] (P = total pixels)
+  int32_t* last = nullptr;     // [K P]
+  bool forward_done = false;
+};
+
+struct splx_graph_s {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+int splx_create(splx_ctx_t* out, int device, size_t hbm_budget_bytes) {
+  if (!out) return SPLX_ERR_INVALID;
+  *out = nullptr;
+  int n = 0;
+  CK(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return SPLX_ERR_INVALID;
+  splx_ctx_t c = new (std::nothrow) splx_ctx_s();
+  if (!c) return SPLX_ERR_BUDGET;
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(device);
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  cudaError_t e = cudaMemPoolCreate(&c->pool, &props);
+  if (e == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "splx_create");
+  }
+  *out = c;
+  return SPLX_OK;
+}
+
+int splx_destroy(splx_ctx_t c) {
+  if (!c) return SPLX_ERR_INVALID;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  cudaFree(c->d_status);
+  cudaMemPoolDestroy(c->pool);
+  cudaSetDevice(prev);
+  delete c;
+  return SPLX_OK;
+}
+
+size_t splx_scratch_bytes(splx_ctx_t c) {
+  if (!c) return 0;
+  std::lock_guard<std::mutex> lk(c->mu);
+  return c->in_use;
+}
+
+int splx_render_partial(splx_ctx_t ctx, const splx_gaussians* subset, const splx_camera* cam,
+                        const splx_opts* opts, const splx_partial* out, splx_state_t* state_out,
+                        splx_stream_t stream) {
+  if (!ctx || !out || !out->rgb || !out->T || !out->depth || !out->last) return SPLX_ERR_INVALID;
+  int r;
+  if ((r = check_gaussians(subset)) || (r = check_cam(cam)) || (r = check_opts(opts))) return r;
+  if (state_out) *state_out = nullptr;
+  CtxScope scope(ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  splx_state_s* st = new (std::nothrow) splx_state_s();
+  if (!st) return SPLX_ERR_BUDGET;
+  Plan& P = st->plan;
+  P.ctx = ctx; P.V = 1; P.K = 1; P.deg = subset->sh_degree; P.tile = opts->tile; P.N = subset->n;
+  P.opts = *opts;
+  P.subsets_h.push_back(make_subset(*subset, 0));
+  P.views_h.push_back(make_view(*cam, opts->tile));
+  ImgDev im;
+  im.rgb = out->rgb; im.T = out->T; im.D = out->depth; im.last = out->last; im.gCT = nullptr;
+  P.imgs_h.push_back(im);
+  P.layout();
+  auto fail = [&](int code) {
+    P.release(s);
+    delete st;
+    return code;
+  };
+  if ((r = P.alloc_common(s))) return fail(r);
+  if ((r = P.bin(s))) return fail(r);
+  uint64_t total = 0;
+  {
+    cudaError_t e = cudaMemcpyAsync(&total, P.offsets + P.N, sizeof(uint64_t),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "pair count readback"));
+  }
+  if (total >= (uint64_t)UINT32_MAX) return fail(SPLX_ERR_CAPACITY);
+  if ((r = P.alloc_pairs((int64_t)total, s))) return fail(r);
+  {
+    // emit, sort, ranges (project/scan already done)
+    const BatchDev b = P.dev();
+    launch_emit(b, s);
+    const int bits = 32 + b.tile_bits;
+    P.sorted_alt = radix_sort_pairs(P.keys[0], P.vals[0], P.keys[1], P.vals[1],
+                                    P.offsets + P.N, P.capacity, bits, P.sort_temp, s) ? 1 : 0;
+    cudaError_t e = cudaMemsetAsync(P.ranges, 0, sizeof(uint2) * (size_t)std::max<int64_t>(P.n_tiles, 1), s);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "memset ranges"));
+    BatchDev b2 = P.dev();
+    launch_ranges(b2, P.keys[P.sorted_alt], s);
+    launch_raster_fwd(b2, P.vals[P.sorted_alt], s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(cuda_fail(e, "render_partial launch"));
+  }
+  // keep only what the backward needs
+  ctx_free(ctx, P.counts, s); P.counts = nullptr;
+  ctx_free(ctx, P.scan_temp, s); P.scan_temp = nullptr;
+  ctx_free(ctx, P.sort_temp, s); P.sort_temp = nullptr;
+  ctx_free(ctx, P.keys[0], s); P.keys[0] = nullptr;
+  ctx_free(ctx, P.keys[1], s); P.keys[1] = nullptr;
+  ctx_free(ctx, P.vals[1 - P.sorted_alt], s); P.vals[1 - P.sorted_alt] = nullptr;
+  if (!state_out) return fail(SPLX_OK);
+  *state_out = st;
+  return SPLX_OK;
+}
+
+int splx_state_export(splx_ctx_t ctx, splx_state_t st, int64_t* n_pairs, int64_t* n_tiles,
+                      uint32_t* ranges_out, uint32_t* vals_out, float* rec_out,
+                      splx_stream_t stream) {
+  if (!ctx || !st) return SPLX_ERR_INVALID;
+  CtxScope scope(ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const Plan& P = st->plan;
+  if (n_pairs) *n_pairs = P.capacity;
+  if (n_tiles) *n_tiles = P.n_tiles;
+  if (ranges_out && P.n_tiles > 0)
+    CK(cudaMemcpyAsync(ranges_out, P.ranges, sizeof(uint2) * P.n_tiles, cudaMemcpyDeviceToDevice, s));
+  if (vals_out && P.capacity > 0)
+    CK(cudaMemcpyAsync(vals_out, P.vals[P.sorted_alt], sizeof(uint32_t) * P.capacity,
+                       cudaMemcpyDeviceToDevice, s));
+  if (rec_out && P.N > 0)
+    CK(cudaMemcpyAsync(rec_out, P.rec, sizeof(Rec) * P.N, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return SPLX_OK;
+}
+
+int splx_state_release(splx_ctx_t ctx, splx_state_t st, splx_stream_t stream) {
+  if (!ctx || !st) return SPLX_ERR_INVALID;
+  CtxScope scope(ctx);
+  st->plan.release(reinterpret_cast<cudaStream_t>(stream));
+  delete st;
+  return SPLX_OK;
+}
+
+int splx_composite(splx_ctx_t ctx, const splx_partial* parts, int32_t K, int32_t width,
+                   int32_t height, const splx_opts* opts, float* out_rgb, float* out_T,
+                   splx_stream_t stream) {
+  if (!ctx || !parts || K < 1 || K > kMaxK || width < 1 || height < 1 || !out_rgb)
+    return SPLX_ERR_INVALID;
+  int r;
+  if ((r = check_opts(opts))) return r;
+  for (int k = 0; k < K; ++k)
+    if (!parts[k].rgb || !parts[k].T || !parts[k].depth) return SPLX_ERR_INVALID;
+  CtxScope scope(ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Plan P;
+  P.ctx = ctx; P.V = 1; P.K = K; P.tile = opts->tile; P.opts = *opts;
+  splx_camera cam;
+  std::memset(&cam, 0, sizeof(cam));
+  cam.width = width; cam.height = height; cam.fx = cam.fy = 1.0f;
+  P.views_h.push_back(make_view(cam, opts->tile));
+  for (int k = 0; k < K; ++k) {
+    ImgDev im;
+    im.rgb = parts[k].rgb; im.T = parts[k].T; im.D = parts[k].depth; im.last = parts[k].last;
+    im.gCT = nullptr;
+    P.imgs_h.push_back(im);
+  }
+  P.layout();
+  if ((r = ctx_alloc_t(ctx, &P.views_d, 1, s))) return r;
+  if ((r = ctx_alloc_t(ctx, &P.imgs_d, (size_t)K, s))) { P.release(s); return r; }
+  cudaError_t e = cudaMemcpyAsync(P.views_d, P.views_h.data(), sizeof(ViewDev), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(P.imgs_d, P.imgs_h.data(), sizeof(ImgDev) * K, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) { P.release(s); return cuda_fail(e, "composite upload"); }
+  BatchDev b = P.dev();
+  b.out_rgb = out_rgb;
+  b.out_T = out_T;
+  launch_composite(b, P.total_pixels, s);
+  e = cudaGetLastError();
+  P.release(s);
+  if (e != cudaSuccess) return cuda_fail(e, "composite launch");
+  return SPLX_OK;
+}
+
+int splx_backward(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
+                  const splx_camera* cam, const splx_partial* parts, const splx_state_t* states,
+                  const float* dL_drgb, const float* dL_dT, const splx_opts* opts,
+                  const splx_params* grads, splx_stream_t stream) {
+  if (!ctx || !subsets || K < 1 || K > kMaxK || !parts || !states || !dL_drgb || !grads)
+    return SPLX_ERR_INVALID;
+  int r;
+  if ((r = check_cam(cam)) || (r = check_opts(opts))) return r;
+  for (int k = 0; k < K; ++k) {
+    if (!states[k] || (r = check_gaussians(&subsets[k]))) return r ? r : SPLX_ERR_INVALID;
+    if (states[k]->plan.N != subsets[k].n || states[k]->plan.views_h[0].W != cam->width ||
+        states[k]->plan.views_h[0].H != cam->height || states[k]->plan.tile != opts->tile)
+      return SPLX_ERR_STATE;
+    if (subsets[k].n > 0 && (!grads[k].means || !grads[k].log_scales || !grads[k].quats ||
+                             !grads[k].opacity_logits || !grads[k].sh || !aligned16(grads[k].quats)))
+      return SPLX_ERR_INVALID;
+  }
+  CtxScope scope(ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t HW = (int64_t)cam->width * cam->height;
+  // 1. composite adjoint for all K subsets of this view
+  Plan C;
+  C.ctx = ctx; C.V = 1; C.K = K; C.tile = opts->tile; C.opts = *opts;
+  C.views_h.push_back(make_view(*cam, opts->tile));
+  float4* gCT = nullptr;
+  if ((r = ctx_alloc_t(ctx, &gCT, (size_t)K * HW, s))) return r;
+  for (int k = 0; k < K; ++k) {
+    ImgDev im;
+    im.rgb = parts[k].rgb; im.T = parts[k].T; im.D = parts[k].depth; im.last = parts[k].last;
+    im.gCT = gCT + (int64_t)k * HW;
+    C.imgs_h.push_back(im);
+  }
+  C.layout();
+  auto cleanup = [&](int code) {
+    C.release(s);
+    ctx_free(ctx, gCT, s);
+    return code;
+  };
+  if ((r = ctx_alloc_t(ctx, &C.views_d, 1, s))) return cleanup(r);
+  if ((r = ctx_alloc_t(ctx, &C.imgs_d, (size_t)K, s))) return cleanup(r);
+  cudaError_t e = cudaMemcpyAsync(C.views_d, C.views_h.data(), sizeof(ViewDev), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(C.imgs_d, C.imgs_h.data(), sizeof(ImgDev) * K, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "backward upload"));
+  {
+    BatchDev b = C.dev();
+    b.dL_drgb = dL_drgb;
+    b.dL_dT = dL_dT;
+    launch_composite_bwd(b, C.total_pixels, s);
+  }
+  // 2. per subset: raster adjoint into per-Gaussian 2-D gradients, then projection adjoint
+  for (int k = 0; k < K; ++k) {
+    Plan& P = states[k]->plan;
+    if (P.N == 0) continue;
+    // refresh the image table with this view's adjoint plane
+    P.imgs_h[0].rgb = parts[k].rgb; P.imgs_h[0].T = parts[k].T; P.imgs_h[0].D = parts[k].depth;
+    P.imgs_h[0].last = parts[k].last; P.imgs_h[0].gCT = gCT + (int64_t)k * HW;
+    e = cudaMemcpyAsync(P.imgs_d, P.imgs_h.data(), sizeof(ImgDev), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "backward upload"));
+    if (!P.grad2d) {
+      if ((r = ctx_alloc_t(ctx, &P.grad2d, (size_t)P.N * 3, s))) return cleanup(r);
+      e = cudaMemsetAsync(P.grad2d, 0, sizeof(float4) * 3 * (size_t)P.N, s);
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "memset grad2d"));
+    }
+    BatchDev b = P.dev();
+    launch_raster_bwd(b, P.vals[P.sorted_alt], s);
+    GradTable gt;
+    std::memset(&gt, 0, sizeof(gt));
+    gt.p[0][0] = grads[k].means; gt.p[0][1] = grads[k].log_scales; gt.p[0][2] = grads[k].quats;
+    gt.p[0][3] = grads[k].opacity_logits; gt.p[0][4] = grads[k].sh;
+    launch_project_bwd(b, gt, s);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "backward launch"));
+  return cleanup(SPLX_OK);
+}
+
+namespace {
+int adam_all(splx_ctx_t ctx, const splx_params* p, const splx_params* g, const splx_params* m,
+             const splx_params* v, const splx_adam* hp, int64_t step, int64_t* step_dev,
+             cudaStream_t s) {
+  if (!p || !g || !m || !v || !hp) return SPLX_ERR_INVALID;
+  if (p->n < 0 || p->sh_degree < 0 || p->sh_degree > 3) return SPLX_ERR_INVALID;
+  if (g->n != p->n || m->n != p->n || v->n != p->n) return SPLX_ERR_INVALID;
+  const int nc = n_sh(p->sh_degree);
+  float* const P[5] = {p->means, p->log_scales, p->quats, p->opacity_logits, p->sh};
+  float* const G[5] = {g->means, g->log_scales, g->quats, g->opacity_logits, g->sh};
+  float* const M[5] = {m->means, m->log_scales, m->quats, m->opacity_logits, m->sh};
+  float* const Vv[5] = {v->means, v->log_scales, v->quats, v->opacity_logits, v->sh};
+  const int64_t cnt[5] = {3 * p->n, 3 * p->n, 4 * p->n, p->n, (int64_t)3 * nc * p->n};
+  if (p->n == 0) return SPLX_OK;
+  for (int i = 0; i < 5; ++i)
+    if (!P[i] || !G[i] || !M[i] || !Vv[i]) return SPLX_ERR_INVALID;
+  if (step_dev) launch_step_increment(step_dev, s);
+  for (int i = 0; i < 5; ++i) {
+    const bool vec = aligned16(P[i]) && aligned16(G[i]) && aligned16(M[i]) && aligned16(Vv[i]);
+    const float lr = hp->lr[i < 4 ? i : 4];
+    const float lr_rest = i == 4 ? hp->lr[5] : lr;
+    launch_adam(P[i], G[i], M[i], Vv[i], cnt[i], i == 4 ? 3 * nc : 0, lr, lr_rest, hp->beta1,
+                hp->beta2, hp->eps, step, step_dev, hp->zero_grad != 0, vec, s);
+  }
+  CK_LAUNCH();
+  return SPLX_OK;
+}
+}  // namespace
+
+int splx_step(splx_ctx_t ctx, const splx_params* p, const splx_params* g, const splx_params* m,
+              const splx_params* v, const splx_adam* hp, int64_t step, splx_stream_t stream) {
+  if (!ctx || step < 1) return SPLX_ERR_INVALID;
+  CtxScope scope(ctx);
+  return adam_all(ctx, p, g, m, v, hp, step, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int splx_step_device(splx_ctx_t ctx, const splx_params* p, const splx_params* g,
+                     const splx_params* m, const splx_params* v, const splx_adam* hp,
+                     int64_t* step_dev, splx_stream_t stream) {
+  if (!ctx || !step_dev) return SPLX_ERR_INVALID;
+  CtxScope scope(ctx);
+  return adam_all(ctx, p, g, m, v, hp, 0, step_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int splx_loss_l1(splx_ctx_t ctx, const float* img, const float* target, int64_t n,
+                 float* loss_out, float* dL_dimg, splx_stream_t stream) {
+  if (!ctx || !img || !target || !loss_out || n < 0) return SPLX_ERR_INVALID;
+  CtxScope scope(ctx);
+  launch_loss_l1(img, target, n, loss_out, dL_dimg, reinterpret_cast<cudaStream_t>(stream));
+  CK_LAUNCH();
+  return SPLX_OK;
+}
+
+// ---------------------------------------------------------------- batch
+int splx_batch_create(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
+                      const splx_camera* cams, int32_t V, const splx_opts* opts,
+                      int64_t pair_capacity, splx_batch_t* out, splx_stream_t stream) {
+  if (!ctx || !subsets || !cams || !out || K < 1 || K > kMaxK || V < 1 || V > kMaxViews ||
+      pair_capacity < 0)
+    return SPLX_ERR_INVALID;
+  *out = nullptr;
+  int r;
+  if ((r = check_opts(opts))) return r;
+  int64_t N = 0;
+  for (int k = 0; k < K; ++k) {
+    if ((r = check_gaussians(&subsets[k]))) return r;
+    if (subsets[k].sh_degree != subsets[0].sh_degree) return SPLX_ERR_INVALID;
+    N += subsets[k].n;
+  }
+  if (N >= (int64_t(1) << 32)) return SPLX_ERR_INVALID;
+  for (int v = 0; v < V; ++v)
+    if ((r = check_cam(&cams[v]))) return r;
+  CtxScope scope(ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  splx_batch_s* bt = new (std::nothrow) splx_batch_s();
+  if (!bt) return SPLX_ERR_BUDGET;
+  Plan& P = bt->plan;
+  P.ctx = ctx; P.V = V; P.K = K; P.deg = subsets[0].sh_degree; P.tile = opts->tile; P.N = N;
+  P.opts = *opts;
+  int64_t goff = 0;
+  for (int k = 0; k < K; ++k) {
+    P.subsets_h.push_back(make_subset(subsets[k], goff));
+    goff += subsets[k].n;
+  }
+  for (int v = 0; v < V; ++v) P.views_h.push_back(make_view(cams[v], opts->tile));
+  P.layout();
+  const int64_t TP = P.total_pixels;
+  auto fail = [&](int code) {
+    P.release(s);
+    ctx_free(ctx, bt->gCT, s);
+    ctx_free(ctx, bt->partial, s);
+    ctx_free(ctx, bt->last, s);
+    if (bt->pinned_cams) cudaFreeHost(bt->pinned_cams);
+    delete bt;
+    return code;
+  };
+  if ((r = ctx_alloc_t(ctx, &bt->partial, (size_t)5 * K * TP, s))) return fail(r);
+  if ((r = ctx_alloc_t(ctx, &bt->last, (size_t)K * TP, s))) return fail(r);
+  if ((r = ctx_alloc_t(ctx, &bt->gCT, (size_t)K * TP, s))) return fail(r);
+  // image (v, k): rgb planes at 3*(K*pix_off[v] + k*HW_v), T/D/last at K*pix_off[v] + k*HW_v
+  float* rgb_base = bt->partial;
+  float* T_base = bt->partial + (size_t)3 * K * TP;
+  float* D_base = T_base + (size_t)K * TP;
+  for (int v = 0; v < V; ++v) {
+    const int64_t HW = (int64_t)P.views_h[v].W * P.views_h[v].H;
+    for (int k = 0; k < K; ++k) {
+      const int64_t o = (int64_t)K * P.pix_off[v] + (int64_t)k * HW;
+      ImgDev im;
+      im.rgb = rgb_base + 3 * o; im.T = T_base + o; im.D = D_base + o; im.last = bt->last + o;
+      im.gCT = bt->gCT + o;
+      P.imgs_h.push_back(im);
+    }
+  }
+  if ((r = P.alloc_common(s))) return fail(r);
+  if ((r = ctx_alloc_t(ctx, &P.grad2d, (size_t)V * N * 3, s))) return fail(r);
+  if ((r = ctx_alloc_t(ctx, &P.counters, 4, s))) return fail(r);
+  cudaError_t e = cudaMemsetAsync(P.grad2d, 0, sizeof(float4) * 3 * (size_t)V * N, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.counters, 0, 4 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "memset grad2d"));
+  if (cudaMallocHost(&bt->pinned_cams, sizeof(splx_camera) * kMaxViews) != cudaSuccess)
+    bt->pinned_cams = nullptr;
+  int64_t cap = pair_capacity;
+  if (cap == 0) {
+    P.capacity = 0;
+    if ((r = P.bin(s))) return fail(r);
+    uint64_t total = 0;
+    e = cudaMemcpyAsync(&total, P.offsets + (int64_t)V * N, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "pair count readback"));
+    cap = (int64_t)(total + total / 4 + 1024);
+  }
+  if (cap >= (int64_t)UINT32_MAX) return fail(SPLX_ERR_CAPACITY);
+  if ((r = P.alloc_pairs(cap, s))) return fail(r);
+  *out = bt;
+  return SPLX_OK;
+}
+
+int splx_batch_set_cameras(splx_batch_t bt, const splx_camera* cams, int32_t V, splx_stream_t stream) {
+  if (!bt || !cams || V != bt->plan.V) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  for (int v = 0; v < V; ++v) {
+    int r = check_cam(&cams[v]);
+    if (r) return r;
+    if (cams[v].width != P.views_h[v].W || cams[v].height != P.views_h[v].H) return SPLX_ERR_INVALID;
+  }
+  CtxScope scope(P.ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CK(cudaStreamSynchronize(s));
+  for (int v = 0; v < V; ++v) P.views_h[v] = make_view(cams[v], P.tile);
+  CK(cudaMemcpyAsync(P.views_d, P.views_h.data(), sizeof(ViewDev) * V, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return SPLX_OK;
+}
+
+int splx_batch_layout(splx_batch_t bt, int64_t* rgb_off, int64_t* pix_off) {
+  if (!bt) return SPLX_ERR_INVALID;
+  const Plan& P = bt->plan;
+  for (int v = 0; v <= P.V; ++v) {
+    if (rgb_off) rgb_off[v] = 3 * P.pix_off[v];
+    if (pix_off) pix_off[v] = P.pix_off[v];
+  }
+  return SPLX_OK;
+}
+
+int splx_batch_forward(splx_batch_t bt, float* out_rgb, float* out_T, splx_stream_t stream) {
+  if (!bt || !out_rgb) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  CtxScope scope(P.ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int r;
+  if ((r = P.bin(s))) return r;
+  BatchDev b = P.dev();
+  b.out_rgb = out_rgb;
+  b.out_T = out_T;
+  launch_raster_fwd(b, P.vals[P.sorted_alt], s);
+  P.mark(6, s);
+  launch_composite(b, P.total_pixels, s);
+  P.mark(7, s);
+  CK_LAUNCH();
+  bt->forward_done = true;
+  return SPLX_OK;
+}
+
+int splx_batch_backward(splx_batch_t bt, const float* dL_drgb, const float* dL_dT,
+                        const splx_params* grads, splx_stream_t stream) {
+  if (!bt || !dL_drgb || !grads) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  if (!bt->forward_done) return SPLX_ERR_STATE;
+  GradTable gt;
+  std::memset(&gt, 0, sizeof(gt));
+  for (int k = 0; k < P.K; ++k) {
+    if (P.subsets_h[k].n > 0 && (!grads[k].means || !grads[k].log_scales || !grads[k].quats ||
+                                 !grads[k].opacity_logits || !grads[k].sh || !aligned16(grads[k].quats)))
+      return SPLX_ERR_INVALID;
+    gt.p[k][0] = grads[k].means; gt.p[k][1] = grads[k].log_scales; gt.p[k][2] = grads[k].quats;
+    gt.p[k][3] = grads[k].opacity_logits; gt.p[k][4] = grads[k].sh;
+  }
+  CtxScope scope(P.ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  BatchDev b = P.dev();
+  b.dL_drgb = dL_drgb;
+  b.dL_dT = dL_dT;
+  P.mark(8, s);
+  launch_composite_bwd(b, P.total_pixels, s);
+  P.mark(9, s);
+  launch_raster_bwd(b, P.vals[P.sorted_alt], s);
+  P.mark(10, s);
+  launch_project_bwd(b, gt, s);
+  P.mark(11, s);
+  CK_LAUNCH();
+  return SPLX_OK;
+}
+
+int splx_batch_set_timing(splx_batch_t bt, int enable) {
+  if (!bt) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  CtxScope scope(P.ctx);
+  if (enable)
+    for (auto& e : P.ev)
+      if (!e) CK(cudaEventCreate(&e));
+  P.timing = enable != 0;
+  return SPLX_OK;
+}
+
+int splx_batch_kernel_times(splx_batch_t bt, float* ms_out) {
+  if (!bt || !ms_out) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  if (!P.timing) return SPLX_ERR_STATE;
+  CtxScope scope(P.ctx);
+  CK(cudaEventSynchronize(P.ev[11]));
+  const int pairs[10][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {5, 6}, {6, 7},
+                            {8, 9}, {9, 10}, {10, 11}};
+  for (int i = 0; i < 10; ++i) {
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, P.ev[pairs[i][0]], P.ev[pairs[i][1]]));
+    ms_out[i] = ms;
+  }
+  return SPLX_OK;
+}
+
+int splx_batch_counters(splx_batch_t bt, int64_t* out, splx_stream_t stream) {
+  if (!bt || !out) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  CtxScope scope(P.ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long c[4] = {0, 0, 0, 0};
+  uint64_t total = 0;
+  CK(cudaMemcpyAsync(c, P.counters, sizeof(c), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&total, P.offsets + (int64_t)P.V * P.N, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  out[0] = (int64_t)total;
+  out[1] = (int64_t)c[0];
+  out[2] = (int64_t)c[1];
+  out[3] = (int64_t)c[2];
+  return SPLX_OK;
+}
+
+int splx_batch_status(splx_batch_t bt, int64_t* pairs_out, splx_stream_t stream) {
+  if (!bt) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  CtxScope scope(P.ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  uint64_t total = 0;
+  int st = 0;
+  CK(cudaMemcpyAsync(&total, P.offsets + (int64_t)P.V * P.N, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&st, P.ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (pairs_out) *pairs_out = (int64_t)total;
+  if (st & ST_CAPACITY || total > (uint64_t)P.capacity) return SPLX_ERR_CAPACITY;
+  if (st & ST_TIMEOUT) return SPLX_ERR_TIMEOUT;
+  return SPLX_OK;
+}
+
+int splx_batch_destroy(splx_batch_t bt) {
+  if (!bt) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  CtxScope scope(P.ctx);
+  cudaDeviceSynchronize();
+  P.release(nullptr);
+  ctx_free(P.ctx, bt->gCT, nullptr);
+  ctx_free(P.ctx, bt->partial, nullptr);
+  ctx_free(P.ctx, bt->last, nullptr);
+  cudaDeviceSynchronize();
+  if (bt->pinned_cams) cudaFreeHost(bt->pinned_cams);
+  delete bt;
+  return SPLX_OK;
+}
+
+// ---------------------------------------------------------------- graphs
+int splx_graph_begin(splx_ctx_t ctx, splx_stream_t stream) {
+  if (!ctx || !stream) return SPLX_ERR_INVALID;
+  CtxScope scope(ctx);
+  CK(cudaStreamBeginCapture(reinterpret_cast<cudaStream_t>(stream), cudaStreamCaptureModeThreadLocal));
+  return SPLX_OK;
+}
+
+int splx_graph_end(splx_ctx_t ctx, splx_stream_t stream, splx_graph_t* out) {
+  if (!ctx || !stream || !out) return SPLX_ERR_INVALID;
+  CtxScope scope(ctx);
+  splx_graph_s* g = new (std::nothrow) splx_graph_s();
+  if (!g) return SPLX_ERR_BUDGET;
+  cudaError_t e = cudaStreamEndCapture(reinterpret_cast<cudaStream_t>(stream), &g->graph);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  if (e != cudaSuccess) {
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return cuda_fail(e, "graph capture");
+  }
+  *out = g;
+  return SPLX_OK;
+}
+
+int splx_graph_launch(splx_graph_t g, splx_stream_t stream) {
+  if (!g) return SPLX_ERR_INVALID;
+  CK(cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)));
+  return SPLX_OK;
+}
+
+int splx_graph_destroy(splx_graph_t g) {
+  if (!g) return SPLX_ERR_INVALID;
+  cudaGraphExecDestroy(g->exec);
+  cudaGraphDestroy(g->graph);
+  delete g;
+  return SPLX_OK;
+}
+
+// ---------------------------------------------------------------- diagnostics
+int splx_device_status(splx_ctx_t ctx, splx_stream_t stream) {
+  if (!ctx) return SPLX_ERR_INVALID;
+  CtxScope scope(ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s));
+  CK(cudaStreamSynchronize(s));
+  if (st & ST_CAPACITY) return SPLX_ERR_CAPACITY;
+  if (st & ST_TIMEOUT) return SPLX_ERR_TIMEOUT;
+  if (st & ST_BOUNDS) return SPLX_ERR_STATE;
+  return SPLX_OK;
+}
+
+const char* splx_strerror(int st) {
+  switch (st) {
+    case SPLX_OK: return "ok";
+    case SPLX_ERR_INVALID: return "invalid argument";
+    case SPLX_ERR_BUDGET: return "HBM budget exceeded";
+    case SPLX_ERR_CAPACITY: return "pair capacity exceeded";
+    case SPLX_ERR_CUDA: return "CUDA error";
+    case SPLX_ERR_TIMEOUT: return "bounded device wait timed out";
+    case SPLX_ERR_STATE: return "object in wrong state";
+    default: return "unknown status";
+  }
+}
+
+const char* splx_last_cuda_error(void) { return g_cuda_err; }
+
+int64_t splx_launch_count(splx_ctx_t ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,160 @@
+// Internal definitions shared by the libsplx kernels and the C-ABI layer.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "splx.h"
+
+namespace splx {
+
+constexpr int kMaxK = 64;        // subsets per view
+constexpr int kMaxViews = 256;   // views per batch
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// Device status bits (OR-ed by kernels, read and cleared by the host).
+enum : int { ST_CAPACITY = 1, ST_TIMEOUT = 2, ST_BOUNDS = 4 };
+
+// One subset as seen by the kernels: parameters, gradient targets, global index base.
+struct SubsetDev {
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* opacity_logits;
+  const float* sh;
+  float* g_means;
+  float* g_log_scales;
+  float* g_quats;
+  float* g_opacity_logits;
+  float* g_sh;
+  int64_t n;
+  int64_t goff;  // first global index of this subset
+};
+
+// One view: camera, image geometry, where its tiles and pixels live, its I/O planes.
+struct ViewDev {
+  float R[9], t[3];
+  float fx, fy, cx, cy, near_plane;
+  float eye[3];  // camera centre in world space
+  int32_t W, H, tiles_x, tiles_y;
+};
+
+// Planes of one (view, subset) partial image.
+struct ImgDev {
+  float* rgb;      // [3][H][W]
+  float* T;        // [H][W]
+  float* D;        // [H][W]
+  int32_t* last;   // [H][W]
+  float4* gCT;     // [H][W] composite adjoint (dL/dC^m rgb, dL/dT^m)
+};
+
+// Projected record of one (view, Gaussian): 64 bytes, gathered by the rasterisers.
+//   a = (u, v, qa, qb)      2-D mean, conic scaled by -log2(e)/2 ... see project.cu
+//   b = (qc, opacity, depth, rect_x)   rect_x = x0 | x1 << 16 (bit pattern)
+//   c = (r, g, b, rect_y)              rect_y = y0 | y1 << 16
+//   d = (unused)
+struct Rec {
+  float4 a, b, c, d;
+};
+
+// Everything a batch kernel needs, passed by value.
+struct BatchDev {
+  int32_t V, K, sh_degree, nc;  // nc = (deg+1)^2
+  int64_t N;                    // Gaussians over all subsets
+  int32_t tile;                 // tile side
+  int32_t tile_bits;            // bits of the image-tile id in a sort key
+  int64_t n_tiles;              // image tiles over all (view, subset)
+  int64_t capacity;             // pair capacity
+  float eps_T, eps_comp, alpha_min, alpha_max;
+  float bg[3];
+  const SubsetDev* subsets;     // [K]
+  const ViewDev* views;         // [V]
+  const ImgDev* imgs;           // [V*K], image (v,k) at v*K+k
+  Rec* rec;                     // [V][N]
+  uint32_t* counts;             // [V*N] tiles touched
+  uint64_t* offsets;            // [V*N+1] exclusive scan of counts
+  uint64_t* keys;               // [capacity]
+  uint32_t* vals;               // [capacity]
+  uint2* ranges;                // [n_tiles] sorted [start, end)
+  int64_t goff[kMaxK + 1];      // subset k = global indices [goff[k], goff[k+1])
+  int64_t tile_base[kMaxViews + 1];  // view v's image tiles start at tile_base[v]
+  int64_t pix_off[kMaxViews + 1];    // view v's pixels start at pix_off[v]
+  float4* grad2d;               // [V][N][3]: (gu, gv, gA, gB), (gC, go, gr, gg), (gb, 0, 0, 0)
+  int* status;                  // device status word
+  // work counters (nullable): [0] list entries examined by the forward rasteriser,
+  // [1] Gaussians blended, [2] entries examined by the backward rasteriser
+  unsigned long long* counters;
+  // concatenated per-view I/O: view v's rgb at 3*pix_off[v], its T plane at pix_off[v]
+  float* out_rgb;
+  float* out_T;                 // nullable
+  const float* dL_drgb;
+  const float* dL_dT;           // nullable
+};
+
+// Gradient targets of the K subsets (means, log_scales, quats, opacity_logits, sh).
+struct GradTable {
+  float* p[kMaxK][5];
+};
+
+__host__ __device__ inline int n_sh(int deg) { return (deg + 1) * (deg + 1); }
+
+// ---- launch wrappers (defined in the .cu files) ------------------------------------
+void launch_project(const BatchDev& b, cudaStream_t s);
+void launch_emit(const BatchDev& b, cudaStream_t s);
+void launch_ranges(const BatchDev& b, const uint64_t* keys, cudaStream_t s);
+void launch_raster_fwd(const BatchDev& b, const uint32_t* vals, cudaStream_t s);
+void launch_composite(const BatchDev& b, int64_t total_pixels, cudaStream_t s);
+void launch_composite_bwd(const BatchDev& b, int64_t total_pixels, cudaStream_t s);
+void launch_raster_bwd(const BatchDev& b, const uint32_t* vals, cudaStream_t s);
+void launch_project_bwd(const BatchDev& b, const GradTable& gt, cudaStream_t s);
+
+// exclusive scan of n u32 values into u64 (out has n+1 entries; out[n] = total)
+size_t scan_u32_u64_temp_bytes(int64_t n);
+void scan_u32_u64(const uint32_t* in, uint64_t* out, int64_t n, void* temp, cudaStream_t s);
+
+// LSD radix sort of (u64 key, u32 value) pairs on key bits [0, bits).  The number of
+// items is read from *n_dev (<= capacity); buffers are ping-ponged and the result ends
+// in (keys, vals) or (keys_alt, vals_alt): returns true if in the alt buffers.
+size_t radix_sort_temp_bytes(int64_t capacity);
+bool radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                      const uint64_t* n_dev, int64_t capacity, int bits, void* temp,
+                      cudaStream_t s);
+
+// Adam over one parameter array.  The step number is `step` or, if step_dev is non-NULL,
+// *step_dev read on the device.
+void launch_adam(float* p, float* g, float* m, float* v, int64_t n, int64_t sh_stride,
+                 float lr, float lr_rest, float b1, float b2, float eps, int64_t step,
+                 const int64_t* step_dev, bool zero_grad, bool vec4, cudaStream_t s);
+void launch_step_increment(int64_t* step_dev, cudaStream_t s);
+void launch_loss_l1(const float* img, const float* target, int64_t n, float* loss,
+                    float* dL, cudaStream_t s);
+
+// Counts kernel launches issued by the library (for reporting).
+extern thread_local int64_t* g_launch_counter;
+inline void count_launch(int n = 1) {
+  if (g_launch_counter) *g_launch_counter += n;
+}
+
+}  // namespace splx
+
+namespace splx {
+// Subset of global Gaussian index g (binary search over the by-value offsets).
+__device__ __forceinline__ int subset_of(const BatchDev& b, int64_t g) {
+  int lo = 0, hi = b.K - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (b.goff[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+// View of global image-tile id / global pixel index.
+__device__ __forceinline__ int view_of(const int64_t* base, int V, int64_t x) {
+  int lo = 0, hi = V - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (base[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+}  // namespace splx

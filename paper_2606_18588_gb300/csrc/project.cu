@@ -1,0 +1,202 @@
+// Projection (Sec. 2 step 1), pair emission and tile ranges (Sec. 2 step 2).
+//
+// project: one thread per Gaussian loops over every view of the batch, so the 59
+// parameters of a degree-3 Gaussian are read from HBM once per batch, not once per
+// view.  Per (view, Gaussian) it writes one 64-byte record (2-D mean, scaled conic,
+// opacity, depth, SH colour, packed pixel rectangle) and the number of tiles touched.
+// emit: one thread per (view, Gaussian) writes a (key, value) pair per touched tile;
+// key = image-tile id << 32 | FP32 depth bits, value = global Gaussian index.
+// ranges: start/end of each image tile in the sorted pair list.
+#include "common.cuh"
+#include "spec.cuh"
+
+namespace splx {
+
+// Real SH basis with the Condon-Shortley phase, degrees 0-3, ordered m = -l..l.
+// Constants: sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times the polynomial prefactors:
+//   Y00 = 1/(2 sqrt(pi)); k1 = sqrt(3/(4pi)); k2a = sqrt(15/(4pi)); k2b = sqrt(5/(16pi));
+//   k2c = sqrt(15/(16pi)); k3a = sqrt(35/(32pi)); k3b = sqrt(105/(4pi));
+//   k3c = sqrt(21/(32pi)); k3d = sqrt(7/(16pi)); k3e = sqrt(105/(16pi)).
+struct ShK {
+  static constexpr float Y00 = 0.28209479177387814f;
+  static constexpr float k1 = 0.48860251190291992f;
+  static constexpr float k2a = 1.09254843059207907f;
+  static constexpr float k2b = 0.31539156525252005f;
+  static constexpr float k2c = 0.54627421529603953f;
+  static constexpr float k3a = 0.59004358992664352f;
+  static constexpr float k3b = 2.89061144264055405f;
+  static constexpr float k3c = 0.45704579946446572f;
+  static constexpr float k3d = 0.37317633259011540f;
+  static constexpr float k3e = 1.44530572132027702f;
+};
+
+template <int DEG>
+__device__ __forceinline__ void sh_eval(float x, float y, float z, float* Y) {
+  Y[0] = ShK::Y00;
+  if (DEG >= 1) {
+    Y[1] = -ShK::k1 * y;
+    Y[2] = ShK::k1 * z;
+    Y[3] = -ShK::k1 * x;
+  }
+  if (DEG >= 2) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = ShK::k2a * x * y;
+    Y[5] = -ShK::k2a * y * z;
+    Y[6] = ShK::k2b * (2.0f * zz - xx - yy);
+    Y[7] = -ShK::k2a * x * z;
+    Y[8] = ShK::k2c * (xx - yy);
+    if (DEG >= 3) {
+      Y[9] = -ShK::k3a * y * (3.0f * xx - yy);
+      Y[10] = ShK::k3b * x * y * z;
+      Y[11] = -ShK::k3c * y * (4.0f * zz - xx - yy);
+      Y[12] = ShK::k3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+      Y[13] = -ShK::k3c * x * (4.0f * zz - xx - yy);
+      Y[14] = ShK::k3e * z * (xx - yy);
+      Y[15] = -ShK::k3a * x * (xx - 3.0f * yy);
+    }
+  }
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) k_project(const BatchDev b) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= b.N) return;
+  const int k = subset_of(b, g);
+  const SubsetDev S = b.subsets[k];
+  const int64_t i = g - S.goff;
+  float m[3], ls[3], q[4];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    m[e] = __ldg(S.means + 3 * i + e);
+    ls[e] = __ldg(S.log_scales + 3 * i + e);
+  }
+  const float4 qv = __ldg(reinterpret_cast<const float4*>(S.quats) + i);
+  q[0] = qv.x; q[1] = qv.y; q[2] = qv.z; q[3] = qv.w;
+  const float opac = 1.0f / (1.0f + __expf(-__ldg(S.opacity_logits + i)));
+  constexpr int NC = (DEG + 1) * (DEG + 1);
+  float sh[NC * 3];
+#pragma unroll
+  for (int e = 0; e < NC * 3; ++e) sh[e] = __ldg(S.sh + i * NC * 3 + e);
+
+  for (int v = 0; v < b.V; ++v) {
+    const ViewDev& cam = b.views[v];
+    const SpecOut so = bin_spec(m, ls, q, cam.R, cam.t, cam.fx, cam.fy, cam.cx, cam.cy, cam.W,
+                                cam.H, cam.near_plane);
+    Rec r;
+    uint32_t tiles = 0;
+    if (so.visible) {
+      const float inv = 1.0f / so.det;
+      const float A = so.c * inv, B = -so.b * inv, Cc = so.a * inv;
+      // p2 = power * log2(e) = qa dx^2 + qb dx dy + qc dy^2
+      r.a = make_float4(so.u, so.v, -0.5f * kLog2e * A, -kLog2e * B);
+      float dx = m[0] - cam.eye[0], dy = m[1] - cam.eye[1], dz = m[2] - cam.eye[2];
+      const float rn = rsqrtf(dx * dx + dy * dy + dz * dz);
+      dx *= rn; dy *= rn; dz *= rn;
+      float Y[NC];
+      sh_eval<DEG>(dx, dy, dz, Y);
+      float col[3];
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.5f;
+#pragma unroll
+        for (int kk = 0; kk < NC; ++kk) acc = fmaf(Y[kk], sh[3 * kk + ch], acc);
+        col[ch] = fmaxf(acc, 0.0f);
+      }
+      const uint32_t rx = (uint32_t)so.x0 | ((uint32_t)so.x1 << 16);
+      const uint32_t ry = (uint32_t)so.y0 | ((uint32_t)so.y1 << 16);
+      r.b = make_float4(-0.5f * kLog2e * Cc, opac, so.tz, __uint_as_float(rx));
+      r.c = make_float4(col[0], col[1], col[2], __uint_as_float(ry));
+      const int B_ = b.tile;
+      tiles = (uint32_t)((so.x1 / B_ - so.x0 / B_ + 1) * (so.y1 / B_ - so.y0 / B_ + 1));
+    } else {
+      r.a = make_float4(0.f, 0.f, 0.f, 0.f);
+      r.b = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFu));
+      r.c = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFu));
+    }
+    r.d = make_float4(0.f, 0.f, 0.f, 0.f);
+    Rec* dst = b.rec + (int64_t)v * b.N + g;
+    dst->a = r.a; dst->b = r.b; dst->c = r.c; dst->d = r.d;
+    b.counts[(int64_t)v * b.N + g] = tiles;
+  }
+}
+
+void launch_project(const BatchDev& b, cudaStream_t s) {
+  const BatchDev& P = b;
+  const int threads = 256;
+  const int64_t blocks = (b.N + threads - 1) / threads;
+  if (blocks == 0) return;
+  switch (b.sh_degree) {
+    case 0: k_project<0><<<(unsigned)blocks, threads, 0, s>>>(P); break;
+    case 1: k_project<1><<<(unsigned)blocks, threads, 0, s>>>(P); break;
+    case 2: k_project<2><<<(unsigned)blocks, threads, 0, s>>>(P); break;
+    default: k_project<3><<<(unsigned)blocks, threads, 0, s>>>(P); break;
+  }
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_emit(const BatchDev b) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)b.V * b.N) return;
+  const uint32_t tiles = b.counts[idx];
+  if (tiles == 0) return;
+  const uint64_t off = b.offsets[idx];
+  if (off + tiles > (uint64_t)b.capacity) {
+    atomicOr(b.status, ST_CAPACITY);
+    return;
+  }
+  const int v = (int)(idx / b.N);
+  const int64_t g = idx - (int64_t)v * b.N;
+  const int k = subset_of(b, g);
+  const ViewDev& cam = b.views[v];
+  const Rec* r = b.rec + idx;
+  const float4 rb = r->b;
+  const uint32_t rx = __float_as_uint(rb.w), ry = __float_as_uint(r->c.w);
+  const int B_ = b.tile;
+  const int tx0 = (int)(rx & 0xFFFFu) / B_, tx1 = (int)(rx >> 16) / B_;
+  const int ty0 = (int)(ry & 0xFFFFu) / B_, ty1 = (int)(ry >> 16) / B_;
+  const uint64_t depth = (uint64_t)__float_as_uint(rb.z);
+  const int64_t base = b.tile_base[v] + (int64_t)k * cam.tiles_x * cam.tiles_y;
+  uint64_t o = off;
+  for (int ty = ty0; ty <= ty1; ++ty)
+    for (int tx = tx0; tx <= tx1; ++tx) {
+      const uint64_t tid = (uint64_t)(base + (int64_t)ty * cam.tiles_x + tx);
+      b.keys[o] = (tid << 32) | depth;
+      b.vals[o] = (uint32_t)g;
+      ++o;
+    }
+}
+
+void launch_emit(const BatchDev& b, cudaStream_t s) {
+  const int64_t n = (int64_t)b.V * b.N;
+  const int threads = 256;
+  const int64_t blocks = (n + threads - 1) / threads;
+  if (blocks == 0) return;
+  k_emit<<<(unsigned)blocks, threads, 0, s>>>(b);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_ranges(const BatchDev b, const uint64_t* __restrict__ keys) {
+  const uint64_t total = b.offsets[(int64_t)b.V * b.N];
+  const uint64_t n = total < (uint64_t)b.capacity ? total : (uint64_t)b.capacity;
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t t = (uint32_t)(keys[i] >> 32);
+  if ((int64_t)t >= b.n_tiles) {  // only reachable after a capacity overflow
+    atomicOr(b.status, ST_BOUNDS);
+    return;
+  }
+  if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) b.ranges[t].x = (uint32_t)i;
+  if (i + 1 == n || (uint32_t)(keys[i + 1] >> 32) != t) b.ranges[t].y = (uint32_t)(i + 1);
+}
+
+void launch_ranges(const BatchDev& b, const uint64_t* keys, cudaStream_t s) {
+  const int threads = 256;
+  const int64_t blocks = (b.capacity + threads - 1) / threads;
+  if (blocks == 0) return;
+  k_ranges<<<(unsigned)blocks, threads, 0, s>>>(b, keys);
+  count_launch();
+}
+
+}  // namespace splx

@@ -1,0 +1,367 @@
+// Backward of the projection (Sec. 2 step 1) and the parameter update (Sec. 2 step 4).
+//
+// project_bwd: one thread per Gaussian loops over the views of the batch.  For each view
+// where the rasteriser left a nonzero 2-D gradient (dL/du, dL/dv, dL/dconic, dL/do,
+// dL/dcolour) it recomputes the FP32 projection, consumes and clears that gradient, and
+// chains it to the mean (through the 2-D mean, the EWA Jacobian J and the SH viewing
+// direction), the SH coefficients, the opacity logit, and - accumulated over views as
+// dL/dM for M = R(q) diag(s) - the log-scales and the quaternion.  Results are added
+// to the caller's gradient arrays (one thread owns one Gaussian: no atomics).
+#include "common.cuh"
+#include "spec.cuh"
+
+namespace splx {
+
+namespace {
+struct ShC {
+  static constexpr float k1 = 0.48860251190291992f;
+  static constexpr float k2a = 1.09254843059207907f;
+  static constexpr float k2b = 0.31539156525252005f;
+  static constexpr float k2c = 0.54627421529603953f;
+  static constexpr float k3a = 0.59004358992664352f;
+  static constexpr float k3b = 2.89061144264055405f;
+  static constexpr float k3c = 0.45704579946446572f;
+  static constexpr float k3d = 0.37317633259011540f;
+  static constexpr float k3e = 1.44530572132027702f;
+};
+
+// Y (value) and sum_k w_k grad Y_k for the real SH basis (same ordering as project.cu).
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
+  Y[0] = 0.28209479177387814f;
+  if (DEG >= 1) { Y[1] = -ShC::k1 * y; Y[2] = ShC::k1 * z; Y[3] = -ShC::k1 * x; }
+  if (DEG >= 2) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = ShC::k2a * x * y; Y[5] = -ShC::k2a * y * z; Y[6] = ShC::k2b * (2.f * zz - xx - yy);
+    Y[7] = -ShC::k2a * x * z; Y[8] = ShC::k2c * (xx - yy);
+    if (DEG >= 3) {
+      Y[9] = -ShC::k3a * y * (3.f * xx - yy); Y[10] = ShC::k3b * x * y * z;
+      Y[11] = -ShC::k3c * y * (4.f * zz - xx - yy);
+      Y[12] = ShC::k3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+      Y[13] = -ShC::k3c * x * (4.f * zz - xx - yy); Y[14] = ShC::k3e * z * (xx - yy);
+      Y[15] = -ShC::k3a * x * (xx - 3.f * yy);
+    }
+  }
+}
+
+template <int DEG>
+__device__ __forceinline__ void sh_dir_grad(float x, float y, float z, const float* w, float* gd) {
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+  if (DEG >= 1) {
+    gy += -ShC::k1 * w[1];
+    gz += ShC::k1 * w[2];
+    gx += -ShC::k1 * w[3];
+  }
+  if (DEG >= 2) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    gx += ShC::k2a * y * w[4]; gy += ShC::k2a * x * w[4];
+    gy += -ShC::k2a * z * w[5]; gz += -ShC::k2a * y * w[5];
+    gx += -2.f * ShC::k2b * x * w[6]; gy += -2.f * ShC::k2b * y * w[6]; gz += 4.f * ShC::k2b * z * w[6];
+    gx += -ShC::k2a * z * w[7]; gz += -ShC::k2a * x * w[7];
+    gx += 2.f * ShC::k2c * x * w[8]; gy += -2.f * ShC::k2c * y * w[8];
+    if (DEG >= 3) {
+      gx += -6.f * ShC::k3a * x * y * w[9]; gy += -ShC::k3a * (3.f * xx - 3.f * yy) * w[9];
+      gx += ShC::k3b * y * z * w[10]; gy += ShC::k3b * x * z * w[10]; gz += ShC::k3b * x * y * w[10];
+      gx += 2.f * ShC::k3c * x * y * w[11]; gy += -ShC::k3c * (4.f * zz - xx - 3.f * yy) * w[11];
+      gz += -8.f * ShC::k3c * y * z * w[11];
+      gx += -6.f * ShC::k3d * x * z * w[12]; gy += -6.f * ShC::k3d * y * z * w[12];
+      gz += ShC::k3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+      gx += -ShC::k3c * (4.f * zz - 3.f * xx - yy) * w[13]; gy += 2.f * ShC::k3c * x * y * w[13];
+      gz += -8.f * ShC::k3c * x * z * w[13];
+      gx += 2.f * ShC::k3e * x * z * w[14]; gy += -2.f * ShC::k3e * y * z * w[14];
+      gz += ShC::k3e * (xx - yy) * w[14];
+      gx += -ShC::k3a * (3.f * xx - 3.f * yy) * w[15]; gy += 6.f * ShC::k3a * x * y * w[15];
+    }
+  }
+  gd[0] = gx; gd[1] = gy; gd[2] = gz;
+}
+}  // namespace
+
+template <int DEG>
+__global__ void __launch_bounds__(128) k_project_bwd(const BatchDev b, const GradTable gt) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= b.N) return;
+  const int k = subset_of(b, g);
+  const SubsetDev& S = b.subsets[k];
+  const int64_t i = g - b.goff[k];
+  constexpr int NC = (DEG + 1) * (DEG + 1);
+  float m[3], ls[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) { m[e] = S.means[3 * i + e]; ls[e] = S.log_scales[3 * i + e]; }
+  const float4 qv = reinterpret_cast<const float4*>(S.quats)[i];
+  const float qn = sqrtf(qv.x * qv.x + qv.y * qv.y + qv.z * qv.z + qv.w * qv.w);
+  const float qw = qv.x / qn, qx = qv.y / qn, qy = qv.z / qn, qz = qv.w / qn;
+  float Rq[9];
+  Rq[0] = 1.f - 2.f * (qy * qy + qz * qz); Rq[1] = 2.f * (qx * qy - qw * qz); Rq[2] = 2.f * (qx * qz + qw * qy);
+  Rq[3] = 2.f * (qx * qy + qw * qz); Rq[4] = 1.f - 2.f * (qx * qx + qz * qz); Rq[5] = 2.f * (qy * qz - qw * qx);
+  Rq[6] = 2.f * (qx * qz - qw * qy); Rq[7] = 2.f * (qy * qz + qw * qx); Rq[8] = 1.f - 2.f * (qx * qx + qy * qy);
+  const float s[3] = {exp_spec(ls[0]), exp_spec(ls[1]), exp_spec(ls[2])};
+  float M[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) M[3 * r + c] = Rq[3 * r + c] * s[c];
+  const float o = 1.0f / (1.0f + __expf(-S.opacity_logits[i]));
+  float sh[NC * 3];
+#pragma unroll
+  for (int e = 0; e < NC * 3; ++e) sh[e] = S.sh[i * NC * 3 + e];
+
+  float gm[3] = {0.f, 0.f, 0.f}, gM[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) gM[e] = 0.f;
+  float glogit = 0.f;
+  float gsh[NC * 3];
+#pragma unroll
+  for (int e = 0; e < NC * 3; ++e) gsh[e] = 0.f;
+  bool any = false;
+
+  for (int v = 0; v < b.V; ++v) {
+    float4* gp = b.grad2d + ((int64_t)v * b.N + g) * 3;
+    const float4 G0 = gp[0], G1 = gp[1];
+    const float gbl = gp[2].x;
+    if (G0.x == 0.f && G0.y == 0.f && G0.z == 0.f && G0.w == 0.f && G1.x == 0.f && G1.y == 0.f &&
+        G1.z == 0.f && G1.w == 0.f && gbl == 0.f)
+      continue;
+    any = true;
+    gp[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    gp[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    gp[2].x = 0.f;
+    const ViewDev& cam = b.views[v];
+    const float* R = cam.R;
+    const float tx = R[0] * m[0] + R[1] * m[1] + R[2] * m[2] + cam.t[0];
+    const float ty = R[3] * m[0] + R[4] * m[1] + R[5] * m[2] + cam.t[1];
+    const float tz = R[6] * m[0] + R[7] * m[1] + R[8] * m[2] + cam.t[2];
+    const float fx = cam.fx, fy = cam.fy;
+    const float itz = 1.0f / tz;
+    const float limx = 1.3f * 0.5f * (float)cam.W / fx, limy = 1.3f * 0.5f * (float)cam.H / fy;
+    const float rx = tx * itz, ry = ty * itz;
+    const bool clx = rx < -limx || rx > limx, cly = ry < -limy || ry > limy;
+    const float rxc = fminf(limx, fmaxf(-limx, rx)), ryc = fminf(limy, fmaxf(-limy, ry));
+    const float j00 = fx * itz, j02 = -fx * rxc * itz, j11 = fy * itz, j12 = -fy * ryc * itz;
+    float V[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        V[3 * r + c] = R[3 * r] * M[c] + R[3 * r + 1] * M[3 + c] + R[3 * r + 2] * M[6 + c];
+    float P0[3], P1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      P0[c] = j00 * V[c] + j02 * V[6 + c];
+      P1[c] = j11 * V[3 + c] + j12 * V[6 + c];
+    }
+    const float a0 = P0[0] * P0[0] + P0[1] * P0[1] + P0[2] * P0[2];
+    const float c0 = P1[0] * P1[0] + P1[1] * P1[1] + P1[2] * P1[2];
+    const float bb = P0[0] * P1[0] + P0[1] * P1[1] + P0[2] * P1[2];
+    const float d01 = P0[0] * P1[1] - P0[1] * P1[0];
+    const float d02 = P0[0] * P1[2] - P0[2] * P1[0];
+    const float d12 = P0[1] * P1[2] - P0[2] * P1[1];
+    const float det = d01 * d01 + d02 * d02 + d12 * d12 + 0.3f * (a0 + c0) + 0.09f;
+    const float idet = 1.0f / det;
+    const float QA = (c0 + 0.3f) * idet, QB = -bb * idet, QC = (a0 + 0.3f) * idet;
+    const float gu = G0.x, gv = G0.y, gA = G0.z, gB = G0.w, gCc = G1.x, go = G1.y;
+    const float gcol[3] = {G1.z, G1.w, gbl};
+    glogit += go * o * (1.0f - o);
+    // colour -> SH coefficients and viewing direction
+    float dx = m[0] - cam.eye[0], dy = m[1] - cam.eye[1], dz = m[2] - cam.eye[2];
+    const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float idist = 1.0f / dist;
+    dx *= idist; dy *= idist; dz *= idist;
+    float Y[NC];
+    sh_basis<DEG>(dx, dy, dz, Y);
+    float gc[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float raw = 0.5f;
+#pragma unroll
+      for (int kk = 0; kk < NC; ++kk) raw = fmaf(Y[kk], sh[3 * kk + ch], raw);
+      gc[ch] = raw < 0.0f ? 0.0f : gcol[ch];
+    }
+    float w[NC];
+#pragma unroll
+    for (int kk = 0; kk < NC; ++kk) {
+      gsh[3 * kk + 0] += Y[kk] * gc[0];
+      gsh[3 * kk + 1] += Y[kk] * gc[1];
+      gsh[3 * kk + 2] += Y[kk] * gc[2];
+      w[kk] = sh[3 * kk] * gc[0] + sh[3 * kk + 1] * gc[1] + sh[3 * kk + 2] * gc[2];
+    }
+    if (DEG > 0) {
+      float gd[3];
+      sh_dir_grad<DEG>(dx, dy, dz, w, gd);
+      const float dd = dx * gd[0] + dy * gd[1] + dz * gd[2];
+      gm[0] += (gd[0] - dx * dd) * idist;
+      gm[1] += (gd[1] - dy * dd) * idist;
+      gm[2] += (gd[2] - dz * dd) * idist;
+    }
+    // conic -> Sigma2D:  H = -Q Gq Q,  Gq = [[gA, gB/2], [gB/2, gC]]
+    const float hB = 0.5f * gB;
+    const float QG00 = QA * gA + QB * hB, QG01 = QA * hB + QB * gCc;
+    const float QG10 = QB * gA + QC * hB, QG11 = QB * hB + QC * gCc;
+    const float H00 = -(QG00 * QA + QG01 * QB), H01 = -(QG00 * QB + QG01 * QC);
+    const float H10 = -(QG10 * QA + QG11 * QB), H11 = -(QG10 * QB + QG11 * QC);
+    // Sigma2D0 = P P^T  ->  gP = 2 H P
+    float gP0[3], gP1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      gP0[c] = 2.f * (H00 * P0[c] + H01 * P1[c]);
+      gP1[c] = 2.f * (H10 * P0[c] + H11 * P1[c]);
+    }
+    // P = J V
+    const float gj00 = gP0[0] * V[0] + gP0[1] * V[1] + gP0[2] * V[2];
+    const float gj02 = gP0[0] * V[6] + gP0[1] * V[7] + gP0[2] * V[8];
+    const float gj11 = gP1[0] * V[3] + gP1[1] * V[4] + gP1[2] * V[5];
+    const float gj12 = gP1[0] * V[6] + gP1[1] * V[7] + gP1[2] * V[8];
+    float gV[9];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      gV[c] = j00 * gP0[c];
+      gV[3 + c] = j11 * gP1[c];
+      gV[6 + c] = j02 * gP0[c] + j12 * gP1[c];
+    }
+    // J and the 2-D mean -> camera-space mean
+    const float itz2 = itz * itz;
+    float gtx = 0.f, gty = 0.f, gtz = 0.f;
+    gtz += -fx * itz2 * gj00 - fy * itz2 * gj11;
+    if (!clx) { gtx += -fx * itz2 * gj02; gtz += 2.f * fx * tx * itz2 * itz * gj02; }
+    else { gtz += fx * rxc * itz2 * gj02; }
+    if (!cly) { gty += -fy * itz2 * gj12; gtz += 2.f * fy * ty * itz2 * itz * gj12; }
+    else { gtz += fy * ryc * itz2 * gj12; }
+    gtx += fx * itz * gu;
+    gtz += -fx * tx * itz2 * gu;
+    gty += fy * itz * gv;
+    gtz += -fy * ty * itz2 * gv;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) gm[e] += R[e] * gtx + R[3 + e] * gty + R[6 + e] * gtz;
+    // V = W M  ->  gM += W^T gV
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        gM[3 * r + c] += R[r] * gV[c] + R[3 + r] * gV[3 + c] + R[6 + r] * gV[6 + c];
+  }
+  if (!any) return;
+  // M = Rq diag(s)
+  float gR[9], gls[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gR[3 * r + c] = gM[3 * r + c] * s[c];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    gls[c] = (gM[c] * Rq[c] + gM[3 + c] * Rq[3 + c] + gM[6 + c] * Rq[6 + c]) * s[c];
+  float gw = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+  gy += -4.f * qy * gR[0]; gz += -4.f * qz * gR[0];
+  gx += 2.f * qy * gR[1]; gy += 2.f * qx * gR[1]; gw += -2.f * qz * gR[1]; gz += -2.f * qw * gR[1];
+  gx += 2.f * qz * gR[2]; gz += 2.f * qx * gR[2]; gw += 2.f * qy * gR[2]; gy += 2.f * qw * gR[2];
+  gx += 2.f * qy * gR[3]; gy += 2.f * qx * gR[3]; gw += 2.f * qz * gR[3]; gz += 2.f * qw * gR[3];
+  gx += -4.f * qx * gR[4]; gz += -4.f * qz * gR[4];
+  gy += 2.f * qz * gR[5]; gz += 2.f * qy * gR[5]; gw += -2.f * qx * gR[5]; gx += -2.f * qw * gR[5];
+  gx += 2.f * qz * gR[6]; gz += 2.f * qx * gR[6]; gw += -2.f * qy * gR[6]; gy += -2.f * qw * gR[6];
+  gy += 2.f * qz * gR[7]; gz += 2.f * qy * gR[7]; gw += 2.f * qx * gR[7]; gx += 2.f * qw * gR[7];
+  gx += -4.f * qx * gR[8]; gy += -4.f * qy * gR[8];
+  const float dq = qw * gw + qx * gx + qy * gy + qz * gz;
+  const float iqn = 1.0f / qn;
+  float* const* P = gt.p[k];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    P[0][3 * i + e] += gm[e];
+    P[1][3 * i + e] += gls[e];
+  }
+  float4* gq4 = reinterpret_cast<float4*>(P[2]) + i;
+  float4 cur = *gq4;
+  cur.x += (gw - qw * dq) * iqn;
+  cur.y += (gx - qx * dq) * iqn;
+  cur.z += (gy - qy * dq) * iqn;
+  cur.w += (gz - qz * dq) * iqn;
+  *gq4 = cur;
+  P[3][i] += glogit;
+#pragma unroll
+  for (int e = 0; e < NC * 3; ++e) P[4][i * NC * 3 + e] += gsh[e];
+}
+
+void launch_project_bwd(const BatchDev& b, const GradTable& gt, cudaStream_t s) {
+  const int threads = 128;
+  const int64_t blocks = (b.N + threads - 1) / threads;
+  if (blocks == 0) return;
+  switch (b.sh_degree) {
+    case 0: k_project_bwd<0><<<(unsigned)blocks, threads, 0, s>>>(b, gt); break;
+    case 1: k_project_bwd<1><<<(unsigned)blocks, threads, 0, s>>>(b, gt); break;
+    case 2: k_project_bwd<2><<<(unsigned)blocks, threads, 0, s>>>(b, gt); break;
+    default: k_project_bwd<3><<<(unsigned)blocks, threads, 0, s>>>(b, gt); break;
+  }
+  count_launch();
+}
+
+// ---------------------------------------------------------------- Adam
+// torch.optim.Adam semantics: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+// p -= (lr / bc1) * m / (sqrt(v) / sqrt(bc2) + eps), bc_i = 1 - b_i^step.  sh_stride > 0
+// selects lr_rest for elements whose index modulo sh_stride is >= 3 (SH coefficients
+// above degree 0).  With zero_grad the gradient is cleared after it is read.
+__global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, float* __restrict__ g,
+                                              float* __restrict__ m, float* __restrict__ v, int64_t n,
+                                              int64_t sh_stride, float lr_in, float lr_rest_in,
+                                              float b1, float b2, float eps, int64_t step_host,
+                                              const int64_t* __restrict__ step_dev, bool zero_grad,
+                                              bool vec4) {
+  const int64_t step = step_dev ? *step_dev : step_host;
+  const double bc1 = 1.0 - pow((double)b1, (double)step);
+  const double bc2 = 1.0 - pow((double)b2, (double)step);
+  const float step_lr = (float)(lr_in / bc1), step_lr_rest = (float)(lr_rest_in / bc1);
+  const float bc2_sqrt_inv = (float)(1.0 / sqrt(bc2));
+  const int64_t n4 = vec4 ? (n >> 2) : 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const float ob1 = 1.0f - b1, ob2 = 1.0f - b2;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
+    float4 pp = reinterpret_cast<float4*>(p)[q];
+    const float4 gg = reinterpret_cast<const float4*>(g)[q];
+    float4 mm = reinterpret_cast<float4*>(m)[q];
+    float4 vv = reinterpret_cast<float4*>(v)[q];
+    float* pe = &pp.x;
+    const float* ge = &gg.x;
+    float* me = &mm.x;
+    float* ve = &vv.x;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int64_t idx = 4 * q + e;
+      const float lr = (sh_stride > 0 && (idx % sh_stride) >= 3) ? step_lr_rest : step_lr;
+      me[e] = b1 * me[e] + ob1 * ge[e];
+      ve[e] = b2 * ve[e] + ob2 * ge[e] * ge[e];
+      pe[e] -= lr * me[e] / (sqrtf(ve[e]) * bc2_sqrt_inv + eps);
+    }
+    reinterpret_cast<float4*>(p)[q] = pp;
+    reinterpret_cast<float4*>(m)[q] = mm;
+    reinterpret_cast<float4*>(v)[q] = vv;
+    if (zero_grad) reinterpret_cast<float4*>(g)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  for (int64_t idx = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
+    const float lr = (sh_stride > 0 && (idx % sh_stride) >= 3) ? step_lr_rest : step_lr;
+    const float gg = g[idx];
+    const float mm = b1 * m[idx] + ob1 * gg;
+    const float vv = b2 * v[idx] + ob2 * gg * gg;
+    m[idx] = mm;
+    v[idx] = vv;
+    p[idx] -= lr * mm / (sqrtf(vv) * bc2_sqrt_inv + eps);
+    if (zero_grad) g[idx] = 0.0f;
+  }
+}
+
+__global__ void k_step_increment(int64_t* step) { *step += 1; }
+
+void launch_step_increment(int64_t* step_dev, cudaStream_t s) {
+  k_step_increment<<<1, 1, 0, s>>>(step_dev);
+  count_launch();
+}
+
+void launch_adam(float* p, float* g, float* m, float* v, int64_t n, int64_t sh_stride,
+                 float lr, float lr_rest, float b1, float b2, float eps, int64_t step,
+                 const int64_t* step_dev, bool zero_grad, bool vec4, cudaStream_t s) {
+  if (n <= 0) return;
+  int64_t blocks = ((n >> 2) + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_adam<<<(unsigned)blocks, 256, 0, s>>>(p, g, m, v, n, sh_stride, lr, lr_rest, b1, b2, eps, step,
+                                          step_dev, zero_grad, vec4);
+  count_launch();
+}
+
+}  // namespace splx

@@ -1,0 +1,138 @@
+// FP32 binning specification on the GPU.
+//
+// The discrete structure of the render (cull decision, integer 3-sigma pixel
+// rectangle, tile rectangle, depth sort key) must match the CPU reference bit for bit,
+// so it is computed here with explicitly rounded IEEE operations (__fmul_rn, __fadd_rn,
+// __fsub_rn, __fdiv_rn, __fsqrt_rn: no contraction into FMA, no approximate division)
+// in a fixed evaluation order.  Projection follows Sec. 2 step 1: Sigma2D = J W Sigma
+// W^T J^T with Sigma = R S S^T R^T, plus a 0.3 px^2 low-pass dilation; the determinant
+// uses the Cauchy-Binet sum of squared 2x2 minors so it never cancels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace splx {
+
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fd(float a, float b) { return __fdiv_rn(a, b); }
+
+// Exponential from basic operations only: Cody-Waite range reduction with ln 2 split
+// as in Moshier's Cephes library, degree-7 Taylor polynomial of e^r (Horner), exact
+// power-of-two scaling.  Within a few ulp of e^x on [-87, 88].
+__device__ __forceinline__ float exp_spec(float x) {
+  x = fminf(fmaxf(x, -87.0f), 88.0f);
+  const float k = rintf(fm(x, 1.44269502f));
+  float r = fs(x, fm(k, 0.693359375f));
+  r = fs(r, fm(k, -2.12194440e-4f));
+  float p = 1.98412698e-4f;
+  p = fa(fm(p, r), 1.38888889e-3f);
+  p = fa(fm(p, r), 8.33333377e-3f);
+  p = fa(fm(p, r), 4.16666679e-2f);
+  p = fa(fm(p, r), 1.66666672e-1f);
+  p = fa(fm(p, r), 0.5f);
+  p = fa(fm(p, r), 1.0f);
+  p = fa(fm(p, r), 1.0f);
+  const float scale = __int_as_float(((int)k + 127) << 23);
+  return fm(p, scale);
+}
+
+struct SpecOut {
+  bool visible;
+  int x0, x1, y0, y1;
+  float tz;         // camera depth (its bits are the sort key)
+  float u, v;       // 2-D mean
+  float a, b, c;    // dilated Sigma2D
+  float det;        // det(Sigma2D)
+  float sx, sy, sz; // activated scales
+};
+
+// cam: R[9], t[3], fx, fy, cx, cy, W, H, near.
+__device__ __forceinline__ SpecOut bin_spec(const float m[3], const float ls[3],
+                                            const float q[4], const float* R, const float* tc,
+                                            float fx, float fy, float cx, float cy, int W, int H,
+                                            float near_plane) {
+  SpecOut o;
+  o.visible = false;
+  o.x0 = 0; o.x1 = -1; o.y0 = 0; o.y1 = -1;
+  const float tx = fa(fa(fa(fm(R[0], m[0]), fm(R[1], m[1])), fm(R[2], m[2])), tc[0]);
+  const float ty = fa(fa(fa(fm(R[3], m[0]), fm(R[4], m[1])), fm(R[5], m[2])), tc[1]);
+  const float tz = fa(fa(fa(fm(R[6], m[0]), fm(R[7], m[1])), fm(R[8], m[2])), tc[2]);
+  o.tz = tz;
+  if (!(tz > near_plane)) return o;
+
+  const float qn = fa(fa(fa(fm(q[0], q[0]), fm(q[1], q[1])), fm(q[2], q[2])), fm(q[3], q[3]));
+  if (!(qn > 0.0f)) return o;
+  const float inv = fd(1.0f, __fsqrt_rn(qn));
+  const float w = fm(q[0], inv), x = fm(q[1], inv), y = fm(q[2], inv), z = fm(q[3], inv);
+  float Rq[9];
+  Rq[0] = fs(1.0f, fm(2.0f, fa(fm(y, y), fm(z, z))));
+  Rq[1] = fm(2.0f, fs(fm(x, y), fm(w, z)));
+  Rq[2] = fm(2.0f, fa(fm(x, z), fm(w, y)));
+  Rq[3] = fm(2.0f, fa(fm(x, y), fm(w, z)));
+  Rq[4] = fs(1.0f, fm(2.0f, fa(fm(x, x), fm(z, z))));
+  Rq[5] = fm(2.0f, fs(fm(y, z), fm(w, x)));
+  Rq[6] = fm(2.0f, fs(fm(x, z), fm(w, y)));
+  Rq[7] = fm(2.0f, fa(fm(y, z), fm(w, x)));
+  Rq[8] = fs(1.0f, fm(2.0f, fa(fm(x, x), fm(y, y))));
+  const float s[3] = {exp_spec(ls[0]), exp_spec(ls[1]), exp_spec(ls[2])};
+  o.sx = s[0]; o.sy = s[1]; o.sz = s[2];
+  float M[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M[3 * i + j] = fm(Rq[3 * i + j], s[j]);
+  float V[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      V[3 * i + j] = fa(fa(fm(R[3 * i + 0], M[j]), fm(R[3 * i + 1], M[3 + j])),
+                        fm(R[3 * i + 2], M[6 + j]));
+  const float limx = fd(fm(1.3f, fm(0.5f, (float)W)), fx);
+  const float limy = fd(fm(1.3f, fm(0.5f, (float)H)), fy);
+  const float rx = fminf(limx, fmaxf(-limx, fd(tx, tz)));
+  const float ry = fminf(limy, fmaxf(-limy, fd(ty, tz)));
+  const float j00 = fd(fx, tz);
+  const float j02 = -fd(fm(fx, rx), tz);
+  const float j11 = fd(fy, tz);
+  const float j12 = -fd(fm(fy, ry), tz);
+  float P0[3], P1[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    P0[j] = fa(fm(j00, V[j]), fm(j02, V[6 + j]));
+    P1[j] = fa(fm(j11, V[3 + j]), fm(j12, V[6 + j]));
+  }
+  const float a0 = fa(fa(fm(P0[0], P0[0]), fm(P0[1], P0[1])), fm(P0[2], P0[2]));
+  const float c0 = fa(fa(fm(P1[0], P1[0]), fm(P1[1], P1[1])), fm(P1[2], P1[2]));
+  const float b0 = fa(fa(fm(P0[0], P1[0]), fm(P0[1], P1[1])), fm(P0[2], P1[2]));
+  const float d01 = fs(fm(P0[0], P1[1]), fm(P0[1], P1[0]));
+  const float d02 = fs(fm(P0[0], P1[2]), fm(P0[2], P1[0]));
+  const float d12 = fs(fm(P0[1], P1[2]), fm(P0[2], P1[1]));
+  const float det0 = fa(fa(fm(d01, d01), fm(d02, d02)), fm(d12, d12));
+  const float a = fa(a0, 0.3f), c = fa(c0, 0.3f);
+  const float det = fa(fa(det0, fm(0.3f, fa(a0, c0))), 0.09f);
+  o.a = a; o.b = b0; o.c = c; o.det = det;
+  if (!(det > 0.0f)) return o;
+  const float mid = fm(0.5f, fa(a, c));
+  const float lam = fa(mid, __fsqrt_rn(fmaxf(0.1f, fs(fm(mid, mid), det))));
+  if (!(lam < 1.0e30f)) return o;
+  const float r = ceilf(fm(3.0f, __fsqrt_rn(lam)));
+  if (!(r > 0.0f)) return o;
+  const float u = fa(fd(fm(fx, tx), tz), cx);
+  const float v = fa(fd(fm(fy, ty), tz), cy);
+  o.u = u; o.v = v;
+  if (!(fabsf(u) < 1.0e7f) || !(fabsf(v) < 1.0e7f)) return o;
+  const float xlo = ceilf(fs(fs(u, r), 0.5f)), xhi = floorf(fs(fa(u, r), 0.5f));
+  const float ylo = ceilf(fs(fs(v, r), 0.5f)), yhi = floorf(fs(fa(v, r), 0.5f));
+  const float x0 = fmaxf(xlo, 0.0f), x1 = fminf(xhi, (float)(W - 1));
+  const float y0 = fmaxf(ylo, 0.0f), y1 = fminf(yhi, (float)(H - 1));
+  if (x0 > x1 || y0 > y1) return o;
+  o.visible = true;
+  o.x0 = (int)x0; o.x1 = (int)x1; o.y0 = (int)y0; o.y1 = (int)y1;
+  return o;
+}
+
+}  // namespace splx

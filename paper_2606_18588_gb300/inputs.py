@@ -95,9 +95,9 @@ def pinhole(width: int, height: int, fov_x_deg: float, eye, target, near=0.01,
 
 
 def _quats(rng, n):
-    q = rng.standard_normal((n, 4))
+    q = rng.standard_normal((n, 4), dtype=np.float32)
     q /= np.linalg.norm(q, axis=1, keepdims=True)
-    return q.astype(np.float32)
+    return q
 
 
 def _sh(rng, n, deg, rgb):
@@ -105,7 +105,7 @@ def _sh(rng, n, deg, rgb):
     sh = np.zeros((n, c, 3), np.float32)
     sh[:, 0, :] = (rgb - 0.5) * _INV_Y00
     if c > 1:
-        sh[:, 1:, :] = rng.normal(0.0, 0.2, (n, c - 1, 3))
+        sh[:, 1:, :] = rng.standard_normal((n, c - 1, 3), dtype=np.float32) * np.float32(0.2)
     return sh
 
 

@@ -1,0 +1,411 @@
+"""Python binding of libsplx (include/splx.h): argument marshalling only.
+
+Every function here converts torch tensors / numpy cameras into the C structs of the ABI
+and calls the library; all arithmetic of the path runs in the library's CUDA kernels.
+There is no fallback: if libsplx.so is missing or fails to load, importing this module
+raises.  Names follow the C entry points without the `splx_` prefix.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsplx.so")
+
+OK, ERR_INVALID, ERR_BUDGET, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+
+
+class SplxError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = _lib.splx_strerror(code).decode()
+        if code == ERR_CUDA:
+            msg += f" ({_lib.splx_last_cuda_error().decode()})"
+        super().__init__(f"{where}: {msg} [{code}]")
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libsplx.so not built at {LIB_PATH}: run __graft_entry__.build() "
+                      "(the CUDA path has no fallback)")
+_lib = C.CDLL(LIB_PATH)
+
+
+class Gaussians(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p), ("n", C.c_int64),
+                ("sh_degree", C.c_int32)]
+
+
+class Params(C.Structure):
+    _fields_ = Gaussians._fields_
+
+
+class Camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("near_plane", C.c_float)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("eps_T", C.c_float), ("eps_comp", C.c_float),
+                ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("bg", C.c_float * 3)]
+
+
+class Partial(C.Structure):
+    _fields_ = [("rgb", C.c_void_p), ("T", C.c_void_p), ("depth", C.c_void_p), ("last", C.c_void_p)]
+
+
+class Adam(C.Structure):
+    _fields_ = [("lr", C.c_float * 6), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("zero_grad", C.c_int32)]
+
+
+_P = C.c_void_p
+_sigs = {
+    "splx_create": (C.c_int, [C.POINTER(_P), C.c_int, C.c_size_t]),
+    "splx_destroy": (C.c_int, [_P]),
+    "splx_scratch_bytes": (C.c_size_t, [_P]),
+    "splx_render_partial": (C.c_int, [_P, _P, _P, _P, _P, C.POINTER(_P), _P]),
+    "splx_composite": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, _P]),
+    "splx_backward": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "splx_state_release": (C.c_int, [_P, _P, _P]),
+    "splx_state_export": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _P, _P, _P,
+                                    _P]),
+    "splx_step": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int64, _P]),
+    "splx_step_device": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "splx_loss_l1": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
+    "splx_batch_create": (C.c_int, [_P, _P, C.c_int32, _P, C.c_int32, _P, C.c_int64,
+                                    C.POINTER(_P), _P]),
+    "splx_batch_set_cameras": (C.c_int, [_P, _P, C.c_int32, _P]),
+    "splx_batch_layout": (C.c_int, [_P, _P, _P]),
+    "splx_batch_forward": (C.c_int, [_P, _P, _P, _P]),
+    "splx_batch_backward": (C.c_int, [_P, _P, _P, _P, _P]),
+    "splx_batch_status": (C.c_int, [_P, C.POINTER(C.c_int64), _P]),
+    "splx_batch_destroy": (C.c_int, [_P]),
+    "splx_batch_set_timing": (C.c_int, [_P, C.c_int]),
+    "splx_batch_kernel_times": (C.c_int, [_P, _P]),
+    "splx_batch_counters": (C.c_int, [_P, _P, _P]),
+    "splx_graph_begin": (C.c_int, [_P, _P]),
+    "splx_graph_end": (C.c_int, [_P, _P, C.POINTER(_P)]),
+    "splx_graph_launch": (C.c_int, [_P, _P]),
+    "splx_graph_destroy": (C.c_int, [_P]),
+    "splx_device_status": (C.c_int, [_P, _P]),
+    "splx_strerror": (C.c_char_p, [C.c_int]),
+    "splx_last_cuda_error": (C.c_char_p, []),
+    "splx_launch_count": (C.c_int64, [_P]),
+}
+for _name, (_res, _args) in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sigs)
+
+
+def _check(code, where):
+    if code != OK:
+        raise SplxError(code, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda or t.dtype not in (torch.float32, torch.int32) or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA float32/int32 tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------- struct helpers
+def gaussians(means, log_scales, quats, opacity_logits, sh, sh_degree) -> Gaussians:
+    n = means.shape[0]
+    return Gaussians(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity_logits), _ptr(sh),
+                     n, sh_degree)
+
+
+def params(means, log_scales, quats, opacity_logits, sh, sh_degree) -> Params:
+    return Params(*[getattr(gaussians(means, log_scales, quats, opacity_logits, sh, sh_degree), f)
+                    for f, _ in Gaussians._fields_])
+
+
+def camera(cam) -> Camera:
+    c = Camera()
+    c.R[:] = [float(x) for x in np.asarray(cam.R, np.float32).reshape(-1)]
+    c.t[:] = [float(x) for x in np.asarray(cam.t, np.float32).reshape(-1)]
+    c.fx, c.fy, c.cx, c.cy = cam.fx, cam.fy, cam.cx, cam.cy
+    c.width, c.height, c.near_plane = cam.width, cam.height, cam.near
+    return c
+
+
+def opts(tile=16, eps_T=1e-4, eps_comp=1e-4, alpha_min=1.0 / 255.0, alpha_max=0.99,
+         bg=(0.0, 0.0, 0.0)) -> Opts:
+    o = Opts()
+    o.tile, o.eps_T, o.eps_comp, o.alpha_min, o.alpha_max = tile, eps_T, eps_comp, alpha_min, alpha_max
+    o.bg[:] = list(bg)
+    return o
+
+
+# ---------------------------------------------------------------- context
+class Context:
+    """A libsplx context on one CUDA device (scratch pool + HBM budget)."""
+
+    def __init__(self, device: int | None = None, hbm_budget_bytes: int = 0):
+        self.device = torch.cuda.current_device() if device is None else device
+        h = C.c_void_p()
+        _check(_lib.splx_create(C.byref(h), self.device, hbm_budget_bytes), "splx_create")
+        self.h = h
+        self._lock = threading.Lock()
+
+    def close(self):
+        if self.h:
+            _lib.splx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def scratch_bytes(self) -> int:
+        return int(_lib.splx_scratch_bytes(self.h))
+
+    @property
+    def launch_count(self) -> int:
+        return int(_lib.splx_launch_count(self.h))
+
+    def device_status(self, stream=None) -> int:
+        return int(_lib.splx_device_status(self.h, _stream(stream)))
+
+
+class State:
+    """Forward state of one (view, subset) render, released on close/garbage collection."""
+
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+
+    def export(self, stream=None):
+        """(ranges [n_tiles,2] uint32, sorted indices [n_pairs] uint32, records [n,16] f32)
+        as CPU numpy arrays."""
+        npairs, ntiles = C.c_int64(), C.c_int64()
+        _check(_lib.splx_state_export(self.ctx.h, self.h, C.byref(npairs), C.byref(ntiles), None,
+                                      None, None, _stream(stream)), "splx_state_export")
+        n = _lib_state_n(self)
+        ranges = torch.empty(max(ntiles.value, 1) * 2, dtype=torch.int32, device="cuda")
+        vals = torch.empty(max(npairs.value, 1), dtype=torch.int32, device="cuda")
+        rec = torch.empty(max(n, 1) * 16, dtype=torch.float32, device="cuda")
+        _check(_lib.splx_state_export(self.ctx.h, self.h, None, None, _ptr(ranges), _ptr(vals),
+                                      _ptr(rec), _stream(stream)), "splx_state_export")
+        r = ranges.cpu().numpy().view(np.uint32)[:2 * ntiles.value].reshape(-1, 2)
+        v = vals.cpu().numpy().view(np.uint32)[:npairs.value]
+        return r, v, rec.cpu().numpy()[:16 * n].reshape(-1, 16)
+
+    def close(self, stream=None):
+        if self.h:
+            _lib.splx_state_release(self.ctx.h, self.h, _stream(stream))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _lib_state_n(state) -> int:
+    return state.n
+
+
+def new_partial(H, W, device=None):
+    dev = device or torch.device("cuda")
+    return dict(rgb=torch.empty(3, H, W, device=dev), T=torch.empty(H, W, device=dev),
+                depth=torch.empty(H, W, device=dev),
+                last=torch.empty(H, W, device=dev, dtype=torch.int32))
+
+
+def _partial_struct(p) -> Partial:
+    return Partial(_ptr(p["rgb"]), _ptr(p["T"]), _ptr(p["depth"]), _ptr(p["last"]))
+
+
+# ---------------------------------------------------------------- per-view entry points
+def render_partial(ctx: Context, subset: Gaussians, cam, o: Opts, out: dict, keep_state=True,
+                   stream=None):
+    """Local render of one subset into `out` (a new_partial dict); returns a State."""
+    c = cam if isinstance(cam, Camera) else camera(cam)
+    h = C.c_void_p()
+    ps = _partial_struct(out)
+    _check(_lib.splx_render_partial(ctx.h, C.byref(subset), C.byref(c), C.byref(o), C.byref(ps),
+                                    C.byref(h) if keep_state else None, _stream(stream)),
+           "splx_render_partial")
+    if not keep_state:
+        return None
+    st = State(ctx, h)
+    st.n = int(subset.n)
+    return st
+
+
+def composite(ctx: Context, parts, W, H, o: Opts, out_rgb, out_T=None, stream=None):
+    arr = (Partial * len(parts))(*[_partial_struct(p) for p in parts])
+    _check(_lib.splx_composite(ctx.h, arr, len(parts), W, H, C.byref(o), _ptr(out_rgb),
+                               _ptr(out_T), _stream(stream)), "splx_composite")
+
+
+def backward(ctx: Context, subsets, cam, parts, states, dL_drgb, dL_dT, o: Opts, grads,
+             stream=None):
+    K = len(subsets)
+    c = cam if isinstance(cam, Camera) else camera(cam)
+    sarr = (Gaussians * K)(*subsets)
+    parr = (Partial * K)(*[_partial_struct(p) for p in parts])
+    starr = (C.c_void_p * K)(*[s.h for s in states])
+    garr = (Params * K)(*grads)
+    _check(_lib.splx_backward(ctx.h, sarr, K, C.byref(c), parr, starr, _ptr(dL_drgb), _ptr(dL_dT),
+                              C.byref(o), garr, _stream(stream)), "splx_backward")
+
+
+def adam_hp(lr, betas=(0.9, 0.999), eps=1e-15, zero_grad=False) -> Adam:
+    hp = Adam()
+    hp.lr[:] = list(lr)
+    hp.beta1, hp.beta2, hp.eps, hp.zero_grad = betas[0], betas[1], eps, int(bool(zero_grad))
+    return hp
+
+
+def step(ctx: Context, p: Params, g: Params, m: Params, v: Params, lr, step_idx, betas=(0.9, 0.999),
+         eps=1e-15, zero_grad=False, stream=None):
+    hp = adam_hp(lr, betas, eps, zero_grad)
+    _check(_lib.splx_step(ctx.h, C.byref(p), C.byref(g), C.byref(m), C.byref(v), C.byref(hp),
+                          int(step_idx), _stream(stream)), "splx_step")
+
+
+def step_device(ctx: Context, p: Params, g: Params, m: Params, v: Params, hp: Adam, step_dev,
+                stream=None):
+    """Adam with the step counter in device memory (an int64 CUDA tensor of one element)."""
+    if step_dev.dtype != torch.int64 or not step_dev.is_cuda:
+        raise ValueError("step_dev must be a CUDA int64 tensor")
+    _check(_lib.splx_step_device(ctx.h, C.byref(p), C.byref(g), C.byref(m), C.byref(v),
+                                 C.byref(hp), C.c_void_p(step_dev.data_ptr()), _stream(stream)),
+           "splx_step_device")
+
+
+def loss_l1(ctx: Context, img, target, loss_out, dL_dimg=None, stream=None):
+    _check(_lib.splx_loss_l1(ctx.h, _ptr(img), _ptr(target), img.numel(), _ptr(loss_out),
+                             _ptr(dL_dimg), _stream(stream)), "splx_loss_l1")
+
+
+# ---------------------------------------------------------------- batched path
+class Batch:
+    """A planned batch of V views x K subsets (persistent scratch, capturable runs)."""
+
+    def __init__(self, ctx: Context, subsets, cams, o: Opts, pair_capacity=0, stream=None):
+        self.ctx = ctx
+        self.K, self.V = len(subsets), len(cams)
+        self._subsets = (Gaussians * self.K)(*subsets)
+        self._cams = (Camera * self.V)(*[c if isinstance(c, Camera) else camera(c) for c in cams])
+        self.sizes = [(c.height, c.width) for c in self._cams]
+        h = C.c_void_p()
+        _check(_lib.splx_batch_create(ctx.h, self._subsets, self.K, self._cams, self.V, C.byref(o),
+                                      int(pair_capacity), C.byref(h), _stream(stream)),
+               "splx_batch_create")
+        self.h = h
+        rgb_off = (C.c_int64 * (self.V + 1))()
+        pix_off = (C.c_int64 * (self.V + 1))()
+        _check(_lib.splx_batch_layout(self.h, rgb_off, pix_off), "splx_batch_layout")
+        self.rgb_off = list(rgb_off)
+        self.pix_off = list(pix_off)
+
+    @property
+    def total_pixels(self) -> int:
+        return self.pix_off[-1]
+
+    def set_cameras(self, cams, stream=None):
+        arr = (Camera * self.V)(*[c if isinstance(c, Camera) else camera(c) for c in cams])
+        _check(_lib.splx_batch_set_cameras(self.h, arr, self.V, _stream(stream)),
+               "splx_batch_set_cameras")
+
+    def forward(self, out_rgb, out_T=None, stream=None):
+        _check(_lib.splx_batch_forward(self.h, _ptr(out_rgb), _ptr(out_T), _stream(stream)),
+               "splx_batch_forward")
+
+    def backward(self, dL_drgb, dL_dT, grads, stream=None):
+        garr = (Params * self.K)(*grads)
+        _check(_lib.splx_batch_backward(self.h, _ptr(dL_drgb), _ptr(dL_dT), garr, _stream(stream)),
+               "splx_batch_backward")
+
+    def status(self, stream=None):
+        pairs = C.c_int64()
+        code = _lib.splx_batch_status(self.h, C.byref(pairs), _stream(stream))
+        return code, int(pairs.value)
+
+    KERNELS = ("project", "scan", "emit", "sort", "ranges", "raster_fwd", "composite",
+               "composite_bwd", "raster_bwd", "project_bwd")
+
+    def set_timing(self, enable=True):
+        _check(_lib.splx_batch_set_timing(self.h, int(bool(enable))), "splx_batch_set_timing")
+
+    def kernel_times(self) -> dict:
+        arr = (C.c_float * 10)()
+        _check(_lib.splx_batch_kernel_times(self.h, arr), "splx_batch_kernel_times")
+        return dict(zip(self.KERNELS, [float(x) for x in arr]))
+
+    def counters(self, stream=None) -> dict:
+        arr = (C.c_int64 * 4)()
+        _check(_lib.splx_batch_counters(self.h, arr, _stream(stream)), "splx_batch_counters")
+        return dict(pairs=arr[0], evaluated_fwd=arr[1], blended=arr[2], evaluated_bwd=arr[3])
+
+    def views(self, flat_rgb):
+        """Split a concatenated rgb buffer into per-view [3,H,W] tensors."""
+        return [flat_rgb[self.rgb_off[v]:self.rgb_off[v + 1]].view(3, *self.sizes[v])
+                for v in range(self.V)]
+
+    def close(self):
+        if self.h:
+            _lib.splx_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    """A CUDA graph of library calls captured on one stream."""
+
+    def __init__(self, h):
+        self.h = h
+
+    def launch(self, stream=None):
+        _check(_lib.splx_graph_launch(self.h, _stream(stream)), "splx_graph_launch")
+
+    def close(self):
+        if self.h:
+            _lib.splx_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def graph_begin(ctx: Context, stream):
+    _check(_lib.splx_graph_begin(ctx.h, _stream(stream)), "splx_graph_begin")
+
+
+def graph_end(ctx: Context, stream) -> Graph:
+    h = C.c_void_p()
+    _check(_lib.splx_graph_end(ctx.h, _stream(stream), C.byref(h)), "splx_graph_end")
+    return Graph(h)

@@ -1,0 +1,135 @@
+"""Batched V x K path (one launch per stage for all views and subsets) against the plain
+per-view path, CUDA-graph replay, capacity overflow detection and the L1 loss."""
+import numpy as np
+import pytest
+
+from paper_2606_18588_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2606_18588_gb300 import splx as S
+    c = S.Context()
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def scene():
+    sc, off, _, cams = I.cluster_case(30_000, 11, 4, 3, [(200, 120), (96, 64), (131, 77)])
+    return sc, off, cams
+
+
+def _subsets(dev, off, deg):
+    from gpu_util import subset_struct
+    return [subset_struct(dev, int(off[k]), int(off[k + 1]), deg) for k in range(len(off) - 1)]
+
+
+def _grads(g, off, deg):
+    from gpu_util import params_struct
+    return [params_struct(g, int(off[k]), int(off[k + 1]), deg) for k in range(len(off) - 1)]
+
+
+def test_batch_forward_equals_plain_and_backward_matches(ctx, scene):
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import backward_view, render_view, rel_l2, to_device, zeros_like_params
+    sc, off, cams = scene
+    dev = to_device(sc)
+    o = S.opts()
+    b = S.Batch(ctx, _subsets(dev, off, sc.sh_degree), cams, o)
+    rgb = torch.empty(b.rgb_off[-1], device="cuda")
+    T = torch.empty(b.total_pixels, device="cuda")
+    b.forward(rgb, T)
+    code, pairs = b.status()
+    assert code == S.OK and pairs > 0
+    rng = np.random.default_rng(0)
+    dL = torch.from_numpy(rng.standard_normal(b.rgb_off[-1]).astype(np.float32)).cuda()
+    g = zeros_like_params(dev)
+    b.backward(dL, None, _grads(g, off, sc.sh_degree))
+    torch.cuda.synchronize()
+    g_plain = zeros_like_params(dev)
+    for v, cam in enumerate(cams):
+        img, Tv, parts, states = render_view(ctx, dev, off, cam, o, sc.sh_degree)
+        assert torch.equal(b.views(rgb)[v], img)
+        assert torch.equal(T[b.pix_off[v]:b.pix_off[v + 1]].view(cam.height, cam.width), Tv)
+        gv = backward_view(ctx, dev, off, cam, o, sc.sh_degree, parts, states,
+                           b.views(dL)[v].contiguous(), None)
+        for k in GROUPS:
+            g_plain[k] += gv[k]
+        for s in states:
+            s.close()
+    for k in GROUPS:
+        assert rel_l2(g[k].cpu().numpy(), g_plain[k].cpu().numpy()) < 1e-5, k
+    b.close()
+
+
+def test_graph_replay_is_identical(ctx, scene):
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import to_device, zeros_like_params
+    sc, off, cams = scene
+    dev = to_device(sc)
+    o = S.opts()
+    b = S.Batch(ctx, _subsets(dev, off, sc.sh_degree), cams, o)
+    rgb = torch.empty(b.rgb_off[-1], device="cuda")
+    b.forward(rgb)
+    torch.cuda.synchronize()
+    ref = rgb.clone()
+    rgb.zero_()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        S.graph_begin(ctx, s)
+        b.forward(rgb, stream=s)
+        gr = S.graph_end(ctx, s)
+        gr.launch(s)
+    s.synchronize()
+    assert torch.equal(rgb, ref)
+    gr.close()
+    b.close()
+
+
+def test_capacity_overflow_is_reported_not_faulted(ctx, scene):
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import to_device
+    sc, off, cams = scene
+    dev = to_device(sc)
+    b = S.Batch(ctx, _subsets(dev, off, sc.sh_degree), cams, S.opts(), pair_capacity=1000)
+    rgb = torch.empty(b.rgb_off[-1], device="cuda")
+    b.forward(rgb)
+    code, pairs = b.status()
+    assert code == S.ERR_CAPACITY and pairs > 1000
+    ctx.device_status()  # clears the status word
+    b.close()
+
+
+def test_loss_l1_value_and_gradient(ctx):
+    from paper_2606_18588_gb300 import splx as S
+    rng = np.random.default_rng(1)
+    a = rng.uniform(0, 1, 10007).astype(np.float32)
+    t = rng.uniform(0, 1, 10007).astype(np.float32)
+    t[:7] = a[:7]  # exact ties: zero gradient
+    ad, td = torch.from_numpy(a).cuda(), torch.from_numpy(t).cuda()
+    loss = torch.empty(1, device="cuda")
+    dL = torch.empty_like(ad)
+    S.loss_l1(ctx, ad, td, loss, dL)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(loss.item(), np.abs(a.astype(np.float64) - t).mean(), rtol=1e-5)
+    np.testing.assert_array_equal(dL.cpu().numpy(), (np.sign(a - t) / a.size).astype(np.float32))
+
+
+def test_hbm_budget_is_enforced(ctx):
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import subset_struct, to_device
+    small = S.Context(hbm_budget_bytes=1 << 16)
+    sc, cam = I.plain_forward_case(0, n=5000)
+    dev = to_device(sc)
+    p = S.new_partial(cam.height, cam.width)
+    with pytest.raises(S.SplxError) as e:
+        S.render_partial(small, subset_struct(dev, 0, sc.n, 0), cam, S.opts(), p)
+    assert e.value.code == S.ERR_BUDGET
+    assert small.scratch_bytes == 0
+    small.close()

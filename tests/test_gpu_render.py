@@ -1,0 +1,199 @@
+"""GPU parity of the forward path (through the C ABI) against the FP64 oracle.
+
+Binning (cull, rectangle, depth key, per-tile sorted lists) must match bit for bit;
+pixels within 1e-4 max-abs outside the oracle's ambiguity guard band."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2606_18588_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2606_18588_gb300 import splx as S
+    c = S.Context()
+    yield c
+    c.close()
+
+
+def _cases():
+    sc1, cam1 = I.plain_forward_case(0)
+    sc2 = I.cluster_scene(20_000, 2, 3)
+    cam2 = I.orbit_cameras(1, 3, [(333, 197)])[0]
+    sc3 = I.uniform_scene(3000, 4, 1, log_scale_mu=-2.5)
+    cam3 = I.pinhole(97, 61, 75.0, (0.4, -0.3, -2.2), (0, 0, 0))
+    return {"plain_10k_sh0_256": (sc1, cam1), "cluster_20k_sh3_ragged": (sc2, cam2),
+            "uniform_3k_sh1_large": (sc3, cam3)}
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("tile", [16, 8, 32])
+def test_binning_bit_exact(ctx, name, tile):
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import decode_records, subset_struct, to_device
+    sc, cam = CASES[name]
+    dev = to_device(sc)
+    p = S.new_partial(cam.height, cam.width)
+    st = S.render_partial(ctx, subset_struct(dev, 0, sc.n, sc.sh_degree), cam, S.opts(tile=tile), p)
+    ranges, vals, rec = st.export()
+    vis_g, rect_g, db_g = decode_records(rec)
+    vis_o, rect_o, db_o = O.bin(sc, cam)
+    assert np.array_equal(vis_g, vis_o)
+    m = vis_o.astype(bool)
+    assert np.array_equal(rect_g[m], rect_o[m])
+    assert np.array_equal(db_g[m], db_o[m])
+    start, lst = O.tile_lists(sc, cam, tile)
+    assert vals.size == lst.size
+    nt = start.size - 1
+    assert ranges.shape[0] == nt
+    for t in range(nt):
+        a, b = int(start[t]), int(start[t + 1])
+        ga, gb = int(ranges[t, 0]), int(ranges[t, 1])
+        if b == a:
+            assert gb <= ga
+            continue
+        assert np.array_equal(vals[ga:gb], lst[a:b].astype(np.uint32)), t
+    st.close()
+
+
+def _compare_pixels(gpu, orc, amb, tol=1e-4):
+    ok = amb == 0
+    assert ok.mean() > 0.99
+    err = np.abs(gpu - orc)
+    if err.ndim == 3:
+        err = err.max(axis=0)
+    return float(err[ok].max()) if ok.any() else 0.0
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_partial_render_matches_oracle(ctx, name):
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import PIXEL_TOL, subset_struct, to_device
+    sc, cam = CASES[name]
+    dev = to_device(sc)
+    o = S.opts()
+    p = S.new_partial(cam.height, cam.width)
+    st = S.render_partial(ctx, subset_struct(dev, 0, sc.n, sc.sh_degree), cam, o, p)
+    ranges, vals, _ = st.export()
+    torch.cuda.synchronize()
+    ref = O.render(sc, cam, O.opts())
+    amb = ref["amb"]
+    assert _compare_pixels(p["rgb"].cpu().numpy(), ref["C"], amb) <= PIXEL_TOL
+    assert _compare_pixels(p["T"].cpu().numpy(), ref["T"], amb) <= PIXEL_TOL
+    D = p["depth"].cpu().numpy()
+    ok = amb == 0
+    assert np.all(np.abs(D - ref["D"])[ok] <= PIXEL_TOL * (1.0 + np.abs(ref["D"][ok])))
+    # last blended Gaussian: GPU list position -> Gaussian index, exact off the guard band
+    last = p["last"].cpu().numpy()
+    H, W = cam.height, cam.width
+    tw = (W + 15) // 16
+    ty, tx = np.mgrid[0:H, 0:W]
+    tiles = (ty // 16) * tw + (tx // 16)
+    gid = np.where(last >= 0, vals[np.minimum(ranges[tiles, 0] + np.maximum(last, 0),
+                                              max(vals.size - 1, 0))].astype(np.int64), -1)
+    assert np.array_equal(gid[ok], ref["last"][ok])
+    st.close()
+
+
+def test_forward_bit_identical_across_tile_sizes(ctx):
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import subset_struct, to_device
+    sc, cam = CASES["cluster_20k_sh3_ragged"]
+    dev = to_device(sc)
+    outs = []
+    for tile in (8, 16, 32):
+        p = S.new_partial(cam.height, cam.width)
+        S.render_partial(ctx, subset_struct(dev, 0, sc.n, sc.sh_degree), cam, S.opts(tile=tile), p,
+                         keep_state=False)
+        torch.cuda.synchronize()
+        outs.append({k: p[k].cpu().numpy() for k in ("rgb", "T", "depth")})
+    for o in outs[1:]:
+        for k in ("rgb", "T", "depth"):
+            assert np.array_equal(o[k], outs[0][k]), k
+
+
+def test_composite_matches_oracle_and_monolithic(ctx):
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import PIXEL_TOL, render_view, to_device
+    sc, off, _, cams = I.cluster_case(40_000, 5, 4, 1, [(320, 200)])
+    cam = cams[0]
+    dev = to_device(sc)
+    o = S.opts()
+    img, T, parts, states = render_view(ctx, dev, off, cam, o, sc.sh_degree)
+    ref = O.render_view(sc, off, cam, O.opts(), separable=True)
+    ok = ref["amb"] == 0
+    assert ok.mean() > 0.99
+    err = np.abs(img.cpu().numpy() - ref["image"]).max(axis=0)
+    assert err[ok].max() <= PIXEL_TOL
+    assert np.abs(T.cpu().numpy() - ref["T"])[ok].max() <= PIXEL_TOL
+    # composition alone: the oracle's Eq. 5 on the GPU's own partials
+    Cp = np.stack([p["rgb"].cpu().numpy() for p in parts]).astype(np.float64)
+    Tp = np.stack([p["T"].cpu().numpy() for p in parts]).astype(np.float64)
+    Dp = np.stack([p["depth"].cpu().numpy() for p in parts]).astype(np.float64)
+    rc = O.composite(Cp, Tp, Dp, O.opts())
+    okc = rc["amb"] == 0
+    assert np.abs(img.cpu().numpy() - rc["image"]).max(axis=0)[okc].max() <= 1e-5
+    # Eq. 5 == Eq. 2 on separable pixels: GPU composite vs GPU monolithic render
+    mono = S.new_partial(cam.height, cam.width)
+    from gpu_util import subset_struct
+    S.render_partial(ctx, subset_struct(dev, 0, sc.n, sc.sh_degree), cam, o, mono, keep_state=False)
+    torch.cuda.synchronize()
+    mono_ref = O.render(sc, cam, O.opts())
+    sep = (ref["sep"] == 1) & ok & (mono_ref["amb"] == 0)
+    assert sep.mean() > 0.5
+    e2 = np.abs(img.cpu().numpy() - mono["rgb"].cpu().numpy()).max(axis=0)
+    assert e2[sep].max() <= 2e-4 + 1e-5
+    for s in states:
+        s.close()
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (17, 3), (5, 40)])
+def test_tiny_and_ragged_images(ctx, W, H):
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import PIXEL_TOL, subset_struct, to_device
+    sc = I.uniform_scene(500, 9, 0, log_scale_mu=-2.0)
+    cam = I.pinhole(W, H, 60.0, (0, 0, -3), (0, 0, 0))
+    dev = to_device(sc)
+    p = S.new_partial(H, W)
+    S.render_partial(ctx, subset_struct(dev, 0, sc.n, 0), cam, S.opts(tile=8), p, keep_state=False)
+    torch.cuda.synchronize()
+    ref = O.render(sc, cam, O.opts(tile=8))
+    assert _compare_pixels(p["rgb"].cpu().numpy(), ref["C"], ref["amb"]) <= PIXEL_TOL
+
+
+def test_empty_and_fully_culled_subsets(ctx):
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import subset_struct, to_device
+    sc = I.uniform_scene(64, 1, 0)
+    sc.means[:, 2] = -10.0  # all behind the camera at z = -3
+    cam = I.pinhole(40, 30, 60.0, (0, 0, -3), (0, 0, 0))
+    dev = to_device(sc)
+    for lo, hi in ((0, 0), (0, 64)):
+        p = S.new_partial(30, 40)
+        S.render_partial(ctx, subset_struct(dev, lo, hi, 0), cam, S.opts(), p, keep_state=False)
+        torch.cuda.synchronize()
+        assert torch.all(p["T"] == 1.0) and torch.all(p["rgb"] == 0.0)
+        assert torch.all(p["last"] == -1)
+
+
+def test_invalid_arguments_are_rejected(ctx):
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import subset_struct, to_device
+    sc, cam = I.plain_forward_case(0, n=100)
+    dev = to_device(sc)
+    p = S.new_partial(cam.height, cam.width)
+    with pytest.raises(S.SplxError) as e:
+        S.render_partial(ctx, subset_struct(dev, 0, sc.n, 0), cam, S.opts(tile=12), p)
+    assert e.value.code == S.ERR_INVALID
+    bad = subset_struct(dev, 0, sc.n, 0)
+    bad.quats = dev["quats"].data_ptr() + 4  # misaligned quaternion array
+    with pytest.raises(S.SplxError):
+        S.render_partial(ctx, bad, cam, S.opts(), p)
