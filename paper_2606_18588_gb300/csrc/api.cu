@@ -189,7 +189,13 @@ struct Plan {
   cudaEvent_t ev[12] = {};
 
   void mark(int i, cudaStream_t s) {
-    if (timing && ev[i]) cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
+    if (!timing || !ev[i]) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+      cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
+    else
+      cudaEventRecord(ev[i], s);
   }
 
   void layout() {
@@ -218,7 +224,8 @@ struct Plan {
     b.keys = keys[0]; b.vals = vals[0]; b.ranges = ranges; b.grad2d = grad2d;
     b.status = ctx->d_status;
     b.counters = counters;
-    for (int k = 0; k <= K; ++k) b.goff[k] = k < K ? subsets_h[k].goff : N;
+    // composite-only plans carry no subsets; their offsets are unused
+    for (int k = 0; k <= K; ++k) b.goff[k] = k < (int)subsets_h.size() ? subsets_h[k].goff : N;
     for (int v = 0; v <= V; ++v) { b.tile_base[v] = tile_base[v]; b.pix_off[v] = pix_off[v]; }
     return b;
   }
