@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched_10m_k8")
-    ap.add_argument("--n", type=int, default=0, help="override Gaussian count (testing)")
+    ap.add_argument("--n", type=int, default=0, help="override Gaussian count (profiling)")
+    ap.add_argument("--views", type=int, default=0, help="override view count (profiling)")
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--no-plain", action="store_true")
@@ -56,11 +57,11 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def make_workload(name, n_override=0, seed=3, rank=0):
+def make_workload(name, n_override=0, seed=3, rank=0, views_override=0):
     from paper_2606_18588_gb300 import inputs as I
     w = dict(I.WORKLOADS[name])
     n = n_override or w["n"]
-    views = max(1, w["views"])
+    views = views_override or max(1, w["views"])
     sc, off, _, cams = I.cluster_case(n, seed, w["K"], views, w["sizes"], w["sh_degree"])
     if rank:
         cams = I.orbit_cameras(views, seed + 1 + 1000 * rank, w["sizes"])
@@ -207,7 +208,7 @@ def run_reference(args):
         return 0
     from oracle import oracle as O
     O.build()
-    sc, off, cams, _, desc = make_workload(args.workload, args.n)
+    sc, off, cams, _, desc = make_workload(args.workload, args.n, views_override=args.views)
     cam = cams[0]
     times = []
     info = ""
@@ -244,7 +245,8 @@ def main():
     from paper_2606_18588_gb300 import splx as S
     from paper_2606_18588_gb300.train import BatchedStep, PlainStep, scene_to_device
 
-    sc, off, cams, targets, desc = make_workload(args.workload, args.n, rank=rank)
+    sc, off, cams, targets, desc = make_workload(args.workload, args.n, rank=rank,
+                                                 views_override=args.views)
     ctx = S.Context(local)
     dev = scene_to_device(sc)
     o = S.opts(tile=args.tile)
