@@ -241,6 +241,27 @@ int splx_graph_end(splx_ctx_t ctx, splx_stream_t stream, splx_graph_t* out);
 int splx_graph_launch(splx_graph_t g, splx_stream_t stream);
 int splx_graph_destroy(splx_graph_t g);
 
+/* ---- allocation-free local render ----------------------------------------------- */
+/* The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory: a process whose HBM is reserved up front by another allocator
+ * (an inference server's arena, a framework caching allocator that already holds the
+ * device), or a latency-critical loop where the implicit device synchronisation of
+ * cudaMalloc/cudaFree is not acceptable.  It computes exactly what splx_render_partial
+ * computes (same kernels) but takes no context, keeps no forward state and allocates
+ * nothing: its scratch is one fixed 32 MiB array that every GPU which loads libsplx holds
+ * until the process exits.  The caller passes the inputs and the output planes.
+ *   - Limits: subset->n <= 65536 Gaussians, at most 2^20 (Gaussian, tile) pairs and at
+ *     most 65536 tiles; larger requests return SPLX_ERR_INVALID before any work, and a
+ *     pair overflow found on the device returns SPLX_ERR_CAPACITY (output not valid).
+ *   - The first call on a device looks up the array's device address (with that device
+ *     current) and caches it; make that first call before any stream capture.
+ *   - All calls share the array and leave their contents in it: calls that overlap on
+ *     the GPU (other streams, other host threads) race on it and must be serialised.
+ *   - Synchronises `stream` once at the end to read the device status. */
+int splx_render_partial_noalloc(const splx_gaussians* subset, const splx_camera* cam,
+                                const splx_opts* opts, const splx_partial* out,
+                                splx_stream_t stream);
+
 /* ---- diagnostics ---------------------------------------------------------------- */
 /* Synchronises `stream`, returns and clears the context's device status word
  * (SPLX_OK, SPLX_ERR_CAPACITY or SPLX_ERR_TIMEOUT). */

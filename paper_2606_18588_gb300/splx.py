@@ -94,6 +94,7 @@ _sigs = {
     "splx_graph_end": (C.c_int, [_P, _P, C.POINTER(_P)]),
     "splx_graph_launch": (C.c_int, [_P, _P]),
     "splx_graph_destroy": (C.c_int, [_P]),
+    "splx_render_partial_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "splx_device_status": (C.c_int, [_P, _P]),
     "splx_strerror": (C.c_char_p, [C.c_int]),
     "splx_last_cuda_error": (C.c_char_p, []),
@@ -254,6 +255,17 @@ def render_partial(ctx: Context, subset: Gaussians, cam, o: Opts, out: dict, kee
     st = State(ctx, h)
     st.n = int(subset.n)
     return st
+
+
+def render_partial_noalloc(subset: Gaussians, cam, o: Opts, out: dict, stream=None):
+    """Local render of one subset without any device allocation, for callers that cannot
+    allocate (their HBM is held by another allocator, or cudaMalloc's implicit
+    synchronisation is not allowed in their loop).  Uses the library's fixed 32 MiB
+    scratch array; limits and sharing rules are those of splx_render_partial_noalloc."""
+    c = cam if isinstance(cam, Camera) else camera(cam)
+    ps = _partial_struct(out)
+    _check(_lib.splx_render_partial_noalloc(C.byref(subset), C.byref(c), C.byref(o), C.byref(ps),
+                                            _stream(stream)), "splx_render_partial_noalloc")
 
 
 def composite(ctx: Context, parts, W, H, o: Opts, out_rgb, out_T=None, stream=None):
