@@ -151,15 +151,13 @@ def roofline(name, ms, counts, w, pk):
                 "work": f"{pairs} examined pairs x {per} FP32 instr"}
     param_bytes = (3 + 3 + 4 + 1 + 3 * nc) * 4
     if name == "sort":
-        bits = 32 + max(1, math.ceil(math.log2(w["n_tiles"] + 1)))
-        passes = math.ceil(bits / 8)
-        byts = counts["pairs"] * passes * 24
+        byts = counts["pairs"] * 16  # each tile segment read and written once
     elif name == "project":
         byts = N * param_bytes + V * N * (64 + 4)
     elif name == "project_bwd":
         byts = N * (3 * param_bytes) + V * N * 96
-    elif name == "emit":
-        byts = V * N * (4 + 8 + 16) + counts["pairs"] * 12
+    elif name == "fill":
+        byts = V * N * (4 + 32) + counts["pairs"] * 8
     elif name in ("composite", "composite_bwd"):
         byts = pixels * (K * 20 + 16) if name == "composite" else pixels * (K * 36 + 12)
     elif name == "adam":
@@ -359,9 +357,9 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "global_batch": len(cams) * world,
                        "pixels_per_step": pixels * world, "tile": args.tile,
-                       "path": "batched: one CUDA graph per step (project, scan, emit, radix sort, "
-                               "ranges, raster fwd, composite, L1 loss, composite bwd, raster bwd, "
-                               "project bwd, Adam)",
+                       "path": "batched: one CUDA graph per step (project + tile counts, scan, "
+                               "fill tile buckets, per-tile depth sort, raster fwd, composite, L1 "
+                               "loss, composite bwd, raster bwd, project bwd, Adam)",
                        "l2": "inputs larger than L2 (2.4 GB parameters, 10 GB projected records)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "plain": plain, "kernel_ms": kmean, "counters": counts},

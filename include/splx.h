@@ -128,8 +128,8 @@ size_t splx_scratch_bytes(splx_ctx_t ctx);
 /* ---- per-view entry points (Sec. 4.1) ------------------------------------------- */
 
 /* Local rendering of one subset for one view (Sec. 4.1, Eq. 3-4; steps 1-3 of Sec. 2):
- * projection with EWA covariance, SH colour, 16x16 (opts->tile) binning, radix sort by
- * (tile, depth) with the Gaussian index as tie-break, front-to-back alpha blending into
+ * projection with EWA covariance, SH colour, 16x16 (opts->tile) binning, sort of each
+ * tile's list by depth with the Gaussian index as tie-break, front-to-back blending into
  * `out` (sized to cam->width x cam->height).  If state_out is non-NULL the projected
  * records and sorted lists are kept for splx_backward and must be released with
  * splx_state_release.  Synchronises once (to size the pair list). */
@@ -159,13 +159,14 @@ int splx_backward(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
 /* Diagnostic export of a forward state (synchronises): the pair count and tile count
  * (host, either nullable), then - for each non-NULL device buffer - the per-tile
  * [start, end) ranges into the sorted list (ranges_out: n_tiles x 2 uint32), the sorted
- * Gaussian indices (vals_out: n_pairs uint32) and the 64-byte projected records
+ * keys (keys_out: n_pairs uint64, FP32 depth bits << 32 | Gaussian index, each tile's
+ * segment ascending) and the 64-byte projected records
  * (rec_out: n x 16 floats: u, v, qa, qb | qc, opacity, depth, rect_x | r, g, b, rect_y |
  * 0,0,0,0 where rect_x = x0 | x1 << 16 and rect_y = y0 | y1 << 16 as bit patterns and
  * (qa, qb, qc) = -log2(e) * (A/2, B, C/2) for the conic (A, B, C); a culled Gaussian has
  * x0 = 0xFFFF > x1).  Tiles are numbered row-major. */
 int splx_state_export(splx_ctx_t ctx, splx_state_t state, int64_t* n_pairs, int64_t* n_tiles,
-                      uint32_t* ranges_out, uint32_t* vals_out, float* rec_out,
+                      uint32_t* ranges_out, uint64_t* keys_out, float* rec_out,
                       splx_stream_t stream);
 
 /* Releases a forward state (stream-ordered). */
@@ -224,7 +225,7 @@ int splx_batch_destroy(splx_batch_t b);
 /* Per-kernel timing (off by default).  When enabled the batch records CUDA events around
  * each of its kernels; inside a captured graph they become event nodes, so every replay
  * re-records them.  splx_batch_kernel_times waits for the last run's final event and
- * writes 10 durations in ms (host array): project, scan, emit, sort, ranges, raster_fwd,
+ * writes 9 durations in ms (host array): project, scan, fill, sort, raster_fwd,
  * composite, composite_bwd, raster_bwd, project_bwd. */
 int splx_batch_set_timing(splx_batch_t b, int enable);
 int splx_batch_kernel_times(splx_batch_t b, float* ms_out);

@@ -171,22 +171,25 @@ struct Plan {
   ImgDev* imgs_d = nullptr;
   Rec* rec = nullptr;
   uint32_t* counts = nullptr;
-  uint64_t* offsets = nullptr;
-  uint64_t* keys[2] = {nullptr, nullptr};
-  uint32_t* vals[2] = {nullptr, nullptr};
+  uint32_t* tile_cnt = nullptr;
+  uint32_t* tile_start = nullptr;
+  uint64_t* keys = nullptr;
+  uint64_t* keys_alt = nullptr;
+  uint32_t* big_list = nullptr;
+  unsigned* big_count = nullptr;
   uint2* ranges = nullptr;
   float4* grad2d = nullptr;
   unsigned long long* counters = nullptr;  // [4]: see BatchDev::counters
   void* scan_temp = nullptr;
-  void* sort_temp = nullptr;
   int64_t capacity = 0, n_tiles = 0, total_pixels = 0;
-  int sorted_alt = 0;  // which buffer holds the sorted pairs
   splx_opts opts{};
   std::vector<int64_t> tile_base, pix_off;
-  // per-kernel timing: events at the marks of Mark, recorded as graph event nodes when
-  // the stream is being captured
+  // per-kernel timing: events at the marks below, recorded as graph event nodes when
+  // the stream is being captured.  Forward: 0 start, 1 project, 2 scan, 3 fill, 4 sort,
+  // 5 raster_fwd, 6 composite; backward: 7 start, 8 composite_bwd, 9 raster_bwd,
+  // 10 project_bwd.
   bool timing = false;
-  cudaEvent_t ev[12] = {};
+  cudaEvent_t ev[11] = {};
 
   void mark(int i, cudaStream_t s) {
     if (!timing || !ev[i]) return;
@@ -220,8 +223,9 @@ struct Plan {
     b.alpha_min = opts.alpha_min; b.alpha_max = opts.alpha_max;
     for (int c = 0; c < 3; ++c) b.bg[c] = opts.bg[c];
     b.subsets = subsets_d; b.views = views_d; b.imgs = imgs_d;
-    b.rec = rec; b.counts = counts; b.offsets = offsets;
-    b.keys = keys[0]; b.vals = vals[0]; b.ranges = ranges; b.grad2d = grad2d;
+    b.rec = rec; b.counts = counts; b.tile_cnt = tile_cnt; b.tile_start = tile_start;
+    b.keys = keys; b.keys_alt = keys_alt; b.big_list = big_list; b.big_count = big_count;
+    b.ranges = ranges; b.grad2d = grad2d;
     b.status = ctx->d_status;
     b.counters = counters;
     // composite-only plans carry no subsets; their offsets are unused
@@ -230,77 +234,95 @@ struct Plan {
     return b;
   }
 
-  void release(cudaStream_t s) {
-    void* ps[] = {subsets_d, views_d, imgs_d, rec, counts, offsets, keys[0], keys[1],
-                  vals[0], vals[1], ranges, grad2d, scan_temp, sort_temp, counters};
-    for (void* p : ps) ctx_free(ctx, p, s);
-    counters = nullptr;
-    for (auto& e : ev)
-      if (e) { cudaEventDestroy(e); e = nullptr; }
-    subsets_d = nullptr; views_d = nullptr; imgs_d = nullptr; rec = nullptr; counts = nullptr;
-    offsets = nullptr; keys[0] = keys[1] = nullptr; vals[0] = vals[1] = nullptr;
-    ranges = nullptr; grad2d = nullptr; scan_temp = nullptr; sort_temp = nullptr;
+  void free_ptr(void*& p, cudaStream_t s) {
+    ctx_free(ctx, p, s);
+    p = nullptr;
   }
 
-  // Project, scan and (if capacity > 0) emit, sort and build ranges.
-  int bin(cudaStream_t s) {
+  void release(cudaStream_t s) {
+    void** ps[] = {(void**)&subsets_d, (void**)&views_d, (void**)&imgs_d, (void**)&rec,
+                   (void**)&counts, (void**)&tile_cnt, (void**)&tile_start, (void**)&keys,
+                   (void**)&keys_alt, (void**)&big_list, (void**)&big_count, (void**)&ranges,
+                   (void**)&grad2d, (void**)&scan_temp, (void**)&counters};
+    for (void** p : ps) free_ptr(*p, s);
+    for (auto& e : ev)
+      if (e) { cudaEventDestroy(e); e = nullptr; }
+  }
+
+  // Project (counting pairs per tile) and scan the counts into segment starts.
+  int project_and_count(cudaStream_t s) {
     const BatchDev b = dev();
     if (counters) CK(cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(n_tiles, 1), s));
+    CK(cudaMemsetAsync(big_count, 0, sizeof(unsigned), s));
     mark(0, s);
     launch_project(b, s);
     CK_LAUNCH();
     mark(1, s);
-    scan_u32_u64(counts, offsets, (int64_t)V * N, scan_temp, s);
+    scan_u32(tile_cnt, tile_start, n_tiles, scan_temp, s);
     CK_LAUNCH();
     mark(2, s);
-    if (capacity <= 0) return SPLX_OK;
-    launch_emit(b, s);
+    return SPLX_OK;
+  }
+
+  // Fill the tile buckets and sort every segment (needs capacity > 0).
+  int fill_and_sort(cudaStream_t s) {
+    const BatchDev b = dev();
+    launch_fill(b, s);
     CK_LAUNCH();
     mark(3, s);
-    const int bits = 32 + b.tile_bits;
-    const uint64_t* n_dev = offsets + (int64_t)V * N;
-    sorted_alt = radix_sort_pairs(keys[0], vals[0], keys[1], vals[1], n_dev, capacity, bits,
-                                  sort_temp, s) ? 1 : 0;
+    launch_seg_sort(b, s);
     CK_LAUNCH();
     mark(4, s);
-    CK(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)std::max<int64_t>(n_tiles, 1), s));
-    BatchDev b2 = b;
-    b2.keys = keys[sorted_alt];
-    b2.vals = vals[sorted_alt];
-    launch_ranges(b2, keys[sorted_alt], s);
-    CK_LAUNCH();
-    mark(5, s);
     return SPLX_OK;
+  }
+
+  int bin(cudaStream_t s) {
+    int r;
+    if ((r = project_and_count(s))) return r;
+    if (capacity <= 0) return SPLX_OK;
+    return fill_and_sort(s);
   }
 
   int alloc_pairs(int64_t cap, cudaStream_t s) {
     capacity = cap;
     int r;
-    for (int i = 0; i < 2; ++i) {
-      if ((r = ctx_alloc_t(ctx, &keys[i], (size_t)std::max<int64_t>(cap, 1), s))) return r;
-      if ((r = ctx_alloc_t(ctx, &vals[i], (size_t)std::max<int64_t>(cap, 1), s))) return r;
-    }
-    if ((r = ctx_alloc(ctx, &sort_temp, radix_sort_temp_bytes(cap), s))) return r;
+    if ((r = ctx_alloc_t(ctx, &keys, (size_t)std::max<int64_t>(cap, 1), s))) return r;
+    if ((r = ctx_alloc_t(ctx, &keys_alt, (size_t)std::max<int64_t>(cap, 1), s))) return r;
     return SPLX_OK;
   }
 
   int alloc_common(cudaStream_t s) {
     int r;
-    if ((r = ctx_alloc_t(ctx, &subsets_d, subsets_h.size(), s))) return r;
+    const size_t nt = (size_t)std::max<int64_t>(n_tiles, 1);
+    if ((r = ctx_alloc_t(ctx, &subsets_d, std::max<size_t>(subsets_h.size(), 1), s))) return r;
     if ((r = ctx_alloc_t(ctx, &views_d, views_h.size(), s))) return r;
     if ((r = ctx_alloc_t(ctx, &imgs_d, std::max<size_t>(imgs_h.size(), 1), s))) return r;
     if ((r = ctx_alloc_t(ctx, &rec, (size_t)std::max<int64_t>((int64_t)V * N, 1), s))) return r;
     if ((r = ctx_alloc_t(ctx, &counts, (size_t)std::max<int64_t>((int64_t)V * N, 1), s))) return r;
-    if ((r = ctx_alloc_t(ctx, &offsets, (size_t)V * N + 1, s))) return r;
-    if ((r = ctx_alloc(ctx, &scan_temp, scan_u32_u64_temp_bytes((int64_t)V * N), s))) return r;
-    if ((r = ctx_alloc_t(ctx, &ranges, (size_t)std::max<int64_t>(n_tiles, 1), s))) return r;
-    CK(cudaMemcpyAsync(subsets_d, subsets_h.data(), sizeof(SubsetDev) * subsets_h.size(),
-                       cudaMemcpyHostToDevice, s));
+    if ((r = ctx_alloc_t(ctx, &tile_cnt, nt, s))) return r;
+    if ((r = ctx_alloc_t(ctx, &tile_start, nt + 1, s))) return r;
+    if ((r = ctx_alloc_t(ctx, &big_list, nt, s))) return r;
+    if ((r = ctx_alloc_t(ctx, &big_count, 1, s))) return r;
+    if ((r = ctx_alloc(ctx, &scan_temp, scan_u32_temp_bytes(n_tiles), s))) return r;
+    if ((r = ctx_alloc_t(ctx, &ranges, nt, s))) return r;
+    if (!subsets_h.empty())
+      CK(cudaMemcpyAsync(subsets_d, subsets_h.data(), sizeof(SubsetDev) * subsets_h.size(),
+                         cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(views_d, views_h.data(), sizeof(ViewDev) * views_h.size(),
                        cudaMemcpyHostToDevice, s));
     if (!imgs_h.empty())
       CK(cudaMemcpyAsync(imgs_d, imgs_h.data(), sizeof(ImgDev) * imgs_h.size(),
                          cudaMemcpyHostToDevice, s));
+    return SPLX_OK;
+  }
+
+  // Pair count of the last projection (synchronises).
+  int read_total(uint64_t* total, cudaStream_t s) {
+    uint32_t t = 0;
+    CK(cudaMemcpyAsync(&t, tile_start + n_tiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *total = t;
     return SPLX_OK;
   }
 };
@@ -415,45 +437,31 @@ int splx_render_partial(splx_ctx_t ctx, const splx_gaussians* subset, const splx
     return code;
   };
   if ((r = P.alloc_common(s))) return fail(r);
-  if ((r = P.bin(s))) return fail(r);
+  if ((r = P.project_and_count(s))) return fail(r);
   uint64_t total = 0;
-  {
-    cudaError_t e = cudaMemcpyAsync(&total, P.offsets + P.N, sizeof(uint64_t),
-                                    cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return fail(cuda_fail(e, "pair count readback"));
-  }
+  if ((r = P.read_total(&total, s))) return fail(r);
   if (total >= (uint64_t)UINT32_MAX) return fail(SPLX_ERR_CAPACITY);
   if ((r = P.alloc_pairs((int64_t)total, s))) return fail(r);
+  if ((r = P.fill_and_sort(s))) return fail(r);
+  launch_raster_fwd(P.dev(), s);
   {
-    // emit, sort, ranges (project/scan already done)
-    const BatchDev b = P.dev();
-    launch_emit(b, s);
-    const int bits = 32 + b.tile_bits;
-    P.sorted_alt = radix_sort_pairs(P.keys[0], P.vals[0], P.keys[1], P.vals[1],
-                                    P.offsets + P.N, P.capacity, bits, P.sort_temp, s) ? 1 : 0;
-    cudaError_t e = cudaMemsetAsync(P.ranges, 0, sizeof(uint2) * (size_t)std::max<int64_t>(P.n_tiles, 1), s);
-    if (e != cudaSuccess) return fail(cuda_fail(e, "memset ranges"));
-    BatchDev b2 = P.dev();
-    launch_ranges(b2, P.keys[P.sorted_alt], s);
-    launch_raster_fwd(b2, P.vals[P.sorted_alt], s);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(cuda_fail(e, "render_partial launch"));
   }
-  // keep only what the backward needs
-  ctx_free(ctx, P.counts, s); P.counts = nullptr;
-  ctx_free(ctx, P.scan_temp, s); P.scan_temp = nullptr;
-  ctx_free(ctx, P.sort_temp, s); P.sort_temp = nullptr;
-  ctx_free(ctx, P.keys[0], s); P.keys[0] = nullptr;
-  ctx_free(ctx, P.keys[1], s); P.keys[1] = nullptr;
-  ctx_free(ctx, P.vals[1 - P.sorted_alt], s); P.vals[1 - P.sorted_alt] = nullptr;
+  // keep only what the backward needs (records, sorted keys, ranges, descriptors)
+  P.free_ptr((void*&)P.counts, s);
+  P.free_ptr((void*&)P.scan_temp, s);
+  P.free_ptr((void*&)P.keys_alt, s);
+  P.free_ptr((void*&)P.tile_cnt, s);
+  P.free_ptr((void*&)P.big_list, s);
+  P.free_ptr((void*&)P.big_count, s);
   if (!state_out) return fail(SPLX_OK);
   *state_out = st;
   return SPLX_OK;
 }
 
 int splx_state_export(splx_ctx_t ctx, splx_state_t st, int64_t* n_pairs, int64_t* n_tiles,
-                      uint32_t* ranges_out, uint32_t* vals_out, float* rec_out,
+                      uint32_t* ranges_out, uint64_t* keys_out, float* rec_out,
                       splx_stream_t stream) {
   if (!ctx || !st) return SPLX_ERR_INVALID;
   CtxScope scope(ctx);
@@ -463,9 +471,8 @@ int splx_state_export(splx_ctx_t ctx, splx_state_t st, int64_t* n_pairs, int64_t
   if (n_tiles) *n_tiles = P.n_tiles;
   if (ranges_out && P.n_tiles > 0)
     CK(cudaMemcpyAsync(ranges_out, P.ranges, sizeof(uint2) * P.n_tiles, cudaMemcpyDeviceToDevice, s));
-  if (vals_out && P.capacity > 0)
-    CK(cudaMemcpyAsync(vals_out, P.vals[P.sorted_alt], sizeof(uint32_t) * P.capacity,
-                       cudaMemcpyDeviceToDevice, s));
+  if (keys_out && P.capacity > 0)
+    CK(cudaMemcpyAsync(keys_out, P.keys, sizeof(uint64_t) * P.capacity, cudaMemcpyDeviceToDevice, s));
   if (rec_out && P.N > 0)
     CK(cudaMemcpyAsync(rec_out, P.rec, sizeof(Rec) * P.N, cudaMemcpyDeviceToDevice, s));
   CK(cudaStreamSynchronize(s));
@@ -585,7 +592,7 @@ int splx_backward(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
       if (e != cudaSuccess) return cleanup(cuda_fail(e, "memset grad2d"));
     }
     BatchDev b = P.dev();
-    launch_raster_bwd(b, P.vals[P.sorted_alt], s);
+    launch_raster_bwd(b, s);
     GradTable gt;
     std::memset(&gt, 0, sizeof(gt));
     gt.p[0][0] = grads[k].means; gt.p[0][1] = grads[k].log_scales; gt.p[0][2] = grads[k].quats;
@@ -721,11 +728,9 @@ int splx_batch_create(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
   int64_t cap = pair_capacity;
   if (cap == 0) {
     P.capacity = 0;
-    if ((r = P.bin(s))) return fail(r);
+    if ((r = P.project_and_count(s))) return fail(r);
     uint64_t total = 0;
-    e = cudaMemcpyAsync(&total, P.offsets + (int64_t)V * N, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return fail(cuda_fail(e, "pair count readback"));
+    if ((r = P.read_total(&total, s))) return fail(r);
     cap = (int64_t)(total + total / 4 + 1024);
   }
   if (cap >= (int64_t)UINT32_MAX) return fail(SPLX_ERR_CAPACITY);
@@ -771,10 +776,10 @@ int splx_batch_forward(splx_batch_t bt, float* out_rgb, float* out_T, splx_strea
   BatchDev b = P.dev();
   b.out_rgb = out_rgb;
   b.out_T = out_T;
-  launch_raster_fwd(b, P.vals[P.sorted_alt], s);
-  P.mark(6, s);
+  launch_raster_fwd(b, s);
+  P.mark(5, s);
   launch_composite(b, P.total_pixels, s);
-  P.mark(7, s);
+  P.mark(6, s);
   CK_LAUNCH();
   bt->forward_done = true;
   return SPLX_OK;
@@ -799,13 +804,13 @@ int splx_batch_backward(splx_batch_t bt, const float* dL_drgb, const float* dL_d
   BatchDev b = P.dev();
   b.dL_drgb = dL_drgb;
   b.dL_dT = dL_dT;
-  P.mark(8, s);
+  P.mark(7, s);
   launch_composite_bwd(b, P.total_pixels, s);
+  P.mark(8, s);
+  launch_raster_bwd(b, s);
   P.mark(9, s);
-  launch_raster_bwd(b, P.vals[P.sorted_alt], s);
-  P.mark(10, s);
   launch_project_bwd(b, gt, s);
-  P.mark(11, s);
+  P.mark(10, s);
   CK_LAUNCH();
   return SPLX_OK;
 }
@@ -826,10 +831,10 @@ int splx_batch_kernel_times(splx_batch_t bt, float* ms_out) {
   Plan& P = bt->plan;
   if (!P.timing) return SPLX_ERR_STATE;
   CtxScope scope(P.ctx);
-  CK(cudaEventSynchronize(P.ev[11]));
-  const int pairs[10][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {5, 6}, {6, 7},
-                            {8, 9}, {9, 10}, {10, 11}};
-  for (int i = 0; i < 10; ++i) {
+  CK(cudaEventSynchronize(P.ev[10]));
+  const int pairs[9][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {5, 6},
+                           {7, 8}, {8, 9}, {9, 10}};
+  for (int i = 0; i < 9; ++i) {
     float ms = 0.0f;
     CK(cudaEventElapsedTime(&ms, P.ev[pairs[i][0]], P.ev[pairs[i][1]]));
     ms_out[i] = ms;
@@ -843,9 +848,9 @@ int splx_batch_counters(splx_batch_t bt, int64_t* out, splx_stream_t stream) {
   CtxScope scope(P.ctx);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   unsigned long long c[4] = {0, 0, 0, 0};
-  uint64_t total = 0;
+  uint32_t total = 0;
   CK(cudaMemcpyAsync(c, P.counters, sizeof(c), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&total, P.offsets + (int64_t)P.V * P.N, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&total, P.tile_start + P.n_tiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   out[0] = (int64_t)total;
   out[1] = (int64_t)c[0];
@@ -859,9 +864,9 @@ int splx_batch_status(splx_batch_t bt, int64_t* pairs_out, splx_stream_t stream)
   Plan& P = bt->plan;
   CtxScope scope(P.ctx);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  uint64_t total = 0;
+  uint32_t total = 0;
   int st = 0;
-  CK(cudaMemcpyAsync(&total, P.offsets + (int64_t)P.V * P.N, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&total, P.tile_start + P.n_tiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&st, P.ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (pairs_out) *pairs_out = (int64_t)total;

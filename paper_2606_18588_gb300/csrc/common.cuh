@@ -73,9 +73,12 @@ struct BatchDev {
   const ImgDev* imgs;           // [V*K], image (v,k) at v*K+k
   Rec* rec;                     // [V][N]
   uint32_t* counts;             // [V*N] tiles touched
-  uint64_t* offsets;            // [V*N+1] exclusive scan of counts
-  uint64_t* keys;               // [capacity]
-  uint32_t* vals;               // [capacity]
+  uint32_t* tile_cnt;           // [n_tiles] pairs per image tile (zero between runs)
+  uint32_t* tile_start;         // [n_tiles+1] exclusive scan of tile_cnt (last = total)
+  uint64_t* keys;               // [capacity] depth bits << 32 | Gaussian index, by tile
+  uint64_t* keys_alt;           // [capacity] scratch for the long-segment sort
+  uint32_t* big_list;           // [n_tiles] tiles whose segment exceeds the small sort
+  unsigned* big_count;          // [1]
   uint2* ranges;                // [n_tiles] sorted [start, end)
   int64_t goff[kMaxK + 1];      // subset k = global indices [goff[k], goff[k+1])
   int64_t tile_base[kMaxViews + 1];  // view v's image tiles start at tile_base[v]
@@ -101,25 +104,18 @@ __host__ __device__ inline int n_sh(int deg) { return (deg + 1) * (deg + 1); }
 
 // ---- launch wrappers (defined in the .cu files) ------------------------------------
 void launch_project(const BatchDev& b, cudaStream_t s);
-void launch_emit(const BatchDev& b, cudaStream_t s);
-void launch_ranges(const BatchDev& b, const uint64_t* keys, cudaStream_t s);
-void launch_raster_fwd(const BatchDev& b, const uint32_t* vals, cudaStream_t s);
+void launch_fill(const BatchDev& b, cudaStream_t s);
+void launch_seg_sort(const BatchDev& b, cudaStream_t s);
+size_t seg_sort_big_smem();
+void launch_raster_fwd(const BatchDev& b, cudaStream_t s);
 void launch_composite(const BatchDev& b, int64_t total_pixels, cudaStream_t s);
 void launch_composite_bwd(const BatchDev& b, int64_t total_pixels, cudaStream_t s);
-void launch_raster_bwd(const BatchDev& b, const uint32_t* vals, cudaStream_t s);
+void launch_raster_bwd(const BatchDev& b, cudaStream_t s);
 void launch_project_bwd(const BatchDev& b, const GradTable& gt, cudaStream_t s);
 
-// exclusive scan of n u32 values into u64 (out has n+1 entries; out[n] = total)
-size_t scan_u32_u64_temp_bytes(int64_t n);
-void scan_u32_u64(const uint32_t* in, uint64_t* out, int64_t n, void* temp, cudaStream_t s);
-
-// LSD radix sort of (u64 key, u32 value) pairs on key bits [0, bits).  The number of
-// items is read from *n_dev (<= capacity); buffers are ping-ponged and the result ends
-// in (keys, vals) or (keys_alt, vals_alt): returns true if in the alt buffers.
-size_t radix_sort_temp_bytes(int64_t capacity);
-bool radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
-                      const uint64_t* n_dev, int64_t capacity, int bits, void* temp,
-                      cudaStream_t s);
+// exclusive scan of n u32 values (out has n+1 entries; out[n] = total)
+size_t scan_u32_temp_bytes(int64_t n);
+void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, void* temp, cudaStream_t s);
 
 // Adam over one parameter array.  The step number is `step` or, if step_dev is non-NULL,
 // *step_dev read on the device.

@@ -6,8 +6,8 @@
 // synchronisation of cudaMalloc/cudaFree is not acceptable.  For them this entry point
 // renders one subset for one view using only a fixed scratch array that lives in this
 // file: every GPU that loads libsplx holds those kNoAllocScratchBytes until the process
-// exits.  It runs the same kernels as splx_render_partial (project, scan, emit, radix
-// sort, ranges, raster forward) on sub-ranges of that array.
+// exits.  It runs the same kernels as splx_render_partial (project, scan, fill, segment
+// sort, raster forward) on sub-ranges of that array.
 //
 // Rules a caller must know:
 //   * The first call on a device looks up the array's device address with
@@ -117,13 +117,13 @@ extern "C" int splx_render_partial_noalloc(const splx_gaussians* g, const splx_c
   ImgDev* img_d = cv.take<ImgDev>(1);
   Rec* rec = cv.take<Rec>((size_t)(N > 0 ? N : 1));
   uint32_t* counts = cv.take<uint32_t>((size_t)(N > 0 ? N : 1));
-  uint64_t* offsets = cv.take<uint64_t>((size_t)N + 1);
-  void* scan_temp = cv.take<unsigned char>(scan_u32_u64_temp_bytes(N));
-  uint64_t* keys0 = cv.take<uint64_t>(kNoAllocMaxPairs);
-  uint64_t* keys1 = cv.take<uint64_t>(kNoAllocMaxPairs);
-  uint32_t* vals0 = cv.take<uint32_t>(kNoAllocMaxPairs);
-  uint32_t* vals1 = cv.take<uint32_t>(kNoAllocMaxPairs);
-  void* sort_temp = cv.take<unsigned char>(radix_sort_temp_bytes(kNoAllocMaxPairs));
+  uint32_t* tile_cnt = cv.take<uint32_t>((size_t)n_tiles);
+  uint32_t* tile_start = cv.take<uint32_t>((size_t)n_tiles + 1);
+  uint32_t* big_list = cv.take<uint32_t>((size_t)n_tiles);
+  unsigned* big_count = cv.take<unsigned>(1);
+  void* scan_temp = cv.take<unsigned char>(scan_u32_temp_bytes(n_tiles));
+  uint64_t* keys = cv.take<uint64_t>(kNoAllocMaxPairs);
+  uint64_t* keys_alt = cv.take<uint64_t>(kNoAllocMaxPairs);
   uint2* ranges = cv.take<uint2>((size_t)n_tiles);
   if (!cv.ok) return SPLX_ERR_INVALID;
 
@@ -156,7 +156,8 @@ extern "C" int splx_render_partial_noalloc(const splx_gaussians* g, const splx_c
   b.alpha_max = o->alpha_max;
   for (int k = 0; k < 3; ++k) b.bg[k] = o->bg[k];
   b.subsets = sub_d; b.views = view_d; b.imgs = img_d;
-  b.rec = rec; b.counts = counts; b.offsets = offsets; b.keys = keys0; b.vals = vals0;
+  b.rec = rec; b.counts = counts; b.tile_cnt = tile_cnt; b.tile_start = tile_start;
+  b.keys = keys; b.keys_alt = keys_alt; b.big_list = big_list; b.big_count = big_count;
   b.ranges = ranges; b.grad2d = nullptr; b.status = status; b.counters = nullptr;
   b.goff[0] = 0; b.goff[1] = N;
   b.tile_base[0] = 0; b.tile_base[1] = n_tiles;
@@ -166,25 +167,22 @@ extern "C" int splx_render_partial_noalloc(const splx_gaussians* g, const splx_c
   if (e == cudaSuccess) e = cudaMemcpyAsync(sub_d, &sd, sizeof(sd), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(view_d, &vd, sizeof(vd), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(img_d, &im, sizeof(im), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * (size_t)n_tiles, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(big_count, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return SPLX_ERR_CUDA;
 
   launch_project(b, s);
-  scan_u32_u64(counts, offsets, N, scan_temp, s);
-  launch_emit(b, s);
-  const bool alt = radix_sort_pairs(keys0, vals0, keys1, vals1, offsets + N, kNoAllocMaxPairs,
-                                    32 + b.tile_bits, sort_temp, s);
-  BatchDev b2 = b;
-  b2.keys = alt ? keys1 : keys0;
-  b2.vals = alt ? vals1 : vals0;
-  launch_ranges(b2, b2.keys, s);
-  launch_raster_fwd(b2, b2.vals, s);
+  scan_u32(tile_cnt, tile_start, n_tiles, scan_temp, s);
+  launch_fill(b, s);
+  launch_seg_sort(b, s);
+  launch_raster_fwd(b, s);
   if (cudaGetLastError() != cudaSuccess) return SPLX_ERR_CUDA;
 
   int st = 0;
-  uint64_t total = 0;
+  uint32_t total = 0;
   e = cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&total, offsets + N, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&total, tile_start + n_tiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return SPLX_ERR_CUDA;
   if ((st & ST_CAPACITY) || total > (uint64_t)kNoAllocMaxPairs) return SPLX_ERR_CAPACITY;

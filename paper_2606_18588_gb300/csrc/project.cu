@@ -1,12 +1,10 @@
-// Projection (Sec. 2 step 1), pair emission and tile ranges (Sec. 2 step 2).
+// Projection (Sec. 2 step 1).
 //
-// project: one thread per Gaussian loops over every view of the batch, so the 59
-// parameters of a degree-3 Gaussian are read from HBM once per batch, not once per
-// view.  Per (view, Gaussian) it writes one 64-byte record (2-D mean, scaled conic,
-// opacity, depth, SH colour, packed pixel rectangle) and the number of tiles touched.
-// emit: one thread per (view, Gaussian) writes a (key, value) pair per touched tile;
-// key = image-tile id << 32 | FP32 depth bits, value = global Gaussian index.
-// ranges: start/end of each image tile in the sorted pair list.
+// One thread per Gaussian loops over every view of the batch, so the 59 parameters of
+// a degree-3 Gaussian are read from HBM once per batch, not once per view.  Per (view,
+// Gaussian) it writes one 64-byte record (2-D mean, scaled conic, opacity, depth, SH
+// colour, packed pixel rectangle) and the number of tiles touched, and adds one to the
+// pair count of each of those tiles (the segment sizes of the binning in bin.cu).
 #include "common.cuh"
 #include "spec.cuh"
 
@@ -107,7 +105,13 @@ __global__ void __launch_bounds__(256) k_project(const BatchDev b) {
       r.b = make_float4(-0.5f * kLog2e * Cc, opac, so.tz, __uint_as_float(rx));
       r.c = make_float4(col[0], col[1], col[2], __uint_as_float(ry));
       const int B_ = b.tile;
-      tiles = (uint32_t)((so.x1 / B_ - so.x0 / B_ + 1) * (so.y1 / B_ - so.y0 / B_ + 1));
+      const int tx0 = so.x0 / B_, tx1 = so.x1 / B_, ty0 = so.y0 / B_, ty1 = so.y1 / B_;
+      tiles = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+      // count this Gaussian in every tile its rectangle touches (segment sizes for binning)
+      const int64_t tbase = b.tile_base[v] + (int64_t)k * cam.tiles_x * cam.tiles_y;
+      for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx)
+          atomicAdd(&b.tile_cnt[tbase + (int64_t)ty * cam.tiles_x + tx], 1u);
     } else {
       r.a = make_float4(0.f, 0.f, 0.f, 0.f);
       r.b = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFu));
@@ -131,71 +135,6 @@ void launch_project(const BatchDev& b, cudaStream_t s) {
     case 2: k_project<2><<<(unsigned)blocks, threads, 0, s>>>(P); break;
     default: k_project<3><<<(unsigned)blocks, threads, 0, s>>>(P); break;
   }
-  count_launch();
-}
-
-// ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_emit(const BatchDev b) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)b.V * b.N) return;
-  const uint32_t tiles = b.counts[idx];
-  if (tiles == 0) return;
-  const uint64_t off = b.offsets[idx];
-  if (off + tiles > (uint64_t)b.capacity) {
-    atomicOr(b.status, ST_CAPACITY);
-    return;
-  }
-  const int v = (int)(idx / b.N);
-  const int64_t g = idx - (int64_t)v * b.N;
-  const int k = subset_of(b, g);
-  const ViewDev& cam = b.views[v];
-  const Rec* r = b.rec + idx;
-  const float4 rb = r->b;
-  const uint32_t rx = __float_as_uint(rb.w), ry = __float_as_uint(r->c.w);
-  const int B_ = b.tile;
-  const int tx0 = (int)(rx & 0xFFFFu) / B_, tx1 = (int)(rx >> 16) / B_;
-  const int ty0 = (int)(ry & 0xFFFFu) / B_, ty1 = (int)(ry >> 16) / B_;
-  const uint64_t depth = (uint64_t)__float_as_uint(rb.z);
-  const int64_t base = b.tile_base[v] + (int64_t)k * cam.tiles_x * cam.tiles_y;
-  uint64_t o = off;
-  for (int ty = ty0; ty <= ty1; ++ty)
-    for (int tx = tx0; tx <= tx1; ++tx) {
-      const uint64_t tid = (uint64_t)(base + (int64_t)ty * cam.tiles_x + tx);
-      b.keys[o] = (tid << 32) | depth;
-      b.vals[o] = (uint32_t)g;
-      ++o;
-    }
-}
-
-void launch_emit(const BatchDev& b, cudaStream_t s) {
-  const int64_t n = (int64_t)b.V * b.N;
-  const int threads = 256;
-  const int64_t blocks = (n + threads - 1) / threads;
-  if (blocks == 0) return;
-  k_emit<<<(unsigned)blocks, threads, 0, s>>>(b);
-  count_launch();
-}
-
-// ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_ranges(const BatchDev b, const uint64_t* __restrict__ keys) {
-  const uint64_t total = b.offsets[(int64_t)b.V * b.N];
-  const uint64_t n = total < (uint64_t)b.capacity ? total : (uint64_t)b.capacity;
-  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t t = (uint32_t)(keys[i] >> 32);
-  if ((int64_t)t >= b.n_tiles) {  // only reachable after a capacity overflow
-    atomicOr(b.status, ST_BOUNDS);
-    return;
-  }
-  if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) b.ranges[t].x = (uint32_t)i;
-  if (i + 1 == n || (uint32_t)(keys[i + 1] >> 32) != t) b.ranges[t].y = (uint32_t)(i + 1);
-}
-
-void launch_ranges(const BatchDev& b, const uint64_t* keys, cudaStream_t s) {
-  const int threads = 256;
-  const int64_t blocks = (b.capacity + threads - 1) / threads;
-  if (blocks == 0) return;
-  k_ranges<<<(unsigned)blocks, threads, 0, s>>>(b, keys);
   count_launch();
 }
 

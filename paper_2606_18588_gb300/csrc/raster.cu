@@ -1,17 +1,18 @@
 // Local rendering of every (view, subset) tile: forward (Eq. 1-4) and backward.
 //
-// One CTA per image tile (TS x TS pixels, one pixel per thread).  The tile's sorted
-// list is walked in batches of TS*TS entries: each thread gathers one 64-byte record
-// into shared memory, then every pixel blends the batch front to back.  A pixel takes a
-// Gaussian only inside its integer 3-sigma rectangle (so the result does not depend on
-// TS), with alpha = min(alpha_max, o 2^(p2)) >= alpha_min, and stops before the
-// Gaussian that would take its transmittance below eps_T.  The CTA leaves the list
+// One CTA per image tile of TS x TS pixels; each thread owns PPT vertically adjacent
+// pixels of one column (TS x TS/PPT threads), so the shared-memory loads, the
+// rectangle test and the dx-dependent terms of an entry are shared by PPT pixels, and in
+// the backward the per-entry warp reduction and atomics are amortised over PPT pixels.
+// The tile's sorted list is walked in batches of NB entries staged in shared memory.
+// A pixel takes a Gaussian only inside its integer 3-sigma rectangle (so the result does
+// not depend on TS), with alpha = min(alpha_max, o 2^(p2)) >= alpha_min, and stops before
+// the Gaussian that would take its transmittance below eps_T.  The CTA leaves the list
 // once every pixel has stopped (__syncthreads_count).
 //
-// The backward walks the same list back to front from each pixel's last blended
-// entry, recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final T^m, and
-// applies the adjoint of Eq. 3-4 with the composite adjoint (dL/dC^m, dL/dT^m of
-// Eq. 6-7) as input:
+// The backward walks the same list back to front from each pixel's last blended entry,
+// recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final T^m, and applies the
+// adjoint of Eq. 3-4 with the composite adjoint (dL/dC^m, dL/dT^m of Eq. 6-7) as input:
 //   dC^m/dc_i = alpha_i T_i,  dC^m/dalpha_i = c_i T_i - B_i / (1 - alpha_i),
 //   dT^m/dalpha_i = -T^m / (1 - alpha_i),  B_i = sum_{j>i} c_j alpha_j T_j.
 // Per-Gaussian sums over the tile's pixels are reduced with warp shuffles and added to
@@ -20,29 +21,34 @@
 
 namespace splx {
 
-// alpha of record (a, b) at pixel centre (pcx, pcy); identical code in forward and
-// backward so both take bit-identical decisions.  Returns false if the Gaussian is
-// skipped at this pixel.
-__device__ __forceinline__ bool eval_alpha(const float4 a, const float4 b, float pcx, float pcy,
-                                           float amin, float amax, float& alpha, float& ex,
-                                           float& dx, float& dy, bool& clamped) {
-  dx = __fsub_rn(pcx, a.x);
-  dy = __fsub_rn(pcy, a.y);
-  const float t1 = __fmul_rn(a.w, __fmul_rn(dx, dy));
-  const float t2 = __fmaf_rn(__fmul_rn(b.x, dy), dy, t1);
-  const float p2 = __fmaf_rn(__fmul_rn(a.z, dx), dx, t2);
+namespace {
+
+// Per-entry terms shared by the pixels of one column: dx, qa dx^2 and qb dx.
+struct ColTerms {
+  float dx, hx, bx;
+};
+
+__device__ __forceinline__ ColTerms col_terms(const float4 a, float pcx) {
+  ColTerms c;
+  c.dx = __fsub_rn(pcx, a.x);
+  c.hx = __fmul_rn(__fmul_rn(a.z, c.dx), c.dx);
+  c.bx = __fmul_rn(a.w, c.dx);
+  return c;
+}
+
+// alpha of an entry at one pixel of the column; the same code runs in the forward and
+// the backward so both take bit-identical decisions.  Returns false if skipped.
+__device__ __forceinline__ bool pixel_alpha(const ColTerms& c, float ay, float qc, float o,
+                                            float pcy, float amin, float amax, float& alpha,
+                                            float& ex, float& dy, bool& clamped) {
+  dy = __fsub_rn(pcy, ay);
+  const float p2 = __fmaf_rn(__fmaf_rn(qc, dy, c.bx), dy, c.hx);
   if (p2 > 0.0f) return false;
   ex = exp2f(p2);
-  const float raw = __fmul_rn(b.y, ex);
+  const float raw = __fmul_rn(o, ex);
   clamped = raw > amax;
   alpha = clamped ? amax : raw;
   return alpha >= amin;
-}
-
-__device__ __forceinline__ bool in_rect(uint32_t rx, uint32_t ry, int px, int py) {
-  const int x0 = (int)(rx & 0xFFFFu), x1 = (int)(rx >> 16);
-  const int y0 = (int)(ry & 0xFFFFu), y1 = (int)(ry >> 16);
-  return px >= x0 && px <= x1 && py >= y0 && py <= y1;
 }
 
 // Adds per-thread counts into counters[slot] with one atomic per warp.
@@ -54,210 +60,262 @@ __device__ __forceinline__ void flush_counter(unsigned long long* counters, int 
 }
 
 struct TileInfo {
-  int v, k, px, py, W, H;
-  int64_t t;
+  int v, k, px, py0, W, H;
 };
 
-__device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id, int TS) {
+template <int TS, int PPT>
+__device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
   TileInfo ti;
   ti.v = view_of(b.tile_base, b.V, id);
   const ViewDev& cam = b.views[ti.v];
   const int64_t nt = (int64_t)cam.tiles_x * cam.tiles_y;
   const int64_t rem = id - b.tile_base[ti.v];
   ti.k = (int)(rem / nt);
-  ti.t = rem - (int64_t)ti.k * nt;
-  const int tx = (int)(ti.t % cam.tiles_x), ty = (int)(ti.t / cam.tiles_x);
+  const int64_t t = rem - (int64_t)ti.k * nt;
+  const int tx = (int)(t % cam.tiles_x), ty = (int)(t / cam.tiles_x);
   ti.px = tx * TS + (int)(threadIdx.x % TS);
-  ti.py = ty * TS + (int)(threadIdx.x / TS);
+  ti.py0 = ty * TS + (int)(threadIdx.x / TS) * PPT;
   ti.W = cam.W;
   ti.H = cam.H;
   return ti;
 }
 
-template <int TS>
-__global__ void __launch_bounds__(TS * TS) k_raster_fwd(const BatchDev b, const uint32_t* __restrict__ vals) {
-  constexpr int NT = TS * TS;
-  constexpr int NB = NT > 512 ? 512 : NT;  // records staged per batch
+}  // namespace
+
+template <int TS, int PPT>
+__global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) {
+  constexpr int NTH = TS * TS / PPT;
+  constexpr int NB = 256;  // entries staged per batch
   __shared__ float4 sA[NB], sB[NB], sC[NB];
   const int64_t id = blockIdx.x;
-  const TileInfo ti = decode_tile(b, id, TS);
-  const bool inside = ti.px < ti.W && ti.py < ti.H;
+  const TileInfo ti = decode_tile<TS, PPT>(b, id);
   const uint2 rg = b.ranges[id];
   const int64_t start = rg.x, end = rg.y > rg.x ? rg.y : rg.x;
   const Rec* rec = b.rec + (int64_t)ti.v * b.N;
-  const float pcx = (float)ti.px + 0.5f, pcy = (float)ti.py + 0.5f;
+  const float pcx = (float)ti.px + 0.5f;
   const float amin = b.alpha_min, amax = b.alpha_max, epsT = b.eps_T;
-  float T = 1.0f, c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, D = 0.0f;
-  int last = -1;
-  bool done = !inside;
+  float T[PPT], c0[PPT], c1[PPT], c2[PPT], D[PPT];
+  int last[PPT];
+  unsigned live = 0;  // bit i: pixel i still blending
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    T[i] = 1.0f; c0[i] = c1[i] = c2[i] = D[i] = 0.0f; last[i] = -1;
+    if (ti.px < ti.W && ti.py0 + i < ti.H) live |= 1u << i;
+  }
   unsigned n_eval = 0, n_blend = 0;
   for (int64_t base = start; base < end; base += NB) {
-    if (__syncthreads_count(done) == NT) break;
-    const int64_t j = base + threadIdx.x;
-    if (threadIdx.x < NB && j < end) {
-      uint32_t g = vals[j];
-      if (g >= (uint32_t)b.N) { atomicOr(b.status, ST_BOUNDS); g = 0; }
-      const Rec* r = rec + g;
-      sA[threadIdx.x] = r->a;
-      sB[threadIdx.x] = r->b;
-      sC[threadIdx.x] = r->c;
+    if (__syncthreads_count(live == 0) == NTH) break;
+#pragma unroll
+    for (int r = 0; r < NB / NTH; ++r) {
+      const int slot = r * NTH + (int)threadIdx.x;
+      const int64_t j = base + slot;
+      if (j < end) {
+        uint32_t g = (uint32_t)b.keys[j];  // low half of the sorted key
+        if (g >= (uint32_t)b.N) { atomicOr(b.status, ST_BOUNDS); g = 0; }
+        const Rec* rp = rec + g;
+        sA[slot] = rp->a;
+        sB[slot] = rp->b;
+        sC[slot] = rp->c;
+      }
     }
     __syncthreads();
-    if (!done) {
+    if (live) {
       const int cnt = (int)((end - base) < NB ? (end - base) : NB);
       int jj = 0;
-      for (; jj < cnt; ++jj) {
-        const float4 B = sB[jj];
-        const float4 C = sC[jj];
-        if (!in_rect(__float_as_uint(B.w), __float_as_uint(C.w), ti.px, ti.py)) continue;
-        const float4 A = sA[jj];
-        float alpha, ex, dx, dy;
-        bool cl;
-        if (!eval_alpha(A, B, pcx, pcy, amin, amax, alpha, ex, dx, dy, cl)) continue;
-        const float Tn = T * (1.0f - alpha);
-        if (Tn < epsT) { done = true; ++jj; break; }
-        const float w = alpha * T;
-        c0 = fmaf(C.x, w, c0);
-        c1 = fmaf(C.y, w, c1);
-        c2 = fmaf(C.z, w, c2);
-        D = fmaf(B.z, w, D);
-        T = Tn;
-        last = (int)(base - start) + jj;
-        ++n_blend;
+      for (; jj < cnt && live; ++jj) {
+        const float4 Bv = sB[jj];
+        const float4 Cv = sC[jj];
+        const uint32_t rx = __float_as_uint(Bv.w), ry = __float_as_uint(Cv.w);
+        const int x0 = (int)(rx & 0xFFFFu), x1 = (int)(rx >> 16);
+        const int y0 = (int)(ry & 0xFFFFu), y1 = (int)(ry >> 16);
+        if (ti.px < x0 || ti.px > x1 || ti.py0 + PPT - 1 < y0 || ti.py0 > y1) continue;
+        const float4 Av = sA[jj];
+        const ColTerms ct = col_terms(Av, pcx);
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+          const int py = ti.py0 + i;
+          if (!((live >> i) & 1u) || py < y0 || py > y1) continue;
+          float alpha, ex, dy;
+          bool cl;
+          if (!pixel_alpha(ct, Av.y, Bv.x, Bv.y, (float)py + 0.5f, amin, amax, alpha, ex, dy, cl))
+            continue;
+          const float Tn = T[i] * (1.0f - alpha);
+          if (Tn < epsT) { live &= ~(1u << i); continue; }
+          const float w = alpha * T[i];
+          c0[i] = fmaf(Cv.x, w, c0[i]);
+          c1[i] = fmaf(Cv.y, w, c1[i]);
+          c2[i] = fmaf(Cv.z, w, c2[i]);
+          D[i] = fmaf(Bv.z, w, D[i]);
+          T[i] = Tn;
+          last[i] = (int)(base - start) + jj;
+          ++n_blend;
+        }
       }
       n_eval += (unsigned)jj;
     }
   }
   flush_counter(b.counters, 0, n_eval);
   flush_counter(b.counters, 1, n_blend);
-  if (inside) {
-    const ImgDev im = b.imgs[ti.v * b.K + ti.k];
-    const int64_t HW = (int64_t)ti.W * ti.H;
-    const int64_t p = (int64_t)ti.py * ti.W + ti.px;
-    im.rgb[p] = c0;
-    im.rgb[HW + p] = c1;
-    im.rgb[2 * HW + p] = c2;
-    im.T[p] = T;
-    im.D[p] = D;
-    im.last[p] = last;
+  const ImgDev im = b.imgs[ti.v * b.K + ti.k];
+  const int64_t HW = (int64_t)ti.W * ti.H;
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    if (ti.px >= ti.W || ti.py0 + i >= ti.H) continue;
+    const int64_t p = (int64_t)(ti.py0 + i) * ti.W + ti.px;
+    im.rgb[p] = c0[i];
+    im.rgb[HW + p] = c1[i];
+    im.rgb[2 * HW + p] = c2[i];
+    im.T[p] = T[i];
+    im.D[p] = D[i];
+    im.last[p] = last[i];
   }
 }
 
-template <int TS>
-__global__ void __launch_bounds__(TS * TS) k_raster_bwd(const BatchDev b, const uint32_t* __restrict__ vals) {
-  constexpr int NB = TS * TS > 512 ? 512 : TS * TS;  // records staged per batch
+template <int TS, int PPT>
+__global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const BatchDev b) {
+  constexpr int NTH = TS * TS / PPT;
+  constexpr int NB = 256;
   __shared__ float4 sA[NB], sB[NB], sC[NB];
   __shared__ uint32_t sG[NB];
   __shared__ int s_maxlast;
   const int64_t id = blockIdx.x;
-  const TileInfo ti = decode_tile(b, id, TS);
-  const bool inside = ti.px < ti.W && ti.py < ti.H;
+  const TileInfo ti = decode_tile<TS, PPT>(b, id);
   const uint2 rg = b.ranges[id];
   const int64_t start = rg.x;
   const ImgDev im = b.imgs[ti.v * b.K + ti.k];
-  const int64_t p = (int64_t)ti.py * ti.W + ti.px;
-  float4 gct = make_float4(0.f, 0.f, 0.f, 0.f);
-  float Tf = 1.0f;
-  int mylast = -1;
-  if (inside) {
-    gct = im.gCT[p];
-    Tf = im.T[p];
-    mylast = im.last[p];
-    if (gct.x == 0.0f && gct.y == 0.0f && gct.z == 0.0f && gct.w == 0.0f) mylast = -1;
+  float4 gct[PPT];
+  float T[PPT], ninvTf[PPT], B0[PPT], B1[PPT], B2[PPT];
+  int mylast[PPT];
+  int tlast = -1;  // largest last over this thread's pixels
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    gct[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    T[i] = 1.0f;
+    mylast[i] = -1;
+    B0[i] = B1[i] = B2[i] = 0.0f;
+    if (ti.px < ti.W && ti.py0 + i < ti.H) {
+      const int64_t p = (int64_t)(ti.py0 + i) * ti.W + ti.px;
+      gct[i] = im.gCT[p];
+      T[i] = im.T[p];
+      mylast[i] = im.last[p];
+      if (gct[i].x == 0.0f && gct[i].y == 0.0f && gct[i].z == 0.0f && gct[i].w == 0.0f)
+        mylast[i] = -1;
+    }
+    ninvTf[i] = -T[i] * gct[i].w;
+    tlast = mylast[i] > tlast ? mylast[i] : tlast;
   }
   if (threadIdx.x == 0) s_maxlast = -1;
   __syncthreads();
-  if (mylast >= 0) atomicMax(&s_maxlast, mylast);
+  if (tlast >= 0) atomicMax(&s_maxlast, tlast);
   __syncthreads();
   const int maxlast = s_maxlast;
   if (maxlast < 0) return;
 
   const Rec* rec = b.rec + (int64_t)ti.v * b.N;
   float4* g2 = b.grad2d + (int64_t)ti.v * b.N * 3;
-  const float pcx = (float)ti.px + 0.5f, pcy = (float)ti.py + 0.5f;
+  const float pcx = (float)ti.px + 0.5f;
   const float amin = b.alpha_min, amax = b.alpha_max;
-  float T = Tf;
-  float B0 = 0.f, B1 = 0.f, B2 = 0.f;
-  const float ninvTf = -Tf * gct.w;
   const int lane = threadIdx.x & 31;
   unsigned n_evalb = 0;
 
   for (int top = maxlast; top >= 0; top -= NB) {
     const int lo = top - NB + 1 > 0 ? top - NB + 1 : 0;
     __syncthreads();
-    {
-      const int j = top - (int)threadIdx.x;  // shared slot t holds entry top - t
-      if ((int)threadIdx.x < NB && j >= lo) {
-        uint32_t g = vals[start + j];
+#pragma unroll
+    for (int r = 0; r < NB / NTH; ++r) {
+      const int slot = r * NTH + (int)threadIdx.x;  // slot s holds entry top - s
+      const int j = top - slot;
+      if (j >= lo) {
+        uint32_t g = (uint32_t)b.keys[start + j];
         if (g >= (uint32_t)b.N) { atomicOr(b.status, ST_BOUNDS); g = 0; }
-        const Rec* r = rec + g;
-        sA[threadIdx.x] = r->a;
-        sB[threadIdx.x] = r->b;
-        sC[threadIdx.x] = r->c;
-        sG[threadIdx.x] = g;
+        const Rec* rp = rec + g;
+        sA[slot] = rp->a;
+        sB[slot] = rp->b;
+        sC[slot] = rp->c;
+        sG[slot] = g;
       }
     }
     __syncthreads();
     const int cnt = top - lo + 1;
-    if (mylast >= lo) n_evalb += (unsigned)((mylast < top ? mylast : top) - lo + 1);
+    if (tlast >= lo) n_evalb += (unsigned)((tlast < top ? tlast : top) - lo + 1);
     for (int jj = 0; jj < cnt; ++jj) {
       const int j = top - jj;
       float gu = 0.f, gv = 0.f, gA = 0.f, gB = 0.f, gC = 0.f, go = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
       bool act = false;
-      if (j <= mylast) {
+      if (j <= tlast) {
         const float4 Bv = sB[jj];
         const float4 Cv = sC[jj];
-        if (in_rect(__float_as_uint(Bv.w), __float_as_uint(Cv.w), ti.px, ti.py)) {
+        const uint32_t rx = __float_as_uint(Bv.w), ry = __float_as_uint(Cv.w);
+        const int x0 = (int)(rx & 0xFFFFu), x1 = (int)(rx >> 16);
+        const int y0 = (int)(ry & 0xFFFFu), y1 = (int)(ry >> 16);
+        if (ti.px >= x0 && ti.px <= x1 && ti.py0 + PPT - 1 >= y0 && ti.py0 <= y1) {
           const float4 Av = sA[jj];
-          float alpha, ex, dx, dy;
-          bool cl;
-          if (eval_alpha(Av, Bv, pcx, pcy, amin, amax, alpha, ex, dx, dy, cl)) {
+          const ColTerms ct = col_terms(Av, pcx);
+          // conic (A, B, C) recovered from the scaled record: A = -2 ln2 qa, B = -ln2 qb, C = -2 ln2 qc
+          const float A_ = -2.0f * kLn2 * Av.z, Bc = -kLn2 * Av.w, C_ = -2.0f * kLn2 * Bv.x;
+#pragma unroll
+          for (int i = 0; i < PPT; ++i) {
+            const int py = ti.py0 + i;
+            if (j > mylast[i] || py < y0 || py > y1) continue;
+            float alpha, ex, dy;
+            bool cl;
+            if (!pixel_alpha(ct, Av.y, Bv.x, Bv.y, (float)py + 0.5f, amin, amax, alpha, ex, dy, cl))
+              continue;
             act = true;
-            const float om = 1.0f - alpha;
-            const float rinv = 1.0f / om;
-            const float Ti = T * rinv;
+            const float rinv = 1.0f / (1.0f - alpha);
+            const float Ti = T[i] * rinv;
             const float aT = alpha * Ti;
-            gr = gct.x * aT;
-            gg = gct.y * aT;
-            gb = gct.z * aT;
-            float ga = gct.x * (Cv.x * Ti - B0 * rinv) + gct.y * (Cv.y * Ti - B1 * rinv) +
-                       gct.z * (Cv.z * Ti - B2 * rinv) + ninvTf * rinv;
+            const float4 q = gct[i];
+            gr = fmaf(q.x, aT, gr);
+            gg = fmaf(q.y, aT, gg);
+            gb = fmaf(q.z, aT, gb);
+            const float ga = q.x * (Cv.x * Ti - B0[i] * rinv) + q.y * (Cv.y * Ti - B1[i] * rinv) +
+                             q.z * (Cv.z * Ti - B2[i] * rinv) + ninvTf[i] * rinv;
             if (!cl) {
-              go = ga * ex;
+              go = fmaf(ga, ex, go);
               const float gp = ga * alpha;  // dL/dpower
-              // conic (A, B, C) recovered from the scaled record: A = -2 ln2 qa, ...
-              const float A_ = -2.0f * kLn2 * Av.z, Bc = -kLn2 * Av.w, C_ = -2.0f * kLn2 * Bv.x;
-              gu = (A_ * dx + Bc * dy) * gp;
-              gv = (C_ * dy + Bc * dx) * gp;
-              gA = -0.5f * dx * dx * gp;
-              gB = -dx * dy * gp;
-              gC = -0.5f * dy * dy * gp;
+              gu = fmaf(A_ * ct.dx + Bc * dy, gp, gu);
+              gv = fmaf(C_ * dy + Bc * ct.dx, gp, gv);
+              gA = fmaf(-0.5f * ct.dx * ct.dx, gp, gA);
+              gB = fmaf(-ct.dx * dy, gp, gB);
+              gC = fmaf(-0.5f * dy * dy, gp, gC);
             }
-            B0 = fmaf(Cv.x, aT, B0);
-            B1 = fmaf(Cv.y, aT, B1);
-            B2 = fmaf(Cv.z, aT, B2);
-            T = Ti;
+            B0[i] = fmaf(Cv.x, aT, B0[i]);
+            B1[i] = fmaf(Cv.y, aT, B1[i]);
+            B2[i] = fmaf(Cv.z, aT, B2[i]);
+            T[i] = Ti;
           }
         }
       }
-      if (__any_sync(0xffffffffu, act)) {
+      const unsigned am = __ballot_sync(0xffffffffu, act);
+      if (am) {
+        if ((am & (am - 1)) == 0) {
+          // a single lane holds the whole warp's contribution: no reduction needed
+          if (act) {
+            float4* dst = g2 + (int64_t)sG[jj] * 3;
+            atomicAdd(dst, make_float4(gu, gv, gA, gB));
+            atomicAdd(dst + 1, make_float4(gC, go, gr, gg));
+            atomicAdd(&dst[2].x, gb);
+          }
+        } else {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          gu += __shfl_xor_sync(0xffffffffu, gu, o);
-          gv += __shfl_xor_sync(0xffffffffu, gv, o);
-          gA += __shfl_xor_sync(0xffffffffu, gA, o);
-          gB += __shfl_xor_sync(0xffffffffu, gB, o);
-          gC += __shfl_xor_sync(0xffffffffu, gC, o);
-          go += __shfl_xor_sync(0xffffffffu, go, o);
-          gr += __shfl_xor_sync(0xffffffffu, gr, o);
-          gg += __shfl_xor_sync(0xffffffffu, gg, o);
-          gb += __shfl_xor_sync(0xffffffffu, gb, o);
-        }
-        if (lane == 0) {
-          float4* dst = g2 + (int64_t)sG[jj] * 3;
-          atomicAdd(dst, make_float4(gu, gv, gA, gB));
-          atomicAdd(dst + 1, make_float4(gC, go, gr, gg));
-          atomicAdd(&dst[2].x, gb);
+          for (int o = 16; o > 0; o >>= 1) {
+            gu += __shfl_xor_sync(0xffffffffu, gu, o);
+            gv += __shfl_xor_sync(0xffffffffu, gv, o);
+            gA += __shfl_xor_sync(0xffffffffu, gA, o);
+            gB += __shfl_xor_sync(0xffffffffu, gB, o);
+            gC += __shfl_xor_sync(0xffffffffu, gC, o);
+            go += __shfl_xor_sync(0xffffffffu, go, o);
+            gr += __shfl_xor_sync(0xffffffffu, gr, o);
+            gg += __shfl_xor_sync(0xffffffffu, gg, o);
+            gb += __shfl_xor_sync(0xffffffffu, gb, o);
+          }
+          if (lane == 0) {
+            float4* dst = g2 + (int64_t)sG[jj] * 3;
+            atomicAdd(dst, make_float4(gu, gv, gA, gB));
+            atomicAdd(dst + 1, make_float4(gC, go, gr, gg));
+            atomicAdd(&dst[2].x, gb);
+          }
         }
       }
     }
@@ -265,31 +323,39 @@ __global__ void __launch_bounds__(TS * TS) k_raster_bwd(const BatchDev b, const 
   flush_counter(b.counters, 2, n_evalb);
 }
 
+// Tile side -> pixels per thread: 8x8 tiles use 2 (32 threads), 16x16 and 32x32 use 4.
 template <int TS>
-static void launch_fwd_t(const BatchDev& b, const uint32_t* vals, cudaStream_t s) {
-  k_raster_fwd<TS><<<(unsigned)b.n_tiles, TS * TS, 0, s>>>(b, vals);
+struct Ppt {
+  static constexpr int value = TS == 8 ? 2 : 4;
+};
+
+template <int TS>
+static void launch_fwd_t(const BatchDev& b, cudaStream_t s) {
+  constexpr int P = Ppt<TS>::value;
+  k_raster_fwd<TS, P><<<(unsigned)b.n_tiles, TS * TS / P, 0, s>>>(b);
 }
 template <int TS>
-static void launch_bwd_t(const BatchDev& b, const uint32_t* vals, cudaStream_t s) {
-  k_raster_bwd<TS><<<(unsigned)b.n_tiles, TS * TS, 0, s>>>(b, vals);
+static void launch_bwd_t(const BatchDev& b, cudaStream_t s) {
+  constexpr int P = Ppt<TS>::value;
+  k_raster_bwd<TS, P><<<(unsigned)b.n_tiles, TS * TS / P, 0, s>>>(b);
 }
 
-void launch_raster_fwd(const BatchDev& b, const uint32_t* vals, cudaStream_t s) {
+void launch_raster_fwd(const BatchDev& b, cudaStream_t s) {
   if (b.n_tiles == 0) return;
   switch (b.tile) {
-    case 8: launch_fwd_t<8>(b, vals, s); break;
-    case 32: launch_fwd_t<32>(b, vals, s); break;
-    default: launch_fwd_t<16>(b, vals, s); break;
+    case 8: launch_fwd_t<8>(b, s); break;
+    case 32: launch_fwd_t<32>(b, s); break;
+    default: launch_fwd_t<16>(b, s); break;
   }
   count_launch();
 }
 
-void launch_raster_bwd(const BatchDev& b, const uint32_t* vals, cudaStream_t s) {
+void launch_raster_bwd(const BatchDev& b, cudaStream_t s) {
   if (b.n_tiles == 0) return;
   switch (b.tile) {
-    case 8: launch_bwd_t<8>(b, vals, s); break;
-    case 32: launch_bwd_t<32>(b, vals, s); break;
-    default: launch_bwd_t<16>(b, vals, s); break;
+    case 8: launch_bwd_t<8>(b, s); break;
+    case 32: launch_bwd_t<32>(b, s); break;
+    default: launch_bwd_t<16>(b, s); break;
   }
   count_launch();
 }

@@ -198,19 +198,19 @@ class State:
         self.ctx, self.h = ctx, h
 
     def export(self, stream=None):
-        """(ranges [n_tiles,2] uint32, sorted indices [n_pairs] uint32, records [n,16] f32)
-        as CPU numpy arrays."""
+        """(ranges [n_tiles,2] uint32, sorted keys [n_pairs] uint64 (depth bits << 32 |
+        index), records [n,16] f32) as CPU numpy arrays."""
         npairs, ntiles = C.c_int64(), C.c_int64()
         _check(_lib.splx_state_export(self.ctx.h, self.h, C.byref(npairs), C.byref(ntiles), None,
                                       None, None, _stream(stream)), "splx_state_export")
         n = _lib_state_n(self)
         ranges = torch.empty(max(ntiles.value, 1) * 2, dtype=torch.int32, device="cuda")
-        vals = torch.empty(max(npairs.value, 1), dtype=torch.int32, device="cuda")
+        keys = torch.empty(max(npairs.value, 1) * 2, dtype=torch.int32, device="cuda")
         rec = torch.empty(max(n, 1) * 16, dtype=torch.float32, device="cuda")
-        _check(_lib.splx_state_export(self.ctx.h, self.h, None, None, _ptr(ranges), _ptr(vals),
+        _check(_lib.splx_state_export(self.ctx.h, self.h, None, None, _ptr(ranges), _ptr(keys),
                                       _ptr(rec), _stream(stream)), "splx_state_export")
         r = ranges.cpu().numpy().view(np.uint32)[:2 * ntiles.value].reshape(-1, 2)
-        v = vals.cpu().numpy().view(np.uint32)[:npairs.value]
+        v = keys.cpu().numpy().view(np.uint64)[:npairs.value]
         return r, v, rec.cpu().numpy()[:16 * n].reshape(-1, 16)
 
     def close(self, stream=None):
@@ -359,14 +359,14 @@ class Batch:
         code = _lib.splx_batch_status(self.h, C.byref(pairs), _stream(stream))
         return code, int(pairs.value)
 
-    KERNELS = ("project", "scan", "emit", "sort", "ranges", "raster_fwd", "composite",
-               "composite_bwd", "raster_bwd", "project_bwd")
+    KERNELS = ("project", "scan", "fill", "sort", "raster_fwd", "composite", "composite_bwd",
+               "raster_bwd", "project_bwd")
 
     def set_timing(self, enable=True):
         _check(_lib.splx_batch_set_timing(self.h, int(bool(enable))), "splx_batch_set_timing")
 
     def kernel_times(self) -> dict:
-        arr = (C.c_float * 10)()
+        arr = (C.c_float * len(self.KERNELS))()
         _check(_lib.splx_batch_kernel_times(self.h, arr), "splx_batch_kernel_times")
         return dict(zip(self.KERNELS, [float(x) for x in arr]))
 

@@ -43,7 +43,8 @@ def test_binning_bit_exact(ctx, name, tile):
     dev = to_device(sc)
     p = S.new_partial(cam.height, cam.width)
     st = S.render_partial(ctx, subset_struct(dev, 0, sc.n, sc.sh_degree), cam, S.opts(tile=tile), p)
-    ranges, vals, rec = st.export()
+    ranges, keys, rec = st.export()
+    vals = (keys & np.uint64(0xFFFFFFFF)).astype(np.uint32)
     vis_g, rect_g, db_g = decode_records(rec)
     vis_o, rect_o, db_o = O.bin(sc, cam)
     assert np.array_equal(vis_g, vis_o)
@@ -52,6 +53,8 @@ def test_binning_bit_exact(ctx, name, tile):
     assert np.array_equal(db_g[m], db_o[m])
     start, lst = O.tile_lists(sc, cam, tile)
     assert vals.size == lst.size
+    # every key carries its Gaussian's exact FP32 depth bits
+    assert np.array_equal((keys >> np.uint64(32)).astype(np.uint32), db_o[vals])
     nt = start.size - 1
     assert ranges.shape[0] == nt
     for t in range(nt):
@@ -60,6 +63,38 @@ def test_binning_bit_exact(ctx, name, tile):
         if b == a:
             assert gb <= ga
             continue
+        assert np.array_equal(vals[ga:gb], lst[a:b].astype(np.uint32)), t
+    st.close()
+
+
+def test_binning_bit_exact_on_long_segments(ctx):
+    """Tile lists of 5k and 40k entries (the two large-segment sorts), with many exactly
+    equal depths so the index tie-break decides the order."""
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import subset_struct, to_device
+    rng = np.random.default_rng(17)
+    n1, n2 = 40_000, 5_000
+    m = np.zeros((n1 + n2, 3), np.float32)
+    m[:n1, :2] = -0.433 + rng.uniform(-0.004, 0.004, (n1, 2))  # inside tile (1, 1)
+    m[n1:, 0] = 0.433 + rng.uniform(-0.004, 0.004, n2)          # tile (2, 1)
+    m[n1:, 1] = -0.433 + rng.uniform(-0.004, 0.004, n2)
+    m[:, 2] = rng.choice(np.float32([-0.5, 0.0, 0.25]), n1 + n2)  # three depths only
+    sc = I.Scene(m, np.full((n1 + n2, 3), -7.0, np.float32),
+                 np.tile(np.float32([1, 0, 0, 0]), (n1 + n2, 1)),
+                 np.zeros(n1 + n2, np.float32), np.zeros((n1 + n2, 1, 3), np.float32), 0)
+    cam = I.pinhole(64, 64, 60.0, (0.0, 0.0, -3.0), (0.0, 0.0, 0.0))
+    dev = to_device(sc)
+    p = S.new_partial(64, 64)
+    st = S.render_partial(ctx, subset_struct(dev, 0, sc.n, 0), cam, S.opts(tile=16), p)
+    ranges, keys, _ = st.export()
+    vals = (keys & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    start, lst = O.tile_lists(sc, cam, 16)
+    seg = np.diff(start)
+    assert seg.max() > 16384 and ((seg > 2048) & (seg <= 16384)).any()
+    for t in range(start.size - 1):
+        a, b = int(start[t]), int(start[t + 1])
+        ga, gb = int(ranges[t, 0]), int(ranges[t, 1])
+        assert gb - ga == b - a
         assert np.array_equal(vals[ga:gb], lst[a:b].astype(np.uint32)), t
     st.close()
 
@@ -82,7 +117,8 @@ def test_partial_render_matches_oracle(ctx, name):
     o = S.opts()
     p = S.new_partial(cam.height, cam.width)
     st = S.render_partial(ctx, subset_struct(dev, 0, sc.n, sc.sh_degree), cam, o, p)
-    ranges, vals, _ = st.export()
+    ranges, keys, _ = st.export()
+    vals = (keys & np.uint64(0xFFFFFFFF)).astype(np.uint32)
     torch.cuda.synchronize()
     ref = O.render(sc, cam, O.opts())
     amb = ref["amb"]
