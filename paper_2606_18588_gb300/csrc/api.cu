@@ -177,6 +177,8 @@ struct Plan {
   uint64_t* keys_alt = nullptr;
   uint32_t* big_list = nullptr;
   unsigned* big_count = nullptr;
+  uint2* chunks = nullptr;
+  unsigned* chunk_count = nullptr;
   uint2* ranges = nullptr;
   float4* grad2d = nullptr;
   unsigned long long* counters = nullptr;  // [4]: see BatchDev::counters
@@ -225,6 +227,7 @@ struct Plan {
     b.subsets = subsets_d; b.views = views_d; b.imgs = imgs_d;
     b.rec = rec; b.counts = counts; b.tile_cnt = tile_cnt; b.tile_start = tile_start;
     b.keys = keys; b.keys_alt = keys_alt; b.big_list = big_list; b.big_count = big_count;
+    b.chunks = chunks; b.chunk_count = chunk_count;
     b.ranges = ranges; b.grad2d = grad2d;
     b.status = ctx->d_status;
     b.counters = counters;
@@ -242,7 +245,8 @@ struct Plan {
   void release(cudaStream_t s) {
     void** ps[] = {(void**)&subsets_d, (void**)&views_d, (void**)&imgs_d, (void**)&rec,
                    (void**)&counts, (void**)&tile_cnt, (void**)&tile_start, (void**)&keys,
-                   (void**)&keys_alt, (void**)&big_list, (void**)&big_count, (void**)&ranges,
+                   (void**)&keys_alt, (void**)&big_list, (void**)&big_count, (void**)&chunks,
+                   (void**)&chunk_count, (void**)&ranges,
                    (void**)&grad2d, (void**)&scan_temp, (void**)&counters};
     for (void** p : ps) free_ptr(*p, s);
     for (auto& e : ev)
@@ -255,6 +259,7 @@ struct Plan {
     if (counters) CK(cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(n_tiles, 1), s));
     CK(cudaMemsetAsync(big_count, 0, sizeof(unsigned), s));
+    CK(cudaMemsetAsync(chunk_count, 0, sizeof(unsigned), s));
     mark(0, s);
     launch_project(b, s);
     CK_LAUNCH();
@@ -271,7 +276,7 @@ struct Plan {
     launch_fill(b, s);
     CK_LAUNCH();
     mark(3, s);
-    launch_seg_sort(b, s);
+    launch_seg_sort(b, merge_rounds_bound(max_subset()), s);
     CK_LAUNCH();
     mark(4, s);
     return SPLX_OK;
@@ -289,6 +294,7 @@ struct Plan {
     int r;
     if ((r = ctx_alloc_t(ctx, &keys, (size_t)std::max<int64_t>(cap, 1), s))) return r;
     if ((r = ctx_alloc_t(ctx, &keys_alt, (size_t)std::max<int64_t>(cap, 1), s))) return r;
+    if ((r = ctx_alloc_t(ctx, &chunks, (size_t)chunk_list_capacity(n_tiles, cap), s))) return r;
     return SPLX_OK;
   }
 
@@ -304,6 +310,7 @@ struct Plan {
     if ((r = ctx_alloc_t(ctx, &tile_start, nt + 1, s))) return r;
     if ((r = ctx_alloc_t(ctx, &big_list, nt, s))) return r;
     if ((r = ctx_alloc_t(ctx, &big_count, 1, s))) return r;
+    if ((r = ctx_alloc_t(ctx, &chunk_count, 1, s))) return r;
     if ((r = ctx_alloc(ctx, &scan_temp, scan_u32_temp_bytes(n_tiles), s))) return r;
     if ((r = ctx_alloc_t(ctx, &ranges, nt, s))) return r;
     if (!subsets_h.empty())
@@ -315,6 +322,12 @@ struct Plan {
       CK(cudaMemcpyAsync(imgs_d, imgs_h.data(), sizeof(ImgDev) * imgs_h.size(),
                          cudaMemcpyHostToDevice, s));
     return SPLX_OK;
+  }
+
+  int64_t max_subset() const {
+    int64_t m = 0;
+    for (const SubsetDev& d : subsets_h) m = std::max<int64_t>(m, d.n);
+    return m;
   }
 
   // Pair count of the last projection (synchronises).
@@ -455,6 +468,8 @@ int splx_render_partial(splx_ctx_t ctx, const splx_gaussians* subset, const splx
   P.free_ptr((void*&)P.tile_cnt, s);
   P.free_ptr((void*&)P.big_list, s);
   P.free_ptr((void*&)P.big_count, s);
+  P.free_ptr((void*&)P.chunks, s);
+  P.free_ptr((void*&)P.chunk_count, s);
   if (!state_out) return fail(SPLX_OK);
   *state_out = st;
   return SPLX_OK;

@@ -1,25 +1,27 @@
 // Binning and per-tile depth sort (Sec. 2 step 2 "Sorting"), bucketed by tile.
 //
-// The projection kernel counts the (Gaussian, tile) pairs of every image tile with
-// atomics; an exclusive scan of those counts gives each tile's segment.  fill writes one
-// key per pair into its tile's segment, key = FP32 depth bits << 32 | Gaussian index,
-// taking its slot by counting the tile's counter back down (the counters end at zero).
-// Keys are unique within a tile, so sorting each segment by the full 64-bit key yields the
-// (depth, index) order exactly, whatever order fill placed them in.  Segments are sorted
-// in shared memory (bitonic network) by one CTA each: up to 2048 keys in a 256-thread CTA,
-// up to 16384 in a 1024-thread CTA; longer segments use an in-CTA stable LSD radix sort in
-// global memory.  Every pair is read and written a handful of times instead of once per
-// 8-bit pass over 50+ key bits.
+// The projection kernel counts the (Gaussian, tile) pairs of every image tile; an
+// exclusive scan of those counts gives each tile's segment.  fill writes one key per pair
+// into its tile's segment, key = FP32 depth bits << 32 | Gaussian index, taking slots by
+// counting the tile's counter back down (lanes of a warp that hit the same tile take a
+// block of slots with one atomic; the counters end at zero).  Keys are unique within a
+// tile, so sorting each segment by the full 64-bit key yields the (depth, index) order
+// exactly, whatever order fill placed them in.
+//
+// Sorting: a segment of up to 2048 keys is sorted in shared memory by one CTA (bitonic
+// network).  Longer segments are cut into 2048-key chunks, each sorted the same way, and
+// then merged pairwise in rounds (run width 2048, 4096, ...) with merge-path partitioning,
+// one CTA per 2048 outputs, ping-ponging between the key buffer and its twin; segments
+// that end in the twin are copied back.  Every pair is read and written a few times
+// instead of once per 8-bit pass over 50+ key bits.
 #include "common.cuh"
 
 namespace splx {
 
 namespace {
 
-constexpr int kSmallKeys = 2048;
-constexpr int kSmallThreads = 256;
-constexpr int kBigKeys = 16384;
-constexpr int kBigThreads = 1024;
+constexpr int kChunk = 2048;     // keys sorted in shared memory by one CTA
+constexpr int kSortThreads = 256;
 
 __device__ __forceinline__ int next_pow2(int n) {
   int p = 1;
@@ -47,6 +49,15 @@ __device__ __forceinline__ void bitonic_smem(uint64_t* s, int P) {
   }
 }
 
+// Sorts keys[0, n) (n <= kChunk) in place through shared memory.
+__device__ __forceinline__ void sort_chunk(uint64_t* keys, int n, uint64_t* sk) {
+  const int P = next_pow2(n);
+  for (int i = threadIdx.x; i < P; i += kSortThreads) sk[i] = i < n ? keys[i] : ~0ull;
+  __syncthreads();
+  bitonic_smem<kSortThreads>(sk, P);
+  for (int i = threadIdx.x; i < n; i += kSortThreads) keys[i] = sk[i];
+}
+
 __device__ __forceinline__ void segment_of(const BatchDev& b, int64_t t, uint32_t& s, uint32_t& e) {
   const uint64_t cap = (uint64_t)b.capacity;
   uint64_t s64 = b.tile_start[t], e64 = b.tile_start[t + 1];
@@ -57,33 +68,69 @@ __device__ __forceinline__ void segment_of(const BatchDev& b, int64_t t, uint32_
   e = (uint32_t)e64;
 }
 
+// Merge rounds a segment of n keys needs: ceil(log2(number of chunks)).
+__device__ __forceinline__ int rounds_for(uint32_t n) {
+  const uint32_t nch = (n + kChunk - 1) / kChunk;
+  int r = 0;
+  while ((1u << r) < nch) ++r;
+  return r;
+}
+
+// Number of elements taken from A among the first d of merge(A, B) (unique keys).
+__device__ __forceinline__ uint32_t merge_path(const uint64_t* A, uint32_t na, const uint64_t* B,
+                                               uint32_t nb, uint32_t d) {
+  uint32_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (A[mid] < B[d - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- fill
 __global__ void __launch_bounds__(256) k_fill(const BatchDev b) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lanes = __ballot_sync(0xffffffffu, idx < (int64_t)b.V * b.N);
   if (idx >= (int64_t)b.V * b.N) return;
-  if (b.counts[idx] == 0) return;
+  const uint32_t tiles = b.counts[idx];
   const int v = (int)(idx / b.N);
   const int64_t g = idx - (int64_t)v * b.N;
-  const int k = subset_of(b, g);
-  const ViewDev& cam = b.views[v];
-  const Rec* r = b.rec + idx;
-  const float4 rb = r->b;
-  const uint32_t rx = __float_as_uint(rb.w), ry = __float_as_uint(r->c.w);
-  const int B_ = b.tile;
-  const int tx0 = (int)(rx & 0xFFFFu) / B_, tx1 = (int)(rx >> 16) / B_;
-  const int ty0 = (int)(ry & 0xFFFFu) / B_, ty1 = (int)(ry >> 16) / B_;
-  const uint64_t key_hi = (uint64_t)__float_as_uint(rb.z) << 32;
-  const int64_t base = b.tile_base[v] + (int64_t)k * cam.tiles_x * cam.tiles_y;
+  int tw = 1, tiles_x = 0;
+  int64_t tbase = 0;
+  uint64_t key = 0;
+  if (tiles) {
+    const int k = subset_of(b, g);
+    const ViewDev& cam = b.views[v];
+    const Rec* r = b.rec + idx;
+    const float4 rb = r->b;
+    const uint32_t rx = __float_as_uint(rb.w), ry = __float_as_uint(r->c.w);
+    const int B_ = b.tile;
+    const int tx0 = (int)(rx & 0xFFFFu) / B_, tx1 = (int)(rx >> 16) / B_;
+    const int ty0 = (int)(ry & 0xFFFFu) / B_;
+    tw = tx1 - tx0 + 1;
+    tiles_x = cam.tiles_x;
+    tbase = b.tile_base[v] + (int64_t)k * cam.tiles_x * cam.tiles_y + (int64_t)ty0 * cam.tiles_x + tx0;
+    key = ((uint64_t)__float_as_uint(rb.z) << 32) | (uint64_t)(uint32_t)g;
+  }
+  const int maxt = __reduce_max_sync(lanes, (int)tiles);
+  const unsigned lane = threadIdx.x & 31u, lt = (1u << lane) - 1u;
   bool overflow = false;
-  for (int ty = ty0; ty <= ty1; ++ty)
-    for (int tx = tx0; tx <= tx1; ++tx) {
-      const int64_t t = base + (int64_t)ty * cam.tiles_x + tx;
-      const uint64_t pos = (uint64_t)b.tile_start[t] + (atomicSub(&b.tile_cnt[t], 1u) - 1u);
-      if (pos < (uint64_t)b.capacity) b.keys[pos] = key_hi | (uint64_t)(uint32_t)g;
+  for (int j = 0; j < maxt; ++j) {
+    const unsigned t = j < (int)tiles ? (unsigned)(tbase + (j / tw) * tiles_x + j % tw) : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(lanes, t);
+    const int leader = __ffs(peers) - 1;
+    unsigned old = 0;
+    if (t != 0xFFFFFFFFu && (int)lane == leader) old = atomicSub(&b.tile_cnt[t], (unsigned)__popc(peers));
+    old = __shfl_sync(lanes, old, leader);
+    if (t != 0xFFFFFFFFu) {
+      const uint64_t pos = (uint64_t)b.tile_start[t] + (old - 1u - (unsigned)__popc(peers & lt));
+      if (pos < (uint64_t)b.capacity) b.keys[pos] = key;
       else overflow = true;
     }
+  }
   if (overflow) atomicOr(b.status, ST_CAPACITY);
 }
 
@@ -96,138 +143,134 @@ void launch_fill(const BatchDev& b, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- segment sorts
-__global__ void __launch_bounds__(kSmallThreads) k_seg_sort_small(const BatchDev b) {
-  __shared__ uint64_t sk[kSmallKeys];
+// One CTA per tile: ranges, then either the whole segment (<= kChunk keys) or, for a
+// longer one, its registration as chunk work items (segment list index, chunk index).
+__global__ void __launch_bounds__(kSortThreads) k_seg_sort_small(const BatchDev b) {
+  __shared__ uint64_t sk[kChunk];
+  __shared__ unsigned s_base[2];
   const int64_t t = blockIdx.x;
   uint32_t s, e;
   segment_of(b, t, s, e);
   if (threadIdx.x == 0) b.ranges[t] = make_uint2(s, e);
   const int n = (int)(e - s);
   if (n <= 1) return;
-  if (n > kSmallKeys) {
+  if (n > kChunk) {
+    const unsigned nch = (unsigned)((n + kChunk - 1) / kChunk);
     if (threadIdx.x == 0) {
-      const unsigned i = atomicAdd(b.big_count, 1u);
-      b.big_list[i] = (uint32_t)t;
+      s_base[0] = atomicAdd(b.big_count, 1u);
+      s_base[1] = atomicAdd(b.chunk_count, nch);
     }
+    __syncthreads();
+    const unsigned i = s_base[0];
+    if (threadIdx.x == 0) b.big_list[i] = (uint32_t)t;
+    for (unsigned c = threadIdx.x; c < nch; c += kSortThreads) b.chunks[s_base[1] + c] = make_uint2(i, c);
     return;
   }
-  const int P = next_pow2(n);
-  uint64_t* keys = b.keys + s;
-  for (int i = threadIdx.x; i < P; i += kSmallThreads) sk[i] = i < n ? keys[i] : ~0ull;
-  __syncthreads();
-  bitonic_smem<kSmallThreads>(sk, P);
-  for (int i = threadIdx.x; i < n; i += kSmallThreads) keys[i] = sk[i];
+  sort_chunk(b.keys + s, n, sk);
 }
 
-namespace {
-
-// In-CTA stable LSD radix sort of a[0, n) by the full 64-bit key (8 passes of 8 bits),
-// ping-ponging with tmp; the result ends in a.  smem: 32 x 256 warp counters + 2 x 256.
-__device__ void cta_lsd_sort(uint64_t* a, uint64_t* tmp, int n, uint32_t* sm) {
-  constexpr int NW = kBigThreads / 32;
-  uint32_t* wcnt = sm;                    // [NW][256]
-  uint32_t* base = sm + NW * 256;         // [256] running output offset of each digit
-  uint32_t* ctot = base + 256;            // [256] digit totals of the current chunk
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint32_t lt = (1u << lane) - 1u;
-  for (int pass = 0; pass < 8; ++pass) {
-    const int shift = 8 * pass;
-    const uint64_t* src = (pass & 1) ? tmp : a;
-    uint64_t* dst = (pass & 1) ? a : tmp;
-    for (int d = threadIdx.x; d < 256; d += kBigThreads) base[d] = 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += kBigThreads) atomicAdd(&base[(src[i] >> shift) & 0xFFu], 1u);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t run = 0;
-      for (int d = 0; d < 256; ++d) {
-        const uint32_t c = base[d];
-        base[d] = run;
-        run += c;
-      }
-    }
-    __syncthreads();
-    // chunks of 4 x 1024 keys in order; warp w owns 128 consecutive keys of a chunk
-    for (int c0 = 0; c0 < n; c0 += 4 * kBigThreads) {
-      for (int d = threadIdx.x; d < NW * 256; d += kBigThreads) wcnt[d] = 0;
-      __syncthreads();
-      uint64_t kv[4];
-      uint32_t rk[4], dg[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int i = c0 + w * 128 + r * 32 + lane;
-        const bool valid = i < n;
-        kv[r] = valid ? src[i] : 0ull;
-        const uint32_t d = valid ? (uint32_t)(kv[r] >> shift) & 0xFFu : 0x100u;
-        dg[r] = d;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t before = 0;
-        if (valid) before = wcnt[w * 256 + d];
-        __syncwarp();
-        if (valid && (peers & lt) == 0) wcnt[w * 256 + d] = before + __popc(peers);
-        __syncwarp();
-        rk[r] = before + __popc(peers & lt);
-      }
-      __syncthreads();
-      for (int d = threadIdx.x; d < 256; d += kBigThreads) {
-        uint32_t run = 0;
-        for (int ww = 0; ww < NW; ++ww) {
-          const uint32_t c = wcnt[ww * 256 + d];
-          wcnt[ww * 256 + d] = run;
-          run += c;
-        }
-        ctot[d] = run;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-        if (dg[r] < 0x100u) dst[base[dg[r]] + wcnt[w * 256 + dg[r]] + rk[r]] = kv[r];
-      __syncthreads();
-      for (int d = threadIdx.x; d < 256; d += kBigThreads) base[d] += ctot[d];
-      __syncthreads();
-    }
-  }
-}
-
-}  // namespace
-
-__global__ void __launch_bounds__(kBigThreads) k_seg_sort_big(const BatchDev b) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint64_t* sk = reinterpret_cast<uint64_t*>(smem_raw);
-  const unsigned count = *b.big_count;
-  for (unsigned i = blockIdx.x; i < count; i += gridDim.x) {
-    const int64_t t = b.big_list[i];
-    if (t >= b.n_tiles) continue;
+// Sorts every 2048-key chunk of the long segments (grid-stride over the chunk list).
+__global__ void __launch_bounds__(kSortThreads) k_chunk_sort(const BatchDev b) {
+  __shared__ uint64_t sk[kChunk];
+  const unsigned count = *b.chunk_count;
+  for (unsigned w = blockIdx.x; w < count; w += gridDim.x) {
+    const uint2 ch = b.chunks[w];
+    const int64_t t = b.big_list[ch.x];
     uint32_t s, e;
     segment_of(b, t, s, e);
-    const int n = (int)(e - s);
-    uint64_t* keys = b.keys + s;
-    if (n <= kBigKeys) {
-      const int P = next_pow2(n);
-      for (int j = threadIdx.x; j < P; j += kBigThreads) sk[j] = j < n ? keys[j] : ~0ull;
-      __syncthreads();
-      bitonic_smem<kBigThreads>(sk, P);
-      for (int j = threadIdx.x; j < n; j += kBigThreads) keys[j] = sk[j];
-    } else {
-      cta_lsd_sort(keys, b.keys_alt + s, n, reinterpret_cast<uint32_t*>(smem_raw));
+    const uint32_t c0 = s + ch.y * kChunk;
+    if (c0 >= e) continue;
+    const uint32_t c1 = c0 + kChunk < e ? c0 + kChunk : e;
+    sort_chunk(b.keys + c0, (int)(c1 - c0), sk);
+    __syncthreads();
+  }
+}
+
+// Merge round r (run width 2048 << r): each chunk work item produces 2048 outputs of the
+// merge of the two runs its output range falls in.  Data of round r lives in keys when r
+// is even and in keys_alt when r is odd.
+__global__ void __launch_bounds__(kSortThreads) k_merge_round(const BatchDev b, int r) {
+  __shared__ uint64_t sm[kChunk];
+  __shared__ uint32_t s_split[4];
+  constexpr int PER = kChunk / kSortThreads;  // outputs per thread
+  const unsigned count = *b.chunk_count;
+  const uint32_t w = (uint32_t)kChunk << r;
+  for (unsigned wi = blockIdx.x; wi < count; wi += gridDim.x) {
+    const uint2 ch = b.chunks[wi];
+    const int64_t t = b.big_list[ch.x];
+    uint32_t s, e;
+    segment_of(b, t, s, e);
+    const uint32_t n = e - s;
+    if (n <= w) continue;  // this segment needs no merge at this width
+    const uint64_t* src = ((r & 1) ? b.keys_alt : b.keys) + s;
+    uint64_t* dst = ((r & 1) ? b.keys : b.keys_alt) + s;
+    const uint32_t o0 = ch.y * kChunk;
+    if (o0 >= n) continue;
+    const uint32_t o1 = o0 + kChunk < n ? o0 + kChunk : n;
+    const uint32_t p0 = (o0 / (2 * w)) * (2 * w);
+    const uint32_t na = (p0 + w < n ? p0 + w : n) - p0;
+    const uint32_t nb = (p0 + 2 * w < n ? p0 + 2 * w : n) - (p0 + na);
+    const uint64_t* A = src + p0;
+    const uint64_t* B = A + na;
+    if (threadIdx.x == 0) {
+      const uint32_t a0 = merge_path(A, na, B, nb, o0 - p0);
+      const uint32_t a1 = merge_path(A, na, B, nb, o1 - p0);
+      s_split[0] = a0; s_split[1] = a1;
+      s_split[2] = (o0 - p0) - a0; s_split[3] = (o1 - p0) - a1;
+    }
+    __syncthreads();
+    const uint32_t a0 = s_split[0], a1 = s_split[1], b0 = s_split[2], b1 = s_split[3];
+    const uint32_t la = a1 - a0, lb = b1 - b0;
+    for (uint32_t i = threadIdx.x; i < la; i += kSortThreads) sm[i] = A[a0 + i];
+    for (uint32_t i = threadIdx.x; i < lb; i += kSortThreads) sm[la + i] = B[b0 + i];
+    __syncthreads();
+    // each thread merges PER consecutive outputs of sm[0,la) and sm[la,la+lb)
+    const uint32_t d = threadIdx.x * PER;
+    if (d < la + lb) {
+      uint32_t ia = merge_path(sm, la, sm + la, lb, d);
+      uint32_t ib = d - ia;
+      const uint32_t dend = d + PER < la + lb ? d + PER : la + lb;
+      for (uint32_t o = d; o < dend; ++o) {
+        const bool takeA = ib >= lb || (ia < la && sm[ia] < sm[la + ib]);
+        dst[o0 + o - 0] = takeA ? sm[ia++] : sm[la + ib++];
+      }
     }
     __syncthreads();
   }
 }
 
-size_t seg_sort_big_smem() { return (size_t)kBigKeys * sizeof(uint64_t); }
-
-void launch_seg_sort(const BatchDev& b, cudaStream_t s) {
-  if (b.n_tiles == 0) return;
-  k_seg_sort_small<<<(unsigned)b.n_tiles, kSmallThreads, 0, s>>>(b);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_seg_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)seg_sort_big_smem());
-    attr = true;
+// Copies back the segments whose last merge round wrote keys_alt (odd round count).
+__global__ void __launch_bounds__(kSortThreads) k_merge_fixup(const BatchDev b) {
+  const unsigned count = *b.chunk_count;
+  for (unsigned wi = blockIdx.x; wi < count; wi += gridDim.x) {
+    const uint2 ch = b.chunks[wi];
+    const int64_t t = b.big_list[ch.x];
+    uint32_t s, e;
+    segment_of(b, t, s, e);
+    if ((rounds_for(e - s) & 1) == 0) continue;
+    const uint32_t c0 = s + ch.y * kChunk;
+    const uint32_t c1 = c0 + kChunk < e ? c0 + kChunk : e;
+    for (uint32_t i = c0 + threadIdx.x; i < c1; i += kSortThreads) b.keys[i] = b.keys_alt[i];
   }
-  k_seg_sort_big<<<2 * 152, kBigThreads, seg_sort_big_smem(), s>>>(b);
-  count_launch(2);
+}
+
+void launch_seg_sort(const BatchDev& b, int max_rounds, cudaStream_t s) {
+  if (b.n_tiles == 0) return;
+  k_seg_sort_small<<<(unsigned)b.n_tiles, kSortThreads, 0, s>>>(b);
+  const unsigned grid = 152 * 8;
+  k_chunk_sort<<<grid, kSortThreads, 0, s>>>(b);
+  for (int r = 0; r < max_rounds; ++r) k_merge_round<<<grid, kSortThreads, 0, s>>>(b, r);
+  k_merge_fixup<<<grid, kSortThreads, 0, s>>>(b);
+  count_launch(3 + max_rounds);
+}
+
+// Merge rounds that cover any segment of a batch whose largest subset has max_n Gaussians
+// (a tile's segment holds at most one key per Gaussian of its subset).
+int merge_rounds_bound(int64_t max_n) {
+  const int64_t nch = (max_n + kChunk - 1) / kChunk;
+  int r = 0;
+  while ((int64_t(1) << r) < nch) ++r;
+  return r;
 }
 
 }  // namespace splx

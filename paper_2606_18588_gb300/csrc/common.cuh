@@ -77,8 +77,10 @@ struct BatchDev {
   uint32_t* tile_start;         // [n_tiles+1] exclusive scan of tile_cnt (last = total)
   uint64_t* keys;               // [capacity] depth bits << 32 | Gaussian index, by tile
   uint64_t* keys_alt;           // [capacity] scratch for the long-segment sort
-  uint32_t* big_list;           // [n_tiles] tiles whose segment exceeds the small sort
+  uint32_t* big_list;           // [n_tiles] tiles whose segment exceeds one sort chunk
   unsigned* big_count;          // [1]
+  uint2* chunks;                // [n_tiles + capacity/2048 + 1] (big_list index, chunk)
+  unsigned* chunk_count;        // [1]
   uint2* ranges;                // [n_tiles] sorted [start, end)
   int64_t goff[kMaxK + 1];      // subset k = global indices [goff[k], goff[k+1])
   int64_t tile_base[kMaxViews + 1];  // view v's image tiles start at tile_base[v]
@@ -105,8 +107,12 @@ __host__ __device__ inline int n_sh(int deg) { return (deg + 1) * (deg + 1); }
 // ---- launch wrappers (defined in the .cu files) ------------------------------------
 void launch_project(const BatchDev& b, cudaStream_t s);
 void launch_fill(const BatchDev& b, cudaStream_t s);
-void launch_seg_sort(const BatchDev& b, cudaStream_t s);
-size_t seg_sort_big_smem();
+// Sorts every tile segment; max_rounds = merge_rounds_bound(largest subset size).
+void launch_seg_sort(const BatchDev& b, int max_rounds, cudaStream_t s);
+int merge_rounds_bound(int64_t max_n);
+inline int64_t chunk_list_capacity(int64_t n_tiles, int64_t capacity) {
+  return n_tiles + capacity / 2048 + 1;
+}
 void launch_raster_fwd(const BatchDev& b, cudaStream_t s);
 void launch_composite(const BatchDev& b, int64_t total_pixels, cudaStream_t s);
 void launch_composite_bwd(const BatchDev& b, int64_t total_pixels, cudaStream_t s);

@@ -121,6 +121,8 @@ extern "C" int splx_render_partial_noalloc(const splx_gaussians* g, const splx_c
   uint32_t* tile_start = cv.take<uint32_t>((size_t)n_tiles + 1);
   uint32_t* big_list = cv.take<uint32_t>((size_t)n_tiles);
   unsigned* big_count = cv.take<unsigned>(1);
+  uint2* chunks = cv.take<uint2>((size_t)chunk_list_capacity(n_tiles, kNoAllocMaxPairs));
+  unsigned* chunk_count = cv.take<unsigned>(1);
   void* scan_temp = cv.take<unsigned char>(scan_u32_temp_bytes(n_tiles));
   uint64_t* keys = cv.take<uint64_t>(kNoAllocMaxPairs);
   uint64_t* keys_alt = cv.take<uint64_t>(kNoAllocMaxPairs);
@@ -158,6 +160,7 @@ extern "C" int splx_render_partial_noalloc(const splx_gaussians* g, const splx_c
   b.subsets = sub_d; b.views = view_d; b.imgs = img_d;
   b.rec = rec; b.counts = counts; b.tile_cnt = tile_cnt; b.tile_start = tile_start;
   b.keys = keys; b.keys_alt = keys_alt; b.big_list = big_list; b.big_count = big_count;
+  b.chunks = chunks; b.chunk_count = chunk_count;
   b.ranges = ranges; b.grad2d = nullptr; b.status = status; b.counters = nullptr;
   b.goff[0] = 0; b.goff[1] = N;
   b.tile_base[0] = 0; b.tile_base[1] = n_tiles;
@@ -169,12 +172,13 @@ extern "C" int splx_render_partial_noalloc(const splx_gaussians* g, const splx_c
   if (e == cudaSuccess) e = cudaMemcpyAsync(img_d, &im, sizeof(im), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * (size_t)n_tiles, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(big_count, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(chunk_count, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return SPLX_ERR_CUDA;
 
   launch_project(b, s);
   scan_u32(tile_cnt, tile_start, n_tiles, scan_temp, s);
   launch_fill(b, s);
-  launch_seg_sort(b, s);
+  launch_seg_sort(b, merge_rounds_bound(N), s);
   launch_raster_fwd(b, s);
   if (cudaGetLastError() != cudaSuccess) return SPLX_ERR_CUDA;
 

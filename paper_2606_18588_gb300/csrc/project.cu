@@ -58,6 +58,7 @@ __device__ __forceinline__ void sh_eval(float x, float y, float z, float* Y) {
 template <int DEG>
 __global__ void __launch_bounds__(256) k_project(const BatchDev b) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lanes = __ballot_sync(0xffffffffu, g < b.N);  // lanes in the warp collectives
   if (g >= b.N) return;
   const int k = subset_of(b, g);
   const SubsetDev S = b.subsets[k];
@@ -107,11 +108,6 @@ __global__ void __launch_bounds__(256) k_project(const BatchDev b) {
       const int B_ = b.tile;
       const int tx0 = so.x0 / B_, tx1 = so.x1 / B_, ty0 = so.y0 / B_, ty1 = so.y1 / B_;
       tiles = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
-      // count this Gaussian in every tile its rectangle touches (segment sizes for binning)
-      const int64_t tbase = b.tile_base[v] + (int64_t)k * cam.tiles_x * cam.tiles_y;
-      for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx)
-          atomicAdd(&b.tile_cnt[tbase + (int64_t)ty * cam.tiles_x + tx], 1u);
     } else {
       r.a = make_float4(0.f, 0.f, 0.f, 0.f);
       r.b = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFu));
@@ -121,6 +117,21 @@ __global__ void __launch_bounds__(256) k_project(const BatchDev b) {
     Rec* dst = b.rec + (int64_t)v * b.N + g;
     dst->a = r.a; dst->b = r.b; dst->c = r.c; dst->d = r.d;
     b.counts[(int64_t)v * b.N + g] = tiles;
+    // count this Gaussian in every tile its rectangle touches (the segment sizes of the
+    // binning); lanes that hit the same tile add together (neighbouring Gaussians are
+    // neighbours in memory), so most tiles see one atomic per warp
+    const int tw = so.visible ? so.x1 / b.tile - so.x0 / b.tile + 1 : 1;
+    const int64_t tbase = b.tile_base[v] + (int64_t)k * cam.tiles_x * cam.tiles_y +
+                          (int64_t)(so.visible ? so.y0 / b.tile : 0) * cam.tiles_x +
+                          (so.visible ? so.x0 / b.tile : 0);
+    const int maxt = __reduce_max_sync(lanes, (int)tiles);
+    for (int j = 0; j < maxt; ++j) {
+      const unsigned t = j < (int)tiles ? (unsigned)(tbase + (j / tw) * cam.tiles_x + j % tw)
+                                        : 0xFFFFFFFFu;
+      const unsigned peers = __match_any_sync(lanes, t);
+      if (t != 0xFFFFFFFFu && (threadIdx.x & 31) == __ffs(peers) - 1)
+        atomicAdd(&b.tile_cnt[t], (unsigned)__popc(peers));
+    }
   }
 }
 

@@ -147,14 +147,29 @@ def cluster_scene(n: int, seed: int, sh_degree: int = 3, n_clusters: int = 64,
     return Scene(means, log_scales, quats, logits, _sh(rng, n, sh_degree, rgb), sh_degree)
 
 
-def kd_partition(means: np.ndarray, K: int, axes=(0, 2)):
+def morton_codes(points: np.ndarray) -> np.ndarray:
+    """30-bit Morton (Z-order) codes of points quantised to 1024 cells per axis of their
+    bounding box."""
+    lo = points.min(axis=0)
+    ext = np.maximum(points.max(axis=0) - lo, 1e-12)
+    q = np.clip(((points - lo) / ext * 1023.0).astype(np.int64), 0, 1023)
+    code = np.zeros(points.shape[0], np.int64)
+    for bit in range(10):
+        for a in range(3):
+            code |= ((q[:, a] >> bit) & 1) << (3 * bit + a)
+    return code
+
+
+def kd_partition(means: np.ndarray, K: int, axes=(0, 2), spatial_order: bool = True):
     """Recursive median split into K (a power of two) axis-aligned boxes.
 
     At every node the split axis is the one of `axes` with the largest extent of the
     node's means; the node's Gaussians are ordered by (coordinate, index) and the left
-    child takes the first floor(n/2) (Sec. 8.1, partition strategy).  Returns the
-    permutation that makes subsets contiguous, the K+1 subset offsets, and each subset's
-    (lo, hi) split-plane box (infinite on unsplit sides).
+    child takes the first floor(n/2) (Sec. 8.1, partition strategy).  Within each box the
+    Gaussians are then laid out in Morton order of their means (spatial_order), so that
+    neighbours in memory are neighbours on screen.  Returns the permutation that makes
+    subsets contiguous, the K+1 subset offsets, and each subset's (lo, hi) split-plane box
+    (infinite on unsplit sides).
     """
     if K < 1 or (K & (K - 1)) != 0:
         raise ValueError("K must be a power of two")
@@ -179,6 +194,9 @@ def kd_partition(means: np.ndarray, K: int, axes=(0, 2)):
             nxt.append((np.sort(left), lo, lhi))
             nxt.append((np.sort(right), rlo, hi))
         groups = nxt
+    if spatial_order:
+        groups = [(idx[np.argsort(morton_codes(m[idx]), kind="stable")], lo, hi)
+                  for idx, lo, hi in groups]
     perm = np.concatenate([g[0] for g in groups]).astype(np.int64)
     offsets = np.zeros(K + 1, np.int64)
     offsets[1:] = np.cumsum([g[0].size for g in groups])
