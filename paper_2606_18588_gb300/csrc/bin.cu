@@ -29,33 +29,72 @@ __device__ __forceinline__ int next_pow2(int n) {
   return p;
 }
 
-// Ascending bitonic sort of s[0, P) in shared memory (P a power of two), NT threads.
-template <int NT>
-__device__ __forceinline__ void bitonic_smem(uint64_t* s, int P) {
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < (P >> 1); i += NT) {
-        const int lo = 2 * j * (i / j) + (i % j);
-        const int hi = lo + j;
-        const uint64_t a = s[lo], c = s[hi];
-        const bool up = (lo & k) == 0;
-        if ((a > c) == up) {
-          s[lo] = c;
-          s[hi] = a;
-        }
-      }
-      __syncthreads();
-    }
-  }
+constexpr int kItems = kChunk / kSortThreads;  // 8 keys per thread
+
+__device__ __forceinline__ void cas(uint64_t& a, uint64_t& b) {
+  const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+  a = lo;
+  b = hi;
 }
 
-// Sorts keys[0, n) (n <= kChunk) in place through shared memory.
-__device__ __forceinline__ void sort_chunk(uint64_t* keys, int n, uint64_t* sk) {
-  const int P = next_pow2(n);
-  for (int i = threadIdx.x; i < P; i += kSortThreads) sk[i] = i < n ? keys[i] : ~0ull;
+// Number of elements taken from A among the first d of merge(A, B), in shared memory.
+__device__ __forceinline__ int merge_path_smem(const uint64_t* A, int na, const uint64_t* B, int nb,
+                                               int d) {
+  int lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (A[mid] < B[d - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Sorts keys[0, n) (n <= kChunk) in place: each thread sorts kItems keys in registers
+// (odd-even transposition network), then runs of 8, 16, ... are merged pairwise through
+// two shared buffers, every thread producing kItems outputs located by merge path.
+// The array is padded to a power of two P >= 8 with ~0 keys.  sa, sb: kChunk keys each.
+__device__ __forceinline__ void sort_chunk(uint64_t* keys, int n, uint64_t* sa, uint64_t* sb) {
+  int P = next_pow2(n);
+  if (P < kItems) P = kItems;
+  for (int i = threadIdx.x; i < P; i += kSortThreads) sa[i] = i < n ? keys[i] : ~0ull;
   __syncthreads();
-  bitonic_smem<kSortThreads>(sk, P);
-  for (int i = threadIdx.x; i < n; i += kSortThreads) keys[i] = sk[i];
+  const int active = P / kItems;  // threads holding keys
+  const int t = threadIdx.x;
+  if (t < active) {
+    uint64_t v[kItems];
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) v[r] = sa[t * kItems + r];
+#pragma unroll
+    for (int pass = 0; pass < kItems; ++pass)
+#pragma unroll
+      for (int r = pass & 1; r + 1 < kItems; r += 2) cas(v[r], v[r + 1]);
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) sa[t * kItems + r] = v[r];
+  }
+  __syncthreads();
+  uint64_t* src = sa;
+  uint64_t* dst = sb;
+  for (int w = kItems; w < P; w <<= 1) {
+    if (t < active) {
+      const int o = t * kItems;
+      const int p0 = (o / (2 * w)) * (2 * w);
+      const uint64_t* A = src + p0;
+      const uint64_t* B = A + w;
+      const int d = o - p0;
+      int ia = merge_path_smem(A, w, B, w, d);
+      int ib = d - ia;
+#pragma unroll
+      for (int r = 0; r < kItems; ++r) {
+        const bool takeA = ib >= w || (ia < w && A[ia] < B[ib]);
+        dst[o + r] = takeA ? A[ia++] : B[ib++];
+      }
+    }
+    __syncthreads();
+    uint64_t* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  for (int i = threadIdx.x; i < n; i += kSortThreads) keys[i] = src[i];
 }
 
 __device__ __forceinline__ void segment_of(const BatchDev& b, int64_t t, uint32_t& s, uint32_t& e) {
@@ -118,8 +157,10 @@ __global__ void __launch_bounds__(256) k_fill(const BatchDev b) {
   const int maxt = __reduce_max_sync(lanes, (int)tiles);
   const unsigned lane = threadIdx.x & 31u, lt = (1u << lane) - 1u;
   bool overflow = false;
+  int jx = 0, jy = 0;  // column / row of the j-th tile inside the rectangle
   for (int j = 0; j < maxt; ++j) {
-    const unsigned t = j < (int)tiles ? (unsigned)(tbase + (j / tw) * tiles_x + j % tw) : 0xFFFFFFFFu;
+    const unsigned t = j < (int)tiles ? (unsigned)(tbase + jy * tiles_x + jx) : 0xFFFFFFFFu;
+    if (++jx == tw) { jx = 0; ++jy; }
     const unsigned peers = __match_any_sync(lanes, t);
     const int leader = __ffs(peers) - 1;
     unsigned old = 0;
@@ -146,7 +187,7 @@ void launch_fill(const BatchDev& b, cudaStream_t s) {
 // One CTA per tile: ranges, then either the whole segment (<= kChunk keys) or, for a
 // longer one, its registration as chunk work items (segment list index, chunk index).
 __global__ void __launch_bounds__(kSortThreads) k_seg_sort_small(const BatchDev b) {
-  __shared__ uint64_t sk[kChunk];
+  __shared__ uint64_t sk[2][kChunk];
   __shared__ unsigned s_base[2];
   const int64_t t = blockIdx.x;
   uint32_t s, e;
@@ -166,12 +207,12 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_sort_small(const BatchDev 
     for (unsigned c = threadIdx.x; c < nch; c += kSortThreads) b.chunks[s_base[1] + c] = make_uint2(i, c);
     return;
   }
-  sort_chunk(b.keys + s, n, sk);
+  sort_chunk(b.keys + s, n, sk[0], sk[1]);
 }
 
 // Sorts every 2048-key chunk of the long segments (grid-stride over the chunk list).
 __global__ void __launch_bounds__(kSortThreads) k_chunk_sort(const BatchDev b) {
-  __shared__ uint64_t sk[kChunk];
+  __shared__ uint64_t sk[2][kChunk];
   const unsigned count = *b.chunk_count;
   for (unsigned w = blockIdx.x; w < count; w += gridDim.x) {
     const uint2 ch = b.chunks[w];
@@ -181,7 +222,7 @@ __global__ void __launch_bounds__(kSortThreads) k_chunk_sort(const BatchDev b) {
     const uint32_t c0 = s + ch.y * kChunk;
     if (c0 >= e) continue;
     const uint32_t c1 = c0 + kChunk < e ? c0 + kChunk : e;
-    sort_chunk(b.keys + c0, (int)(c1 - c0), sk);
+    sort_chunk(b.keys + c0, (int)(c1 - c0), sk[0], sk[1]);
     __syncthreads();
   }
 }

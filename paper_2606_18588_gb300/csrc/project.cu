@@ -125,9 +125,10 @@ __global__ void __launch_bounds__(256) k_project(const BatchDev b) {
                           (int64_t)(so.visible ? so.y0 / b.tile : 0) * cam.tiles_x +
                           (so.visible ? so.x0 / b.tile : 0);
     const int maxt = __reduce_max_sync(lanes, (int)tiles);
+    int jx = 0, jy = 0;  // column / row of the j-th tile inside the rectangle
     for (int j = 0; j < maxt; ++j) {
-      const unsigned t = j < (int)tiles ? (unsigned)(tbase + (j / tw) * cam.tiles_x + j % tw)
-                                        : 0xFFFFFFFFu;
+      const unsigned t = j < (int)tiles ? (unsigned)(tbase + jy * cam.tiles_x + jx) : 0xFFFFFFFFu;
+      if (++jx == tw) { jx = 0; ++jy; }
       const unsigned peers = __match_any_sync(lanes, t);
       if (t != 0xFFFFFFFFu && (threadIdx.x & 31) == __ffs(peers) - 1)
         atomicAdd(&b.tile_cnt[t], (unsigned)__popc(peers));
