@@ -61,28 +61,7 @@ __device__ __forceinline__ void flush_counter(unsigned long long* counters, int 
 
 struct TileInfo {
   int v, k, px, py0, W, H;
-  int ox, oy;    // tile origin (pixels)
-  int lx, rgi;   // this thread's column and row group inside the tile
 };
-
-// Coverage word of an entry for one tile: the tile-relative column range [lx0, lx1] of
-// its rectangle (bits 0-4 and 5-9) and a mask of the PPT-row groups it overlaps (bits
-// 10+).  Computed once per entry when it is staged, so that a thread rejects an entry
-// with one 4-byte shared load.
-template <int TS, int PPT>
-__device__ __forceinline__ uint32_t coverage(uint32_t rx, uint32_t ry, int ox, int oy) {
-  const int x0 = (int)(rx & 0xFFFFu) - ox, x1 = (int)(rx >> 16) - ox;
-  const int y0 = (int)(ry & 0xFFFFu) - oy, y1 = (int)(ry >> 16) - oy;
-  const int lx0 = x0 > 0 ? x0 : 0, lx1 = x1 < TS - 1 ? x1 : TS - 1;
-  const int r0 = (y0 > 0 ? y0 : 0) / PPT, r1 = (y1 < TS - 1 ? y1 : TS - 1) / PPT;
-  uint32_t mask = 0;
-  if (lx0 <= lx1 && r0 <= r1) mask = ((2u << r1) - 1u) & ~((1u << r0) - 1u);
-  return (uint32_t)lx0 | ((uint32_t)lx1 << 5) | (mask << 10);
-}
-
-__device__ __forceinline__ bool covers(uint32_t cov, int lx, int rgi) {
-  return ((cov >> (10 + rgi)) & 1u) && lx >= (int)(cov & 31u) && lx <= (int)((cov >> 5) & 31u);
-}
 
 template <int TS, int PPT>
 __device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
@@ -94,12 +73,8 @@ __device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
   ti.k = (int)(rem / nt);
   const int64_t t = rem - (int64_t)ti.k * nt;
   const int tx = (int)(t % cam.tiles_x), ty = (int)(t / cam.tiles_x);
-  ti.ox = tx * TS;
-  ti.oy = ty * TS;
-  ti.lx = (int)(threadIdx.x % TS);
-  ti.rgi = (int)(threadIdx.x / TS);
-  ti.px = ti.ox + ti.lx;
-  ti.py0 = ti.oy + ti.rgi * PPT;
+  ti.px = tx * TS + (int)(threadIdx.x % TS);
+  ti.py0 = ty * TS + (int)(threadIdx.x / TS) * PPT;
   ti.W = cam.W;
   ti.H = cam.H;
   return ti;
@@ -112,7 +87,6 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) 
   constexpr int NTH = TS * TS / PPT;
   constexpr int NB = 256;  // entries staged per batch
   __shared__ float4 sA[NB], sB[NB], sC[NB];
-  __shared__ uint32_t sV[NB];
   const int64_t id = blockIdx.x;
   const TileInfo ti = decode_tile<TS, PPT>(b, id);
   const uint2 rg = b.ranges[id];
@@ -139,11 +113,9 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) 
         uint32_t g = (uint32_t)b.keys[j];  // low half of the sorted key
         if (g >= (uint32_t)b.N) { atomicOr(b.status, ST_BOUNDS); g = 0; }
         const Rec* rp = rec + g;
-        const float4 bb = rp->b, cc = rp->c;
         sA[slot] = rp->a;
-        sB[slot] = bb;
-        sC[slot] = cc;
-        sV[slot] = coverage<TS, PPT>(__float_as_uint(bb.w), __float_as_uint(cc.w), ti.ox, ti.oy);
+        sB[slot] = rp->b;
+        sC[slot] = rp->c;
       }
     }
     __syncthreads();
@@ -151,11 +123,12 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) 
       const int cnt = (int)((end - base) < NB ? (end - base) : NB);
       int jj = 0;
       for (; jj < cnt && live; ++jj) {
-        if (!covers(sV[jj], ti.lx, ti.rgi)) continue;
         const float4 Bv = sB[jj];
         const float4 Cv = sC[jj];
-        const uint32_t ry = __float_as_uint(Cv.w);
+        const uint32_t rx = __float_as_uint(Bv.w), ry = __float_as_uint(Cv.w);
+        const int x0 = (int)(rx & 0xFFFFu), x1 = (int)(rx >> 16);
         const int y0 = (int)(ry & 0xFFFFu), y1 = (int)(ry >> 16);
+        if (ti.px < x0 || ti.px > x1 || ti.py0 + PPT - 1 < y0 || ti.py0 > y1) continue;
         const float4 Av = sA[jj];
         const ColTerms ct = col_terms(Av, pcx);
 #pragma unroll
@@ -203,7 +176,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const BatchDev b) 
   constexpr int NTH = TS * TS / PPT;
   constexpr int NB = 256;
   __shared__ float4 sA[NB], sB[NB], sC[NB];
-  __shared__ uint32_t sG[NB], sV[NB];
+  __shared__ uint32_t sG[NB];
   __shared__ int s_maxlast;
   const int64_t id = blockIdx.x;
   const TileInfo ti = decode_tile<TS, PPT>(b, id);
@@ -256,12 +229,10 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const BatchDev b) 
         uint32_t g = (uint32_t)b.keys[start + j];
         if (g >= (uint32_t)b.N) { atomicOr(b.status, ST_BOUNDS); g = 0; }
         const Rec* rp = rec + g;
-        const float4 bb = rp->b, cc = rp->c;
         sA[slot] = rp->a;
-        sB[slot] = bb;
-        sC[slot] = cc;
+        sB[slot] = rp->b;
+        sC[slot] = rp->c;
         sG[slot] = g;
-        sV[slot] = coverage<TS, PPT>(__float_as_uint(bb.w), __float_as_uint(cc.w), ti.ox, ti.oy);
       }
     }
     __syncthreads();
@@ -271,12 +242,13 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const BatchDev b) 
       const int j = top - jj;
       float gu = 0.f, gv = 0.f, gA = 0.f, gB = 0.f, gC = 0.f, go = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
       bool act = false;
-      if (j <= tlast && covers(sV[jj], ti.lx, ti.rgi)) {
+      if (j <= tlast) {
         const float4 Bv = sB[jj];
         const float4 Cv = sC[jj];
-        const uint32_t ry = __float_as_uint(Cv.w);
+        const uint32_t rx = __float_as_uint(Bv.w), ry = __float_as_uint(Cv.w);
+        const int x0 = (int)(rx & 0xFFFFu), x1 = (int)(rx >> 16);
         const int y0 = (int)(ry & 0xFFFFu), y1 = (int)(ry >> 16);
-        {
+        if (ti.px >= x0 && ti.px <= x1 && ti.py0 + PPT - 1 >= y0 && ti.py0 <= y1) {
           const float4 Av = sA[jj];
           const ColTerms ct = col_terms(Av, pcx);
           // conic (A, B, C) recovered from the scaled record: A = -2 ln2 qa, B = -ln2 qb, C = -2 ln2 qc
@@ -317,8 +289,8 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const BatchDev b) 
       }
       const unsigned am = __ballot_sync(0xffffffffu, act);
       if (am) {
-        if (__popc(am) <= 4) {
-          // few contributing lanes: each adds its own share, cheaper than the butterfly
+        if ((am & (am - 1)) == 0) {
+          // a single lane holds the whole warp's contribution: no reduction needed
           if (act) {
             float4* dst = g2 + (int64_t)sG[jj] * 3;
             atomicAdd(dst, make_float4(gu, gv, gA, gB));
