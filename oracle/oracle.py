@@ -69,11 +69,12 @@ def lib():
             _lib.orc_exp_spec.restype = C.c_float
             _lib.orc_exp_spec.argtypes = [C.c_float]
             _lib.orc_exp_spec_n.argtypes = [P, P, C.c_int64]
+            _lib.orc_log_spec_n.argtypes = [P, P, C.c_int64]
             _lib.orc_sh_basis.argtypes = [P, C.c_int64, P]
             _lib.orc_sh_basis_grad.argtypes = [P, C.c_int64, P]
             _lib.orc_bin.argtypes = [P, P, P, P, P]
             _lib.orc_tile_lists.restype = C.c_int64
-            _lib.orc_tile_lists.argtypes = [P, P, C.c_int32, P, P, C.c_int64]
+            _lib.orc_tile_lists.argtypes = [P, P, C.c_int32, C.c_double, P, P, C.c_int64]
             _lib.orc_project.argtypes = [P, P, P]
             _lib.orc_render.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
             _lib.orc_composite.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P, P, P]
@@ -124,6 +125,14 @@ def exp_spec(x: np.ndarray) -> np.ndarray:
     return y
 
 
+def log_spec(x: np.ndarray) -> np.ndarray:
+    """FP32 natural logarithm of the binning specification (arguments >= 1)."""
+    x = np.ascontiguousarray(x, np.float32)
+    y = np.empty_like(x)
+    lib().orc_log_spec_n(_ptr(x), _ptr(y), x.size)
+    return y
+
+
 def sh_basis(dirs: np.ndarray, grad: bool = False) -> np.ndarray:
     d = np.ascontiguousarray(dirs, np.float64).reshape(-1, 3)
     if grad:
@@ -147,15 +156,17 @@ def bin(scene, cam):
     return vis, rect, db
 
 
-def tile_lists(scene, cam, tile=16):
-    """Sorted per-tile Gaussian lists: (tile_start[ntiles+1] int64, list[int32])."""
+def tile_lists(scene, cam, tile=16, alpha_min=1.0 / 255.0):
+    """Sorted per-tile Gaussian lists after tile culling: (tile_start[ntiles+1] int64,
+    list[int32])."""
     k = _Keep(scene)
     c = camera(cam)
     nt = ((cam.width + tile - 1) // tile) * ((cam.height + tile - 1) // tile)
     start = np.empty(nt + 1, np.int64)
-    total = lib().orc_tile_lists(C.byref(k.p), C.byref(c), tile, _ptr(start), None, 0)
+    total = lib().orc_tile_lists(C.byref(k.p), C.byref(c), tile, alpha_min, _ptr(start), None, 0)
     lst = np.empty(max(total, 1), np.int32)
-    got = lib().orc_tile_lists(C.byref(k.p), C.byref(c), tile, _ptr(start), _ptr(lst), lst.size)
+    got = lib().orc_tile_lists(C.byref(k.p), C.byref(c), tile, alpha_min, _ptr(start), _ptr(lst),
+                               lst.size)
     assert got == total
     return start, lst[:total]
 

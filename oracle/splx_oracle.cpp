@@ -104,10 +104,85 @@ struct BinRec {
   int visible;
   int x0, x1, y0, y1;     // inclusive pixel rectangle, clipped to the image
   uint32_t depth_bits;    // bit pattern of the FP32 camera-space depth
+  float u, v;             // 2-D mean
+  float A, B, C;          // conic of the dilated Sigma2D
+  float o;                // opacity sigmoid(logit)
 };
 
-BinRec bin_spec(const float m[3], const float ls[3], const float q[4], const orc_camera& c) {
-  BinRec b{0, 0, -1, 0, -1, 0u};
+// Natural logarithm of x >= 1 from basic operations only: x = m 2^e with m in
+// [sqrt(1/2), sqrt(2)), ln m = 2 atanh(s) with s = (m - 1)/(m + 1) as its odd series
+// through s^9 (truncation below 1e-9 for |s| <= 0.172), ln 2 split as in exp_spec.
+float log_spec(float x) {
+  uint32_t bits;
+  std::memcpy(&bits, &x, 4);
+  int e = (int)(bits >> 23) - 127;
+  bits = (bits & 0x7FFFFFu) | 0x3F800000u;
+  float m;
+  std::memcpy(&m, &bits, 4);
+  if (m > 1.41421354f) { m = m * 0.5f; e += 1; }
+  const float s = (m - 1.0f) / (m + 1.0f);
+  const float s2 = s * s;
+  float p = 0.222222222f;
+  p = p * s2 + 0.285714287f;
+  p = p * s2 + 0.400000006f;
+  p = p * s2 + 0.666666687f;
+  p = p * s2 + 2.0f;
+  const float fe = (float)e;
+  return fe * 0.693359375f + (s * p + fe * -2.12194440e-4f);
+}
+
+// Tile culling, part of the binning specification.  A (Gaussian, tile) pair is listed
+// only if the conic's quadratic form q = A x^2 + 2B xy + C y^2 (offsets from the mean)
+// reaches q_max = 2 ln(o / (0.999 alpha_min)) somewhere on the box spanned by the pixel
+// centres that the Gaussian's rectangle shares with the tile, i.e. only if alpha can
+// reach 0.999 alpha_min there; the 0.1% margin makes every culled pair one that the
+// per-pixel alpha >= alpha_min test rejects at every pixel of the tile.  The minimum of
+// the convex q over the box is 0 if the mean lies inside; otherwise it lies on an edge
+// whose outer side holds the mean, and along such an edge at the clamped stationary
+// point.  TileCull holds the per-Gaussian part; a Gaussian with o < 0.999 alpha_min
+// reaches no tile.
+struct TileCull {
+  bool any;
+  float qmax, rBC, rBA;  // q_max, B/C, B/A
+};
+
+TileCull tile_cull_prep(const BinRec& b, float amin) {
+  TileCull t{false, 0.0f, 0.0f, 0.0f};
+  const float thr = amin * 0.999f;
+  if (!(b.o >= thr)) return t;
+  t.any = true;
+  t.qmax = 2.0f * log_spec(b.o / thr);
+  t.rBC = b.B / b.C;
+  t.rBA = b.B / b.A;
+  return t;
+}
+
+bool tile_hits_spec(const BinRec& b, const TileCull& t, int tx, int ty, int B_) {
+  if (!t.any) return false;
+  const int px0 = std::max(tx * B_, b.x0), px1 = std::min(tx * B_ + B_ - 1, b.x1);
+  const int py0 = std::max(ty * B_, b.y0), py1 = std::min(ty * B_ + B_ - 1, b.y1);
+  const float xa = ((float)px0 + 0.5f) - b.u, xb = ((float)px1 + 0.5f) - b.u;
+  const float ya = ((float)py0 + 0.5f) - b.v, yb = ((float)py1 + 0.5f) - b.v;
+  const bool xout = xa > 0.0f || xb < 0.0f, yout = ya > 0.0f || yb < 0.0f;
+  if (!xout && !yout) return true;  // q = 0 at the mean
+  const float twoB = 2.0f * b.B;
+  float q = INFINITY;
+  if (xout) {
+    const float x = xa > 0.0f ? xa : xb;
+    const float y = std::fmin(std::fmax(-(t.rBC * x), ya), yb);
+    q = ((b.A * x) * x + (twoB * x) * y) + (b.C * y) * y;
+  }
+  if (yout) {
+    const float y = ya > 0.0f ? ya : yb;
+    const float x = std::fmin(std::fmax(-(t.rBA * y), xa), xb);
+    q = std::fmin(q, ((b.A * x) * x + (twoB * x) * y) + (b.C * y) * y);
+  }
+  return q <= t.qmax;
+}
+
+BinRec bin_spec(const float m[3], const float ls[3], const float q[4], float logit,
+                const orc_camera& c) {
+  BinRec b{0, 0, -1, 0, -1, 0u, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   const float* R = c.R;
   const float tx = ((R[0] * m[0] + R[1] * m[1]) + R[2] * m[2]) + c.t[0];
   const float ty = ((R[3] * m[0] + R[4] * m[1]) + R[5] * m[2]) + c.t[1];
@@ -152,6 +227,7 @@ BinRec bin_spec(const float m[3], const float ls[3], const float q[4], const orc
   }
   const float a0 = (P0[0] * P0[0] + P0[1] * P0[1]) + P0[2] * P0[2];
   const float c0 = (P1[0] * P1[0] + P1[1] * P1[1]) + P1[2] * P1[2];
+  const float b0 = (P0[0] * P1[0] + P0[1] * P1[1]) + P0[2] * P1[2];
   const float d01 = P0[0] * P1[1] - P0[1] * P1[0];
   const float d02 = P0[0] * P1[2] - P0[2] * P1[0];
   const float d12 = P0[1] * P1[2] - P0[2] * P1[1];
@@ -175,6 +251,12 @@ BinRec bin_spec(const float m[3], const float ls[3], const float q[4], const orc
   b.visible = 1;
   b.x0 = (int)x0; b.x1 = (int)x1; b.y0 = (int)y0; b.y1 = (int)y1;
   std::memcpy(&b.depth_bits, &tz, 4);
+  b.u = u;
+  b.v = v;
+  b.A = cc / det;
+  b.B = -(b0 / det);
+  b.C = a / det;
+  b.o = 1.0f / (1.0f + exp_spec(-logit));
   return b;
 }
 
@@ -185,7 +267,7 @@ BinRec bin_of(const orc_params& p, int64_t i, const orc_camera& c) {
     ls[k] = (float)p.log_scales[3 * i + k];
   }
   for (int k = 0; k < 4; ++k) q[k] = (float)p.quats[4 * i + k];
-  return bin_spec(m, ls, q, c);
+  return bin_spec(m, ls, q, (float)p.opacity_logits[i], c);
 }
 
 // ---------------------------------------------------------------------------------
@@ -325,7 +407,7 @@ struct Tiles {
   std::vector<int32_t> list;    // Gaussian indices
 };
 
-Tiles build_tiles(const std::vector<BinRec>& bins, int W, int H, int B) {
+Tiles build_tiles(const std::vector<BinRec>& bins, int W, int H, int B, float amin) {
   Tiles T;
   T.tw = (W + B - 1) / B;
   T.th = (H + B - 1) / B;
@@ -334,9 +416,11 @@ Tiles build_tiles(const std::vector<BinRec>& bins, int W, int H, int B) {
   for (size_t i = 0; i < bins.size(); ++i) {
     const BinRec& b = bins[i];
     if (!b.visible) continue;
+    const TileCull tc = tile_cull_prep(b, amin);
     for (int ty = b.y0 / B; ty <= b.y1 / B; ++ty)
       for (int tx = b.x0 / B; tx <= b.x1 / B; ++tx)
-        per[ty * T.tw + tx].push_back({((uint64_t)b.depth_bits << 32) | (uint64_t)i, (int32_t)i});
+        if (tile_hits_spec(b, tc, tx, ty, B))
+          per[ty * T.tw + tx].push_back({((uint64_t)b.depth_bits << 32) | (uint64_t)i, (int32_t)i});
   }
   T.start.assign(nt + 1, 0);
   for (int t = 0; t < nt; ++t) {
@@ -405,7 +489,7 @@ struct Subset {
   Tiles tiles;
 };
 
-Subset prepare(const orc_params& p, const orc_camera& cam, int B) {
+Subset prepare(const orc_params& p, const orc_camera& cam, int B, float amin) {
   Subset s;
   s.bins.resize(p.n);
   s.pr.resize(p.n);
@@ -414,7 +498,7 @@ Subset prepare(const orc_params& p, const orc_camera& cam, int B) {
     s.bins[i] = bin_of(p, i, cam);
     if (s.bins[i].visible) s.pr[i] = project64(p, i, cam);
   }
-  s.tiles = build_tiles(s.bins, cam.width, cam.height, B);
+  s.tiles = build_tiles(s.bins, cam.width, cam.height, B, amin);
   return s;
 }
 
@@ -465,6 +549,10 @@ void orc_exp_spec_n(const float* x, float* y, int64_t n) {
   for (int64_t i = 0; i < n; ++i) y[i] = exp_spec(x[i]);
 }
 
+void orc_log_spec_n(const float* x, float* y, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) y[i] = log_spec(x[i]);
+}
+
 void orc_sh_basis(const double* dirs, int64_t n, double* Y) {
   for (int64_t i = 0; i < n; ++i) sh_basis(dirs + 3 * i, Y + 16 * i, nullptr);
 }
@@ -489,12 +577,12 @@ void orc_bin(const orc_params* p, const orc_camera* cam, int32_t* visible, int32
 
 // Sorted tile lists.  Pass list == NULL to get the pair count; tile_start has
 // ceil(W/B)*ceil(H/B)+1 entries.
-int64_t orc_tile_lists(const orc_params* p, const orc_camera* cam, int32_t tile,
+int64_t orc_tile_lists(const orc_params* p, const orc_camera* cam, int32_t tile, double alpha_min,
                        int64_t* tile_start, int32_t* list, int64_t capacity) {
   std::vector<BinRec> bins(p->n);
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < p->n; ++i) bins[i] = bin_of(*p, i, *cam);
-  Tiles T = build_tiles(bins, cam->width, cam->height, tile);
+  Tiles T = build_tiles(bins, cam->width, cam->height, tile, (float)alpha_min);
   const int64_t total = (int64_t)T.list.size();
   if (tile_start) std::memcpy(tile_start, T.start.data(), T.start.size() * sizeof(int64_t));
   if (list) {
@@ -526,7 +614,7 @@ int orc_render(const orc_params* p, const orc_camera* cam, const orc_opts* o,
                const uint8_t* tile_mask, double* C, double* T, double* D, int32_t* last,
                int32_t* ncontrib, uint8_t* amb, int64_t* stats) {
   const int W = cam->width, H = cam->height, B = o->tile;
-  Subset s = prepare(*p, *cam, B);
+  Subset s = prepare(*p, *cam, B, (float)o->alpha_min);
   const int nt = s.tiles.tw * s.tiles.th;
   int64_t evaluated = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : evaluated)
@@ -611,7 +699,7 @@ int orc_render_view(const orc_params* p, const int64_t* offsets, int32_t K, cons
     // monolithic contributor lists without termination, subset id per contributor
     orc_opts o2 = *o;
     o2.eps_T = 0.0;
-    Subset s = prepare(*p, *cam, o->tile);
+    Subset s = prepare(*p, *cam, o->tile, (float)o->alpha_min);
     const int W = cam->width, H = cam->height, B = o->tile;
     const int nt = s.tiles.tw * s.tiles.th;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -664,7 +752,7 @@ int orc_backward_view(const orc_params* p, const int64_t* offsets, int32_t K,
   std::vector<double> C((size_t)K * 3 * HW, 0.0), T((size_t)K * HW, 1.0), D((size_t)K * HW, 0.0);
   for (int m = 0; m < K; ++m) {
     orc_params q = slice(*p, offsets[m], offsets[m + 1]);
-    subs[m] = prepare(q, *cam, B);
+    subs[m] = prepare(q, *cam, B, (float)o->alpha_min);
     orc_render(&q, cam, o, tile_mask, C.data() + (size_t)m * 3 * HW, T.data() + (size_t)m * HW,
                D.data() + (size_t)m * HW, nullptr, nullptr, nullptr, nullptr);
   }

@@ -45,6 +45,19 @@ def test_exp_spec_within_3_ulp_of_exp():
     assert O.exp_spec(np.array([0.0], np.float32))[0] == 1.0
 
 
+def test_log_spec_within_3_ulp_of_log():
+    # the tile test's threshold 2 ln(o / (0.999 alpha_min)) takes arguments in [1, 256)
+    x = np.concatenate([np.linspace(1.0, 256.0, 200001), np.geomspace(1.0, 1e30, 20001)])
+    x = x.astype(np.float32)
+    y = O.log_spec(x).astype(np.float64)
+    ref = np.log(x.astype(np.float64))
+    ulp = np.spacing(np.maximum(ref, 1e-30).astype(np.float32)).astype(np.float64)
+    big = ref > 1e-3  # near x = 1 the result is tiny: compare absolutely there
+    assert np.max(np.abs(y - ref)[big] / ulp[big]) <= 3.0
+    assert np.max(np.abs(y - ref)[~big]) <= 1e-9
+    assert O.log_spec(np.array([1.0], np.float32))[0] == 0.0
+
+
 # --------------------------------------------------------------------------- SH basis
 def test_sh_basis_matches_scipy_real_harmonics():
     sp = pytest.importorskip("scipy.special")
@@ -215,6 +228,76 @@ def test_render_matches_brute_force(n, seed, tile):
     np.testing.assert_allclose(got["D"], Db, atol=1e-12)
 
 
+def test_tile_culling_drops_only_pairs_below_alpha_min():
+    # every (Gaussian, tile) pair of the rectangle that the lists omit must have
+    # alpha < alpha_min at every pixel centre it shares with the tile (FP64)
+    sc, cam = I.plain_forward_case(6, n=1500)
+    vis, rect, db = O.bin(sc, cam)
+    pr = O.project(sc, cam)
+    B = 16
+    start, lst = O.tile_lists(sc, cam, B)
+    tw = (cam.width + B - 1) // B
+    listed = set()
+    for t in range(start.size - 1):
+        for g in lst[start[t]:start[t + 1]]:
+            listed.add((int(g), t))
+    culled = 0
+    for g in np.nonzero(vis)[0]:
+        x0, x1, y0, y1 = rect[g]
+        u, v, A, Bc, Cc, o = pr[g, :6]
+        for ty in range(y0 // B, y1 // B + 1):
+            for tx in range(x0 // B, x1 // B + 1):
+                if (int(g), ty * tw + tx) in listed:
+                    continue
+                culled += 1
+                px = np.arange(max(tx * B, x0), min(tx * B + B - 1, x1) + 1) + 0.5 - u
+                py = np.arange(max(ty * B, y0), min(ty * B + B - 1, y1) + 1) + 0.5 - v
+                X, Y = np.meshgrid(px, py)
+                alpha = o * np.exp(-0.5 * (A * X * X + Cc * Y * Y) - Bc * X * Y)
+                assert alpha.max() < 1.0 / 255.0, (g, tx, ty, alpha.max())
+    assert culled > 0.05 * len(listed)  # the culling does remove a real share of pairs
+
+
+def test_tile_culling_is_the_box_maximum_of_alpha():
+    # brute force: the largest alpha over the box of shared pixel centres (its boundary
+    # sampled densely, its interior only through the mean) decides each pair; pairs
+    # clearly above 0.999 alpha_min are listed, pairs clearly below are not
+    sc, cam = I.plain_forward_case(7, n=800)
+    vis, rect, db = O.bin(sc, cam)
+    pr = O.project(sc, cam)
+    B = 16
+    start, lst = O.tile_lists(sc, cam, B)
+    tw = (cam.width + B - 1) // B
+    listed = {(int(g), t) for t in range(start.size - 1) for g in lst[start[t]:start[t + 1]]}
+    s = np.linspace(0.0, 1.0, 4001)
+    thr = 0.999 / 255.0
+    checked = 0
+    for g in np.nonzero(vis)[0]:
+        x0, x1, y0, y1 = rect[g]
+        u, v, A, Bc, Cc, o = pr[g, :6]
+        for ty in range(y0 // B, y1 // B + 1):
+            for tx in range(x0 // B, x1 // B + 1):
+                xa, xb = max(tx * B, x0) + 0.5 - u, min(tx * B + B - 1, x1) + 0.5 - u
+                ya, yb = max(ty * B, y0) + 0.5 - v, min(ty * B + B - 1, y1) + 0.5 - v
+                if xa <= 0 <= xb and ya <= 0 <= yb:
+                    qmin = 0.0
+                else:
+                    ex = np.concatenate([xa + (xb - xa) * s, xa + (xb - xa) * s,
+                                         np.full_like(s, xa), np.full_like(s, xb)])
+                    ey = np.concatenate([np.full_like(s, ya), np.full_like(s, yb),
+                                         ya + (yb - ya) * s, ya + (yb - ya) * s])
+                    qmin = np.min(A * ex * ex + 2.0 * Bc * ex * ey + Cc * ey * ey)
+                amax = o * np.exp(-0.5 * qmin)
+                key = (int(g), ty * tw + tx)
+                if amax > thr * (1 + 1e-4):
+                    assert key in listed, (g, tx, ty, amax)
+                    checked += 1
+                elif amax < thr * (1 - 1e-4):
+                    assert key not in listed, (g, tx, ty, amax)
+                    checked += 1
+    assert checked > 500
+
+
 def test_tile_lists_invariants_and_tile_size_independence():
     sc, cam = I.plain_forward_case(5, n=2000)
     vis, rect, db = O.bin(sc, cam)
@@ -224,7 +307,7 @@ def test_tile_lists_invariants_and_tile_size_independence():
         tw = (cam.width + B - 1) // B
         expect = sum((r[1] // B - r[0] // B + 1) * (r[3] // B - r[2] // B + 1)
                      for r, v in zip(rect, vis) if v)
-        assert lst.size == expect
+        assert 0 < lst.size <= expect
         for t in range(start.size - 1):
             seg = lst[start[t]:start[t + 1]]
             tx, ty = t % tw, t // tw
