@@ -26,10 +26,14 @@ sys.path.insert(0, ROOT)
 METRIC = "fwd+bwd Mpixel/s at 10M Gaussians, batched vs plain; serve p50/p99 ms"
 UNIT = "Mpixel/s"
 
-# Algorithmic work per unit (FP32-pipe instructions per examined (pixel, entry) pair for
-# the rasterisers; bytes per item for the memory-bound kernels).
-INSTR_PER_PAIR_FWD = 16
-INSTR_PER_PAIR_BWD = 45
+# Algorithmic FP32 operations of the rasterisers per counted (pixel, list entry) event:
+# an alpha evaluation (dx, dy, the conic's quadratic form, exp2, times opacity, clamp,
+# threshold), a forward blend (1 - alpha, T update, stop test, alpha T, rgb and depth
+# accumulation) and a backward contribution (T_i recovery, colour, opacity and conic /
+# mean gradients of Eq. 3-4, suffix sums).
+OPS_PER_ALPHA = 10
+OPS_PER_BLEND = 8
+OPS_PER_CONTRIB = 36
 FP32_LANES_PER_SM = 128
 SMS = 152
 
@@ -43,18 +47,38 @@ def parse():
     ap.add_argument("--workload", default="batched_10m_k8")
     ap.add_argument("--n", type=int, default=0, help="override Gaussian count (profiling)")
     ap.add_argument("--views", type=int, default=0, help="override view count (profiling)")
-    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--tile", type=int, default=0,
+                    help="tile side 8/16/32 (0: the autotuner picks tile and CTAs per SM)")
+    ap.add_argument("--ctas-per-sm", type=int, default=0,
+                    help="rasteriser CTAs per SM when --tile is given (0: one per work item)")
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-tile-fraction", type=float, default=1.0 / 48.0)
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the serving run (0: skip it)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrivals per second")
+    ap.add_argument("--serve-n", type=int, default=0, help="override the served scene's size")
     return ap.parse_args()
 
 
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x: float) -> float:
+    """Largest x over all ranks (the timing rule of the replica harness); x itself when
+    there is no process group.  NCCL groups reduce on the GPU, gloo groups on the host."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def make_workload(name, n_override=0, seed=3, rank=0, views_override=0):
@@ -143,12 +167,16 @@ def roofline(name, ms, counts, w, pk):
     hbm = pk["hbm_gbs"]
     sec = ms / 1e3
     if name in ("raster_fwd", "raster_bwd"):
-        pairs = counts["evaluated_fwd"] if name == "raster_fwd" else counts["evaluated_bwd"]
-        per = INSTR_PER_PAIR_FWD if name == "raster_fwd" else INSTR_PER_PAIR_BWD
-        a = pairs * per / sec / 1e12
+        if name == "raster_fwd":
+            ev, more, per = counts["alpha_fwd"], counts["blended"], OPS_PER_BLEND
+        else:
+            ev, more, per = counts["alpha_bwd"], counts["contrib_bwd"], OPS_PER_CONTRIB
+        ops = ev * OPS_PER_ALPHA + more * per
+        a = ops / sec / 1e12
         return {"kernel": name, "bound": "alu", "achieved": a, "peak": alu_peak,
-                "unit": "Tinstr/s (FP32 pipe)", "frac": a / alu_peak, "traffic": None,
-                "work": f"{pairs} examined pairs x {per} FP32 instr"}
+                "unit": "T FP32 ops/s", "frac": a / alu_peak, "traffic": None,
+                "work": f"{ev} alpha evaluations x {OPS_PER_ALPHA} + {more} "
+                        f"{'blends' if name == 'raster_fwd' else 'contributions'} x {per} FP32 ops"}
     param_bytes = (3 + 3 + 4 + 1 + 3 * nc) * 4
     if name == "sort":
         byts = counts["pairs"] * 16  # each tile segment read and written once
@@ -227,6 +255,45 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- serving
+def serve_leg(args, ctx, rank, world):
+    """Serving run: the serve_20m_k8 scene resident, a seeded Poisson stream of render
+    requests (resolution uniform over 512^2, 1280x720, 1920x1080, 3840x2160; random
+    poses around the scene) driven in real time through the native server."""
+    import torch
+    import torch.distributed as dist
+    from paper_2606_18588_gb300 import inputs as I
+    from paper_2606_18588_gb300 import serve
+    from paper_2606_18588_gb300 import splx as S
+    from paper_2606_18588_gb300.train import _subset_structs, scene_to_device
+    w = I.WORKLOADS["serve_20m_k8"]
+    n = args.serve_n or w["n"]
+    t0 = time.perf_counter()
+    sc, off, _, _ = I.cluster_case(n, 5 + rank, w["K"], 1, [(64, 64)], w["sh_degree"])
+    gen_s = time.perf_counter() - t0
+    dev = scene_to_device(sc)
+    subs = _subset_structs(dev, off, sc.sh_degree)
+    budget = 120 << 30
+    srv = S.Server(ctx, subs, S.opts(), budget, slots=4, max_views=8)
+    warm = serve.poisson_requests(8, 1e6, 999 + rank, (0, 0, 0), 25.0)
+    serve.run(srv, warm, realtime=False)
+    reqs = serve.poisson_requests(args.serve_requests, args.serve_rate, 7 + rank, (0, 0, 0), 25.0)
+    if world > 1:
+        dist.barrier()
+    res = serve.run(srv, reqs)
+    srv.close()
+    out = res.summary()
+    out.update({"workload": f"serve_20m_k8: {n} Gaussians SH{sc.sh_degree}, K={w['K']} resident, "
+                            f"Poisson {args.serve_rate:g} req/s, resolutions uniform over "
+                            "512x512/1280x720/1920x1080/3840x2160, random poses",
+                "slots": 4, "max_views_per_launch": 8, "hbm_budget_gb": budget / 2**30,
+                "latency": "arrival (scheduled time) to the host seeing the result finished",
+                "scene_gen_s": gen_s})
+    del dev, subs
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- our path
 def main():
     args = parse()
@@ -247,12 +314,22 @@ def main():
                                                  views_override=args.views)
     ctx = S.Context(local)
     dev = scene_to_device(sc)
-    o = S.opts(tile=args.tile)
     stream = torch.cuda.Stream()
+    tune = None
+    if args.tile == 0:
+        from paper_2606_18588_gb300.autotune import autotune
+        tgt = torch.cat([torch.from_numpy(t).reshape(-1) for t in targets]).cuda()
+        tune = autotune(ctx, dev, off, sc.sh_degree, cams, tgt, stream=stream)
+        tile, ctas = tune.tile, tune.ctas_per_sm
+        del tgt
+    else:
+        tile, ctas = args.tile, args.ctas_per_sm
+    o = S.opts(tile=tile)
     with torch.cuda.stream(stream):
         st = BatchedStep(ctx, dev, off, sc.sh_degree, cams, [torch.from_numpy(t) for t in targets],
                          o, stream=stream)
         st.batch.set_timing(True)
+        st.batch.set_launch(ctas)
         st.run()  # eager once: sizes everything, checks status
         stream.synchronize()
         code, pairs = st.status()
@@ -292,10 +369,7 @@ def main():
         code, _ = st.status()
         if code != S.OK:
             raise RuntimeError(f"status after timed region {code}")
-        ms_t = torch.tensor([ms], device="cuda")
-        if world > 1:
-            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        ms = float(ms_t.item())
+        ms = max_over_ranks(ms)
         pixels = st.pixels
         value = pixels * world / (ms / 1e3) / 1e6
         kmean = {k: statistics.mean(t[k] for t in ktimes) for k in ktimes[0]}
@@ -317,13 +391,10 @@ def main():
             t1.record(stream)
             torch.cuda.synchronize()
             barrier()
-            ems = t0.elapsed_time(t1) / args.steps
-            et = torch.tensor([ems], device="cuda")
-            if world > 1:
-                dist.all_reduce(et, op=dist.ReduceOp.MAX)
-            e2e = {"value": pixels * world / (float(et.item()) / 1e3) / 1e6, "unit": UNIT,
+            ems = max_over_ranks(t0.elapsed_time(t1) / args.steps)
+            e2e = {"value": pixels * world / (ems / 1e3) / 1e6, "unit": UNIT,
                    "h2d_bytes_per_step": host_t.numel() * 4, "d2h_bytes_per_step": 4,
-                   "ms_per_step": float(et.item())}
+                   "ms_per_step": ems}
 
         # ---- plain per-view path (same work, launched per view and subset)
         plain = None
@@ -343,8 +414,8 @@ def main():
     # ---- roofline of the dominant kernel
     pk, pk_src = peaks()
     wl = {"V": len(cams), "N": sc.n, "K": len(off) - 1, "nc": (sc.sh_degree + 1) ** 2,
-          "pixels": pixels, "n_tiles": sum(((c.width + args.tile - 1) // args.tile) *
-                                           ((c.height + args.tile - 1) // args.tile)
+          "pixels": pixels, "n_tiles": sum(((c.width + tile - 1) // tile) *
+                                           ((c.height + tile - 1) // tile)
                                            for c in cams) * (len(off) - 1)}
     cand = {k: v for k, v in kmean.items() if k != "loss+adam"}
     dom = max(cand, key=cand.get)
@@ -356,7 +427,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "global_batch": len(cams) * world,
-                       "pixels_per_step": pixels * world, "tile": args.tile,
+                       "pixels_per_step": pixels * world, "tile": tile,
+                       "raster_ctas_per_sm": ctas,
+                       "autotune": tune.as_dict() if tune else None,
                        "path": "batched: one CUDA graph per step (project + tile counts, scan, "
                                "fill tile buckets, per-tile depth sort, raster fwd, composite, L1 "
                                "loss, composite bwd, raster bwd, project bwd, Adam)",
@@ -365,6 +438,14 @@ def main():
                        "plain": plain, "kernel_ms": kmean, "counters": counts},
             "roofline": roof, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches_per_step * args.steps}
+
+    # ---- serving: resident 20M-Gaussian scene, Poisson requests of mixed resolution
+    st.close()
+    st = None
+    del dev
+    torch.cuda.empty_cache()
+    if args.serve_requests > 0:
+        line["serve"] = serve_leg(args, ctx, rank, world)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -377,7 +458,6 @@ def main():
                                     "sample": f"failed: {ex}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    st.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

@@ -51,6 +51,7 @@ typedef struct splx_ctx_s* splx_ctx_t;     /* library-owned context (scratch poo
 typedef struct splx_state_s* splx_state_t; /* forward state of one (view, subset) render */
 typedef struct splx_batch_s* splx_batch_t; /* planned batch of V views x K subsets */
 typedef struct splx_graph_s* splx_graph_t; /* captured CUDA graph of library calls */
+typedef struct splx_server_s* splx_server_t; /* render server over a resident scene */
 
 /* One Gaussian subset Q^m (read-only parameters). */
 typedef struct {
@@ -228,11 +229,61 @@ int splx_batch_destroy(splx_batch_t b);
  * writes 9 durations in ms (host array): project, scan, fill, sort, raster_fwd,
  * composite, composite_bwd, raster_bwd, project_bwd. */
 int splx_batch_set_timing(splx_batch_t b, int enable);
+/* Launch shape of the batch's rasterisers (the autotuner's second axis beside the tile
+ * side; Sec. 4.3's aim of keeping every SM busy).  raster_ctas_per_sm = 0 launches one
+ * CTA per (view, subset, tile) work item; n > 0 launches n CTAs per SM that take work
+ * items in order from a device counter until none is left (persistent).  Results do not
+ * depend on it except for the summation order of gradient atomics.  0..64, else
+ * SPLX_ERR_INVALID.  Applies to launches issued afterwards (a captured graph keeps the
+ * shape it was captured with). */
+int splx_batch_set_launch(splx_batch_t b, int32_t raster_ctas_per_sm);
+/* Largest number of persistent forward / backward rasteriser CTAs resident on one SM at
+ * the batch's tile side (host outputs). */
+int splx_batch_max_ctas_per_sm(splx_batch_t b, int32_t* fwd, int32_t* bwd);
 int splx_batch_kernel_times(splx_batch_t b, float* ms_out);
-/* Work counters of the last run (synchronises): out[0] = (Gaussian, tile) pairs,
- * out[1] = list entries examined by the forward rasteriser over all pixels, out[2] =
- * Gaussians blended, out[3] = list entries examined by the backward rasteriser. */
+/* Work counters (synchronises; host array of 7): out[0] = (Gaussian, tile) pairs of the
+ * last run; then, from the last EAGER run (replays of a captured graph do not count):
+ * forward rasteriser out[1] = (thread, list entry) pairs examined, out[2] = (pixel,
+ * entry) alpha evaluations, out[3] = (pixel, entry) blends; backward rasteriser out[4] =
+ * (thread, entry) pairs, out[5] = alpha evaluations, out[6] = contributions (alpha >=
+ * alpha_min).  A thread owns a column of 2 (8x8 tiles) or 4 (16x16, 32x32) pixels. */
 int splx_batch_counters(splx_batch_t b, int64_t* out, splx_stream_t stream);
+
+/* ---- serving: continuous batching of render requests --------------------------- */
+/* A render server keeps K resident subsets and renders requests (a camera of any
+ * resolution) with the forward of the hot path: local render of every (view, subset)
+ * (Sec. 4.1 "Local Rendering", Eq. 3-4) and composition (Eq. 5).  It has `slots` launch
+ * slots, each with its own CUDA stream, so launches overlap on the device.  A slot that
+ * is idle takes the oldest queued requests, up to `max_views` of them, as one launch
+ * (the spirit of Sec. 4.3's view consolidation); requests are admitted in arrival order
+ * while the launch's device footprint (records, partial planes, pair buffers estimated
+ * from the largest pairs-per-pixel ratio seen so far) fits the server's budget next to
+ * the launches in flight.  A launch projects and counts its pairs, and the server reads
+ * the exact count behind an event before it allocates the pair buffers, so nothing here
+ * blocks the host.  A request's image does not depend on the other requests of its
+ * launch (every (view, subset, tile) work item is independent), so results alone and in
+ * the mix are bit-identical.
+ *
+ * Not thread-safe: one host thread drives a server.  Results are written to the
+ * caller's device buffer out_rgb [3][H][W] (keep it alive until the request finishes).
+ * A request that cannot fit the budget even alone finishes with SPLX_ERR_BUDGET. */
+int splx_server_create(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
+                       const splx_opts* opts, size_t hbm_budget_bytes, int32_t slots,
+                       int32_t max_views, splx_server_t* out);
+/* Queues one request (host camera copied) and runs a scheduling pass; *id_out (host) is
+ * its id, increasing from 0 in submission order. */
+int splx_server_submit(splx_server_t s, const splx_camera* cam, float* out_rgb,
+                       int64_t* id_out);
+/* Scheduling pass (never waits on the device): retires finished launches, renders
+ * launches whose pair count has arrived, admits queued requests into idle slots; then
+ * reports up to `cap` finished requests as (ids[i], status[i]) host arrays, *n_out of
+ * them.  status is SPLX_OK or the error that ended the request. */
+int splx_server_poll(splx_server_t s, int64_t* ids, int32_t* status, int32_t cap,
+                     int32_t* n_out);
+/* Host outputs (each nullable): queued requests, requests in flight, reserved bytes. */
+int splx_server_stats(splx_server_t s, int32_t* queued, int32_t* inflight, size_t* reserved);
+/* Waits for the launches in flight, releases everything; queued requests are dropped. */
+int splx_server_destroy(splx_server_t s);
 
 /* ---- CUDA graphs of library calls --------------------------------------------- */
 /* Begins capturing `stream` (thread-local mode).  Any capturable splx_* calls issued

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <mutex>
 #include <new>
 #include <unordered_map>
@@ -181,7 +182,9 @@ struct Plan {
   unsigned* chunk_count = nullptr;
   uint2* ranges = nullptr;
   float4* grad2d = nullptr;
-  unsigned long long* counters = nullptr;  // [4]: see BatchDev::counters
+  unsigned long long* counters = nullptr;  // [kCounters]: see BatchDev::counters
+  unsigned long long* work_ctr = nullptr;  // [2]: persistent rasterisers' work counters
+  int persist_grid = 0;                    // persistent raster grid (0: one CTA per item)
   void* scan_temp = nullptr;
   int64_t capacity = 0, n_tiles = 0, total_pixels = 0;
   splx_opts opts{};
@@ -195,9 +198,7 @@ struct Plan {
 
   void mark(int i, cudaStream_t s) {
     if (!timing || !ev[i]) return;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(s, &cs);
-    if (cs == cudaStreamCaptureStatusActive)
+    if (stream_capturing(s))
       cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
     else
       cudaEventRecord(ev[i], s);
@@ -231,6 +232,8 @@ struct Plan {
     b.ranges = ranges; b.grad2d = grad2d;
     b.status = ctx->d_status;
     b.counters = counters;
+    b.persist_grid = persist_grid;
+    b.work_ctr = work_ctr;
     // composite-only plans carry no subsets; their offsets are unused
     for (int k = 0; k <= K; ++k) b.goff[k] = k < (int)subsets_h.size() ? subsets_h[k].goff : N;
     for (int v = 0; v <= V; ++v) { b.tile_base[v] = tile_base[v]; b.pix_off[v] = pix_off[v]; }
@@ -247,7 +250,7 @@ struct Plan {
                    (void**)&counts, (void**)&tile_cnt, (void**)&tile_start, (void**)&keys,
                    (void**)&keys_alt, (void**)&big_list, (void**)&big_count, (void**)&chunks,
                    (void**)&chunk_count, (void**)&ranges,
-                   (void**)&grad2d, (void**)&scan_temp, (void**)&counters};
+                   (void**)&grad2d, (void**)&scan_temp, (void**)&counters, (void**)&work_ctr};
     for (void** p : ps) free_ptr(*p, s);
     for (auto& e : ev)
       if (e) { cudaEventDestroy(e); e = nullptr; }
@@ -256,7 +259,8 @@ struct Plan {
   // Project (counting pairs per tile) and scan the counts into segment starts.
   int project_and_count(cudaStream_t s) {
     const BatchDev b = dev();
-    if (counters) CK(cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned long long), s));
+    if (counters && !stream_capturing(s))
+      CK(cudaMemsetAsync(counters, 0, kCounters * sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(n_tiles, 1), s));
     CK(cudaMemsetAsync(big_count, 0, sizeof(unsigned), s));
     CK(cudaMemsetAsync(chunk_count, 0, sizeof(unsigned), s));
@@ -734,9 +738,10 @@ int splx_batch_create(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
   }
   if ((r = P.alloc_common(s))) return fail(r);
   if ((r = ctx_alloc_t(ctx, &P.grad2d, (size_t)V * N * 3, s))) return fail(r);
-  if ((r = ctx_alloc_t(ctx, &P.counters, 4, s))) return fail(r);
+  if ((r = ctx_alloc_t(ctx, &P.counters, kCounters, s))) return fail(r);
+  if ((r = ctx_alloc_t(ctx, &P.work_ctr, 2, s))) return fail(r);
   cudaError_t e = cudaMemsetAsync(P.grad2d, 0, sizeof(float4) * 3 * (size_t)V * N, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(P.counters, 0, 4 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.counters, 0, kCounters * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return fail(cuda_fail(e, "memset grad2d"));
   if (cudaMallocHost(&bt->pinned_cams, sizeof(splx_camera) * kMaxViews) != cudaSuccess)
     bt->pinned_cams = nullptr;
@@ -841,6 +846,26 @@ int splx_batch_set_timing(splx_batch_t bt, int enable) {
   return SPLX_OK;
 }
 
+int splx_batch_set_launch(splx_batch_t bt, int32_t raster_ctas_per_sm) {
+  if (!bt || raster_ctas_per_sm < 0 || raster_ctas_per_sm > 64) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  CtxScope scope(P.ctx);
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P.ctx->device));
+  P.persist_grid = raster_ctas_per_sm * sms;
+  return SPLX_OK;
+}
+
+int splx_batch_max_ctas_per_sm(splx_batch_t bt, int32_t* fwd, int32_t* bwd) {
+  if (!bt || !fwd || !bwd) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  CtxScope scope(P.ctx);
+  *fwd = raster_max_ctas_per_sm(P.tile, false);
+  *bwd = raster_max_ctas_per_sm(P.tile, true);
+  if (*fwd <= 0 || *bwd <= 0) return SPLX_ERR_CUDA;
+  return SPLX_OK;
+}
+
 int splx_batch_kernel_times(splx_batch_t bt, float* ms_out) {
   if (!bt || !ms_out) return SPLX_ERR_INVALID;
   Plan& P = bt->plan;
@@ -862,15 +887,13 @@ int splx_batch_counters(splx_batch_t bt, int64_t* out, splx_stream_t stream) {
   Plan& P = bt->plan;
   CtxScope scope(P.ctx);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  unsigned long long c[4] = {0, 0, 0, 0};
+  unsigned long long c[kCounters] = {};
   uint32_t total = 0;
   CK(cudaMemcpyAsync(c, P.counters, sizeof(c), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&total, P.tile_start + P.n_tiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   out[0] = (int64_t)total;
-  out[1] = (int64_t)c[0];
-  out[2] = (int64_t)c[1];
-  out[3] = (int64_t)c[2];
+  for (int i = 0; i < kCounters; ++i) out[1 + i] = (int64_t)c[i];
   return SPLX_OK;
 }
 
@@ -902,6 +925,340 @@ int splx_batch_destroy(splx_batch_t bt) {
   cudaDeviceSynchronize();
   if (bt->pinned_cams) cudaFreeHost(bt->pinned_cams);
   delete bt;
+  return SPLX_OK;
+}
+
+// ---------------------------------------------------------------- serving
+namespace {
+
+struct SrvReq {
+  int64_t id;
+  splx_camera cam;
+  float* out;  // device [3][H][W], caller-owned
+};
+
+// One launch of a server slot: the views of up to max_views requests x K subsets, on the
+// slot's own stream.  Phase 1 = projected, waiting for the pair count (copied to pinned
+// memory behind an event); phase 2 = binned, rendered, composited and copied out.
+struct SrvLaunch {
+  int phase = 0;
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev = nullptr;
+  uint32_t* total_h = nullptr;
+  Plan P;
+  float* partial = nullptr;
+  int32_t* last = nullptr;
+  float* out_cat = nullptr;
+  std::vector<SrvReq> reqs;
+  size_t reserved = 0;
+};
+
+}  // namespace
+
+struct splx_server_s {
+  splx_ctx_t ctx = nullptr;
+  std::vector<splx_gaussians> subsets;
+  int64_t N = 0;
+  splx_opts opts{};
+  size_t budget = 0, reserved = 0;
+  int max_views = 1;
+  double pairs_per_px = 32.0;  // admission estimate; raised to the largest count seen
+  int64_t next_id = 0;
+  std::deque<SrvReq> pending;
+  std::vector<SrvLaunch> slots;
+  std::deque<std::pair<int64_t, int>> finished;  // (request id, status) not yet reported
+};
+
+namespace {
+
+// Device bytes one launch holds: records and tile counts per (view, Gaussian), the K
+// partial planes and the composited views, per-tile arrays, and the pair buffers.
+size_t launch_bytes(const splx_server_s& S, const std::vector<SrvReq>& reqs, double pairs) {
+  const int K = (int)S.subsets.size();
+  int64_t px = 0, tiles = 0;
+  for (const SrvReq& r : reqs) {
+    px += (int64_t)r.cam.width * r.cam.height;
+    tiles += (int64_t)K * ((r.cam.width + S.opts.tile - 1) / S.opts.tile) *
+             ((r.cam.height + S.opts.tile - 1) / S.opts.tile);
+  }
+  const double b = (double)reqs.size() * S.N * (sizeof(Rec) + 4) + (double)px * K * 24.0 +
+                   (double)px * 12.0 + (double)tiles * 48.0 + pairs * 16.0 +
+                   (pairs / 2048.0 + 1.0) * 8.0 + 65536.0;
+  return (size_t)b;
+}
+
+int64_t launch_pixels(const std::vector<SrvReq>& reqs) {
+  int64_t px = 0;
+  for (const SrvReq& r : reqs) px += (int64_t)r.cam.width * r.cam.height;
+  return px;
+}
+
+void srv_free_launch(splx_server_s* S, SrvLaunch& L) {
+  L.P.release(L.s);
+  ctx_free(S->ctx, L.partial, L.s);
+  ctx_free(S->ctx, L.last, L.s);
+  ctx_free(S->ctx, L.out_cat, L.s);
+  L.partial = nullptr; L.last = nullptr; L.out_cat = nullptr;
+  S->reserved -= std::min(S->reserved, L.reserved);
+  L.reserved = 0;
+  L.phase = 0;
+  L.reqs.clear();
+  Plan fresh;
+  L.P = fresh;
+}
+
+void srv_fail_launch(splx_server_s* S, SrvLaunch& L, int code) {
+  for (const SrvReq& r : L.reqs) S->finished.emplace_back(r.id, code);
+  srv_free_launch(S, L);
+}
+
+// Plans the launch and enqueues projection + tile counting + scan and the copy of the
+// pair count; returns an error code (the caller fails the launch's requests).
+int srv_start(splx_server_s* S, SrvLaunch& L) {
+  Plan& P = L.P;
+  const int K = (int)S->subsets.size();
+  const int V = (int)L.reqs.size();
+  P.ctx = S->ctx; P.V = V; P.K = K; P.deg = S->subsets[0].sh_degree; P.tile = S->opts.tile;
+  P.N = S->N; P.opts = S->opts;
+  int64_t goff = 0;
+  for (int k = 0; k < K; ++k) {
+    P.subsets_h.push_back(make_subset(S->subsets[k], goff));
+    goff += S->subsets[k].n;
+  }
+  for (int v = 0; v < V; ++v) P.views_h.push_back(make_view(L.reqs[v].cam, S->opts.tile));
+  P.layout();
+  const int64_t TP = P.total_pixels;
+  int r;
+  if ((r = ctx_alloc_t(S->ctx, &L.partial, (size_t)5 * K * TP, L.s))) return r;
+  if ((r = ctx_alloc_t(S->ctx, &L.last, (size_t)K * TP, L.s))) return r;
+  if ((r = ctx_alloc_t(S->ctx, &L.out_cat, (size_t)3 * TP, L.s))) return r;
+  float* rgb_base = L.partial;
+  float* T_base = L.partial + (size_t)3 * K * TP;
+  float* D_base = T_base + (size_t)K * TP;
+  for (int v = 0; v < V; ++v) {
+    const int64_t HW = (int64_t)P.views_h[v].W * P.views_h[v].H;
+    for (int k = 0; k < K; ++k) {
+      const int64_t o = (int64_t)K * P.pix_off[v] + (int64_t)k * HW;
+      ImgDev im;
+      im.rgb = rgb_base + 3 * o; im.T = T_base + o; im.D = D_base + o; im.last = L.last + o;
+      im.gCT = nullptr;
+      P.imgs_h.push_back(im);
+    }
+  }
+  if ((r = P.alloc_common(L.s))) return r;
+  if ((r = P.project_and_count(L.s))) return r;
+  CK(cudaMemcpyAsync(L.total_h, P.tile_start + P.n_tiles, sizeof(uint32_t),
+                     cudaMemcpyDeviceToHost, L.s));
+  CK(cudaEventRecord(L.ev, L.s));
+  L.phase = 1;
+  return SPLX_OK;
+}
+
+// Binning, local render, composition and the copies into the requests' buffers.
+int srv_render(splx_server_s* S, SrvLaunch& L, uint64_t total) {
+  Plan& P = L.P;
+  int r;
+  if (total >= (uint64_t)UINT32_MAX) return SPLX_ERR_CAPACITY;
+  if ((r = P.alloc_pairs((int64_t)total, L.s))) return r;
+  if ((r = P.fill_and_sort(L.s))) return r;
+  BatchDev b = P.dev();
+  b.out_rgb = L.out_cat;
+  b.out_T = nullptr;
+  launch_raster_fwd(b, L.s);
+  launch_composite(b, P.total_pixels, L.s);
+  CK_LAUNCH();
+  for (int v = 0; v < P.V; ++v) {
+    const size_t bytes = sizeof(float) * 3 * (size_t)P.views_h[v].W * P.views_h[v].H;
+    CK(cudaMemcpyAsync(L.reqs[v].out, L.out_cat + 3 * P.pix_off[v], bytes,
+                       cudaMemcpyDeviceToDevice, L.s));
+  }
+  CK(cudaEventRecord(L.ev, L.s));
+  L.phase = 2;
+  return SPLX_OK;
+}
+
+bool srv_any_inflight(const splx_server_s* S) {
+  for (const SrvLaunch& L : S->slots)
+    if (L.phase != 0) return true;
+  return false;
+}
+
+// One scheduling pass: retire finished launches, move counted launches on to rendering
+// once their pair buffers fit the budget, then admit pending requests into idle slots.
+int srv_advance(splx_server_s* S) {
+  for (SrvLaunch& L : S->slots) {
+    if (L.phase == 0) continue;
+    const cudaError_t q = cudaEventQuery(L.ev);
+    if (q == cudaErrorNotReady) continue;
+    if (q != cudaSuccess) {
+      srv_fail_launch(S, L, cuda_fail(q, "server launch"));
+      continue;
+    }
+    if (L.phase == 2) {
+      for (const SrvReq& r : L.reqs) S->finished.emplace_back(r.id, SPLX_OK);
+      srv_free_launch(S, L);
+      continue;
+    }
+    // phase 1: the pair count is known; re-reserve with it and render if it fits.  If it
+    // does not: wait while a rendering launch will free memory; fail if this launch is
+    // alone; otherwise (only other counted launches hold memory) give its requests back
+    // to the head of the queue, so no two launches wait on each other.
+    const uint64_t total = *L.total_h;
+    const int64_t px = launch_pixels(L.reqs);
+    if (px > 0) S->pairs_per_px = std::max(S->pairs_per_px, (double)total / (double)px);
+    const size_t need = launch_bytes(*S, L.reqs, (double)total);
+    const size_t others = S->reserved - std::min(S->reserved, L.reserved);
+    if (others + need > S->budget) {
+      bool rendering = false, alone = true;
+      for (const SrvLaunch& o : S->slots) {
+        if (&o == &L || o.phase == 0) continue;
+        alone = false;
+        if (o.phase == 2) rendering = true;
+      }
+      if (rendering) continue;
+      if (alone) {
+        srv_fail_launch(S, L, SPLX_ERR_BUDGET);
+      } else {
+        for (auto it = L.reqs.rbegin(); it != L.reqs.rend(); ++it) S->pending.push_front(*it);
+        L.reqs.clear();
+        srv_free_launch(S, L);
+      }
+      continue;
+    }
+    S->reserved = others + need;
+    L.reserved = need;
+    const int r = srv_render(S, L, total);
+    if (r) srv_fail_launch(S, L, r);
+  }
+  for (SrvLaunch& L : S->slots) {
+    if (L.phase != 0 || S->pending.empty()) continue;
+    std::vector<SrvReq> take;
+    size_t bytes = 0;
+    while (!S->pending.empty() && (int)take.size() < S->max_views) {
+      take.push_back(S->pending.front());
+      const size_t b = launch_bytes(*S, take, S->pairs_per_px * launch_pixels(take));
+      if (S->reserved + b > S->budget) {
+        take.pop_back();
+        break;
+      }
+      bytes = b;
+      S->pending.pop_front();
+    }
+    if (take.empty()) {
+      if (srv_any_inflight(S)) break;  // wait for memory to free up
+      // nothing in flight: the estimate alone never rejects a request.  Admit the oldest
+      // if its footprint without pair buffers fits; its exact pair count decides later.
+      take.push_back(S->pending.front());
+      S->pending.pop_front();
+      bytes = launch_bytes(*S, take, 0.0);
+      if (S->reserved + bytes > S->budget) {
+        S->finished.emplace_back(take[0].id, SPLX_ERR_BUDGET);
+        continue;
+      }
+    }
+    L.reqs = std::move(take);
+    L.reserved = bytes;
+    S->reserved += bytes;
+    const int r = srv_start(S, L);
+    if (r) srv_fail_launch(S, L, r);
+  }
+  return SPLX_OK;
+}
+
+}  // namespace
+
+int splx_server_create(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
+                       const splx_opts* opts, size_t hbm_budget_bytes, int32_t slots,
+                       int32_t max_views, splx_server_t* out) {
+  if (!ctx || !subsets || !out || K < 1 || K > kMaxK || slots < 1 || slots > 16 ||
+      max_views < 1 || max_views > kMaxViews || hbm_budget_bytes == 0)
+    return SPLX_ERR_INVALID;
+  *out = nullptr;
+  int r;
+  if ((r = check_opts(opts))) return r;
+  int64_t N = 0;
+  for (int k = 0; k < K; ++k) {
+    if ((r = check_gaussians(&subsets[k]))) return r;
+    if (subsets[k].sh_degree != subsets[0].sh_degree) return SPLX_ERR_INVALID;
+    N += subsets[k].n;
+  }
+  if (N >= (int64_t(1) << 32)) return SPLX_ERR_INVALID;
+  CtxScope scope(ctx);
+  splx_server_s* S = new (std::nothrow) splx_server_s();
+  if (!S) return SPLX_ERR_BUDGET;
+  S->ctx = ctx;
+  S->subsets.assign(subsets, subsets + K);
+  S->N = N;
+  S->opts = *opts;
+  S->budget = hbm_budget_bytes;
+  S->max_views = max_views;
+  S->slots.resize((size_t)slots);
+  cudaError_t e = cudaSuccess;
+  for (SrvLaunch& L : S->slots) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(&L.total_h, sizeof(uint32_t));
+  }
+  if (e != cudaSuccess) {
+    splx_server_destroy(S);
+    return cuda_fail(e, "splx_server_create");
+  }
+  *out = S;
+  return SPLX_OK;
+}
+
+int splx_server_submit(splx_server_t S, const splx_camera* cam, float* out_rgb, int64_t* id_out) {
+  if (!S || !out_rgb || !id_out) return SPLX_ERR_INVALID;
+  int r;
+  if ((r = check_cam(cam))) return r;
+  SrvReq q;
+  q.id = S->next_id++;
+  q.cam = *cam;
+  q.out = out_rgb;
+  S->pending.push_back(q);
+  *id_out = q.id;
+  CtxScope scope(S->ctx);
+  return srv_advance(S);
+}
+
+int splx_server_poll(splx_server_t S, int64_t* ids, int32_t* status, int32_t cap, int32_t* n_out) {
+  if (!S || !n_out || cap < 0 || (cap > 0 && (!ids || !status))) return SPLX_ERR_INVALID;
+  CtxScope scope(S->ctx);
+  int r = srv_advance(S);
+  int n = 0;
+  while (n < cap && !S->finished.empty()) {
+    ids[n] = S->finished.front().first;
+    status[n] = S->finished.front().second;
+    S->finished.pop_front();
+    ++n;
+  }
+  *n_out = n;
+  return r;
+}
+
+int splx_server_stats(splx_server_t S, int32_t* queued, int32_t* inflight, size_t* reserved) {
+  if (!S) return SPLX_ERR_INVALID;
+  int n = 0;
+  for (const SrvLaunch& L : S->slots)
+    if (L.phase != 0) n += (int)L.reqs.size();
+  if (queued) *queued = (int32_t)S->pending.size();
+  if (inflight) *inflight = n;
+  if (reserved) *reserved = S->reserved;
+  return SPLX_OK;
+}
+
+int splx_server_destroy(splx_server_t S) {
+  if (!S) return SPLX_ERR_INVALID;
+  CtxScope scope(S->ctx);
+  for (SrvLaunch& L : S->slots) {
+    if (L.s) cudaStreamSynchronize(L.s);
+    if (L.phase != 0) srv_free_launch(S, L);
+    if (L.s) cudaStreamSynchronize(L.s);
+    if (L.s) cudaStreamDestroy(L.s);
+    if (L.ev) cudaEventDestroy(L.ev);
+    if (L.total_h) cudaFreeHost(L.total_h);
+  }
+  delete S;
   return SPLX_OK;
 }
 

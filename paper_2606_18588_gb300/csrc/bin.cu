@@ -15,6 +15,7 @@
 // that end in the twin are copied back.  Every pair is read and written a few times
 // instead of once per 8-bit pass over 50+ key bits.
 #include "common.cuh"
+#include "spec.cuh"
 
 namespace splx {
 
@@ -37,13 +38,19 @@ __device__ __forceinline__ void cas(uint64_t& a, uint64_t& b) {
   b = hi;
 }
 
-// Number of elements taken from A among the first d of merge(A, B), in shared memory.
-__device__ __forceinline__ int merge_path_smem(const uint64_t* A, int na, const uint64_t* B, int nb,
+// Shared buffers hold one spare slot per 8 keys, so that the 8-key runs a warp touches
+// with stride 8 fall into different banks.
+__device__ __forceinline__ int pad(int i) { return i + (i >> 3); }
+constexpr int kPadded = kChunk + kChunk / 8;
+
+// Number of elements taken from A = s[pad(a0 + i)] among the first d of merge(A, B) with
+// B = s[pad(b0 + j)], in shared memory.
+__device__ __forceinline__ int merge_path_smem(const uint64_t* s, int a0, int na, int b0, int nb,
                                                int d) {
   int lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (A[mid] < B[d - 1 - mid]) lo = mid + 1;
+    if (s[pad(a0 + mid)] < s[pad(b0 + d - 1 - mid)]) lo = mid + 1;
     else hi = mid;
   }
   return lo;
@@ -52,24 +59,24 @@ __device__ __forceinline__ int merge_path_smem(const uint64_t* A, int na, const 
 // Sorts keys[0, n) (n <= kChunk) in place: each thread sorts kItems keys in registers
 // (odd-even transposition network), then runs of 8, 16, ... are merged pairwise through
 // two shared buffers, every thread producing kItems outputs located by merge path.
-// The array is padded to a power of two P >= 8 with ~0 keys.  sa, sb: kChunk keys each.
+// The array is padded to a power of two P >= 8 with ~0 keys.  sa, sb: kPadded keys each.
 __device__ __forceinline__ void sort_chunk(uint64_t* keys, int n, uint64_t* sa, uint64_t* sb) {
   int P = next_pow2(n);
   if (P < kItems) P = kItems;
-  for (int i = threadIdx.x; i < P; i += kSortThreads) sa[i] = i < n ? keys[i] : ~0ull;
+  for (int i = threadIdx.x; i < P; i += kSortThreads) sa[pad(i)] = i < n ? keys[i] : ~0ull;
   __syncthreads();
   const int active = P / kItems;  // threads holding keys
   const int t = threadIdx.x;
   if (t < active) {
     uint64_t v[kItems];
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) v[r] = sa[t * kItems + r];
+    for (int r = 0; r < kItems; ++r) v[r] = sa[pad(t * kItems + r)];
 #pragma unroll
     for (int pass = 0; pass < kItems; ++pass)
 #pragma unroll
       for (int r = pass & 1; r + 1 < kItems; r += 2) cas(v[r], v[r + 1]);
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) sa[t * kItems + r] = v[r];
+    for (int r = 0; r < kItems; ++r) sa[pad(t * kItems + r)] = v[r];
   }
   __syncthreads();
   uint64_t* src = sa;
@@ -78,15 +85,16 @@ __device__ __forceinline__ void sort_chunk(uint64_t* keys, int n, uint64_t* sa, 
     if (t < active) {
       const int o = t * kItems;
       const int p0 = (o / (2 * w)) * (2 * w);
-      const uint64_t* A = src + p0;
-      const uint64_t* B = A + w;
       const int d = o - p0;
-      int ia = merge_path_smem(A, w, B, w, d);
+      int ia = merge_path_smem(src, p0, w, p0 + w, w, d);
       int ib = d - ia;
 #pragma unroll
       for (int r = 0; r < kItems; ++r) {
-        const bool takeA = ib >= w || (ia < w && A[ia] < B[ib]);
-        dst[o + r] = takeA ? A[ia++] : B[ib++];
+        const uint64_t va = ia < w ? src[pad(p0 + ia)] : ~0ull;
+        const uint64_t vb = ib < w ? src[pad(p0 + w + ib)] : ~0ull;
+        const bool takeA = ib >= w || (ia < w && va < vb);
+        dst[pad(o + r)] = takeA ? va : vb;
+        if (takeA) ++ia; else ++ib;
       }
     }
     __syncthreads();
@@ -94,7 +102,7 @@ __device__ __forceinline__ void sort_chunk(uint64_t* keys, int n, uint64_t* sa, 
     src = dst;
     dst = tmp;
   }
-  for (int i = threadIdx.x; i < n; i += kSortThreads) keys[i] = src[i];
+  for (int i = threadIdx.x; i < n; i += kSortThreads) keys[i] = src[pad(i)];
 }
 
 __device__ __forceinline__ void segment_of(const BatchDev& b, int64_t t, uint32_t& s, uint32_t& e) {
@@ -115,14 +123,22 @@ __device__ __forceinline__ int rounds_for(uint32_t n) {
   return r;
 }
 
-// Number of elements taken from A among the first d of merge(A, B) (unique keys).
-__device__ __forceinline__ uint32_t merge_path(const uint64_t* A, uint32_t na, const uint64_t* B,
-                                               uint32_t nb, uint32_t d) {
+// Number of elements taken from A among the first d of merge(A, B) (unique keys), found
+// by one warp with 32 probes per step (a 33-ary search over global memory).
+__device__ __forceinline__ uint32_t merge_path_warp(const uint64_t* A, uint32_t na,
+                                                    const uint64_t* B, uint32_t nb, uint32_t d) {
+  const unsigned lane = threadIdx.x & 31u;
   uint32_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
   while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (A[mid] < B[d - 1 - mid]) lo = mid + 1;
-    else hi = mid;
+    const uint32_t span = hi - lo;
+    const uint32_t m = lo + (uint32_t)(((uint64_t)span * (lane + 1)) / 33u);
+    const bool pred = A[m] < B[d - 1 - m];  // true exactly for m below the answer
+    const unsigned bal = __ballot_sync(0xffffffffu, pred);
+    const int nt = __popc(bal);
+    const uint32_t m_last_true = __shfl_sync(0xffffffffu, m, nt > 0 ? nt - 1 : 0);
+    const uint32_t m_first_false = __shfl_sync(0xffffffffu, m, nt < 32 ? nt : 31);
+    if (nt > 0) lo = m_last_true + 1;
+    if (nt < 32) hi = m_first_false;
   }
   return lo;
 }
@@ -137,9 +153,10 @@ __global__ void __launch_bounds__(256) k_fill(const BatchDev b) {
   const uint32_t tiles = b.counts[idx];
   const int v = (int)(idx / b.N);
   const int64_t g = idx - (int64_t)v * b.N;
-  int tw = 1, tiles_x = 0;
+  int tw = 1, tiles_x = 0, tx0 = 0, ty0 = 0, rx0 = 0, rx1 = 0, ry0 = 0, ry1 = 0;
   int64_t tbase = 0;
   uint64_t key = 0;
+  TileCull tc = tile_cull_prep(0.f, 0.f, 1.f, 0.f, 1.f, -1.0f);
   if (tiles) {
     const int k = subset_of(b, g);
     const ViewDev& cam = b.views[v];
@@ -147,9 +164,14 @@ __global__ void __launch_bounds__(256) k_fill(const BatchDev b) {
     const float4 rb = r->b;
     const uint32_t rx = __float_as_uint(rb.w), ry = __float_as_uint(r->c.w);
     const int B_ = b.tile;
-    const int tx0 = (int)(rx & 0xFFFFu) / B_, tx1 = (int)(rx >> 16) / B_;
-    const int ty0 = (int)(ry & 0xFFFFu) / B_;
+    rx0 = (int)(rx & 0xFFFFu); rx1 = (int)(rx >> 16);
+    ry0 = (int)(ry & 0xFFFFu); ry1 = (int)(ry >> 16);
+    tx0 = rx0 / B_;
+    ty0 = ry0 / B_;
+    const int tx1 = rx1 / B_;
     tw = tx1 - tx0 + 1;
+    const float4 ra = r->a, rd = r->d;  // rd: spec conic and threshold of the tile test
+    tc = tile_cull_prep(ra.x, ra.y, rd.x, rd.y, rd.z, rd.w);
     tiles_x = cam.tiles_x;
     tbase = b.tile_base[v] + (int64_t)k * cam.tiles_x * cam.tiles_y + (int64_t)ty0 * cam.tiles_x + tx0;
     key = ((uint64_t)__float_as_uint(rb.z) << 32) | (uint64_t)(uint32_t)g;
@@ -159,7 +181,9 @@ __global__ void __launch_bounds__(256) k_fill(const BatchDev b) {
   bool overflow = false;
   int jx = 0, jy = 0;  // column / row of the j-th tile inside the rectangle
   for (int j = 0; j < maxt; ++j) {
-    const unsigned t = j < (int)tiles ? (unsigned)(tbase + jy * tiles_x + jx) : 0xFFFFFFFFu;
+    unsigned t = 0xFFFFFFFFu;
+    if (j < (int)tiles && tile_hits_spec(tc, rx0, rx1, ry0, ry1, tx0 + jx, ty0 + jy, b.tile))
+      t = (unsigned)(tbase + jy * tiles_x + jx);
     if (++jx == tw) { jx = 0; ++jy; }
     const unsigned peers = __match_any_sync(lanes, t);
     const int leader = __ffs(peers) - 1;
@@ -187,7 +211,7 @@ void launch_fill(const BatchDev& b, cudaStream_t s) {
 // One CTA per tile: ranges, then either the whole segment (<= kChunk keys) or, for a
 // longer one, its registration as chunk work items (segment list index, chunk index).
 __global__ void __launch_bounds__(kSortThreads) k_seg_sort_small(const BatchDev b) {
-  __shared__ uint64_t sk[2][kChunk];
+  __shared__ uint64_t sk[2][kPadded];
   __shared__ unsigned s_base[2];
   const int64_t t = blockIdx.x;
   uint32_t s, e;
@@ -212,7 +236,7 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_sort_small(const BatchDev 
 
 // Sorts every 2048-key chunk of the long segments (grid-stride over the chunk list).
 __global__ void __launch_bounds__(kSortThreads) k_chunk_sort(const BatchDev b) {
-  __shared__ uint64_t sk[2][kChunk];
+  __shared__ uint64_t sk[2][kPadded];
   const unsigned count = *b.chunk_count;
   for (unsigned w = blockIdx.x; w < count; w += gridDim.x) {
     const uint2 ch = b.chunks[w];
@@ -231,7 +255,7 @@ __global__ void __launch_bounds__(kSortThreads) k_chunk_sort(const BatchDev b) {
 // merge of the two runs its output range falls in.  Data of round r lives in keys when r
 // is even and in keys_alt when r is odd.
 __global__ void __launch_bounds__(kSortThreads) k_merge_round(const BatchDev b, int r) {
-  __shared__ uint64_t sm[kChunk];
+  __shared__ uint64_t sm[kPadded];
   __shared__ uint32_t s_split[4];
   constexpr int PER = kChunk / kSortThreads;  // outputs per thread
   const unsigned count = *b.chunk_count;
@@ -253,27 +277,33 @@ __global__ void __launch_bounds__(kSortThreads) k_merge_round(const BatchDev b, 
     const uint32_t nb = (p0 + 2 * w < n ? p0 + 2 * w : n) - (p0 + na);
     const uint64_t* A = src + p0;
     const uint64_t* B = A + na;
-    if (threadIdx.x == 0) {
-      const uint32_t a0 = merge_path(A, na, B, nb, o0 - p0);
-      const uint32_t a1 = merge_path(A, na, B, nb, o1 - p0);
-      s_split[0] = a0; s_split[1] = a1;
-      s_split[2] = (o0 - p0) - a0; s_split[3] = (o1 - p0) - a1;
+    // warp 0 finds the split at the block's first output, warp 1 at its end
+    if (threadIdx.x < 64) {
+      const uint32_t dd = (threadIdx.x < 32 ? o0 : o1) - p0;
+      const uint32_t a = merge_path_warp(A, na, B, nb, dd);
+      if ((threadIdx.x & 31) == 0) {
+        s_split[threadIdx.x >> 5] = a;
+        s_split[2 + (threadIdx.x >> 5)] = dd - a;
+      }
     }
     __syncthreads();
     const uint32_t a0 = s_split[0], a1 = s_split[1], b0 = s_split[2], b1 = s_split[3];
-    const uint32_t la = a1 - a0, lb = b1 - b0;
-    for (uint32_t i = threadIdx.x; i < la; i += kSortThreads) sm[i] = A[a0 + i];
-    for (uint32_t i = threadIdx.x; i < lb; i += kSortThreads) sm[la + i] = B[b0 + i];
+    const int la = (int)(a1 - a0), lb = (int)(b1 - b0);
+    for (int i = threadIdx.x; i < la; i += kSortThreads) sm[pad(i)] = A[a0 + i];
+    for (int i = threadIdx.x; i < lb; i += kSortThreads) sm[pad(la + i)] = B[b0 + i];
     __syncthreads();
     // each thread merges PER consecutive outputs of sm[0,la) and sm[la,la+lb)
-    const uint32_t d = threadIdx.x * PER;
+    const int d = threadIdx.x * PER;
     if (d < la + lb) {
-      uint32_t ia = merge_path(sm, la, sm + la, lb, d);
-      uint32_t ib = d - ia;
-      const uint32_t dend = d + PER < la + lb ? d + PER : la + lb;
-      for (uint32_t o = d; o < dend; ++o) {
-        const bool takeA = ib >= lb || (ia < la && sm[ia] < sm[la + ib]);
-        dst[o0 + o - 0] = takeA ? sm[ia++] : sm[la + ib++];
+      int ia = merge_path_smem(sm, 0, la, la, lb, d);
+      int ib = d - ia;
+      const int dend = d + PER < la + lb ? d + PER : la + lb;
+      for (int o = d; o < dend; ++o) {
+        const uint64_t va = ia < la ? sm[pad(ia)] : ~0ull;
+        const uint64_t vb = ib < lb ? sm[pad(la + ib)] : ~0ull;
+        const bool takeA = ib >= lb || (ia < la && va < vb);
+        dst[o0 + o] = takeA ? va : vb;
+        if (takeA) ++ia; else ++ib;
       }
     }
     __syncthreads();

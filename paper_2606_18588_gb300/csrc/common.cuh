@@ -9,6 +9,14 @@
 namespace splx {
 
 constexpr int kMaxK = 64;        // subsets per view
+constexpr int kCounters = 6;     // work counters of a batch (BatchDev::counters)
+
+// True while `s` is being captured into a CUDA graph.
+inline bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  return cs != cudaStreamCaptureStatusNone;
+}
 constexpr int kMaxViews = 256;   // views per batch
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
@@ -53,7 +61,8 @@ struct ImgDev {
 //   a = (u, v, qa, qb)      2-D mean, conic scaled by -log2(e)/2 ... see project.cu
 //   b = (qc, opacity, depth, rect_x)   rect_x = x0 | x1 << 16 (bit pattern)
 //   c = (r, g, b, rect_y)              rect_y = y0 | y1 << 16
-//   d = (unused)
+//   d = (A, B, C, q_max)     conic and tile-test threshold in the binning specification
+//                            (inputs of the tile test, read again by fill)
 struct Rec {
   float4 a, b, c, d;
 };
@@ -87,9 +96,14 @@ struct BatchDev {
   int64_t pix_off[kMaxViews + 1];    // view v's pixels start at pix_off[v]
   float4* grad2d;               // [V][N][3]: (gu, gv, gA, gB), (gC, go, gr, gg), (gb, 0, 0, 0)
   int* status;                  // device status word
-  // work counters (nullable): [0] list entries examined by the forward rasteriser,
-  // [1] Gaussians blended, [2] entries examined by the backward rasteriser
+  // work counters (nullable; kept by eager runs): forward [0] thread-entries examined,
+  // [1] (pixel, entry) alpha evaluations, [2] blends; backward [3] thread-entries,
+  // [4] alpha evaluations, [5] contributions (alpha >= alpha_min)
   unsigned long long* counters;
+  // persistent rasterisers: grid size (0 = one CTA per work item) and the two work
+  // counters they take items from ([0] forward, [1] backward; reset before each launch)
+  int persist_grid;
+  unsigned long long* work_ctr;
   // concatenated per-view I/O: view v's rgb at 3*pix_off[v], its T plane at pix_off[v]
   float* out_rgb;
   float* out_T;                 // nullable
@@ -117,6 +131,8 @@ void launch_raster_fwd(const BatchDev& b, cudaStream_t s);
 void launch_composite(const BatchDev& b, int64_t total_pixels, cudaStream_t s);
 void launch_composite_bwd(const BatchDev& b, int64_t total_pixels, cudaStream_t s);
 void launch_raster_bwd(const BatchDev& b, cudaStream_t s);
+// Largest number of persistent rasteriser CTAs that fit on one SM (0 on error).
+int raster_max_ctas_per_sm(int tile, bool bwd);
 void launch_project_bwd(const BatchDev& b, const GradTable& gt, cudaStream_t s);
 
 // exclusive scan of n u32 values (out has n+1 entries; out[n] = total)

@@ -71,7 +71,10 @@ __global__ void __launch_bounds__(256) k_project(const BatchDev b) {
   }
   const float4 qv = __ldg(reinterpret_cast<const float4*>(S.quats) + i);
   q[0] = qv.x; q[1] = qv.y; q[2] = qv.z; q[3] = qv.w;
-  const float opac = 1.0f / (1.0f + __expf(-__ldg(S.opacity_logits + i)));
+  const float logit = __ldg(S.opacity_logits + i);
+  const float opac = 1.0f / (1.0f + __expf(-logit));
+  // the tile test's threshold on the conic's quadratic form (view independent)
+  const float qmax = tile_cull_qmax(spec_opacity(logit), b.alpha_min);
   constexpr int NC = (DEG + 1) * (DEG + 1);
   float sh[NC * 3];
 #pragma unroll
@@ -83,7 +86,9 @@ __global__ void __launch_bounds__(256) k_project(const BatchDev b) {
                                 cam.H, cam.near_plane);
     Rec r;
     uint32_t tiles = 0;
+    float sA = 0.f, sB = 0.f, sC = 0.f;
     if (so.visible) {
+      spec_conic(so, sA, sB, sC);
       const float inv = 1.0f / so.det;
       const float A = so.c * inv, B = -so.b * inv, Cc = so.a * inv;
       // p2 = power * log2(e) = qa dx^2 + qb dx dy + qc dy^2
@@ -113,21 +118,28 @@ __global__ void __launch_bounds__(256) k_project(const BatchDev b) {
       r.b = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFu));
       r.c = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFu));
     }
-    r.d = make_float4(0.f, 0.f, 0.f, 0.f);
+    // the tile test's inputs, so that fill repeats exactly the same decisions
+    r.d = make_float4(sA, sB, sC, so.visible ? qmax : -1.0f);
     Rec* dst = b.rec + (int64_t)v * b.N + g;
     dst->a = r.a; dst->b = r.b; dst->c = r.c; dst->d = r.d;
     b.counts[(int64_t)v * b.N + g] = tiles;
-    // count this Gaussian in every tile its rectangle touches (the segment sizes of the
-    // binning); lanes that hit the same tile add together (neighbouring Gaussians are
-    // neighbours in memory), so most tiles see one atomic per warp
+    // count this Gaussian in every tile of its rectangle that passes the tile test (the
+    // segment sizes of the binning); lanes that hit the same tile add together
+    // (neighbouring Gaussians are neighbours in memory), so most tiles see one atomic
+    // per warp
     const int tw = so.visible ? so.x1 / b.tile - so.x0 / b.tile + 1 : 1;
     const int64_t tbase = b.tile_base[v] + (int64_t)k * cam.tiles_x * cam.tiles_y +
                           (int64_t)(so.visible ? so.y0 / b.tile : 0) * cam.tiles_x +
                           (so.visible ? so.x0 / b.tile : 0);
     const int maxt = __reduce_max_sync(lanes, (int)tiles);
     int jx = 0, jy = 0;  // column / row of the j-th tile inside the rectangle
+    const int tx0 = so.visible ? so.x0 / b.tile : 0, ty0 = so.visible ? so.y0 / b.tile : 0;
+    const TileCull tc = tile_cull_prep(so.u, so.v, sA, sB, sC, so.visible ? qmax : -1.0f);
     for (int j = 0; j < maxt; ++j) {
-      const unsigned t = j < (int)tiles ? (unsigned)(tbase + jy * cam.tiles_x + jx) : 0xFFFFFFFFu;
+      unsigned t = 0xFFFFFFFFu;
+      if (j < (int)tiles &&
+          tile_hits_spec(tc, so.x0, so.x1, so.y0, so.y1, tx0 + jx, ty0 + jy, b.tile))
+        t = (unsigned)(tbase + jy * cam.tiles_x + jx);
       if (++jx == tw) { jx = 0; ++jy; }
       const unsigned peers = __match_any_sync(lanes, t);
       if (t != 0xFFFFFFFFu && (threadIdx.x & 31) == __ffs(peers) - 1)

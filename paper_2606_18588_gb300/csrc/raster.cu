@@ -82,12 +82,15 @@ __device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
 
 }  // namespace
 
-template <int TS, int PPT>
-__global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) {
+// kCount variants (eager runs only) also count the work for the roofline: thread-entries
+// examined, (pixel, entry) alpha evaluations and blends / contributions.
+constexpr int kNB = 256;  // list entries staged in shared memory per batch
+
+template <int TS, int PPT, bool kCount>
+__device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, float4* sA,
+                                         float4* sB, float4* sC) {
   constexpr int NTH = TS * TS / PPT;
-  constexpr int NB = 256;  // entries staged per batch
-  __shared__ float4 sA[NB], sB[NB], sC[NB];
-  const int64_t id = blockIdx.x;
+  constexpr int NB = kNB;
   const TileInfo ti = decode_tile<TS, PPT>(b, id);
   const uint2 rg = b.ranges[id];
   const int64_t start = rg.x, end = rg.y > rg.x ? rg.y : rg.x;
@@ -102,7 +105,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) 
     T[i] = 1.0f; c0[i] = c1[i] = c2[i] = D[i] = 0.0f; last[i] = -1;
     if (ti.px < ti.W && ti.py0 + i < ti.H) live |= 1u << i;
   }
-  unsigned n_eval = 0, n_blend = 0;
+  unsigned n_eval = 0, n_pix = 0, n_blend = 0;
   for (int64_t base = start; base < end; base += NB) {
     if (__syncthreads_count(live == 0) == NTH) break;
 #pragma unroll
@@ -135,6 +138,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) 
         for (int i = 0; i < PPT; ++i) {
           const int py = ti.py0 + i;
           if (!((live >> i) & 1u) || py < y0 || py > y1) continue;
+          if (kCount) ++n_pix;
           float alpha, ex, dy;
           bool cl;
           if (!pixel_alpha(ct, Av.y, Bv.x, Bv.y, (float)py + 0.5f, amin, amax, alpha, ex, dy, cl))
@@ -148,14 +152,17 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) 
           D[i] = fmaf(Bv.z, w, D[i]);
           T[i] = Tn;
           last[i] = (int)(base - start) + jj;
-          ++n_blend;
+          if (kCount) ++n_blend;
         }
       }
-      n_eval += (unsigned)jj;
+      if (kCount) n_eval += (unsigned)jj;
     }
   }
-  flush_counter(b.counters, 0, n_eval);
-  flush_counter(b.counters, 1, n_blend);
+  if (kCount) {
+    flush_counter(b.counters, 0, n_eval);
+    flush_counter(b.counters, 1, n_pix);
+    flush_counter(b.counters, 2, n_blend);
+  }
   const ImgDev im = b.imgs[ti.v * b.K + ti.k];
   const int64_t HW = (int64_t)ti.W * ti.H;
 #pragma unroll
@@ -171,14 +178,11 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) 
   }
 }
 
-template <int TS, int PPT>
-__global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const BatchDev b) {
+template <int TS, int PPT, bool kCount>
+__device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, float4* sA,
+                                         float4* sB, float4* sC, uint32_t* sG, int& s_maxlast) {
   constexpr int NTH = TS * TS / PPT;
-  constexpr int NB = 256;
-  __shared__ float4 sA[NB], sB[NB], sC[NB];
-  __shared__ uint32_t sG[NB];
-  __shared__ int s_maxlast;
-  const int64_t id = blockIdx.x;
+  constexpr int NB = kNB;
   const TileInfo ti = decode_tile<TS, PPT>(b, id);
   const uint2 rg = b.ranges[id];
   const int64_t start = rg.x;
@@ -216,7 +220,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const BatchDev b) 
   const float pcx = (float)ti.px + 0.5f;
   const float amin = b.alpha_min, amax = b.alpha_max;
   const int lane = threadIdx.x & 31;
-  unsigned n_evalb = 0;
+  unsigned n_evalb = 0, n_pixb = 0, n_actb = 0;
 
   for (int top = maxlast; top >= 0; top -= NB) {
     const int lo = top - NB + 1 > 0 ? top - NB + 1 : 0;
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const BatchDev b) 
     }
     __syncthreads();
     const int cnt = top - lo + 1;
-    if (tlast >= lo) n_evalb += (unsigned)((tlast < top ? tlast : top) - lo + 1);
+    if (kCount && tlast >= lo) n_evalb += (unsigned)((tlast < top ? tlast : top) - lo + 1);
     for (int jj = 0; jj < cnt; ++jj) {
       const int j = top - jj;
       float gu = 0.f, gv = 0.f, gA = 0.f, gB = 0.f, gC = 0.f, go = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
@@ -257,10 +261,12 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const BatchDev b) 
           for (int i = 0; i < PPT; ++i) {
             const int py = ti.py0 + i;
             if (j > mylast[i] || py < y0 || py > y1) continue;
+            if (kCount) ++n_pixb;
             float alpha, ex, dy;
             bool cl;
             if (!pixel_alpha(ct, Av.y, Bv.x, Bv.y, (float)py + 0.5f, amin, amax, alpha, ex, dy, cl))
               continue;
+            if (kCount) ++n_actb;
             act = true;
             const float rinv = 1.0f / (1.0f - alpha);
             const float Ti = T[i] * rinv;
@@ -320,7 +326,51 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const BatchDev b) 
       }
     }
   }
-  flush_counter(b.counters, 2, n_evalb);
+  if (kCount) {
+    flush_counter(b.counters, 3, n_evalb);
+    flush_counter(b.counters, 4, n_pixb);
+    flush_counter(b.counters, 5, n_actb);
+  }
+}
+
+// One CTA per work item, or (kPersist) a grid sized to the SMs whose CTAs take work items
+// in order from a device counter until none is left.
+template <int TS, int PPT, bool kCount, bool kPersist>
+__global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) {
+  __shared__ float4 sA[kNB], sB[kNB], sC[kNB];
+  if constexpr (!kPersist) {
+    fwd_item<TS, PPT, kCount>(b, blockIdx.x, sA, sB, sC);
+  } else {
+    __shared__ long long s_id;
+    for (;;) {
+      __syncthreads();  // the previous item is done with shared memory and s_id
+      if (threadIdx.x == 0) s_id = (long long)atomicAdd(b.work_ctr, 1ull);
+      __syncthreads();
+      const int64_t id = s_id;
+      if (id >= b.n_tiles) return;
+      fwd_item<TS, PPT, kCount>(b, id, sA, sB, sC);
+    }
+  }
+}
+
+template <int TS, int PPT, bool kCount, bool kPersist>
+__global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const BatchDev b) {
+  __shared__ float4 sA[kNB], sB[kNB], sC[kNB];
+  __shared__ uint32_t sG[kNB];
+  __shared__ int s_maxlast;
+  if constexpr (!kPersist) {
+    bwd_item<TS, PPT, kCount>(b, blockIdx.x, sA, sB, sC, sG, s_maxlast);
+  } else {
+    __shared__ long long s_id;
+    for (;;) {
+      __syncthreads();
+      if (threadIdx.x == 0) s_id = (long long)atomicAdd(b.work_ctr + 1, 1ull);
+      __syncthreads();
+      const int64_t id = s_id;
+      if (id >= b.n_tiles) return;
+      bwd_item<TS, PPT, kCount>(b, id, sA, sB, sC, sG, s_maxlast);
+    }
+  }
 }
 
 // Tile side -> pixels per thread: 8x8 tiles use 2 (32 threads), 16x16 and 32x32 use 4.
@@ -329,15 +379,59 @@ struct Ppt {
   static constexpr int value = TS == 8 ? 2 : 4;
 };
 
+// Work is counted only by eager runs with a counter buffer: a captured graph launches the
+// plain variants, so replays carry no counting instructions (and keep the eager counts).
+static bool counting(const BatchDev& b, cudaStream_t s) {
+  return b.counters && !stream_capturing(s);
+}
+
+template <int TS, bool kCount, bool kPersist>
+static void launch_fwd_k(const BatchDev& b, cudaStream_t s) {
+  constexpr int P = Ppt<TS>::value;
+  const unsigned grid = kPersist ? (unsigned)std::min<int64_t>(b.n_tiles, (int64_t)b.persist_grid)
+                                 : (unsigned)b.n_tiles;
+  k_raster_fwd<TS, P, kCount, kPersist><<<grid, TS * TS / P, 0, s>>>(b);
+}
+template <int TS, bool kCount, bool kPersist>
+static void launch_bwd_k(const BatchDev& b, cudaStream_t s) {
+  constexpr int P = Ppt<TS>::value;
+  const unsigned grid = kPersist ? (unsigned)std::min<int64_t>(b.n_tiles, (int64_t)b.persist_grid)
+                                 : (unsigned)b.n_tiles;
+  k_raster_bwd<TS, P, kCount, kPersist><<<grid, TS * TS / P, 0, s>>>(b);
+}
 template <int TS>
 static void launch_fwd_t(const BatchDev& b, cudaStream_t s) {
-  constexpr int P = Ppt<TS>::value;
-  k_raster_fwd<TS, P><<<(unsigned)b.n_tiles, TS * TS / P, 0, s>>>(b);
+  const bool c = counting(b, s), p = b.persist_grid > 0 && b.work_ctr;
+  if (p) cudaMemsetAsync(b.work_ctr, 0, sizeof(unsigned long long), s);
+  if (c) { if (p) launch_fwd_k<TS, true, true>(b, s); else launch_fwd_k<TS, true, false>(b, s); }
+  else   { if (p) launch_fwd_k<TS, false, true>(b, s); else launch_fwd_k<TS, false, false>(b, s); }
 }
 template <int TS>
 static void launch_bwd_t(const BatchDev& b, cudaStream_t s) {
+  const bool c = counting(b, s), p = b.persist_grid > 0 && b.work_ctr;
+  if (p) cudaMemsetAsync(b.work_ctr + 1, 0, sizeof(unsigned long long), s);
+  if (c) { if (p) launch_bwd_k<TS, true, true>(b, s); else launch_bwd_k<TS, true, false>(b, s); }
+  else   { if (p) launch_bwd_k<TS, false, true>(b, s); else launch_bwd_k<TS, false, false>(b, s); }
+}
+
+template <int TS>
+static int max_ctas_t(bool bwd) {
   constexpr int P = Ppt<TS>::value;
-  k_raster_bwd<TS, P><<<(unsigned)b.n_tiles, TS * TS / P, 0, s>>>(b);
+  int n = 0;
+  cudaError_t e =
+      bwd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_bwd<TS, P, false, true>,
+                                                          TS * TS / P, 0)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd<TS, P, false, true>,
+                                                          TS * TS / P, 0);
+  return e == cudaSuccess ? n : 0;
+}
+
+int raster_max_ctas_per_sm(int tile, bool bwd) {
+  switch (tile) {
+    case 8: return max_ctas_t<8>(bwd);
+    case 32: return max_ctas_t<32>(bwd);
+    default: return max_ctas_t<16>(bwd);
+  }
 }
 
 void launch_raster_fwd(const BatchDev& b, cudaStream_t s) {

@@ -135,4 +135,85 @@ __device__ __forceinline__ SpecOut bin_spec(const float m[3], const float ls[3],
   return o;
 }
 
+// Conic of the dilated Sigma2D and opacity in the specification's arithmetic.
+__device__ __forceinline__ void spec_conic(const SpecOut& so, float& A, float& B, float& C) {
+  A = fd(so.c, so.det);
+  B = -fd(so.b, so.det);
+  C = fd(so.a, so.det);
+}
+__device__ __forceinline__ float spec_opacity(float logit) {
+  return fd(1.0f, fa(1.0f, exp_spec(-logit)));
+}
+
+// Natural logarithm of x >= 1 from basic operations only: x = m 2^e with m in
+// [sqrt(1/2), sqrt(2)), ln m = 2 atanh(s), s = (m - 1)/(m + 1), by its odd series through
+// s^9, and ln 2 split as in exp_spec.
+__device__ __forceinline__ float log_spec(float x) {
+  uint32_t bits = __float_as_uint(x);
+  int e = (int)(bits >> 23) - 127;
+  float m = __uint_as_float((bits & 0x7FFFFFu) | 0x3F800000u);
+  if (m > 1.41421354f) { m = fm(m, 0.5f); e += 1; }
+  const float s = fd(fs(m, 1.0f), fa(m, 1.0f));
+  const float s2 = fm(s, s);
+  float p = 0.222222222f;
+  p = fa(fm(p, s2), 0.285714287f);
+  p = fa(fm(p, s2), 0.400000006f);
+  p = fa(fm(p, s2), 0.666666687f);
+  p = fa(fm(p, s2), 2.0f);
+  const float fe = (float)e;
+  return fa(fm(fe, 0.693359375f), fa(fm(s, p), fm(fe, -2.12194440e-4f)));
+}
+
+// Tile culling, part of the binning specification.  A (Gaussian, tile) pair is listed
+// only if the conic's quadratic form q = A x^2 + 2B xy + C y^2 (offsets from the mean)
+// reaches q_max = 2 ln(o / (0.999 alpha_min)) on the box spanned by the pixel centres the
+// Gaussian's rectangle [x0,x1]x[y0,y1] shares with the tile, i.e. only if alpha can reach
+// 0.999 alpha_min there; the 0.1% margin makes every culled pair one that the per-pixel
+// alpha >= alpha_min test rejects at every pixel.  The minimum of the convex q over the
+// box is 0 if the mean lies inside, else it lies on an edge whose outer side holds the
+// mean, at the clamped stationary point of that edge.  q_max < 0 marks a Gaussian with
+// o < 0.999 alpha_min, which reaches no tile.
+struct TileCull {
+  float u, v, A, B, C, qmax, rBC, rBA;
+};
+
+__device__ __forceinline__ float tile_cull_qmax(float o, float amin) {
+  const float thr = fm(amin, 0.999f);
+  if (!(o >= thr)) return -1.0f;
+  return fm(2.0f, log_spec(fd(o, thr)));
+}
+
+__device__ __forceinline__ TileCull tile_cull_prep(float u, float v, float A, float B, float C,
+                                                   float qmax) {
+  TileCull t;
+  t.u = u; t.v = v; t.A = A; t.B = B; t.C = C; t.qmax = qmax;
+  t.rBC = fd(B, C);
+  t.rBA = fd(B, A);
+  return t;
+}
+
+__device__ __forceinline__ bool tile_hits_spec(const TileCull& t, int x0, int x1, int y0, int y1,
+                                               int tx, int ty, int T) {
+  if (!(t.qmax >= 0.0f)) return false;
+  const int px0 = max(tx * T, x0), px1 = min(tx * T + T - 1, x1);
+  const int py0 = max(ty * T, y0), py1 = min(ty * T + T - 1, y1);
+  const float xa = fs(fa((float)px0, 0.5f), t.u), xb = fs(fa((float)px1, 0.5f), t.u);
+  const float ya = fs(fa((float)py0, 0.5f), t.v), yb = fs(fa((float)py1, 0.5f), t.v);
+  const bool xout = xa > 0.0f || xb < 0.0f, yout = ya > 0.0f || yb < 0.0f;
+  if (!xout && !yout) return true;  // q = 0 at the mean
+  const float twoB = fm(2.0f, t.B);
+  float q = __int_as_float(0x7f800000);
+  if (xout) {
+    const float x = xa > 0.0f ? xa : xb;
+    const float y = fminf(fmaxf(-fm(t.rBC, x), ya), yb);
+    q = fa(fa(fm(fm(t.A, x), x), fm(fm(twoB, x), y)), fm(fm(t.C, y), y));
+  }
+  if (yout) {
+    const float y = ya > 0.0f ? ya : yb;
+    const float x = fminf(fmaxf(-fm(t.rBA, y), xa), xb);
+    q = fminf(q, fa(fa(fm(fm(t.A, x), x), fm(fm(twoB, x), y)), fm(fm(t.C, y), y)));
+  }
+  return q <= t.qmax;
+}
+
 }  // namespace splx

@@ -133,11 +133,10 @@ def cluster_scene(n: int, seed: int, sh_degree: int = 3, n_clusters: int = 64,
     sig = rng.uniform(sigma_range[0], sigma_range[1], n_clusters)
     lab = rng.integers(0, n_clusters, n)
     means = centres[lab] + sig[lab, None] * rng.standard_normal((n, 3))
-    bad = np.any(np.abs(means) > half, axis=1)
-    while bad.any():
-        k = int(bad.sum())
-        means[bad] = centres[lab[bad]] + sig[lab[bad], None] * rng.standard_normal((k, 3))
-        bad = np.any(np.abs(means) > half, axis=1)
+    bad = np.nonzero(np.any(np.abs(means) > half, axis=1))[0]  # ascending indices
+    while bad.size:
+        means[bad] = centres[lab[bad]] + sig[lab[bad], None] * rng.standard_normal((bad.size, 3))
+        bad = bad[np.any(np.abs(means[bad]) > half, axis=1)]
     means = means.astype(np.float32)
     mu = math.log(0.33 * (box ** 3 / n) ** (1.0 / 3.0))
     log_scales = rng.normal(mu, log_scale_sigma, (n, 3)).astype(np.float32)
@@ -181,7 +180,8 @@ def kd_partition(means: np.ndarray, K: int, axes=(0, 2), spatial_order: bool = T
         for idx, lo, hi in groups:
             ext = [m[idx, a].max() - m[idx, a].min() if idx.size else 0.0 for a in axes]
             ax = axes[int(np.argmax(ext))]
-            order = np.lexsort((idx, m[idx, ax]))
+            # idx is ascending, so a stable sort by coordinate orders by (coordinate, index)
+            order = np.argsort(m[idx, ax], kind="stable")
             idx = idx[order]
             h = idx.size // 2
             left, right = idx[:h], idx[h:]

@@ -90,6 +90,15 @@ _sigs = {
     "splx_batch_set_timing": (C.c_int, [_P, C.c_int]),
     "splx_batch_kernel_times": (C.c_int, [_P, _P]),
     "splx_batch_counters": (C.c_int, [_P, _P, _P]),
+    "splx_batch_set_launch": (C.c_int, [_P, C.c_int32]),
+    "splx_batch_max_ctas_per_sm": (C.c_int, [_P, _P, _P]),
+    "splx_server_create": (C.c_int, [_P, _P, C.c_int32, _P, C.c_size_t, C.c_int32, C.c_int32,
+                                     C.POINTER(_P)]),
+    "splx_server_submit": (C.c_int, [_P, _P, _P, C.POINTER(C.c_int64)]),
+    "splx_server_poll": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(C.c_int32)]),
+    "splx_server_stats": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_size_t)]),
+    "splx_server_destroy": (C.c_int, [_P]),
     "splx_graph_begin": (C.c_int, [_P, _P]),
     "splx_graph_end": (C.c_int, [_P, _P, C.POINTER(_P)]),
     "splx_graph_launch": (C.c_int, [_P, _P]),
@@ -316,6 +325,67 @@ def loss_l1(ctx: Context, img, target, loss_out, dL_dimg=None, stream=None):
 
 
 # ---------------------------------------------------------------- batched path
+class Server:
+    """Render server over K resident subsets: continuous batching of camera requests
+    of any resolution, admission by an HBM budget, launches overlapping on `slots`
+    streams.  submit() takes the device output tensor [3,H,W]; poll() returns the
+    (id, status) pairs finished since the last call."""
+
+    def __init__(self, ctx: Context, subsets, o: Opts, hbm_budget_bytes: int, slots: int = 4,
+                 max_views: int = 8):
+        self.ctx = ctx
+        self.K = len(subsets)
+        self._subsets = (Gaussians * self.K)(*subsets)
+        h = C.c_void_p()
+        _check(_lib.splx_server_create(ctx.h, self._subsets, self.K, C.byref(o),
+                                       int(hbm_budget_bytes), int(slots), int(max_views),
+                                       C.byref(h)), "splx_server_create")
+        self.h = h
+        self._outs = {}  # id -> output tensor, kept alive until the request finishes
+        self._ids = (C.c_int64 * 256)()
+        self._st = (C.c_int32 * 256)()
+
+    def submit(self, cam, out_rgb) -> int:
+        c = cam if isinstance(cam, Camera) else camera(cam)
+        if tuple(out_rgb.shape) != (3, c.height, c.width):
+            raise ValueError("out_rgb must be [3, H, W]")
+        rid = C.c_int64()
+        _check(_lib.splx_server_submit(self.h, C.byref(c), _ptr(out_rgb), C.byref(rid)),
+               "splx_server_submit")
+        self._outs[rid.value] = out_rgb
+        return rid.value
+
+    def poll(self):
+        done = []
+        while True:
+            n = C.c_int32()
+            _check(_lib.splx_server_poll(self.h, self._ids, self._st, 256, C.byref(n)),
+                   "splx_server_poll")
+            for i in range(n.value):
+                self._outs.pop(self._ids[i], None)
+                done.append((self._ids[i], self._st[i]))
+            if n.value < 256:
+                return done
+
+    def stats(self):
+        q, f, r = C.c_int32(), C.c_int32(), C.c_size_t()
+        _check(_lib.splx_server_stats(self.h, C.byref(q), C.byref(f), C.byref(r)),
+               "splx_server_stats")
+        return {"queued": q.value, "inflight": f.value, "reserved_bytes": r.value}
+
+    def close(self):
+        if self.h:
+            _lib.splx_server_destroy(self.h)
+            self.h = None
+            self._outs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Batch:
     """A planned batch of V views x K subsets (persistent scratch, capturable runs)."""
 
@@ -370,10 +440,21 @@ class Batch:
         _check(_lib.splx_batch_kernel_times(self.h, arr), "splx_batch_kernel_times")
         return dict(zip(self.KERNELS, [float(x) for x in arr]))
 
+    def set_launch(self, raster_ctas_per_sm: int):
+        """0: one rasteriser CTA per work item; n > 0: n persistent CTAs per SM."""
+        _check(_lib.splx_batch_set_launch(self.h, int(raster_ctas_per_sm)), "splx_batch_set_launch")
+
+    def max_ctas_per_sm(self) -> tuple[int, int]:
+        f, b = C.c_int32(0), C.c_int32(0)
+        _check(_lib.splx_batch_max_ctas_per_sm(self.h, C.byref(f), C.byref(b)),
+               "splx_batch_max_ctas_per_sm")
+        return f.value, b.value
+
     def counters(self, stream=None) -> dict:
-        arr = (C.c_int64 * 4)()
+        arr = (C.c_int64 * 7)()
         _check(_lib.splx_batch_counters(self.h, arr, _stream(stream)), "splx_batch_counters")
-        return dict(pairs=arr[0], evaluated_fwd=arr[1], blended=arr[2], evaluated_bwd=arr[3])
+        return dict(pairs=arr[0], entries_fwd=arr[1], alpha_fwd=arr[2], blended=arr[3],
+                    entries_bwd=arr[4], alpha_bwd=arr[5], contrib_bwd=arr[6])
 
     def views(self, flat_rgb):
         """Split a concatenated rgb buffer into per-view [3,H,W] tensors."""

@@ -133,3 +133,55 @@ def test_hbm_budget_is_enforced(ctx):
     assert e.value.code == S.ERR_BUDGET
     assert small.scratch_bytes == 0
     small.close()
+
+
+def test_persistent_launch_shapes_agree(ctx, scene):
+    # every (tile side, CTAs per SM) launch shape renders the same image bit for bit and
+    # the same gradients up to the summation order of the atomics
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import rel_l2, to_device, zeros_like_params
+    sc, off, cams = scene
+    dev = to_device(sc)
+    rng = np.random.default_rng(1)
+    ref_rgb = ref_g = None
+    for tile in (8, 16, 32):
+        b = S.Batch(ctx, _subsets(dev, off, sc.sh_degree), cams, S.opts(tile=tile))
+        fmax, bmax = b.max_ctas_per_sm()
+        assert fmax >= 1 and bmax >= 1
+        if ref_rgb is None:
+            dL = torch.from_numpy(rng.standard_normal(b.rgb_off[-1]).astype(np.float32)).cuda()
+        for c in (0, 1, 3, min(fmax, bmax)):
+            b.set_launch(c)
+            rgb = torch.empty(b.rgb_off[-1], device="cuda")
+            b.forward(rgb)
+            g = zeros_like_params(dev)
+            b.backward(dL, None, _grads(g, off, sc.sh_degree))
+            torch.cuda.synchronize()
+            code, _ = b.status()
+            assert code == S.OK
+            if ref_rgb is None:
+                ref_rgb, ref_g = rgb, g
+                continue
+            assert torch.equal(rgb, ref_rgb), (tile, c)
+            for k in GROUPS:
+                assert rel_l2(g[k].cpu().numpy(), ref_g[k].cpu().numpy()) < 1e-5, (tile, c, k)
+        with pytest.raises(S.SplxError):
+            b.set_launch(-1)
+        b.close()
+
+
+def test_autotuner_picks_a_timed_candidate(ctx, scene):
+    from paper_2606_18588_gb300 import splx as S
+    from paper_2606_18588_gb300.autotune import autotune
+    from gpu_util import to_device
+    sc, off, cams = scene
+    dev = to_device(sc)
+    npx = sum(3 * c.width * c.height for c in cams)
+    target = torch.rand(npx, device="cuda")
+    before = {k: v.clone() for k, v in dev.items()}
+    r = autotune(ctx, dev, off, sc.sh_degree, cams, target, tiles=(8, 16), ctas=(0, 2), reps=2)
+    assert len(r.table) == 4
+    assert (r.tile, r.ctas_per_sm, r.ms) in [tuple(t) for t in r.table]
+    assert r.ms == min(t[2] for t in r.table)
+    for k in dev:  # the tuner never updates the parameters
+        assert torch.equal(dev[k], before[k])
