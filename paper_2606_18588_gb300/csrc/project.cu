@@ -56,7 +56,7 @@ __device__ __forceinline__ void sh_eval(float x, float y, float z, float* Y) {
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(256) k_project(const BatchDev b) {
+__global__ void __launch_bounds__(256, 4) k_project(const BatchDev b) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned lanes = __ballot_sync(0xffffffffu, g < b.N);  // lanes in the warp collectives
   if (g >= b.N) return;
@@ -76,9 +76,10 @@ __global__ void __launch_bounds__(256) k_project(const BatchDev b) {
   // the tile test's threshold on the conic's quadratic form (view independent)
   const float qmax = tile_cull_qmax(spec_opacity(logit), b.alpha_min);
   constexpr int NC = (DEG + 1) * (DEG + 1);
-  float sh[NC * 3];
-#pragma unroll
-  for (int e = 0; e < NC * 3; ++e) sh[e] = __ldg(S.sh + i * NC * 3 + e);
+  // SH coefficients are read per visible view (L1/L2-resident across the view loop)
+  // rather than held in registers, which keeps the kernel's occupancy up
+  const float* shp = S.sh + i * (NC * 3);
+  const bool sh_vec = (NC * 3) % 4 == 0 && (reinterpret_cast<uintptr_t>(shp) & 15) == 0;
 
   for (int v = 0; v < b.V; ++v) {
     const ViewDev& cam = b.views[v];
@@ -98,14 +99,25 @@ __global__ void __launch_bounds__(256) k_project(const BatchDev b) {
       dx *= rn; dy *= rn; dz *= rn;
       float Y[NC];
       sh_eval<DEG>(dx, dy, dz, Y);
-      float col[3];
+      // colour = SH(direction) + 0.5 per channel, coefficients summed in degree order
+      float acc[3] = {0.5f, 0.5f, 0.5f};
+      if (sh_vec) {
+        const float4* s4 = reinterpret_cast<const float4*>(shp);
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        float acc = 0.5f;
+        for (int q4 = 0; q4 < (NC * 3) / 4; ++q4) {
+          const float4 sv = __ldg(s4 + q4);
+          const float vals[4] = {sv.x, sv.y, sv.z, sv.w};
 #pragma unroll
-        for (int kk = 0; kk < NC; ++kk) acc = fmaf(Y[kk], sh[3 * kk + ch], acc);
-        col[ch] = fmaxf(acc, 0.0f);
+          for (int c = 0; c < 4; ++c) {
+            const int e = 4 * q4 + c;
+            acc[e % 3] = fmaf(Y[e / 3], vals[c], acc[e % 3]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < NC * 3; ++e) acc[e % 3] = fmaf(Y[e / 3], __ldg(shp + e), acc[e % 3]);
       }
+      const float col[3] = {fmaxf(acc[0], 0.0f), fmaxf(acc[1], 0.0f), fmaxf(acc[2], 0.0f)};
       const uint32_t rx = (uint32_t)so.x0 | ((uint32_t)so.x1 << 16);
       const uint32_t ry = (uint32_t)so.y0 | ((uint32_t)so.y1 << 16);
       r.b = make_float4(-0.5f * kLog2e * Cc, opac, so.tz, __uint_as_float(rx));

@@ -36,6 +36,19 @@ __device__ __forceinline__ ColTerms col_terms(const float4 a, float pcx) {
   return c;
 }
 
+// 2^x and 1/x as single special-function-unit instructions (relative error about 2^-22;
+// subnormal results flush to zero, which the alpha threshold rejects anyway).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // alpha of an entry at one pixel of the column; the same code runs in the forward and
 // the backward so both take bit-identical decisions.  Returns false if skipped.
 __device__ __forceinline__ bool pixel_alpha(const ColTerms& c, float ay, float qc, float o,
@@ -44,7 +57,7 @@ __device__ __forceinline__ bool pixel_alpha(const ColTerms& c, float ay, float q
   dy = __fsub_rn(pcy, ay);
   const float p2 = __fmaf_rn(__fmaf_rn(qc, dy, c.bx), dy, c.hx);
   if (p2 > 0.0f) return false;
-  ex = exp2f(p2);
+  ex = ex2_approx(p2);
   const float raw = __fmul_rn(o, ex);
   clamped = raw > amax;
   alpha = clamped ? amax : raw;
@@ -59,9 +72,50 @@ __device__ __forceinline__ void flush_counter(unsigned long long* counters, int 
   if ((threadIdx.x & 31) == 0 && v) atomicAdd(counters + slot, (unsigned long long)v);
 }
 
+// Sum of v[0..8] over the warp by reduce-scatter: each exchange sends half of the
+// values a lane still holds, so 8 values take 4 + 2 + 1 + 1 + 1 shuffles instead of
+// 8 x 5.  Afterwards lane l holds the full sum of value (l >> 2) & 7 in `mine`, and
+// every lane holds the sum of value 8 in `v8`.
+__device__ __forceinline__ void warp_reduce9(const float (&v)[9], int lane, float& mine,
+                                             float& v8) {
+  const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0, h2 = (lane & 4) != 0;
+  float a[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float send = h4 ? v[k] : v[k + 4];
+    const float keep = h4 ? v[k + 4] : v[k];
+    a[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float c[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = h3 ? a[k] : a[k + 2];
+    const float keep = h3 ? a[k + 2] : a[k];
+    c[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float d = (h2 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, h2 ? c[0] : c[1], 4);
+  d += __shfl_xor_sync(0xffffffffu, d, 2);
+  d += __shfl_xor_sync(0xffffffffu, d, 1);
+  mine = d;
+  float e = v[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  v8 = e;
+}
+
+// Pixels of a thread: slot i of PPT is an 8 x 4 block of the tile, lanes laid out as
+// 8 columns x 4 rows inside it; a warp's PPT blocks tile a 16 x 8 region (8 x 8 for
+// 8 x 8 tiles).  A Gaussian's footprint then meets few blocks, and a block it meets
+// keeps many lanes busy.  (x, y) is the thread's pixel in slot 0; slot i adds
+// (8 (i & 1), 4 (i >> 1)) for PPT = 4 and (0, 4 i) for PPT = 2.
 struct TileInfo {
-  int v, k, px, py0, W, H;
+  int v, k, x, y, W, H;
 };
+
+template <int PPT>
+__device__ __forceinline__ int slot_col(int i) { return PPT == 4 ? (i & 1) : 0; }
+template <int PPT>
+__device__ __forceinline__ int slot_row(int i) { return PPT == 4 ? (i >> 1) : i; }
 
 template <int TS, int PPT>
 __device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
@@ -73,8 +127,15 @@ __device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
   ti.k = (int)(rem / nt);
   const int64_t t = rem - (int64_t)ti.k * nt;
   const int tx = (int)(t % cam.tiles_x), ty = (int)(t / cam.tiles_x);
-  ti.px = tx * TS + (int)(threadIdx.x % TS);
-  ti.py0 = ty * TS + (int)(threadIdx.x / TS) * PPT;
+  const int w = (int)(threadIdx.x >> 5), l = (int)(threadIdx.x & 31);
+  int rx0 = 0, ry0 = 0;
+  if (PPT == 4) {
+    constexpr int kRegionsPerRow = TS / 16;
+    rx0 = 16 * (w % kRegionsPerRow);
+    ry0 = 8 * (w / kRegionsPerRow);
+  }
+  ti.x = tx * TS + rx0 + (l & 7);
+  ti.y = ty * TS + ry0 + (l >> 3);
   ti.W = cam.W;
   ti.H = cam.H;
   return ti;
@@ -95,7 +156,7 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
   const uint2 rg = b.ranges[id];
   const int64_t start = rg.x, end = rg.y > rg.x ? rg.y : rg.x;
   const Rec* rec = b.rec + (int64_t)ti.v * b.N;
-  const float pcx = (float)ti.px + 0.5f;
+  const float pcx0 = (float)ti.x + 0.5f, pcx1 = (float)(ti.x + 8) + 0.5f;
   const float amin = b.alpha_min, amax = b.alpha_max, epsT = b.eps_T;
   float T[PPT], c0[PPT], c1[PPT], c2[PPT], D[PPT];
   int last[PPT];
@@ -103,7 +164,7 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
 #pragma unroll
   for (int i = 0; i < PPT; ++i) {
     T[i] = 1.0f; c0[i] = c1[i] = c2[i] = D[i] = 0.0f; last[i] = -1;
-    if (ti.px < ti.W && ti.py0 + i < ti.H) live |= 1u << i;
+    if (ti.x + 8 * slot_col<PPT>(i) < ti.W && ti.y + 4 * slot_row<PPT>(i) < ti.H) live |= 1u << i;
   }
   unsigned n_eval = 0, n_pix = 0, n_blend = 0;
   for (int64_t base = start; base < end; base += NB) {
@@ -131,17 +192,21 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
         const uint32_t rx = __float_as_uint(Bv.w), ry = __float_as_uint(Cv.w);
         const int x0 = (int)(rx & 0xFFFFu), x1 = (int)(rx >> 16);
         const int y0 = (int)(ry & 0xFFFFu), y1 = (int)(ry >> 16);
-        if (ti.px < x0 || ti.px > x1 || ti.py0 + PPT - 1 < y0 || ti.py0 > y1) continue;
+        const bool cA = ti.x >= x0 && ti.x <= x1;
+        const bool cB = PPT == 4 && ti.x + 8 >= x0 && ti.x + 8 <= x1;
+        const bool rA = ti.y >= y0 && ti.y <= y1, rB = ti.y + 4 >= y0 && ti.y + 4 <= y1;
+        if (!(cA || cB) || !(rA || rB)) continue;
         const float4 Av = sA[jj];
-        const ColTerms ct = col_terms(Av, pcx);
+        const ColTerms ct0 = col_terms(Av, pcx0), ct1 = col_terms(Av, pcx1);
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
-          const int py = ti.py0 + i;
-          if (!((live >> i) & 1u) || py < y0 || py > y1) continue;
+          const int ci = slot_col<PPT>(i), ri = slot_row<PPT>(i);
+          if (!((live >> i) & 1u) || !(ci ? cB : cA) || !(ri ? rB : rA)) continue;
           if (kCount) ++n_pix;
           float alpha, ex, dy;
           bool cl;
-          if (!pixel_alpha(ct, Av.y, Bv.x, Bv.y, (float)py + 0.5f, amin, amax, alpha, ex, dy, cl))
+          if (!pixel_alpha(ci ? ct1 : ct0, Av.y, Bv.x, Bv.y, (float)(ti.y + 4 * ri) + 0.5f, amin,
+                           amax, alpha, ex, dy, cl))
             continue;
           const float Tn = T[i] * (1.0f - alpha);
           if (Tn < epsT) { live &= ~(1u << i); continue; }
@@ -167,8 +232,9 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
   const int64_t HW = (int64_t)ti.W * ti.H;
 #pragma unroll
   for (int i = 0; i < PPT; ++i) {
-    if (ti.px >= ti.W || ti.py0 + i >= ti.H) continue;
-    const int64_t p = (int64_t)(ti.py0 + i) * ti.W + ti.px;
+    const int px = ti.x + 8 * slot_col<PPT>(i), py = ti.y + 4 * slot_row<PPT>(i);
+    if (px >= ti.W || py >= ti.H) continue;
+    const int64_t p = (int64_t)py * ti.W + px;
     im.rgb[p] = c0[i];
     im.rgb[HW + p] = c1[i];
     im.rgb[2 * HW + p] = c2[i];
@@ -197,8 +263,9 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
     T[i] = 1.0f;
     mylast[i] = -1;
     B0[i] = B1[i] = B2[i] = 0.0f;
-    if (ti.px < ti.W && ti.py0 + i < ti.H) {
-      const int64_t p = (int64_t)(ti.py0 + i) * ti.W + ti.px;
+    const int px = ti.x + 8 * slot_col<PPT>(i), py = ti.y + 4 * slot_row<PPT>(i);
+    if (px < ti.W && py < ti.H) {
+      const int64_t p = (int64_t)py * ti.W + px;
       gct[i] = im.gCT[p];
       T[i] = im.T[p];
       mylast[i] = im.last[p];
@@ -217,7 +284,7 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
 
   const Rec* rec = b.rec + (int64_t)ti.v * b.N;
   float4* g2 = b.grad2d + (int64_t)ti.v * b.N * 3;
-  const float pcx = (float)ti.px + 0.5f;
+  const float pcx0 = (float)ti.x + 0.5f, pcx1 = (float)(ti.x + 8) + 0.5f;
   const float amin = b.alpha_min, amax = b.alpha_max;
   const int lane = threadIdx.x & 31;
   unsigned n_evalb = 0, n_pixb = 0, n_actb = 0;
@@ -252,23 +319,28 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
         const uint32_t rx = __float_as_uint(Bv.w), ry = __float_as_uint(Cv.w);
         const int x0 = (int)(rx & 0xFFFFu), x1 = (int)(rx >> 16);
         const int y0 = (int)(ry & 0xFFFFu), y1 = (int)(ry >> 16);
-        if (ti.px >= x0 && ti.px <= x1 && ti.py0 + PPT - 1 >= y0 && ti.py0 <= y1) {
+        const bool cA = ti.x >= x0 && ti.x <= x1;
+        const bool cB = PPT == 4 && ti.x + 8 >= x0 && ti.x + 8 <= x1;
+        const bool rA = ti.y >= y0 && ti.y <= y1, rB = ti.y + 4 >= y0 && ti.y + 4 <= y1;
+        if ((cA || cB) && (rA || rB)) {
           const float4 Av = sA[jj];
-          const ColTerms ct = col_terms(Av, pcx);
+          const ColTerms ct0 = col_terms(Av, pcx0), ct1 = col_terms(Av, pcx1);
           // conic (A, B, C) recovered from the scaled record: A = -2 ln2 qa, B = -ln2 qb, C = -2 ln2 qc
           const float A_ = -2.0f * kLn2 * Av.z, Bc = -kLn2 * Av.w, C_ = -2.0f * kLn2 * Bv.x;
 #pragma unroll
           for (int i = 0; i < PPT; ++i) {
-            const int py = ti.py0 + i;
-            if (j > mylast[i] || py < y0 || py > y1) continue;
+            const int ci = slot_col<PPT>(i), ri = slot_row<PPT>(i);
+            if (j > mylast[i] || !(ci ? cB : cA) || !(ri ? rB : rA)) continue;
             if (kCount) ++n_pixb;
+            const ColTerms& ct = ci ? ct1 : ct0;
             float alpha, ex, dy;
             bool cl;
-            if (!pixel_alpha(ct, Av.y, Bv.x, Bv.y, (float)py + 0.5f, amin, amax, alpha, ex, dy, cl))
+            if (!pixel_alpha(ct, Av.y, Bv.x, Bv.y, (float)(ti.y + 4 * ri) + 0.5f, amin, amax, alpha,
+                             ex, dy, cl))
               continue;
             if (kCount) ++n_actb;
             act = true;
-            const float rinv = 1.0f / (1.0f - alpha);
+            const float rinv = rcp_approx(1.0f - alpha);
             const float Ti = T[i] * rinv;
             const float aT = alpha * Ti;
             const float4 q = gct[i];
@@ -304,24 +376,14 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
             atomicAdd(&dst[2].x, gb);
           }
         } else {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            gu += __shfl_xor_sync(0xffffffffu, gu, o);
-            gv += __shfl_xor_sync(0xffffffffu, gv, o);
-            gA += __shfl_xor_sync(0xffffffffu, gA, o);
-            gB += __shfl_xor_sync(0xffffffffu, gB, o);
-            gC += __shfl_xor_sync(0xffffffffu, gC, o);
-            go += __shfl_xor_sync(0xffffffffu, go, o);
-            gr += __shfl_xor_sync(0xffffffffu, gr, o);
-            gg += __shfl_xor_sync(0xffffffffu, gg, o);
-            gb += __shfl_xor_sync(0xffffffffu, gb, o);
-          }
-          if (lane == 0) {
-            float4* dst = g2 + (int64_t)sG[jj] * 3;
-            atomicAdd(dst, make_float4(gu, gv, gA, gB));
-            atomicAdd(dst + 1, make_float4(gC, go, gr, gg));
-            atomicAdd(&dst[2].x, gb);
-          }
+          float v[9] = {gu, gv, gA, gB, gC, go, gr, gg, gb};
+          float mine, v8;
+          warp_reduce9(v, lane, mine, v8);
+          // lanes 0, 4, ..., 28 hold the sums of values 0..7, lane 0 also value 8; the
+          // 2-D gradient record is 12 floats (gu, gv, gA, gB, gC, go, gr, gg, gb, -, -, -)
+          float* dst = reinterpret_cast<float*>(g2 + (int64_t)sG[jj] * 3);
+          if ((lane & 3) == 0) atomicAdd(dst + (lane >> 2), mine);
+          if (lane == 0) atomicAdd(dst + 8, v8);
         }
       }
     }
