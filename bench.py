@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-skip", action="store_true",
+                    help="render every (view, subset, tile) item (no saturation skipping)")
     ap.add_argument("--cpu-tile-fraction", type=float, default=1.0 / 48.0)
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving run (0: skip it)")
@@ -86,14 +88,14 @@ def make_workload(name, n_override=0, seed=3, rank=0, views_override=0):
     w = dict(I.WORKLOADS[name])
     n = n_override or w["n"]
     views = views_override or max(1, w["views"])
-    sc, off, _, cams = I.cluster_case(n, seed, w["K"], views, w["sizes"], w["sh_degree"])
+    sc, off, boxes, cams = I.cluster_case(n, seed, w["K"], views, w["sizes"], w["sh_degree"])
     if rank:
         cams = I.orbit_cameras(views, seed + 1 + 1000 * rank, w["sizes"])
     targets = [I.random_image(c.height, c.width, 100 + 17 * rank + i) for i, c in enumerate(cams)]
     desc = (f"{name}: {n} Gaussians SH{w['sh_degree']}, K={w['K']} k-d subsets (x/z), "
             f"{views} views " + "+".join(f"{sum(1 for c in cams if (c.width, c.height) == s)}x{s[0]}x{s[1]}"
                                          for s in w["sizes"]) + ", L1 loss vs seeded target, Adam")
-    return sc, off, cams, targets, desc
+    return sc, off, boxes, cams, targets, desc
 
 
 # ---------------------------------------------------------------- clocks
@@ -157,6 +159,42 @@ def peaks():
         return d, "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# DRAM traffic per unit of work measured by ncu (profiles/dram_traffic.md): one line per
+# kernel, "kernel | source file | sha256 of that file at capture | bytes per unit | unit".
+KERNEL_SOURCE = {"raster_fwd": "raster.cu", "raster_bwd": "raster.cu", "project": "project.cu",
+                 "fill": "bin.cu", "sort": "bin.cu", "project_bwd": "project_bwd.cu",
+                 "composite": "composite.cu", "composite_bwd": "composite.cu"}
+
+
+def measured_traffic(name, counts):
+    """DRAM bytes per launch of `name` from the committed ncu summary, scaled to this
+    launch by its units of work; None if there is no entry or the kernel's source changed
+    since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        cells = [c.strip() for c in ln.strip().strip("|").split("|")]
+        if len(cells) != 5 or cells[0] != name:
+            continue
+        src = os.path.join(ROOT, "paper_2606_18588_gb300", "csrc", cells[1])
+        try:
+            digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        except OSError:
+            return None
+        if digest != cells[2]:
+            return None
+        unit = cells[4]
+        units = counts.get(unit)
+        if units is None:
+            return None
+        return float(cells[3]) * units
+    return None
 
 
 def roofline(name, ms, counts, w, pk):
@@ -234,7 +272,7 @@ def run_reference(args):
         return 0
     from oracle import oracle as O
     O.build()
-    sc, off, cams, _, desc = make_workload(args.workload, args.n, views_override=args.views)
+    sc, off, _, cams, _, desc = make_workload(args.workload, args.n, views_override=args.views)
     cam = cams[0]
     times = []
     info = ""
@@ -310,16 +348,19 @@ def main():
     from paper_2606_18588_gb300 import splx as S
     from paper_2606_18588_gb300.train import BatchedStep, PlainStep, scene_to_device
 
-    sc, off, cams, targets, desc = make_workload(args.workload, args.n, rank=rank,
+    sc, off, boxes, cams, targets, desc = make_workload(args.workload, args.n, rank=rank,
                                                  views_override=args.views)
     ctx = S.Context(local)
     dev = scene_to_device(sc)
     stream = torch.cuda.Stream()
+    # saturation skipping: per view the front-to-back order of the k-d cells
+    from paper_2606_18588_gb300.visibility import orders_for_views
+    order = None if args.no_skip else orders_for_views(boxes, cams)
     tune = None
     if args.tile == 0:
         from paper_2606_18588_gb300.autotune import autotune
         tgt = torch.cat([torch.from_numpy(t).reshape(-1) for t in targets]).cuda()
-        tune = autotune(ctx, dev, off, sc.sh_degree, cams, tgt, stream=stream)
+        tune = autotune(ctx, dev, off, sc.sh_degree, cams, tgt, stream=stream, order=order)
         tile, ctas = tune.tile, tune.ctas_per_sm
         del tgt
     else:
@@ -327,7 +368,7 @@ def main():
     o = S.opts(tile=tile)
     with torch.cuda.stream(stream):
         st = BatchedStep(ctx, dev, off, sc.sh_degree, cams, [torch.from_numpy(t) for t in targets],
-                         o, stream=stream)
+                         o, stream=stream, order=order)
         st.batch.set_timing(True)
         st.batch.set_launch(ctas)
         st.run()  # eager once: sizes everything, checks status
@@ -422,6 +463,7 @@ def main():
     roof = roofline(dom, cand[dom], counts, wl, pk)
     roof["peak_source"] = f"{pk_src} ({'HBM copy' if roof['bound'] == 'hbm' else 'SMs x FP32 lanes x max SM clock'})"
     roof["share_of_step"] = cand[dom] / ms
+    roof["traffic"] = measured_traffic(dom, counts)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -433,6 +475,9 @@ def main():
                        "path": "batched: one CUDA graph per step (project + tile counts, scan, "
                                "fill tile buckets, per-tile depth sort, raster fwd, composite, L1 "
                                "loss, composite bwd, raster bwd, project bwd, Adam)",
+                       "saturation_skipping": order is not None,
+                       "plain_path": "one render_partial per (view, subset) + composite + "
+                                     "backward per view, every subset rendered (no skipping)",
                        "l2": "inputs larger than L2 (2.4 GB parameters, 10 GB projected records)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "plain": plain, "kernel_ms": kmean, "counters": counts},

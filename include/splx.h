@@ -237,16 +237,29 @@ int splx_batch_set_timing(splx_batch_t b, int enable);
  * SPLX_ERR_INVALID.  Applies to launches issued afterwards (a captured graph keeps the
  * shape it was captured with). */
 int splx_batch_set_launch(splx_batch_t b, int32_t raster_ctas_per_sm);
+/* Saturation skipping (Sec. 4.2 "saturation skipping", with the composite's threshold
+ * eps_comp of splx_opts).  order (host, [V][K]) is, per view, a front-to-back order of the
+ * K subsets (for k-d cells: the BSP order from the camera centre).  Once set, the forward
+ * renders the subsets in K waves in that order and leaves a (view, subset, tile) work item
+ * empty (C = 0, T = 1, D = 0, no contributor) when the product of the transmittances of
+ * the subsets rendered before it is below eps_comp at every pixel of the tile; its
+ * backward then has nothing to do.  The composite skips such subsets at those pixels
+ * anyway, so images and gradients are unchanged wherever the per-pixel subset order of
+ * Eq. 5 agrees with the given order.  NULL turns skipping off.  Each row must be a
+ * permutation of 0..K-1, else SPLX_ERR_INVALID.  Synchronises; applies to launches
+ * issued afterwards. */
+int splx_batch_set_order(splx_batch_t b, const int32_t* order);
 /* Largest number of persistent forward / backward rasteriser CTAs resident on one SM at
  * the batch's tile side (host outputs). */
 int splx_batch_max_ctas_per_sm(splx_batch_t b, int32_t* fwd, int32_t* bwd);
 int splx_batch_kernel_times(splx_batch_t b, float* ms_out);
-/* Work counters (synchronises; host array of 7): out[0] = (Gaussian, tile) pairs of the
+/* Work counters (synchronises; host array of 8): out[0] = (Gaussian, tile) pairs of the
  * last run; then, from the last EAGER run (replays of a captured graph do not count):
  * forward rasteriser out[1] = (thread, list entry) pairs examined, out[2] = (pixel,
  * entry) alpha evaluations, out[3] = (pixel, entry) blends; backward rasteriser out[4] =
  * (thread, entry) pairs, out[5] = alpha evaluations, out[6] = contributions (alpha >=
- * alpha_min).  A thread owns a column of 2 (8x8 tiles) or 4 (16x16, 32x32) pixels. */
+ * alpha_min); out[7] = (view, subset, tile) work items left empty by saturation skipping.
+ * A thread owns 2 (8x8 tiles) or 4 (16x16, 32x32) pixels. */
 int splx_batch_counters(splx_batch_t b, int64_t* out, splx_stream_t stream);
 
 /* ---- serving: continuous batching of render requests --------------------------- */

@@ -78,8 +78,9 @@ def lib():
             _lib.orc_project.argtypes = [P, P, P]
             _lib.orc_render.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
             _lib.orc_composite.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P, P, P]
-            _lib.orc_render_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P, P, P, P]
-            _lib.orc_backward_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P]
+            _lib.orc_render_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P, P, P, P, P,
+                                             P]
+            _lib.orc_backward_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P]
             _lib.orc_adam.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_double,
                                       C.c_double, C.c_int64]
             _lib.orc_num_threads.restype = C.c_int
@@ -208,8 +209,20 @@ def composite(Cp, Tp, Dp, o: Opts | None = None):
     return dict(image=out, T=To, nused=nu, amb=amb)
 
 
-def render_view(scene, offsets, cam, o: Opts | None = None, tile_mask=None, separable=False):
-    """K contiguous subsets rendered and composited: dict(image, T, Cp, Tp, Dp, amb, sep)."""
+def _order(order, K):
+    if order is None:
+        return None
+    a = np.ascontiguousarray(order, np.int32)
+    if sorted(a.tolist()) != list(range(K)):
+        raise ValueError("order must be a permutation of the K subsets")
+    return a
+
+
+def render_view(scene, offsets, cam, o: Opts | None = None, tile_mask=None, separable=False,
+                order=None):
+    """K contiguous subsets rendered and composited: dict(image, T, Cp, Tp, Dp, amb, sep,
+    skip).  With `order` (front-to-back subset order) the partials are rendered in that
+    order with saturation skipping; skip[m, t] marks the tiles subset m left empty."""
     o = o or opts()
     k = _Keep(scene)
     c = camera(cam)
@@ -222,14 +235,21 @@ def render_view(scene, offsets, cam, o: Opts | None = None, tile_mask=None, sepa
     sep = np.ones((H, W), np.uint8) if separable else None
     st = np.zeros(1, np.int64)
     tm = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8)
-    lib().orc_render_view(C.byref(k.p), _ptr(off), K, C.byref(c), C.byref(o), _ptr(tm), _ptr(out),
-                          _ptr(To), _ptr(Cp), _ptr(Tp), _ptr(Dp), _ptr(amb), _ptr(sep), _ptr(st))
-    return dict(image=out, T=To, Cp=Cp, Tp=Tp, Dp=Dp, amb=amb, sep=sep, evaluated=int(st[0]))
+    od = _order(order, K)
+    B = int(o.tile)
+    skip = np.zeros((K, ((H + B - 1) // B) * ((W + B - 1) // B)), np.uint8)
+    lib().orc_render_view(C.byref(k.p), _ptr(off), K, C.byref(c), C.byref(o), _ptr(tm), _ptr(od),
+                          _ptr(out), _ptr(To), _ptr(Cp), _ptr(Tp), _ptr(Dp), _ptr(amb), _ptr(sep),
+                          _ptr(skip), _ptr(st))
+    return dict(image=out, T=To, Cp=Cp, Tp=Tp, Dp=Dp, amb=amb, sep=sep, skip=skip,
+                evaluated=int(st[0]))
 
 
-def backward_view(scene, offsets, cam, dLdC, dLdT=None, o: Opts | None = None, tile_mask=None):
+def backward_view(scene, offsets, cam, dLdC, dLdT=None, o: Opts | None = None, tile_mask=None,
+                  order=None):
     """Gradients (float64) of sum(dLdC*C) + sum(dLdT*T) w.r.t. every parameter array
-    (restricted to the pixels of tiles where tile_mask is nonzero, if given)."""
+    (restricted to the pixels of tiles where tile_mask is nonzero, if given; with `order`,
+    of the saturation-skipping render)."""
     o = o or opts()
     k = _Keep(scene)
     c = camera(cam)
@@ -241,7 +261,7 @@ def backward_view(scene, offsets, cam, dLdC, dLdT=None, o: Opts | None = None, t
     dT = None if dLdT is None else np.ascontiguousarray(dLdT, np.float64)
     tm = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8)
     lib().orc_backward_view(C.byref(k.p), _ptr(off), K, C.byref(c), C.byref(o), _ptr(dC), _ptr(dT),
-                            _ptr(tm), C.byref(gr))
+                            _ptr(tm), _ptr(_order(order, K)), C.byref(gr))
     return g
 
 
@@ -254,3 +274,35 @@ def adam(p, g, m, v, lr, b1, b2, eps, step):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def cell_order(boxes, eye):
+    """Front-to-back order of k-d cells ([K, 2, 3] lo/hi boxes, infinite on unsplit sides)
+    from `eye` (Sec. 4.2): an explicit stack of cell sets; each set is cut by the first
+    axis-aligned plane (axes x, y, z, ascending coordinate) that leaves every cell of the
+    set on one side, and the side holding the eye is taken first."""
+    b = np.asarray(boxes, np.float64)
+    eye = np.asarray(eye, np.float64)
+    out = []
+    stack = [list(range(b.shape[0]))]
+    while stack:
+        ids = stack.pop()
+        if len(ids) == 1:
+            out.append(ids[0])
+            continue
+        cut = None
+        for ax in range(3):
+            coords = np.unique(b[ids][:, :, ax])
+            for p in coords[np.isfinite(coords)]:
+                lo_side = [i for i in ids if b[i, 1, ax] <= p]
+                hi_side = [i for i in ids if b[i, 0, ax] >= p]
+                if lo_side and hi_side and len(lo_side) + len(hi_side) == len(ids):
+                    cut = (lo_side, hi_side) if eye[ax] <= p else (hi_side, lo_side)
+                    break
+            if cut:
+                break
+        if cut is None:
+            raise ValueError("not a k-d partition")
+        stack.append(cut[1])  # popped after the whole first side
+        stack.append(cut[0])
+    return out

@@ -541,6 +541,60 @@ int composite_order(int K, const double* Tm, const double* Dm, const orc_opts& o
 
 }  // namespace
 
+extern "C" int orc_render(const orc_params* p, const orc_camera* cam, const orc_opts* o,
+                          const uint8_t* tile_mask, double* C, double* T, double* D,
+                          int32_t* last, int32_t* ncontrib, uint8_t* amb, int64_t* stats);
+
+namespace {
+
+// Saturation skipping (Sec. 4.2, with the composite's threshold eps_comp): the K partials
+// of a view are rendered in the given front-to-back subset order, and the subset at rank
+// r leaves tile t empty (C = 0, T = 1, D = 0) when the product of the transmittances of
+// the subsets ranked before it is below eps_comp at every pixel of the tile.  Renders
+// into C, T, D (planar per subset) and fills skip[m * nt + t].  With order == nullptr
+// every subset is rendered on every tile of tile_mask.
+void render_partials(const orc_params& p, const int64_t* offsets, int K, const orc_camera& cam,
+                     const orc_opts& o, const uint8_t* tile_mask, const int32_t* order,
+                     std::vector<double>& C, std::vector<double>& T, std::vector<double>& D,
+                     std::vector<uint8_t>& skip, uint8_t* amb, int64_t* stats) {
+  const int W = cam.width, H = cam.height, B = o.tile;
+  const int64_t HW = (int64_t)W * H;
+  const int tw = (W + B - 1) / B, th = (H + B - 1) / B, nt = tw * th;
+  C.assign((size_t)K * 3 * HW, 0.0);
+  T.assign((size_t)K * HW, 1.0);
+  D.assign((size_t)K * HW, 0.0);
+  skip.assign((size_t)K * nt, 0);
+  std::vector<double> prefix(HW, 1.0);
+  std::vector<uint8_t> mask(nt), a1(HW, 0);
+  for (int r = 0; r < K; ++r) {
+    const int m = order ? order[r] : r;
+    for (int t = 0; t < nt; ++t) {
+      mask[t] = (uint8_t)(!tile_mask || tile_mask[t]);
+      if (order && r > 0 && mask[t]) {
+        const int tx = t % tw, ty = t / tw;
+        double mx = 0.0;
+        for (int py = ty * B; py < std::min(H, (ty + 1) * B); ++py)
+          for (int px = tx * B; px < std::min(W, (tx + 1) * B); ++px)
+            mx = std::max(mx, prefix[(int64_t)py * W + px]);
+        if (mx < o.eps_comp) {
+          mask[t] = 0;
+          skip[(size_t)m * nt + t] = 1;
+        }
+      }
+    }
+    orc_params q = slice(p, offsets[m], offsets[m + 1]);
+    std::fill(a1.begin(), a1.end(), 0);
+    orc_render(&q, &cam, &o, mask.data(), C.data() + (size_t)m * 3 * HW, T.data() + (size_t)m * HW,
+               D.data() + (size_t)m * HW, nullptr, nullptr, a1.data(), stats);
+    if (amb)
+      for (int64_t i = 0; i < HW; ++i) amb[i] |= a1[i];
+    if (order)
+      for (int64_t i = 0; i < HW; ++i) prefix[i] *= T[(size_t)m * HW + i];
+  }
+}
+
+}  // namespace
+
 extern "C" {
 
 float orc_exp_spec(float x) { return exp_spec(x); }
@@ -677,18 +731,14 @@ int orc_composite(int32_t K, int32_t H, int32_t W, const double* Cp, const doubl
 // separable, i.e. its monolithic contributor list (all Gaussians, no termination) is a
 // concatenation of per-subset runs in composite order (where Eq. 5 equals Eq. 2).
 int orc_render_view(const orc_params* p, const int64_t* offsets, int32_t K, const orc_camera* cam,
-                    const orc_opts* o, const uint8_t* tile_mask, double* out, double* Tout,
-                    double* Cp, double* Tp, double* Dp, uint8_t* amb, uint8_t* sep,
-                    int64_t* stats) {
+                    const orc_opts* o, const uint8_t* tile_mask, const int32_t* order,
+                    double* out, double* Tout, double* Cp, double* Tp, double* Dp, uint8_t* amb,
+                    uint8_t* sep, uint8_t* skip_out, int64_t* stats) {
   const int64_t HW = (int64_t)cam->width * cam->height;
-  std::vector<double> C((size_t)K * 3 * HW, 0.0), T((size_t)K * HW, 1.0), D((size_t)K * HW, 0.0);
-  std::vector<uint8_t> a(HW, 0), a1(HW, 0);
-  for (int m = 0; m < K; ++m) {
-    orc_params q = slice(*p, offsets[m], offsets[m + 1]);
-    orc_render(&q, cam, o, tile_mask, C.data() + (size_t)m * 3 * HW, T.data() + (size_t)m * HW,
-               D.data() + (size_t)m * HW, nullptr, nullptr, a1.data(), stats);
-    for (int64_t i = 0; i < HW; ++i) a[i] |= a1[i];
-  }
+  std::vector<double> C, T, D;
+  std::vector<uint8_t> a(HW, 0), skip;
+  render_partials(*p, offsets, K, *cam, *o, tile_mask, order, C, T, D, skip, a.data(), stats);
+  if (skip_out) std::memcpy(skip_out, skip.data(), skip.size());
   orc_composite(K, cam->height, cam->width, C.data(), T.data(), D.data(), o, out, Tout, nullptr,
                 a.data());
   if (Cp) std::memcpy(Cp, C.data(), C.size() * sizeof(double));
@@ -744,18 +794,19 @@ int orc_render_view(const orc_params* p, const int64_t* offsets, int32_t K, cons
 // as if dLdC and dLdT were zero elsewhere.
 int orc_backward_view(const orc_params* p, const int64_t* offsets, int32_t K,
                       const orc_camera* cam, const orc_opts* o, const double* dLdC,
-                      const double* dLdT, const uint8_t* tile_mask, const orc_grads* gr) {
+                      const double* dLdT, const uint8_t* tile_mask, const int32_t* order,
+                      const orc_grads* gr) {
   const int W = cam->width, H = cam->height, B = o->tile;
   const int64_t HW = (int64_t)W * H;
   const int nc = (p->sh_degree + 1) * (p->sh_degree + 1);
   std::vector<Subset> subs(K);
-  std::vector<double> C((size_t)K * 3 * HW, 0.0), T((size_t)K * HW, 1.0), D((size_t)K * HW, 0.0);
   for (int m = 0; m < K; ++m) {
     orc_params q = slice(*p, offsets[m], offsets[m + 1]);
     subs[m] = prepare(q, *cam, B, (float)o->alpha_min);
-    orc_render(&q, cam, o, tile_mask, C.data() + (size_t)m * 3 * HW, T.data() + (size_t)m * HW,
-               D.data() + (size_t)m * HW, nullptr, nullptr, nullptr, nullptr);
   }
+  std::vector<double> C, T, D;
+  std::vector<uint8_t> skip;
+  render_partials(*p, offsets, K, *cam, *o, tile_mask, order, C, T, D, skip, nullptr, nullptr);
   // per-Gaussian 2-D gradients: u, v, A, B, C, o, r, g, b (threads add atomically)
   std::vector<double> g2((size_t)p->n * 9, 0.0);
   const int tw = (W + B - 1) / B, th = (H + B - 1) / B;
@@ -797,6 +848,7 @@ int orc_backward_view(const orc_params* p, const int64_t* offsets, int32_t K,
           // local-render adjoint per subset, back to front
           for (int j = 0; j < L; ++j) {
             const int m = ord[j];
+            if (skip[(size_t)m * tw * th + t]) continue;  // not rendered: no contributors
             const Subset& s = subs[m];
             const int32_t* lst = s.tiles.list.data() + s.tiles.start[t];
             const int64_t cnt = s.tiles.start[t + 1] - s.tiles.start[t];

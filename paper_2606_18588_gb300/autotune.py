@@ -52,9 +52,10 @@ def _time(fn, stream, reps):
 
 def autotune(ctx: S.Context, params: dict, offsets, sh_degree: int, cams, target: torch.Tensor,
              tiles=TILES, ctas=CTAS_PER_SM, reps: int = 3, stream=None,
-             base_opts: S.Opts | None = None) -> TuneResult:
+             base_opts: S.Opts | None = None, order=None) -> TuneResult:
     """Times forward + L1 loss + backward of the V views x K subsets batch for every
-    (tile, CTAs per SM) candidate.  `target` is the flat concatenated target image."""
+    (tile, CTAs per SM) candidate.  `target` is the flat concatenated target image;
+    `order` ([V, K] front-to-back subset orders) tunes the saturation-skipping forward."""
     stream = stream or torch.cuda.current_stream()
     offsets = np.asarray(offsets)
     subs = _subset_structs(params, offsets, sh_degree)
@@ -66,6 +67,8 @@ def autotune(ctx: S.Context, params: dict, offsets, sh_degree: int, cams, target
             o = S.opts(tile=tile) if base_opts is None else _with_tile(base_opts, tile)
             batch = S.Batch(ctx, subs, cams, o, 0, stream=stream)
             try:
+                if order is not None:
+                    batch.set_order(order)
                 rgb = torch.empty(batch.rgb_off[-1], device="cuda")
                 dL = torch.empty_like(rgb)
                 loss = torch.zeros(1, device="cuda")

@@ -185,6 +185,8 @@ struct Plan {
   unsigned long long* counters = nullptr;  // [kCounters]: see BatchDev::counters
   unsigned long long* work_ctr = nullptr;  // [2]: persistent rasterisers' work counters
   int persist_grid = 0;                    // persistent raster grid (0: one CTA per item)
+  int32_t* order_d = nullptr;              // [V][K] front-to-back subset order (skipping on)
+  float* tpre = nullptr;                   // [total pixels] prefix transmittance of the waves
   void* scan_temp = nullptr;
   int64_t capacity = 0, n_tiles = 0, total_pixels = 0;
   splx_opts opts{};
@@ -234,6 +236,9 @@ struct Plan {
     b.counters = counters;
     b.persist_grid = persist_grid;
     b.work_ctr = work_ctr;
+    b.order = nullptr;  // set per launch by the forward's waves
+    b.wave = 0;
+    b.tpre = tpre;
     // composite-only plans carry no subsets; their offsets are unused
     for (int k = 0; k <= K; ++k) b.goff[k] = k < (int)subsets_h.size() ? subsets_h[k].goff : N;
     for (int v = 0; v <= V; ++v) { b.tile_base[v] = tile_base[v]; b.pix_off[v] = pix_off[v]; }
@@ -250,7 +255,8 @@ struct Plan {
                    (void**)&counts, (void**)&tile_cnt, (void**)&tile_start, (void**)&keys,
                    (void**)&keys_alt, (void**)&big_list, (void**)&big_count, (void**)&chunks,
                    (void**)&chunk_count, (void**)&ranges,
-                   (void**)&grad2d, (void**)&scan_temp, (void**)&counters, (void**)&work_ctr};
+                   (void**)&grad2d, (void**)&scan_temp, (void**)&counters, (void**)&work_ctr,
+                   (void**)&order_d, (void**)&tpre};
     for (void** p : ps) free_ptr(*p, s);
     for (auto& e : ev)
       if (e) { cudaEventDestroy(e); e = nullptr; }
@@ -796,7 +802,17 @@ int splx_batch_forward(splx_batch_t bt, float* out_rgb, float* out_T, splx_strea
   BatchDev b = P.dev();
   b.out_rgb = out_rgb;
   b.out_T = out_T;
-  launch_raster_fwd(b, s);
+  if (P.order_d) {
+    // saturation skipping: K waves, each rendering one subset of every view, front to back
+    for (int r = 0; r < P.K; ++r) {
+      BatchDev bw = b;
+      bw.order = P.order_d;
+      bw.wave = r;
+      launch_raster_fwd(bw, s);
+    }
+  } else {
+    launch_raster_fwd(b, s);
+  }
   P.mark(5, s);
   launch_composite(b, P.total_pixels, s);
   P.mark(6, s);
@@ -856,6 +872,33 @@ int splx_batch_set_launch(splx_batch_t bt, int32_t raster_ctas_per_sm) {
   return SPLX_OK;
 }
 
+int splx_batch_set_order(splx_batch_t bt, const int32_t* order) {
+  if (!bt) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  CtxScope scope(P.ctx);
+  if (!order) {
+    P.free_ptr((void*&)P.order_d, nullptr);
+    P.free_ptr((void*&)P.tpre, nullptr);
+    return SPLX_OK;
+  }
+  for (int v = 0; v < P.V; ++v) {
+    std::vector<int> seen(P.K, 0);
+    for (int r = 0; r < P.K; ++r) {
+      const int k = order[v * P.K + r];
+      if (k < 0 || k >= P.K || seen[k]++) return SPLX_ERR_INVALID;
+    }
+  }
+  int r;
+  if (!P.order_d && (r = ctx_alloc_t(P.ctx, &P.order_d, (size_t)P.V * P.K, nullptr))) return r;
+  if (!P.tpre &&
+      (r = ctx_alloc_t(P.ctx, &P.tpre, (size_t)std::max<int64_t>(P.total_pixels, 1), nullptr))) {
+    P.free_ptr((void*&)P.order_d, nullptr);
+    return r;
+  }
+  CK(cudaMemcpy(P.order_d, order, sizeof(int32_t) * P.V * P.K, cudaMemcpyHostToDevice));
+  return SPLX_OK;
+}
+
 int splx_batch_max_ctas_per_sm(splx_batch_t bt, int32_t* fwd, int32_t* bwd) {
   if (!bt || !fwd || !bwd) return SPLX_ERR_INVALID;
   Plan& P = bt->plan;
@@ -887,7 +930,7 @@ int splx_batch_counters(splx_batch_t bt, int64_t* out, splx_stream_t stream) {
   Plan& P = bt->plan;
   CtxScope scope(P.ctx);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  unsigned long long c[kCounters] = {};
+  unsigned long long c[kCounters] = {};  // host copy of the device counters
   uint32_t total = 0;
   CK(cudaMemcpyAsync(c, P.counters, sizeof(c), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&total, P.tile_start + P.n_tiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));

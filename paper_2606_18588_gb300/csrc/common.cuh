@@ -9,7 +9,7 @@
 namespace splx {
 
 constexpr int kMaxK = 64;        // subsets per view
-constexpr int kCounters = 6;     // work counters of a batch (BatchDev::counters)
+constexpr int kCounters = 7;     // work counters of a batch (BatchDev::counters)
 
 // True while `s` is being captured into a CUDA graph.
 inline bool stream_capturing(cudaStream_t s) {
@@ -98,8 +98,15 @@ struct BatchDev {
   int* status;                  // device status word
   // work counters (nullable; kept by eager runs): forward [0] thread-entries examined,
   // [1] (pixel, entry) alpha evaluations, [2] blends; backward [3] thread-entries,
-  // [4] alpha evaluations, [5] contributions (alpha >= alpha_min)
+  // [4] alpha evaluations, [5] contributions (alpha >= alpha_min); [6] work items left
+  // empty by saturation skipping
   unsigned long long* counters;
+  // saturation skipping (order != nullptr): the forward rasteriser runs in K waves; wave r
+  // renders subset order[v * K + r] of every view v, and tpre [total pixels] holds the
+  // product of the transmittances of the subsets rendered so far
+  const int32_t* order;
+  int wave;
+  float* tpre;
   // persistent rasterisers: grid size (0 = one CTA per work item) and the two work
   // counters they take items from ([0] forward, [1] backward; reset before each launch)
   int persist_grid;

@@ -112,6 +112,44 @@ struct TileInfo {
   int v, k, x, y, W, H;
 };
 
+// Blocks of a warp's region (origin RX, RY) that the rectangle [x0,x1] x [y0,y1] meets:
+// bit i for slot i (PPT = 4: blocks at x offsets 0/8, y offsets 0/4; PPT = 2: y 0/4).
+template <int PPT>
+__device__ __forceinline__ unsigned block_mask(int x0, int x1, int y0, int y1, int RX, int RY) {
+  const bool xb0 = x0 <= RX + 7 && x1 >= RX;
+  const bool xb1 = PPT == 4 && x0 <= RX + 15 && x1 >= RX + 8;
+  const bool yb0 = y0 <= RY + 3 && y1 >= RY;
+  const bool yb1 = y0 <= RY + 7 && y1 >= RY + 4;
+  if (PPT == 4)
+    return (unsigned)(xb0 && yb0) | ((unsigned)(xb1 && yb0) << 1) |
+           ((unsigned)(xb0 && yb1) << 2) | ((unsigned)(xb1 && yb1) << 3);
+  return (unsigned)(xb0 && yb0) | ((unsigned)(xb0 && yb1) << 1);
+}
+
+// Compacts the staged entries [0, cnt) that meet the warp's region (and pass `keep`) into
+// list[] as (entry | block mask << 16), in entry order; returns their number.  One lane
+// tests one entry, 32 at a time.
+template <int PPT, typename Keep>
+__device__ __forceinline__ int compact_entries(const float4* sB, const float4* sC, int cnt,
+                                               int RX, int RY, int lane, uint32_t* list,
+                                               Keep keep) {
+  int nl = 0;
+  for (int g0 = 0; g0 < cnt; g0 += 32) {
+    const int e = g0 + lane;
+    unsigned m = 0;
+    if (e < cnt && keep(e)) {
+      const uint32_t rx = __float_as_uint(sB[e].w), ry = __float_as_uint(sC[e].w);
+      m = block_mask<PPT>((int)(rx & 0xFFFFu), (int)(rx >> 16), (int)(ry & 0xFFFFu),
+                          (int)(ry >> 16), RX, RY);
+    }
+    const unsigned hit = __ballot_sync(0xffffffffu, m != 0);
+    if (m) list[nl + __popc(hit & ((1u << lane) - 1u))] = (uint32_t)e | (m << 16);
+    nl += __popc(hit);
+  }
+  __syncwarp();
+  return nl;
+}
+
 template <int PPT>
 __device__ __forceinline__ int slot_col(int i) { return PPT == 4 ? (i & 1) : 0; }
 template <int PPT>
@@ -130,7 +168,7 @@ __device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
   const int w = (int)(threadIdx.x >> 5), l = (int)(threadIdx.x & 31);
   int rx0 = 0, ry0 = 0;
   if (PPT == 4) {
-    constexpr int kRegionsPerRow = TS / 16;
+    constexpr int kRegionsPerRow = TS >= 16 ? TS / 16 : 1;
     rx0 = 16 * (w % kRegionsPerRow);
     ry0 = 8 * (w / kRegionsPerRow);
   }
@@ -141,6 +179,20 @@ __device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
   return ti;
 }
 
+// Work item of a launch: every (view, subset, tile), or in a saturation-skipping wave the
+// tiles of subset order[v][wave] of every view v (n_tiles / K items).
+__device__ __forceinline__ int64_t item_of(const BatchDev& b, int64_t w) {
+  if (!b.order) return w;
+  const int v = view_of(b.tile_base, b.V, w * b.K);
+  const int64_t nt = (b.tile_base[v + 1] - b.tile_base[v]) / b.K;
+  const int k = b.order[v * b.K + b.wave];
+  return b.tile_base[v] + (int64_t)k * nt + (w - b.tile_base[v] / b.K);
+}
+
+__device__ __forceinline__ int64_t items_of_launch(const BatchDev& b) {
+  return b.order ? b.n_tiles / b.K : b.n_tiles;
+}
+
 }  // namespace
 
 // kCount variants (eager runs only) also count the work for the roofline: thread-entries
@@ -149,7 +201,7 @@ constexpr int kNB = 256;  // list entries staged in shared memory per batch
 
 template <int TS, int PPT, bool kCount>
 __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, float4* sA,
-                                         float4* sB, float4* sC) {
+                                         float4* sB, float4* sC, uint32_t* sL) {
   constexpr int NTH = TS * TS / PPT;
   constexpr int NB = kNB;
   const TileInfo ti = decode_tile<TS, PPT>(b, id);
@@ -165,6 +217,35 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
   for (int i = 0; i < PPT; ++i) {
     T[i] = 1.0f; c0[i] = c1[i] = c2[i] = D[i] = 0.0f; last[i] = -1;
     if (ti.x + 8 * slot_col<PPT>(i) < ti.W && ti.y + 4 * slot_row<PPT>(i) < ti.H) live |= 1u << i;
+  }
+  const ImgDev im = b.imgs[ti.v * b.K + ti.k];
+  const int64_t HW = (int64_t)ti.W * ti.H;
+  if (b.order && b.wave > 0) {
+    // saturation skipping: leave the tile empty if the subsets rendered before this one
+    // took the transmittance below eps_comp at every pixel (the composite would skip this
+    // subset there anyway)
+    const float* tp = b.tpre + b.pix_off[ti.v];
+    bool open = false;
+#pragma unroll
+    for (int i = 0; i < PPT; ++i)
+      if ((live >> i) & 1u)
+        open |= tp[(int64_t)(ti.y + 4 * slot_row<PPT>(i)) * ti.W + ti.x + 8 * slot_col<PPT>(i)] >=
+                b.eps_comp;
+    if (!__syncthreads_or(open)) {
+      if (kCount && threadIdx.x == 0 && b.counters) atomicAdd(b.counters + 6, 1ull);
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) {
+        if (!((live >> i) & 1u)) continue;
+        const int64_t p = (int64_t)(ti.y + 4 * slot_row<PPT>(i)) * ti.W + ti.x + 8 * slot_col<PPT>(i);
+        im.rgb[p] = 0.0f;
+        im.rgb[HW + p] = 0.0f;
+        im.rgb[2 * HW + p] = 0.0f;
+        im.T[p] = 1.0f;
+        im.D[p] = 0.0f;
+        im.last[p] = -1;
+      }
+      return;
+    }
   }
   unsigned n_eval = 0, n_pix = 0, n_blend = 0;
   for (int64_t base = start; base < end; base += NB) {
@@ -183,10 +264,18 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
       }
     }
     __syncthreads();
-    if (live) {
+    if (__any_sync(0xffffffffu, live != 0)) {
       const int cnt = (int)((end - base) < NB ? (end - base) : NB);
-      int jj = 0;
-      for (; jj < cnt && live; ++jj) {
+      const int lane = (int)(threadIdx.x & 31);
+      uint32_t* list = sL + (threadIdx.x >> 5) * NB;
+      const int nl = compact_entries<PPT>(sB, sC, cnt, ti.x - (lane & 7), ti.y - (lane >> 3),
+                                          lane, list, [](int) { return true; });
+      int q = 0;
+      for (; q < nl; ++q) {
+        if (!__any_sync(0xffffffffu, live != 0)) break;
+        const uint32_t item = list[q];
+        const int jj = (int)(item & 0xFFFFu);
+        const unsigned bm = item >> 16;
         const float4 Bv = sB[jj];
         const float4 Cv = sC[jj];
         const uint32_t rx = __float_as_uint(Bv.w), ry = __float_as_uint(Cv.w);
@@ -195,11 +284,11 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
         const bool cA = ti.x >= x0 && ti.x <= x1;
         const bool cB = PPT == 4 && ti.x + 8 >= x0 && ti.x + 8 <= x1;
         const bool rA = ti.y >= y0 && ti.y <= y1, rB = ti.y + 4 >= y0 && ti.y + 4 <= y1;
-        if (!(cA || cB) || !(rA || rB)) continue;
         const float4 Av = sA[jj];
         const ColTerms ct0 = col_terms(Av, pcx0), ct1 = col_terms(Av, pcx1);
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
+          if (!((bm >> i) & 1u)) continue;  // no lane of the warp has slot i in the rectangle
           const int ci = slot_col<PPT>(i), ri = slot_row<PPT>(i);
           if (!((live >> i) & 1u) || !(ci ? cB : cA) || !(ri ? rB : rA)) continue;
           if (kCount) ++n_pix;
@@ -220,7 +309,7 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
           if (kCount) ++n_blend;
         }
       }
-      if (kCount) n_eval += (unsigned)jj;
+      if (kCount && lane == 0) n_eval += (unsigned)q;
     }
   }
   if (kCount) {
@@ -228,8 +317,6 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
     flush_counter(b.counters, 1, n_pix);
     flush_counter(b.counters, 2, n_blend);
   }
-  const ImgDev im = b.imgs[ti.v * b.K + ti.k];
-  const int64_t HW = (int64_t)ti.W * ti.H;
 #pragma unroll
   for (int i = 0; i < PPT; ++i) {
     const int px = ti.x + 8 * slot_col<PPT>(i), py = ti.y + 4 * slot_row<PPT>(i);
@@ -241,6 +328,10 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
     im.T[p] = T[i];
     im.D[p] = D[i];
     im.last[p] = last[i];
+    if (b.order) {
+      float* tp = b.tpre + b.pix_off[ti.v] + p;
+      *tp = b.wave == 0 ? T[i] : *tp * T[i];
+    }
   }
 }
 
@@ -400,8 +491,9 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
 template <int TS, int PPT, bool kCount, bool kPersist>
 __global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) {
   __shared__ float4 sA[kNB], sB[kNB], sC[kNB];
+  __shared__ uint32_t sL[(TS * TS / PPT / 32) * kNB];  // per-warp compacted entry lists
   if constexpr (!kPersist) {
-    fwd_item<TS, PPT, kCount>(b, blockIdx.x, sA, sB, sC);
+    fwd_item<TS, PPT, kCount>(b, item_of(b, blockIdx.x), sA, sB, sC, sL);
   } else {
     __shared__ long long s_id;
     for (;;) {
@@ -409,8 +501,8 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) 
       if (threadIdx.x == 0) s_id = (long long)atomicAdd(b.work_ctr, 1ull);
       __syncthreads();
       const int64_t id = s_id;
-      if (id >= b.n_tiles) return;
-      fwd_item<TS, PPT, kCount>(b, id, sA, sB, sC);
+      if (id >= items_of_launch(b)) return;
+      fwd_item<TS, PPT, kCount>(b, item_of(b, id), sA, sB, sC, sL);
     }
   }
 }
@@ -450,8 +542,9 @@ static bool counting(const BatchDev& b, cudaStream_t s) {
 template <int TS, bool kCount, bool kPersist>
 static void launch_fwd_k(const BatchDev& b, cudaStream_t s) {
   constexpr int P = Ppt<TS>::value;
-  const unsigned grid = kPersist ? (unsigned)std::min<int64_t>(b.n_tiles, (int64_t)b.persist_grid)
-                                 : (unsigned)b.n_tiles;
+  const int64_t items = b.order ? b.n_tiles / b.K : b.n_tiles;
+  const unsigned grid = kPersist ? (unsigned)std::min<int64_t>(items, (int64_t)b.persist_grid)
+                                 : (unsigned)items;
   k_raster_fwd<TS, P, kCount, kPersist><<<grid, TS * TS / P, 0, s>>>(b);
 }
 template <int TS, bool kCount, bool kPersist>

@@ -91,6 +91,7 @@ _sigs = {
     "splx_batch_kernel_times": (C.c_int, [_P, _P]),
     "splx_batch_counters": (C.c_int, [_P, _P, _P]),
     "splx_batch_set_launch": (C.c_int, [_P, C.c_int32]),
+    "splx_batch_set_order": (C.c_int, [_P, _P]),
     "splx_batch_max_ctas_per_sm": (C.c_int, [_P, _P, _P]),
     "splx_server_create": (C.c_int, [_P, _P, C.c_int32, _P, C.c_size_t, C.c_int32, C.c_int32,
                                      C.POINTER(_P)]),
@@ -444,6 +445,18 @@ class Batch:
         """0: one rasteriser CTA per work item; n > 0: n persistent CTAs per SM."""
         _check(_lib.splx_batch_set_launch(self.h, int(raster_ctas_per_sm)), "splx_batch_set_launch")
 
+    def set_order(self, order):
+        """Saturation skipping with a [V, K] front-to-back subset order per view (None:
+        off); see splx_batch_set_order."""
+        if order is None:
+            _check(_lib.splx_batch_set_order(self.h, None), "splx_batch_set_order")
+            return
+        a = np.ascontiguousarray(order, np.int32)
+        if a.shape != (self.V, self.K):
+            raise ValueError(f"order must be [{self.V}, {self.K}]")
+        _check(_lib.splx_batch_set_order(self.h, a.ctypes.data_as(C.c_void_p)),
+               "splx_batch_set_order")
+
     def max_ctas_per_sm(self) -> tuple[int, int]:
         f, b = C.c_int32(0), C.c_int32(0)
         _check(_lib.splx_batch_max_ctas_per_sm(self.h, C.byref(f), C.byref(b)),
@@ -451,10 +464,11 @@ class Batch:
         return f.value, b.value
 
     def counters(self, stream=None) -> dict:
-        arr = (C.c_int64 * 7)()
+        arr = (C.c_int64 * 8)()
         _check(_lib.splx_batch_counters(self.h, arr, _stream(stream)), "splx_batch_counters")
         return dict(pairs=arr[0], entries_fwd=arr[1], alpha_fwd=arr[2], blended=arr[3],
-                    entries_bwd=arr[4], alpha_bwd=arr[5], contrib_bwd=arr[6])
+                    entries_bwd=arr[4], alpha_bwd=arr[5], contrib_bwd=arr[6],
+                    skipped_items=arr[7])
 
     def views(self, flat_rgb):
         """Split a concatenated rgb buffer into per-view [3,H,W] tensors."""

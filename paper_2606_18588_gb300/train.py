@@ -40,7 +40,9 @@ class BatchedStep:
 
     def __init__(self, ctx: S.Context, params: dict, offsets, sh_degree: int, cams, targets,
                  opts: S.Opts | None = None, lr=DEFAULT_LR, pair_capacity: int = 0,
-                 stream: torch.cuda.Stream | None = None):
+                 stream: torch.cuda.Stream | None = None, order=None):
+        """order: optional [V, K] front-to-back subset order per view, which turns on
+        saturation skipping (visibility.orders_for_views gives it for k-d cells)."""
         self.ctx, self.p, self.off, self.deg = ctx, params, np.asarray(offsets), sh_degree
         self.opts = opts or S.opts()
         self.stream = stream or torch.cuda.current_stream()
@@ -51,6 +53,8 @@ class BatchedStep:
         self.step_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
         self.batch = S.Batch(ctx, _subset_structs(params, offsets, sh_degree), cams, self.opts,
                              pair_capacity, stream=self.stream)
+        if order is not None:
+            self.batch.set_order(order)
         self.rgb = torch.empty(self.batch.rgb_off[-1], device="cuda")
         self.dL = torch.empty_like(self.rgb)
         self.loss = torch.zeros(1, device="cuda")

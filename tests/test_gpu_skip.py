@@ -1,0 +1,186 @@
+"""Saturation skipping (front-to-back waves, empty work items behind saturated tiles)
+through the batch C ABI: parity with the oracle's skipping render and backward, the same
+skip decisions, and images/gradients unchanged against the render without skipping."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2606_18588_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2606_18588_gb300 import splx as S
+    c = S.Context()
+    yield c
+    c.close()
+
+
+def _slabs():
+    from test_oracle_pins import _cam, _saturating_slabs
+    sc, off, boxes = _saturating_slabs(21)
+    cams = [_cam(64, 48), _cam(80, 56, eye=(0.3, -0.2, -3.2))]
+    return sc, off, boxes, cams
+
+
+def _batch(ctx, sc, off, cams, order, tile=16):
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import subset_struct, to_device
+    dev = to_device(sc)
+    subs = [subset_struct(dev, int(off[k]), int(off[k + 1]), sc.sh_degree)
+            for k in range(len(off) - 1)]
+    b = S.Batch(ctx, subs, cams, S.opts(tile=tile))
+    b.set_order(order)
+    return b, dev
+
+
+def _run(ctx, sc, off, cams, order, dL=None, tile=16):
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import params_struct, zeros_like_params
+    b, dev = _batch(ctx, sc, off, cams, order, tile)
+    rgb = torch.empty(b.rgb_off[-1], device="cuda")
+    T = torch.empty(b.total_pixels, device="cuda")
+    b.forward(rgb, T)
+    g = None
+    if dL is not None:
+        g = zeros_like_params(dev)
+        b.backward(dL, None, [params_struct(g, int(off[k]), int(off[k + 1]), sc.sh_degree)
+                              for k in range(len(off) - 1)])
+    torch.cuda.synchronize()
+    code, _ = b.status()
+    assert code == S.OK
+    counts = b.counters()
+    views = [v.clone() for v in b.views(rgb)]
+    b.close()
+    return views, T, g, counts
+
+
+def test_orders_are_the_oracles(ctx):
+    from paper_2606_18588_gb300.visibility import orders_for_views
+    sc, off, boxes, cams = _slabs()
+    orders = orders_for_views(boxes, cams)
+    for c, row in zip(cams, orders):
+        assert list(row) == O.cell_order(boxes, c.eye)
+
+
+def test_skipping_matches_oracle_and_leaves_results_unchanged(ctx):
+    from paper_2606_18588_gb300.visibility import orders_for_views
+    from gpu_util import PIXEL_TOL, rel_l2
+    sc, off, boxes, cams = _slabs()
+    orders = orders_for_views(boxes, cams)
+    npx = sum(3 * c.width * c.height for c in cams)
+    rng = np.random.default_rng(4)
+    dL = torch.from_numpy(rng.standard_normal(npx).astype(np.float32)).cuda()
+    img_s, T_s, g_s, cnt = _run(ctx, sc, off, cams, orders, dL)
+    img_f, T_f, g_f, cnt_f = _run(ctx, sc, off, cams, None, dL)
+    assert cnt_f["skipped_items"] == 0
+    # the oracle's skip map for the same orders; same number of empty work items
+    refs = [O.render_view(sc, off, c, O.opts(), order=list(orders[v])) for v, c in enumerate(cams)]
+    assert cnt["skipped_items"] == sum(int(r["skip"].sum()) for r in refs) > 0
+    for v, (c, r) in enumerate(zip(cams, refs)):
+        ok = r["amb"] == 0
+        assert ok.mean() > 0.99
+        err = np.abs(img_s[v].cpu().numpy() - r["image"]).max(axis=0)
+        assert err[ok].max() <= PIXEL_TOL
+        # skipping changes nothing on this depth-separated scene
+        assert torch.equal(img_s[v], img_f[v])
+    assert torch.equal(T_s, T_f)
+    for k in GROUPS:
+        assert rel_l2(g_s[k].cpu().numpy(), g_f[k].cpu().numpy()) < 1e-5, k
+
+
+def test_skipping_backward_matches_oracle(ctx):
+    from paper_2606_18588_gb300.visibility import orders_for_views
+    from gpu_util import GRAD_TOL, rel_l2
+    sc, off, boxes, cams = _slabs()
+    cams = cams[:1]
+    orders = orders_for_views(boxes, cams)
+    c = cams[0]
+    ref = O.render_view(sc, off, c, O.opts(), order=list(orders[0]))
+    ok = (ref["amb"] == 0).astype(np.float64)
+    rng = np.random.default_rng(6)
+    dLdC = rng.standard_normal((3, c.height, c.width)) * ok[None]
+    dL = torch.from_numpy(dLdC.reshape(-1).astype(np.float32)).cuda()
+    _, _, g, _ = _run(ctx, sc, off, cams, orders, dL)
+    g_ref = O.backward_view(sc, off, c, dLdC, None, O.opts(), order=list(orders[0]))
+    errs = {k: rel_l2(g[k].cpu().numpy(), gr) for k, gr in zip(GROUPS, g_ref)}
+    assert all(e <= GRAD_TOL for e in errs.values()), errs
+
+
+@pytest.mark.parametrize("tile", [8, 32])
+def test_skipping_is_tile_size_independent(ctx, tile):
+    # the skip test runs per work item, so other tile sides skip other pixel sets; the
+    # images stay those of the render without skipping on this scene
+    from paper_2606_18588_gb300.visibility import orders_for_views
+    sc, off, boxes, cams = _slabs()
+    orders = orders_for_views(boxes, cams)
+    img_s, _, _, cnt = _run(ctx, sc, off, cams, orders, tile=tile)
+    img_f, _, _, _ = _run(ctx, sc, off, cams, None, tile=16)
+    assert cnt["skipped_items"] > 0
+    for a, b in zip(img_s, img_f):
+        assert torch.equal(a, b)
+
+
+def test_skipping_on_a_cluster_scene(ctx):
+    # k-d cells of a cluster scene: Gaussians near a split plane can put a pixel's subsets
+    # out of BSP order.  Wherever the Eq. 5 order of the non-empty subsets (normalised-depth
+    # keys of the full render, no near ties) equals their BSP order, skipping must change
+    # nothing; the other pixels are few
+    from paper_2606_18588_gb300 import splx as S
+    from paper_2606_18588_gb300.visibility import orders_for_views
+    from gpu_util import render_view, to_device
+    sc, off, boxes, cams = I.cluster_case(120_000, 9, 8, 3, [(160, 120), (96, 64)])
+    orders = orders_for_views(boxes, cams)
+    img_s, _, _, cnt = _run(ctx, sc, off, cams, orders)
+    img_f, _, _, _ = _run(ctx, sc, off, cams, None)
+    assert cnt["skipped_items"] > 0
+    dev = to_device(sc)
+    agree_all = 0
+    for v, c in enumerate(cams):
+        _, _, parts, states = render_view(ctx, dev, off, c, S.opts(), sc.sh_degree)
+        for st in states:
+            st.close()
+        Tm = np.stack([p["T"].cpu().numpy() for p in parts]).astype(np.float64)
+        Dm = np.stack([p["depth"].cpu().numpy() for p in parts]).astype(np.float64)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            key = np.where(Tm < 1.0, Dm / (1.0 - Tm), np.inf)
+        K = len(off) - 1
+        rank = np.empty(K, np.int64)
+        rank[orders[v]] = np.arange(K)
+        ks = np.sort(key, axis=0)
+        fin = np.isfinite(ks[1:]) & np.isfinite(ks[:-1])
+        tie = (fin & (np.abs(ks[1:] - ks[:-1]) <= 1e-5 * np.abs(ks[1:]))).any(axis=0)
+        # BSP order of the non-empty subsets equals their key order
+        by_key = np.argsort(key, axis=0, kind="stable")
+        agree = np.ones(key.shape[1:], bool)
+        prev = np.full(key.shape[1:], -1)
+        for j in range(K):
+            m = by_key[j]
+            nonempty = np.take_along_axis(np.isfinite(key), m[None], 0)[0]
+            r = rank[m]
+            agree &= ~nonempty | (r > prev)
+            prev = np.where(nonempty, r, prev)
+        ok = agree & ~tie
+        same = torch.eq(img_s[v], img_f[v]).all(dim=0).cpu().numpy()
+        assert same[ok].all(), (v, int((~same[ok]).sum()))
+        agree_all += ok.mean()
+    assert agree_all / len(cams) > 0.85  # 93% on this scene
+
+
+def test_set_order_rejects_bad_orders(ctx):
+    from paper_2606_18588_gb300 import splx as S
+    sc, off, boxes, cams = _slabs()
+    b, _ = _batch(ctx, sc, off, cams, None)
+    with pytest.raises(S.SplxError):
+        b.set_order(np.array([[0, 0, 1], [0, 1, 2]]))
+    with pytest.raises(S.SplxError):
+        b.set_order(np.array([[0, 1, 3], [0, 1, 2]]))
+    b.set_order(np.array([[2, 1, 0], [0, 1, 2]]))
+    b.set_order(None)
+    b.close()

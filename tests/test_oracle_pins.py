@@ -542,3 +542,96 @@ def test_oracle_regression_fixture():
                          None, o)
     np.testing.assert_allclose(gr[0], np.asarray(g["grad_means"]), rtol=1e-9, atol=1e-12)
     np.testing.assert_allclose(gr[3], np.asarray(g["grad_opacity_logits"]), rtol=1e-9, atol=1e-12)
+
+
+# --------------------------------------------------------------------------- saturation skipping
+def test_cell_order_is_a_visibility_order():
+    # for every ordered pair (i before j) some axis-aligned plane separates the two cells
+    # with the eye not strictly on j's side (what a BSP's front-to-back order guarantees);
+    # the product's implementation gives the same order
+    from paper_2606_18588_gb300 import visibility as Vz
+    rng = np.random.default_rng(5)
+    for K in (2, 4, 8, 16):
+        means = rng.normal(0.0, 3.0, (4000, 3))
+        _, _, boxes = I.kd_partition(means.astype(np.float32), K)
+        for _ in range(12):
+            eye = rng.uniform(-12.0, 12.0, 3)
+            order = O.cell_order(boxes, eye)
+            assert sorted(order) == list(range(K))
+            assert order == Vz.front_to_back(boxes, eye)
+            for a in range(K):
+                for c in range(a + 1, K):
+                    i, j = order[a], order[c]
+                    lo_i, hi_i, lo_j, hi_j = boxes[i, 0], boxes[i, 1], boxes[j, 0], boxes[j, 1]
+                    ok = any((hi_i[x] <= lo_j[x] and eye[x] <= lo_j[x]) or
+                             (lo_i[x] >= hi_j[x] and eye[x] >= hi_j[x]) for x in range(3))
+                    assert ok, (K, eye, order, i, j)
+
+
+def _saturating_slabs(seed):
+    """Three dense opaque slabs one behind the other (camera at z = -3 looking along +z),
+    and the three cells split at z = -0.4 and z = 0.4."""
+    rng = np.random.default_rng(seed)
+    per = (4000, 4000, 4000)
+    means, ls, logits = [], [], []
+    for k, n in enumerate(per):
+        m = rng.uniform(-1.8, 1.8, (n, 3))
+        m[:, 2] = -0.8 + 0.8 * k + rng.uniform(-0.15, 0.15, n)
+        means.append(m)
+        ls.append(rng.normal(-2.6, 0.15, (n, 3)))
+        logits.append(rng.normal(4.0, 0.5, n))
+    n = sum(per)
+    sc = _scene(np.concatenate(means), np.concatenate(ls), rng.standard_normal((n, 4)),
+                np.concatenate(logits), rgb=rng.uniform(0, 1, (n, 3)))
+    offsets = np.concatenate([[0], np.cumsum(per)])
+    inf = np.inf
+    boxes = np.array([[[-inf, -inf, -inf], [inf, inf, -0.4]],
+                      [[-inf, -inf, -0.4], [inf, inf, 0.4]],
+                      [[-inf, -inf, 0.4], [inf, inf, inf]]])
+    return sc, offsets, boxes
+
+
+def test_saturation_skipping_leaves_the_image_and_gradients_unchanged():
+    # subsets rendered front to back; a tile of a later subset is left empty when the
+    # prefix transmittance is below eps_comp at all its pixels.  The composite skips such
+    # subsets per pixel anyway, so on a depth-separated scene images and gradients are
+    # exactly those of the full render
+    sc, off, boxes = _saturating_slabs(21)
+    cam = _cam(64, 48)
+    order = O.cell_order(boxes, cam.eye)
+    assert order == [0, 1, 2]
+    o = O.opts()
+    full = O.render_view(sc, off, cam, o)
+    skipr = O.render_view(sc, off, cam, o, order=order)
+    B = 16
+    tw, th = (cam.width + B - 1) // B, (cam.height + B - 1) // B
+    assert skipr["skip"][0].sum() == 0 and skipr["skip"][2].sum() > 0
+    # every skip decision follows from the prefix of the returned partials
+    prefix = np.ones((cam.height, cam.width))
+    for r, m in enumerate(order):
+        pad = np.zeros((th * B, tw * B))
+        pad[:cam.height, :cam.width] = prefix
+        tmax = pad.reshape(th, B, tw, B).max(axis=(1, 3)).reshape(-1)
+        expect = (tmax < o.eps_comp) if r > 0 else np.zeros(tw * th, bool)
+        assert np.array_equal(skipr["skip"][m].astype(bool), expect)
+        prefix = prefix * skipr["Tp"][m]
+    np.testing.assert_allclose(skipr["image"], full["image"], atol=1e-12, rtol=0)
+    np.testing.assert_allclose(skipr["T"], full["T"], atol=1e-12, rtol=0)
+    rng = np.random.default_rng(2)
+    dC = rng.standard_normal((3, cam.height, cam.width))
+    g_full = O.backward_view(sc, off, cam, dC, None, o)
+    g_skip = O.backward_view(sc, off, cam, dC, None, o, order=order)
+    for a, b in zip(g_full, g_skip):
+        np.testing.assert_allclose(b, a, atol=1e-12, rtol=1e-10)
+
+
+def test_saturation_skipping_drops_a_front_subset_when_ordered_wrongly():
+    # the skip is only as good as the order: rendering back to front skips tiles of the
+    # front slab and changes the image (the pins above are not vacuous)
+    sc, off, boxes = _saturating_slabs(22)
+    cam = _cam(64, 48)
+    o = O.opts()
+    full = O.render_view(sc, off, cam, o)
+    wrong = O.render_view(sc, off, cam, o, order=[2, 1, 0])
+    assert wrong["skip"][0].sum() > 0
+    assert np.abs(wrong["image"] - full["image"]).max() > 1e-2
