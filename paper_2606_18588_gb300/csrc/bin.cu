@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(256) k_fill(const BatchDev b) {
   int64_t tbase = 0;
   uint64_t key = 0;
   TileCull tc = tile_cull_prep(0.f, 0.f, 1.f, 0.f, 1.f, -1.0f);
+  uint32_t hits = 0;
   if (tiles) {
     const int k = subset_of(b, g);
     const ViewDev& cam = b.views[v];
@@ -170,8 +171,13 @@ __global__ void __launch_bounds__(256) k_fill(const BatchDev b) {
     ty0 = ry0 / B_;
     const int tx1 = rx1 / B_;
     tw = tx1 - tx0 + 1;
-    const float4 ra = r->a, rd = r->d;  // rd: spec conic and threshold of the tile test
-    tc = tile_cull_prep(ra.x, ra.y, rd.x, rd.y, rd.z, rd.w);
+    const float4 rd = r->d;  // the tile test's pass bits, or its inputs (> 32 tiles)
+    if (tiles <= 32u) {
+      hits = __float_as_uint(rd.w);
+    } else {
+      const float4 ra = r->a;
+      tc = tile_cull_prep(ra.x, ra.y, rd.x, rd.y, rd.z, rd.w);
+    }
     tiles_x = cam.tiles_x;
     tbase = b.tile_base[v] + (int64_t)k * cam.tiles_x * cam.tiles_y + (int64_t)ty0 * cam.tiles_x + tx0;
     key = ((uint64_t)__float_as_uint(rb.z) << 32) | (uint64_t)(uint32_t)g;
@@ -182,7 +188,9 @@ __global__ void __launch_bounds__(256) k_fill(const BatchDev b) {
   int jx = 0, jy = 0;  // column / row of the j-th tile inside the rectangle
   for (int j = 0; j < maxt; ++j) {
     unsigned t = 0xFFFFFFFFu;
-    if (j < (int)tiles && tile_hits_spec(tc, rx0, rx1, ry0, ry1, tx0 + jx, ty0 + jy, b.tile))
+    if (j < (int)tiles && (tiles <= 32u ? ((hits >> j) & 1u) != 0
+                                        : tile_hits_spec(tc, rx0, rx1, ry0, ry1, tx0 + jx,
+                                                         ty0 + jy, b.tile)))
       t = (unsigned)(tbase + jy * tiles_x + jx);
     if (++jx == tw) { jx = 0; ++jy; }
     const unsigned peers = __match_any_sync(lanes, t);

@@ -61,8 +61,9 @@ struct ImgDev {
 //   a = (u, v, qa, qb)      2-D mean, conic scaled by -log2(e)/2 ... see project.cu
 //   b = (qc, opacity, depth, rect_x)   rect_x = x0 | x1 << 16 (bit pattern)
 //   c = (r, g, b, rect_y)              rect_y = y0 | y1 << 16
-//   d = (A, B, C, q_max)     conic and tile-test threshold in the binning specification
-//                            (inputs of the tile test, read again by fill)
+//   d = (A, B, C, q_max | hits)   conic and tile-test threshold in the binning
+//                            specification; w holds instead the pass bits of the
+//                            rectangle's tiles when it spans at most 32 (read by fill)
 struct Rec {
   float4 a, b, c, d;
 };

@@ -130,10 +130,8 @@ __global__ void __launch_bounds__(256, 4) k_project(const BatchDev b) {
       r.b = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFu));
       r.c = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFu));
     }
-    // the tile test's inputs, so that fill repeats exactly the same decisions
-    r.d = make_float4(sA, sB, sC, so.visible ? qmax : -1.0f);
     Rec* dst = b.rec + (int64_t)v * b.N + g;
-    dst->a = r.a; dst->b = r.b; dst->c = r.c; dst->d = r.d;
+    dst->a = r.a; dst->b = r.b; dst->c = r.c;
     b.counts[(int64_t)v * b.N + g] = tiles;
     // count this Gaussian in every tile of its rectangle that passes the tile test (the
     // segment sizes of the binning); lanes that hit the same tile add together
@@ -147,16 +145,23 @@ __global__ void __launch_bounds__(256, 4) k_project(const BatchDev b) {
     int jx = 0, jy = 0;  // column / row of the j-th tile inside the rectangle
     const int tx0 = so.visible ? so.x0 / b.tile : 0, ty0 = so.visible ? so.y0 / b.tile : 0;
     const TileCull tc = tile_cull_prep(so.u, so.v, sA, sB, sC, so.visible ? qmax : -1.0f);
+    uint32_t hits = 0;  // bit j: the j-th tile of the rectangle passes the tile test
     for (int j = 0; j < maxt; ++j) {
       unsigned t = 0xFFFFFFFFu;
       if (j < (int)tiles &&
-          tile_hits_spec(tc, so.x0, so.x1, so.y0, so.y1, tx0 + jx, ty0 + jy, b.tile))
+          tile_hits_spec(tc, so.x0, so.x1, so.y0, so.y1, tx0 + jx, ty0 + jy, b.tile)) {
         t = (unsigned)(tbase + jy * cam.tiles_x + jx);
+        if (j < 32) hits |= 1u << j;
+      }
       if (++jx == tw) { jx = 0; ++jy; }
       const unsigned peers = __match_any_sync(lanes, t);
       if (t != 0xFFFFFFFFu && (threadIdx.x & 31) == __ffs(peers) - 1)
         atomicAdd(&b.tile_cnt[t], (unsigned)__popc(peers));
     }
+    // what fill needs to repeat exactly these decisions: the pass bits of the rectangle's
+    // tiles when there are at most 32 of them, else the test's inputs
+    dst->d = make_float4(sA, sB, sC,
+                         tiles <= 32u ? __uint_as_float(hits) : (so.visible ? qmax : -1.0f));
   }
 }
 

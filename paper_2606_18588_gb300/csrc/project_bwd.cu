@@ -77,8 +77,10 @@ __device__ __forceinline__ void sh_dir_grad(float x, float y, float z, const flo
 }
 }  // namespace
 
+constexpr int kProjBwdThreads = 128;
+
 template <int DEG>
-__global__ void __launch_bounds__(128) k_project_bwd(const BatchDev b, const GradTable gt) {
+__global__ void __launch_bounds__(kProjBwdThreads, 4) k_project_bwd(const BatchDev b, const GradTable gt) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= b.N) return;
   const int k = subset_of(b, g);
@@ -102,23 +104,34 @@ __global__ void __launch_bounds__(128) k_project_bwd(const BatchDev b, const Gra
 #pragma unroll
     for (int c = 0; c < 3; ++c) M[3 * r + c] = Rq[3 * r + c] * s[c];
   const float o = 1.0f / (1.0f + __expf(-S.opacity_logits[i]));
-  float sh[NC * 3];
-#pragma unroll
-  for (int e = 0; e < NC * 3; ++e) sh[e] = S.sh[i * NC * 3 + e];
+  // SH coefficients are read per visible view (L1-resident) and their gradient sums live in
+  // shared memory (one column per thread): 96 fewer registers, so more warps hide the
+  // latency of the per-view 2-D gradient loads
+  const float* shp = S.sh + i * NC * 3;
+  __shared__ float s_gsh[NC * 3 * kProjBwdThreads];
+  float* gsh = s_gsh + threadIdx.x;  // element e at gsh[e * kProjBwdThreads]
 
   float gm[3] = {0.f, 0.f, 0.f}, gM[9];
 #pragma unroll
   for (int e = 0; e < 9; ++e) gM[e] = 0.f;
   float glogit = 0.f;
-  float gsh[NC * 3];
 #pragma unroll
-  for (int e = 0; e < NC * 3; ++e) gsh[e] = 0.f;
+  for (int e = 0; e < NC * 3; ++e) gsh[e * kProjBwdThreads] = 0.f;
   bool any = false;
 
+  // the next view's 2-D gradient is loaded while this view's is processed
+  float4 nG0 = b.grad2d[g * 3], nG1 = b.grad2d[g * 3 + 1];
+  float ngb = b.grad2d[g * 3 + 2].x;
   for (int v = 0; v < b.V; ++v) {
     float4* gp = b.grad2d + ((int64_t)v * b.N + g) * 3;
-    const float4 G0 = gp[0], G1 = gp[1];
-    const float gbl = gp[2].x;
+    const float4 G0 = nG0, G1 = nG1;
+    const float gbl = ngb;
+    if (v + 1 < b.V) {
+      const float4* np = gp + (int64_t)b.N * 3;
+      nG0 = np[0];
+      nG1 = np[1];
+      ngb = np[2].x;
+    }
     if (G0.x == 0.f && G0.y == 0.f && G0.z == 0.f && G0.w == 0.f && G1.x == 0.f && G1.y == 0.f &&
         G1.z == 0.f && G1.w == 0.f && gbl == 0.f)
       continue;
@@ -174,16 +187,17 @@ __global__ void __launch_bounds__(128) k_project_bwd(const BatchDev b, const Gra
     for (int ch = 0; ch < 3; ++ch) {
       float raw = 0.5f;
 #pragma unroll
-      for (int kk = 0; kk < NC; ++kk) raw = fmaf(Y[kk], sh[3 * kk + ch], raw);
+      for (int kk = 0; kk < NC; ++kk) raw = fmaf(Y[kk], __ldg(shp + 3 * kk + ch), raw);
       gc[ch] = raw < 0.0f ? 0.0f : gcol[ch];
     }
     float w[NC];
 #pragma unroll
     for (int kk = 0; kk < NC; ++kk) {
-      gsh[3 * kk + 0] += Y[kk] * gc[0];
-      gsh[3 * kk + 1] += Y[kk] * gc[1];
-      gsh[3 * kk + 2] += Y[kk] * gc[2];
-      w[kk] = sh[3 * kk] * gc[0] + sh[3 * kk + 1] * gc[1] + sh[3 * kk + 2] * gc[2];
+      gsh[(3 * kk + 0) * kProjBwdThreads] += Y[kk] * gc[0];
+      gsh[(3 * kk + 1) * kProjBwdThreads] += Y[kk] * gc[1];
+      gsh[(3 * kk + 2) * kProjBwdThreads] += Y[kk] * gc[2];
+      w[kk] = __ldg(shp + 3 * kk) * gc[0] + __ldg(shp + 3 * kk + 1) * gc[1] +
+              __ldg(shp + 3 * kk + 2) * gc[2];
     }
     if (DEG > 0) {
       float gd[3];
@@ -276,11 +290,11 @@ __global__ void __launch_bounds__(128) k_project_bwd(const BatchDev b, const Gra
   *gq4 = cur;
   P[3][i] += glogit;
 #pragma unroll
-  for (int e = 0; e < NC * 3; ++e) P[4][i * NC * 3 + e] += gsh[e];
+  for (int e = 0; e < NC * 3; ++e) P[4][i * NC * 3 + e] += gsh[e * kProjBwdThreads];
 }
 
 void launch_project_bwd(const BatchDev& b, const GradTable& gt, cudaStream_t s) {
-  const int threads = 128;
+  const int threads = kProjBwdThreads;
   const int64_t blocks = (b.N + threads - 1) / threads;
   if (blocks == 0) return;
   switch (b.sh_degree) {
@@ -303,15 +317,30 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, float* __re
                                               float b1, float b2, float eps, int64_t step_host,
                                               const int64_t* __restrict__ step_dev, bool zero_grad,
                                               bool vec4) {
-  const int64_t step = step_dev ? *step_dev : step_host;
-  const double bc1 = 1.0 - pow((double)b1, (double)step);
-  const double bc2 = 1.0 - pow((double)b2, (double)step);
-  const float step_lr = (float)(lr_in / bc1), step_lr_rest = (float)(lr_rest_in / bc1);
-  const float bc2_sqrt_inv = (float)(1.0 / sqrt(bc2));
+  // bias corrections in double precision, once per CTA (FP64 is slow on this part)
+  __shared__ float s_sc[3];
+  if (threadIdx.x == 0) {
+    const int64_t step = step_dev ? *step_dev : step_host;
+    const double bc1 = 1.0 - pow((double)b1, (double)step);
+    const double bc2 = 1.0 - pow((double)b2, (double)step);
+    s_sc[0] = (float)(lr_in / bc1);
+    s_sc[1] = (float)(lr_rest_in / bc1);
+    s_sc[2] = (float)(1.0 / sqrt(bc2));
+  }
+  __syncthreads();
+  const float step_lr = s_sc[0], step_lr_rest = s_sc[1], bc2_sqrt_inv = s_sc[2];
   const int64_t n4 = vec4 ? (n >> 2) : 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const float ob1 = 1.0f - b1, ob2 = 1.0f - b2;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
+  // SH learning rates: element idx takes lr_rest when idx % sh_stride >= 3.  When
+  // sh_stride is a multiple of 4 the float4 q starts at (q % (sh_stride / 4)) * 4 within
+  // its Gaussian, kept incrementally (no division per element)
+  const bool sh4 = sh_stride > 0 && (sh_stride & 3) == 0;
+  const int64_t m4 = sh4 ? (sh_stride >> 2) : 1;
+  const int64_t q0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t rem = q0 % m4;
+  const int64_t rem_step = stride % m4;
+  for (int64_t q = q0; q < n4; q += stride) {
     float4 pp = reinterpret_cast<float4*>(p)[q];
     const float4 gg = reinterpret_cast<const float4*>(g)[q];
     float4 mm = reinterpret_cast<float4*>(m)[q];
@@ -322,8 +351,12 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, float* __re
     float* ve = &vv.x;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const int64_t idx = 4 * q + e;
-      const float lr = (sh_stride > 0 && (idx % sh_stride) >= 3) ? step_lr_rest : step_lr;
+      float lr = step_lr;
+      if (sh4) {
+        if (rem != 0 || e >= 3) lr = step_lr_rest;
+      } else if (sh_stride > 0 && ((4 * q + e) % sh_stride) >= 3) {
+        lr = step_lr_rest;
+      }
       me[e] = b1 * me[e] + ob1 * ge[e];
       ve[e] = b2 * ve[e] + ob2 * ge[e] * ge[e];
       pe[e] -= lr * me[e] / (sqrtf(ve[e]) * bc2_sqrt_inv + eps);
@@ -332,6 +365,8 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, float* __re
     reinterpret_cast<float4*>(m)[q] = mm;
     reinterpret_cast<float4*>(v)[q] = vv;
     if (zero_grad) reinterpret_cast<float4*>(g)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    rem += rem_step;
+    if (rem >= m4) rem -= m4;
   }
   for (int64_t idx = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
     const float lr = (sh_stride > 0 && (idx % sh_stride) >= 3) ? step_lr_rest : step_lr;
