@@ -467,10 +467,15 @@ int blend_pixel(int px, int py, const int32_t* lst, int64_t cnt, const std::vect
     const double raw = q.o * ex;
     const int clamped = raw > o.alpha_max;
     const double alpha = clamped ? o.alpha_max : raw;
-    if (std::fabs(alpha - o.alpha_min) <= o.amb_alpha * o.alpha_min) amb |= AMB_ALPHA;
+    // alpha's relative error in FP32 is the exponent's absolute error, which grows with
+    // the magnitude of its terms (they cancel for elongated Gaussians): the alpha and
+    // T-stop margins include it
+    const double rel_alpha = clamped ? 0.0 : 0.5 * o.amb_power * (std::fabs(t1) + std::fabs(t2) + std::fabs(t3));
+    if (std::fabs(alpha - o.alpha_min) <= (o.amb_alpha + rel_alpha) * o.alpha_min) amb |= AMB_ALPHA;
     if (alpha < o.alpha_min) continue;
     const double Tn = T * (1.0 - alpha);
-    if (o.eps_T > 0.0 && std::fabs(Tn - o.eps_T) <= o.amb_T * o.eps_T) amb |= AMB_TSTOP;
+    const double rel_T = o.amb_T + rel_alpha * alpha / (1.0 - alpha);
+    if (o.eps_T > 0.0 && std::fabs(Tn - o.eps_T) <= rel_T * o.eps_T) amb |= AMB_TSTOP;
     if (Tn < o.eps_T) break;
     const double w = alpha * T;
     for (int ch = 0; ch < 3; ++ch) C[ch] += q.col[ch] * w;

@@ -81,9 +81,10 @@ __global__ void __launch_bounds__(256, 4) k_project(const BatchDev b) {
   const float* shp = S.sh + i * (NC * 3);
   const bool sh_vec = (NC * 3) % 4 == 0 && (reinterpret_cast<uintptr_t>(shp) & 15) == 0;
 
+  const SpecG G = spec_gaussian(ls, q);  // view-independent part of the specification
   for (int v = 0; v < b.V; ++v) {
     const ViewDev& cam = b.views[v];
-    const SpecOut so = bin_spec(m, ls, q, cam.R, cam.t, cam.fx, cam.fy, cam.cx, cam.cy, cam.W,
+    const SpecOut so = bin_spec(m, G, cam.R, cam.t, cam.fx, cam.fy, cam.cx, cam.cy, cam.W,
                                 cam.H, cam.near_plane);
     Rec r;
     uint32_t tiles = 0;

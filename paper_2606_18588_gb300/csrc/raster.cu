@@ -337,33 +337,36 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
 
 template <int TS, int PPT, bool kCount>
 __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, float4* sA,
-                                         float4* sB, float4* sC, uint32_t* sG, int& s_maxlast) {
+                                         float4* sB, float4* sC, uint32_t* sG, int& s_maxlast,
+                                         float4* sQ) {
   constexpr int NTH = TS * TS / PPT;
   constexpr int NB = kNB;
   const TileInfo ti = decode_tile<TS, PPT>(b, id);
   const uint2 rg = b.ranges[id];
   const int64_t start = rg.x;
   const ImgDev im = b.imgs[ti.v * b.K + ti.k];
-  float4 gct[PPT];
-  float T[PPT], ninvTf[PPT], B0[PPT], B1[PPT], B2[PPT];
+  // composite adjoint of the thread's pixels: (dL/dC^m rgb, -T^m dL/dT^m) per slot, in
+  // shared memory (read only where a pixel takes an entry), which keeps registers down
+  float4* gq = sQ + threadIdx.x;  // slot i at gq[i * NTH]
+  float T[PPT], B0[PPT], B1[PPT], B2[PPT];
   int mylast[PPT];
   int tlast = -1;  // largest last over this thread's pixels
 #pragma unroll
   for (int i = 0; i < PPT; ++i) {
-    gct[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 gct = make_float4(0.f, 0.f, 0.f, 0.f);
     T[i] = 1.0f;
     mylast[i] = -1;
     B0[i] = B1[i] = B2[i] = 0.0f;
     const int px = ti.x + 8 * slot_col<PPT>(i), py = ti.y + 4 * slot_row<PPT>(i);
     if (px < ti.W && py < ti.H) {
       const int64_t p = (int64_t)py * ti.W + px;
-      gct[i] = im.gCT[p];
+      gct = im.gCT[p];
       T[i] = im.T[p];
       mylast[i] = im.last[p];
-      if (gct[i].x == 0.0f && gct[i].y == 0.0f && gct[i].z == 0.0f && gct[i].w == 0.0f)
+      if (gct.x == 0.0f && gct.y == 0.0f && gct.z == 0.0f && gct.w == 0.0f)
         mylast[i] = -1;
     }
-    ninvTf[i] = -T[i] * gct[i].w;
+    gq[i * NTH] = make_float4(gct.x, gct.y, gct.z, -T[i] * gct.w);
     tlast = mylast[i] > tlast ? mylast[i] : tlast;
   }
   if (threadIdx.x == 0) s_maxlast = -1;
@@ -434,12 +437,12 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
             const float rinv = rcp_approx(1.0f - alpha);
             const float Ti = T[i] * rinv;
             const float aT = alpha * Ti;
-            const float4 q = gct[i];
+            const float4 q = gq[i * NTH];
             gr = fmaf(q.x, aT, gr);
             gg = fmaf(q.y, aT, gg);
             gb = fmaf(q.z, aT, gb);
             const float ga = q.x * (Cv.x * Ti - B0[i] * rinv) + q.y * (Cv.y * Ti - B1[i] * rinv) +
-                             q.z * (Cv.z * Ti - B2[i] * rinv) + ninvTf[i] * rinv;
+                             q.z * (Cv.z * Ti - B2[i] * rinv) + q.w * rinv;
             if (!cl) {
               go = fmaf(ga, ex, go);
               const float gp = ga * alpha;  // dL/dpower
@@ -508,12 +511,13 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) 
 }
 
 template <int TS, int PPT, bool kCount, bool kPersist>
-__global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const BatchDev b) {
+__global__ void __launch_bounds__(TS * TS / PPT, TS == 16 ? 14 : 1) k_raster_bwd(const BatchDev b) {
   __shared__ float4 sA[kNB], sB[kNB], sC[kNB];
   __shared__ uint32_t sG[kNB];
+  __shared__ float4 sQ[TS * TS];  // composite adjoint per pixel slot
   __shared__ int s_maxlast;
   if constexpr (!kPersist) {
-    bwd_item<TS, PPT, kCount>(b, blockIdx.x, sA, sB, sC, sG, s_maxlast);
+    bwd_item<TS, PPT, kCount>(b, blockIdx.x, sA, sB, sC, sG, s_maxlast, sQ);
   } else {
     __shared__ long long s_id;
     for (;;) {
@@ -522,7 +526,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const BatchDev b) 
       __syncthreads();
       const int64_t id = s_id;
       if (id >= b.n_tiles) return;
-      bwd_item<TS, PPT, kCount>(b, id, sA, sB, sC, sG, s_maxlast);
+      bwd_item<TS, PPT, kCount>(b, id, sA, sB, sC, sG, s_maxlast, sQ);
     }
   }
 }

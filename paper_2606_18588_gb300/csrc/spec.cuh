@@ -49,22 +49,21 @@ struct SpecOut {
   float sx, sy, sz; // activated scales
 };
 
-// cam: R[9], t[3], fx, fy, cx, cy, W, H, near.
-__device__ __forceinline__ SpecOut bin_spec(const float m[3], const float ls[3],
-                                            const float q[4], const float* R, const float* tc,
-                                            float fx, float fy, float cx, float cy, int W, int H,
-                                            float near_plane) {
-  SpecOut o;
-  o.visible = false;
-  o.x0 = 0; o.x1 = -1; o.y0 = 0; o.y1 = -1;
-  const float tx = fa(fa(fa(fm(R[0], m[0]), fm(R[1], m[1])), fm(R[2], m[2])), tc[0]);
-  const float ty = fa(fa(fa(fm(R[3], m[0]), fm(R[4], m[1])), fm(R[5], m[2])), tc[1]);
-  const float tz = fa(fa(fa(fm(R[6], m[0]), fm(R[7], m[1])), fm(R[8], m[2])), tc[2]);
-  o.tz = tz;
-  if (!(tz > near_plane)) return o;
+// View-independent part of the specification: M = R(q) diag(exp(log_scale)).  `ok` is
+// false for a zero quaternion (never visible).
+struct SpecG {
+  bool ok;
+  float M[9];
+  float sx, sy, sz;
+};
 
+__device__ __forceinline__ SpecG spec_gaussian(const float ls[3], const float q[4]) {
+  SpecG G;
+  G.ok = false;
+  G.sx = G.sy = G.sz = 0.0f;
   const float qn = fa(fa(fa(fm(q[0], q[0]), fm(q[1], q[1])), fm(q[2], q[2])), fm(q[3], q[3]));
-  if (!(qn > 0.0f)) return o;
+  if (!(qn > 0.0f)) return G;
+  G.ok = true;
   const float inv = fd(1.0f, __fsqrt_rn(qn));
   const float w = fm(q[0], inv), x = fm(q[1], inv), y = fm(q[2], inv), z = fm(q[3], inv);
   float Rq[9];
@@ -78,12 +77,29 @@ __device__ __forceinline__ SpecOut bin_spec(const float m[3], const float ls[3],
   Rq[7] = fm(2.0f, fa(fm(y, z), fm(w, x)));
   Rq[8] = fs(1.0f, fm(2.0f, fa(fm(x, x), fm(y, y))));
   const float s[3] = {exp_spec(ls[0]), exp_spec(ls[1]), exp_spec(ls[2])};
-  o.sx = s[0]; o.sy = s[1]; o.sz = s[2];
-  float M[9];
+  G.sx = s[0]; G.sy = s[1]; G.sz = s[2];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) M[3 * i + j] = fm(Rq[3 * i + j], s[j]);
+    for (int j = 0; j < 3; ++j) G.M[3 * i + j] = fm(Rq[3 * i + j], s[j]);
+  return G;
+}
+
+// Per-view part; cam: R[9], t[3], fx, fy, cx, cy, W, H, near.
+__device__ __forceinline__ SpecOut bin_spec(const float m[3], const SpecG& G, const float* R,
+                                            const float* tc, float fx, float fy, float cx,
+                                            float cy, int W, int H, float near_plane) {
+  SpecOut o;
+  o.visible = false;
+  o.x0 = 0; o.x1 = -1; o.y0 = 0; o.y1 = -1;
+  const float tx = fa(fa(fa(fm(R[0], m[0]), fm(R[1], m[1])), fm(R[2], m[2])), tc[0]);
+  const float ty = fa(fa(fa(fm(R[3], m[0]), fm(R[4], m[1])), fm(R[5], m[2])), tc[1]);
+  const float tz = fa(fa(fa(fm(R[6], m[0]), fm(R[7], m[1])), fm(R[8], m[2])), tc[2]);
+  o.tz = tz;
+  o.sx = G.sx; o.sy = G.sy; o.sz = G.sz;
+  if (!(tz > near_plane)) return o;
+  if (!G.ok) return o;
+  const float* M = G.M;
   float V[9];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
