@@ -191,6 +191,15 @@ int splx_step_device(splx_ctx_t ctx, const splx_params* p, const splx_params* g,
  * loss_out is a device float (overwritten). */
 int splx_loss_l1(splx_ctx_t ctx, const float* img, const float* target, int64_t n,
                  float* loss_out, float* dL_dimg, splx_stream_t stream);
+/* Photometric loss with the structural term (Sec. 2 step 4: L = L_RGB + L_D-SSIM, read as
+ * (1 - lambda) L1 + lambda (1 - SSIM); lambda = 0.2 in 3DGS practice).  SSIM per channel
+ * with an 11 x 11 Gaussian window (sigma 1.5), zero padding, C1 = 0.01^2, C2 = 0.03^2; both
+ * terms are means over the 3 W H elements of the image [3][H][W].  loss_out (device float)
+ * is overwritten; dL_dimg [3][H][W] receives the gradient (overwritten).  lambda in [0, 1],
+ * else SPLX_ERR_INVALID.  Allocates its scratch (12 floats per pixel) from the context. */
+int splx_loss_l1_dssim(splx_ctx_t ctx, const float* img, const float* target, int32_t width,
+                       int32_t height, float lambda, float* loss_out, float* dL_dimg,
+                       splx_stream_t stream);
 
 /* ---- batched path: V views x K subsets per launch (conflict-free view consolidation
  *      of Sec. 4.3 in spirit: many independent views run in the same kernels) ------- */
@@ -237,6 +246,20 @@ int splx_batch_set_timing(splx_batch_t b, int enable);
  * SPLX_ERR_INVALID.  Applies to launches issued afterwards (a captured graph keeps the
  * shape it was captured with). */
 int splx_batch_set_launch(splx_batch_t b, int32_t raster_ctas_per_sm);
+/* The loss of splx_loss_l1_dssim over the batch's V views: rgb and target are the
+ * concatenated images (layout from splx_batch_layout), the means run over all 3 x total
+ * pixels, dL_drgb is concatenated like rgb.  Scratch (12 floats per pixel) is allocated by
+ * the first call, which must not be inside a stream capture (SPLX_ERR_STATE); later calls
+ * are capturable. */
+int splx_batch_loss_l1_dssim(splx_batch_t b, const float* rgb, const float* target,
+                             float lambda, float* loss_out, float* dL_drgb, splx_stream_t stream);
+/* Spatial visibility (Sec. 4.2 "spatial visibility", the region Omega_v^m of subset m in
+ * view v).  On by default for batches: the projection records, per (view, subset), the
+ * bounding tile rectangle of the subset's (Gaussian, tile) pairs; work items outside it
+ * have no pairs, so the rasterisers skip them and the composites neither write nor read
+ * their partial planes (treated as empty: C = 0, T = 1).  Results are identical with it on
+ * or off.  enable = 0 turns it off for launches issued afterwards. */
+int splx_batch_set_visibility(splx_batch_t b, int32_t enable);
 /* Saturation skipping (Sec. 4.2 "saturation skipping", with the composite's threshold
  * eps_comp of splx_opts).  order (host, [V][K]) is, per view, a front-to-back order of the
  * K subsets (for k-d cells: the BSP order from the camera centre).  Once set, the forward
@@ -253,12 +276,13 @@ int splx_batch_set_order(splx_batch_t b, const int32_t* order);
  * the batch's tile side (host outputs). */
 int splx_batch_max_ctas_per_sm(splx_batch_t b, int32_t* fwd, int32_t* bwd);
 int splx_batch_kernel_times(splx_batch_t b, float* ms_out);
-/* Work counters (synchronises; host array of 8): out[0] = (Gaussian, tile) pairs of the
+/* Work counters (synchronises; host array of 9): out[0] = (Gaussian, tile) pairs of the
  * last run; then, from the last EAGER run (replays of a captured graph do not count):
  * forward rasteriser out[1] = (thread, list entry) pairs examined, out[2] = (pixel,
  * entry) alpha evaluations, out[3] = (pixel, entry) blends; backward rasteriser out[4] =
  * (thread, entry) pairs, out[5] = alpha evaluations, out[6] = contributions (alpha >=
- * alpha_min); out[7] = (view, subset, tile) work items left empty by saturation skipping.
+ * alpha_min); out[7] = (view, subset, tile) work items left empty by saturation skipping;
+ * out[8] = work items outside their subset's visible region.
  * A thread owns 2 (8x8 tiles) or 4 (16x16, 32x32) pixels. */
 int splx_batch_counters(splx_batch_t b, int64_t* out, splx_stream_t stream);
 

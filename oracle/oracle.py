@@ -306,3 +306,64 @@ def cell_order(boxes, eye):
         stack.append(cut[1])  # popped after the whole first side
         stack.append(cut[0])
     return out
+
+
+# ---------------------------------------------------------------- D-SSIM loss (Sec. 2, step 4)
+# The photometric loss is L = (1 - lam) L1 + lam (1 - SSIM) (the paper's L_RGB + L_D-SSIM,
+# read with the 3DGS convention lam = 0.2).  SSIM per channel with an 11 x 11 Gaussian
+# window (sigma 1.5), zero padding outside the image, C1 = 0.01^2, C2 = 0.03^2; both terms
+# are means over all pixels and channels of all views.
+SSIM_C1, SSIM_C2 = 0.01 ** 2, 0.03 ** 2
+
+
+def ssim_window(size=11, sigma=1.5):
+    x = np.arange(size, dtype=np.float64) - (size - 1) / 2.0
+    g = np.exp(-x * x / (2.0 * sigma * sigma))
+    return g / g.sum()
+
+
+def _window_sum(a, w):
+    """sum_{i,j} w[i] w[j] a[y + i - r, x + j - r] with zeros outside [H, W]."""
+    r = len(w) // 2
+    H, W = a.shape
+    p = np.pad(a, r)
+    h = sum(w[k] * p[:, k:k + W] for k in range(len(w)))
+    return sum(w[k] * h[k:k + H, :] for k in range(len(w)))
+
+
+def ssim_terms(x, y, w=None):
+    """Per-pixel SSIM map S and its partial derivatives with respect to the local mean of x,
+    the local mean of x^2 and the local mean of x y (one channel, FP64)."""
+    w = ssim_window() if w is None else w
+    mx, my = _window_sum(x, w), _window_sum(y, w)
+    exx, eyy, exy = _window_sum(x * x, w), _window_sum(y * y, w), _window_sum(x * y, w)
+    vx, vy, cxy = exx - mx * mx, eyy - my * my, exy - mx * my
+    a1, a2 = 2 * mx * my + SSIM_C1, 2 * cxy + SSIM_C2
+    b1, b2 = mx * mx + my * my + SSIM_C1, vx + vy + SSIM_C2
+    S = a1 * a2 / (b1 * b2)
+    dS_dmx = (2 * my * a2 - 2 * my * a1) / (b1 * b2) - S * 2 * mx / b1 + S * 2 * mx / b2
+    dS_dexx = -S / b2
+    dS_dexy = 2 * a1 / (b1 * b2)
+    return S, dS_dmx, dS_dexx, dS_dexy
+
+
+def loss_l1_dssim(imgs, tgts, lam=0.2):
+    """(loss, [dL/dimg per view]) for lists of [3, H, W] images and targets (FP64)."""
+    w = ssim_window()
+    N = sum(a.size for a in imgs)
+    l1 = sum(np.abs(np.asarray(a, np.float64) - b).sum() for a, b in zip(imgs, tgts)) / N
+    ssum = 0.0
+    grads = []
+    for a, b in zip(imgs, tgts):
+        a = np.asarray(a, np.float64)
+        b = np.asarray(b, np.float64)
+        g = (1.0 - lam) * np.sign(a - b) / N
+        for ch in range(a.shape[0]):
+            S, dmx, dexx, dexy = ssim_terms(a[ch], b[ch], w)
+            ssum += S.sum()
+            # the window is symmetric, so the adjoint of the windowed sum is itself
+            dS = _window_sum(dmx, w) + 2 * a[ch] * _window_sum(dexx, w) + b[ch] * _window_sum(dexy, w)
+            g[ch] -= lam * dS / N
+        grads.append(g)
+    loss = (1.0 - lam) * l1 + lam * (1.0 - ssum / N)
+    return loss, grads

@@ -186,6 +186,8 @@ struct Plan {
   unsigned long long* work_ctr = nullptr;  // [2]: persistent rasterisers' work counters
   int persist_grid = 0;                    // persistent raster grid (0: one CTA per item)
   int32_t* order_d = nullptr;              // [V][K] front-to-back subset order (skipping on)
+  uint32_t* omega = nullptr;               // [V][K][4] visible regions (internal partials only)
+  bool visibility = false;                 // use omega (batches and server launches)
   float* tpre = nullptr;                   // [total pixels] prefix transmittance of the waves
   void* scan_temp = nullptr;
   int64_t capacity = 0, n_tiles = 0, total_pixels = 0;
@@ -236,6 +238,7 @@ struct Plan {
     b.counters = counters;
     b.persist_grid = persist_grid;
     b.work_ctr = work_ctr;
+    b.omega = visibility ? omega : nullptr;
     b.order = nullptr;  // set per launch by the forward's waves
     b.wave = 0;
     b.tpre = tpre;
@@ -256,7 +259,7 @@ struct Plan {
                    (void**)&keys_alt, (void**)&big_list, (void**)&big_count, (void**)&chunks,
                    (void**)&chunk_count, (void**)&ranges,
                    (void**)&grad2d, (void**)&scan_temp, (void**)&counters, (void**)&work_ctr,
-                   (void**)&order_d, (void**)&tpre};
+                   (void**)&order_d, (void**)&tpre, (void**)&omega};
     for (void** p : ps) free_ptr(*p, s);
     for (auto& e : ev)
       if (e) { cudaEventDestroy(e); e = nullptr; }
@@ -268,6 +271,8 @@ struct Plan {
     if (counters && !stream_capturing(s))
       CK(cudaMemsetAsync(counters, 0, kCounters * sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(n_tiles, 1), s));
+    if (visibility && omega)
+      CK(cudaMemsetAsync(omega, 0xFF, sizeof(uint32_t) * 4 * (size_t)V * K, s));
     CK(cudaMemsetAsync(big_count, 0, sizeof(unsigned), s));
     CK(cudaMemsetAsync(chunk_count, 0, sizeof(unsigned), s));
     mark(0, s);
@@ -371,6 +376,8 @@ struct splx_batch_s {
   float4* gCT = nullptr;       // [K * total_pixels]
   float* partial = nullptr;    // rgb [3 K P], T [K P], D [K P] (P = total pixels)
   int32_t* last = nullptr;     // [K P]
+  float* ssim_maps = nullptr;  // [3][3 P]: D-SSIM partial-derivative maps
+  double* ssim_sums = nullptr; // [2]: sum of SSIM, sum of |x - y|
   bool forward_done = false;
 };
 
@@ -405,6 +412,7 @@ int splx_create(splx_ctx_t* out, int device, size_t hbm_budget_bytes) {
     e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
+  if (e == cudaSuccess && ssim_init() != 0) e = cudaErrorInvalidValue;
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
   cudaSetDevice(prev);
   if (e != cudaSuccess) {
@@ -682,6 +690,30 @@ int splx_loss_l1(splx_ctx_t ctx, const float* img, const float* target, int64_t 
   return SPLX_OK;
 }
 
+int splx_loss_l1_dssim(splx_ctx_t ctx, const float* img, const float* target, int32_t width,
+                       int32_t height, float lambda, float* loss_out, float* dL_dimg,
+                       splx_stream_t stream) {
+  if (!ctx || !img || !target || !loss_out || !dL_dimg || width < 1 || height < 1 ||
+      !(lambda >= 0.0f) || !(lambda <= 1.0f))
+    return SPLX_ERR_INVALID;
+  CtxScope scope(ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const LossImgs L = make_loss_imgs(1, &width, &height);
+  const size_t n = 3 * (size_t)width * height;
+  float* maps = nullptr;
+  double* sums = nullptr;
+  int r;
+  if ((r = ctx_alloc_t(ctx, &maps, 3 * n, s))) return r;
+  if ((r = ctx_alloc_t(ctx, &sums, 2, s))) { ctx_free(ctx, maps, s); return r; }
+  launch_loss_l1_dssim(L, img, target, lambda, maps, maps + n, maps + 2 * n, sums, loss_out,
+                       dL_dimg, s);
+  const cudaError_t e = cudaGetLastError();
+  ctx_free(ctx, maps, s);
+  ctx_free(ctx, sums, s);
+  if (e != cudaSuccess) return cuda_fail(e, "loss_l1_dssim");
+  return SPLX_OK;
+}
+
 // ---------------------------------------------------------------- batch
 int splx_batch_create(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
                       const splx_camera* cams, int32_t V, const splx_opts* opts,
@@ -746,6 +778,8 @@ int splx_batch_create(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
   if ((r = ctx_alloc_t(ctx, &P.grad2d, (size_t)V * N * 3, s))) return fail(r);
   if ((r = ctx_alloc_t(ctx, &P.counters, kCounters, s))) return fail(r);
   if ((r = ctx_alloc_t(ctx, &P.work_ctr, 2, s))) return fail(r);
+  if ((r = ctx_alloc_t(ctx, &P.omega, (size_t)4 * V * K, s))) return fail(r);
+  P.visibility = true;
   cudaError_t e = cudaMemsetAsync(P.grad2d, 0, sizeof(float4) * 3 * (size_t)V * N, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(P.counters, 0, kCounters * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return fail(cuda_fail(e, "memset grad2d"));
@@ -872,6 +906,35 @@ int splx_batch_set_launch(splx_batch_t bt, int32_t raster_ctas_per_sm) {
   return SPLX_OK;
 }
 
+int splx_batch_loss_l1_dssim(splx_batch_t bt, const float* rgb, const float* target, float lambda,
+                             float* loss_out, float* dL_drgb, splx_stream_t stream) {
+  if (!bt || !rgb || !target || !loss_out || !dL_drgb || !(lambda >= 0.0f) || !(lambda <= 1.0f))
+    return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  CtxScope scope(P.ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<int> W(P.V), H(P.V);
+  for (int v = 0; v < P.V; ++v) { W[v] = P.views_h[v].W; H[v] = P.views_h[v].H; }
+  const LossImgs L = make_loss_imgs(P.V, W.data(), H.data());
+  const size_t n = 3 * (size_t)P.total_pixels;
+  int r;
+  if (!bt->ssim_maps) {
+    if (stream_capturing(s)) return SPLX_ERR_STATE;  // allocate in an eager call first
+    if ((r = ctx_alloc_t(P.ctx, &bt->ssim_maps, 3 * n, s))) return r;
+    if ((r = ctx_alloc_t(P.ctx, &bt->ssim_sums, 2, s))) return r;
+  }
+  launch_loss_l1_dssim(L, rgb, target, lambda, bt->ssim_maps, bt->ssim_maps + n,
+                       bt->ssim_maps + 2 * n, bt->ssim_sums, loss_out, dL_drgb, s);
+  CK_LAUNCH();
+  return SPLX_OK;
+}
+
+int splx_batch_set_visibility(splx_batch_t bt, int32_t enable) {
+  if (!bt || !bt->plan.omega) return SPLX_ERR_INVALID;
+  bt->plan.visibility = enable != 0;
+  return SPLX_OK;
+}
+
 int splx_batch_set_order(splx_batch_t bt, const int32_t* order) {
   if (!bt) return SPLX_ERR_INVALID;
   Plan& P = bt->plan;
@@ -965,6 +1028,8 @@ int splx_batch_destroy(splx_batch_t bt) {
   ctx_free(P.ctx, bt->gCT, nullptr);
   ctx_free(P.ctx, bt->partial, nullptr);
   ctx_free(P.ctx, bt->last, nullptr);
+  ctx_free(P.ctx, bt->ssim_maps, nullptr);
+  ctx_free(P.ctx, bt->ssim_sums, nullptr);
   cudaDeviceSynchronize();
   if (bt->pinned_cams) cudaFreeHost(bt->pinned_cams);
   delete bt;
@@ -1089,6 +1154,8 @@ int srv_start(splx_server_s* S, SrvLaunch& L) {
     }
   }
   if ((r = P.alloc_common(L.s))) return r;
+  if ((r = ctx_alloc_t(S->ctx, &P.omega, (size_t)4 * V * K, L.s))) return r;
+  P.visibility = true;
   if ((r = P.project_and_count(L.s))) return r;
   CK(cudaMemcpyAsync(L.total_h, P.tile_start + P.n_tiles, sizeof(uint32_t),
                      cudaMemcpyDeviceToHost, L.s));

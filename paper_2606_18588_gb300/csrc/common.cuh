@@ -9,7 +9,22 @@
 namespace splx {
 
 constexpr int kMaxK = 64;        // subsets per view
-constexpr int kCounters = 7;     // work counters of a batch (BatchDev::counters)
+constexpr int kCounters = 8;     // work counters of a batch (BatchDev::counters)
+constexpr int kMaxViews = 256;   // views per batch
+
+// Concatenated views of the D-SSIM loss: view v's [3][H][W] image at 3 * pix_off[v];
+// blk_off[v] = first (channel, 32 x 32 tile) work item of view v.
+struct LossImgs {
+  int V;
+  int W[kMaxViews], H[kMaxViews];
+  int64_t pix_off[kMaxViews + 1];
+  int64_t blk_off[kMaxViews + 1];
+};
+LossImgs make_loss_imgs(int V, const int* W, const int* H);
+int ssim_init();
+void launch_loss_l1_dssim(const LossImgs& L, const float* x, const float* y, float lam,
+                          float* dmx, float* dexx, float* dexy, double* sums, float* loss,
+                          float* dL, cudaStream_t s);
 
 // True while `s` is being captured into a CUDA graph.
 inline bool stream_capturing(cudaStream_t s) {
@@ -17,7 +32,6 @@ inline bool stream_capturing(cudaStream_t s) {
   cudaStreamIsCapturing(s, &cs);
   return cs != cudaStreamCaptureStatusNone;
 }
-constexpr int kMaxViews = 256;   // views per batch
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
@@ -100,8 +114,13 @@ struct BatchDev {
   // work counters (nullable; kept by eager runs): forward [0] thread-entries examined,
   // [1] (pixel, entry) alpha evaluations, [2] blends; backward [3] thread-entries,
   // [4] alpha evaluations, [5] contributions (alpha >= alpha_min); [6] work items left
-  // empty by saturation skipping
+  // empty by saturation skipping; [7] work items outside their subset's visible region
   unsigned long long* counters;
+  // spatial visibility (nullable): per (view, subset) the bounding tile rectangle of the
+  // subset's (Gaussian, tile) pairs as (min tx, min ty, ~max tx, ~max ty), built by the
+  // projection with atomicMin (all four start at 0xFFFFFFFF, i.e. empty).  Work items
+  // outside it have no pairs; their partial planes are neither written nor read.
+  uint32_t* omega;
   // saturation skipping (order != nullptr): the forward rasteriser runs in K waves; wave r
   // renders subset order[v * K + r] of every view v, and tpre [total pixels] holds the
   // product of the transmittances of the subsets rendered so far
@@ -182,5 +201,13 @@ __device__ __forceinline__ int view_of(const int64_t* base, int V, int64_t x) {
     if (base[mid] <= x) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+// Whether tile (tx, ty) of view v lies in subset k's visible region (always, if off).
+__device__ __forceinline__ bool in_omega(const BatchDev& b, int v, int k, int tx, int ty) {
+  if (!b.omega) return true;
+  const uint4 o = reinterpret_cast<const uint4*>(b.omega)[v * b.K + k];
+  const uint32_t x = (uint32_t)tx, y = (uint32_t)ty;
+  return x >= o.x && y >= o.y && x <= ~o.z && y <= ~o.w;
 }
 }  // namespace splx

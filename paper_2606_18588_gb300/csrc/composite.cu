@@ -18,12 +18,29 @@ struct PixOrder {
   float T[MK], key[MK];
   int ord[MK];
   int K;
+  uint64_t outside;  // bit m: the pixel's tile lies outside subset m's visible region
 
-  __device__ __forceinline__ void load(const BatchDev& b, int v, int64_t p) {
+  // Partials of subsets whose visible region misses the pixel's tile were never written:
+  // they are empty (C = 0, T = 1, D = 0) and are not read.
+  __device__ __forceinline__ void load(const BatchDev& b, int v, int64_t p, int W) {
     K = b.K;
+    outside = 0;
+    int tx = 0, ty = 0;
+    if (b.omega) {
+      const int sh = __ffs(b.tile) - 1;  // the tile side is a power of two
+      const uint32_t py = (uint32_t)p / (uint32_t)W;
+      tx = (int)(((uint32_t)p - py * (uint32_t)W) >> sh);
+      ty = (int)(py >> sh);
+    }
 #pragma unroll
     for (int m = 0; m < MK; ++m) {
       if (m < K) {
+        if (!in_omega(b, v, m, tx, ty)) {
+          outside |= 1ull << m;
+          T[m] = 1.0f;
+          key[m] = __int_as_float(0x7f800000);
+          continue;
+        }
         const ImgDev& im = b.imgs[v * b.K + m];
         const float t = im.T[p];
         const float d = im.D[p];
@@ -53,11 +70,12 @@ __global__ void __launch_bounds__(256) k_composite(const BatchDev b, int64_t tot
   const int64_t HW = (int64_t)cam.W * cam.H;
   const int64_t p = gp - b.pix_off[v];
   PixOrder<MK> po;
-  po.load(b, v, p);
+  po.load(b, v, p, cam.W);
   float P = 1.0f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
   for (int j = 0; j < po.K; ++j) {
     if (P < b.eps_comp) break;
     const int m = po.ord[j];
+    if ((po.outside >> m) & 1ull) continue;  // empty: adds nothing, T = 1
     const float* rgb = b.imgs[v * b.K + m].rgb;
     c0 = fmaf(rgb[p], P, c0);
     c1 = fmaf(rgb[HW + p], P, c1);
@@ -80,7 +98,7 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const BatchDev b, int64_t
   const int64_t HW = (int64_t)cam.W * cam.H;
   const int64_t p = gp - b.pix_off[v];
   PixOrder<MK> po;
-  po.load(b, v, p);
+  po.load(b, v, p, cam.W);
   float Pj[MK];
   float P = 1.0f;
   int L = 0;
@@ -97,6 +115,7 @@ __global__ void __launch_bounds__(256) k_composite_bwd(const BatchDev b, int64_t
   for (int j = po.K - 1; j >= 0; --j) {
     const int m = po.ord[j];
     const ImgDev& im = b.imgs[v * b.K + m];
+    if ((po.outside >> m) & 1ull) continue;  // empty and never rendered: T = 1, C = 0
     if (j >= L) {
       im.gCT[p] = make_float4(0.f, 0.f, 0.f, 0.f);
       continue;

@@ -147,17 +147,35 @@ __global__ void __launch_bounds__(256, 4) k_project(const BatchDev b) {
     const int tx0 = so.visible ? so.x0 / b.tile : 0, ty0 = so.visible ? so.y0 / b.tile : 0;
     const TileCull tc = tile_cull_prep(so.u, so.v, sA, sB, sC, so.visible ? qmax : -1.0f);
     uint32_t hits = 0;  // bit j: the j-th tile of the rectangle passes the tile test
+    bool any_pair = false;
     for (int j = 0; j < maxt; ++j) {
       unsigned t = 0xFFFFFFFFu;
       if (j < (int)tiles &&
           tile_hits_spec(tc, so.x0, so.x1, so.y0, so.y1, tx0 + jx, ty0 + jy, b.tile)) {
         t = (unsigned)(tbase + jy * cam.tiles_x + jx);
+        any_pair = true;
         if (j < 32) hits |= 1u << j;
       }
       if (++jx == tw) { jx = 0; ++jy; }
       const unsigned peers = __match_any_sync(lanes, t);
       if (t != 0xFFFFFFFFu && (threadIdx.x & 31) == __ffs(peers) - 1)
         atomicAdd(&b.tile_cnt[t], (unsigned)__popc(peers));
+    }
+    // spatial visibility: grow the subset's bounding tile rectangle in this view by this
+    // Gaussian's tile rectangle (lanes of one subset reduce first, one atomic each)
+    if (b.omega) {
+      const unsigned peers = __match_any_sync(lanes, any_pair ? k : -1);
+      if (any_pair) {
+        uint32_t e[4] = {(uint32_t)tx0, (uint32_t)ty0, ~(uint32_t)(so.x1 / b.tile),
+                         ~(uint32_t)(so.y1 / b.tile)};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) e[q] = __reduce_min_sync(peers, e[q]);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) {
+          uint32_t* om = b.omega + ((int64_t)v * b.K + k) * 4;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) atomicMin(om + q, e[q]);
+        }
+      }
     }
     // what fill needs to repeat exactly these decisions: the pass bits of the rectangle's
     // tiles when there are at most 32 of them, else the test's inputs

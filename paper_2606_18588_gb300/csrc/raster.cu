@@ -109,7 +109,7 @@ __device__ __forceinline__ void warp_reduce9(const float (&v)[9], int lane, floa
 // keeps many lanes busy.  (x, y) is the thread's pixel in slot 0; slot i adds
 // (8 (i & 1), 4 (i >> 1)) for PPT = 4 and (0, 4 i) for PPT = 2.
 struct TileInfo {
-  int v, k, x, y, W, H;
+  int v, k, x, y, W, H, tx, ty;
 };
 
 // Blocks of a warp's region (origin RX, RY) that the rectangle [x0,x1] x [y0,y1] meets:
@@ -165,6 +165,8 @@ __device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
   ti.k = (int)(rem / nt);
   const int64_t t = rem - (int64_t)ti.k * nt;
   const int tx = (int)(t % cam.tiles_x), ty = (int)(t / cam.tiles_x);
+  ti.tx = tx;
+  ti.ty = ty;
   const int w = (int)(threadIdx.x >> 5), l = (int)(threadIdx.x & 31);
   int rx0 = 0, ry0 = 0;
   if (PPT == 4) {
@@ -205,6 +207,19 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
   constexpr int NTH = TS * TS / PPT;
   constexpr int NB = kNB;
   const TileInfo ti = decode_tile<TS, PPT>(b, id);
+  if (!in_omega(b, ti.v, ti.k, ti.tx, ti.ty)) {
+    // outside the subset's visible region: no pairs; the composite never reads this tile.
+    // Its transmittance is 1, which the first saturation-skipping wave must still record.
+    if (kCount && threadIdx.x == 0 && b.counters) atomicAdd(b.counters + 7, 1ull);
+    if (b.order && b.wave == 0) {
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) {
+        const int px = ti.x + 8 * slot_col<PPT>(i), py = ti.y + 4 * slot_row<PPT>(i);
+        if (px < ti.W && py < ti.H) b.tpre[b.pix_off[ti.v] + (int64_t)py * ti.W + px] = 1.0f;
+      }
+    }
+    return;
+  }
   const uint2 rg = b.ranges[id];
   const int64_t start = rg.x, end = rg.y > rg.x ? rg.y : rg.x;
   const Rec* rec = b.rec + (int64_t)ti.v * b.N;
@@ -342,6 +357,7 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
   constexpr int NTH = TS * TS / PPT;
   constexpr int NB = kNB;
   const TileInfo ti = decode_tile<TS, PPT>(b, id);
+  if (!in_omega(b, ti.v, ti.k, ti.tx, ti.ty)) return;  // nothing written there, nothing to do
   const uint2 rg = b.ranges[id];
   const int64_t start = rg.x;
   const ImgDev im = b.imgs[ti.v * b.K + ti.k];

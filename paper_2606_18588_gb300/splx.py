@@ -92,6 +92,9 @@ _sigs = {
     "splx_batch_counters": (C.c_int, [_P, _P, _P]),
     "splx_batch_set_launch": (C.c_int, [_P, C.c_int32]),
     "splx_batch_set_order": (C.c_int, [_P, _P]),
+    "splx_batch_set_visibility": (C.c_int, [_P, C.c_int32]),
+    "splx_batch_loss_l1_dssim": (C.c_int, [_P, _P, _P, C.c_float, _P, _P, _P]),
+    "splx_loss_l1_dssim": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32, C.c_float, _P, _P, _P]),
     "splx_batch_max_ctas_per_sm": (C.c_int, [_P, _P, _P]),
     "splx_server_create": (C.c_int, [_P, _P, C.c_int32, _P, C.c_size_t, C.c_int32, C.c_int32,
                                      C.POINTER(_P)]),
@@ -325,6 +328,14 @@ def loss_l1(ctx: Context, img, target, loss_out, dL_dimg=None, stream=None):
                              _ptr(dL_dimg), _stream(stream)), "splx_loss_l1")
 
 
+def loss_l1_dssim(ctx: Context, img, target, loss_out, dL_dimg, lam=0.2, stream=None):
+    """(1 - lam) L1 + lam (1 - SSIM) of one [3, H, W] image."""
+    _, H, W = img.shape
+    _check(_lib.splx_loss_l1_dssim(ctx.h, _ptr(img), _ptr(target), int(W), int(H), float(lam),
+                                   _ptr(loss_out), _ptr(dL_dimg), _stream(stream)),
+           "splx_loss_l1_dssim")
+
+
 # ---------------------------------------------------------------- batched path
 class Server:
     """Render server over K resident subsets: continuous batching of camera requests
@@ -445,6 +456,16 @@ class Batch:
         """0: one rasteriser CTA per work item; n > 0: n persistent CTAs per SM."""
         _check(_lib.splx_batch_set_launch(self.h, int(raster_ctas_per_sm)), "splx_batch_set_launch")
 
+    def loss_l1_dssim(self, rgb, target, loss, dL, lam=0.2, stream=None):
+        """(1 - lam) L1 + lam (1 - SSIM) over the batch's views into loss[0], gradient into dL."""
+        _check(_lib.splx_batch_loss_l1_dssim(self.h, _ptr(rgb), _ptr(target), float(lam), _ptr(loss),
+                                             _ptr(dL), _stream(stream)), "splx_batch_loss_l1_dssim")
+
+    def set_visibility(self, enable: bool):
+        """Spatial visibility regions on (default) or off; results are identical."""
+        _check(_lib.splx_batch_set_visibility(self.h, int(bool(enable))),
+               "splx_batch_set_visibility")
+
     def set_order(self, order):
         """Saturation skipping with a [V, K] front-to-back subset order per view (None:
         off); see splx_batch_set_order."""
@@ -464,11 +485,11 @@ class Batch:
         return f.value, b.value
 
     def counters(self, stream=None) -> dict:
-        arr = (C.c_int64 * 8)()
+        arr = (C.c_int64 * 9)()
         _check(_lib.splx_batch_counters(self.h, arr, _stream(stream)), "splx_batch_counters")
         return dict(pairs=arr[0], entries_fwd=arr[1], alpha_fwd=arr[2], blended=arr[3],
                     entries_bwd=arr[4], alpha_bwd=arr[5], contrib_bwd=arr[6],
-                    skipped_items=arr[7])
+                    skipped_items=arr[7], outside_items=arr[8])
 
     def views(self, flat_rgb):
         """Split a concatenated rgb buffer into per-view [3,H,W] tensors."""

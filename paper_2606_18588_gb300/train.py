@@ -40,9 +40,11 @@ class BatchedStep:
 
     def __init__(self, ctx: S.Context, params: dict, offsets, sh_degree: int, cams, targets,
                  opts: S.Opts | None = None, lr=DEFAULT_LR, pair_capacity: int = 0,
-                 stream: torch.cuda.Stream | None = None, order=None):
+                 stream: torch.cuda.Stream | None = None, order=None, dssim: float = 0.0):
         """order: optional [V, K] front-to-back subset order per view, which turns on
-        saturation skipping (visibility.orders_for_views gives it for k-d cells)."""
+        saturation skipping (visibility.orders_for_views gives it for k-d cells).
+        dssim: weight lambda of the D-SSIM term (0: plain L1)."""
+        self.dssim = float(dssim)
         self.ctx, self.p, self.off, self.deg = ctx, params, np.asarray(offsets), sh_degree
         self.opts = opts or S.opts()
         self.stream = stream or torch.cuda.current_stream()
@@ -84,7 +86,10 @@ class BatchedStep:
         if ev[0] is not None: ev[0].record(s)
         self.batch.forward(self.rgb, None, stream=s)
         if ev[1] is not None: ev[1].record(s)
-        S.loss_l1(self.ctx, self.rgb, self.target, self.loss, self.dL, stream=s)
+        if self.dssim > 0.0:
+            self.batch.loss_l1_dssim(self.rgb, self.target, self.loss, self.dL, self.dssim, stream=s)
+        else:
+            S.loss_l1(self.ctx, self.rgb, self.target, self.loss, self.dL, stream=s)
         if ev[2] is not None: ev[2].record(s)
         self.batch.backward(self.dL, None, self._grads, stream=s)
         if ev[3] is not None: ev[3].record(s)

@@ -185,3 +185,35 @@ def test_autotuner_picks_a_timed_candidate(ctx, scene):
     assert r.ms == min(t[2] for t in r.table)
     for k in dev:  # the tuner never updates the parameters
         assert torch.equal(dev[k], before[k])
+
+
+def test_spatial_visibility_changes_nothing(ctx, scene):
+    # work items outside a subset's visible region are skipped and their partial planes
+    # neither written nor read; images are bit-identical with the regions off and
+    # gradients agree up to the order of the atomics
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import rel_l2, to_device, zeros_like_params
+    sc, off, cams = scene
+    dev = to_device(sc)
+    rng = np.random.default_rng(8)
+    out = {}
+    for vis in (True, False):
+        b = S.Batch(ctx, _subsets(dev, off, sc.sh_degree), cams, S.opts())
+        b.set_visibility(vis)
+        rgb = torch.empty(b.rgb_off[-1], device="cuda")
+        T = torch.empty(b.total_pixels, device="cuda")
+        b.forward(rgb, T)
+        if vis:
+            dL = torch.from_numpy(rng.standard_normal(b.rgb_off[-1]).astype(np.float32)).cuda()
+        g = zeros_like_params(dev)
+        b.backward(dL, None, _grads(g, off, sc.sh_degree))
+        torch.cuda.synchronize()
+        code, _ = b.status()
+        assert code == S.OK
+        out[vis] = (rgb, T, g, b.counters())
+        b.close()
+    assert out[True][3]["outside_items"] > 0 and out[False][3]["outside_items"] == 0
+    assert torch.equal(out[True][0], out[False][0])
+    assert torch.equal(out[True][1], out[False][1])
+    for k in GROUPS:
+        assert rel_l2(out[True][2][k].cpu().numpy(), out[False][2][k].cpu().numpy()) < 1e-5, k

@@ -184,3 +184,28 @@ def test_set_order_rejects_bad_orders(ctx):
     b.set_order(np.array([[2, 1, 0], [0, 1, 2]]))
     b.set_order(None)
     b.close()
+
+
+def test_skipping_with_and_without_visibility_regions(ctx):
+    # both on a cluster scene whose subsets cover parts of the images: the first wave must
+    # record T = 1 for tiles outside a subset's visible region
+    from paper_2606_18588_gb300 import splx as S
+    from paper_2606_18588_gb300.visibility import orders_for_views
+    from gpu_util import subset_struct, to_device
+    sc, off, boxes, cams = I.cluster_case(120_000, 9, 8, 3, [(160, 120), (96, 64)])
+    orders = orders_for_views(boxes, cams)
+    dev = to_device(sc)
+    subs = [subset_struct(dev, int(off[k]), int(off[k + 1]), sc.sh_degree) for k in range(8)]
+    res = {}
+    for vis in (True, False):
+        b = S.Batch(ctx, subs, cams, S.opts())
+        b.set_visibility(vis)
+        b.set_order(orders)
+        rgb = torch.empty(b.rgb_off[-1], device="cuda")
+        for _ in range(2):  # a second forward must not see the first one's leftovers
+            b.forward(rgb)
+        torch.cuda.synchronize()
+        res[vis] = (rgb.clone(), b.counters())
+        b.close()
+    assert res[True][1]["outside_items"] > 0 and res[True][1]["skipped_items"] > 0
+    assert torch.equal(res[True][0], res[False][0])

@@ -635,3 +635,57 @@ def test_saturation_skipping_drops_a_front_subset_when_ordered_wrongly():
     wrong = O.render_view(sc, off, cam, o, order=[2, 1, 0])
     assert wrong["skip"][0].sum() > 0
     assert np.abs(wrong["image"] - full["image"]).max() > 1e-2
+
+
+# --------------------------------------------------------------------------- D-SSIM loss
+def test_ssim_window_sum_is_the_windowed_sum():
+    # brute force: every output pixel sums the 11 x 11 window of weights w_i w_j over the
+    # pixels inside the image
+    rng = np.random.default_rng(1)
+    a = rng.uniform(0, 1, (9, 13))
+    w = O.ssim_window()
+    assert abs(w.sum() - 1.0) < 1e-15 and np.allclose(w, w[::-1])
+    assert np.isclose(w[5] / w[4], np.exp(0.5 / 1.5 ** 2))  # Gaussian, sigma 1.5
+    ref = np.zeros_like(a)
+    for y in range(9):
+        for x in range(13):
+            for i in range(11):
+                for j in range(11):
+                    yy, xx = y + i - 5, x + j - 5
+                    if 0 <= yy < 9 and 0 <= xx < 13:
+                        ref[y, x] += w[i] * w[j] * a[yy, xx]
+    np.testing.assert_allclose(O._window_sum(a, w), ref, rtol=1e-13, atol=1e-15)
+
+
+def test_ssim_closed_forms():
+    # identical images: SSIM = 1, loss 0, zero gradient
+    rng = np.random.default_rng(2)
+    x = rng.uniform(0, 1, (3, 20, 24))
+    loss, g = O.loss_l1_dssim([x], [x])
+    assert abs(loss) < 1e-12 and np.abs(g[0]).max() < 1e-12
+    # constant images a, b: away from the border every window sees only a and b, the
+    # variances vanish, and S = (2ab + C1) / (a^2 + b^2 + C1)
+    a, b = 0.3, 0.7
+    S, _, _, _ = O.ssim_terms(np.full((30, 30), a), np.full((30, 30), b))
+    expect = (2 * a * b + O.SSIM_C1) / (a * a + b * b + O.SSIM_C1)
+    np.testing.assert_allclose(S[5:-5, 5:-5], expect, rtol=1e-12)
+    # lam = 0 is the plain L1 loss
+    y = rng.uniform(0, 1, x.shape)
+    loss0, g0 = O.loss_l1_dssim([x], [y], lam=0.0)
+    assert np.isclose(loss0, np.abs(x - y).mean())
+    np.testing.assert_allclose(g0[0], np.sign(x - y) / x.size)
+
+
+def test_ssim_gradient_finite_differences():
+    rng = np.random.default_rng(3)
+    xs = [rng.uniform(0.1, 0.9, (3, 14, 17)), rng.uniform(0.1, 0.9, (3, 9, 11))]
+    ys = [rng.uniform(0, 1, a.shape) for a in xs]
+    _, g = O.loss_l1_dssim(xs, ys, lam=0.2)
+    h = 1e-6
+    for v, idx in [(0, (0, 0, 0)), (0, (1, 7, 8)), (0, (2, 13, 16)), (1, (1, 0, 10)), (1, (0, 4, 5))]:
+        xp = [a.copy() for a in xs]
+        xm = [a.copy() for a in xs]
+        xp[v][idx] += h
+        xm[v][idx] -= h
+        fd = (O.loss_l1_dssim(xp, ys)[0] - O.loss_l1_dssim(xm, ys)[0]) / (2 * h)
+        assert abs(fd - g[v][idx]) <= 1e-7 * max(1.0, abs(fd)) + 1e-9, (v, idx, fd, g[v][idx])
