@@ -199,6 +199,17 @@ struct Plan {
   // 10 project_bwd.
   bool timing = false;
   cudaEvent_t ev[11] = {};
+  // saturation-skipping waves: events before wave r's sort (2r), between its sort and its
+  // rasteriser (2r + 1), and after the last rasteriser (2K)
+  std::vector<cudaEvent_t> wev;
+
+  void mark_wave(int i, cudaStream_t s) {
+    if (!timing || i >= (int)wev.size() || !wev[i]) return;
+    if (stream_capturing(s))
+      cudaEventRecordWithFlags(wev[i], s, cudaEventRecordExternal);
+    else
+      cudaEventRecord(wev[i], s);
+  }
 
   void mark(int i, cudaStream_t s) {
     if (!timing || !ev[i]) return;
@@ -263,6 +274,9 @@ struct Plan {
     for (void** p : ps) free_ptr(*p, s);
     for (auto& e : ev)
       if (e) { cudaEventDestroy(e); e = nullptr; }
+    for (auto& e : wev)
+      if (e) cudaEventDestroy(e);
+    wev.clear();
   }
 
   // Project (counting pairs per tile) and scan the counts into segment starts.
@@ -291,9 +305,30 @@ struct Plan {
     launch_fill(b, s);
     CK_LAUNCH();
     mark(3, s);
-    launch_seg_sort(b, merge_rounds_bound(max_subset()), s);
-    CK_LAUNCH();
+    if (!order_d) {  // with saturation skipping each wave sorts its own segments
+      launch_seg_sort(b, merge_rounds_bound(max_subset()), s);
+      CK_LAUNCH();
+    }
     mark(4, s);
+    return SPLX_OK;
+  }
+
+  // Forward rasterisation with saturation skipping: per wave, sort the wave's segments
+  // (those of saturated items are left unsorted) and render them.
+  int waves(const BatchDev& b, cudaStream_t s) {
+    for (int r = 0; r < K; ++r) {
+      BatchDev bw = b;
+      bw.order = order_d;
+      bw.wave = r;
+      mark_wave(2 * r, s);
+      CK(cudaMemsetAsync(big_count, 0, sizeof(unsigned), s));
+      CK(cudaMemsetAsync(chunk_count, 0, sizeof(unsigned), s));
+      launch_seg_sort(bw, merge_rounds_bound(max_subset()), s);
+      mark_wave(2 * r + 1, s);
+      launch_raster_fwd(bw, s);
+      CK_LAUNCH();
+    }
+    mark_wave(2 * K, s);
     return SPLX_OK;
   }
 
@@ -837,13 +872,9 @@ int splx_batch_forward(splx_batch_t bt, float* out_rgb, float* out_T, splx_strea
   b.out_rgb = out_rgb;
   b.out_T = out_T;
   if (P.order_d) {
-    // saturation skipping: K waves, each rendering one subset of every view, front to back
-    for (int r = 0; r < P.K; ++r) {
-      BatchDev bw = b;
-      bw.order = P.order_d;
-      bw.wave = r;
-      launch_raster_fwd(bw, s);
-    }
+    // saturation skipping: K waves, each sorting and rendering one subset of every view,
+    // front to back
+    if ((r = P.waves(b, s))) return r;
   } else {
     launch_raster_fwd(b, s);
   }
@@ -889,9 +920,14 @@ int splx_batch_set_timing(splx_batch_t bt, int enable) {
   if (!bt) return SPLX_ERR_INVALID;
   Plan& P = bt->plan;
   CtxScope scope(P.ctx);
-  if (enable)
+  if (enable) {
     for (auto& e : P.ev)
       if (!e) CK(cudaEventCreate(&e));
+    if (P.wev.empty()) {
+      P.wev.assign(2 * P.K + 1, nullptr);
+      for (auto& e : P.wev) CK(cudaEventCreate(&e));
+    }
+  }
   P.timing = enable != 0;
   return SPLX_OK;
 }
@@ -984,6 +1020,19 @@ int splx_batch_kernel_times(splx_batch_t bt, float* ms_out) {
     float ms = 0.0f;
     CK(cudaEventElapsedTime(&ms, P.ev[pairs[i][0]], P.ev[pairs[i][1]]));
     ms_out[i] = ms;
+  }
+  if (P.order_d && (int)P.wev.size() == 2 * P.K + 1) {
+    // waves interleave sort and rasteriser: sum each over the waves
+    float sort = 0.0f, ras = 0.0f;
+    for (int r = 0; r < P.K; ++r) {
+      float a = 0.0f, c = 0.0f;
+      CK(cudaEventElapsedTime(&a, P.wev[2 * r], P.wev[2 * r + 1]));
+      CK(cudaEventElapsedTime(&c, P.wev[2 * r + 1], P.wev[2 * r + 2]));
+      sort += a;
+      ras += c;
+    }
+    ms_out[3] += sort;
+    ms_out[4] = ras;
   }
   return SPLX_OK;
 }

@@ -221,12 +221,14 @@ void launch_fill(const BatchDev& b, cudaStream_t s) {
 __global__ void __launch_bounds__(kSortThreads) k_seg_sort_small(const BatchDev b) {
   __shared__ uint64_t sk[2][kPadded];
   __shared__ unsigned s_base[2];
-  const int64_t t = blockIdx.x;
+  const int64_t t = item_of(b, blockIdx.x);
   uint32_t s, e;
   segment_of(b, t, s, e);
   if (threadIdx.x == 0) b.ranges[t] = make_uint2(s, e);
   const int n = (int)(e - s);
   if (n <= 1) return;
+  // saturation-skipping waves sort only what the wave's rasteriser will walk
+  if (b.order && b.wave > 0 && item_saturated(b, t)) return;
   if (n > kChunk) {
     const unsigned nch = (unsigned)((n + kChunk - 1) / kChunk);
     if (threadIdx.x == 0) {
@@ -335,7 +337,8 @@ __global__ void __launch_bounds__(kSortThreads) k_merge_fixup(const BatchDev b) 
 
 void launch_seg_sort(const BatchDev& b, int max_rounds, cudaStream_t s) {
   if (b.n_tiles == 0) return;
-  k_seg_sort_small<<<(unsigned)b.n_tiles, kSortThreads, 0, s>>>(b);
+  const int64_t items = b.order ? b.n_tiles / b.K : b.n_tiles;
+  k_seg_sort_small<<<(unsigned)items, kSortThreads, 0, s>>>(b);
   const unsigned grid = 152 * 8;
   k_chunk_sort<<<grid, kSortThreads, 0, s>>>(b);
   for (int r = 0; r < max_rounds; ++r) k_merge_round<<<grid, kSortThreads, 0, s>>>(b, r);

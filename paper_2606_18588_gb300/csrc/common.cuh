@@ -203,6 +203,38 @@ __device__ __forceinline__ int view_of(const int64_t* base, int V, int64_t x) {
   return lo;
 }
 
+// Work item of a launch: every (view, subset, tile), or in a saturation-skipping wave the
+// tiles of subset order[v][wave] of every view v (n_tiles / K items).
+__device__ __forceinline__ int64_t item_of(const BatchDev& b, int64_t w) {
+  if (!b.order) return w;
+  const int v = view_of(b.tile_base, b.V, w * b.K);
+  const int64_t nt = (b.tile_base[v + 1] - b.tile_base[v]) / b.K;
+  const int k = b.order[v * b.K + b.wave];
+  return b.tile_base[v] + (int64_t)k * nt + (w - b.tile_base[v] / b.K);
+}
+
+__device__ __forceinline__ int64_t items_of_launch(const BatchDev& b) {
+  return b.order ? b.n_tiles / b.K : b.n_tiles;
+}
+
+// Saturation skipping test of work item `id` in a wave after the first: true if every pixel
+// of its tile has prefix transmittance below eps_comp.  Whole-CTA call (uses
+// __syncthreads_or); the rasteriser and the segment sort take the same decision.
+__device__ __forceinline__ bool item_saturated(const BatchDev& b, int64_t id) {
+  const int v = view_of(b.tile_base, b.V, id);
+  const ViewDev& cam = b.views[v];
+  const int64_t nt = (int64_t)cam.tiles_x * cam.tiles_y;
+  const int64_t t = (id - b.tile_base[v]) % nt;
+  const int x0 = (int)(t % cam.tiles_x) * b.tile, y0 = (int)(t / cam.tiles_x) * b.tile;
+  const float* tp = b.tpre + b.pix_off[v];
+  bool open = false;
+  for (int i = threadIdx.x; i < b.tile * b.tile; i += blockDim.x) {
+    const int x = x0 + i % b.tile, y = y0 + i / b.tile;
+    if (x < cam.W && y < cam.H) open |= tp[(int64_t)y * cam.W + x] >= b.eps_comp;
+  }
+  return !__syncthreads_or(open);
+}
+
 // Whether tile (tx, ty) of view v lies in subset k's visible region (always, if off).
 __device__ __forceinline__ bool in_omega(const BatchDev& b, int v, int k, int tx, int ty) {
   if (!b.omega) return true;

@@ -181,20 +181,6 @@ __device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
   return ti;
 }
 
-// Work item of a launch: every (view, subset, tile), or in a saturation-skipping wave the
-// tiles of subset order[v][wave] of every view v (n_tiles / K items).
-__device__ __forceinline__ int64_t item_of(const BatchDev& b, int64_t w) {
-  if (!b.order) return w;
-  const int v = view_of(b.tile_base, b.V, w * b.K);
-  const int64_t nt = (b.tile_base[v + 1] - b.tile_base[v]) / b.K;
-  const int k = b.order[v * b.K + b.wave];
-  return b.tile_base[v] + (int64_t)k * nt + (w - b.tile_base[v] / b.K);
-}
-
-__device__ __forceinline__ int64_t items_of_launch(const BatchDev& b) {
-  return b.order ? b.n_tiles / b.K : b.n_tiles;
-}
-
 }  // namespace
 
 // kCount variants (eager runs only) also count the work for the roofline: thread-entries
