@@ -307,24 +307,27 @@ def serve_leg(args, ctx, rank, world):
     w = I.WORKLOADS["serve_20m_k8"]
     n = args.serve_n or w["n"]
     t0 = time.perf_counter()
-    sc, off, _, _ = I.cluster_case(n, 5 + rank, w["K"], 1, [(64, 64)], w["sh_degree"])
+    sc, off, boxes, _ = I.cluster_case(n, 5 + rank, w["K"], 1, [(64, 64)], w["sh_degree"])
     gen_s = time.perf_counter() - t0
+    from paper_2606_18588_gb300.visibility import front_to_back
+    order_fn = None if args.no_skip else (lambda c: front_to_back(boxes, c.eye))
     dev = scene_to_device(sc)
     subs = _subset_structs(dev, off, sc.sh_degree)
     budget = 120 << 30
     srv = S.Server(ctx, subs, S.opts(), budget, slots=4, max_views=8)
     warm = serve.poisson_requests(8, 1e6, 999 + rank, (0, 0, 0), 25.0)
-    serve.run(srv, warm, realtime=False)
+    serve.run(srv, warm, realtime=False, order_fn=order_fn)
     reqs = serve.poisson_requests(args.serve_requests, args.serve_rate, 7 + rank, (0, 0, 0), 25.0)
     if world > 1:
         dist.barrier()
-    res = serve.run(srv, reqs)
+    res = serve.run(srv, reqs, order_fn=order_fn)
     srv.close()
     out = res.summary()
     out.update({"workload": f"serve_20m_k8: {n} Gaussians SH{sc.sh_degree}, K={w['K']} resident, "
                             f"Poisson {args.serve_rate:g} req/s, resolutions uniform over "
                             "512x512/1280x720/1920x1080/3840x2160, random poses",
                 "slots": 4, "max_views_per_launch": 8, "hbm_budget_gb": budget / 2**30,
+                "saturation_skipping": order_fn is not None,
                 "latency": "arrival (scheduled time) to the host seeing the result finished",
                 "scene_gen_s": gen_s})
     del dev, subs

@@ -308,9 +308,13 @@ int splx_server_create(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
                        const splx_opts* opts, size_t hbm_budget_bytes, int32_t slots,
                        int32_t max_views, splx_server_t* out);
 /* Queues one request (host camera copied) and runs a scheduling pass; *id_out (host) is
- * its id, increasing from 0 in submission order. */
-int splx_server_submit(splx_server_t s, const splx_camera* cam, float* out_rgb,
-                       int64_t* id_out);
+ * its id, increasing from 0 in submission order.  order (host, K entries, nullable) is a
+ * front-to-back order of the subsets for this camera (see splx_batch_set_order): a launch
+ * whose requests all carry one renders with saturation skipping, which leaves the images
+ * unchanged wherever a pixel's Eq. 5 order agrees with it.  SPLX_ERR_INVALID if order is
+ * not a permutation of 0..K-1. */
+int splx_server_submit(splx_server_t s, const splx_camera* cam, const int32_t* order,
+                       float* out_rgb, int64_t* id_out);
 /* Scheduling pass (never waits on the device): retires finished launches, renders
  * launches whose pair count has arrived, admits queued requests into idle slots; then
  * reports up to `cap` finished requests as (ids[i], status[i]) host arrays, *n_out of

@@ -1092,6 +1092,8 @@ struct SrvReq {
   int64_t id;
   splx_camera cam;
   float* out;  // device [3][H][W], caller-owned
+  bool has_order = false;
+  int32_t order[kMaxK];  // front-to-back subset order (saturation skipping)
 };
 
 // One launch of a server slot: the views of up to max_views requests x K subsets, on the
@@ -1139,7 +1141,7 @@ size_t launch_bytes(const splx_server_s& S, const std::vector<SrvReq>& reqs, dou
              ((r.cam.height + S.opts.tile - 1) / S.opts.tile);
   }
   const double b = (double)reqs.size() * S.N * (sizeof(Rec) + 4) + (double)px * K * 24.0 +
-                   (double)px * 12.0 + (double)tiles * 48.0 + pairs * 16.0 +
+                   (double)px * 16.0 + (double)tiles * 48.0 + pairs * 16.0 +
                    (pairs / 2048.0 + 1.0) * 8.0 + 65536.0;
   return (size_t)b;
 }
@@ -1205,6 +1207,17 @@ int srv_start(splx_server_s* S, SrvLaunch& L) {
   if ((r = P.alloc_common(L.s))) return r;
   if ((r = ctx_alloc_t(S->ctx, &P.omega, (size_t)4 * V * K, L.s))) return r;
   P.visibility = true;
+  bool ordered = true;
+  for (const SrvReq& q : L.reqs) ordered = ordered && q.has_order;
+  if (ordered) {  // saturation skipping for the launch: per-view orders, prefix buffer
+    std::vector<int32_t> ord((size_t)V * K);
+    for (int v = 0; v < V; ++v)
+      for (int k = 0; k < K; ++k) ord[(size_t)v * K + k] = L.reqs[v].order[k];
+    if ((r = ctx_alloc_t(S->ctx, &P.order_d, ord.size(), L.s))) return r;
+    if ((r = ctx_alloc_t(S->ctx, &P.tpre, (size_t)std::max<int64_t>(TP, 1), L.s))) return r;
+    CK(cudaMemcpyAsync(P.order_d, ord.data(), sizeof(int32_t) * ord.size(),
+                       cudaMemcpyHostToDevice, L.s));
+  }
   if ((r = P.project_and_count(L.s))) return r;
   CK(cudaMemcpyAsync(L.total_h, P.tile_start + P.n_tiles, sizeof(uint32_t),
                      cudaMemcpyDeviceToHost, L.s));
@@ -1223,7 +1236,11 @@ int srv_render(splx_server_s* S, SrvLaunch& L, uint64_t total) {
   BatchDev b = P.dev();
   b.out_rgb = L.out_cat;
   b.out_T = nullptr;
-  launch_raster_fwd(b, L.s);
+  if (P.order_d) {
+    if ((r = P.waves(b, L.s))) return r;
+  } else {
+    launch_raster_fwd(b, L.s);
+  }
   launch_composite(b, P.total_pixels, L.s);
   CK_LAUNCH();
   for (int v = 0; v < P.V; ++v) {
@@ -1366,11 +1383,20 @@ int splx_server_create(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
   return SPLX_OK;
 }
 
-int splx_server_submit(splx_server_t S, const splx_camera* cam, float* out_rgb, int64_t* id_out) {
+int splx_server_submit(splx_server_t S, const splx_camera* cam, const int32_t* order,
+                       float* out_rgb, int64_t* id_out) {
   if (!S || !out_rgb || !id_out) return SPLX_ERR_INVALID;
   int r;
   if ((r = check_cam(cam))) return r;
   SrvReq q;
+  const int K = (int)S->subsets.size();
+  if (order) {
+    std::vector<int> seen(K, 0);
+    for (int k = 0; k < K; ++k)
+      if (order[k] < 0 || order[k] >= K || seen[order[k]]++) return SPLX_ERR_INVALID;
+    std::memcpy(q.order, order, sizeof(int32_t) * K);
+    q.has_order = true;
+  }
   q.id = S->next_id++;
   q.cam = *cam;
   q.out = out_rgb;

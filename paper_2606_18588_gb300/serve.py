@@ -64,10 +64,11 @@ class ServeResult:
 
 
 def run(server: S.Server, requests: list[Request], keep=None, realtime: bool = True,
-        idle_sleep_s: float = 1e-4) -> ServeResult:
+        idle_sleep_s: float = 1e-4, order_fn=None) -> ServeResult:
     """Submits each request at its arrival time (realtime) or all at once, polls until all
     finished.  `keep` (a set of request indices) keeps those outputs: they are returned in
-    the result's `outputs` attribute as {index: tensor}."""
+    the result's `outputs` attribute as {index: tensor}.  order_fn(camera), if given, gives
+    each request's front-to-back subset order (saturation skipping)."""
     outs = {}
     id_to_idx = {}
     done_t = {}
@@ -80,7 +81,7 @@ def run(server: S.Server, requests: list[Request], keep=None, realtime: bool = T
         while i < n and (not realtime or requests[i].arrival <= now):
             c = requests[i].cam
             out = torch.empty(3, c.height, c.width, device="cuda")
-            rid = server.submit(c, out)
+            rid = server.submit(c, out, None if order_fn is None else order_fn(c))
             id_to_idx[rid] = i
             if keep is not None and i in keep:
                 outs[i] = out

@@ -98,7 +98,7 @@ _sigs = {
     "splx_batch_max_ctas_per_sm": (C.c_int, [_P, _P, _P]),
     "splx_server_create": (C.c_int, [_P, _P, C.c_int32, _P, C.c_size_t, C.c_int32, C.c_int32,
                                      C.POINTER(_P)]),
-    "splx_server_submit": (C.c_int, [_P, _P, _P, C.POINTER(C.c_int64)]),
+    "splx_server_submit": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_int64)]),
     "splx_server_poll": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(C.c_int32)]),
     "splx_server_stats": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                     C.POINTER(C.c_size_t)]),
@@ -357,12 +357,19 @@ class Server:
         self._ids = (C.c_int64 * 256)()
         self._st = (C.c_int32 * 256)()
 
-    def submit(self, cam, out_rgb) -> int:
+    def submit(self, cam, out_rgb, order=None) -> int:
+        """order: optional front-to-back subset order for this camera (saturation skipping)."""
         c = cam if isinstance(cam, Camera) else camera(cam)
         if tuple(out_rgb.shape) != (3, c.height, c.width):
             raise ValueError("out_rgb must be [3, H, W]")
         rid = C.c_int64()
-        _check(_lib.splx_server_submit(self.h, C.byref(c), _ptr(out_rgb), C.byref(rid)),
+        op = None
+        if order is not None:
+            oa = np.ascontiguousarray(order, np.int32)
+            if oa.shape != (self.K,):
+                raise ValueError(f"order must have {self.K} entries")
+            op = oa.ctypes.data_as(C.c_void_p)
+        _check(_lib.splx_server_submit(self.h, C.byref(c), op, _ptr(out_rgb), C.byref(rid)),
                "splx_server_submit")
         self._outs[rid.value] = out_rgb
         return rid.value

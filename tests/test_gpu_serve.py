@@ -34,14 +34,14 @@ def _subsets(dev, off, deg):
     return [subset_struct(dev, int(off[k]), int(off[k + 1]), deg) for k in range(len(off) - 1)]
 
 
-def _serve(ctx, subs, cams, slots, max_views, budget=8 << 30, one_by_one=False):
+def _serve(ctx, subs, cams, slots, max_views, budget=8 << 30, one_by_one=False, orders=None):
     from paper_2606_18588_gb300 import splx as S
     srv = S.Server(ctx, subs, S.opts(), budget, slots=slots, max_views=max_views)
     outs, status = {}, {}
     ids = []
-    for c in cams:
+    for i, c in enumerate(cams):
         out = torch.full((3, c.height, c.width), float("nan"), device="cuda")
-        rid = srv.submit(c, out)
+        rid = srv.submit(c, out, None if orders is None else orders[i])
         outs[rid] = out
         ids.append(rid)
         while one_by_one and rid not in status:
@@ -126,3 +126,27 @@ def test_poisson_driver_reports_latency(ctx, scene):
     assert s["requests"] == 40 and s["failed"] == 0
     assert 0 < s["p50_ms"] <= s["p99_ms"]
     assert set(res.outputs) == {0, 5}
+
+
+def test_server_with_saturation_skipping(ctx):
+    # per-request front-to-back orders: the same images as the batched forward with those
+    # orders, alone and in a mix
+    from paper_2606_18588_gb300 import splx as S
+    from paper_2606_18588_gb300.visibility import orders_for_views
+    from gpu_util import to_device
+    sc, off, boxes, cams = I.cluster_case(120_000, 9, 8, 6, [(160, 120), (96, 64), (200, 150)])
+    orders = orders_for_views(boxes, cams)
+    dev = to_device(sc)
+    subs = _subsets(dev, off, sc.sh_degree)
+    alone, st_a = _serve(ctx, subs, cams, slots=1, max_views=1, one_by_one=True, orders=orders)
+    mix, st_m = _serve(ctx, subs, cams, slots=3, max_views=4, orders=orders)
+    assert all(s == S.OK for s in st_a + st_m)
+    b = S.Batch(ctx, subs, cams, S.opts())
+    b.set_order(orders)
+    rgb = torch.empty(b.rgb_off[-1], device="cuda")
+    b.forward(rgb)
+    torch.cuda.synchronize()
+    for v in range(len(cams)):
+        assert torch.equal(alone[v], mix[v])
+        assert torch.equal(b.views(rgb)[v], alone[v])
+    b.close()
