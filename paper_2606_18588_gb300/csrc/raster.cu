@@ -186,6 +186,7 @@ __device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
 // kCount variants (eager runs only) also count the work for the roofline: thread-entries
 // examined, (pixel, entry) alpha evaluations and blends / contributions.
 constexpr int kNB = 256;  // list entries staged in shared memory per batch
+constexpr int kDirectLanes = 3;  // backward: lanes that add their gradients directly
 
 template <int TS, int PPT, bool kCount>
 __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, float4* sA,
@@ -463,8 +464,9 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
       }
       const unsigned am = __ballot_sync(0xffffffffu, act);
       if (am) {
-        if ((am & (am - 1)) == 0) {
-          // a single lane holds the whole warp's contribution: no reduction needed
+        if (__popc(am) <= kDirectLanes) {
+          // few lanes hold the warp's contribution: their own atomics cost the L2 no more
+          // operations than the reduction's nine, and skip its shuffles
           if (act) {
             float4* dst = g2 + (int64_t)sG[jj] * 3;
             atomicAdd(dst, make_float4(gu, gv, gA, gB));
