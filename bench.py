@@ -335,11 +335,124 @@ def serve_leg(args, ctx, rank, world):
     return out
 
 
+# ---------------------------------------------------------------- aerial city, 120M
+def city_main(args):
+    """Training steps on the aerial-city scene (train_120m_k32): 120M Gaussians SH3 in K = 32
+    k-d cells, each step a batch of 8 1920x1080 views sampled from a pool of 500 aerial
+    cameras, forward + composite + L1 + backward + Adam over all parameters.  The scene is
+    generated cell by cell straight into device memory; each step's views, subset orders
+    and target images are set between graph replays (targets staged on the device first)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2606_18588_gb300 import inputs as I
+    from paper_2606_18588_gb300 import splx as S
+    from paper_2606_18588_gb300.train import BatchedStep, _subset_structs, city_to_device
+    from paper_2606_18588_gb300.visibility import orders_for_views
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    w = I.WORKLOADS["train_120m_k32"]
+    n, seed = args.n or w["n"], 4 + rank
+    t0 = time.perf_counter()
+    layout = I.city_layout(n, seed, w["K"], w["sh_degree"])
+    pool = I.aerial_cameras(seed, size=w["sizes"][0])
+    ctx = S.Context(local)
+    dev = city_to_device(layout)
+    gen_s = time.perf_counter() - t0
+    nsteps = args.warmup + args.steps
+    views = [[pool[i] for i in I.step_views(seed, s, len(pool), w["views"])] for s in range(nsteps)]
+    orders = [None if args.no_skip else orders_for_views(layout.boxes, v) for v in views]
+    px = sum(c.width * c.height for c in views[0])
+    tgt = torch.empty((nsteps, 3 * px), device="cuda")
+    for s, vs in enumerate(views):
+        tgt[s].copy_(torch.cat([torch.from_numpy(I.random_image(c.height, c.width, 7919 * s + i))
+                                .reshape(-1) for i, c in enumerate(vs)]))
+    stream = torch.cuda.Stream()
+    o = S.opts(tile=args.tile or 16)
+    with torch.cuda.stream(stream):
+        # pair capacity: the largest pair count over the steps' view sets (eager forwards of
+        # a probe batch, whose memory the step's batch then reuses)
+        pb = S.Batch(ctx, _subset_structs(dev, layout.offsets, layout.sh_degree), views[0], o,
+                     0, stream=stream)
+        rgb = torch.empty(pb.rgb_off[-1], device="cuda")
+        need = 0
+        for s in range(nsteps):
+            pb.set_cameras(views[s], stream=stream)
+            pb.set_order(orders[s])
+            pb.forward(rgb, None, stream=stream)
+            need = max(need, pb.status(stream)[1])
+        ctx.device_status(stream)
+        pb.close()
+        del rgb
+        st = BatchedStep(ctx, dev, layout.offsets, layout.sh_degree, views[0], None, o,
+                         pair_capacity=int(need * 1.05) + 1024, stream=stream, order=orders[0])
+        st.set_targets(tgt[0])
+        st.run()
+        stream.synchronize()
+        code, _ = st.status()
+        if code != S.OK:
+            raise RuntimeError(f"city step status {code}")
+        launches0 = ctx.launch_count
+        st.capture()
+        launches_per_step = ctx.launch_count - launches0
+        for s in range(args.warmup):
+            st.set_views(views[s], orders[s])
+            st.target.copy_(tgt[s], non_blocking=True)
+            st.replay()
+        stream.synchronize()
+        clocks = Clocks(local)
+        clocks.start()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(args.warmup, nsteps):
+            st.set_views(views[s], orders[s])  # waits for the previous replay
+            st.target.copy_(tgt[s], non_blocking=True)
+            st.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        clk = clocks.stop()
+        code, _ = st.status()
+        if code != S.OK:
+            raise RuntimeError(f"city status after timed region {code}")
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        value = px * world / (ms / 1e3) / 1e6
+        st.close()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"train_120m_k32: {n} Gaussians SH{layout.sh_degree} on an "
+                                   f"aerial city (1 km^2), K={layout.K} k-d subsets (x/z), "
+                                   f"{w['views']} views 1920x1080 per step sampled from "
+                                   f"{len(pool)} aerial cameras, L1 loss, Adam",
+                       "global_batch": w["views"] * world, "pixels_per_step": px * world,
+                       "tile": o.tile, "pair_capacity": int(need * 1.05) + 1024,
+                       "saturation_skipping": not args.no_skip, "scene_gen_s": gen_s,
+                       "l2": "inputs larger than L2 (28 GB parameters)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": None, "e2e": None, "clocks": clk,
+            "gpu_launches": launches_per_step * args.steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 # ---------------------------------------------------------------- our path
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "train_120m_k32":
+        return city_main(args)
     import numpy as np
     import torch
     import torch.distributed as dist

@@ -146,7 +146,7 @@ __device__ __forceinline__ uint32_t merge_path_warp(const uint64_t* A, uint32_t 
 }  // namespace
 
 // ---------------------------------------------------------------- fill
-__global__ void __launch_bounds__(256) k_fill(const BatchDev b) {
+__global__ void __launch_bounds__(256, 6) k_fill(const BatchDev b) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned lanes = __ballot_sync(0xffffffffu, idx < (int64_t)b.V * b.N);
   if (idx >= (int64_t)b.V * b.N) return;
@@ -175,8 +175,15 @@ __global__ void __launch_bounds__(256) k_fill(const BatchDev b) {
     if (tiles <= 32u) {
       hits = __float_as_uint(rd.w);
     } else {
-      const float4 ra = r->a;
-      tc = tile_cull_prep(ra.x, ra.y, rd.x, rd.y, rd.z, rd.w);
+      // the test centres on the specification's 2-D mean (the record holds the blend's)
+      const SubsetDev S = b.subsets[k];
+      const int64_t i = g - S.goff;
+      const float m[3] = {__ldg(S.means + 3 * i), __ldg(S.means + 3 * i + 1),
+                          __ldg(S.means + 3 * i + 2)};
+      float t[3], terr[3], u, v;
+      spec_camera(m, cam.R, cam.t, t, terr);
+      spec_center(t[0], t[1], t[2], cam.fx, cam.fy, cam.cx, cam.cy, u, v);
+      tc = tile_cull_prep(u, v, rd.x, rd.y, rd.z, rd.w);
     }
     tiles_x = cam.tiles_x;
     tbase = b.tile_base[v] + (int64_t)k * cam.tiles_x * cam.tiles_y + (int64_t)ty0 * cam.tiles_x + tx0;

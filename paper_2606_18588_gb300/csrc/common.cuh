@@ -72,7 +72,8 @@ struct ImgDev {
 };
 
 // Projected record of one (view, Gaussian): 64 bytes, gathered by the rasterisers.
-//   a = (u, v, qa, qb)      2-D mean, conic scaled by -log2(e)/2 ... see project.cu
+//   a = (u, v, qa, qb)      the blend's 2-D mean (double-float, see blend_center), conic
+//                            scaled by -log2(e)/2 ... see project.cu
 //   b = (qc, opacity, depth, rect_x)   rect_x = x0 | x1 << 16 (bit pattern)
 //   c = (r, g, b, rect_y)              rect_y = y0 | y1 << 16
 //   d = (A, B, C, q_max | hits)   conic and tile-test threshold in the binning

@@ -90,11 +90,13 @@ __global__ void __launch_bounds__(256, 4) k_project(const BatchDev b) {
     uint32_t tiles = 0;
     float sA = 0.f, sB = 0.f, sC = 0.f;
     if (so.visible) {
+      float bu, bv;
+      blend_center(so, cam.fx, cam.fy, cam.cx, cam.cy, bu, bv);
       spec_conic(so, sA, sB, sC);
       const float inv = 1.0f / so.det;
       const float A = so.c * inv, B = -so.b * inv, Cc = so.a * inv;
-      // p2 = power * log2(e) = qa dx^2 + qb dx dy + qc dy^2
-      r.a = make_float4(so.u, so.v, -0.5f * kLog2e * A, -kLog2e * B);
+      // p2 = power * log2(e) = qa dx^2 + qb dx dy + qc dy^2, about the blend's 2-D mean
+      r.a = make_float4(bu, bv, -0.5f * kLog2e * A, -kLog2e * B);
       float dx = m[0] - cam.eye[0], dy = m[1] - cam.eye[1], dz = m[2] - cam.eye[2];
       const float rn = rsqrtf(dx * dx + dy * dy + dz * dz);
       dx *= rn; dy *= rn; dz *= rn;

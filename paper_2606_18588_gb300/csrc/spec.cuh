@@ -43,6 +43,8 @@ struct SpecOut {
   bool visible;
   int x0, x1, y0, y1;
   float tz;         // camera depth (its bits are the sort key)
+  float tx, ty;     // camera-space x, y
+  float ex, ey, ez; // rounding errors of tx, ty, tz (for the blend's centre, not the spec)
   float u, v;       // 2-D mean
   float a, b, c;    // dilated Sigma2D
   float det;        // det(Sigma2D)
@@ -86,16 +88,52 @@ __device__ __forceinline__ SpecG spec_gaussian(const float ls[3], const float q[
 }
 
 // Per-view part; cam: R[9], t[3], fx, fy, cx, cy, W, H, near.
+// Knuth's TwoSum: s = fl(a + b) and its exact rounding error e (s + e = a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = fa(a, b);
+  const float bb = fs(s, a);
+  e = fa(fs(a, fs(s, bb)), fs(b, bb));
+}
+
+// Camera-space position of a mean in the specification's arithmetic,
+// t_i = ((R_i0 m_0 + R_i1 m_1) + R_i2 m_2) + tc_i, each step rounded.  err, if the caller
+// uses it, receives the sum of those steps' exact rounding errors (Dot2 of Ogita, Rump and
+// Oishi, "Accurate sum and dot product", 2005: products split by an FMA, sums by TwoSum),
+// so that t_i + err_i is R m + tc to about twice the precision; it is not part of the
+// specification and leaves t_i as it is.
+__device__ __forceinline__ void spec_camera(const float m[3], const float* R, const float* tc,
+                                            float t[3], float err[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float p0 = fm(R[3 * i], m[0]), p1 = fm(R[3 * i + 1], m[1]), p2 = fm(R[3 * i + 2], m[2]);
+    float s1, s2, s3, e1, e2, e3;
+    two_sum(p0, p1, s1, e1);
+    two_sum(s1, p2, s2, e2);
+    two_sum(s2, tc[i], s3, e3);
+    const float ep = fa(fa(__fmaf_rn(R[3 * i], m[0], -p0), __fmaf_rn(R[3 * i + 1], m[1], -p1)),
+                        __fmaf_rn(R[3 * i + 2], m[2], -p2));
+    t[i] = s3;
+    err[i] = fa(ep, fa(fa(e1, e2), e3));
+  }
+}
+// Its 2-D mean (the centre of the pixel rectangle).
+__device__ __forceinline__ void spec_center(float tx, float ty, float tz, float fx, float fy,
+                                            float cx, float cy, float& u, float& v) {
+  u = fa(fd(fm(fx, tx), tz), cx);
+  v = fa(fd(fm(fy, ty), tz), cy);
+}
+
 __device__ __forceinline__ SpecOut bin_spec(const float m[3], const SpecG& G, const float* R,
                                             const float* tc, float fx, float fy, float cx,
                                             float cy, int W, int H, float near_plane) {
   SpecOut o;
   o.visible = false;
   o.x0 = 0; o.x1 = -1; o.y0 = 0; o.y1 = -1;
-  const float tx = fa(fa(fa(fm(R[0], m[0]), fm(R[1], m[1])), fm(R[2], m[2])), tc[0]);
-  const float ty = fa(fa(fa(fm(R[3], m[0]), fm(R[4], m[1])), fm(R[5], m[2])), tc[1]);
-  const float tz = fa(fa(fa(fm(R[6], m[0]), fm(R[7], m[1])), fm(R[8], m[2])), tc[2]);
-  o.tz = tz;
+  float t[3], terr[3];
+  spec_camera(m, R, tc, t, terr);
+  const float tx = t[0], ty = t[1], tz = t[2];
+  o.ex = terr[0]; o.ey = terr[1]; o.ez = terr[2];
+  o.tz = tz; o.tx = tx; o.ty = ty;
   o.sx = G.sx; o.sy = G.sy; o.sz = G.sz;
   if (!(tz > near_plane)) return o;
   if (!G.ok) return o;
@@ -137,8 +175,8 @@ __device__ __forceinline__ SpecOut bin_spec(const float m[3], const SpecG& G, co
   if (!(lam < 1.0e30f)) return o;
   const float r = ceilf(fm(3.0f, __fsqrt_rn(lam)));
   if (!(r > 0.0f)) return o;
-  const float u = fa(fd(fm(fx, tx), tz), cx);
-  const float v = fa(fd(fm(fy, ty), tz), cy);
+  float u, v;
+  spec_center(tx, ty, tz, fx, fy, cx, cy, u, v);
   o.u = u; o.v = v;
   if (!(fabsf(u) < 1.0e7f) || !(fabsf(v) < 1.0e7f)) return o;
   const float xlo = ceilf(fs(fs(u, r), 0.5f)), xhi = floorf(fs(fa(u, r), 0.5f));
@@ -149,6 +187,32 @@ __device__ __forceinline__ SpecOut bin_spec(const float m[3], const SpecG& G, co
   o.visible = true;
   o.x0 = (int)x0; o.x1 = (int)x1; o.y0 = (int)y0; o.y1 = (int)y1;
   return o;
+}
+
+// ---- the blend's 2-D mean, outside the specification ----------------------------------
+// The specification's u, v round each of its steps, so with a mean hundreds of metres from
+// the camera they can be off by several 1e-4 pixels, which a footprint of a pixel turns
+// into alpha errors of that order.  The blend therefore takes u = fx (tx + ex)/(tz + ez) + cx
+// (and v alike) from the camera-space position with its rounding errors (spec_camera),
+// the quotient with its remainder and one final rounding: within half an ulp of the exact
+// projection of the FP32 inputs.
+__device__ __forceinline__ float project_df(float f, float nh, float nl, float dh, float dl,
+                                            float c) {
+  const float q = fd(nh, dh);
+  // remainder n - q d: exact for the high parts, then the low parts
+  float r = __fmaf_rn(-q, dh, nh);
+  r = fa(r, fs(nl, fm(q, dl)));
+  const float ql = fd(r, dh);
+  const float p = fm(f, q);
+  const float pe = __fmaf_rn(f, ql, __fmaf_rn(f, q, -p));
+  float s, e;
+  two_sum(p, c, s, e);
+  return fa(s, fa(e, pe));
+}
+__device__ __forceinline__ void blend_center(const SpecOut& so, float fx, float fy, float cx,
+                                             float cy, float& u, float& v) {
+  u = project_df(fx, so.tx, so.ex, so.tz, so.ez, cx);
+  v = project_df(fy, so.ty, so.ey, so.tz, so.ez, cy);
 }
 
 // Conic of the dilated Sigma2D and opacity in the specification's arithmetic.

@@ -105,7 +105,9 @@ def _sh(rng, n, deg, rgb):
     sh = np.zeros((n, c, 3), np.float32)
     sh[:, 0, :] = (rgb - 0.5) * _INV_Y00
     if c > 1:
-        sh[:, 1:, :] = rng.standard_normal((n, c - 1, 3), dtype=np.float32) * np.float32(0.2)
+        rest = rng.standard_normal((n, c - 1, 3), dtype=np.float32)
+        rest *= np.float32(0.2)
+        sh[:, 1:, :] = rest
     return sh
 
 
@@ -153,9 +155,13 @@ def morton_codes(points: np.ndarray) -> np.ndarray:
     ext = np.maximum(points.max(axis=0) - lo, 1e-12)
     q = np.clip(((points - lo) / ext * 1023.0).astype(np.int64), 0, 1023)
     code = np.zeros(points.shape[0], np.int64)
-    for bit in range(10):
-        for a in range(3):
-            code |= ((q[:, a] >> bit) & 1) << (3 * bit + a)
+    for a in range(3):  # bit b of axis a goes to bit 3 b + a
+        v = q[:, a]
+        v = (v | (v << 16)) & 0x030000FF
+        v = (v | (v << 8)) & 0x0300F00F
+        v = (v | (v << 4)) & 0x030C30C3
+        v = (v | (v << 2)) & 0x09249249
+        code |= v << a
     return code
 
 
@@ -242,6 +248,163 @@ def cluster_case(n: int, seed: int, K: int, n_views: int, sizes, sh_degree: int 
     scene = scene.take(perm)
     cams = orbit_cameras(n_views, seed + 1, sizes)
     return scene, offsets, boxes, cams
+
+
+# ---------------------------------------------------------------- city layout
+# The 120M-Gaussian training step stands in for an aerial city capture (the paper's
+# MatrixCity aerial scenes, Sec. 5): a street grid of square blocks over 1 km x 1 km, each
+# block's lots holding a building box with a lognormal height; Gaussians lie on the ground,
+# the facades and the roofs, with a lognormal density per block.  The scene is generated
+# one k-d cell at a time, so that no host ever holds all of it.
+
+@dataclasses.dataclass
+class CityLayout:
+    """Surface pieces of the city clipped to the K k-d cells, with their Gaussian counts.
+
+    Piece p is the axis-aligned box [lo[p], hi[p]] with one degenerate axis (a flat
+    rectangle); its count[p] Gaussians are uniform on it.  Cell k holds the pieces with
+    cell[p] == k and becomes the contiguous subset [offsets[k], offsets[k+1]).
+    """
+    n: int
+    seed: int
+    K: int
+    sh_degree: int
+    lo: np.ndarray
+    hi: np.ndarray
+    cell: np.ndarray
+    count: np.ndarray
+    offsets: np.ndarray
+    boxes: np.ndarray
+    log_scale_mu: float
+
+    def cell_scene(self, k: int) -> Scene:
+        """The Gaussians of cell k, means in Morton order (deterministic in (seed, k)
+        alone).  The other attributes are i.i.d., drawn after the means in their final
+        order."""
+        rng = np.random.Generator(np.random.PCG64([self.seed, 3, k]))
+        sel = np.nonzero(self.cell == k)[0]
+        n = int(self.count[sel].sum())
+        means = np.empty((n, 3), np.float64)
+        at = 0
+        for p in sel:
+            c = int(self.count[p])
+            if c:
+                u = rng.uniform(0.0, 1.0, (c, 3))
+                means[at:at + c] = self.lo[p] + u * (self.hi[p] - self.lo[p])
+                at += c
+        means = means.astype(np.float32)
+        if n:
+            means = means[np.argsort(morton_codes(means), kind="stable")]
+        log_scales = rng.normal(self.log_scale_mu, 0.5, (n, 3)).astype(np.float32)
+        quats = _quats(rng, n)
+        logits = rng.standard_normal(n).astype(np.float32)
+        rgb = rng.uniform(0.0, 1.0, (n, 3))
+        return Scene(means, log_scales, quats, logits, _sh(rng, n, self.sh_degree, rgb),
+                     self.sh_degree)
+
+
+def _city_surfaces(rng, extent, block, street):
+    """Axis-aligned surface rectangles (lo, hi) of the city and their density weights."""
+    nb = int(round(extent / block))
+    half = 0.5 * extent
+    lo, hi, dens = [], [], []
+
+    def add(a, b, d):
+        lo.append(a); hi.append(b); dens.append(d)
+
+    for bi in range(nb):
+        for bj in range(nb):
+            x0, z0 = -half + bi * block, -half + bj * block
+            d = float(rng.lognormal(0.0, 0.6))
+            add((x0, 0.0, z0), (x0 + block, 0.0, z0 + block), d)  # ground, streets included
+            g = int(rng.integers(2, 4))
+            lot = (block - street) / g
+            for li in range(g):
+                for lj in range(g):
+                    w, dp = lot * rng.uniform(0.6, 0.9), lot * rng.uniform(0.6, 0.9)
+                    cx = x0 + 0.5 * street + (li + 0.5) * lot
+                    cz = z0 + 0.5 * street + (lj + 0.5) * lot
+                    h = float(np.clip(rng.lognormal(math.log(25.0), 0.6), 4.0, 200.0))
+                    ax0, ax1, az0, az1 = cx - 0.5 * w, cx + 0.5 * w, cz - 0.5 * dp, cz + 0.5 * dp
+                    add((ax0, -h, az0), (ax1, -h, az1), d)  # roof (world up is -y)
+                    add((ax0, -h, az0), (ax0, 0.0, az1), d)  # facades
+                    add((ax1, -h, az0), (ax1, 0.0, az1), d)
+                    add((ax0, -h, az0), (ax1, 0.0, az0), d)
+                    add((ax0, -h, az1), (ax1, 0.0, az1), d)
+    return np.array(lo), np.array(hi), np.array(dens)
+
+
+def _area(lo, hi):
+    e = hi - lo
+    return e[:, 0] * e[:, 1] + e[:, 1] * e[:, 2] + e[:, 0] * e[:, 2]  # one extent is zero
+
+
+def city_layout(n: int, seed: int, K: int, sh_degree: int = 3, extent=1000.0, block=100.0,
+                street=20.0, sample=1 << 20) -> CityLayout:
+    """Lays out the city, splits it into K k-d cells on x/z (median splits of a 1M-point
+    sample of the surface distribution) and draws each clipped piece's Gaussian count.
+    Log-scales ~ N(ln(0.5 s), 0.5) with s = sqrt(surface area / n), the mean spacing of
+    the Gaussians on the surfaces."""
+    rng = np.random.Generator(np.random.PCG64([seed, 0]))
+    lo, hi, dens = _city_surfaces(rng, extent, block, street)
+    area = _area(lo, hi)
+    w = area * dens
+    srng = np.random.Generator(np.random.PCG64([seed, 1]))
+    pick = srng.choice(len(w), size=sample, p=w / w.sum())
+    pts = lo[pick] + srng.uniform(0.0, 1.0, (sample, 3)) * (hi[pick] - lo[pick])
+    _, _, boxes = kd_partition(pts, K, spatial_order=False)
+    # clip every surface to every cell; a flat side on a split plane belongs to the cell
+    # whose box starts there (half-open cells)
+    plo, phi, pcell, pw = [], [], [], []
+    for k in range(K):
+        blo, bhi = boxes[k, 0], boxes[k, 1]
+        a, b = np.maximum(lo, blo), np.minimum(hi, bhi)
+        flat = lo == hi
+        ok = np.all(np.where(flat, (lo >= blo) & (lo < bhi), b > a), axis=1)
+        a, b = np.where(flat, lo, a), np.where(flat, hi, b)
+        idx = np.nonzero(ok)[0]
+        plo.append(a[idx]); phi.append(b[idx]); pcell.append(np.full(idx.size, k))
+        pw.append(_area(a[idx], b[idx]) * dens[idx])
+    plo, phi = np.concatenate(plo), np.concatenate(phi)
+    pcell, pw = np.concatenate(pcell), np.concatenate(pw)
+    count = np.random.Generator(np.random.PCG64([seed, 2])).multinomial(n, pw / pw.sum())
+    offsets = np.zeros(K + 1, np.int64)
+    offsets[1:] = np.cumsum(np.bincount(pcell, weights=count, minlength=K).astype(np.int64))
+    mu = math.log(0.5 * math.sqrt(area.sum() / n))
+    return CityLayout(n, seed, K, sh_degree, plo, phi, pcell, count.astype(np.int64), offsets,
+                      boxes, mu)
+
+
+def aerial_cameras(seed: int, n: int = 500, grid=(25, 20), extent=1000.0, altitude=(150.0, 300.0),
+                   pitch_deg=(45.0, 90.0), fov_x_deg=60.0, size=(1920, 1080), near=0.01):
+    """Aerial cameras on a grid x grid[1] lattice over the city, altitude, heading and
+    downward pitch uniform (world up is -y)."""
+    rng = np.random.Generator(np.random.PCG64([seed, 4]))
+    half = 0.5 * extent
+    xs = np.linspace(-half, half, grid[0] + 2)[1:-1]
+    zs = np.linspace(-half, half, grid[1] + 2)[1:-1]
+    w, h = size
+    fx = float(np.float32(0.5 * w / math.tan(math.radians(fov_x_deg) * 0.5)))
+    cams = []
+    for i in range(n):
+        gx, gz = xs[i % grid[0]], zs[(i // grid[0]) % grid[1]]
+        alt = rng.uniform(*altitude)
+        head = rng.uniform(0.0, 2.0 * math.pi)
+        p = math.radians(rng.uniform(*pitch_deg))
+        f = np.array([math.cos(p) * math.cos(head), math.sin(p), math.cos(p) * math.sin(head)])
+        r = np.array([math.sin(head), 0.0, -math.cos(head)])
+        d = np.cross(f, r)
+        R = np.stack([r, d, f]).astype(np.float32)
+        eye = np.array([gx, -alt, gz])
+        t = (-(R.astype(np.float64) @ eye)).astype(np.float32)
+        cams.append(Camera(R, t, fx, fx, 0.5 * w, 0.5 * h, int(w), int(h), float(near)))
+    return cams
+
+
+def step_views(seed: int, step: int, pool: int, n: int = 8) -> np.ndarray:
+    """The n distinct camera indices a training step samples from the pool."""
+    rng = np.random.Generator(np.random.PCG64([seed, 5, step]))
+    return np.sort(rng.choice(pool, size=n, replace=False))
 
 
 # Named workloads (sizes follow the five configurations the hot path is quoted on).

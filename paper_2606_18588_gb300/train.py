@@ -25,6 +25,27 @@ def scene_to_device(scene) -> dict:
             for k, a in zip(GROUPS, scene.arrays())}
 
 
+def city_to_device(layout, workers: int = 4, on_cell=None) -> dict:
+    """Device parameter tensors of a CityLayout, generated one k-d cell at a time by
+    `workers` spawned processes and copied into place, so the host holds a few cells at
+    most.  on_cell(k, scene), if given, sees each cell's host arrays on the way."""
+    import multiprocessing
+    from .inputs import n_sh_coeffs
+    N, nc = int(layout.offsets[-1]), n_sh_coeffs(layout.sh_degree)
+    shapes = {"means": (N, 3), "log_scales": (N, 3), "quats": (N, 4), "opacity_logits": (N,),
+              "sh": (N, nc, 3)}
+    dev = {k: torch.empty(shapes[k], device="cuda") for k in GROUPS}
+    with multiprocessing.get_context("spawn").Pool(workers) as pool:
+        for k, sc in enumerate(pool.imap(layout.cell_scene, range(layout.K))):
+            lo, hi = int(layout.offsets[k]), int(layout.offsets[k + 1])
+            for name, arr in zip(GROUPS, sc.arrays()):
+                dev[name][lo:hi].copy_(torch.from_numpy(arr))
+            if on_cell is not None:
+                on_cell(k, sc)
+    torch.cuda.synchronize()
+    return dev
+
+
 def _subset_structs(dev, offsets, deg, mutable=False):
     f = S.params if mutable else S.gaussians
     return [f(*(dev[k][int(offsets[i]):int(offsets[i + 1])] for k in GROUPS), deg)
@@ -77,6 +98,13 @@ class BatchedStep:
             return
         flat = torch.cat([torch.as_tensor(t).reshape(-1) for t in targets])
         self.target.copy_(flat, non_blocking=True)
+
+    def set_views(self, cams, order=None):
+        """New camera poses (same resolutions, in the same order) and, with saturation
+        skipping on, their front-to-back subset orders; a captured graph stays valid."""
+        self.batch.set_cameras(cams, stream=self.stream)
+        if order is not None:
+            self.batch.set_order(order)
 
     def run(self, events=None):
         """Forward, loss, backward, Adam on self.stream.  `events`, if given, is a list of
