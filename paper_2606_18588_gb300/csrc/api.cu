@@ -514,8 +514,8 @@ int splx_render_partial(splx_ctx_t ctx, const splx_gaussians* subset, const splx
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(cuda_fail(e, "render_partial launch"));
   }
-  // keep only what the backward needs (records, sorted keys, ranges, descriptors)
-  P.free_ptr((void*&)P.counts, s);
+  // keep only what the backward needs (records, tile counts, sorted keys, ranges,
+  // descriptors; a zero count marks a culled Gaussian, whose record is not written)
   P.free_ptr((void*&)P.scan_temp, s);
   P.free_ptr((void*&)P.keys_alt, s);
   P.free_ptr((void*&)P.tile_cnt, s);
@@ -527,6 +527,21 @@ int splx_render_partial(splx_ctx_t ctx, const splx_gaussians* subset, const splx
   *state_out = st;
   return SPLX_OK;
 }
+
+namespace splx {
+// The projection writes no record for a culled Gaussian; the export shows it as documented
+// (zeros, rectangle x0 = y0 = 0xFFFF > x1 = y1 = 0).
+__global__ void k_export_culled(Rec* rec, const uint32_t* counts, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || counts[i]) return;
+  Rec r;
+  r.a = make_float4(0.f, 0.f, 0.f, 0.f);
+  r.b = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFu));
+  r.c = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFu));
+  r.d = make_float4(0.f, 0.f, 0.f, 0.f);
+  rec[i] = r;
+}
+}  // namespace splx
 
 int splx_state_export(splx_ctx_t ctx, splx_state_t st, int64_t* n_pairs, int64_t* n_tiles,
                       uint32_t* ranges_out, uint64_t* keys_out, float* rec_out,
@@ -541,8 +556,13 @@ int splx_state_export(splx_ctx_t ctx, splx_state_t st, int64_t* n_pairs, int64_t
     CK(cudaMemcpyAsync(ranges_out, P.ranges, sizeof(uint2) * P.n_tiles, cudaMemcpyDeviceToDevice, s));
   if (keys_out && P.capacity > 0)
     CK(cudaMemcpyAsync(keys_out, P.keys, sizeof(uint64_t) * P.capacity, cudaMemcpyDeviceToDevice, s));
-  if (rec_out && P.N > 0)
+  if (rec_out && P.N > 0) {
+    if (!P.counts) return SPLX_ERR_STATE;
     CK(cudaMemcpyAsync(rec_out, P.rec, sizeof(Rec) * P.N, cudaMemcpyDeviceToDevice, s));
+    k_export_culled<<<(unsigned)((P.N + 255) / 256), 256, 0, s>>>(reinterpret_cast<Rec*>(rec_out),
+                                                                  P.counts, P.N);
+    CK_LAUNCH();
+  }
   CK(cudaStreamSynchronize(s));
   return SPLX_OK;
 }

@@ -16,6 +16,7 @@
 // instead of once per 8-bit pass over 50+ key bits.
 #include "common.cuh"
 #include "spec.cuh"
+#include "walk.cuh"
 
 namespace splx {
 
@@ -88,13 +89,23 @@ __device__ __forceinline__ void sort_chunk(uint64_t* keys, int n, uint64_t* sa, 
       const int d = o - p0;
       int ia = merge_path_smem(src, p0, w, p0 + w, w, d);
       int ib = d - ia;
+      // heads of both runs in registers (~0 past a run's end; keys are below 2^63, and
+      // the ~0 padding keys are equal, so their order does not matter); each output
+      // reloads only the head it consumed
+      uint64_t va = ia < w ? src[pad(p0 + ia)] : ~0ull;
+      uint64_t vb = ib < w ? src[pad(p0 + w + ib)] : ~0ull;
 #pragma unroll
       for (int r = 0; r < kItems; ++r) {
-        const uint64_t va = ia < w ? src[pad(p0 + ia)] : ~0ull;
-        const uint64_t vb = ib < w ? src[pad(p0 + w + ib)] : ~0ull;
-        const bool takeA = ib >= w || (ia < w && va < vb);
+        const bool takeA = va < vb;
         dst[pad(o + r)] = takeA ? va : vb;
-        if (takeA) ++ia; else ++ib;
+        if (r + 1 < kItems) {
+          ia += takeA ? 1 : 0;
+          ib += takeA ? 0 : 1;
+          const bool more = takeA ? ia < w : ib < w;
+          const uint64_t nv = more ? src[takeA ? pad(p0 + ia) : pad(p0 + w + ib)] : ~0ull;
+          va = takeA ? nv : va;
+          vb = takeA ? vb : nv;
+        }
       }
     }
     __syncthreads();
@@ -146,14 +157,20 @@ __device__ __forceinline__ uint32_t merge_path_warp(const uint64_t* A, uint32_t 
 }  // namespace
 
 // ---------------------------------------------------------------- fill
-__global__ void __launch_bounds__(256, 6) k_fill(const BatchDev b) {
+constexpr int kFillThreads = 256;
+constexpr int kFillFields = 18;  // per lane: tile test (8), rect x, rect y, tile base, width,
+                                 // 1/width, tiles per row, pass bits, key (2), tiles
+
+__global__ void __launch_bounds__(kFillThreads, 6) k_fill(const BatchDev b) {
+  __shared__ float s_walk[kFillThreads / 32][kFillFields][32];
+  __shared__ int s_own[kFillThreads / 32][32];
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned lanes = __ballot_sync(0xffffffffu, idx < (int64_t)b.V * b.N);
   if (idx >= (int64_t)b.V * b.N) return;
   const uint32_t tiles = b.counts[idx];
   const int v = (int)(idx / b.N);
   const int64_t g = idx - (int64_t)v * b.N;
-  int tw = 1, tiles_x = 0, tx0 = 0, ty0 = 0, rx0 = 0, rx1 = 0, ry0 = 0, ry1 = 0;
+  int tw = 1, tiles_x = 0, rx0 = 0, rx1 = 0, ry0 = 0, ry1 = 0;
   int64_t tbase = 0;
   uint64_t key = 0;
   TileCull tc = tile_cull_prep(0.f, 0.f, 1.f, 0.f, 1.f, -1.0f);
@@ -167,10 +184,8 @@ __global__ void __launch_bounds__(256, 6) k_fill(const BatchDev b) {
     const int B_ = b.tile;
     rx0 = (int)(rx & 0xFFFFu); rx1 = (int)(rx >> 16);
     ry0 = (int)(ry & 0xFFFFu); ry1 = (int)(ry >> 16);
-    tx0 = rx0 / B_;
-    ty0 = ry0 / B_;
-    const int tx1 = rx1 / B_;
-    tw = tx1 - tx0 + 1;
+    const int tx0 = rx0 / B_, ty0 = ry0 / B_;
+    tw = rx1 / B_ - tx0 + 1;
     const float4 rd = r->d;  // the tile test's pass bits, or its inputs (> 32 tiles)
     if (tiles <= 32u) {
       hits = __float_as_uint(rd.w);
@@ -180,26 +195,20 @@ __global__ void __launch_bounds__(256, 6) k_fill(const BatchDev b) {
       const int64_t i = g - S.goff;
       const float m[3] = {__ldg(S.means + 3 * i), __ldg(S.means + 3 * i + 1),
                           __ldg(S.means + 3 * i + 2)};
-      float t[3], terr[3], u, v;
-      spec_camera(m, cam.R, cam.t, t, terr);
-      spec_center(t[0], t[1], t[2], cam.fx, cam.fy, cam.cx, cam.cy, u, v);
-      tc = tile_cull_prep(u, v, rd.x, rd.y, rd.z, rd.w);
+      float tcam[3], terr[3], su, sv;
+      spec_camera(m, cam.R, cam.t, tcam, terr);
+      spec_center(tcam[0], tcam[1], tcam[2], cam.fx, cam.fy, cam.cx, cam.cy, su, sv);
+      tc = tile_cull_prep(su, sv, rd.x, rd.y, rd.z, rd.w);
     }
     tiles_x = cam.tiles_x;
     tbase = b.tile_base[v] + (int64_t)k * cam.tiles_x * cam.tiles_y + (int64_t)ty0 * cam.tiles_x + tx0;
     key = ((uint64_t)__float_as_uint(rb.z) << 32) | (uint64_t)(uint32_t)g;
   }
-  const int maxt = __reduce_max_sync(lanes, (int)tiles);
+  const int warp = (int)(threadIdx.x >> 5);
   const unsigned lane = threadIdx.x & 31u, lt = (1u << lane) - 1u;
   bool overflow = false;
-  int jx = 0, jy = 0;  // column / row of the j-th tile inside the rectangle
-  for (int j = 0; j < maxt; ++j) {
-    unsigned t = 0xFFFFFFFFu;
-    if (j < (int)tiles && (tiles <= 32u ? ((hits >> j) & 1u) != 0
-                                        : tile_hits_spec(tc, rx0, rx1, ry0, ry1, tx0 + jx,
-                                                         ty0 + jy, b.tile)))
-      t = (unsigned)(tbase + jy * tiles_x + jx);
-    if (++jx == tw) { jx = 0; ++jy; }
+  // one (tile, key) candidate per lane: aggregate per tile, take slots, write the keys
+  auto place = [&](unsigned t, uint64_t k) {
     const unsigned peers = __match_any_sync(lanes, t);
     const int leader = __ffs(peers) - 1;
     unsigned old = 0;
@@ -207,8 +216,53 @@ __global__ void __launch_bounds__(256, 6) k_fill(const BatchDev b) {
     old = __shfl_sync(lanes, old, leader);
     if (t != 0xFFFFFFFFu) {
       const uint64_t pos = (uint64_t)b.tile_start[t] + (old - 1u - (unsigned)__popc(peers & lt));
-      if (pos < (uint64_t)b.capacity) b.keys[pos] = key;
+      if (pos < (uint64_t)b.capacity) b.keys[pos] = k;
       else overflow = true;
+    }
+  };
+  // the warp's (Gaussian, tile) candidates spread evenly over its lanes (see walk.cuh;
+  // here the whole list: a head walked in lockstep measured slower for this kernel)
+  {
+    float(*f)[32] = s_walk[warp];
+    f[0][lane] = tc.u; f[1][lane] = tc.v; f[2][lane] = tc.A; f[3][lane] = tc.B;
+    f[4][lane] = tc.C; f[5][lane] = tc.qmax; f[6][lane] = tc.rBC; f[7][lane] = tc.rBA;
+    f[8][lane] = __uint_as_float((uint32_t)rx0 | ((uint32_t)rx1 << 16));
+    f[9][lane] = __uint_as_float((uint32_t)ry0 | ((uint32_t)ry1 << 16));
+    f[10][lane] = __uint_as_float((uint32_t)tbase);
+    f[11][lane] = __int_as_float(tw);
+    f[12][lane] = 1.0f / (float)tw;
+    f[13][lane] = __int_as_float(tiles_x);
+    f[14][lane] = __uint_as_float(hits);
+    f[15][lane] = __uint_as_float((uint32_t)key);
+    f[16][lane] = __uint_as_float((uint32_t)(key >> 32));
+    f[17][lane] = __uint_as_float(tiles);
+    const WarpWalk walk = warp_walk_begin(lanes, (int)tiles);
+    for (int base = 0; base < walk.total; base += walk.nact) {
+      int j;
+      const int o = warp_walk_owner(walk, base, s_own[warp], j);
+      unsigned t = 0xFFFFFFFFu;
+      uint64_t okey = 0;
+      if (o >= 0) {
+        int jx, jy;
+        walk_tile(j, __float_as_int(f[11][o]), f[12][o], jx, jy);
+        bool pass;
+        if (__float_as_uint(f[17][o]) <= 32u) {
+          pass = ((__float_as_uint(f[14][o]) >> j) & 1u) != 0u;
+        } else {
+          TileCull oc;
+          oc.u = f[0][o]; oc.v = f[1][o]; oc.A = f[2][o]; oc.B = f[3][o];
+          oc.C = f[4][o]; oc.qmax = f[5][o]; oc.rBC = f[6][o]; oc.rBA = f[7][o];
+          const uint32_t rx = __float_as_uint(f[8][o]), ry = __float_as_uint(f[9][o]);
+          const int x0 = (int)(rx & 0xFFFFu), x1 = (int)(rx >> 16);
+          const int y0 = (int)(ry & 0xFFFFu), y1 = (int)(ry >> 16);
+          pass = tile_hits_spec(oc, x0, x1, y0, y1, x0 / b.tile + jx, y0 / b.tile + jy, b.tile);
+        }
+        if (pass) {
+          t = __float_as_uint(f[10][o]) + (unsigned)(jy * __float_as_int(f[13][o]) + jx);
+          okey = ((uint64_t)__float_as_uint(f[16][o]) << 32) | __float_as_uint(f[15][o]);
+        }
+      }
+      place(t, okey);
     }
   }
   if (overflow) atomicOr(b.status, ST_CAPACITY);
@@ -216,9 +270,9 @@ __global__ void __launch_bounds__(256, 6) k_fill(const BatchDev b) {
 
 void launch_fill(const BatchDev& b, cudaStream_t s) {
   const int64_t n = (int64_t)b.V * b.N;
-  const int64_t blocks = (n + 255) / 256;
+  const int64_t blocks = (n + kFillThreads - 1) / kFillThreads;
   if (blocks == 0) return;
-  k_fill<<<(unsigned)blocks, 256, 0, s>>>(b);
+  k_fill<<<(unsigned)blocks, kFillThreads, 0, s>>>(b);
   count_launch();
 }
 
@@ -315,12 +369,17 @@ __global__ void __launch_bounds__(kSortThreads) k_merge_round(const BatchDev b, 
       int ia = merge_path_smem(sm, 0, la, la, lb, d);
       int ib = d - ia;
       const int dend = d + PER < la + lb ? d + PER : la + lb;
+      uint64_t va = ia < la ? sm[pad(ia)] : ~0ull;  // run heads (~0 past the end)
+      uint64_t vb = ib < lb ? sm[pad(la + ib)] : ~0ull;
       for (int o = d; o < dend; ++o) {
-        const uint64_t va = ia < la ? sm[pad(ia)] : ~0ull;
-        const uint64_t vb = ib < lb ? sm[pad(la + ib)] : ~0ull;
-        const bool takeA = ib >= lb || (ia < la && va < vb);
+        const bool takeA = va < vb;
         dst[o0 + o] = takeA ? va : vb;
-        if (takeA) ++ia; else ++ib;
+        ia += takeA ? 1 : 0;
+        ib += takeA ? 0 : 1;
+        const bool more = takeA ? ia < la : ib < lb;
+        const uint64_t nv = more ? sm[takeA ? pad(ia) : pad(la + ib)] : ~0ull;
+        va = takeA ? nv : va;
+        vb = takeA ? vb : nv;
       }
     }
     __syncthreads();

@@ -7,6 +7,7 @@
 // pair count of each of those tiles (the segment sizes of the binning in bin.cu).
 #include "common.cuh"
 #include "spec.cuh"
+#include "walk.cuh"
 
 namespace splx {
 
@@ -55,8 +56,15 @@ __device__ __forceinline__ void sh_eval(float x, float y, float z, float* Y) {
   }
 }
 
+constexpr int kProjThreads = 256;
+constexpr int kWalkFields = 13;  // per lane: tile test (8), rect x, rect y, tile base, width, 1/width
+
 template <int DEG>
-__global__ void __launch_bounds__(256, 4) k_project(const BatchDev b) {
+__global__ void __launch_bounds__(kProjThreads, 4) k_project(const BatchDev b) {
+  // the warp's tile walk: each lane's tile-test inputs, [field][lane], and its outcome
+  __shared__ float s_walk[kProjThreads / 32][kWalkFields][32];
+  __shared__ int s_own[kProjThreads / 32][32];
+  __shared__ uint32_t s_hits[kProjThreads / 32][32], s_any[kProjThreads / 32][32];
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned lanes = __ballot_sync(0xffffffffu, g < b.N);  // lanes in the warp collectives
   if (g >= b.N) return;
@@ -128,13 +136,11 @@ __global__ void __launch_bounds__(256, 4) k_project(const BatchDev b) {
       const int B_ = b.tile;
       const int tx0 = so.x0 / B_, tx1 = so.x1 / B_, ty0 = so.y0 / B_, ty1 = so.y1 / B_;
       tiles = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
-    } else {
-      r.a = make_float4(0.f, 0.f, 0.f, 0.f);
-      r.b = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFu));
-      r.c = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFu));
     }
+    // a culled Gaussian's record is never read (its count is 0; nothing lists it), so it
+    // is not written: for views that see a small part of the scene that is most records
     Rec* dst = b.rec + (int64_t)v * b.N + g;
-    dst->a = r.a; dst->b = r.b; dst->c = r.c;
+    if (so.visible) { dst->a = r.a; dst->b = r.b; dst->c = r.c; }
     b.counts[(int64_t)v * b.N + g] = tiles;
     // count this Gaussian in every tile of its rectangle that passes the tile test (the
     // segment sizes of the binning); lanes that hit the same tile add together
@@ -144,13 +150,16 @@ __global__ void __launch_bounds__(256, 4) k_project(const BatchDev b) {
     const int64_t tbase = b.tile_base[v] + (int64_t)k * cam.tiles_x * cam.tiles_y +
                           (int64_t)(so.visible ? so.y0 / b.tile : 0) * cam.tiles_x +
                           (so.visible ? so.x0 / b.tile : 0);
-    const int maxt = __reduce_max_sync(lanes, (int)tiles);
-    int jx = 0, jy = 0;  // column / row of the j-th tile inside the rectangle
     const int tx0 = so.visible ? so.x0 / b.tile : 0, ty0 = so.visible ? so.y0 / b.tile : 0;
+    const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
     const TileCull tc = tile_cull_prep(so.u, so.v, sA, sB, sC, so.visible ? qmax : -1.0f);
     uint32_t hits = 0;  // bit j: the j-th tile of the rectangle passes the tile test
     bool any_pair = false;
-    for (int j = 0; j < maxt; ++j) {
+    // head: every lane tests its own first H tiles, H = the warp's mean count rounded up
+    const int nact = __popc(lanes);
+    const int H = ((int)__reduce_add_sync(lanes, tiles) + nact - 1) / nact;
+    int jx = 0, jy = 0;  // column / row of the j-th tile inside the rectangle
+    for (int j = 0; j < H; ++j) {
       unsigned t = 0xFFFFFFFFu;
       if (j < (int)tiles &&
           tile_hits_spec(tc, so.x0, so.x1, so.y0, so.y1, tx0 + jx, ty0 + jy, b.tile)) {
@@ -160,8 +169,50 @@ __global__ void __launch_bounds__(256, 4) k_project(const BatchDev b) {
       }
       if (++jx == tw) { jx = 0; ++jy; }
       const unsigned peers = __match_any_sync(lanes, t);
-      if (t != 0xFFFFFFFFu && (threadIdx.x & 31) == __ffs(peers) - 1)
+      if (t != 0xFFFFFFFFu && lane == __ffs(peers) - 1)
         atomicAdd(&b.tile_cnt[t], (unsigned)__popc(peers));
+    }
+    // tail: the tiles beyond H of the lanes that have more, spread evenly over the warp
+    const int rest = (int)tiles > H ? (int)tiles - H : 0;
+    if (__any_sync(lanes, rest > 0)) {
+      float(*f)[32] = s_walk[warp];
+      f[0][lane] = tc.u; f[1][lane] = tc.v; f[2][lane] = tc.A; f[3][lane] = tc.B;
+      f[4][lane] = tc.C; f[5][lane] = tc.qmax; f[6][lane] = tc.rBC; f[7][lane] = tc.rBA;
+      f[8][lane] = __uint_as_float((uint32_t)so.x0 | ((uint32_t)so.x1 << 16));
+      f[9][lane] = __uint_as_float((uint32_t)so.y0 | ((uint32_t)so.y1 << 16));
+      f[10][lane] = __uint_as_float((uint32_t)tbase);
+      f[11][lane] = __int_as_float(tw);
+      f[12][lane] = 1.0f / (float)tw;
+      s_hits[warp][lane] = 0u;
+      s_any[warp][lane] = 0u;
+      const WarpWalk walk = warp_walk_begin(lanes, rest);
+      for (int base = 0; base < walk.total; base += walk.nact) {
+        int jr;
+        const int o = warp_walk_owner(walk, base, s_own[warp], jr);
+        unsigned t = 0xFFFFFFFFu;
+        if (o >= 0) {
+          const int j = H + jr;
+          TileCull oc;
+          oc.u = f[0][o]; oc.v = f[1][o]; oc.A = f[2][o]; oc.B = f[3][o];
+          oc.C = f[4][o]; oc.qmax = f[5][o]; oc.rBC = f[6][o]; oc.rBA = f[7][o];
+          const uint32_t rx = __float_as_uint(f[8][o]), ry = __float_as_uint(f[9][o]);
+          const int x0 = (int)(rx & 0xFFFFu), x1 = (int)(rx >> 16);
+          const int y0 = (int)(ry & 0xFFFFu), y1 = (int)(ry >> 16);
+          int ox, oy;
+          walk_tile(j, __float_as_int(f[11][o]), f[12][o], ox, oy);
+          if (tile_hits_spec(oc, x0, x1, y0, y1, x0 / b.tile + ox, y0 / b.tile + oy, b.tile)) {
+            t = __float_as_uint(f[10][o]) + (unsigned)(oy * cam.tiles_x + ox);
+            if (j < 32) atomicOr(&s_hits[warp][o], 1u << j);
+            s_any[warp][o] = 1u;
+          }
+        }
+        const unsigned peers = __match_any_sync(lanes, t);
+        if (t != 0xFFFFFFFFu && lane == __ffs(peers) - 1)
+          atomicAdd(&b.tile_cnt[t], (unsigned)__popc(peers));
+      }
+      __syncwarp(lanes);
+      hits |= s_hits[warp][lane];
+      any_pair = any_pair || s_any[warp][lane] != 0u;
     }
     // spatial visibility: grow the subset's bounding tile rectangle in this view by this
     // Gaussian's tile rectangle (lanes of one subset reduce first, one atomic each)
@@ -181,14 +232,14 @@ __global__ void __launch_bounds__(256, 4) k_project(const BatchDev b) {
     }
     // what fill needs to repeat exactly these decisions: the pass bits of the rectangle's
     // tiles when there are at most 32 of them, else the test's inputs
-    dst->d = make_float4(sA, sB, sC,
-                         tiles <= 32u ? __uint_as_float(hits) : (so.visible ? qmax : -1.0f));
+    if (so.visible)
+      dst->d = make_float4(sA, sB, sC, tiles <= 32u ? __uint_as_float(hits) : qmax);
   }
 }
 
 void launch_project(const BatchDev& b, cudaStream_t s) {
   const BatchDev& P = b;
-  const int threads = 256;
+  const int threads = kProjThreads;
   const int64_t blocks = (b.N + threads - 1) / threads;
   if (blocks == 0) return;
   switch (b.sh_degree) {

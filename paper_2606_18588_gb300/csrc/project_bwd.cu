@@ -119,18 +119,29 @@ __global__ void __launch_bounds__(kProjBwdThreads, 4) k_project_bwd(const BatchD
   for (int e = 0; e < NC * 3; ++e) gsh[e * kProjBwdThreads] = 0.f;
   bool any = false;
 
-  // the next view's 2-D gradient is loaded while this view's is processed
-  float4 nG0 = b.grad2d[g * 3], nG1 = b.grad2d[g * 3 + 1];
-  float ngb = b.grad2d[g * 3 + 2].x;
+  // the next view's 2-D gradient is loaded while this view's is processed; only views in
+  // which the Gaussian was projected (tile count > 0) can hold one
+  // (the count of the view after next is loaded a step ahead, off the loads' critical path)
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto seen_in = [&](int v) { return !b.counts || b.counts[(int64_t)v * b.N + g] != 0u; };
+  float4 nG0 = z4, nG1 = z4;
+  float ngb = 0.f;
+  if (seen_in(0)) {
+    nG0 = b.grad2d[g * 3];
+    nG1 = b.grad2d[g * 3 + 1];
+    ngb = b.grad2d[g * 3 + 2].x;
+  }
+  bool seen_next = b.V > 1 && seen_in(1);
   for (int v = 0; v < b.V; ++v) {
     float4* gp = b.grad2d + ((int64_t)v * b.N + g) * 3;
     const float4 G0 = nG0, G1 = nG1;
     const float gbl = ngb;
     if (v + 1 < b.V) {
       const float4* np = gp + (int64_t)b.N * 3;
-      nG0 = np[0];
-      nG1 = np[1];
-      ngb = np[2].x;
+      nG0 = seen_next ? np[0] : z4;
+      nG1 = seen_next ? np[1] : z4;
+      ngb = seen_next ? np[2].x : 0.f;
+      seen_next = v + 2 < b.V && seen_in(v + 2);
     }
     if (G0.x == 0.f && G0.y == 0.f && G0.z == 0.f && G0.w == 0.f && G1.x == 0.f && G1.y == 0.f &&
         G1.z == 0.f && G1.w == 0.f && gbl == 0.f)

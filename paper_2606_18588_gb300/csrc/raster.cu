@@ -150,6 +150,21 @@ __device__ __forceinline__ int compact_entries(const float4* sB, const float4* s
   return nl;
 }
 
+// Slots of a thread whose pixel lies in the rectangle [x0, x1] x [y0, y1]: bit i for slot i
+// (pixel (x + 8 col(i), y + 4 row(i))).  Unsigned differences test both bounds at once (a
+// pixel left of x0 wraps to a large value).
+template <int PPT>
+__device__ __forceinline__ unsigned rect_slots(int x, int y, int x0, int x1, int y0, int y1) {
+  const unsigned dx = (unsigned)(x - x0), dy = (unsigned)(y - y0);
+  const unsigned w = (unsigned)(x1 - x0), h = (unsigned)(y1 - y0);
+  const unsigned rows = (unsigned)(dy <= h) | ((unsigned)(dy + 4u <= h) << 1);
+  if (PPT == 4) {
+    const unsigned cols = (unsigned)(dx <= w) | ((unsigned)(dx + 8u <= w) << 1);
+    return ((rows & 1u) ? cols : 0u) | ((rows & 2u) ? cols << 2 : 0u);
+  }
+  return dx <= w ? rows : 0u;
+}
+
 template <int PPT>
 __device__ __forceinline__ int slot_col(int i) { return PPT == 4 ? (i & 1) : 0; }
 template <int PPT>
@@ -281,18 +296,16 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
         const float4 Bv = sB[jj];
         const float4 Cv = sC[jj];
         const uint32_t rx = __float_as_uint(Bv.w), ry = __float_as_uint(Cv.w);
-        const int x0 = (int)(rx & 0xFFFFu), x1 = (int)(rx >> 16);
-        const int y0 = (int)(ry & 0xFFFFu), y1 = (int)(ry >> 16);
-        const bool cA = ti.x >= x0 && ti.x <= x1;
-        const bool cB = PPT == 4 && ti.x + 8 >= x0 && ti.x + 8 <= x1;
-        const bool rA = ti.y >= y0 && ti.y <= y1, rB = ti.y + 4 >= y0 && ti.y + 4 <= y1;
+        // slots to evaluate: in the warp's blocks (bm), in the rectangle, still blending
+        const unsigned todo = bm & live &
+                              rect_slots<PPT>(ti.x, ti.y, (int)(rx & 0xFFFFu), (int)(rx >> 16),
+                                              (int)(ry & 0xFFFFu), (int)(ry >> 16));
         const float4 Av = sA[jj];
         const ColTerms ct0 = col_terms(Av, pcx0), ct1 = col_terms(Av, pcx1);
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
-          if (!((bm >> i) & 1u)) continue;  // no lane of the warp has slot i in the rectangle
+          if (!((todo >> i) & 1u)) continue;
           const int ci = slot_col<PPT>(i), ri = slot_row<PPT>(i);
-          if (!((live >> i) & 1u) || !(ci ? cB : cA) || !(ri ? rB : rA)) continue;
           if (kCount) ++n_pix;
           float alpha, ex, dy;
           bool cl;
@@ -515,7 +528,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) 
 }
 
 template <int TS, int PPT, bool kCount, bool kPersist>
-__global__ void __launch_bounds__(TS * TS / PPT, TS == 16 ? 14 : 1) k_raster_bwd(const BatchDev b) {
+__global__ void __launch_bounds__(TS * TS / PPT, TS == 16 ? 12 : 1) k_raster_bwd(const BatchDev b) {
   __shared__ float4 sA[kNB], sB[kNB], sC[kNB];
   __shared__ uint32_t sG[kNB];
   __shared__ float4 sQ[TS * TS];  // composite adjoint per pixel slot
