@@ -260,6 +260,17 @@ int splx_batch_loss_l1_dssim(splx_batch_t b, const float* rgb, const float* targ
  * their partial planes (treated as empty: C = 0, T = 1).  Results are identical with it on
  * or off.  enable = 0 turns it off for launches issued afterwards. */
 int splx_batch_set_visibility(splx_batch_t b, int32_t enable);
+/* Cross-boundary per-ray filtering (Sec. 8.1, appendix "Cross-boundary Gaussians
+ * Handling").  cells (host, [K][6] floats: lo x, y, z, hi x, y, z of subset k's k-d box,
+ * +-INFINITY on open sides; NaN rejected) turns it on for launches issued afterwards (and
+ * spatial visibility with it); NULL turns it off.  A Gaussian of subset k whose support box
+ * mu +- 3 s_max (FP32, s_max its largest activated scale exp(log_scale)) meets another
+ * cell s leaves the rays of every tile of view v that lies in Omega_v^s (the visible region
+ * of splx_batch_set_visibility) when its FP32 camera depth lies in the overlap of the two
+ * subsets' depth ranges in view v (min and max depth of the Gaussians the projection
+ * keeps).  Forward and backward take the same decisions; results change where a filtered
+ * Gaussian contributed.  Device memory: 8 B per Gaussian + 8 B per (view, subset). */
+int splx_batch_set_cross_filter(splx_batch_t b, const float* cells);
 /* Saturation skipping (Sec. 4.2 "saturation skipping", with the composite's threshold
  * eps_comp of splx_opts).  order (host, [V][K]) is, per view, a front-to-back order of the
  * K subsets (for k-d cells: the BSP order from the camera centre).  Once set, the forward

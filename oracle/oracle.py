@@ -79,8 +79,8 @@ def lib():
             _lib.orc_render.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
             _lib.orc_composite.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P, P, P]
             _lib.orc_render_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P, P, P, P, P,
-                                             P]
-            _lib.orc_backward_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P]
+                                             P, P]
+            _lib.orc_backward_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P]
             _lib.orc_adam.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_double,
                                       C.c_double, C.c_int64]
             _lib.orc_num_threads.restype = C.c_int
@@ -218,11 +218,21 @@ def _order(order, K):
     return a
 
 
+def _cells(cells, K):
+    """[K, 2, 3] k-d boxes (lo, hi; infinite on open sides) as the oracle's [K][6] floats."""
+    if cells is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(cells, np.float32).reshape(K, 6))
+    return a
+
+
 def render_view(scene, offsets, cam, o: Opts | None = None, tile_mask=None, separable=False,
-                order=None):
+                order=None, cells=None):
     """K contiguous subsets rendered and composited: dict(image, T, Cp, Tp, Dp, amb, sep,
     skip).  With `order` (front-to-back subset order) the partials are rendered in that
-    order with saturation skipping; skip[m, t] marks the tiles subset m left empty."""
+    order with saturation skipping; skip[m, t] marks the tiles subset m left empty.  With
+    `cells` (the subsets' k-d boxes [K, 2, 3]) cross-boundary Gaussians are filtered per
+    ray as in Sec. 8.1."""
     o = o or opts()
     k = _Keep(scene)
     c = camera(cam)
@@ -238,15 +248,16 @@ def render_view(scene, offsets, cam, o: Opts | None = None, tile_mask=None, sepa
     od = _order(order, K)
     B = int(o.tile)
     skip = np.zeros((K, ((H + B - 1) // B) * ((W + B - 1) // B)), np.uint8)
+    cl = _cells(cells, K)
     lib().orc_render_view(C.byref(k.p), _ptr(off), K, C.byref(c), C.byref(o), _ptr(tm), _ptr(od),
-                          _ptr(out), _ptr(To), _ptr(Cp), _ptr(Tp), _ptr(Dp), _ptr(amb), _ptr(sep),
-                          _ptr(skip), _ptr(st))
+                          _ptr(cl), _ptr(out), _ptr(To), _ptr(Cp), _ptr(Tp), _ptr(Dp), _ptr(amb),
+                          _ptr(sep), _ptr(skip), _ptr(st))
     return dict(image=out, T=To, Cp=Cp, Tp=Tp, Dp=Dp, amb=amb, sep=sep, skip=skip,
                 evaluated=int(st[0]))
 
 
 def backward_view(scene, offsets, cam, dLdC, dLdT=None, o: Opts | None = None, tile_mask=None,
-                  order=None):
+                  order=None, cells=None):
     """Gradients (float64) of sum(dLdC*C) + sum(dLdT*T) w.r.t. every parameter array
     (restricted to the pixels of tiles where tile_mask is nonzero, if given; with `order`,
     of the saturation-skipping render)."""
@@ -260,8 +271,9 @@ def backward_view(scene, offsets, cam, dLdC, dLdT=None, o: Opts | None = None, t
     dC = np.ascontiguousarray(dLdC, np.float64)
     dT = None if dLdT is None else np.ascontiguousarray(dLdT, np.float64)
     tm = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8)
+    cl = _cells(cells, K)
     lib().orc_backward_view(C.byref(k.p), _ptr(off), K, C.byref(c), C.byref(o), _ptr(dC), _ptr(dT),
-                            _ptr(tm), _ptr(_order(order, K)), C.byref(gr))
+                            _ptr(tm), _ptr(_order(order, K)), _ptr(cl), C.byref(gr))
     return g
 
 

@@ -24,6 +24,7 @@
 //   3-sigma rectangle; alpha in [1/255, 0.99]; a pixel stops before the Gaussian that would
 //   take its transmittance below eps_T; colour = max(0, SH + 0.5).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -494,7 +495,51 @@ struct Subset {
   Tiles tiles;
 };
 
-Subset prepare(const orc_params& p, const orc_camera& cam, int B, float amin) {
+// Cross-boundary per-ray filtering (Sec. 8.1, appendix "Cross-boundary Gaussians
+// Handling"), in one view.  Q_cross: a Gaussian of cell k whose support box
+// mu +- 3 s_max (FP32; s_max its largest activated scale) meets another cell s.  D_m: the
+// range of the specification's FP32 depths of subset m's kept Gaussians; Omega_m: the
+// bounding rectangle of the tile rectangles of its Gaussians that have a (Gaussian, tile)
+// pair.  The Gaussian leaves the rays of
+// tile t (a tile of its own pairs, hence of Omega_k) when, for some such s, t lies in
+// Omega_s and its depth in D_k n D_s.
+struct CrossFilter {
+  std::vector<uint64_t> cross;       // per global Gaussian: bit s, the support meets cell s
+  std::vector<int> omega;            // [K][4] tx0, ty0, tx1, ty1 (tx0 > tx1: empty)
+  std::vector<uint32_t> dmin, dmax;  // [K] depth bits (dmin > dmax: no kept Gaussian)
+  bool removes(int64_t g, int k, int tx, int ty, uint32_t dbits) const {
+    const uint64_t c = cross[g];
+    for (int s = 0; s < 64; ++s) {
+      if (!((c >> s) & 1ull)) continue;
+      const int* o = &omega[4 * s];
+      if (tx < o[0] || tx > o[2] || ty < o[1] || ty > o[3]) continue;
+      const uint32_t lo = std::max(dmin[k], dmin[s]), hi = std::min(dmax[k], dmax[s]);
+      if (dbits >= lo && dbits <= hi) return true;
+    }
+    return false;
+  }
+};
+
+// Removes from subset m's tile lists the pairs the filter takes out (global index goff + i).
+void apply_filter(Subset& s, const CrossFilter& f, int m, int64_t goff) {
+  const int nt = s.tiles.tw * s.tiles.th;
+  std::vector<int64_t> start(nt + 1, 0);
+  std::vector<int32_t> list;
+  list.reserve(s.tiles.list.size());
+  for (int t = 0; t < nt; ++t) {
+    const int tx = t % s.tiles.tw, ty = t / s.tiles.tw;
+    for (int64_t j = s.tiles.start[t]; j < s.tiles.start[t + 1]; ++j) {
+      const int32_t i = s.tiles.list[j];
+      if (!f.removes(goff + i, m, tx, ty, s.bins[i].depth_bits)) list.push_back(i);
+    }
+    start[t + 1] = (int64_t)list.size();
+  }
+  s.tiles.start.swap(start);
+  s.tiles.list.swap(list);
+}
+
+Subset prepare(const orc_params& p, const orc_camera& cam, int B, float amin,
+               const CrossFilter* f = nullptr, int m = 0, int64_t goff = 0) {
   Subset s;
   s.bins.resize(p.n);
   s.pr.resize(p.n);
@@ -504,6 +549,7 @@ Subset prepare(const orc_params& p, const orc_camera& cam, int B, float amin) {
     if (s.bins[i].visible) s.pr[i] = project64(p, i, cam);
   }
   s.tiles = build_tiles(s.bins, cam.width, cam.height, B, amin);
+  if (f) apply_filter(s, *f, m, goff);
   return s;
 }
 
@@ -517,6 +563,60 @@ orc_params slice(const orc_params& p, int64_t lo, int64_t hi) {
   q.sh = p.sh + lo * nc * 3;
   q.n = hi - lo;
   return q;
+}
+
+// The filter of one view over K contiguous subsets; cells [K][6] = (lo x, y, z, hi x, y, z)
+// of the k-d boxes (infinite on open sides).
+CrossFilter make_filter(const orc_params& p, const int64_t* offsets, int K, const orc_camera& cam,
+                        const orc_opts& o, const float* cells) {
+  CrossFilter f;
+  f.cross.assign((size_t)p.n, 0ull);
+  f.omega.assign((size_t)4 * K, 0);
+  f.dmin.assign(K, 0xFFFFFFFFu);
+  f.dmax.assign(K, 0u);
+  for (int m = 0; m < K; ++m) {
+    orc_params q = slice(p, offsets[m], offsets[m + 1]);
+    const Subset s = prepare(q, cam, o.tile, (float)o.alpha_min);
+    // Omega (reading 14): the bounding rectangle of the tile rectangles of the subset's
+    // Gaussians that have at least one (Gaussian, tile) pair
+    int* om = &f.omega[(size_t)4 * m];
+    om[0] = om[1] = INT_MAX;
+    om[2] = om[3] = -1;
+    std::vector<uint8_t> paired((size_t)q.n, 0);
+    for (size_t j = 0; j < s.tiles.list.size(); ++j) paired[s.tiles.list[j]] = 1;
+    const int B = o.tile;
+    for (int64_t i = 0; i < q.n; ++i) {
+      if (!paired[i]) continue;
+      const BinRec& b = s.bins[i];
+      om[0] = std::min(om[0], b.x0 / B); om[1] = std::min(om[1], b.y0 / B);
+      om[2] = std::max(om[2], b.x1 / B); om[3] = std::max(om[3], b.y1 / B);
+    }
+    for (int64_t i = 0; i < q.n; ++i) {
+      if (!s.bins[i].visible) continue;
+      f.dmin[m] = std::min(f.dmin[m], s.bins[i].depth_bits);
+      f.dmax[m] = std::max(f.dmax[m], s.bins[i].depth_bits);
+    }
+    for (int64_t i = 0; i < q.n; ++i) {
+      float smax = 0.0f;
+      for (int a = 0; a < 3; ++a) smax = std::max(smax, exp_spec((float)q.log_scales[3 * i + a]));
+      const float r3 = 3.0f * smax;
+      float lo[3], hi[3];
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = (float)q.means[3 * i + a] - r3;
+        hi[a] = (float)q.means[3 * i + a] + r3;
+      }
+      uint64_t mask = 0;
+      for (int c = 0; c < K; ++c) {
+        if (c == m) continue;
+        const float* b = cells + 6 * c;
+        if (lo[0] <= b[3] && hi[0] >= b[0] && lo[1] <= b[4] && hi[1] >= b[1] && lo[2] <= b[5] &&
+            hi[2] >= b[2])
+          mask |= 1ull << c;
+      }
+      f.cross[(size_t)(offsets[m] + i)] = mask;
+    }
+  }
+  return f;
 }
 
 // Composite order of one pixel (Eq. 5 with the normalised-depth reading).  Fills `ord`
@@ -546,9 +646,11 @@ int composite_order(int K, const double* Tm, const double* Dm, const orc_opts& o
 
 }  // namespace
 
-extern "C" int orc_render(const orc_params* p, const orc_camera* cam, const orc_opts* o,
-                          const uint8_t* tile_mask, double* C, double* T, double* D,
-                          int32_t* last, int32_t* ncontrib, uint8_t* amb, int64_t* stats);
+// Local render of one subset (filtered by f as subset m with global offset goff, if given).
+int render_subset(const orc_params* p, const orc_camera* cam, const orc_opts* o,
+                  const uint8_t* tile_mask, double* C, double* T, double* D, int32_t* last,
+                  int32_t* ncontrib, uint8_t* amb, int64_t* stats, const CrossFilter* f, int m,
+                  int64_t goff);
 
 namespace {
 
@@ -561,7 +663,8 @@ namespace {
 void render_partials(const orc_params& p, const int64_t* offsets, int K, const orc_camera& cam,
                      const orc_opts& o, const uint8_t* tile_mask, const int32_t* order,
                      std::vector<double>& C, std::vector<double>& T, std::vector<double>& D,
-                     std::vector<uint8_t>& skip, uint8_t* amb, int64_t* stats) {
+                     std::vector<uint8_t>& skip, uint8_t* amb, int64_t* stats,
+                     const CrossFilter* f) {
   const int W = cam.width, H = cam.height, B = o.tile;
   const int64_t HW = (int64_t)W * H;
   const int tw = (W + B - 1) / B, th = (H + B - 1) / B, nt = tw * th;
@@ -589,8 +692,9 @@ void render_partials(const orc_params& p, const int64_t* offsets, int K, const o
     }
     orc_params q = slice(p, offsets[m], offsets[m + 1]);
     std::fill(a1.begin(), a1.end(), 0);
-    orc_render(&q, &cam, &o, mask.data(), C.data() + (size_t)m * 3 * HW, T.data() + (size_t)m * HW,
-               D.data() + (size_t)m * HW, nullptr, nullptr, a1.data(), stats);
+    render_subset(&q, &cam, &o, mask.data(), C.data() + (size_t)m * 3 * HW,
+                  T.data() + (size_t)m * HW, D.data() + (size_t)m * HW, nullptr, nullptr,
+                  a1.data(), stats, f, m, offsets[m]);
     if (amb)
       for (int64_t i = 0; i < HW; ++i) amb[i] |= a1[i];
     if (order)
@@ -672,8 +776,16 @@ void orc_project(const orc_params* p, const orc_camera* cam, double* out) {
 int orc_render(const orc_params* p, const orc_camera* cam, const orc_opts* o,
                const uint8_t* tile_mask, double* C, double* T, double* D, int32_t* last,
                int32_t* ncontrib, uint8_t* amb, int64_t* stats) {
+  return render_subset(p, cam, o, tile_mask, C, T, D, last, ncontrib, amb, stats, nullptr, 0, 0);
+}
+}  // extern "C"
+
+int render_subset(const orc_params* p, const orc_camera* cam, const orc_opts* o,
+                  const uint8_t* tile_mask, double* C, double* T, double* D, int32_t* last,
+                  int32_t* ncontrib, uint8_t* amb, int64_t* stats, const CrossFilter* f, int m,
+                  int64_t goff) {
   const int W = cam->width, H = cam->height, B = o->tile;
-  Subset s = prepare(*p, *cam, B, (float)o->alpha_min);
+  Subset s = prepare(*p, *cam, B, (float)o->alpha_min, f, m, goff);
   const int nt = s.tiles.tw * s.tiles.th;
   int64_t evaluated = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : evaluated)
@@ -699,6 +811,8 @@ int orc_render(const orc_params* p, const orc_camera* cam, const orc_opts* o,
   if (stats) stats[0] += evaluated;
   return 0;
 }
+
+extern "C" {
 
 // Global composition of K partials [Eq. 5].  Partials planar: C[K][3][H][W],
 // T[K][H][W], D[K][H][W].  Outputs image [3][H][W], total transmittance [H][W], the
@@ -737,12 +851,15 @@ int orc_composite(int32_t K, int32_t H, int32_t W, const double* Cp, const doubl
 // concatenation of per-subset runs in composite order (where Eq. 5 equals Eq. 2).
 int orc_render_view(const orc_params* p, const int64_t* offsets, int32_t K, const orc_camera* cam,
                     const orc_opts* o, const uint8_t* tile_mask, const int32_t* order,
-                    double* out, double* Tout, double* Cp, double* Tp, double* Dp, uint8_t* amb,
-                    uint8_t* sep, uint8_t* skip_out, int64_t* stats) {
+                    const float* cells, double* out, double* Tout, double* Cp, double* Tp,
+                    double* Dp, uint8_t* amb, uint8_t* sep, uint8_t* skip_out, int64_t* stats) {
   const int64_t HW = (int64_t)cam->width * cam->height;
   std::vector<double> C, T, D;
   std::vector<uint8_t> a(HW, 0), skip;
-  render_partials(*p, offsets, K, *cam, *o, tile_mask, order, C, T, D, skip, a.data(), stats);
+  CrossFilter cf;
+  if (cells) cf = make_filter(*p, offsets, K, *cam, *o, cells);
+  render_partials(*p, offsets, K, *cam, *o, tile_mask, order, C, T, D, skip, a.data(), stats,
+                  cells ? &cf : nullptr);
   if (skip_out) std::memcpy(skip_out, skip.data(), skip.size());
   orc_composite(K, cam->height, cam->width, C.data(), T.data(), D.data(), o, out, Tout, nullptr,
                 a.data());
@@ -800,18 +917,21 @@ int orc_render_view(const orc_params* p, const int64_t* offsets, int32_t K, cons
 int orc_backward_view(const orc_params* p, const int64_t* offsets, int32_t K,
                       const orc_camera* cam, const orc_opts* o, const double* dLdC,
                       const double* dLdT, const uint8_t* tile_mask, const int32_t* order,
-                      const orc_grads* gr) {
+                      const float* cells, const orc_grads* gr) {
   const int W = cam->width, H = cam->height, B = o->tile;
   const int64_t HW = (int64_t)W * H;
   const int nc = (p->sh_degree + 1) * (p->sh_degree + 1);
+  CrossFilter cf;
+  if (cells) cf = make_filter(*p, offsets, K, *cam, *o, cells);
+  const CrossFilter* fp = cells ? &cf : nullptr;
   std::vector<Subset> subs(K);
   for (int m = 0; m < K; ++m) {
     orc_params q = slice(*p, offsets[m], offsets[m + 1]);
-    subs[m] = prepare(q, *cam, B, (float)o->alpha_min);
+    subs[m] = prepare(q, *cam, B, (float)o->alpha_min, fp, m, offsets[m]);
   }
   std::vector<double> C, T, D;
   std::vector<uint8_t> skip;
-  render_partials(*p, offsets, K, *cam, *o, tile_mask, order, C, T, D, skip, nullptr, nullptr);
+  render_partials(*p, offsets, K, *cam, *o, tile_mask, order, C, T, D, skip, nullptr, nullptr, fp);
   // per-Gaussian 2-D gradients: u, v, A, B, C, o, r, g, b (threads add atomically)
   std::vector<double> g2((size_t)p->n * 9, 0.0);
   const int tw = (W + B - 1) / B, th = (H + B - 1) / B;

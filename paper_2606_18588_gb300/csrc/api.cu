@@ -189,6 +189,11 @@ struct Plan {
   uint32_t* omega = nullptr;               // [V][K][4] visible regions (internal partials only)
   bool visibility = false;                 // use omega (batches and server launches)
   float* tpre = nullptr;                   // [total pixels] prefix transmittance of the waves
+  float* cells_d = nullptr;                // [K][6] k-d boxes (cross-boundary filtering)
+  unsigned long long* cross = nullptr;     // [N] cells each Gaussian's support meets
+  uint32_t* zr = nullptr;                  // [V][K][2] depth ranges (min, ~max bits)
+  uint32_t* removed = nullptr;             // [n_tiles] pairs the filter removed per tile
+  bool cross_filter = false;               // filter cross-boundary Gaussians per ray
   void* scan_temp = nullptr;
   int64_t capacity = 0, n_tiles = 0, total_pixels = 0;
   splx_opts opts{};
@@ -250,6 +255,11 @@ struct Plan {
     b.persist_grid = persist_grid;
     b.work_ctr = work_ctr;
     b.omega = visibility ? omega : nullptr;
+    const bool cf = cross_filter && visibility && omega && cells_d && cross && zr && removed;
+    b.cells = cf ? cells_d : nullptr;
+    b.cross = cf ? cross : nullptr;
+    b.zr = cf ? zr : nullptr;
+    b.removed = cf ? removed : nullptr;
     b.order = nullptr;  // set per launch by the forward's waves
     b.wave = 0;
     b.tpre = tpre;
@@ -270,7 +280,8 @@ struct Plan {
                    (void**)&keys_alt, (void**)&big_list, (void**)&big_count, (void**)&chunks,
                    (void**)&chunk_count, (void**)&ranges,
                    (void**)&grad2d, (void**)&scan_temp, (void**)&counters, (void**)&work_ctr,
-                   (void**)&order_d, (void**)&tpre, (void**)&omega};
+                   (void**)&order_d, (void**)&tpre, (void**)&omega, (void**)&cells_d,
+                   (void**)&cross, (void**)&zr, (void**)&removed};
     for (void** p : ps) free_ptr(*p, s);
     for (auto& e : ev)
       if (e) { cudaEventDestroy(e); e = nullptr; }
@@ -287,6 +298,10 @@ struct Plan {
     CK(cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(n_tiles, 1), s));
     if (visibility && omega)
       CK(cudaMemsetAsync(omega, 0xFF, sizeof(uint32_t) * 4 * (size_t)V * K, s));
+    if (b.zr) {
+      CK(cudaMemsetAsync(zr, 0xFF, sizeof(uint32_t) * 2 * (size_t)V * K, s));
+      CK(cudaMemsetAsync(removed, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(n_tiles, 1), s));
+    }
     CK(cudaMemsetAsync(big_count, 0, sizeof(unsigned), s));
     CK(cudaMemsetAsync(chunk_count, 0, sizeof(unsigned), s));
     mark(0, s);
@@ -1015,6 +1030,30 @@ int splx_batch_set_order(splx_batch_t bt, const int32_t* order) {
     return r;
   }
   CK(cudaMemcpy(P.order_d, order, sizeof(int32_t) * P.V * P.K, cudaMemcpyHostToDevice));
+  return SPLX_OK;
+}
+
+int splx_batch_set_cross_filter(splx_batch_t bt, const float* cells) {
+  if (!bt) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  CtxScope scope(P.ctx);
+  if (!cells) {
+    P.cross_filter = false;
+    return SPLX_OK;
+  }
+  for (int i = 0; i < 6 * P.K; ++i)
+    if (std::isnan(cells[i])) return SPLX_ERR_INVALID;
+  int r;
+  if (!P.cells_d && (r = ctx_alloc_t(P.ctx, &P.cells_d, (size_t)6 * P.K, nullptr))) return r;
+  if (!P.cross && (r = ctx_alloc_t(P.ctx, &P.cross, (size_t)std::max<int64_t>(P.N, 1), nullptr)))
+    return r;
+  if (!P.zr && (r = ctx_alloc_t(P.ctx, &P.zr, (size_t)2 * P.V * P.K, nullptr))) return r;
+  if (!P.removed &&
+      (r = ctx_alloc_t(P.ctx, &P.removed, (size_t)std::max<int64_t>(P.n_tiles, 1), nullptr)))
+    return r;
+  CK(cudaMemcpy(P.cells_d, cells, sizeof(float) * 6 * P.K, cudaMemcpyHostToDevice));
+  P.cross_filter = true;
+  P.visibility = true;
   return SPLX_OK;
 }
 

@@ -6,10 +6,12 @@
 // counting the tile's counter back down (lanes of a warp that hit the same tile take a
 // block of slots with one atomic; the counters end at zero).  Keys are unique within a
 // tile, so sorting each segment by the full 64-bit key yields the (depth, index) order
-// exactly, whatever order fill placed them in.
+// exactly, whatever order fill placed them in.  With cross-boundary filtering on, a pair
+// the filter removes keeps its slot with depth bits 0xFFFFFFFF, so it sorts last, and the
+// tile's range ends before it.
 //
-// Sorting: a segment of up to 2048 keys is sorted in shared memory by one CTA (bitonic
-// network).  Longer segments are cut into 2048-key chunks, each sorted the same way, and
+// Sorting: a segment of up to 2048 keys is sorted in shared memory by one CTA (8 keys per
+// thread by a transposition network, then merge-path merges of runs).  Longer segments are cut into 2048-key chunks, each sorted the same way, and
 // then merged pairwise in rounds (run width 2048, 4096, ...) with merge-path partitioning,
 // one CTA per 2048 outputs, ping-ponging between the key buffer and its twin; segments
 // that end in the twin are copied back.  Every pair is read and written a few times
@@ -89,9 +91,9 @@ __device__ __forceinline__ void sort_chunk(uint64_t* keys, int n, uint64_t* sa, 
       const int d = o - p0;
       int ia = merge_path_smem(src, p0, w, p0 + w, w, d);
       int ib = d - ia;
-      // heads of both runs in registers (~0 past a run's end; keys are below 2^63, and
-      // the ~0 padding keys are equal, so their order does not matter); each output
-      // reloads only the head it consumed
+      // heads of both runs in registers (~0 past a run's end; a key is below ~0 (its index
+      // is below 2^32 - 1), and the ~0 padding keys are equal, so their order does not
+      // matter); each output reloads only the head it consumed
       uint64_t va = ia < w ? src[pad(p0 + ia)] : ~0ull;
       uint64_t vb = ib < w ? src[pad(p0 + w + ib)] : ~0ull;
 #pragma unroll
@@ -209,6 +211,23 @@ __global__ void __launch_bounds__(kFillThreads, 6) k_fill(const BatchDev b) {
   bool overflow = false;
   // one (tile, key) candidate per lane: aggregate per tile, take slots, write the keys
   auto place = [&](unsigned t, uint64_t k) {
+    if (b.cross && t != 0xFFFFFFFFu) {
+      // cross-boundary filtering: a removed pair keeps its slot with the largest depth
+      const unsigned long long c = b.cross[(uint32_t)k];
+      if (c) {
+        const int v = view_of(b.tile_base, b.V, (int64_t)t);
+        const ViewDev& cam = b.views[v];
+        const int64_t nt = (int64_t)cam.tiles_x * cam.tiles_y;
+        const int64_t rem = (int64_t)t - b.tile_base[v];
+        const int km = (int)(rem / nt);
+        const int loc = (int)(rem - (int64_t)km * nt);
+        if (cross_removed(b, v, km, c, loc % cam.tiles_x, loc / cam.tiles_x,
+                          (uint32_t)(k >> 32))) {
+          k = (0xFFFFFFFFull << 32) | (k & 0xFFFFFFFFull);
+          atomicAdd(&b.removed[t], 1u);
+        }
+      }
+    }
     const unsigned peers = __match_any_sync(lanes, t);
     const int leader = __ffs(peers) - 1;
     unsigned old = 0;
@@ -285,7 +304,11 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_sort_small(const BatchDev 
   const int64_t t = item_of(b, blockIdx.x);
   uint32_t s, e;
   segment_of(b, t, s, e);
-  if (threadIdx.x == 0) b.ranges[t] = make_uint2(s, e);
+  // the pairs the cross-boundary filter removed sort last and stay out of the range
+  if (threadIdx.x == 0) {
+    const uint32_t cut = b.removed ? min(b.removed[t], e - s) : 0u;
+    b.ranges[t] = make_uint2(s, e - cut);
+  }
   const int n = (int)(e - s);
   if (n <= 1) return;
   // saturation-skipping waves sort only what the wave's rasteriser will walk

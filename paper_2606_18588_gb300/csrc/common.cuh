@@ -122,6 +122,17 @@ struct BatchDev {
   // projection with atomicMin (all four start at 0xFFFFFFFF, i.e. empty).  Work items
   // outside it have no pairs; their partial planes are neither written nor read.
   uint32_t* omega;
+  // cross-boundary per-ray filtering (cross != nullptr; needs omega): cells [K][6] = the
+  // subsets' k-d boxes (lo x, y, z, hi x, y, z); cross [N] = per Gaussian the mask of other
+  // cells its support box mu +- 3 s_max meets; zr [V][K][2] = per (view, subset) the depth
+  // range of its kept Gaussians as (min bits, ~max bits), built by the projection with
+  // atomicMin (both start at 0xFFFFFFFF, i.e. empty)
+  const float* cells;
+  unsigned long long* cross;
+  uint32_t* zr;
+  // per image tile, the pairs the filter removed: the fill gives them the largest depth,
+  // so they sort last, and the tile's range ends before them (zero between runs)
+  uint32_t* removed;
   // saturation skipping (order != nullptr): the forward rasteriser runs in K waves; wave r
   // renders subset order[v * K + r] of every view v, and tpre [total pixels] holds the
   // product of the transmittances of the subsets rendered so far
@@ -234,6 +245,29 @@ __device__ __forceinline__ bool item_saturated(const BatchDev& b, int64_t id) {
     if (x < cam.W && y < cam.H) open |= tp[(int64_t)y * cam.W + x] >= b.eps_comp;
   }
   return !__syncthreads_or(open);
+}
+
+// Cross-boundary per-ray filtering (Sec. 8.1): whether a Gaussian of subset k whose support
+// meets the other cells in mask c, at depth bits dbits, leaves the rays of tile (tx, ty) of
+// view v: for some such cell s, the tile lies in subset s's visible region and the depth in
+// the overlap of the two subsets' depth ranges.  (The tile holds a pair of the Gaussian, so
+// it lies in k's.)
+__device__ __forceinline__ bool cross_removed(const BatchDev& b, int v, int k,
+                                              unsigned long long c, int tx, int ty,
+                                              uint32_t dbits) {
+  const uint32_t* zk = b.zr + 2 * ((int64_t)v * b.K + k);
+  const uint32_t kmin = zk[0], kmax = ~zk[1];
+  while (c) {
+    const int s = __ffsll((long long)c) - 1;
+    c &= c - 1ull;
+    const uint4 o = reinterpret_cast<const uint4*>(b.omega)[v * b.K + s];
+    const uint32_t x = (uint32_t)tx, y = (uint32_t)ty;
+    if (x < o.x || y < o.y || x > ~o.z || y > ~o.w) continue;
+    const uint32_t* zs = b.zr + 2 * ((int64_t)v * b.K + s);
+    const uint32_t lo = max(kmin, zs[0]), hi = min(kmax, ~zs[1]);
+    if (dbits >= lo && dbits <= hi) return true;
+  }
+  return false;
 }
 
 // Whether tile (tx, ty) of view v lies in subset k's visible region (always, if off).

@@ -90,6 +90,25 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(const BatchDev b) {
   const bool sh_vec = (NC * 3) % 4 == 0 && (reinterpret_cast<uintptr_t>(shp) & 15) == 0;
 
   const SpecG G = spec_gaussian(ls, q);  // view-independent part of the specification
+  if (b.cross) {
+    // cross-boundary filtering: the other cells that the support box mu +- 3 s_max meets
+    // (FP32 basic operations on the specification's activated scales)
+    float smax = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) smax = fmaxf(smax, exp_spec(ls[a]));
+    const float r3 = fm(3.0f, smax);
+    const float lo[3] = {fs(m[0], r3), fs(m[1], r3), fs(m[2], r3)};
+    const float hi[3] = {fa(m[0], r3), fa(m[1], r3), fa(m[2], r3)};
+    unsigned long long mask = 0ull;
+    for (int c = 0; c < b.K; ++c) {
+      if (c == k) continue;
+      const float* cb = b.cells + 6 * c;
+      if (lo[0] <= cb[3] && hi[0] >= cb[0] && lo[1] <= cb[4] && hi[1] >= cb[1] &&
+          lo[2] <= cb[5] && hi[2] >= cb[2])
+        mask |= 1ull << c;
+    }
+    b.cross[g] = mask;
+  }
   for (int v = 0; v < b.V; ++v) {
     const ViewDev& cam = b.views[v];
     const SpecOut so = bin_spec(m, G, cam.R, cam.t, cam.fx, cam.fy, cam.cx, cam.cy, cam.W,
@@ -213,6 +232,19 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(const BatchDev b) {
       __syncwarp(lanes);
       hits |= s_hits[warp][lane];
       any_pair = any_pair || s_any[warp][lane] != 0u;
+    }
+    // cross-boundary filtering: the depth range of the subset's kept Gaussians in this view
+    if (b.zr) {
+      const unsigned peers = __match_any_sync(lanes, so.visible ? k : -1);
+      if (so.visible) {
+        const uint32_t d = __float_as_uint(so.tz);
+        const uint32_t dmin = __reduce_min_sync(peers, d), ndmax = __reduce_min_sync(peers, ~d);
+        if (lane == __ffs(peers) - 1) {
+          uint32_t* z = b.zr + 2 * ((int64_t)v * b.K + k);
+          atomicMin(z, dmin);
+          atomicMin(z + 1, ndmax);
+        }
+      }
     }
     // spatial visibility: grow the subset's bounding tile rectangle in this view by this
     // Gaussian's tile rectangle (lanes of one subset reduce first, one atomic each)

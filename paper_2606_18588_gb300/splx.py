@@ -93,6 +93,7 @@ _sigs = {
     "splx_batch_set_launch": (C.c_int, [_P, C.c_int32]),
     "splx_batch_set_order": (C.c_int, [_P, _P]),
     "splx_batch_set_visibility": (C.c_int, [_P, C.c_int32]),
+    "splx_batch_set_cross_filter": (C.c_int, [_P, _P]),
     "splx_batch_loss_l1_dssim": (C.c_int, [_P, _P, _P, C.c_float, _P, _P, _P]),
     "splx_loss_l1_dssim": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32, C.c_float, _P, _P, _P]),
     "splx_batch_max_ctas_per_sm": (C.c_int, [_P, _P, _P]),
@@ -472,6 +473,16 @@ class Batch:
         """Spatial visibility regions on (default) or off; results are identical."""
         _check(_lib.splx_batch_set_visibility(self.h, int(bool(enable))),
                "splx_batch_set_visibility")
+
+    def set_cross_filter(self, cells):
+        """Cross-boundary per-ray filtering with the subsets' k-d boxes [K, 2, 3] (lo, hi;
+        infinite on open sides), or off (None); see splx_batch_set_cross_filter."""
+        if cells is None:
+            _check(_lib.splx_batch_set_cross_filter(self.h, None), "splx_batch_set_cross_filter")
+            return
+        a = np.ascontiguousarray(np.asarray(cells, np.float32).reshape(self.K, 6))
+        _check(_lib.splx_batch_set_cross_filter(self.h, a.ctypes.data_as(C.c_void_p)),
+               "splx_batch_set_cross_filter")
 
     def set_order(self, order):
         """Saturation skipping with a [V, K] front-to-back subset order per view (None:

@@ -689,3 +689,90 @@ def test_ssim_gradient_finite_differences():
         xm[v][idx] -= h
         fd = (O.loss_l1_dssim(xp, ys)[0] - O.loss_l1_dssim(xm, ys)[0]) / (2 * h)
         assert abs(fd - g[v][idx]) <= 1e-7 * max(1.0, abs(fd)) + 1e-9, (v, idx, fd, g[v][idx])
+
+
+# --------------------------------------------------------------------------- cross-boundary
+# Per-ray filtering of cross-boundary Gaussians (Sec. 8.1): the configuration of the
+# paper's example.  Two cells split at x = 0; G1 (depth 2) and G3 (depth 4) belong to cell
+# 0, G2 (depth 3) and G4 (depth 5) to cell 1; G3's 3-sigma support reaches into cell 1.
+_INF = float("inf")
+_TWO_CELLS = np.array([[[-_INF, -_INF, -_INF], [0.0, _INF, _INF]],
+                       [[0.0, -_INF, -_INF], [_INF, _INF, _INF]]])
+
+
+def _cross_example(with_g3=True):
+    # camera at z = -1 looking along +z: depth = z + 1
+    g = [((-0.2, 0.0, 1.0), math.log(0.05), (1.0, 0.2, 0.2)),   # G1, cell 0
+         ((-0.02, 0.0, 3.0), math.log(0.3), (0.2, 1.0, 0.2)),   # G3, cell 0, crosses x = 0
+         ((0.2, 0.0, 2.0), math.log(0.02), (0.2, 0.2, 1.0)),    # G2, cell 1
+         ((0.3, 0.0, 4.0), math.log(0.03), (0.9, 0.9, 0.1))]    # G4, cell 1
+    if not with_g3:
+        g = [g[0], g[2], g[3]]
+    n = len(g)
+    sc = _scene([x[0] for x in g], [[x[1]] * 3 for x in g], [[1.0, 0.0, 0.0, 0.0]] * n,
+                [_logit(0.8)] * n, rgb=[x[2] for x in g])
+    off = np.array([0, n - 2, n])
+    cam = I.pinhole(64, 64, 60.0, (0.0, 0.0, -1.0), (0.0, 0.0, 1.0), 0.01)
+    return sc, off, cam
+
+
+def test_cross_boundary_filter_removes_g3_only_where_both_cells_are_seen():
+    o = O.opts(eps_T=0.0, eps_comp=0.0)
+    sc, off, cam = _cross_example()
+    sc3, off3, _ = _cross_example(with_g3=False)
+    filt = O.render_view(sc, off, cam, o, cells=_TWO_CELLS)["image"]
+    full = O.render_view(sc, off, cam, o)["image"]
+    without = O.render_view(sc3, off3, cam, o)["image"]
+    # Omega of cell 1: the bounding rectangle of the tile rectangles of its paired Gaussians
+    B, tw = 16, 4
+    c1 = sc.subset(2, 4)
+    start, lst = O.tile_lists(c1, cam)
+    _, rect, _ = O.bin(c1, cam)
+    r = rect[np.unique(lst)] // B
+    omega1 = [ty * tw + tx for ty in range(r[:, 2].min(), r[:, 3].max() + 1)
+              for tx in range(r[:, 0].min(), r[:, 1].max() + 1)]
+    start3, _ = O.tile_lists(sc.subset(1, 2), cam)
+    g3_tiles = np.nonzero(np.diff(start3) > 0)[0]
+    assert set(omega1) < set(g3_tiles)  # G3 also covers tiles cell 1 does not see
+    changed = 0
+    for t in range(16):
+        ys, xs = slice((t // tw) * B, (t // tw + 1) * B), slice((t % tw) * B, (t % tw + 1) * B)
+        ref = without if t in omega1 else full
+        assert np.array_equal(filt[:, ys, xs], ref[:, ys, xs]), t
+        changed += int(not np.array_equal(full[:, ys, xs], without[:, ys, xs]))
+    assert changed >= 3  # G3 matters on its tiles, so both branches are exercised
+
+
+def test_cross_boundary_filter_keeps_gaussians_outside_the_depth_overlap():
+    # G3 moved in front of cell 1's depth range: kept everywhere
+    o = O.opts(eps_T=0.0, eps_comp=0.0)
+    sc, off, cam = _cross_example()
+    sc.means[1, 2] = 1.5  # depth 2.5 < D_1 = [3, 5]
+    filt = O.render_view(sc, off, cam, o, cells=_TWO_CELLS)["image"]
+    full = O.render_view(sc, off, cam, o)["image"]
+    assert np.array_equal(filt, full)
+
+
+def test_cross_boundary_filter_is_the_identity_without_crossing_gaussians():
+    rng = np.random.default_rng(8)
+    sc = I.uniform_scene(6000, 8, 1, log_scale_mu=-6.0, log_scale_sigma=0.2)
+    perm, off, boxes = I.kd_partition(sc.means, 4)
+    sc = sc.take(perm)
+    planes = [boxes[k, s, a] for k in range(4) for s in range(2) for a in range(3)
+              if np.isfinite(boxes[k, s, a])]
+    far = np.all([np.abs(sc.means[:, a] - p) > 0.05 for p in set(planes) for a in range(3)],
+                 axis=0)
+    keep = np.nonzero(far)[0]
+    cell = np.searchsorted(off, keep, side="right") - 1
+    sc = sc.take(keep)
+    off = np.concatenate([[0], np.cumsum(np.bincount(cell, minlength=4))])
+    cam = _cam(96, 80)
+    o = O.opts()
+    a = O.render_view(sc, off, cam, o, cells=boxes)
+    b = O.render_view(sc, off, cam, o)
+    assert np.array_equal(a["image"], b["image"])
+    dC = rng.standard_normal((3, 80, 96))
+    ga = O.backward_view(sc, off, cam, dC, None, o, cells=boxes)
+    gb = O.backward_view(sc, off, cam, dC, None, o)
+    # the oracle's threads add per-Gaussian sums in any order: equal up to rounding
+    assert all(np.allclose(x, y, rtol=1e-12, atol=1e-15) for x, y in zip(ga, gb))
