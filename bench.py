@@ -580,6 +580,14 @@ def main():
     roof["peak_source"] = f"{pk_src} ({'HBM copy' if roof['bound'] == 'hbm' else 'SMs x FP32 lanes x max SM clock'})"
     roof["share_of_step"] = cand[dom] / ms
     roof["traffic"] = measured_traffic(dom, counts)
+    # the other kernels whose algorithmic work the step's counters fix, against their roofs
+    others = {}
+    for name in ("raster_fwd", "raster_bwd", "sort", "composite", "composite_bwd", "adam"):
+        t = kmean.get("loss+adam" if name == "adam" else name)
+        if t:
+            r = roofline(name, t, counts, wl, pk)
+            others[name] = {"bound": r["bound"], "achieved": r["achieved"], "unit": r["unit"],
+                            "frac": r["frac"], "ms": t}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -596,7 +604,8 @@ def main():
                                      "backward per view, every subset rendered (no skipping)",
                        "l2": "inputs larger than L2 (2.4 GB parameters, 10 GB projected records)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "plain": plain, "kernel_ms": kmean, "counters": counts},
+                       "plain": plain, "kernel_ms": kmean, "counters": counts,
+                       "kernel_rooflines": others},
             "roofline": roof, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches_per_step * args.steps}
 
