@@ -137,6 +137,23 @@ __device__ __forceinline__ SpecOut bin_spec(const float m[3], const SpecG& G, co
   o.sx = G.sx; o.sy = G.sy; o.sz = G.sz;
   if (!(tz > near_plane)) return o;
   if (!G.ok) return o;
+  {
+    // Early exit, outside the specification (it only leaves out work): the rectangle is
+    // empty when the 2-D mean lies farther outside the image than a bound on the radius.
+    // The dilated covariance's largest eigenvalue is at most |J|_F^2 s_max^2 (the view and
+    // the Gaussian's rotations are orthonormal up to FP32 rounding) + 0.6 (the dilation of
+    // both diagonal entries) + 0.32 (the 0.1 floor under the root), and
+    // |J|_F^2 <= (fx^2 (1 + limx^2) + fy^2 (1 + limy^2)) / tz^2 with the clamped x/z, y/z,
+    // where fx limx = 0.65 W; a 0.5 % and 2-pixel margin covers rounding, the approximate
+    // reciprocal, root and 2-D mean used here, and the ceil.
+    const float smax = fmaxf(fmaxf(G.sx, G.sy), G.sz);
+    const float itz = __fdividef(1.0f, tz);
+    const float k2 = fx * fx + fy * fy + 0.4225f * ((float)W * (float)W + (float)H * (float)H);
+    const float q = 1.005f * k2 * itz * itz * smax * smax + 0.93f;
+    const float rb = 3.0f * q * rsqrtf(q) + 2.0f;
+    const float u0 = fx * tx * itz + cx, v0 = fy * ty * itz + cy;
+    if (u0 + rb < 0.0f || u0 - rb > (float)W || v0 + rb < 0.0f || v0 - rb > (float)H) return o;
+  }
   const float* M = G.M;
   float V[9];
 #pragma unroll
