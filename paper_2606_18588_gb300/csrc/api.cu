@@ -302,7 +302,7 @@ struct Plan {
       CK(cudaMemsetAsync(zr, 0xFF, sizeof(uint32_t) * 2 * (size_t)V * K, s));
       CK(cudaMemsetAsync(removed, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(n_tiles, 1), s));
     }
-    CK(cudaMemsetAsync(big_count, 0, sizeof(unsigned), s));
+    CK(cudaMemsetAsync(big_count, 0, 2 * sizeof(unsigned), s));
     CK(cudaMemsetAsync(chunk_count, 0, sizeof(unsigned), s));
     mark(0, s);
     launch_project(b, s);
@@ -336,7 +336,7 @@ struct Plan {
       bw.order = order_d;
       bw.wave = r;
       mark_wave(2 * r, s);
-      CK(cudaMemsetAsync(big_count, 0, sizeof(unsigned), s));
+      CK(cudaMemsetAsync(big_count, 0, 2 * sizeof(unsigned), s));
       CK(cudaMemsetAsync(chunk_count, 0, sizeof(unsigned), s));
       launch_seg_sort(bw, merge_rounds_bound(max_subset()), s);
       mark_wave(2 * r + 1, s);
@@ -374,7 +374,7 @@ struct Plan {
     if ((r = ctx_alloc_t(ctx, &tile_cnt, nt, s))) return r;
     if ((r = ctx_alloc_t(ctx, &tile_start, nt + 1, s))) return r;
     if ((r = ctx_alloc_t(ctx, &big_list, nt, s))) return r;
-    if ((r = ctx_alloc_t(ctx, &big_count, 1, s))) return r;
+    if ((r = ctx_alloc_t(ctx, &big_count, 2, s))) return r;  // count, most chunks of one
     if ((r = ctx_alloc_t(ctx, &chunk_count, 1, s))) return r;
     if ((r = ctx_alloc(ctx, &scan_temp, scan_u32_temp_bytes(n_tiles), s))) return r;
     if ((r = ctx_alloc_t(ctx, &ranges, nt, s))) return r;

@@ -318,6 +318,7 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_sort_small(const BatchDev 
     if (threadIdx.x == 0) {
       s_base[0] = atomicAdd(b.big_count, 1u);
       s_base[1] = atomicAdd(b.chunk_count, nch);
+      atomicMax(b.big_count + 1, nch);
     }
     __syncthreads();
     const unsigned i = s_base[0];
@@ -352,6 +353,9 @@ __global__ void __launch_bounds__(kSortThreads) k_merge_round(const BatchDev b, 
   __shared__ uint64_t sm[kPadded];
   __shared__ uint32_t s_split[4];
   constexpr int PER = kChunk / kSortThreads;  // outputs per thread
+  // a round is needed only while some segment holds more than 2^r chunks (the launches
+  // cover the bound for the largest subset; most rounds of a wave find nothing to do)
+  if ((1u << r) >= b.big_count[1]) return;
   const unsigned count = *b.chunk_count;
   const uint32_t w = (uint32_t)kChunk << r;
   for (unsigned wi = blockIdx.x; wi < count; wi += gridDim.x) {

@@ -103,7 +103,7 @@ struct BatchDev {
   uint64_t* keys;               // [capacity] depth bits << 32 | Gaussian index, by tile
   uint64_t* keys_alt;           // [capacity] scratch for the long-segment sort
   uint32_t* big_list;           // [n_tiles] tiles whose segment exceeds one sort chunk
-  unsigned* big_count;          // [1]
+  unsigned* big_count;          // [2]: tiles in big_list, most chunks of one of them
   uint2* chunks;                // [n_tiles + capacity/2048 + 1] (big_list index, chunk)
   unsigned* chunk_count;        // [1]
   uint2* ranges;                // [n_tiles] sorted [start, end)

@@ -120,7 +120,7 @@ extern "C" int splx_render_partial_noalloc(const splx_gaussians* g, const splx_c
   uint32_t* tile_cnt = cv.take<uint32_t>((size_t)n_tiles);
   uint32_t* tile_start = cv.take<uint32_t>((size_t)n_tiles + 1);
   uint32_t* big_list = cv.take<uint32_t>((size_t)n_tiles);
-  unsigned* big_count = cv.take<unsigned>(1);
+  unsigned* big_count = cv.take<unsigned>(2);  // count, most chunks of one segment
   uint2* chunks = cv.take<uint2>((size_t)chunk_list_capacity(n_tiles, kNoAllocMaxPairs));
   unsigned* chunk_count = cv.take<unsigned>(1);
   void* scan_temp = cv.take<unsigned char>(scan_u32_temp_bytes(n_tiles));
@@ -171,7 +171,7 @@ extern "C" int splx_render_partial_noalloc(const splx_gaussians* g, const splx_c
   if (e == cudaSuccess) e = cudaMemcpyAsync(view_d, &vd, sizeof(vd), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(img_d, &im, sizeof(im), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * (size_t)n_tiles, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(big_count, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(big_count, 0, 2 * sizeof(unsigned), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(chunk_count, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return SPLX_ERR_CUDA;
 
