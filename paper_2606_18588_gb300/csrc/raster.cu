@@ -1,9 +1,10 @@
 // Local rendering of every (view, subset) tile: forward (Eq. 1-4) and backward.
 //
-// One CTA per image tile of TS x TS pixels; each thread owns PPT vertically adjacent
-// pixels of one column (TS x TS/PPT threads), so the shared-memory loads, the
-// rectangle test and the dx-dependent terms of an entry are shared by PPT pixels, and in
-// the backward the per-entry warp reduction and atomics are amortised over PPT pixels.
+// One CTA per image tile of TS x TS pixels; each thread owns PPT pixels, one in each of
+// PPT blocks of 8 x 4 pixels (TS x TS/PPT threads; layout below), so the shared-memory
+// loads, the rectangle test and the dx-dependent terms of an entry are shared by PPT
+// pixels, and in the backward the per-entry warp reduction and atomics are amortised over
+// PPT pixels.
 // The tile's sorted list is walked in batches of NB entries staged in shared memory.
 // A pixel takes a Gaussian only inside its integer 3-sigma rectangle (so the result does
 // not depend on TS), with alpha = min(alpha_max, o 2^(p2)) >= alpha_min, and stops before
@@ -104,8 +105,8 @@ __device__ __forceinline__ void warp_reduce9(const float (&v)[9], int lane, floa
 }
 
 // Pixels of a thread: slot i of PPT is an 8 x 4 block of the tile, lanes laid out as
-// 8 columns x 4 rows inside it; a warp's PPT blocks tile a 16 x 8 region (8 x 8 for
-// 8 x 8 tiles).  A Gaussian's footprint then meets few blocks, and a block it meets
+// 8 columns x 4 rows inside it; a warp's PPT blocks tile a 16 x 8 region (PPT = 4) or an
+// 8 x 8 region (PPT = 2).  A Gaussian's footprint then meets few blocks, and a block it meets
 // keeps many lanes busy.  (x, y) is the thread's pixel in slot 0; slot i adds
 // (8 (i & 1), 4 (i >> 1)) for PPT = 4 and (0, 4 i) for PPT = 2.
 struct TileInfo {
@@ -184,10 +185,13 @@ __device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
   ti.ty = ty;
   const int w = (int)(threadIdx.x >> 5), l = (int)(threadIdx.x & 31);
   int rx0 = 0, ry0 = 0;
-  if (PPT == 4) {
+  if (PPT == 4) {  // 16 x 8 regions
     constexpr int kRegionsPerRow = TS >= 16 ? TS / 16 : 1;
     rx0 = 16 * (w % kRegionsPerRow);
     ry0 = 8 * (w / kRegionsPerRow);
+  } else {  // 8 x 8 regions
+    rx0 = 8 * (w % (TS / 8));
+    ry0 = 8 * (w / (TS / 8));
   }
   ti.x = tx * TS + rx0 + (l & 7);
   ti.y = ty * TS + ry0 + (l >> 3);
@@ -548,9 +552,17 @@ __global__ void __launch_bounds__(TS * TS / PPT, TS == 16 ? 12 : 1) k_raster_bwd
   }
 }
 
-// Tile side -> pixels per thread: 8x8 tiles use 2 (32 threads), 16x16 and 32x32 use 4.
+// Tile side -> pixels per thread.  Forward: 2 (8 x 8 regions per warp) for 8x8 and 16x16
+// tiles, 4 for 32x32; backward: 2 for 8x8, 4 (16 x 8 regions) for 16x16 and 32x32.  At
+// 16x16 the forward's smaller per-thread state gives 40 resident warps per SM instead of
+// 30 and beats the 4-pixel mapping (15.8 vs 17.1 ms on the 10M step); the backward's
+// per-entry reductions favour 4 pixels per lane (26.3 vs 29.2 ms).
 template <int TS>
-struct Ppt {
+struct PptFwd {
+  static constexpr int value = TS == 32 ? 4 : 2;
+};
+template <int TS>
+struct PptBwd {
   static constexpr int value = TS == 8 ? 2 : 4;
 };
 
@@ -562,7 +574,7 @@ static bool counting(const BatchDev& b, cudaStream_t s) {
 
 template <int TS, bool kCount, bool kPersist>
 static void launch_fwd_k(const BatchDev& b, cudaStream_t s) {
-  constexpr int P = Ppt<TS>::value;
+  constexpr int P = PptFwd<TS>::value;
   const int64_t items = b.order ? b.n_tiles / b.K : b.n_tiles;
   const unsigned grid = kPersist ? (unsigned)std::min<int64_t>(items, (int64_t)b.persist_grid)
                                  : (unsigned)items;
@@ -570,7 +582,7 @@ static void launch_fwd_k(const BatchDev& b, cudaStream_t s) {
 }
 template <int TS, bool kCount, bool kPersist>
 static void launch_bwd_k(const BatchDev& b, cudaStream_t s) {
-  constexpr int P = Ppt<TS>::value;
+  constexpr int P = PptBwd<TS>::value;
   const unsigned grid = kPersist ? (unsigned)std::min<int64_t>(b.n_tiles, (int64_t)b.persist_grid)
                                  : (unsigned)b.n_tiles;
   k_raster_bwd<TS, P, kCount, kPersist><<<grid, TS * TS / P, 0, s>>>(b);
@@ -592,13 +604,13 @@ static void launch_bwd_t(const BatchDev& b, cudaStream_t s) {
 
 template <int TS>
 static int max_ctas_t(bool bwd) {
-  constexpr int P = Ppt<TS>::value;
+  constexpr int PF = PptFwd<TS>::value, PB = PptBwd<TS>::value;
   int n = 0;
   cudaError_t e =
-      bwd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_bwd<TS, P, false, true>,
-                                                          TS * TS / P, 0)
-          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd<TS, P, false, true>,
-                                                          TS * TS / P, 0);
+      bwd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_bwd<TS, PB, false, true>,
+                                                          TS * TS / PB, 0)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_fwd<TS, PF, false, true>,
+                                                          TS * TS / PF, 0);
   return e == cudaSuccess ? n : 0;
 }
 
