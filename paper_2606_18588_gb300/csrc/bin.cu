@@ -10,12 +10,13 @@
 // the filter removes keeps its slot with depth bits 0xFFFFFFFF, so it sorts last, and the
 // tile's range ends before it.
 //
-// Sorting: a segment of up to 2048 keys is sorted in shared memory by one CTA (8 keys per
-// thread by a transposition network, then merge-path merges of runs).  Longer segments are cut into 2048-key chunks, each sorted the same way, and
-// then merged pairwise in rounds (run width 2048, 4096, ...) with merge-path partitioning,
-// one CTA per 2048 outputs, ping-ponging between the key buffer and its twin; segments
-// that end in the twin are copied back.  Every pair is read and written a few times
-// instead of once per 8-bit pass over 50+ key bits.
+// Sorting: a segment of up to 2048 keys is sorted in shared memory by one CTA of 256
+// threads (8 keys per thread by a transposition network, then merge-path merges of runs).
+// Longer segments are cut into 4096-key chunks, each sorted the same way by a CTA of 512
+// threads, and then merged pairwise in rounds (run width 4096, 8192, ...) with merge-path
+// partitioning, one CTA per 4096 outputs, ping-ponging between the key buffer and its
+// twin; segments that end in the twin are copied back.  Every pair is read and written a
+// few times instead of once per 8-bit pass over 50+ key bits.
 #include "common.cuh"
 #include "spec.cuh"
 #include "walk.cuh"
@@ -24,8 +25,10 @@ namespace splx {
 
 namespace {
 
-constexpr int kChunk = 2048;     // keys sorted in shared memory by one CTA
+constexpr int kChunk = 2048;     // a segment up to this long is sorted by one CTA
 constexpr int kSortThreads = 256;
+constexpr int kBig = 4096;       // chunk of a longer segment (sorted, then merged)
+constexpr int kBigThreads = 512;
 
 __device__ __forceinline__ int next_pow2(int n) {
   int p = 1;
@@ -34,6 +37,7 @@ __device__ __forceinline__ int next_pow2(int n) {
 }
 
 constexpr int kItems = kChunk / kSortThreads;  // 8 keys per thread
+static_assert(kBig / kBigThreads == kItems, "both sorts hold 8 keys per thread");
 
 __device__ __forceinline__ void cas(uint64_t& a, uint64_t& b) {
   const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
@@ -45,6 +49,7 @@ __device__ __forceinline__ void cas(uint64_t& a, uint64_t& b) {
 // with stride 8 fall into different banks.
 __device__ __forceinline__ int pad(int i) { return i + (i >> 3); }
 constexpr int kPadded = kChunk + kChunk / 8;
+constexpr int kBigPadded = kBig + kBig / 8;
 
 // Number of elements taken from A = s[pad(a0 + i)] among the first d of merge(A, B) with
 // B = s[pad(b0 + j)], in shared memory.
@@ -59,14 +64,15 @@ __device__ __forceinline__ int merge_path_smem(const uint64_t* s, int a0, int na
   return lo;
 }
 
-// Sorts keys[0, n) (n <= kChunk) in place: each thread sorts kItems keys in registers
-// (odd-even transposition network), then runs of 8, 16, ... are merged pairwise through
-// two shared buffers, every thread producing kItems outputs located by merge path.
-// The array is padded to a power of two P >= 8 with ~0 keys.  sa, sb: kPadded keys each.
+// Sorts keys[0, n) (n <= CH) in place with TH threads: each thread sorts kItems keys in
+// registers (odd-even transposition network), then runs of 8, 16, ... are merged pairwise
+// through two shared buffers, every thread producing kItems outputs located by merge path.
+// The array is padded to a power of two P >= 8 with ~0 keys.  sa, sb: CH + CH/8 keys each.
+template <int TH>
 __device__ __forceinline__ void sort_chunk(uint64_t* keys, int n, uint64_t* sa, uint64_t* sb) {
   int P = next_pow2(n);
   if (P < kItems) P = kItems;
-  for (int i = threadIdx.x; i < P; i += kSortThreads) sa[pad(i)] = i < n ? keys[i] : ~0ull;
+  for (int i = threadIdx.x; i < P; i += TH) sa[pad(i)] = i < n ? keys[i] : ~0ull;
   __syncthreads();
   const int active = P / kItems;  // threads holding keys
   const int t = threadIdx.x;
@@ -115,7 +121,7 @@ __device__ __forceinline__ void sort_chunk(uint64_t* keys, int n, uint64_t* sa, 
     src = dst;
     dst = tmp;
   }
-  for (int i = threadIdx.x; i < n; i += kSortThreads) keys[i] = src[pad(i)];
+  for (int i = threadIdx.x; i < n; i += TH) keys[i] = src[pad(i)];
 }
 
 __device__ __forceinline__ void segment_of(const BatchDev& b, int64_t t, uint32_t& s, uint32_t& e) {
@@ -130,7 +136,7 @@ __device__ __forceinline__ void segment_of(const BatchDev& b, int64_t t, uint32_
 
 // Merge rounds a segment of n keys needs: ceil(log2(number of chunks)).
 __device__ __forceinline__ int rounds_for(uint32_t n) {
-  const uint32_t nch = (n + kChunk - 1) / kChunk;
+  const uint32_t nch = (n + kBig - 1) / kBig;
   int r = 0;
   while ((1u << r) < nch) ++r;
   return r;
@@ -314,7 +320,7 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_sort_small(const BatchDev 
   // saturation-skipping waves sort only what the wave's rasteriser will walk
   if (b.order && b.wave > 0 && item_saturated(b, t)) return;
   if (n > kChunk) {
-    const unsigned nch = (unsigned)((n + kChunk - 1) / kChunk);
+    const unsigned nch = (unsigned)((n + kBig - 1) / kBig);
     if (threadIdx.x == 0) {
       s_base[0] = atomicAdd(b.big_count, 1u);
       s_base[1] = atomicAdd(b.chunk_count, nch);
@@ -326,38 +332,41 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_sort_small(const BatchDev 
     for (unsigned c = threadIdx.x; c < nch; c += kSortThreads) b.chunks[s_base[1] + c] = make_uint2(i, c);
     return;
   }
-  sort_chunk(b.keys + s, n, sk[0], sk[1]);
+  sort_chunk<kSortThreads>(b.keys + s, n, sk[0], sk[1]);
 }
 
-// Sorts every 2048-key chunk of the long segments (grid-stride over the chunk list).
-__global__ void __launch_bounds__(kSortThreads) k_chunk_sort(const BatchDev b) {
-  __shared__ uint64_t sk[2][kPadded];
+// Sorts every 4096-key chunk of the long segments (grid-stride over the chunk list); two
+// shared buffers of kBigPadded keys in dynamic shared memory.
+__global__ void __launch_bounds__(kBigThreads) k_chunk_sort(const BatchDev b) {
+  extern __shared__ uint64_t sk_dyn[];
+  uint64_t* sa = sk_dyn;
+  uint64_t* sb = sk_dyn + kBigPadded;
   const unsigned count = *b.chunk_count;
   for (unsigned w = blockIdx.x; w < count; w += gridDim.x) {
     const uint2 ch = b.chunks[w];
     const int64_t t = b.big_list[ch.x];
     uint32_t s, e;
     segment_of(b, t, s, e);
-    const uint32_t c0 = s + ch.y * kChunk;
+    const uint32_t c0 = s + ch.y * kBig;
     if (c0 >= e) continue;
-    const uint32_t c1 = c0 + kChunk < e ? c0 + kChunk : e;
-    sort_chunk(b.keys + c0, (int)(c1 - c0), sk[0], sk[1]);
+    const uint32_t c1 = c0 + kBig < e ? c0 + kBig : e;
+    sort_chunk<kBigThreads>(b.keys + c0, (int)(c1 - c0), sa, sb);
     __syncthreads();
   }
 }
 
-// Merge round r (run width 2048 << r): each chunk work item produces 2048 outputs of the
+// Merge round r (run width 4096 << r): each chunk work item produces 4096 outputs of the
 // merge of the two runs its output range falls in.  Data of round r lives in keys when r
 // is even and in keys_alt when r is odd.
-__global__ void __launch_bounds__(kSortThreads) k_merge_round(const BatchDev b, int r) {
-  __shared__ uint64_t sm[kPadded];
+__global__ void __launch_bounds__(kBigThreads) k_merge_round(const BatchDev b, int r) {
+  __shared__ uint64_t sm[kBigPadded];
   __shared__ uint32_t s_split[4];
-  constexpr int PER = kChunk / kSortThreads;  // outputs per thread
+  constexpr int PER = kBig / kBigThreads;  // outputs per thread
   // a round is needed only while some segment holds more than 2^r chunks (the launches
   // cover the bound for the largest subset; most rounds of a wave find nothing to do)
   if ((1u << r) >= b.big_count[1]) return;
   const unsigned count = *b.chunk_count;
-  const uint32_t w = (uint32_t)kChunk << r;
+  const uint32_t w = (uint32_t)kBig << r;
   for (unsigned wi = blockIdx.x; wi < count; wi += gridDim.x) {
     const uint2 ch = b.chunks[wi];
     const int64_t t = b.big_list[ch.x];
@@ -367,9 +376,9 @@ __global__ void __launch_bounds__(kSortThreads) k_merge_round(const BatchDev b, 
     if (n <= w) continue;  // this segment needs no merge at this width
     const uint64_t* src = ((r & 1) ? b.keys_alt : b.keys) + s;
     uint64_t* dst = ((r & 1) ? b.keys : b.keys_alt) + s;
-    const uint32_t o0 = ch.y * kChunk;
+    const uint32_t o0 = ch.y * kBig;
     if (o0 >= n) continue;
-    const uint32_t o1 = o0 + kChunk < n ? o0 + kChunk : n;
+    const uint32_t o1 = o0 + kBig < n ? o0 + kBig : n;
     const uint32_t p0 = (o0 / (2 * w)) * (2 * w);
     const uint32_t na = (p0 + w < n ? p0 + w : n) - p0;
     const uint32_t nb = (p0 + 2 * w < n ? p0 + 2 * w : n) - (p0 + na);
@@ -387,8 +396,8 @@ __global__ void __launch_bounds__(kSortThreads) k_merge_round(const BatchDev b, 
     __syncthreads();
     const uint32_t a0 = s_split[0], a1 = s_split[1], b0 = s_split[2], b1 = s_split[3];
     const int la = (int)(a1 - a0), lb = (int)(b1 - b0);
-    for (int i = threadIdx.x; i < la; i += kSortThreads) sm[pad(i)] = A[a0 + i];
-    for (int i = threadIdx.x; i < lb; i += kSortThreads) sm[pad(la + i)] = B[b0 + i];
+    for (int i = threadIdx.x; i < la; i += kBigThreads) sm[pad(i)] = A[a0 + i];
+    for (int i = threadIdx.x; i < lb; i += kBigThreads) sm[pad(la + i)] = B[b0 + i];
     __syncthreads();
     // each thread merges PER consecutive outputs of sm[0,la) and sm[la,la+lb)
     const int d = threadIdx.x * PER;
@@ -414,7 +423,7 @@ __global__ void __launch_bounds__(kSortThreads) k_merge_round(const BatchDev b, 
 }
 
 // Copies back the segments whose last merge round wrote keys_alt (odd round count).
-__global__ void __launch_bounds__(kSortThreads) k_merge_fixup(const BatchDev b) {
+__global__ void __launch_bounds__(kBigThreads) k_merge_fixup(const BatchDev b) {
   const unsigned count = *b.chunk_count;
   for (unsigned wi = blockIdx.x; wi < count; wi += gridDim.x) {
     const uint2 ch = b.chunks[wi];
@@ -422,9 +431,9 @@ __global__ void __launch_bounds__(kSortThreads) k_merge_fixup(const BatchDev b) 
     uint32_t s, e;
     segment_of(b, t, s, e);
     if ((rounds_for(e - s) & 1) == 0) continue;
-    const uint32_t c0 = s + ch.y * kChunk;
-    const uint32_t c1 = c0 + kChunk < e ? c0 + kChunk : e;
-    for (uint32_t i = c0 + threadIdx.x; i < c1; i += kSortThreads) b.keys[i] = b.keys_alt[i];
+    const uint32_t c0 = s + ch.y * kBig;
+    const uint32_t c1 = c0 + kBig < e ? c0 + kBig : e;
+    for (uint32_t i = c0 + threadIdx.x; i < c1; i += kBigThreads) b.keys[i] = b.keys_alt[i];
   }
 }
 
@@ -432,17 +441,23 @@ void launch_seg_sort(const BatchDev& b, int max_rounds, cudaStream_t s) {
   if (b.n_tiles == 0) return;
   const int64_t items = b.order ? b.n_tiles / b.K : b.n_tiles;
   k_seg_sort_small<<<(unsigned)items, kSortThreads, 0, s>>>(b);
-  const unsigned grid = 152 * 8;
-  k_chunk_sort<<<grid, kSortThreads, 0, s>>>(b);
-  for (int r = 0; r < max_rounds; ++r) k_merge_round<<<grid, kSortThreads, 0, s>>>(b, r);
-  k_merge_fixup<<<grid, kSortThreads, 0, s>>>(b);
+  const unsigned grid = 152 * 4;
+  // 72 KB of dynamic shared memory: opted in once per process (a refused opt-in shows as
+  // the launch's error, which the callers check)
+  constexpr int kChunkSmem = 2 * kBigPadded * (int)sizeof(uint64_t);
+  static const cudaError_t smem_opt_in =
+      cudaFuncSetAttribute(k_chunk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kChunkSmem);
+  (void)smem_opt_in;
+  k_chunk_sort<<<grid, kBigThreads, kChunkSmem, s>>>(b);
+  for (int r = 0; r < max_rounds; ++r) k_merge_round<<<grid, kBigThreads, 0, s>>>(b, r);
+  k_merge_fixup<<<grid, kBigThreads, 0, s>>>(b);
   count_launch(3 + max_rounds);
 }
 
 // Merge rounds that cover any segment of a batch whose largest subset has max_n Gaussians
 // (a tile's segment holds at most one key per Gaussian of its subset).
 int merge_rounds_bound(int64_t max_n) {
-  const int64_t nch = (max_n + kChunk - 1) / kChunk;
+  const int64_t nch = (max_n + kBig - 1) / kBig;
   int r = 0;
   while ((int64_t(1) << r) < nch) ++r;
   return r;
