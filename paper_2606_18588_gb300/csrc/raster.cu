@@ -205,6 +205,9 @@ __device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
 // kCount variants (eager runs only) also count the work for the roofline: thread-entries
 // examined, (pixel, entry) alpha evaluations and blends / contributions.
 constexpr int kNB = 256;  // list entries staged in shared memory per batch
+// the backward stages fewer at a time where its threads allow (one entry per thread at least)
+template <int TS, int PPT>
+constexpr int kNBBwd = TS * TS / PPT > 128 ? TS * TS / PPT : 128;
 constexpr int kDirectLanes = 3;  // backward: lanes that add their gradients directly
 
 template <int TS, int PPT, bool kCount>
@@ -359,7 +362,7 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
                                          float4* sB, float4* sC, uint32_t* sG, int& s_maxlast,
                                          float4* sQ) {
   constexpr int NTH = TS * TS / PPT;
-  constexpr int NB = kNB;
+  constexpr int NB = kNBBwd<TS, PPT>;
   const TileInfo ti = decode_tile<TS, PPT>(b, id);
   if (!in_omega(b, ti.v, ti.k, ti.tx, ti.ty)) return;  // nothing written there, nothing to do
   const uint2 rg = b.ranges[id];
@@ -532,9 +535,9 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) 
 }
 
 template <int TS, int PPT, bool kCount, bool kPersist>
-__global__ void __launch_bounds__(TS * TS / PPT, TS == 16 ? 12 : 1) k_raster_bwd(const BatchDev b) {
-  __shared__ float4 sA[kNB], sB[kNB], sC[kNB];
-  __shared__ uint32_t sG[kNB];
+__global__ void __launch_bounds__(TS * TS / PPT, TS == 16 ? 16 : 1) k_raster_bwd(const BatchDev b) {
+  __shared__ float4 sA[kNBBwd<TS, PPT>], sB[kNBBwd<TS, PPT>], sC[kNBBwd<TS, PPT>];
+  __shared__ uint32_t sG[kNBBwd<TS, PPT>];
   __shared__ float4 sQ[TS * TS];  // composite adjoint per pixel slot
   __shared__ int s_maxlast;
   if constexpr (!kPersist) {
