@@ -169,7 +169,7 @@ constexpr int kFillThreads = 256;
 constexpr int kFillFields = 18;  // per lane: tile test (8), rect x, rect y, tile base, width,
                                  // 1/width, tiles per row, pass bits, key (2), tiles
 
-__global__ void __launch_bounds__(kFillThreads, 6) k_fill(const BatchDev b) {
+__global__ void __launch_bounds__(kFillThreads, 8) k_fill(const BatchDev b) {
   __shared__ float s_walk[kFillThreads / 32][kFillFields][32];
   __shared__ int s_own[kFillThreads / 32][32];
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -99,6 +99,34 @@ def test_binning_bit_exact_on_long_segments(ctx):
     st.close()
 
 
+@pytest.mark.parametrize("n", [2049, 3000, 4096, 4097, 8192, 8193, 12289])
+def test_segment_sort_at_chunk_boundaries(ctx, n):
+    """One tile's list of n keys around the lengths where the sort switches from one CTA
+    to chunks (2048), fills a chunk (4096) and needs one more merge round (8192, 12288),
+    with many equal depths so the index tie-break decides the order."""
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import to_device, subset_struct
+    rng = np.random.default_rng(n)
+    m = np.zeros((n, 3), np.float32)
+    m[:, :2] = -0.433 + rng.uniform(-0.004, 0.004, (n, 2))  # inside tile (1, 1)
+    m[:, 2] = rng.choice(np.float32([-0.5, -0.25, 0.0, 0.25]), n)
+    sc = I.Scene(m, np.full((n, 3), -7.0, np.float32), np.tile(np.float32([1, 0, 0, 0]), (n, 1)),
+                 np.zeros(n, np.float32), np.zeros((n, 1, 3), np.float32), 0)
+    cam = I.pinhole(64, 64, 60.0, (0.0, 0.0, -3.0), (0.0, 0.0, 0.0))
+    p = S.new_partial(64, 64)
+    st = S.render_partial(ctx, subset_struct(to_device(sc), 0, n, 0), cam, S.opts(tile=16), p)
+    ranges, keys, _ = st.export()
+    vals = (keys & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    start, lst = O.tile_lists(sc, cam, 16)
+    assert np.diff(start).max() == n
+    for t in range(start.size - 1):
+        a, b = int(start[t]), int(start[t + 1])
+        ga, gb = int(ranges[t, 0]), int(ranges[t, 1])
+        assert gb - ga == b - a
+        assert np.array_equal(vals[ga:gb], lst[a:b].astype(np.uint32)), t
+    st.close()
+
+
 def _compare_pixels(gpu, orc, amb, tol=1e-4):
     ok = amb == 0
     assert ok.mean() > 0.99
