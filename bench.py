@@ -29,11 +29,12 @@ UNIT = "Mpixel/s"
 # Algorithmic FP32 operations of the rasterisers per counted (pixel, list entry) event:
 # an alpha evaluation (dx, dy, the conic's quadratic form, exp2, times opacity, clamp,
 # threshold), a forward blend (1 - alpha, T update, stop test, alpha T, rgb and depth
-# accumulation) and a backward contribution (T_i recovery, colour, opacity and conic /
-# mean gradients of Eq. 3-4, suffix sums).
+# accumulation) and a backward contribution (T_i recovery 4, colour gradient 3, the dot
+# product of dL/dC with the colour 3, dL/dalpha 2, opacity 1, dL/dpower 1, its five
+# moments in dx, dy 7, the suffix term 1).
 OPS_PER_ALPHA = 10
 OPS_PER_BLEND = 8
-OPS_PER_CONTRIB = 36
+OPS_PER_CONTRIB = 22
 FP32_LANES_PER_SM = 128
 SMS = 152
 

@@ -17,7 +17,11 @@
 //   dC^m/dc_i = alpha_i T_i,  dC^m/dalpha_i = c_i T_i - B_i / (1 - alpha_i),
 //   dT^m/dalpha_i = -T^m / (1 - alpha_i),  B_i = sum_{j>i} c_j alpha_j T_j.
 // Per-Gaussian sums over the tile's pixels are reduced with warp shuffles and added to
-// the per-(view, Gaussian) 2-D gradient with float4 atomics.
+// the per-(view, Gaussian) 2-D gradient with float4 atomics.  With gp = dL/dpower at a
+// pixel, power = -(A dx^2 + 2 B dx dy + C dy^2) / 2 and (dx, dy) = pixel centre - (u, v),
+// the record holds the conic-free moments sum gp dx, gp dy, gp dx^2, gp dx dy, gp dy^2;
+// dL/du = A sum gp dx + B sum gp dy, dL/dA = -sum gp dx^2 / 2 and the rest follow linearly
+// in the projection adjoint, which knows the conic.
 #include "common.cuh"
 
 namespace splx {
@@ -371,7 +375,9 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
   // composite adjoint of the thread's pixels: (dL/dC^m rgb, -T^m dL/dT^m) per slot, in
   // shared memory (read only where a pixel takes an entry), which keeps registers down
   float4* gq = sQ + threadIdx.x;  // slot i at gq[i * NTH]
-  float T[PPT], B0[PPT], B1[PPT], B2[PPT];
+  // W = -T^m dL/dT^m - sum_ch dL/dC^m_ch B_ch: the colour suffix sums B enter the alpha
+  // adjoint only through this dot product, so one scalar per pixel carries them
+  float T[PPT], W[PPT];
   int mylast[PPT];
   int tlast = -1;  // largest last over this thread's pixels
 #pragma unroll
@@ -379,7 +385,6 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
     float4 gct = make_float4(0.f, 0.f, 0.f, 0.f);
     T[i] = 1.0f;
     mylast[i] = -1;
-    B0[i] = B1[i] = B2[i] = 0.0f;
     const int px = ti.x + 8 * slot_col<PPT>(i), py = ti.y + 4 * slot_row<PPT>(i);
     if (px < ti.W && py < ti.H) {
       const int64_t p = (int64_t)py * ti.W + px;
@@ -389,7 +394,8 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
       if (gct.x == 0.0f && gct.y == 0.0f && gct.z == 0.0f && gct.w == 0.0f)
         mylast[i] = -1;
     }
-    gq[i * NTH] = make_float4(gct.x, gct.y, gct.z, -T[i] * gct.w);
+    W[i] = -T[i] * gct.w;
+    gq[i * NTH] = make_float4(gct.x, gct.y, gct.z, 0.0f);
     tlast = mylast[i] > tlast ? mylast[i] : tlast;
   }
   if (threadIdx.x == 0) s_maxlast = -1;
@@ -428,7 +434,10 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
     if (kCount && tlast >= lo) n_evalb += (unsigned)((tlast < top ? tlast : top) - lo + 1);
     for (int jj = 0; jj < cnt; ++jj) {
       const int j = top - jj;
-      float gu = 0.f, gv = 0.f, gA = 0.f, gB = 0.f, gC = 0.f, go = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
+      // the entry's sums over the warp's pixels: gp dx, gp dy, gp dx^2, gp dx dy, gp dy^2
+      // (gp = dL/dpower), dL/do and dL/dcolour; the projection adjoint applies the conic
+      float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f, go = 0.f, gr = 0.f, gg = 0.f,
+            gb = 0.f;
       bool act = false;
       if (j <= tlast) {
         const float4 Bv = sB[jj];
@@ -442,8 +451,6 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
         if ((cA || cB) && (rA || rB)) {
           const float4 Av = sA[jj];
           const ColTerms ct0 = col_terms(Av, pcx0), ct1 = col_terms(Av, pcx1);
-          // conic (A, B, C) recovered from the scaled record: A = -2 ln2 qa, B = -ln2 qb, C = -2 ln2 qc
-          const float A_ = -2.0f * kLn2 * Av.z, Bc = -kLn2 * Av.w, C_ = -2.0f * kLn2 * Bv.x;
 #pragma unroll
           for (int i = 0; i < PPT; ++i) {
             const int ci = slot_col<PPT>(i), ri = slot_row<PPT>(i);
@@ -464,20 +471,19 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
             gr = fmaf(q.x, aT, gr);
             gg = fmaf(q.y, aT, gg);
             gb = fmaf(q.z, aT, gb);
-            const float ga = q.x * (Cv.x * Ti - B0[i] * rinv) + q.y * (Cv.y * Ti - B1[i] * rinv) +
-                             q.z * (Cv.z * Ti - B2[i] * rinv) + q.w * rinv;
+            const float qc = fmaf(q.z, Cv.z, fmaf(q.y, Cv.y, q.x * Cv.x));  // dL/dC^m . c_i
+            const float ga = fmaf(Ti, qc, W[i] * rinv);                      // dL/dalpha_i
             if (!cl) {
               go = fmaf(ga, ex, go);
               const float gp = ga * alpha;  // dL/dpower
-              gu = fmaf(A_ * ct.dx + Bc * dy, gp, gu);
-              gv = fmaf(C_ * dy + Bc * ct.dx, gp, gv);
-              gA = fmaf(-0.5f * ct.dx * ct.dx, gp, gA);
-              gB = fmaf(-ct.dx * dy, gp, gB);
-              gC = fmaf(-0.5f * dy * dy, gp, gC);
+              const float px = gp * ct.dx, py = gp * dy;
+              sx += px;
+              sy += py;
+              sxx = fmaf(px, ct.dx, sxx);
+              sxy = fmaf(px, dy, sxy);
+              syy = fmaf(py, dy, syy);
             }
-            B0[i] = fmaf(Cv.x, aT, B0[i]);
-            B1[i] = fmaf(Cv.y, aT, B1[i]);
-            B2[i] = fmaf(Cv.z, aT, B2[i]);
+            W[i] = fmaf(-qc, aT, W[i]);
             T[i] = Ti;
           }
         }
@@ -489,16 +495,16 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
           // operations than the reduction's nine, and skip its shuffles
           if (act) {
             float4* dst = g2 + (int64_t)sG[jj] * 3;
-            atomicAdd(dst, make_float4(gu, gv, gA, gB));
-            atomicAdd(dst + 1, make_float4(gC, go, gr, gg));
+            atomicAdd(dst, make_float4(sx, sy, sxx, sxy));
+            atomicAdd(dst + 1, make_float4(syy, go, gr, gg));
             atomicAdd(&dst[2].x, gb);
           }
         } else {
-          float v[9] = {gu, gv, gA, gB, gC, go, gr, gg, gb};
+          float v[9] = {sx, sy, sxx, sxy, syy, go, gr, gg, gb};
           float mine, v8;
           warp_reduce9(v, lane, mine, v8);
           // lanes 0, 4, ..., 28 hold the sums of values 0..7, lane 0 also value 8; the
-          // 2-D gradient record is 12 floats (gu, gv, gA, gB, gC, go, gr, gg, gb, -, -, -)
+          // 2-D gradient record is 12 floats (sx, sy, sxx, sxy, syy, go, gr, gg, gb, -, -, -)
           float* dst = reinterpret_cast<float*>(g2 + (int64_t)sG[jj] * 3);
           if ((lane & 3) == 0) atomicAdd(dst + (lane >> 2), mine);
           if (lane == 0) atomicAdd(dst + 8, v8);
