@@ -109,10 +109,10 @@ __device__ __forceinline__ void warp_reduce9(const float (&v)[9], int lane, floa
 }
 
 // Pixels of a thread: slot i of PPT is an 8 x 4 block of the tile, lanes laid out as
-// 8 columns x 4 rows inside it; a warp's PPT blocks tile a 16 x 8 region (PPT = 4) or an
-// 8 x 8 region (PPT = 2).  A Gaussian's footprint then meets few blocks, and a block it meets
-// keeps many lanes busy.  (x, y) is the thread's pixel in slot 0; slot i adds
-// (8 (i & 1), 4 (i >> 1)) for PPT = 4 and (0, 4 i) for PPT = 2.
+// 8 columns x 4 rows inside it; a warp's PPT blocks tile a 16 x 16 region (PPT = 8), a
+// 16 x 8 region (PPT = 4) or an 8 x 8 region (PPT = 2).  A Gaussian's footprint then meets
+// few blocks, and a block it meets keeps many lanes busy.  (x, y) is the thread's pixel in
+// slot 0; slot i adds (8 (i & 1), 4 (i >> 1)) for PPT = 4 and 8, and (0, 4 i) for PPT = 2.
 struct TileInfo {
   int v, k, x, y, W, H, tx, ty;
 };
@@ -171,9 +171,14 @@ __device__ __forceinline__ unsigned rect_slots(int x, int y, int x0, int x1, int
 }
 
 template <int PPT>
-__device__ __forceinline__ int slot_col(int i) { return PPT == 4 ? (i & 1) : 0; }
+__device__ __forceinline__ int slot_col(int i) { return PPT >= 4 ? (i & 1) : 0; }
 template <int PPT>
-__device__ __forceinline__ int slot_row(int i) { return PPT == 4 ? (i >> 1) : i; }
+__device__ __forceinline__ int slot_row(int i) { return PPT >= 4 ? (i >> 1) : i; }
+// block columns (x offsets 0, 8) and rows (y offsets 0, 4, ...) of a thread's slots
+template <int PPT>
+constexpr int kSlotCols = PPT >= 4 ? 2 : 1;
+template <int PPT>
+constexpr int kSlotRows = PPT / kSlotCols<PPT>;
 
 template <int TS, int PPT>
 __device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
@@ -189,7 +194,10 @@ __device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
   ti.ty = ty;
   const int w = (int)(threadIdx.x >> 5), l = (int)(threadIdx.x & 31);
   int rx0 = 0, ry0 = 0;
-  if (PPT == 4) {  // 16 x 8 regions
+  if (PPT == 8) {  // 16 x 16 regions
+    rx0 = 16 * (w % (TS / 16));
+    ry0 = 16 * (w / (TS / 16));
+  } else if (PPT == 4) {  // 16 x 8 regions
     constexpr int kRegionsPerRow = TS >= 16 ? TS / 16 : 1;
     rx0 = 16 * (w % kRegionsPerRow);
     ry0 = 8 * (w / kRegionsPerRow);
@@ -209,9 +217,13 @@ __device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
 // kCount variants (eager runs only) also count the work for the roofline: thread-entries
 // examined, (pixel, entry) alpha evaluations and blends / contributions.
 constexpr int kNB = 256;  // list entries staged in shared memory per batch
-// the backward stages fewer at a time where its threads allow (one entry per thread at least)
+// the backward stages fewer at a time where its threads allow (one entry per thread at
+// least); one-warp CTAs stage 64, which keeps their shared memory at 7.4 KB
 template <int TS, int PPT>
-constexpr int kNBBwd = TS * TS / PPT > 128 ? TS * TS / PPT : 128;
+constexpr int kNBBwd = TS * TS / PPT > 128 ? TS * TS / PPT : (TS * TS / PPT == 32 ? 64 : 128);
+// resident CTAs the backward's register limit is set for
+template <int TS, int PPT>
+constexpr int kMinBlocksBwd = TS == 16 ? (PPT == 8 ? 28 : 16) : 1;
 constexpr int kDirectLanes = 3;  // backward: lanes that add their gradients directly
 
 template <int TS, int PPT, bool kCount>
@@ -445,16 +457,24 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
         const uint32_t rx = __float_as_uint(Bv.w), ry = __float_as_uint(Cv.w);
         const int x0 = (int)(rx & 0xFFFFu), x1 = (int)(rx >> 16);
         const int y0 = (int)(ry & 0xFFFFu), y1 = (int)(ry >> 16);
-        const bool cA = ti.x >= x0 && ti.x <= x1;
-        const bool cB = PPT == 4 && ti.x + 8 >= x0 && ti.x + 8 <= x1;
-        const bool rA = ti.y >= y0 && ti.y <= y1, rB = ti.y + 4 >= y0 && ti.y + 4 <= y1;
-        if ((cA || cB) && (rA || rB)) {
+        bool cin[kSlotCols<PPT>], rin[kSlotRows<PPT>], anyc = false, anyr = false;
+#pragma unroll
+        for (int c = 0; c < kSlotCols<PPT>; ++c) {
+          cin[c] = ti.x + 8 * c >= x0 && ti.x + 8 * c <= x1;
+          anyc |= cin[c];
+        }
+#pragma unroll
+        for (int r = 0; r < kSlotRows<PPT>; ++r) {
+          rin[r] = ti.y + 4 * r >= y0 && ti.y + 4 * r <= y1;
+          anyr |= rin[r];
+        }
+        if (anyc && anyr) {
           const float4 Av = sA[jj];
           const ColTerms ct0 = col_terms(Av, pcx0), ct1 = col_terms(Av, pcx1);
 #pragma unroll
           for (int i = 0; i < PPT; ++i) {
             const int ci = slot_col<PPT>(i), ri = slot_row<PPT>(i);
-            if (j > mylast[i] || !(ci ? cB : cA) || !(ri ? rB : rA)) continue;
+            if (j > mylast[i] || !cin[ci] || !rin[ri]) continue;
             if (kCount) ++n_pixb;
             const ColTerms& ct = ci ? ct1 : ct0;
             float alpha, ex, dy;
@@ -541,7 +561,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) 
 }
 
 template <int TS, int PPT, bool kCount, bool kPersist>
-__global__ void __launch_bounds__(TS * TS / PPT, TS == 16 ? 16 : 1) k_raster_bwd(const BatchDev b) {
+__global__ void __launch_bounds__(TS * TS / PPT, (kMinBlocksBwd<TS, PPT>)) k_raster_bwd(const BatchDev b) {
   __shared__ float4 sA[kNBBwd<TS, PPT>], sB[kNBBwd<TS, PPT>], sC[kNBBwd<TS, PPT>];
   __shared__ uint32_t sG[kNBBwd<TS, PPT>];
   __shared__ float4 sQ[TS * TS];  // composite adjoint per pixel slot
@@ -562,17 +582,19 @@ __global__ void __launch_bounds__(TS * TS / PPT, TS == 16 ? 16 : 1) k_raster_bwd
 }
 
 // Tile side -> pixels per thread.  Forward: 2 (8 x 8 regions per warp) for 8x8 and 16x16
-// tiles, 4 for 32x32; backward: 2 for 8x8, 4 (16 x 8 regions) for 16x16 and 32x32.  At
-// 16x16 the forward's smaller per-thread state gives 40 resident warps per SM instead of
-// 30 and beats the 4-pixel mapping (15.8 vs 17.1 ms on the 10M step); the backward's
-// per-entry reductions favour 4 pixels per lane (26.3 vs 29.2 ms).
+// tiles, 4 for 32x32; backward: 2 for 8x8, 8 (one warp per 16x16 tile) for 16x16, 4 (16 x 8
+// regions) for 32x32.  At 16x16 the forward's smaller per-thread state gives 40 resident
+// warps per SM instead of 30 and beats the 4-pixel mapping (15.8 vs 17.1 ms on the 10M
+// step); the backward's per-entry work (record loads, rectangle tests, the warp reduction
+// and its atomics) favours more pixels per lane: one warp per tile does it once per entry
+// instead of twice (21.0 ms at 8 pixels and 27 CTAs per SM, 22.0 at 4, 29.2 at 2).
 template <int TS>
 struct PptFwd {
   static constexpr int value = TS == 32 ? 4 : 2;
 };
 template <int TS>
 struct PptBwd {
-  static constexpr int value = TS == 8 ? 2 : 4;
+  static constexpr int value = TS == 8 ? 2 : (TS == 16 ? 8 : 4);
 };
 
 // Work is counted only by eager runs with a counter buffer: a captured graph launches the
