@@ -230,7 +230,9 @@ def render_view(scene, offsets, cam, o: Opts | None = None, tile_mask=None, sepa
                 order=None, cells=None):
     """K contiguous subsets rendered and composited: dict(image, T, Cp, Tp, Dp, amb, sep,
     skip).  With `order` (front-to-back subset order) the partials are rendered in that
-    order with saturation skipping; skip[m, t] marks the tiles subset m left empty.  With
+    order with saturation skipping (Sec. 4.2): a subset leaves empty the pixels whose prefix
+    transmittance is below eps_comp, and skip[m, t] marks the tiles it left empty as a
+    whole (no open pixel).  With
     `cells` (the subsets' k-d boxes [K, 2, 3]) cross-boundary Gaussians are filtered per
     ray as in Sec. 8.1."""
     o = o or opts()

@@ -650,21 +650,24 @@ int composite_order(int K, const double* Tm, const double* Dm, const orc_opts& o
 int render_subset(const orc_params* p, const orc_camera* cam, const orc_opts* o,
                   const uint8_t* tile_mask, double* C, double* T, double* D, int32_t* last,
                   int32_t* ncontrib, uint8_t* amb, int64_t* stats, const CrossFilter* f, int m,
-                  int64_t goff);
+                  int64_t goff, const uint8_t* pix_open = nullptr);
 
 namespace {
 
-// Saturation skipping (Sec. 4.2, with the composite's threshold eps_comp): the K partials
-// of a view are rendered in the given front-to-back subset order, and the subset at rank
-// r leaves tile t empty (C = 0, T = 1, D = 0) when the product of the transmittances of
-// the subsets ranked before it is below eps_comp at every pixel of the tile.  Renders
-// into C, T, D (planar per subset) and fills skip[m * nt + t].  With order == nullptr
-// every subset is rendered on every tile of tile_mask.
+// Saturation skipping (Sec. 4.2 ②, with the composite's threshold eps_comp): the K
+// partials of a view are rendered in the given front-to-back subset order, and the subset
+// at rank r leaves a pixel empty (C = 0, T = 1, D = 0, no contributor) where the product
+// of the transmittances of the subsets ranked before it is below eps_comp: the saturated
+// pixels leave the subset's pixel set.  A tile all of whose pixels are saturated is not
+// rendered at all (skip[m * nt + t] = 1).  A pixel whose prefix lies within the relative
+// margin amb_T of eps_comp is flagged AMB_SAT.  Renders into C, T, D (planar per subset)
+// and, if pskip is given, sets pskip[m * HW + pixel] for the pixels left empty.  With
+// order == nullptr every subset is rendered on every pixel of tile_mask's tiles.
 void render_partials(const orc_params& p, const int64_t* offsets, int K, const orc_camera& cam,
                      const orc_opts& o, const uint8_t* tile_mask, const int32_t* order,
                      std::vector<double>& C, std::vector<double>& T, std::vector<double>& D,
                      std::vector<uint8_t>& skip, uint8_t* amb, int64_t* stats,
-                     const CrossFilter* f) {
+                     const CrossFilter* f, std::vector<uint8_t>* pskip = nullptr) {
   const int W = cam.width, H = cam.height, B = o.tile;
   const int64_t HW = (int64_t)W * H;
   const int tw = (W + B - 1) / B, th = (H + B - 1) / B, nt = tw * th;
@@ -672,10 +675,17 @@ void render_partials(const orc_params& p, const int64_t* offsets, int K, const o
   T.assign((size_t)K * HW, 1.0);
   D.assign((size_t)K * HW, 0.0);
   skip.assign((size_t)K * nt, 0);
+  if (pskip) pskip->assign((size_t)K * HW, 0);
   std::vector<double> prefix(HW, 1.0);
-  std::vector<uint8_t> mask(nt), a1(HW, 0);
+  std::vector<uint8_t> mask(nt), a1(HW, 0), open(HW, 1);
   for (int r = 0; r < K; ++r) {
     const int m = order ? order[r] : r;
+    if (order && r > 0)
+      for (int64_t i = 0; i < HW; ++i) {
+        open[i] = (uint8_t)(prefix[i] >= o.eps_comp);
+        if (amb && std::fabs(prefix[i] - o.eps_comp) <= o.amb_T * o.eps_comp) amb[i] |= AMB_SAT;
+        if (pskip && !open[i]) (*pskip)[(size_t)m * HW + i] = 1;
+      }
     for (int t = 0; t < nt; ++t) {
       mask[t] = (uint8_t)(!tile_mask || tile_mask[t]);
       if (order && r > 0 && mask[t]) {
@@ -694,7 +704,7 @@ void render_partials(const orc_params& p, const int64_t* offsets, int K, const o
     std::fill(a1.begin(), a1.end(), 0);
     render_subset(&q, &cam, &o, mask.data(), C.data() + (size_t)m * 3 * HW,
                   T.data() + (size_t)m * HW, D.data() + (size_t)m * HW, nullptr, nullptr,
-                  a1.data(), stats, f, m, offsets[m]);
+                  a1.data(), stats, f, m, offsets[m], order && r > 0 ? open.data() : nullptr);
     if (amb)
       for (int64_t i = 0; i < HW; ++i) amb[i] |= a1[i];
     if (order)
@@ -780,10 +790,12 @@ int orc_render(const orc_params* p, const orc_camera* cam, const orc_opts* o,
 }
 }  // extern "C"
 
+// pix_open (nullable, [H][W]): a pixel with a zero entry is left empty (C = 0, T = 1,
+// D = 0, no contributor) without being evaluated.
 int render_subset(const orc_params* p, const orc_camera* cam, const orc_opts* o,
                   const uint8_t* tile_mask, double* C, double* T, double* D, int32_t* last,
                   int32_t* ncontrib, uint8_t* amb, int64_t* stats, const CrossFilter* f, int m,
-                  int64_t goff) {
+                  int64_t goff, const uint8_t* pix_open) {
   const int W = cam->width, H = cam->height, B = o->tile;
   Subset s = prepare(*p, *cam, B, (float)o->alpha_min, f, m, goff);
   const int nt = s.tiles.tw * s.tiles.th;
@@ -797,10 +809,12 @@ int render_subset(const orc_params* p, const orc_camera* cam, const orc_opts* o,
     for (int py = ty * B; py < std::min(H, (ty + 1) * B); ++py)
       for (int px = tx * B; px < std::min(W, (tx + 1) * B); ++px) {
         const int64_t pi = (int64_t)py * W + px;
-        double c3[3], tt, dd;
-        int32_t lg, nc;
-        const int a = blend_pixel(px, py, lst, cnt, s.bins, s.pr, *o, c3, tt, dd, lg, nc,
-                                  evaluated, nullptr);
+        double c3[3] = {0.0, 0.0, 0.0}, tt = 1.0, dd = 0.0;
+        int32_t lg = -1, nc = 0;
+        int a = 0;
+        if (!pix_open || pix_open[pi])
+          a = blend_pixel(px, py, lst, cnt, s.bins, s.pr, *o, c3, tt, dd, lg, nc, evaluated,
+                          nullptr);
         for (int ch = 0; ch < 3; ++ch) C[(int64_t)ch * H * W + pi] = c3[ch];
         T[pi] = tt; D[pi] = dd;
         if (last) last[pi] = lg;
@@ -930,8 +944,9 @@ int orc_backward_view(const orc_params* p, const int64_t* offsets, int32_t K,
     subs[m] = prepare(q, *cam, B, (float)o->alpha_min, fp, m, offsets[m]);
   }
   std::vector<double> C, T, D;
-  std::vector<uint8_t> skip;
-  render_partials(*p, offsets, K, *cam, *o, tile_mask, order, C, T, D, skip, nullptr, nullptr, fp);
+  std::vector<uint8_t> skip, pskip;
+  render_partials(*p, offsets, K, *cam, *o, tile_mask, order, C, T, D, skip, nullptr, nullptr, fp,
+                  &pskip);
   // per-Gaussian 2-D gradients: u, v, A, B, C, o, r, g, b (threads add atomically)
   std::vector<double> g2((size_t)p->n * 9, 0.0);
   const int tw = (W + B - 1) / B, th = (H + B - 1) / B;
@@ -973,7 +988,8 @@ int orc_backward_view(const orc_params* p, const int64_t* offsets, int32_t K,
           // local-render adjoint per subset, back to front
           for (int j = 0; j < L; ++j) {
             const int m = ord[j];
-            if (skip[(size_t)m * tw * th + t]) continue;  // not rendered: no contributors
+            // not rendered (the tile or the pixel left empty): no contributors
+            if (skip[(size_t)m * tw * th + t] || pskip[(size_t)m * HW + pi]) continue;
             const Subset& s = subs[m];
             const int32_t* lst = s.tiles.list.data() + s.tiles.start[t];
             const int64_t cnt = s.tiles.start[t + 1] - s.tiles.start[t];

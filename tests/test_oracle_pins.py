@@ -568,14 +568,17 @@ def test_cell_order_is_a_visibility_order():
                     assert ok, (K, eye, order, i, j)
 
 
-def _saturating_slabs(seed):
+def _saturating_slabs(seed, half_middle=False):
     """Three dense opaque slabs one behind the other (camera at z = -3 looking along +z),
-    and the three cells split at z = -0.4 and z = 0.4."""
+    and the three cells split at z = -0.4 and z = 0.4.  half_middle: the middle slab
+    ends at x = 0.1, so the pixels saturated after two slabs end inside a column of tiles."""
     rng = np.random.default_rng(seed)
     per = (4000, 4000, 4000)
     means, ls, logits = [], [], []
     for k, n in enumerate(per):
         m = rng.uniform(-1.8, 1.8, (n, 3))
+        if half_middle and k == 1:
+            m[:, 0] = rng.uniform(-1.8, 0.1, n)
         m[:, 2] = -0.8 + 0.8 * k + rng.uniform(-0.15, 0.15, n)
         means.append(m)
         ls.append(rng.normal(-2.6, 0.15, (n, 3)))
@@ -592,10 +595,10 @@ def _saturating_slabs(seed):
 
 
 def test_saturation_skipping_leaves_the_image_and_gradients_unchanged():
-    # subsets rendered front to back; a tile of a later subset is left empty when the
-    # prefix transmittance is below eps_comp at all its pixels.  The composite skips such
-    # subsets per pixel anyway, so on a depth-separated scene images and gradients are
-    # exactly those of the full render
+    # subsets rendered front to back; a later subset leaves a pixel empty where the prefix
+    # transmittance is below eps_comp, and a tile not rendered at all when that holds at
+    # all its pixels.  The composite skips such subsets per pixel anyway, so on a
+    # depth-separated scene images and gradients are exactly those of the full render
     sc, off, boxes = _saturating_slabs(21)
     cam = _cam(64, 48)
     order = O.cell_order(boxes, cam.eye)
@@ -623,6 +626,41 @@ def test_saturation_skipping_leaves_the_image_and_gradients_unchanged():
     g_skip = O.backward_view(sc, off, cam, dC, None, o, order=order)
     for a, b in zip(g_full, g_skip):
         np.testing.assert_allclose(b, a, atol=1e-12, rtol=1e-10)
+
+
+def test_saturation_skipping_empties_exactly_the_saturated_pixels():
+    # Sec. 4.2: saturated pixels leave a later subset's pixel set.  Where the prefix of the
+    # subsets rendered before is below eps_comp the partial is empty (C = 0, T = 1, D = 0);
+    # everywhere else it is the partial of the render without skipping, also on the open
+    # pixels of tiles that are partly saturated (a tile-only skip would fail the first
+    # check there, a skip of open pixels the second)
+    sc, off, boxes = _saturating_slabs(23, half_middle=True)
+    cam = _cam(64, 48)
+    order = O.cell_order(boxes, cam.eye)
+    o = O.opts()
+    full = O.render_view(sc, off, cam, o)
+    skipr = O.render_view(sc, off, cam, o, order=order)
+    B = 16
+    tw, th = (cam.width + B - 1) // B, (cam.height + B - 1) // B
+    prefix = np.ones((cam.height, cam.width))
+    partial_tiles = 0
+    for r, m in enumerate(order):
+        if r > 0:
+            shut = prefix < o.eps_comp  # the same FP64 products as the oracle's, same order
+            assert np.all(skipr["Cp"][m][:, shut] == 0.0)
+            assert np.all(skipr["Tp"][m][shut] == 1.0) and np.all(skipr["Dp"][m][shut] == 0.0)
+            np.testing.assert_array_equal(skipr["Cp"][m][:, ~shut], full["Cp"][m][:, ~shut])
+            np.testing.assert_array_equal(skipr["Tp"][m][~shut], full["Tp"][m][~shut])
+            np.testing.assert_array_equal(skipr["Dp"][m][~shut], full["Dp"][m][~shut])
+            pad = np.zeros((th * B, tw * B), bool)
+            pad[:cam.height, :cam.width] = shut
+            per_tile = pad.reshape(th, B, tw, B).sum(axis=(1, 3)).reshape(-1)
+            n_in = np.zeros((th * B, tw * B), int)
+            n_in[:cam.height, :cam.width] = 1
+            n_in = n_in.reshape(th, B, tw, B).sum(axis=(1, 3)).reshape(-1)
+            partial_tiles += int(((per_tile > 0) & (per_tile < n_in)).sum())
+        prefix = prefix * skipr["Tp"][m]
+    assert partial_tiles > 0
 
 
 def test_saturation_skipping_drops_a_front_subset_when_ordered_wrongly():
