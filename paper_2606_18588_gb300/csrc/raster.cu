@@ -261,21 +261,23 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
   const ImgDev im = b.imgs[ti.v * b.K + ti.k];
   const int64_t HW = (int64_t)ti.W * ti.H;
   if (b.order && b.wave > 0) {
-    // saturation skipping: leave the tile empty if the subsets rendered before this one
-    // took the transmittance below eps_comp at every pixel (the composite would skip this
-    // subset there anyway)
+    const unsigned inb = live;  // slots inside the image
+    // saturation skipping: a pixel where the subsets rendered before this one took the
+    // transmittance below eps_comp leaves this subset's pixel set (the composite would
+    // skip this subset there anyway): it stays empty (T = 1, no contributor); a tile with
+    // no open pixel is left empty as a whole
     const float* tp = b.tpre + b.pix_off[ti.v];
-    bool open = false;
 #pragma unroll
     for (int i = 0; i < PPT; ++i)
-      if ((live >> i) & 1u)
-        open |= tp[(int64_t)(ti.y + 4 * slot_row<PPT>(i)) * ti.W + ti.x + 8 * slot_col<PPT>(i)] >=
-                b.eps_comp;
-    if (!__syncthreads_or(open)) {
+      if ((live >> i) & 1u &&
+          !(tp[(int64_t)(ti.y + 4 * slot_row<PPT>(i)) * ti.W + ti.x + 8 * slot_col<PPT>(i)] >=
+            b.eps_comp))
+        live &= ~(1u << i);
+    if (!__syncthreads_or(live != 0)) {
       if (kCount && threadIdx.x == 0 && b.counters) atomicAdd(b.counters + 6, 1ull);
 #pragma unroll
       for (int i = 0; i < PPT; ++i) {
-        if (!((live >> i) & 1u)) continue;
+        if (!((inb >> i) & 1u)) continue;
         const int64_t p = (int64_t)(ti.y + 4 * slot_row<PPT>(i)) * ti.W + ti.x + 8 * slot_col<PPT>(i);
         im.rgb[p] = 0.0f;
         im.rgb[HW + p] = 0.0f;
