@@ -274,12 +274,13 @@ int splx_batch_set_cross_filter(splx_batch_t b, const float* cells);
 /* Saturation skipping (Sec. 4.2 "saturation skipping", with the composite's threshold
  * eps_comp of splx_opts).  order (host, [V][K]) is, per view, a front-to-back order of the
  * K subsets (for k-d cells: the BSP order from the camera centre).  Once set, the forward
- * renders the subsets in K waves in that order and leaves a (view, subset, tile) work item
- * empty (C = 0, T = 1, D = 0, no contributor) when the product of the transmittances of
- * the subsets rendered before it is below eps_comp at every pixel of the tile; its
- * backward then has nothing to do.  The composite skips such subsets at those pixels
- * anyway, so images and gradients are unchanged wherever the per-pixel subset order of
- * Eq. 5 agrees with the given order.  NULL turns skipping off.  Each row must be a
+ * renders the subsets in K waves in that order, and a subset leaves a pixel empty (C = 0,
+ * T = 1, D = 0, no contributor) where the product of the transmittances of the subsets
+ * rendered before it is below eps_comp: saturated pixels leave the subset's pixel set.  A
+ * (view, subset, tile) work item with no open pixel is neither sorted nor rendered; the
+ * backward has nothing to do at empty pixels.  The composite skips such subsets at those
+ * pixels anyway, so images and gradients are unchanged wherever the per-pixel subset order
+ * of Eq. 5 agrees with the given order.  NULL turns skipping off.  Each row must be a
  * permutation of 0..K-1, else SPLX_ERR_INVALID.  Synchronises; applies to launches
  * issued afterwards. */
 int splx_batch_set_order(splx_batch_t b, const int32_t* order);
@@ -292,9 +293,10 @@ int splx_batch_kernel_times(splx_batch_t b, float* ms_out);
  * forward rasteriser out[1] = (thread, list entry) pairs examined, out[2] = (pixel,
  * entry) alpha evaluations, out[3] = (pixel, entry) blends; backward rasteriser out[4] =
  * (thread, entry) pairs, out[5] = alpha evaluations, out[6] = contributions (alpha >=
- * alpha_min); out[7] = (view, subset, tile) work items left empty by saturation skipping;
- * out[8] = work items outside their subset's visible region.
- * A thread owns 2 (8x8 tiles) or 4 (16x16, 32x32) pixels. */
+ * alpha_min); out[7] = (view, subset, tile) work items left empty by saturation skipping
+ * (no open pixel); out[8] = work items outside their subset's visible region.
+ * A forward thread owns 2 pixels (8x8, 16x16 tiles) or 4 (32x32); a backward thread 2
+ * (8x8), 8 (16x16: one warp per tile) or 4 (32x32). */
 int splx_batch_counters(splx_batch_t b, int64_t* out, splx_stream_t stream);
 
 /* ---- serving: continuous batching of render requests --------------------------- */
