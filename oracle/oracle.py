@@ -8,6 +8,7 @@ perturb them in FP64; the FP32 binning specification rounds them to float itself
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -60,31 +61,74 @@ class Grads(C.Structure):
                 ("sh", _dp)]
 
 
+def _bind(path):
+    """Loads an oracle build and declares its entry points."""
+    lib_ = C.CDLL(path)
+    P = C.c_void_p
+    _declare(lib_, P)
+    return lib_
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            _lib = C.CDLL(build())
-            P = C.c_void_p
-            _lib.orc_exp_spec.restype = C.c_float
-            _lib.orc_exp_spec.argtypes = [C.c_float]
-            _lib.orc_exp_spec_n.argtypes = [P, P, C.c_int64]
-            _lib.orc_log_spec_n.argtypes = [P, P, C.c_int64]
-            _lib.orc_sh_basis.argtypes = [P, C.c_int64, P]
-            _lib.orc_sh_basis_grad.argtypes = [P, C.c_int64, P]
-            _lib.orc_bin.argtypes = [P, P, P, P, P]
-            _lib.orc_tile_lists.restype = C.c_int64
-            _lib.orc_tile_lists.argtypes = [P, P, C.c_int32, C.c_double, P, P, C.c_int64]
-            _lib.orc_project.argtypes = [P, P, P]
-            _lib.orc_render.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
-            _lib.orc_composite.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P, P, P]
-            _lib.orc_render_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P, P, P, P, P,
-                                             P, P]
-            _lib.orc_backward_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P]
-            _lib.orc_adam.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_double,
-                                      C.c_double, C.c_int64]
-            _lib.orc_num_threads.restype = C.c_int
+            _lib = _bind(build())
     return _lib
+
+
+@contextlib.contextmanager
+def using(path):
+    """Runs the wrapper's functions on another build of the oracle (for instance one with a
+    planted mistake, compiled by a test from a modified copy of the source) inside the
+    `with` block."""
+    global _lib
+    other = _bind(path)
+    with _lock:
+        saved, _lib = _lib, other
+    try:
+        yield other
+    finally:
+        with _lock:
+            _lib = saved
+
+
+def compile_variant(src_text: str, out_path: str) -> str:
+    """Compiles oracle source text (the committed source with a test's change) to out_path
+    with the same flags as build()."""
+    src = out_path + ".cpp"
+    with open(src, "w") as f:
+        f.write(src_text)
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp",
+                    "-ffp-contract=off", "-fno-fast-math", "-o", out_path, src], check=True)
+    return out_path
+
+
+def source() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
+def _declare(L, P):
+    L.orc_exp_spec.restype = C.c_float
+    L.orc_exp_spec.argtypes = [C.c_float]
+    L.orc_exp_spec_n.argtypes = [P, P, C.c_int64]
+    L.orc_log_spec_n.argtypes = [P, P, C.c_int64]
+    L.orc_sh_basis.argtypes = [P, C.c_int64, P]
+    L.orc_sh_basis_grad.argtypes = [P, C.c_int64, P]
+    L.orc_bin.argtypes = [P, P, P, P, P]
+    L.orc_tile_lists.restype = C.c_int64
+    L.orc_tile_lists.argtypes = [P, P, C.c_int32, C.c_double, P, P, C.c_int64]
+    L.orc_project.argtypes = [P, P, P]
+    L.orc_render.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
+    L.orc_composite.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P, P, P]
+    L.orc_render_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P, P, P, P, P,
+                                  P, P]
+    L.orc_backward_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P]
+    L.orc_adam.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_double,
+                           C.c_double, C.c_int64]
+    L.orc_num_threads.restype = C.c_int
+    L.orc_branch_stats.argtypes = [P, P, C.c_int32, P, P, P, P]
 
 
 def _ptr(a):
@@ -277,6 +321,21 @@ def backward_view(scene, offsets, cam, dLdC, dLdT=None, o: Opts | None = None, t
     lib().orc_backward_view(C.byref(k.p), _ptr(off), K, C.byref(c), C.byref(o), _ptr(dC), _ptr(dT),
                             _ptr(tm), _ptr(_order(order, K)), _ptr(cl), C.byref(gr))
     return g
+
+
+def branch_stats(scene, offsets, cam, o: Opts | None = None):
+    """Clamp branches of the adjoint that one view reaches: (flags[n], nclamp[n]).  flags:
+    bit 0 / 1 the Jacobian's x / y clamp, bits 2-4 the colour clamp of r, g, b; nclamp: the
+    pixels at which the Gaussian is blended with alpha held at alpha_max."""
+    o = o or opts()
+    k = _Keep(scene)
+    c = camera(cam)
+    off = np.ascontiguousarray(offsets, np.int64)
+    flags = np.zeros(scene.n, np.int32)
+    ncl = np.zeros(scene.n, np.int64)
+    lib().orc_branch_stats(C.byref(k.p), _ptr(off), off.size - 1, C.byref(c), C.byref(o),
+                           _ptr(flags), _ptr(ncl))
+    return flags, ncl
 
 
 def adam(p, g, m, v, lr, b1, b2, eps, step):

@@ -1141,6 +1141,45 @@ int orc_backward_view(const orc_params* p, const int64_t* offsets, int32_t K,
   return 0;
 }
 
+// Which clamp branches of the adjoint one view exercises, so that a finite-difference pin
+// can show that it reaches each of them.  gflags[n] (visible Gaussians): bit 0 the
+// Jacobian's x clamp, bit 1 its y clamp, bits 2-4 the colour clamp of r, g, b.  nclamp[n]:
+// the number of pixels (over the K local renders) that blend the Gaussian with alpha held
+// at alpha_max, i.e. where dL/do and dL/dpower vanish.
+int orc_branch_stats(const orc_params* p, const int64_t* offsets, int32_t K,
+                     const orc_camera* cam, const orc_opts* o, int32_t* gflags, int64_t* nclamp) {
+  const int W = cam->width, H = cam->height, B = o->tile;
+  std::fill(gflags, gflags + p->n, 0);
+  std::fill(nclamp, nclamp + p->n, (int64_t)0);
+  for (int m = 0; m < K; ++m) {
+    orc_params q = slice(*p, offsets[m], offsets[m + 1]);
+    const Subset s = prepare(q, *cam, B, (float)o->alpha_min);
+    for (int64_t i = 0; i < q.n; ++i) {
+      if (!s.bins[i].visible) continue;
+      const Proj& g = s.pr[i];
+      gflags[offsets[m] + i] = g.clx | (g.cly << 1) | (g.col_clamped[0] << 2) |
+                               (g.col_clamped[1] << 3) | (g.col_clamped[2] << 4);
+    }
+    std::vector<Frag> fr;
+    for (int t = 0; t < s.tiles.tw * s.tiles.th; ++t) {
+      const int tx = t % s.tiles.tw, ty = t / s.tiles.tw;
+      const int32_t* lst = s.tiles.list.data() + s.tiles.start[t];
+      const int64_t cnt = s.tiles.start[t + 1] - s.tiles.start[t];
+      for (int py = ty * B; py < std::min(H, (ty + 1) * B); ++py)
+        for (int px = tx * B; px < std::min(W, (tx + 1) * B); ++px) {
+          fr.clear();
+          double c3[3], tt, dd;
+          int32_t lg, nc;
+          int64_t ev = 0;
+          blend_pixel(px, py, lst, cnt, s.bins, s.pr, *o, c3, tt, dd, lg, nc, ev, &fr);
+          for (const Frag& f : fr)
+            if (f.clamped) ++nclamp[offsets[m] + f.g];
+        }
+    }
+  }
+  return 0;
+}
+
 // Adam with torch.optim.Adam semantics (bias-corrected, eps outside the square root).
 void orc_adam(int64_t n, double* p, const double* g, double* m, double* v, double lr, double b1,
               double b2, double eps, int64_t step) {

@@ -449,8 +449,9 @@ def _signature(sc, off, cam, o):
     v = O.render_view(sc, off, cam, o)
     key = np.where(v["Tp"] < 1, v["Dp"] / np.maximum(1 - v["Tp"], 1e-300), np.inf)
     order = np.argsort(key, axis=0, kind="stable")
+    flags, ncl = O.branch_stats(sc, off, cam, o)
     return (vis.tobytes(), rect.tobytes(), b"".join(a.tobytes() + b.tobytes() for a, b in parts),
-            order.tobytes())
+            order.tobytes(), flags.tobytes(), ncl.tobytes())
 
 
 def _loss(sc, off, cam, o, wC, wT):
@@ -458,35 +459,86 @@ def _loss(sc, off, cam, o, wC, wT):
     return float(np.sum(wC * v["image"]) + np.sum(wT * v["T"]))
 
 
-@pytest.mark.parametrize("deg", [0, 3])
-def test_backward_matches_central_finite_differences(deg):
-    rng = np.random.default_rng(20 + deg)
-    n = 24
-    means = rng.uniform(-0.5, 0.5, (n, 3))
-    sh = np.zeros((n, I.n_sh_coeffs(deg), 3), np.float32)
-    sh[:, 0, :] = (rng.uniform(0.2, 0.8, (n, 3)) - 0.5) / Y00
-    if deg:
-        sh[:, 1:, :] = rng.normal(0, 0.2, (n, I.n_sh_coeffs(deg) - 1, 3))
-    sc = _scene(means, rng.normal(-2.6, 0.3, (n, 3)), rng.standard_normal((n, 4)),
-                rng.normal(0.0, 1.0, n), sh=sh, deg=deg)
-    perm, off, _ = I.kd_partition(sc.means, 2)
-    sc = sc.take(perm)
+# The four Gaussians of the finite-difference scene that drive the adjoint's clamp branches
+# (camera-space mean, log-scale, logit, colour; see _fd_scene).
+FD_SIDE_X, FD_SIDE_Y, FD_OPAQUE, FD_DARK = range(4)
+
+
+def _fd_scene(deg, seed):
+    """24 random Gaussians around the origin, seen from 2.2 away by a 40 x 36 camera, plus
+    four placed (in camera space) so that each clamp of the adjoint is active:
+    - FD_SIDE_X: x / z = 1.15 times the Jacobian's clamp limit 1.3 (W/2)/fx, so J uses the
+      clamped x, yet its 3-sigma footprint reaches into the image from the right;
+    - FD_SIDE_Y: the same below the image, for the y clamp;
+    - FD_OPAQUE: logit 9 (o = 0.99988) and about 8 px across, behind the others, so alpha
+      = min(0.99, o e^power) is held at 0.99 on the pixels within about 1 px of its centre;
+    - FD_DARK: a red SH sum near -0.4, so its red colour is clamped at 0 (degree 3: with
+      higher-order red terms, whose gradient and direction terms the clamp removes)."""
+    rng = np.random.default_rng(seed)
     cam = I.pinhole(40, 36, 60.0, (0.3, -0.2, -2.2), (0.0, 0.0, 0.0), 0.01)
-    # a camera-axis clamp case: one Gaussian far to the side
+    R = np.asarray(cam.R, np.float64)
+    t = np.asarray(cam.t, np.float64)
+    limx = 1.3 * (0.5 * cam.width) / cam.fx
+    limy = 1.3 * (0.5 * cam.height) / cam.fy
+    cam_means = np.array([[1.15 * limx * 2.0, 0.1, 2.0],
+                          [0.1, 1.15 * limy * 2.0, 2.0],
+                          [0.25, -0.2, 3.2],
+                          [-0.45, -0.35, 2.1]])
+    special = (cam_means - t) @ R  # world = R^T (c - t)
+    nc = I.n_sh_coeffs(deg)
+    n = 24
+    means = np.concatenate([special, rng.uniform(-0.5, 0.5, (n, 3))])
+    log_scales = np.concatenate([np.log([[0.35] * 3, [0.35] * 3, [0.45] * 3, [0.12] * 3]),
+                                 rng.normal(-2.6, 0.3, (n, 3))])
+    logits = np.concatenate([[0.5, 0.5, 9.0, 1.0], rng.normal(0.0, 1.0, n)])
+    rgb = np.concatenate([[[0.7, 0.5, 0.3], [0.3, 0.6, 0.8], [0.8, 0.7, 0.2], [-0.4, 0.6, 0.4]],
+                          rng.uniform(0.2, 0.8, (n, 3))])
+    sh = np.zeros((n + 4, nc, 3), np.float32)
+    sh[:, 0, :] = (rgb - 0.5) / Y00
+    if deg:
+        sh[:, 1:, :] = rng.normal(0, 0.2, (n + 4, nc - 1, 3))
+        sh[FD_DARK, 1:, 0] = rng.normal(0, 0.05, nc - 1)
+    sc = _scene(means, log_scales, rng.standard_normal((n + 4, 4)), logits, sh=sh, deg=deg)
+    return sc, cam
+
+
+def _fd_check(deg, seed=20):
+    """Central finite differences (h = 1e-7 max(1, |p|)) of L = sum wC * image + sum wT * T
+    against the oracle's backward, for 40 seeded parameters of every array and for every
+    parameter of the four clamp Gaussians, leaving out parameters whose +-h changes a
+    discrete decision (visibility, rectangle, contributors, subset order, clamp branches).
+    Returns the number of parameters checked and the clamp Gaussians' checked count."""
+    sc, cam = _fd_scene(deg, seed + deg)
+    rng = np.random.default_rng(seed + 100 + deg)
+    perm, off, _ = I.kd_partition(sc.means, 2)
+    inv = np.argsort(perm)
+    specials = inv[:4]  # positions of the clamp Gaussians after the partition's reordering
+    sc = sc.take(perm)
     o = O.opts(eps_T=1e-4, eps_comp=1e-4)
+    flags, ncl = O.branch_stats(sc, off, cam, o)
+    vis, _, _ = O.bin(sc, cam)
+    assert vis[specials].all()
+    assert flags[specials[FD_SIDE_X]] & 1, "x clamp of the Jacobian not reached"
+    assert flags[specials[FD_SIDE_Y]] & 2, "y clamp of the Jacobian not reached"
+    assert ncl[specials[FD_OPAQUE]] > 0, "alpha clamp not reached"
+    assert flags[specials[FD_DARK]] & 4, "colour clamp not reached"
     wC = rng.standard_normal((3, cam.height, cam.width))
     wT = rng.standard_normal((cam.height, cam.width))
     grads = O.backward_view(sc, off, cam, wC, wT, o)
+    for g in specials:  # each clamp Gaussian takes part in the image
+        assert np.abs(grads[0][g]).max() > 0.0
     base_sig = _signature(sc, off, cam, o)
     arrays = list(sc.arrays())
-    checked = 0
+    checked = checked_special = 0
     for ai, (arr, g) in enumerate(zip(arrays, grads)):
+        per = arr.size // sc.n
         flat = arr.reshape(-1)
         gflat = g.reshape(-1)
-        idx = rng.choice(flat.size, size=min(flat.size, 40), replace=False)
-        for j in idx:
+        idx = set(rng.choice(flat.size, size=min(flat.size, 40), replace=False).tolist())
+        sp = {int(s) * per + k for s in specials for k in range(per)}
+        for j in sorted(idx | sp):
             x0 = float(flat[j])
-            h = 1e-6 * max(1.0, abs(x0))
+            h = 1e-7 * max(1.0, abs(x0))
             vals = []
             ok = True
             for sgn in (1, -1):
@@ -502,7 +554,15 @@ def test_backward_matches_central_finite_differences(deg):
             scale = max(1e-3, np.abs(gflat).max() * 1e-3)
             assert abs(fd - gflat[j]) <= 1e-4 * max(abs(fd), scale), (ai, j, fd, gflat[j])
             checked += 1
-    assert checked >= 100
+            checked_special += j in sp
+    return checked, checked_special, sum(len(range(a.size // sc.n)) for a in arrays) * 4
+
+
+@pytest.mark.parametrize("deg", [0, 3])
+def test_backward_matches_central_finite_differences(deg):
+    checked, checked_special, n_special = _fd_check(deg)
+    assert checked >= 150
+    assert checked_special >= 0.8 * n_special
 
 
 # --------------------------------------------------------------------------- Adam
