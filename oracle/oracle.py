@@ -51,6 +51,11 @@ class Opts(C.Structure):
 _dp = C.POINTER(C.c_double)
 
 
+class Bounds(C.Structure):
+    _fields_ = [("image", _dp), ("T", _dp), ("partC", _dp), ("partT", _dp),
+                ("cmax", C.c_double), ("dmax", C.c_double)]
+
+
 class Params(C.Structure):
     _fields_ = [("means", _dp), ("log_scales", _dp), ("quats", _dp), ("opacity_logits", _dp),
                 ("sh", _dp), ("n", C.c_int64), ("sh_degree", C.c_int32)]
@@ -120,10 +125,11 @@ def _declare(L, P):
     L.orc_tile_lists.restype = C.c_int64
     L.orc_tile_lists.argtypes = [P, P, C.c_int32, C.c_double, P, P, C.c_int64]
     L.orc_project.argtypes = [P, P, P]
-    L.orc_render.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
-    L.orc_composite.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P, P, P]
+    L.orc_render.argtypes = [P, P, P, P, P, P, P, P, P, P, P, P]
+    L.orc_composite.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P, P, P, P,
+                                P]
     L.orc_render_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P, P, P, P, P,
-                                  P, P]
+                                  P, P, P]
     L.orc_backward_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P]
     L.orc_adam.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_double,
                            C.c_double, C.c_int64]
@@ -225,8 +231,19 @@ def project(scene, cam) -> np.ndarray:
     return out
 
 
-def render(scene, cam, o: Opts | None = None, tile_mask=None):
-    """Local render of one subset: dict of C[3,H,W], T, D, last, ncontrib, amb, evaluated."""
+def _bounds(H, W, K, image=True):
+    out = dict(partC=np.zeros((K, H, W)), partT=np.zeros((K, H, W)))
+    if image:
+        out.update(image=np.zeros((H, W)), T=np.zeros((H, W)))
+    b = Bounds(*(out[k].ctypes.data_as(_dp) if k in out else None
+                 for k in ("image", "T", "partC", "partT")), 0.0, 0.0)
+    return b, out
+
+
+def render(scene, cam, o: Opts | None = None, tile_mask=None, bounds=False):
+    """Local render of one subset: dict of C[3,H,W], T, D, last, ncontrib, amb, evaluated.
+    With bounds: also "flip", the flip bounds of the ambiguous pixels (|delta C| <=
+    partC cmax, |delta D| <= partC dmax, |delta T| <= partT; see orc_bounds)."""
     o = o or opts()
     k = _Keep(scene)
     c = camera(cam)
@@ -235,22 +252,35 @@ def render(scene, cam, o: Opts | None = None, tile_mask=None):
     last = np.full((H, W), -1, np.int32); nc = np.zeros((H, W), np.int32)
     amb = np.zeros((H, W), np.uint8); st = np.zeros(1, np.int64)
     tm = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8)
+    bd, bout = _bounds(H, W, 1, image=False) if bounds else (None, None)
     lib().orc_render(C.byref(k.p), C.byref(c), C.byref(o), _ptr(tm), _ptr(Cc), _ptr(T), _ptr(D),
-                     _ptr(last), _ptr(nc), _ptr(amb), _ptr(st))
-    return dict(C=Cc, T=T, D=D, last=last, ncontrib=nc, amb=amb, evaluated=int(st[0]))
+                     _ptr(last), _ptr(nc), _ptr(amb), _ptr(st),
+                     C.byref(bd) if bd is not None else None)
+    out = dict(C=Cc, T=T, D=D, last=last, ncontrib=nc, amb=amb, evaluated=int(st[0]))
+    if bounds:
+        out["flip"] = dict(C=bout["partC"][0] * bd.cmax, T=bout["partT"][0],
+                           D=bout["partC"][0] * bd.dmax, cmax=bd.cmax, dmax=bd.dmax)
+    return out
 
 
-def composite(Cp, Tp, Dp, o: Opts | None = None):
-    """Eq. 5 over K partials (C[K,3,H,W], T[K,H,W], D[K,H,W]): image, T, nused, amb."""
+def composite(Cp, Tp, Dp, o: Opts | None = None, bounds=False):
+    """Eq. 5 over K partials (C[K,3,H,W], T[K,H,W], D[K,H,W]): image, T, nused, amb; with
+    bounds also "flip" (image, T): the effect of the flagged near-tied keys and saturation
+    cuts of these exact partials."""
     o = o or opts()
     Cp = np.ascontiguousarray(Cp, np.float64); Tp = np.ascontiguousarray(Tp, np.float64)
     Dp = np.ascontiguousarray(Dp, np.float64)
     K, _, H, W = Cp.shape
     out = np.empty((3, H, W)); To = np.empty((H, W)); nu = np.empty((H, W), np.int32)
     amb = np.zeros((H, W), np.uint8)
+    bi = np.zeros((H, W)) if bounds else None
+    bt = np.zeros((H, W)) if bounds else None
     lib().orc_composite(K, H, W, _ptr(Cp), _ptr(Tp), _ptr(Dp), C.byref(o), _ptr(out), _ptr(To),
-                        _ptr(nu), _ptr(amb))
-    return dict(image=out, T=To, nused=nu, amb=amb)
+                        _ptr(nu), _ptr(amb), _ptr(bi), _ptr(bt))
+    res = dict(image=out, T=To, nused=nu, amb=amb)
+    if bounds:
+        res["flip"] = dict(image=bi, T=bt)
+    return res
 
 
 def _order(order, K):
@@ -271,14 +301,15 @@ def _cells(cells, K):
 
 
 def render_view(scene, offsets, cam, o: Opts | None = None, tile_mask=None, separable=False,
-                order=None, cells=None):
+                order=None, cells=None, bounds=False):
     """K contiguous subsets rendered and composited: dict(image, T, Cp, Tp, Dp, amb, sep,
     skip).  With `order` (front-to-back subset order) the partials are rendered in that
     order with saturation skipping (Sec. 4.2): a subset leaves empty the pixels whose prefix
     transmittance is below eps_comp, and skip[m, t] marks the tiles it left empty as a
     whole (no open pixel).  With
     `cells` (the subsets' k-d boxes [K, 2, 3]) cross-boundary Gaussians are filtered per
-    ray as in Sec. 8.1."""
+    ray as in Sec. 8.1.  With bounds: also "flip", the flip bounds of the ambiguous pixels:
+    image and T of the composite, partC / partT / partD per partial (absolute amounts)."""
     o = o or opts()
     k = _Keep(scene)
     c = camera(cam)
@@ -295,11 +326,17 @@ def render_view(scene, offsets, cam, o: Opts | None = None, tile_mask=None, sepa
     B = int(o.tile)
     skip = np.zeros((K, ((H + B - 1) // B) * ((W + B - 1) // B)), np.uint8)
     cl = _cells(cells, K)
+    bd, bout = _bounds(H, W, K) if bounds else (None, None)
     lib().orc_render_view(C.byref(k.p), _ptr(off), K, C.byref(c), C.byref(o), _ptr(tm), _ptr(od),
                           _ptr(cl), _ptr(out), _ptr(To), _ptr(Cp), _ptr(Tp), _ptr(Dp), _ptr(amb),
-                          _ptr(sep), _ptr(skip), _ptr(st))
-    return dict(image=out, T=To, Cp=Cp, Tp=Tp, Dp=Dp, amb=amb, sep=sep, skip=skip,
-                evaluated=int(st[0]))
+                          _ptr(sep), _ptr(skip), _ptr(st), C.byref(bd) if bd is not None else None)
+    res = dict(image=out, T=To, Cp=Cp, Tp=Tp, Dp=Dp, amb=amb, sep=sep, skip=skip,
+               evaluated=int(st[0]))
+    if bounds:
+        res["flip"] = dict(image=bout["image"], T=bout["T"], partC=bout["partC"] * bd.cmax,
+                           partT=bout["partT"], partD=bout["partC"] * bd.dmax, cmax=bd.cmax,
+                           dmax=bd.dmax)
+    return res
 
 
 def backward_view(scene, offsets, cam, dLdC, dLdT=None, o: Opts | None = None, tile_mask=None,

@@ -68,6 +68,18 @@ typedef struct {
   double *means, *log_scales, *quats, *opacity_logits, *sh;
 } orc_grads;
 
+// Flip bounds of a render (every pointer nullable).  On a pixel with an ambiguous decision
+// an FP32 implementation may legitimately take the other side; these bound how far that
+// moves each output (blend_pixel and composite_bounds say how they are derived).
+typedef struct {
+  double* image;   // [H][W] bound on |delta| of each channel of the composited image
+  double* T;       // [H][W] bound on |delta| of the composited transmittance
+  double* partC;   // [K][H][W] per partial: |delta C^m| <= partC cmax, |delta D^m| <= partC dmax
+  double* partT;   // [K][H][W] per partial: |delta T^m| <= partT
+  double cmax;     // out: largest colour channel of a visible Gaussian (and of the background)
+  double dmax;     // out: largest depth of a visible Gaussian
+} orc_bounds;
+
 }  // extern "C"
 
 namespace {
@@ -444,14 +456,45 @@ struct Frag {
 enum { AMB_ALPHA = 1, AMB_POWER = 2, AMB_TSTOP = 4, AMB_KEY = 8, AMB_SAT = 16 };
 
 // Blend one pixel of one subset front to back.  Returns flags of ambiguous decisions.
+//
+// flip (nullable) receives a bound on how far an implementation that takes any flagged
+// decision the other way (and any later transmittance stop that such a change can move)
+// may end from this result: |delta C| <= flip[0] max c, |delta D| <= flip[0] max d,
+// |delta T| <= flip[1].  Taking the decisions in list order, with rho = prod 1/(1 - alpha)
+// - 1 over the alpha_min decisions flipped so far (the most any transmittance can have
+// grown or shrunk by then):
+//   * an alpha_min decision at Gaussian i moves C by alpha_i T_i (c_i - X) with X the
+//     normalised colour behind i, at most alpha_i T_i (1 + rho) max c, and multiplies
+//     every later transmittance by (1 - alpha_i)^(+-1), which rho accumulates;
+//   * a flagged power sign or transmittance stop at Gaussian k, or an unflagged stop test
+//     that the accumulated rho can move (relative margin <= rho + its own margin), leaves
+//     everything from k on within [0, T_k (1 + rho) max c] in both results: that amount
+//     bounds the rest, and later decisions add nothing;
+//   * T_final moves by at most T_final rho plus the stop amounts.
+// flip[2], flip[3] receive the depth range of the Gaussians that may contribute in either
+// result (those blended, flagged, or in the rectangle after a bounded rest), within which
+// the subset's composite key D / (1 - T) stays whichever of them contribute (+inf, -inf if
+// none may).
 int blend_pixel(int px, int py, const int32_t* lst, int64_t cnt, const std::vector<BinRec>& bins,
                 const std::vector<Proj>& pr, const orc_opts& o, double C[3], double& T,
                 double& D, int32_t& last, int32_t& ncontrib, int64_t& evaluated,
-                std::vector<Frag>* frags) {
+                std::vector<Frag>* frags, double* flip = nullptr) {
   int amb = 0;
   T = 1.0; D = 0.0; C[0] = C[1] = C[2] = 0.0; last = -1; ncontrib = 0;
   const double pcx = px + 0.5, pcy = py + 0.5;
-  for (int64_t j = 0; j < cnt; ++j) {
+  double rho = 0.0, massC = 0.0, massT = 0.0;
+  bool rest_bounded = false;  // a stop amount already bounds everything from here on
+  int64_t rest_from = cnt;    // list position where the rest became bounded
+  double dlo = INFINITY, dhi = -INFINITY;
+  int64_t j = 0;
+  auto bound_rest = [&](double Tk) {
+    if (rest_bounded) return;
+    massC += Tk * (1.0 + rho);
+    massT += Tk * (1.0 + rho);
+    rest_bounded = true;
+    rest_from = j;
+  };
+  for (; j < cnt; ++j) {
     const int32_t g = lst[j];
     const BinRec& b = bins[g];
     ++evaluated;
@@ -461,8 +504,12 @@ int blend_pixel(int px, int py, const int32_t* lst, int64_t cnt, const std::vect
     const double t1 = q.A * dx * dx, t2 = q.C * dy * dy, t3 = 2.0 * q.B * dx * dy;
     const double power = -0.5 * (t1 + t2) - 0.5 * t3;
     if (std::fabs(power) <= o.amb_power * (std::fabs(t1) + std::fabs(t2) + std::fabs(t3)) &&
-        (t1 + t2 + std::fabs(t3)) > 0.0)
+        (t1 + t2 + std::fabs(t3)) > 0.0) {
       amb |= AMB_POWER;
+      bound_rest(T);
+      dlo = std::min(dlo, q.depth);
+      dhi = std::max(dhi, q.depth);
+    }
     if (power > 0.0) continue;
     const double ex = std::exp(power);
     const double raw = q.o * ex;
@@ -472,11 +519,29 @@ int blend_pixel(int px, int py, const int32_t* lst, int64_t cnt, const std::vect
     // the magnitude of its terms (they cancel for elongated Gaussians): the alpha and
     // T-stop margins include it
     const double rel_alpha = clamped ? 0.0 : 0.5 * o.amb_power * (std::fabs(t1) + std::fabs(t2) + std::fabs(t3));
-    if (std::fabs(alpha - o.alpha_min) <= (o.amb_alpha + rel_alpha) * o.alpha_min) amb |= AMB_ALPHA;
+    if (std::fabs(alpha - o.alpha_min) <= (o.amb_alpha + rel_alpha) * o.alpha_min) {
+      amb |= AMB_ALPHA;
+      if (!rest_bounded) {
+        massC += alpha * T * (1.0 + rho);
+        rho = (1.0 + rho) / (1.0 - alpha) - 1.0;
+      }
+      dlo = std::min(dlo, q.depth);
+      dhi = std::max(dhi, q.depth);
+    }
     if (alpha < o.alpha_min) continue;
+    dlo = std::min(dlo, q.depth);
+    dhi = std::max(dhi, q.depth);
     const double Tn = T * (1.0 - alpha);
     const double rel_T = o.amb_T + rel_alpha * alpha / (1.0 - alpha);
-    if (o.eps_T > 0.0 && std::fabs(Tn - o.eps_T) <= rel_T * o.eps_T) amb |= AMB_TSTOP;
+    if (o.eps_T > 0.0) {
+      const double margin = std::fabs(Tn - o.eps_T);
+      if (margin <= rel_T * o.eps_T) {
+        amb |= AMB_TSTOP;
+        bound_rest(T);
+      } else if (rho > 0.0 && margin <= (rel_T + 1.001 * rho) * o.eps_T) {
+        bound_rest(T);
+      }
+    }
     if (Tn < o.eps_T) break;
     const double w = alpha * T;
     for (int ch = 0; ch < 3; ++ch) C[ch] += q.col[ch] * w;
@@ -485,6 +550,21 @@ int blend_pixel(int px, int py, const int32_t* lst, int64_t cnt, const std::vect
     T = Tn;
     last = g;
     ++ncontrib;
+  }
+  if (flip) {
+    flip[0] = massC;
+    flip[1] = massT + (rest_bounded ? 0.0 : T * rho);
+    // after a bounded rest or an early stop any later Gaussian of the rectangle may
+    // contribute in the other result
+    const int64_t from = rest_bounded ? rest_from : cnt;
+    for (int64_t k = from; k < cnt; ++k) {
+      const BinRec& b = bins[lst[k]];
+      if (px < b.x0 || px > b.x1 || py < b.y0 || py > b.y1) continue;
+      dlo = std::min(dlo, pr[lst[k]].depth);
+      dhi = std::max(dhi, pr[lst[k]].depth);
+    }
+    flip[2] = dlo;
+    flip[3] = dhi;
   }
   return amb;
 }
@@ -644,13 +724,139 @@ int composite_order(int K, const double* Tm, const double* Dm, const orc_opts& o
   return amb;
 }
 
+// Eq. 5 at one pixel, in the order ord, with the saturation cut: image rgb and
+// transmittance.
+void composite_one(int K, const double* Tm, const double* Cm, const int* ord, const orc_opts& o,
+                   double out[3], double& Tout) {
+  double P = 1.0;
+  out[0] = out[1] = out[2] = 0.0;
+  for (int j = 0; j < K; ++j) {
+    if (P < o.eps_comp) break;
+    const int m = ord[j];
+    for (int ch = 0; ch < 3; ++ch) out[ch] += Cm[3 * m + ch] * P;
+    P *= Tm[m];
+  }
+  for (int ch = 0; ch < 3; ++ch) out[ch] += o.bg[ch] * P;
+  Tout = P;
+}
+
+// Flip bound of one composited pixel (Eq. 5), from the K partials (Tm, Dm, Cm [K][3]),
+// their flip bounds fC, fT (|delta C^m| <= fC cmax, |delta T^m| <= fT) and the depth
+// range [dlo, dhi] of the Gaussians that may contribute to each (blend_pixel).  With P_j
+// the prefix transmittance at rank j of the composite order and L the ranks before the
+// saturation cut:
+//   * a partial's own change moves the image by at most P_j (fC + fT) cmax (its colour,
+//     and its transmittance times the normalised colour behind it, background included)
+//     and the transmittance by P_j fT;
+//   * a partial with a flagged decision keeps its key D/(1 - T) within [dlo, dhi] (the key
+//     is an alpha-weighted mean of contributor depths) and within the first-order reach
+//     (|delta D| + key |delta T|) / (1 - T - |delta T|), or becomes empty (key +inf, placed
+//     last) if its change can reach its whole occupancy 1 - T; two neighbours whose key
+//     ranges meet (with the FP32 margin of composite_order) may be composited the other
+//     way round, which moves the image by P_j |C_a (1 - T_b) - C_b (1 - T_a)| (Eq. 5); in a
+//     run of three or more, each subset m adds between C_m prod_{k != m} T_k and C_m
+//     whatever the order, so the run moves it by at most P_j sum_m C_m (1 - prod T_k);
+//   * the saturation cut leaves out at most Pu cmax of colour and Pu of transmittance, Pu
+//     the largest prefix, under the partials' flips, at the first rank where the cut can
+//     fall.
+void composite_bounds(int K, const double* Tm, const double* Dm, const double* Cm,
+                      const double* fC, const double* fT, const double* dlo, const double* dhi,
+                      const orc_opts& o, double cmax, double dmax, const int* ord, double& bimg,
+                      double& bT) {
+  bimg = 0.0;
+  bT = 0.0;
+  std::vector<double> P(K + 1, 1.0);
+  int L = 0;
+  for (int j = 0; j < K; ++j) {
+    if (P[j] < o.eps_comp) break;
+    P[j + 1] = P[j] * Tm[ord[j]];
+    ++L;
+  }
+  for (int j = 0; j < L; ++j) {
+    const int m = ord[j];
+    bimg += P[j] * (fC[m] + fT[m]) * cmax;
+    bT += P[j] * fT[m];
+  }
+  // the cut may fall at the first rank whose prefix, moved by the partials' flips before it
+  // (between Pl and Pu: products of T -+ fT), can lie below eps_comp (within amb_T);
+  // everything from there on lies within [0, Pu cmax] in both results
+  if (L < K || o.eps_comp > 0.0) {
+    double Pl = 1.0, Pu = 1.0;
+    for (int j = 0; j <= L && j < K + 1; ++j) {
+      if (j == K) break;
+      if (Pl < o.eps_comp * (1.0 + o.amb_T) || j == L) {
+        if (j < K) {
+          bimg += Pu * cmax;
+          bT += Pu;
+        }
+        break;
+      }
+      const int m = ord[j];
+      Pl *= std::max(0.0, Tm[m] - fT[m]);
+      Pu *= std::min(1.0, Tm[m] + fT[m]);
+    }
+  }
+  // the range each key may take
+  std::vector<double> klo(K), khi(K);
+  for (int m = 0; m < K; ++m) {
+    const double key = Tm[m] < 1.0 ? Dm[m] / (1.0 - Tm[m]) : INFINITY;
+    klo[m] = khi[m] = key;
+    if (fC[m] == 0.0 && fT[m] == 0.0) continue;  // no flagged decision: the key stays
+    if (fT[m] >= 1.0 - Tm[m]) {  // may become empty (or, if empty, take any contributor)
+      klo[m] = std::min(std::isfinite(key) ? key : INFINITY, dlo[m]);
+      khi[m] = INFINITY;
+      continue;
+    }
+    // both the contributors' depth range and the first-order reach
+    // (|delta D| + key |delta T|) / (occupancy - |delta T|) bound the key's change
+    const double reach = (fC[m] * dmax + std::fabs(key) * fT[m]) / ((1.0 - Tm[m]) - fT[m]);
+    klo[m] = std::max(key - reach, std::min(key, dlo[m]));
+    khi[m] = std::min(key + reach, std::max(key, dhi[m]));
+  }
+  std::vector<uint8_t> near(K, 0);  // near[j]: ranks j and j + 1 may swap
+  for (int j = 0; j + 1 < K && j < L; ++j) {
+    const int a = ord[j], b = ord[j + 1];
+    if (!std::isfinite(klo[a]) && !std::isfinite(klo[b])) break;  // both stay empty
+    const double occ = std::max(std::min(1.0 - Tm[a], 1.0 - Tm[b]), 1e-300);
+    const double ref = std::max(std::isfinite(khi[a]) ? std::fabs(khi[a]) : 0.0,
+                                std::isfinite(klo[b]) ? std::fabs(klo[b]) : 0.0);
+    const double tol = (o.amb_key + 1e-6 / occ) * ref;
+    near[j] = khi[a] + tol >= klo[b];
+  }
+  for (int j = 0; j < K && j < L;) {
+    if (!near[j]) { ++j; continue; }
+    int e = j;
+    while (e < K && near[e]) ++e;  // ranks j .. e may be reordered among themselves
+    double sw = 0.0;
+    for (int ch = 0; ch < 3; ++ch) {
+      double d = 0.0;
+      if (e == j + 1) {
+        const int a = ord[j], b = ord[j + 1];
+        d = std::fabs(Cm[3 * a + ch] * (1.0 - Tm[b]) - Cm[3 * b + ch] * (1.0 - Tm[a]));
+      } else {
+        for (int r = j; r <= e && r < K; ++r) {
+          double others = 1.0;
+          for (int r2 = j; r2 <= e && r2 < K; ++r2)
+            if (r2 != r) others *= Tm[ord[r2]];
+          d += Cm[3 * ord[r] + ch] * (1.0 - others);
+        }
+      }
+      sw = std::max(sw, d);
+    }
+    bimg += P[j] * sw;
+    j = e + 1;
+  }
+}
+
 }  // namespace
 
 // Local render of one subset (filtered by f as subset m with global offset goff, if given).
 int render_subset(const orc_params* p, const orc_camera* cam, const orc_opts* o,
                   const uint8_t* tile_mask, double* C, double* T, double* D, int32_t* last,
                   int32_t* ncontrib, uint8_t* amb, int64_t* stats, const CrossFilter* f, int m,
-                  int64_t goff, const uint8_t* pix_open = nullptr);
+                  int64_t goff, const uint8_t* pix_open = nullptr, double* flips = nullptr,
+                  double* cdmax = nullptr, const uint8_t* pix_alt = nullptr,
+                  double* alt = nullptr);
 
 namespace {
 
@@ -663,11 +869,19 @@ namespace {
 // margin amb_T of eps_comp is flagged AMB_SAT.  Renders into C, T, D (planar per subset)
 // and, if pskip is given, sets pskip[m * HW + pixel] for the pixels left empty.  With
 // order == nullptr every subset is rendered on every pixel of tile_mask's tiles.
+// With flips given, flips[0..3] ([K][H][W] each) receive each partial's flip bounds and
+// contributor depth range (blend_pixel) and cdmax (2) the largest colour and depth.  With
+// saturation skipping, a pixel's skip decision for a subset is ambiguous when its prefix
+// lies within amb_T of eps_comp, widened by the relative change that the flip bounds of the
+// subsets before it allow (sum of fT / (T - fT)); for such pixels sat_alt ([K][H][W])
+// is set and alt ([K][5][H][W]: C rgb, T, D) holds the partial's other outcome.
 void render_partials(const orc_params& p, const int64_t* offsets, int K, const orc_camera& cam,
                      const orc_opts& o, const uint8_t* tile_mask, const int32_t* order,
                      std::vector<double>& C, std::vector<double>& T, std::vector<double>& D,
                      std::vector<uint8_t>& skip, uint8_t* amb, int64_t* stats,
-                     const CrossFilter* f, std::vector<uint8_t>* pskip = nullptr) {
+                     const CrossFilter* f, std::vector<uint8_t>* pskip = nullptr,
+                     std::vector<double>* flips = nullptr, double* cdmax = nullptr,
+                     std::vector<uint8_t>* sat_alt = nullptr, std::vector<double>* alt = nullptr) {
   const int W = cam.width, H = cam.height, B = o.tile;
   const int64_t HW = (int64_t)W * H;
   const int tw = (W + B - 1) / B, th = (H + B - 1) / B, nt = tw * th;
@@ -676,14 +890,29 @@ void render_partials(const orc_params& p, const int64_t* offsets, int K, const o
   D.assign((size_t)K * HW, 0.0);
   skip.assign((size_t)K * nt, 0);
   if (pskip) pskip->assign((size_t)K * HW, 0);
-  std::vector<double> prefix(HW, 1.0);
+  if (flips) {
+    flips[0].assign((size_t)K * HW, 0.0);
+    flips[1].assign((size_t)K * HW, 0.0);
+    flips[2].assign((size_t)K * HW, INFINITY);
+    flips[3].assign((size_t)K * HW, -INFINITY);
+  }
+  std::vector<double> fl1(flips ? (size_t)4 * HW : 0);
+  std::vector<double> prefix(HW, 1.0), prefix_rel(HW, 0.0);
+  std::vector<uint8_t> sat_amb(HW, 0);
+  const bool want_alt = flips && order && sat_alt && alt;
+  if (want_alt) {
+    sat_alt->assign((size_t)K * HW, 0);
+    alt->assign((size_t)K * 5 * HW, 0.0);
+  }
   std::vector<uint8_t> mask(nt), a1(HW, 0), open(HW, 1);
   for (int r = 0; r < K; ++r) {
     const int m = order ? order[r] : r;
     if (order && r > 0)
       for (int64_t i = 0; i < HW; ++i) {
         open[i] = (uint8_t)(prefix[i] >= o.eps_comp);
-        if (amb && std::fabs(prefix[i] - o.eps_comp) <= o.amb_T * o.eps_comp) amb[i] |= AMB_SAT;
+        sat_amb[i] = std::fabs(prefix[i] - o.eps_comp) <=
+                     (o.amb_T + prefix_rel[i] * (1.0 + o.amb_T)) * o.eps_comp;
+        if (amb && sat_amb[i]) amb[i] |= AMB_SAT;
         if (pskip && !open[i]) (*pskip)[(size_t)m * HW + i] = 1;
       }
     for (int t = 0; t < nt; ++t) {
@@ -704,11 +933,29 @@ void render_partials(const orc_params& p, const int64_t* offsets, int K, const o
     std::fill(a1.begin(), a1.end(), 0);
     render_subset(&q, &cam, &o, mask.data(), C.data() + (size_t)m * 3 * HW,
                   T.data() + (size_t)m * HW, D.data() + (size_t)m * HW, nullptr, nullptr,
-                  a1.data(), stats, f, m, offsets[m], order && r > 0 ? open.data() : nullptr);
+                  a1.data(), stats, f, m, offsets[m], order && r > 0 ? open.data() : nullptr,
+                  flips ? fl1.data() : nullptr, cdmax,
+                  want_alt && r > 0 ? sat_amb.data() : nullptr,
+                  want_alt ? alt->data() + (size_t)m * 5 * HW : nullptr);
+    if (flips)
+      for (int64_t i = 0; i < HW; ++i)
+        for (int k = 0; k < 4; ++k) flips[k][(size_t)m * HW + i] = fl1[(size_t)k * HW + i];
+    if (want_alt && r > 0)
+      for (int64_t i = 0; i < HW; ++i) (*sat_alt)[(size_t)m * HW + i] = sat_amb[i];
     if (amb)
       for (int64_t i = 0; i < HW; ++i) amb[i] |= a1[i];
     if (order)
-      for (int64_t i = 0; i < HW; ++i) prefix[i] *= T[(size_t)m * HW + i];
+      for (int64_t i = 0; i < HW; ++i) {
+        const double Tb = T[(size_t)m * HW + i];
+        prefix[i] *= Tb;
+        if (flips) {
+          // relative change of the prefix that this subset's flips (or other outcome) allow
+          double dT = flips[1][(size_t)m * HW + i];
+          if (want_alt && r > 0 && sat_amb[i])
+            dT = std::max(dT, std::fabs(alt->at(((size_t)m * 5 + 3) * HW + i) - Tb));
+          prefix_rel[i] += dT > 0.0 ? (Tb - dT > 0.0 ? dT / (Tb - dT) : INFINITY) : 0.0;
+        }
+      }
   }
 }
 
@@ -783,38 +1030,83 @@ void orc_project(const orc_params* p, const orc_camera* cam, double* out) {
 // last Gaussian index [H][W] (-1 if none), contributor count [H][W], ambiguity flags
 // [H][W].  tile_mask (nullable) restricts the work to tiles with a nonzero entry; other
 // pixels are left untouched.  stats[0] += evaluated (pixel, list entry) steps.
+// bd (nullable): flip bounds of the subset (partC, partT [H][W]; cmax, dmax).
 int orc_render(const orc_params* p, const orc_camera* cam, const orc_opts* o,
                const uint8_t* tile_mask, double* C, double* T, double* D, int32_t* last,
-               int32_t* ncontrib, uint8_t* amb, int64_t* stats) {
-  return render_subset(p, cam, o, tile_mask, C, T, D, last, ncontrib, amb, stats, nullptr, 0, 0);
+               int32_t* ncontrib, uint8_t* amb, int64_t* stats, orc_bounds* bd) {
+  double cd[2] = {0.0, 0.0};
+  const int64_t HW = (int64_t)cam->width * cam->height;
+  std::vector<double> fl(bd ? (size_t)4 * HW : 0);
+  const int r = render_subset(p, cam, o, tile_mask, C, T, D, last, ncontrib, amb, stats, nullptr,
+                              0, 0, nullptr, bd ? fl.data() : nullptr, cd);
+  if (bd) {
+    if (bd->partC) std::memcpy(bd->partC, fl.data(), HW * sizeof(double));
+    if (bd->partT) std::memcpy(bd->partT, fl.data() + HW, HW * sizeof(double));
+    bd->cmax = std::max(cd[0], std::max(o->bg[0], std::max(o->bg[1], o->bg[2])));
+    bd->dmax = cd[1];
+  }
+  return r;
 }
 }  // extern "C"
 
 // pix_open (nullable, [H][W]): a pixel with a zero entry is left empty (C = 0, T = 1,
-// D = 0, no contributor) without being evaluated.
+// D = 0, no contributor) without being evaluated.  flips (nullable, [4][H][W]): the
+// pixel's flip bounds and contributor depth range (blend_pixel's flip[0..3]).  cdmax
+// (nullable, 2): raised to the largest colour channel and the largest depth of the
+// subset's visible Gaussians.  pix_alt (nullable, [H][W]): pixels whose saturation decision
+// is ambiguous; alt ([5][H][W]: C rgb, T, D) receives their other outcome (empty where the
+// pixel is rendered, rendered where it is left empty), in tiles outside tile_mask too.
 int render_subset(const orc_params* p, const orc_camera* cam, const orc_opts* o,
                   const uint8_t* tile_mask, double* C, double* T, double* D, int32_t* last,
                   int32_t* ncontrib, uint8_t* amb, int64_t* stats, const CrossFilter* f, int m,
-                  int64_t goff, const uint8_t* pix_open) {
+                  int64_t goff, const uint8_t* pix_open, double* flips, double* cdmax,
+                  const uint8_t* pix_alt, double* alt) {
   const int W = cam->width, H = cam->height, B = o->tile;
   Subset s = prepare(*p, *cam, B, (float)o->alpha_min, f, m, goff);
+  if (cdmax)
+    for (int64_t i = 0; i < p->n; ++i) {
+      if (!s.bins[i].visible) continue;
+      for (int ch = 0; ch < 3; ++ch) cdmax[0] = std::max(cdmax[0], s.pr[i].col[ch]);
+      cdmax[1] = std::max(cdmax[1], s.pr[i].depth);
+    }
   const int nt = s.tiles.tw * s.tiles.th;
   int64_t evaluated = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : evaluated)
   for (int t = 0; t < nt; ++t) {
-    if (tile_mask && !tile_mask[t]) continue;
     const int tx = t % s.tiles.tw, ty = t / s.tiles.tw;
+    const bool main_t = !tile_mask || tile_mask[t];
+    bool alt_t = false;
+    if (pix_alt)
+      for (int py = ty * B; py < std::min(H, (ty + 1) * B); ++py)
+        for (int px = tx * B; px < std::min(W, (tx + 1) * B); ++px)
+          alt_t = alt_t || pix_alt[(int64_t)py * W + px];
+    if (!main_t && !alt_t) continue;
     const int32_t* lst = s.tiles.list.data() + s.tiles.start[t];
     const int64_t cnt = s.tiles.start[t + 1] - s.tiles.start[t];
     for (int py = ty * B; py < std::min(H, (ty + 1) * B); ++py)
       for (int px = tx * B; px < std::min(W, (tx + 1) * B); ++px) {
         const int64_t pi = (int64_t)py * W + px;
+        const bool rendered = main_t && (!pix_open || pix_open[pi]);
+        if (pix_alt && pix_alt[pi]) {
+          double a3[3] = {0.0, 0.0, 0.0}, at = 1.0, ad = 0.0;
+          int32_t alg = -1, anc = 0;
+          int64_t aev = 0;
+          if (!rendered)
+            blend_pixel(px, py, lst, cnt, s.bins, s.pr, *o, a3, at, ad, alg, anc, aev, nullptr);
+          for (int ch = 0; ch < 3; ++ch) alt[(int64_t)ch * H * W + pi] = a3[ch];
+          alt[(int64_t)3 * H * W + pi] = at;
+          alt[(int64_t)4 * H * W + pi] = ad;
+        }
+        if (!main_t) continue;
         double c3[3] = {0.0, 0.0, 0.0}, tt = 1.0, dd = 0.0;
         int32_t lg = -1, nc = 0;
         int a = 0;
+        double fl[4] = {0.0, 0.0, INFINITY, -INFINITY};
         if (!pix_open || pix_open[pi])
           a = blend_pixel(px, py, lst, cnt, s.bins, s.pr, *o, c3, tt, dd, lg, nc, evaluated,
-                          nullptr);
+                          nullptr, fl);
+        if (flips)
+          for (int k = 0; k < 4; ++k) flips[(int64_t)k * H * W + pi] = fl[k];
         for (int ch = 0; ch < 3; ++ch) C[(int64_t)ch * H * W + pi] = c3[ch];
         T[pi] = tt; D[pi] = dd;
         if (last) last[pi] = lg;
@@ -830,10 +1122,12 @@ extern "C" {
 
 // Global composition of K partials [Eq. 5].  Partials planar: C[K][3][H][W],
 // T[K][H][W], D[K][H][W].  Outputs image [3][H][W], total transmittance [H][W], the
-// number of subsets composited [H][W] and ambiguity flags (OR-ed into amb).
+// number of subsets composited [H][W] and ambiguity flags (OR-ed into amb).  bimg, bT
+// (nullable, [H][W]): flip bounds of the image and transmittance for exactly given
+// partials (near-tied keys and the saturation cut; composite_bounds).
 int orc_composite(int32_t K, int32_t H, int32_t W, const double* Cp, const double* Tp,
                   const double* Dp, const orc_opts* o, double* out, double* Tout,
-                  int32_t* nused, uint8_t* amb) {
+                  int32_t* nused, uint8_t* amb, double* bimg, double* bT) {
   const int64_t HW = (int64_t)H * W;
 #pragma omp parallel for schedule(static)
   for (int64_t pi = 0; pi < HW; ++pi) {
@@ -855,6 +1149,22 @@ int orc_composite(int32_t K, int32_t H, int32_t W, const double* Cp, const doubl
     Tout[pi] = P;
     if (nused) nused[pi] = used;
     if (amb) amb[pi] |= (uint8_t)a;
+    if (bimg || bT) {
+      std::vector<double> Cm((size_t)3 * K), zero(K, 0.0);
+      double cmax = std::max(o->bg[0], std::max(o->bg[1], o->bg[2]));
+      for (int m = 0; m < K; ++m)
+        for (int ch = 0; ch < 3; ++ch) {
+          Cm[3 * m + ch] = Cp[((int64_t)m * 3 + ch) * HW + pi];
+          // a partial's colour is at most its occupancy times its largest colour; its
+          // normalised colour bounds what lies behind
+          if (Tm[m] < 1.0) cmax = std::max(cmax, Cm[3 * m + ch] / (1.0 - Tm[m]));
+        }
+      double bi, bt;
+      composite_bounds(K, Tm.data(), Dm.data(), Cm.data(), zero.data(), zero.data(), zero.data(),
+                       zero.data(), *o, cmax, 0.0, ord.data(), bi, bt);
+      if (bimg) bimg[pi] = bi;
+      if (bT) bT[pi] = bt;
+    }
   }
   return 0;
 }
@@ -863,20 +1173,93 @@ int orc_composite(int32_t K, int32_t H, int32_t W, const double* Cp, const doubl
 // Partial outputs (nullable) as in orc_composite.  sep (nullable): 1 where the pixel is
 // separable, i.e. its monolithic contributor list (all Gaussians, no termination) is a
 // concatenation of per-subset runs in composite order (where Eq. 5 equals Eq. 2).
+// bd (nullable): flip bounds of the image and of every partial (orc_bounds).
 int orc_render_view(const orc_params* p, const int64_t* offsets, int32_t K, const orc_camera* cam,
                     const orc_opts* o, const uint8_t* tile_mask, const int32_t* order,
                     const float* cells, double* out, double* Tout, double* Cp, double* Tp,
-                    double* Dp, uint8_t* amb, uint8_t* sep, uint8_t* skip_out, int64_t* stats) {
+                    double* Dp, uint8_t* amb, uint8_t* sep, uint8_t* skip_out, int64_t* stats,
+                    orc_bounds* bd) {
   const int64_t HW = (int64_t)cam->width * cam->height;
   std::vector<double> C, T, D;
   std::vector<uint8_t> a(HW, 0), skip;
   CrossFilter cf;
   if (cells) cf = make_filter(*p, offsets, K, *cam, *o, cells);
+  std::vector<double> flips[4], alt;
+  std::vector<uint8_t> sat_alt;
+  double cd[2] = {0.0, 0.0};
   render_partials(*p, offsets, K, *cam, *o, tile_mask, order, C, T, D, skip, a.data(), stats,
-                  cells ? &cf : nullptr);
+                  cells ? &cf : nullptr, nullptr, bd ? flips : nullptr, cd, &sat_alt, &alt);
   if (skip_out) std::memcpy(skip_out, skip.data(), skip.size());
   orc_composite(K, cam->height, cam->width, C.data(), T.data(), D.data(), o, out, Tout, nullptr,
-                a.data());
+                a.data(), nullptr, nullptr);
+  if (bd) {
+    const double cmax = std::max(cd[0], std::max(o->bg[0], std::max(o->bg[1], o->bg[2])));
+    bd->cmax = cmax;
+    bd->dmax = cd[1];
+    const bool has_alt = !sat_alt.empty();
+    // a partial whose saturation decision is ambiguous may end as its other outcome
+    std::vector<double> pC = flips[0], pT = flips[1];
+    if (has_alt)
+      for (int m = 0; m < K; ++m)
+        for (int64_t i = 0; i < HW; ++i) {
+          const size_t mi = (size_t)m * HW + i;
+          if (!sat_alt[mi]) continue;
+          double dc = std::fabs(alt[((size_t)m * 5 + 4) * HW + i] - D[mi]) / std::max(cd[1], 1e-300);
+          for (int ch = 0; ch < 3; ++ch)
+            dc = std::max(dc, std::fabs(alt[((size_t)m * 5 + ch) * HW + i] -
+                                        C[((size_t)m * 3 + ch) * HW + i]) / std::max(cmax, 1e-300));
+          pC[mi] = std::max(pC[mi], dc);
+          pT[mi] = std::max(pT[mi], std::fabs(alt[((size_t)m * 5 + 3) * HW + i] - T[mi]));
+        }
+    if (bd->partC) std::memcpy(bd->partC, pC.data(), pC.size() * sizeof(double));
+    if (bd->partT) std::memcpy(bd->partT, pT.data(), pT.size() * sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int64_t pi = 0; pi < HW; ++pi) {
+      if (tile_mask) {
+        const int B = o->tile, tw = (cam->width + B - 1) / B;
+        const int px = (int)(pi % cam->width), py = (int)(pi / cam->width);
+        if (!tile_mask[(py / B) * tw + px / B]) continue;
+      }
+      std::vector<double> Tm(K), Dm(K), Cm((size_t)3 * K), fC(K), fT(K), dlo(K), dhi(K);
+      std::vector<int> ord(K);
+      for (int m = 0; m < K; ++m) {
+        Tm[m] = T[(size_t)m * HW + pi];
+        Dm[m] = D[(size_t)m * HW + pi];
+        for (int ch = 0; ch < 3; ++ch) Cm[3 * m + ch] = C[((size_t)m * 3 + ch) * HW + pi];
+        fC[m] = flips[0][(size_t)m * HW + pi];
+        fT[m] = flips[1][(size_t)m * HW + pi];
+        dlo[m] = flips[2][(size_t)m * HW + pi];
+        dhi[m] = flips[3][(size_t)m * HW + pi];
+      }
+      composite_order(K, Tm.data(), Dm.data(), *o, ord.data());
+      double bi, bt;
+      composite_bounds(K, Tm.data(), Dm.data(), Cm.data(), fC.data(), fT.data(), dlo.data(),
+                       dhi.data(), *o, cmax, cd[1], ord.data(), bi, bt);
+      // each ambiguous saturation decision: the composite with that partial's other
+      // outcome, exactly
+      if (has_alt) {
+        double base3[3], baseT;
+        composite_one(K, Tm.data(), Cm.data(), ord.data(), *o, base3, baseT);
+        for (int m = 0; m < K; ++m) {
+          if (!sat_alt[(size_t)m * HW + pi]) continue;
+          std::vector<double> T2 = Tm, D2 = Dm, C2 = Cm;
+          for (int ch = 0; ch < 3; ++ch) C2[3 * m + ch] = alt[((size_t)m * 5 + ch) * HW + pi];
+          T2[m] = alt[((size_t)m * 5 + 3) * HW + pi];
+          D2[m] = alt[((size_t)m * 5 + 4) * HW + pi];
+          std::vector<int> ord2(K);
+          composite_order(K, T2.data(), D2.data(), *o, ord2.data());
+          double alt3[3], altT;
+          composite_one(K, T2.data(), C2.data(), ord2.data(), *o, alt3, altT);
+          double d = 0.0;
+          for (int ch = 0; ch < 3; ++ch) d = std::max(d, std::fabs(alt3[ch] - base3[ch]));
+          bi += d;
+          bt += std::fabs(altT - baseT);
+        }
+      }
+      if (bd->image) bd->image[pi] = bi;
+      if (bd->T) bd->T[pi] = bt;
+    }
+  }
   if (Cp) std::memcpy(Cp, C.data(), C.size() * sizeof(double));
   if (Tp) std::memcpy(Tp, T.data(), T.size() * sizeof(double));
   if (Dp) std::memcpy(Dp, D.data(), D.size() * sizeof(double));

@@ -1,5 +1,6 @@
 """Differentiation wrapper: train.Renderer as a torch.autograd.Function over the batch API.
-Its forward is the oracle's image (pixels within 1e-4 outside the ambiguity band), the
+Its forward is the oracle's image (pixels within 1e-4 outside the ambiguity band, within
+1e-4 plus the oracle's flip bound inside it), the
 .grad that loss.backward() leaves on the parameter tensors is the oracle's gradient of the
 same loss (1e-3 relative L2 per group), a second backward accumulates as torch does, and
 the total transmittance output carries no gradient."""
@@ -25,7 +26,7 @@ def ctx():
 
 
 def test_renderer_forward_and_backward_match_the_oracle(ctx):
-    from gpu_util import GRAD_TOL, PIXEL_TOL, rel_l2, to_device
+    from gpu_util import GRAD_TOL, check_band, rel_l2, to_device
     from paper_2606_18588_gb300.train import Renderer
     sc, off, _, cams = I.cluster_case(20_000, 31, 4, 2, [(120, 88), (72, 56)])
     params = {k: v.requires_grad_() for k, v in to_device(sc).items()}
@@ -37,11 +38,10 @@ def test_renderer_forward_and_backward_match_the_oracle(ctx):
     w = torch.zeros_like(rgb)
     g_ref = None
     for v, (cam, img) in enumerate(zip(cams, r.views(rgb.detach()))):
-        ref = O.render_view(sc, off, cam, O.opts())
+        ref = O.render_view(sc, off, cam, O.opts(), bounds=True)
         ok = ref["amb"] == 0
-        assert ok.mean() > 0.99
-        err = np.abs(img.cpu().numpy() - ref["image"]).max(axis=0)
-        assert err[ok].max() <= PIXEL_TOL, (v, float(err[ok].max()))
+        check_band(img.cpu().numpy(), ref["image"], ref["amb"], ref["flip"]["image"],
+                   label=f"Renderer view {v}")
         wv = (rng.standard_normal((3, cam.height, cam.width)) * ok[None]).astype(np.float32)
         r.views(w)[v].copy_(torch.from_numpy(wv))
         gv = O.backward_view(sc, off, cam, wv.astype(np.float64), None, O.opts())

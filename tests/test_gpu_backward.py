@@ -23,7 +23,7 @@ def ctx():
 
 def _check_grads(ctx, sc, off, cam, use_dT, seed, tol=None):
     from paper_2606_18588_gb300 import splx as S
-    from gpu_util import GRAD_TOL, backward_view, rel_l2, render_view, to_device
+    from gpu_util import GRAD_TOL, backward_view, band_share, rel_l2, render_view, to_device
     tol = tol or GRAD_TOL
     dev = to_device(sc)
     o = S.opts()
@@ -31,6 +31,7 @@ def _check_grads(ctx, sc, off, cam, use_dT, seed, tol=None):
     ref = O.render_view(sc, off, cam, O.opts())
     rng = np.random.default_rng(seed)
     H, W = cam.height, cam.width
+    band_share(ref["amb"], label="backward view")
     ok = (ref["amb"] == 0).astype(np.float64)
     dLdC = rng.standard_normal((3, H, W)) * ok[None]
     dLdT = rng.standard_normal((H, W)) * ok if use_dT else None

@@ -4,7 +4,8 @@ memory and run in the launch configuration the benchmark times (tile 16, saturat
 skipping and spatial visibility on).  Parity on seeded samples of tiles of two of the
 views: the oracle sees the Gaussians that a conservative host bound lets reach a sampled
 tile, in their global order (on the CPU the same oracle gives the same pixels for that
-subset as for the whole scene), pixels within 1e-4 outside the ambiguity band, gradients
+subset as for the whole scene), pixels within 1e-4 outside the ambiguity band and within
+1e-4 plus the oracle's flip bound inside it, gradients
 of a loss on the sampled tiles within 1e-3 relative L2, and exactly zero gradient for every
 Gaussian the bound leaves out."""
 import numpy as np
@@ -28,7 +29,7 @@ def test_training_step_120m_k32_sampled_tiles():
     from paper_2606_18588_gb300 import splx as S
     from paper_2606_18588_gb300.train import _subset_structs, city_to_device
     from paper_2606_18588_gb300.visibility import orders_for_views
-    from gpu_util import GRAD_TOL, PIXEL_TOL, params_struct, rel_l2
+    from gpu_util import GRAD_TOL, check_band, params_struct, rel_l2
 
     lay = I.city_layout(N, SEED, K)
     pool = I.aerial_cameras(SEED)
@@ -66,12 +67,12 @@ def test_training_step_120m_k32_sampled_tiles():
     dls = {}
     for v, (mask, pix) in sample.items():
         ov = list(order[v])
-        ref = O.render_view(sub, sub_off, cams[v], O.opts(), tile_mask=mask, order=ov)
+        ref = O.render_view(sub, sub_off, cams[v], O.opts(), tile_mask=mask, order=ov,
+                            bounds=True)
         ok = pix & (ref["amb"] == 0)
-        assert ok.sum() > 0.98 * pix.sum()
         got = b.views(rgb)[v].cpu().numpy()
-        err = np.abs(got - ref["image"]).max(axis=0)
-        assert err[ok].max() <= PIXEL_TOL, (v, float(err[ok].max()))
+        check_band(got, ref["image"], ref["amb"], ref["flip"]["image"], where=pix, budget=0.02,
+                   label=f"city view {v} image")
         assert ref["T"][pix].min() < 0.5  # the sampled tiles see geometry
         d = rng.standard_normal((3, cams[v].height, cams[v].width)) * ok[None]
         dL[b.rgb_off[v]:b.rgb_off[v + 1]] = d.reshape(-1)

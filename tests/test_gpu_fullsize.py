@@ -1,8 +1,9 @@
 """Parity at the full sizes of the workloads, on seeded samples of tiles the oracle renders
 one by one: the 1M-Gaussian K = 4 1920x1080 forward + backward, and the batched
 10M-Gaussian K = 8 16-view step in the launch configuration the benchmark times (tile 16,
-saturation skipping on).  Pixels within 1e-4 outside the oracle's ambiguity band, and
-gradients of a loss restricted to the sampled tiles within 1e-3 relative L2 per group."""
+saturation skipping on).  Pixels within 1e-4 outside the oracle's ambiguity band and within
+1e-4 plus the oracle's flip bound inside it, and gradients of a loss restricted to the
+sampled tiles (zero on the band) within 1e-3 relative L2 per group."""
 import numpy as np
 import pytest
 
@@ -14,6 +15,10 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+# Denser scenes evaluate more alphas per pixel near the threshold (about 200 per pixel on the
+# 10M-Gaussian views), so their ambiguity band is wider; every band pixel is still checked
+# against its flip bound.
+FULLSIZE_BAND_BUDGET = 0.02
 
 
 @pytest.fixture(scope="module")
@@ -36,7 +41,7 @@ def _tile_sample(cam, n, seed, B=16):
 
 def _parity(ctx, sc, off, cams, sample_views, n_tiles, seed, order=None):
     from paper_2606_18588_gb300 import splx as S
-    from gpu_util import GRAD_TOL, PIXEL_TOL, params_struct, rel_l2, subset_struct, to_device
+    from gpu_util import GRAD_TOL, check_band, params_struct, rel_l2, subset_struct, to_device
     from gpu_util import zeros_like_params
     dev = to_device(sc)
     K = len(off) - 1
@@ -56,12 +61,11 @@ def _parity(ctx, sc, off, cams, sample_views, n_tiles, seed, order=None):
         c = cams[v]
         mask, pix = _tile_sample(c, n_tiles, seed + v)
         ov = None if order is None else list(order[v])
-        ref = O.render_view(sc, off, c, O.opts(), tile_mask=mask, order=ov)
+        ref = O.render_view(sc, off, c, O.opts(), tile_mask=mask, order=ov, bounds=True)
         ok = pix & (ref["amb"] == 0)
-        assert ok.sum() > 0.98 * pix.sum()
         got = b.views(rgb)[v].cpu().numpy()
-        err = np.abs(got - ref["image"]).max(axis=0)
-        assert err[ok].max() <= PIXEL_TOL, (v, float(err[ok].max()))
+        check_band(got, ref["image"], ref["amb"], ref["flip"]["image"], where=pix,
+                   budget=FULLSIZE_BAND_BUDGET, label=f"view {v} image")
         d = rng.standard_normal((3, c.height, c.width)) * ok[None]
         dls[v] = (d, mask, ov)
         dL[b.rgb_off[v]:b.rgb_off[v + 1]] = d.reshape(-1)

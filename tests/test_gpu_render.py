@@ -1,7 +1,8 @@
 """GPU parity of the forward path (through the C ABI) against the FP64 oracle.
 
 Binning (cull, rectangle, depth key, per-tile sorted lists) must match bit for bit;
-pixels within 1e-4 max-abs outside the oracle's ambiguity guard band."""
+pixels within 1e-4 max-abs, and pixels in the oracle's ambiguity band within 1e-4 plus their
+flip bound."""
 import numpy as np
 import pytest
 
@@ -127,19 +128,10 @@ def test_segment_sort_at_chunk_boundaries(ctx, n):
     st.close()
 
 
-def _compare_pixels(gpu, orc, amb, tol=1e-4):
-    ok = amb == 0
-    assert ok.mean() > 0.99
-    err = np.abs(gpu - orc)
-    if err.ndim == 3:
-        err = err.max(axis=0)
-    return float(err[ok].max()) if ok.any() else 0.0
-
-
 @pytest.mark.parametrize("name", list(CASES))
 def test_partial_render_matches_oracle(ctx, name):
     from paper_2606_18588_gb300 import splx as S
-    from gpu_util import PIXEL_TOL, subset_struct, to_device
+    from gpu_util import PIXEL_TOL, check_band, subset_struct, to_device
     sc, cam = CASES[name]
     dev = to_device(sc)
     o = S.opts()
@@ -148,13 +140,13 @@ def test_partial_render_matches_oracle(ctx, name):
     ranges, keys, _ = st.export()
     vals = (keys & np.uint64(0xFFFFFFFF)).astype(np.uint32)
     torch.cuda.synchronize()
-    ref = O.render(sc, cam, O.opts())
-    amb = ref["amb"]
-    assert _compare_pixels(p["rgb"].cpu().numpy(), ref["C"], amb) <= PIXEL_TOL
-    assert _compare_pixels(p["T"].cpu().numpy(), ref["T"], amb) <= PIXEL_TOL
-    D = p["depth"].cpu().numpy()
+    ref = O.render(sc, cam, O.opts(), bounds=True)
+    amb, fb = ref["amb"], ref["flip"]
+    check_band(p["rgb"].cpu().numpy(), ref["C"], amb, fb["C"], label=f"{name} C")
+    check_band(p["T"].cpu().numpy(), ref["T"], amb, fb["T"], label=f"{name} T")
+    check_band(p["depth"].cpu().numpy(), ref["D"], amb, fb["D"],
+               tol=PIXEL_TOL * (1.0 + np.abs(ref["D"])), label=f"{name} D")
     ok = amb == 0
-    assert np.all(np.abs(D - ref["D"])[ok] <= PIXEL_TOL * (1.0 + np.abs(ref["D"][ok])))
     # last blended Gaussian: GPU list position -> Gaussian index, exact off the guard band
     last = p["last"].cpu().numpy()
     H, W = cam.height, cam.width
@@ -186,25 +178,30 @@ def test_forward_bit_identical_across_tile_sizes(ctx):
 
 def test_composite_matches_oracle_and_monolithic(ctx):
     from paper_2606_18588_gb300 import splx as S
-    from gpu_util import PIXEL_TOL, render_view, to_device
+    from gpu_util import PIXEL_TOL, check_band, render_view, to_device
     sc, off, _, cams = I.cluster_case(40_000, 5, 4, 1, [(320, 200)])
     cam = cams[0]
     dev = to_device(sc)
     o = S.opts()
     img, T, parts, states = render_view(ctx, dev, off, cam, o, sc.sh_degree)
-    ref = O.render_view(sc, off, cam, O.opts(), separable=True)
+    ref = O.render_view(sc, off, cam, O.opts(), separable=True, bounds=True)
     ok = ref["amb"] == 0
-    assert ok.mean() > 0.99
-    err = np.abs(img.cpu().numpy() - ref["image"]).max(axis=0)
-    assert err[ok].max() <= PIXEL_TOL
-    assert np.abs(T.cpu().numpy() - ref["T"])[ok].max() <= PIXEL_TOL
-    # composition alone: the oracle's Eq. 5 on the GPU's own partials
+    fb = ref["flip"]
+    check_band(img.cpu().numpy(), ref["image"], ref["amb"], fb["image"], label="composite image")
+    check_band(T.cpu().numpy(), ref["T"], ref["amb"], fb["T"], label="composite T")
+    for k, p in enumerate(parts):
+        check_band(p["rgb"].cpu().numpy(), ref["Cp"][k], ref["amb"], fb["partC"][k],
+                   label=f"partial {k} C")
+        check_band(p["T"].cpu().numpy(), ref["Tp"][k], ref["amb"], fb["partT"][k],
+                   label=f"partial {k} T")
+    # composition alone: the oracle's Eq. 5 on the GPU's own partials (its band: near-tied
+    # keys and the saturation cut, each with its exact effect as the bound)
     Cp = np.stack([p["rgb"].cpu().numpy() for p in parts]).astype(np.float64)
     Tp = np.stack([p["T"].cpu().numpy() for p in parts]).astype(np.float64)
     Dp = np.stack([p["depth"].cpu().numpy() for p in parts]).astype(np.float64)
-    rc = O.composite(Cp, Tp, Dp, O.opts())
-    okc = rc["amb"] == 0
-    assert np.abs(img.cpu().numpy() - rc["image"]).max(axis=0)[okc].max() <= 1e-5
+    rc = O.composite(Cp, Tp, Dp, O.opts(), bounds=True)
+    check_band(img.cpu().numpy(), rc["image"], rc["amb"], rc["flip"]["image"], tol=1e-5,
+               label="Eq. 5 on the GPU partials")
     for s in states:
         s.close()
     # Eq. 5 == Eq. 2 on separable pixels: GPU composite vs GPU monolithic render, exact up
@@ -238,15 +235,17 @@ def test_composite_matches_oracle_and_monolithic(ctx):
 @pytest.mark.parametrize("W,H", [(1, 1), (17, 3), (5, 40)])
 def test_tiny_and_ragged_images(ctx, W, H):
     from paper_2606_18588_gb300 import splx as S
-    from gpu_util import PIXEL_TOL, subset_struct, to_device
+    from gpu_util import check_band, subset_struct, to_device
     sc = I.uniform_scene(500, 9, 0, log_scale_mu=-2.0)
     cam = I.pinhole(W, H, 60.0, (0, 0, -3), (0, 0, 0))
     dev = to_device(sc)
     p = S.new_partial(H, W)
     S.render_partial(ctx, subset_struct(dev, 0, sc.n, 0), cam, S.opts(tile=8), p, keep_state=False)
     torch.cuda.synchronize()
-    ref = O.render(sc, cam, O.opts(tile=8))
-    assert _compare_pixels(p["rgb"].cpu().numpy(), ref["C"], ref["amb"]) <= PIXEL_TOL
+    ref = O.render(sc, cam, O.opts(tile=8), bounds=True)
+    # a handful of pixels: a single band pixel is allowed, checked against its bound
+    check_band(p["rgb"].cpu().numpy(), ref["C"], ref["amb"], ref["flip"]["C"],
+               budget=max(0.01, 1.0 / (W * H)), label=f"{W}x{H} C")
 
 
 def test_empty_and_fully_culled_subsets(ctx):

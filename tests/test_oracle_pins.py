@@ -874,3 +874,64 @@ def test_cross_boundary_filter_is_the_identity_without_crossing_gaussians():
     gb = O.backward_view(sc, off, cam, dC, None, o)
     # the oracle's threads add per-Gaussian sums in any order: equal up to rounding
     assert all(np.allclose(x, y, rtol=1e-12, atol=1e-15) for x, y in zip(ga, gb))
+
+
+# --------------------------------------------------------------------------- flip bounds
+@pytest.mark.parametrize("skipping", [False, True])
+def test_flip_bounds_cover_every_flipped_decision(skipping):
+    """The oracle's flip bound of an ambiguous pixel covers the result of taking its flagged
+    decisions the other way.  Moving alpha_min, eps_T and eps_comp by 0.9 of their relative
+    margins flips exactly decisions that the oracle flags (and whatever later stops those
+    flips move); every pixel must then stay within its bound of the unmoved render, and an
+    unflagged pixel must not change at all."""
+    sc = I.cluster_scene(20_000, 2, 3)
+    cam = I.orbit_cameras(1, 3, [(333, 197)])[0]
+    perm, off, boxes = I.kd_partition(sc.means, 4)
+    sc = sc.take(perm)
+    order = O.cell_order(boxes, cam.eye) if skipping else None
+    base_o = O.opts()
+    base = O.render_view(sc, off, cam, base_o, order=order, bounds=True)
+    amb = base["amb"] != 0
+    assert 0 < amb.mean() < 0.01
+    fb = base["flip"]
+    moved_any = False
+    for sa, st, sc_ in [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+                        (1, -1, 1), (-1, 1, -1)]:
+        o = O.opts(alpha_min=base_o.alpha_min * (1 + 0.9 * sa * base_o.amb_alpha),
+                   eps_T=base_o.eps_T * (1 + 0.9 * st * base_o.amb_T),
+                   eps_comp=base_o.eps_comp * (1 + 0.9 * sc_ * base_o.amb_T))
+        r = O.render_view(sc, off, cam, o, order=order)
+        d_img = np.abs(r["image"] - base["image"]).max(axis=0)
+        d_T = np.abs(r["T"] - base["T"])
+        assert d_img[~amb].max(initial=0.0) == 0.0 and d_T[~amb].max(initial=0.0) == 0.0
+        assert (d_img <= fb["image"] * (1 + 1e-9) + 1e-15).all()
+        assert (d_T <= fb["T"] * (1 + 1e-9) + 1e-15).all()
+        for m in range(len(off) - 1):
+            dC = np.abs(r["Cp"][m] - base["Cp"][m]).max(axis=0)
+            assert (dC <= fb["partC"][m] * (1 + 1e-9) + 1e-15).all()
+            assert (np.abs(r["Tp"][m] - base["Tp"][m]) <= fb["partT"][m] * (1 + 1e-9) + 1e-15).all()
+            assert (np.abs(r["Dp"][m] - base["Dp"][m]) <= fb["partD"][m] * (1 + 1e-9) + 1e-15).all()
+        moved_any |= bool(d_img.max() > 0)
+    assert moved_any
+
+
+def test_composite_flip_bound_covers_a_swapped_near_tie():
+    """Two partials whose normalised depths differ by less than the key margin: the oracle
+    flags the pixel, and its bound covers compositing them the other way round (Eq. 5 with
+    the pair's order exchanged)."""
+    rng = np.random.default_rng(8)
+    K, H, W = 3, 4, 5
+    Tp = rng.uniform(0.2, 0.9, (K, H, W))
+    Cp = rng.uniform(0, 1, (K, 3, H, W)) * (1 - Tp)[:, None]
+    z = rng.uniform(1, 10, (K, H, W))
+    z[1] = z[0] * (1 + 3e-6)            # near-tied with subset 0 everywhere
+    Dp = z * (1 - Tp)
+    o = O.opts(eps_comp=0.0)
+    base = O.composite(Cp, Tp, Dp, o, bounds=True)
+    assert (base["amb"] != 0).all()
+    z2 = z.copy()
+    z2[1] = z[0] * (1 - 3e-6)           # the pair the other way round
+    swapped = O.composite(Cp, Tp, z2 * (1 - Tp), o)
+    d = np.abs(swapped["image"] - base["image"]).max(axis=0)
+    assert d.max() > 1e-3
+    assert (d <= base["flip"]["image"] * (1 + 1e-9) + 1e-15).all()
