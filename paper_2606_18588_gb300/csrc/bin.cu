@@ -441,13 +441,11 @@ void launch_seg_sort(const BatchDev& b, int max_rounds, cudaStream_t s) {
   if (b.n_tiles == 0) return;
   const int64_t items = b.order ? b.n_tiles / b.K : b.n_tiles;
   k_seg_sort_small<<<(unsigned)items, kSortThreads, 0, s>>>(b);
-  const unsigned grid = 152 * 4;
-  // 72 KB of dynamic shared memory: opted in once per process (a refused opt-in shows as
+  const unsigned grid = (unsigned)device_sm_count() * 4;
+  // 72 KB of dynamic shared memory: opted in once per device (a refused opt-in shows as
   // the launch's error, which the callers check)
   constexpr int kChunkSmem = 2 * kBigPadded * (int)sizeof(uint64_t);
-  static const cudaError_t smem_opt_in =
-      cudaFuncSetAttribute(k_chunk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kChunkSmem);
-  (void)smem_opt_in;
+  (void)opt_in_smem((const void*)k_chunk_sort, kChunkSmem, 0);
   k_chunk_sort<<<grid, kBigThreads, kChunkSmem, s>>>(b);
   for (int r = 0; r < max_rounds; ++r) k_merge_round<<<grid, kBigThreads, 0, s>>>(b, r);
   k_merge_fixup<<<grid, kBigThreads, 0, s>>>(b);

@@ -189,6 +189,13 @@ void launch_step_increment(int64_t* step_dev, cudaStream_t s);
 void launch_loss_l1(const float* img, const float* target, int64_t n, float* loss,
                     float* dL, cudaStream_t s);
 
+// Number of SMs of the current device (looked up once per device), for grids sized to the
+// chip; 152 if the query fails.
+int device_sm_count();
+// Opts kernel `fn` into `bytes` of dynamic shared memory on the current device, once per
+// device (function attributes belong to a device's context); returns the opt-in's result.
+cudaError_t opt_in_smem(const void* fn, int bytes, int slot);
+
 // Counts kernel launches issued by the library (for reporting).
 extern thread_local int64_t* g_launch_counter;
 inline void count_launch(int n = 1) {

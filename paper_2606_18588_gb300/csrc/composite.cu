@@ -181,7 +181,8 @@ void launch_loss_l1(const float* img, const float* target, int64_t n, float* los
   cudaMemsetAsync(loss, 0, sizeof(float), s);
   if (n <= 0) return;
   int64_t blocks = (n + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  const int64_t cap = (int64_t)device_sm_count() * 16;
+  if (blocks > cap) blocks = cap;
   k_loss_l1<<<(unsigned)blocks, 256, 0, s>>>(img, target, n, loss, dL);
   count_launch();
 }

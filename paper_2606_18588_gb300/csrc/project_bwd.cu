@@ -407,7 +407,8 @@ void launch_adam(float* p, float* g, float* m, float* v, int64_t n, int64_t sh_s
   if (n <= 0) return;
   int64_t blocks = ((n >> 2) + 255) / 256;
   if (blocks < 1) blocks = 1;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  const int64_t cap = (int64_t)device_sm_count() * 32;
+  if (blocks > cap) blocks = cap;
   k_adam<<<(unsigned)blocks, 256, 0, s>>>(p, g, m, v, n, sh_stride, lr, lr_rest, b1, b2, eps, step,
                                           step_dev, zero_grad, vec4);
   count_launch();
