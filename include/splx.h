@@ -288,6 +288,10 @@ int splx_batch_set_order(splx_batch_t b, const int32_t* order);
  * the batch's tile side (host outputs). */
 int splx_batch_max_ctas_per_sm(splx_batch_t b, int32_t* fwd, int32_t* bwd);
 int splx_batch_kernel_times(splx_batch_t b, float* ms_out);
+/* The same 9 durations for the replay of graph g that took ring slot `slot` of
+ * splx_graph_set_timing_ring (waits for that replay's final event only).  SPLX_ERR_INVALID
+ * for a slot outside the ring. */
+int splx_batch_kernel_times_slot(splx_batch_t b, splx_graph_t g, int32_t slot, float* ms_out);
 /* Work counters (synchronises; host array of 9): out[0] = (Gaussian, tile) pairs of the
  * last run; then, from the last EAGER run (replays of a captured graph do not count):
  * forward rasteriser out[1] = (thread, list entry) pairs examined, out[2] = (pixel,
@@ -345,6 +349,14 @@ int splx_server_destroy(splx_server_t s);
 int splx_graph_begin(splx_ctx_t ctx, splx_stream_t stream);
 int splx_graph_end(splx_ctx_t ctx, splx_stream_t stream, splx_graph_t* out);
 int splx_graph_launch(splx_graph_t g, splx_stream_t stream);
+/* Timing ring (measurement only; the paper has no counterpart).  With slots > 0, launch
+ * number i of g records the graph's event nodes (the batch timing events of
+ * splx_batch_set_timing captured into it) into ring slot i mod slots instead of the
+ * captured events, so the per-kernel times of every replay of a back-to-back run can be read
+ * afterwards with splx_batch_kernel_times_slot, with no host wait between replays.  Creates
+ * slots x (event nodes) events, owned by g (0 removes the ring; 0..4096, else
+ * SPLX_ERR_INVALID).  The next launch takes slot 0. */
+int splx_graph_set_timing_ring(splx_graph_t g, int32_t slots);
 int splx_graph_destroy(splx_graph_t g);
 
 /* ---- allocation-free local render ----------------------------------------------- */

@@ -18,6 +18,42 @@
 
 namespace splx {
 thread_local int64_t* g_launch_counter = nullptr;
+
+namespace {
+constexpr int kMaxDev = 64;
+constexpr int kSmemSlots = 4;
+std::mutex g_dev_mu;
+int g_sm_count[kMaxDev] = {};
+bool g_smem_done[kMaxDev][kSmemSlots] = {};
+cudaError_t g_smem_result[kMaxDev][kSmemSlots] = {};
+int current_device() {
+  int d = 0;
+  return cudaGetDevice(&d) == cudaSuccess && d >= 0 && d < kMaxDev ? d : 0;
+}
+}  // namespace
+
+int device_sm_count() {
+  const int d = current_device();
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (!g_sm_count[d]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || n <= 0)
+      n = 152;
+    g_sm_count[d] = n;
+  }
+  return g_sm_count[d];
+}
+
+cudaError_t opt_in_smem(const void* fn, int bytes, int slot) {
+  const int d = current_device();
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (!g_smem_done[d][slot]) {
+    g_smem_result[d][slot] =
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    g_smem_done[d][slot] = true;
+  }
+  return g_smem_result[d][slot];
+}
 }
 
 using namespace splx;
@@ -434,6 +470,20 @@ struct splx_batch_s {
 struct splx_graph_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // timing ring: the graph's event-record nodes, the events they captured, and per ring
+  // slot the events they record instead on the launch that takes that slot
+  std::vector<cudaGraphNode_t> ev_nodes;
+  std::vector<cudaEvent_t> ev_orig;
+  std::vector<cudaEvent_t> ring;  // [slots][ev_nodes.size()]
+  int slots = 0, next = 0;
+
+  // The event that stands for `e` in ring slot `slot` (e itself without a ring).
+  cudaEvent_t in_slot(cudaEvent_t e, int slot) const {
+    if (slots <= 0 || slot < 0 || slot >= slots) return e;
+    for (size_t k = 0; k < ev_orig.size(); ++k)
+      if (ev_orig[k] == e) return ring[(size_t)slot * ev_orig.size() + k];
+    return e;
+  }
 };
 
 extern "C" {
@@ -1067,17 +1117,16 @@ int splx_batch_max_ctas_per_sm(splx_batch_t bt, int32_t* fwd, int32_t* bwd) {
   return SPLX_OK;
 }
 
-int splx_batch_kernel_times(splx_batch_t bt, float* ms_out) {
-  if (!bt || !ms_out) return SPLX_ERR_INVALID;
-  Plan& P = bt->plan;
-  if (!P.timing) return SPLX_ERR_STATE;
-  CtxScope scope(P.ctx);
-  CK(cudaEventSynchronize(P.ev[10]));
+// Per-kernel times from the batch's timing events, each mapped through the graph's ring
+// slot (no graph: the events themselves).
+static int kernel_times_of(const Plan& P, const splx_graph_s* g, int slot, float* ms_out) {
+  auto E = [&](cudaEvent_t e) { return g ? g->in_slot(e, slot) : e; };
+  CK(cudaEventSynchronize(E(P.ev[10])));
   const int pairs[9][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {5, 6},
                            {7, 8}, {8, 9}, {9, 10}};
   for (int i = 0; i < 9; ++i) {
     float ms = 0.0f;
-    CK(cudaEventElapsedTime(&ms, P.ev[pairs[i][0]], P.ev[pairs[i][1]]));
+    CK(cudaEventElapsedTime(&ms, E(P.ev[pairs[i][0]]), E(P.ev[pairs[i][1]])));
     ms_out[i] = ms;
   }
   if (P.order_d && (int)P.wev.size() == 2 * P.K + 1) {
@@ -1085,8 +1134,8 @@ int splx_batch_kernel_times(splx_batch_t bt, float* ms_out) {
     float sort = 0.0f, ras = 0.0f;
     for (int r = 0; r < P.K; ++r) {
       float a = 0.0f, c = 0.0f;
-      CK(cudaEventElapsedTime(&a, P.wev[2 * r], P.wev[2 * r + 1]));
-      CK(cudaEventElapsedTime(&c, P.wev[2 * r + 1], P.wev[2 * r + 2]));
+      CK(cudaEventElapsedTime(&a, E(P.wev[2 * r]), E(P.wev[2 * r + 1])));
+      CK(cudaEventElapsedTime(&c, E(P.wev[2 * r + 1]), E(P.wev[2 * r + 2])));
       sort += a;
       ras += c;
     }
@@ -1094,6 +1143,22 @@ int splx_batch_kernel_times(splx_batch_t bt, float* ms_out) {
     ms_out[4] = ras;
   }
   return SPLX_OK;
+}
+
+int splx_batch_kernel_times(splx_batch_t bt, float* ms_out) {
+  if (!bt || !ms_out) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  if (!P.timing) return SPLX_ERR_STATE;
+  CtxScope scope(P.ctx);
+  return kernel_times_of(P, nullptr, -1, ms_out);
+}
+
+int splx_batch_kernel_times_slot(splx_batch_t bt, splx_graph_t g, int32_t slot, float* ms_out) {
+  if (!bt || !g || !ms_out || slot < 0 || slot >= g->slots) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  if (!P.timing) return SPLX_ERR_STATE;
+  CtxScope scope(P.ctx);
+  return kernel_times_of(P, g, slot, ms_out);
 }
 
 int splx_batch_counters(splx_batch_t bt, int64_t* out, splx_stream_t stream) {
@@ -1532,12 +1597,49 @@ int splx_graph_end(splx_ctx_t ctx, splx_stream_t stream, splx_graph_t* out) {
 
 int splx_graph_launch(splx_graph_t g, splx_stream_t stream) {
   if (!g) return SPLX_ERR_INVALID;
+  if (g->slots > 0) {
+    // this launch records its timing events into the next ring slot
+    const int slot = g->next;
+    g->next = (g->next + 1) % g->slots;
+    const size_t n = g->ev_nodes.size();
+    for (size_t k = 0; k < n; ++k)
+      CK(cudaGraphExecEventRecordNodeSetEvent(g->exec, g->ev_nodes[k], g->ring[(size_t)slot * n + k]));
+  }
   CK(cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)));
+  return SPLX_OK;
+}
+
+int splx_graph_set_timing_ring(splx_graph_t g, int32_t slots) {
+  if (!g || slots < 0 || slots > 4096) return SPLX_ERR_INVALID;
+  for (cudaEvent_t e : g->ring) cudaEventDestroy(e);
+  g->ring.clear();
+  g->ev_nodes.clear();
+  g->ev_orig.clear();
+  g->slots = 0;
+  g->next = 0;
+  if (slots == 0) return SPLX_OK;
+  size_t n = 0;
+  CK(cudaGraphGetNodes(g->graph, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n) CK(cudaGraphGetNodes(g->graph, nodes.data(), &n));
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(nd, &t));
+    if (t != cudaGraphNodeTypeEventRecord) continue;
+    cudaEvent_t e = nullptr;
+    CK(cudaGraphEventRecordNodeGetEvent(nd, &e));
+    g->ev_nodes.push_back(nd);
+    g->ev_orig.push_back(e);
+  }
+  g->ring.assign((size_t)slots * g->ev_nodes.size(), nullptr);
+  for (auto& e : g->ring) CK(cudaEventCreate(&e));
+  g->slots = slots;
   return SPLX_OK;
 }
 
 int splx_graph_destroy(splx_graph_t g) {
   if (!g) return SPLX_ERR_INVALID;
+  for (cudaEvent_t e : g->ring) cudaEventDestroy(e);
   cudaGraphExecDestroy(g->exec);
   cudaGraphDestroy(g->graph);
   delete g;

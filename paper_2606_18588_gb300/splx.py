@@ -107,6 +107,8 @@ _sigs = {
     "splx_graph_begin": (C.c_int, [_P, _P]),
     "splx_graph_end": (C.c_int, [_P, _P, C.POINTER(_P)]),
     "splx_graph_launch": (C.c_int, [_P, _P]),
+    "splx_graph_set_timing_ring": (C.c_int, [_P, C.c_int32]),
+    "splx_batch_kernel_times_slot": (C.c_int, [_P, _P, C.c_int32, _P]),
     "splx_graph_destroy": (C.c_int, [_P]),
     "splx_render_partial_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "splx_device_status": (C.c_int, [_P, _P]),
@@ -455,9 +457,14 @@ class Batch:
     def set_timing(self, enable=True):
         _check(_lib.splx_batch_set_timing(self.h, int(bool(enable))), "splx_batch_set_timing")
 
-    def kernel_times(self) -> dict:
+    def kernel_times(self, graph=None, slot=None) -> dict:
+        """Per-kernel ms of the last run, or of the replay of `graph` that took ring `slot`."""
         arr = (C.c_float * len(self.KERNELS))()
-        _check(_lib.splx_batch_kernel_times(self.h, arr), "splx_batch_kernel_times")
+        if graph is None:
+            _check(_lib.splx_batch_kernel_times(self.h, arr), "splx_batch_kernel_times")
+        else:
+            _check(_lib.splx_batch_kernel_times_slot(self.h, graph.h, int(slot), arr),
+                   "splx_batch_kernel_times_slot")
         return dict(zip(self.KERNELS, [float(x) for x in arr]))
 
     def set_launch(self, raster_ctas_per_sm: int):
@@ -534,6 +541,10 @@ class Graph:
 
     def launch(self, stream=None):
         _check(_lib.splx_graph_launch(self.h, _stream(stream)), "splx_graph_launch")
+
+    def set_timing_ring(self, slots: int):
+        """Launch i records the graph's timing events into ring slot i mod slots."""
+        _check(_lib.splx_graph_set_timing_ring(self.h, int(slots)), "splx_graph_set_timing_ring")
 
     def close(self):
         if self.h:
