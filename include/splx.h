@@ -340,6 +340,12 @@ int splx_server_poll(splx_server_t s, int64_t* ids, int32_t* status, int32_t cap
                      int32_t* n_out);
 /* Host outputs (each nullable): queued requests, requests in flight, reserved bytes. */
 int splx_server_stats(splx_server_t s, int32_t* queued, int32_t* inflight, size_t* reserved);
+/* Device timeline of a finished request (of the last 65,536): times_ms (host array of 3)
+ * receives, in ms after the server's creation, when its launch began on the GPU (before
+ * its first kernel), when its projection and tile counts were done, and when its image
+ * had been copied out.  Requests launched together share these.  SPLX_ERR_INVALID for an
+ * unknown or unfinished id.  Shows how launches overlap on the device. */
+int splx_server_request_times(splx_server_t s, int64_t id, float* times_ms);
 /* Waits for the launches in flight, releases everything; queued requests are dropped. */
 int splx_server_destroy(splx_server_t s);
 

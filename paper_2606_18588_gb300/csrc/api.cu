@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1227,6 +1228,9 @@ struct SrvLaunch {
   int phase = 0;
   cudaStream_t s = nullptr;
   cudaEvent_t ev = nullptr;
+  // device timeline of the launch: before its first kernel, after its projection and tile
+  // counts (the pair count's copy), after its last copy-out
+  cudaEvent_t t_begin = nullptr, t_counted = nullptr, t_end = nullptr;
   uint32_t* total_h = nullptr;
   Plan P;
   float* partial = nullptr;
@@ -1250,6 +1254,11 @@ struct splx_server_s {
   std::deque<SrvReq> pending;
   std::vector<SrvLaunch> slots;
   std::deque<std::pair<int64_t, int>> finished;  // (request id, status) not yet reported
+  // per finished request: its launch's begin / counted / end times in ms after `epoch`
+  // (the most recent kTimesKept requests)
+  cudaEvent_t epoch = nullptr;
+  std::unordered_map<int64_t, std::array<float, 3>> times;
+  std::deque<int64_t> times_order;
 };
 
 namespace {
@@ -1269,6 +1278,8 @@ size_t launch_bytes(const splx_server_s& S, const std::vector<SrvReq>& reqs, dou
                    (pairs / 2048.0 + 1.0) * 8.0 + 65536.0;
   return (size_t)b;
 }
+
+constexpr size_t kTimesKept = 1 << 16;
 
 int64_t launch_pixels(const std::vector<SrvReq>& reqs) {
   int64_t px = 0;
@@ -1301,6 +1312,7 @@ int srv_start(splx_server_s* S, SrvLaunch& L) {
   Plan& P = L.P;
   const int K = (int)S->subsets.size();
   const int V = (int)L.reqs.size();
+  CK(cudaEventRecord(L.t_begin, L.s));
   P.ctx = S->ctx; P.V = V; P.K = K; P.deg = S->subsets[0].sh_degree; P.tile = S->opts.tile;
   P.N = S->N; P.opts = S->opts;
   int64_t goff = 0;
@@ -1345,6 +1357,7 @@ int srv_start(splx_server_s* S, SrvLaunch& L) {
   if ((r = P.project_and_count(L.s))) return r;
   CK(cudaMemcpyAsync(L.total_h, P.tile_start + P.n_tiles, sizeof(uint32_t),
                      cudaMemcpyDeviceToHost, L.s));
+  CK(cudaEventRecord(L.t_counted, L.s));
   CK(cudaEventRecord(L.ev, L.s));
   L.phase = 1;
   return SPLX_OK;
@@ -1372,6 +1385,7 @@ int srv_render(splx_server_s* S, SrvLaunch& L, uint64_t total) {
     CK(cudaMemcpyAsync(L.reqs[v].out, L.out_cat + 3 * P.pix_off[v], bytes,
                        cudaMemcpyDeviceToDevice, L.s));
   }
+  CK(cudaEventRecord(L.t_end, L.s));
   CK(cudaEventRecord(L.ev, L.s));
   L.phase = 2;
   return SPLX_OK;
@@ -1395,7 +1409,19 @@ int srv_advance(splx_server_s* S) {
       continue;
     }
     if (L.phase == 2) {
-      for (const SrvReq& r : L.reqs) S->finished.emplace_back(r.id, SPLX_OK);
+      std::array<float, 3> t = {0.0f, 0.0f, 0.0f};
+      cudaEvent_t marks[3] = {L.t_begin, L.t_counted, L.t_end};
+      for (int i = 0; i < 3; ++i)
+        if (cudaEventElapsedTime(&t[i], S->epoch, marks[i]) != cudaSuccess) t[i] = -1.0f;
+      for (const SrvReq& r : L.reqs) {
+        S->finished.emplace_back(r.id, SPLX_OK);
+        S->times[r.id] = t;
+        S->times_order.push_back(r.id);
+        if (S->times_order.size() > kTimesKept) {
+          S->times.erase(S->times_order.front());
+          S->times_order.pop_front();
+        }
+      }
       srv_free_launch(S, L);
       continue;
     }
@@ -1497,8 +1523,13 @@ int splx_server_create(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
   for (SrvLaunch& L : S->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&L.t_begin);
+    if (e == cudaSuccess) e = cudaEventCreate(&L.t_counted);
+    if (e == cudaSuccess) e = cudaEventCreate(&L.t_end);
     if (e == cudaSuccess) e = cudaMallocHost(&L.total_h, sizeof(uint32_t));
   }
+  if (e == cudaSuccess) e = cudaEventCreate(&S->epoch);
+  if (e == cudaSuccess) e = cudaEventRecord(S->epoch, S->slots[0].s);
   if (e != cudaSuccess) {
     splx_server_destroy(S);
     return cuda_fail(e, "splx_server_create");
@@ -1565,9 +1596,20 @@ int splx_server_destroy(splx_server_t S) {
     if (L.s) cudaStreamSynchronize(L.s);
     if (L.s) cudaStreamDestroy(L.s);
     if (L.ev) cudaEventDestroy(L.ev);
+    for (cudaEvent_t t : {L.t_begin, L.t_counted, L.t_end})
+      if (t) cudaEventDestroy(t);
     if (L.total_h) cudaFreeHost(L.total_h);
   }
+  if (S->epoch) cudaEventDestroy(S->epoch);
   delete S;
+  return SPLX_OK;
+}
+
+int splx_server_request_times(splx_server_t S, int64_t id, float* times_ms) {
+  if (!S || !times_ms) return SPLX_ERR_INVALID;
+  auto it = S->times.find(id);
+  if (it == S->times.end()) return SPLX_ERR_INVALID;
+  for (int i = 0; i < 3; ++i) times_ms[i] = it->second[i];
   return SPLX_OK;
 }
 
@@ -1611,6 +1653,13 @@ int splx_graph_launch(splx_graph_t g, splx_stream_t stream) {
 
 int splx_graph_set_timing_ring(splx_graph_t g, int32_t slots) {
   if (!g || slots < 0 || slots > 4096) return SPLX_ERR_INVALID;
+  // the executable graph's event nodes go back to their captured events before the ring's
+  // events are destroyed (a later launch must not record into a destroyed event)
+  // (an event still pending in a launch in flight is released once it completes)
+  if (!g->ring.empty()) {
+    for (size_t k = 0; k < g->ev_nodes.size(); ++k)
+      CK(cudaGraphExecEventRecordNodeSetEvent(g->exec, g->ev_nodes[k], g->ev_orig[k]));
+  }
   for (cudaEvent_t e : g->ring) cudaEventDestroy(e);
   g->ring.clear();
   g->ev_nodes.clear();

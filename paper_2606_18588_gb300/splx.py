@@ -107,6 +107,7 @@ _sigs = {
     "splx_graph_begin": (C.c_int, [_P, _P]),
     "splx_graph_end": (C.c_int, [_P, _P, C.POINTER(_P)]),
     "splx_graph_launch": (C.c_int, [_P, _P]),
+    "splx_server_request_times": (C.c_int, [_P, C.c_int64, _P]),
     "splx_graph_set_timing_ring": (C.c_int, [_P, C.c_int32]),
     "splx_batch_kernel_times_slot": (C.c_int, [_P, _P, C.c_int32, _P]),
     "splx_graph_destroy": (C.c_int, [_P]),
@@ -388,6 +389,12 @@ class Server:
                 done.append((self._ids[i], self._st[i]))
             if n.value < 256:
                 return done
+
+    def request_times(self, rid: int) -> dict:
+        """Device timeline of a finished request, ms after the server's creation."""
+        arr = (C.c_float * 3)()
+        _check(_lib.splx_server_request_times(self.h, int(rid), arr), "splx_server_request_times")
+        return {"begin": arr[0], "counted": arr[1], "end": arr[2]}
 
     def stats(self):
         q, f, r = C.c_int32(), C.c_int32(), C.c_size_t()
