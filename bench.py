@@ -36,7 +36,6 @@ OPS_PER_ALPHA = 10
 OPS_PER_BLEND = 8
 OPS_PER_CONTRIB = 22
 FP32_LANES_PER_SM = 128
-SMS = 152
 
 
 def parse():
@@ -52,7 +51,7 @@ def parse():
                     help="tile side 8/16/32 (0: the autotuner picks tile and CTAs per SM)")
     ap.add_argument("--ctas-per-sm", type=int, default=0,
                     help="rasteriser CTAs per SM when --tile is given (0: one per work item)")
-    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--plain-steps", type=int, default=20)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -63,6 +62,9 @@ def parse():
                     help="requests of the serving run (0: skip it)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrivals per second")
     ap.add_argument("--serve-n", type=int, default=0, help="override the served scene's size")
+    ap.add_argument("--city-steps", type=int, default=10,
+                    help="timed steps of the 120M-Gaussian aerial-city training step (0: skip)")
+    ap.add_argument("--city-warmup", type=int, default=3)
     return ap.parse_args()
 
 
@@ -162,47 +164,42 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# DRAM traffic per unit of work measured by ncu (profiles/dram_traffic.md): one line per
-# kernel, "kernel | source file | sha256 of that file at capture | bytes per unit | unit".
+# DRAM traffic per unit of work measured by ncu (profiles/dram_traffic.json: per kernel its
+# source file, that file's sha256 at the capture, bytes per unit and the unit).
 KERNEL_SOURCE = {"raster_fwd": "raster.cu", "raster_bwd": "raster.cu", "project": "project.cu",
                  "fill": "bin.cu", "sort": "bin.cu", "project_bwd": "project_bwd.cu",
                  "composite": "composite.cu", "composite_bwd": "composite.cu"}
 
 
 def measured_traffic(name, counts):
-    """DRAM bytes per launch of `name` from the committed ncu summary, scaled to this
-    launch by its units of work; None if there is no entry or the kernel's source changed
-    since the capture."""
+    """DRAM bytes per launch of `name` from the committed ncu table, scaled to this launch
+    by its units of work; None if there is no entry or the kernel's source changed since
+    the capture."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
-        lines = open(path).read().splitlines()
+        with open(path) as f:
+            table = json.load(f)["kernels"]
+    except (OSError, ValueError, KeyError):
+        return None
+    e = table.get(name)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_2606_18588_gb300", "csrc", e["source"])
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
         return None
-    for ln in lines:
-        cells = [c.strip() for c in ln.strip().strip("|").split("|")]
-        if len(cells) != 5 or cells[0] != name:
-            continue
-        src = os.path.join(ROOT, "paper_2606_18588_gb300", "csrc", cells[1])
-        try:
-            digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        except OSError:
-            return None
-        if digest != cells[2]:
-            return None
-        unit = cells[4]
-        units = counts.get(unit)
-        if units is None:
-            return None
-        return float(cells[3]) * units
-    return None
+    if digest != e["sha256"]:
+        return None
+    units = counts.get(e["unit"])
+    return None if units is None else float(e["bytes_per_unit"]) * units
 
 
 def roofline(name, ms, counts, w, pk):
     """Roofline entry for kernel `name` of mean duration `ms` per launch."""
     V, N, K, nc, pixels = w["V"], w["N"], w["K"], w["nc"], w["pixels"]
-    clock = pk.get("sm_max_mhz", 2070.0) * 1e6
-    alu_peak = SMS * FP32_LANES_PER_SM * clock / 1e12  # T FP32 instr/s
+    alu_peak = w["alu_peak"]  # T FP32 instr/s, derived from the device (device_peak)
     hbm = pk["hbm_gbs"]
     sec = ms / 1e3
     if name in ("raster_fwd", "raster_bwd"):
@@ -217,6 +214,11 @@ def roofline(name, ms, counts, w, pk):
                 "work": f"{ev} alpha evaluations x {OPS_PER_ALPHA} + {more} "
                         f"{'blends' if name == 'raster_fwd' else 'contributions'} x {per} FP32 ops"}
     param_bytes = (3 + 3 + 4 + 1 + 3 * nc) * 4
+    note = None
+    # share of (view, subset, tile) work items inside the subsets' visible regions: the
+    # composites read and write partial planes only there
+    items = counts.get("items_total") or 0
+    inside = 1.0 - (counts.get("outside_items", 0) / items) if items else 1.0
     if name == "sort":
         byts = counts["pairs"] * 16  # each tile segment read and written once
     elif name == "project":
@@ -226,14 +228,21 @@ def roofline(name, ms, counts, w, pk):
     elif name == "fill":
         byts = V * N * (4 + 32) + counts["pairs"] * 8
     elif name in ("composite", "composite_bwd"):
-        byts = pixels * (K * 20 + 16) if name == "composite" else pixels * (K * 36 + 12)
+        per = 20 if name == "composite" else 36
+        byts = pixels * (16 if name == "composite" else 12) + int(pixels * K * per * inside)
+        note = (f"partial planes counted only inside the visible regions ({inside:.3f} of the "
+                "work items)")
     elif name == "adam":
-        byts = N * param_bytes // 4 * 32
+        byts = N * param_bytes // 4 * 32 + pixels * 3 * 12
+        note = "Adam over every parameter (read p, g, m, v; write p, m, v, g = 0) and the L1 loss"
     else:
         byts = V * N * 12
     a = byts / sec / 1e9
-    return {"kernel": name, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
-            "frac": a / hbm, "traffic": None, "work": f"{byts} algorithmic bytes"}
+    out = {"kernel": name, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+           "frac": a / hbm, "traffic": None, "work": f"{byts} algorithmic bytes"}
+    if note:
+        out["note"] = note
+    return out
 
 
 # ---------------------------------------------------------------- CPU oracle leg
@@ -265,6 +274,28 @@ def oracle_sample(sc, off, cam, frac, seed=0, reps=1):
             f"{k}/{nt} seeded tiles ({t1:.1f} s) plus the fixed projection/binning cost "
             f"({t0:.1f} s, no tiles), extrapolated to the full view")
     return full, info, O.num_threads()
+
+
+def cpu_baseline_small():
+    """The oracle on the two small configurations (its fwd or fwd+bwd Mpixel/s on the host
+    cores): the 10k-Gaussian plain forward at 256x256 (whole view, forward only) and the
+    1M-Gaussian K = 4 1920x1080 forward + backward (a seeded 1/64 of the tiles plus the
+    fixed projection cost, extrapolated to the full view)."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2606_18588_gb300 import inputs as I
+    out = {}
+    sc, cam = I.plain_forward_case(0)
+    t = time.perf_counter()
+    O.render_view(sc, np.array([0, sc.n]), cam, O.opts())
+    dt = time.perf_counter() - t
+    out["plain_10k_sh0_256"] = {"value": cam.width * cam.height / dt / 1e6, "unit": UNIT,
+                                "pass": "forward", "sample": "whole view", "seconds": dt}
+    sc, off, _, cams = I.cluster_case(1_000_000, 2, 4, 1, [(1920, 1080)])
+    full, info, _ = oracle_sample(sc, off, cams[0], 1.0 / 64.0)
+    out["fwdbwd_1m_k4_1080p"] = {"value": cams[0].width * cams[0].height / full / 1e6,
+                                 "unit": UNIT, "pass": "forward+backward", "sample": info}
+    return out
 
 
 def run_reference(args):
@@ -337,13 +368,13 @@ def serve_leg(args, ctx, rank, world):
 
 
 # ---------------------------------------------------------------- aerial city, 120M
-def city_main(args):
+def city_leg(args, rank, world, local, steps, warmup):
     """Training steps on the aerial-city scene (train_120m_k32): 120M Gaussians SH3 in K = 32
     k-d cells, each step a batch of 8 1920x1080 views sampled from a pool of 500 aerial
     cameras, forward + composite + L1 + backward + Adam over all parameters.  The scene is
     generated cell by cell straight into device memory; each step's views, subset orders
-    and target images are set between graph replays (targets staged on the device first)."""
-    import numpy as np
+    and target images are set between graph replays (targets staged on the device first).
+    Returns the measurements as a dict."""
     import torch
     import torch.distributed as dist
     from paper_2606_18588_gb300 import inputs as I
@@ -351,10 +382,6 @@ def city_main(args):
     from paper_2606_18588_gb300.train import BatchedStep, _subset_structs, city_to_device
     from paper_2606_18588_gb300.visibility import orders_for_views
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
     w = I.WORKLOADS["train_120m_k32"]
     n, seed = args.n or w["n"], 4 + rank
     t0 = time.perf_counter()
@@ -363,7 +390,7 @@ def city_main(args):
     ctx = S.Context(local)
     dev = city_to_device(layout)
     gen_s = time.perf_counter() - t0
-    nsteps = args.warmup + args.steps
+    nsteps = warmup + steps
     views = [[pool[i] for i in I.step_views(seed, s, len(pool), w["views"])] for s in range(nsteps)]
     orders = [None if args.no_skip else orders_for_views(layout.boxes, v) for v in views]
     px = sum(c.width * c.height for c in views[0])
@@ -388,8 +415,9 @@ def city_main(args):
         ctx.device_status(stream)
         pb.close()
         del rgb
+        cap = int(need * 1.05) + 1024
         st = BatchedStep(ctx, dev, layout.offsets, layout.sh_degree, views[0], None, o,
-                         pair_capacity=int(need * 1.05) + 1024, stream=stream, order=orders[0])
+                         pair_capacity=cap, stream=stream, order=orders[0])
         st.set_targets(tgt[0])
         st.run()
         stream.synchronize()
@@ -399,7 +427,7 @@ def city_main(args):
         launches0 = ctx.launch_count
         st.capture()
         launches_per_step = ctx.launch_count - launches0
-        for s in range(args.warmup):
+        for s in range(warmup):
             st.set_views(views[s], orders[s])
             st.target.copy_(tgt[s], non_blocking=True)
             st.replay()
@@ -411,7 +439,7 @@ def city_main(args):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for s in range(args.warmup, nsteps):
+        for s in range(warmup, nsteps):
             st.set_views(views[s], orders[s])  # waits for the previous replay
             st.target.copy_(tgt[s], non_blocking=True)
             st.replay()
@@ -423,23 +451,43 @@ def city_main(args):
         code, _ = st.status()
         if code != S.OK:
             raise RuntimeError(f"city status after timed region {code}")
-        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
-        value = px * world / (ms / 1e3) / 1e6
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps)
         st.close()
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"train_120m_k32: {n} Gaussians SH{layout.sh_degree} on an "
-                                   f"aerial city (1 km^2), K={layout.K} k-d subsets (x/z), "
-                                   f"{w['views']} views 1920x1080 per step sampled from "
-                                   f"{len(pool)} aerial cameras, L1 loss, Adam",
-                       "global_batch": w["views"] * world, "pixels_per_step": px * world,
-                       "tile": o.tile, "pair_capacity": int(need * 1.05) + 1024,
-                       "saturation_skipping": not args.no_skip, "scene_gen_s": gen_s,
-                       "l2": "inputs larger than L2 (28 GB parameters)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": None, "e2e": None, "clocks": clk,
-            "gpu_launches": launches_per_step * args.steps}
+    ctx.close()
+    del dev, tgt
+    return {"metric": "fwd+bwd Mpixel/s (training step incl. Adam)",
+            "value": px * world / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+            "steps": steps, "warmup": warmup,
+            "workload": f"train_120m_k32: {n} Gaussians SH{layout.sh_degree} on an aerial city "
+                        f"(1 km^2), K={layout.K} k-d subsets (x/z), {w['views']} views 1920x1080 "
+                        f"per step sampled from {len(pool)} aerial cameras, L1 loss, Adam",
+            "global_batch": w["views"] * world, "pixels_per_step": px * world, "tile": o.tile,
+            "pair_capacity": cap, "saturation_skipping": not args.no_skip,
+            "scene_gen_s": gen_s, "l2": "inputs larger than L2 (28 GB parameters)",
+            "timing": "CUDA events around the timed steps; each step sets its views, orders "
+                      "and targets between replays (a host wait for the previous replay)",
+            "clocks": clk, "gpu_launches": launches_per_step * steps}
+
+
+def city_main(args):
+    """`--workload train_120m_k32`: the aerial-city training step as the bench line."""
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    r = city_leg(args, rank, world, local, args.steps, args.warmup)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {k: r[k] for k in ("workload", "global_batch", "pixels_per_step", "tile",
+                                         "pair_capacity", "saturation_skipping", "scene_gen_s",
+                                         "l2", "timing")},
+            "roofline": None, "e2e": None, "clocks": r["clocks"],
+            "gpu_launches": r["gpu_launches"]}
+    line["config"]["parallelism"] = "replicas" if world > 1 else "single GPU"
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -448,13 +496,128 @@ def city_main(args):
 
 
 # ---------------------------------------------------------------- our path
+def timed_replays(st, steps, stream, barrier):
+    """`steps` back-to-back replays of the step's graph with no host wait between them.
+    Events recorded on the stream before each replay and after the last give the step
+    times; the graph's timing ring gives every replay's per-kernel times, read after the
+    loop.  Returns (total ms, per-step ms, per-replay kernel ms dicts)."""
+    import torch
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    st.graph.set_timing_ring(steps)
+    barrier()
+    torch.cuda.synchronize()
+    for i in range(steps):
+        evs[i].record(stream)
+        st.replay()
+    evs[steps].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+    total = evs[0].elapsed_time(evs[steps])
+    ktimes = [st.batch.kernel_times(st.graph, i) for i in range(steps)]
+    st.graph.set_timing_ring(0)
+    return total, step_ms, ktimes
+
+
+def batched_leg(args, ctx, dev, sc, off, cams, targets, o, ctas, order, stream, barrier, world):
+    """Builds, captures and times the batched step (one CUDA graph per step).  Returns the
+    step object (still open) and its measurements."""
+    import torch
+    from paper_2606_18588_gb300 import splx as S
+    from paper_2606_18588_gb300.train import BatchedStep
+    with torch.cuda.stream(stream):
+        st = BatchedStep(ctx, dev, off, sc.sh_degree, cams, [torch.from_numpy(t) for t in targets],
+                         o, stream=stream, order=order)
+        st.batch.set_timing(True)
+        st.batch.set_launch(ctas)
+        st.run()  # eager once: sizes everything, checks status
+        stream.synchronize()
+        code, pairs = st.status()
+        if code != S.OK:
+            raise RuntimeError(f"batched forward status {code}")
+        counts = st.batch.counters(stream)
+        counts["items_total"] = (len(off) - 1) * sum(
+            ((c.width + o.tile - 1) // o.tile) * ((c.height + o.tile - 1) // o.tile) for c in cams)
+        launches0 = ctx.launch_count
+        st.capture()
+        launches_per_step = ctx.launch_count - launches0
+        for _ in range(args.warmup):
+            st.replay()
+        stream.synchronize()
+        code, _ = st.status()
+        if code != S.OK:
+            raise RuntimeError(f"status after warm-up {code}")
+        total, step_ms, ktimes = timed_replays(st, args.steps, stream, barrier)
+        code, _ = st.status()
+        if code != S.OK:
+            raise RuntimeError(f"status after timed region {code}")
+    ms = max_over_ranks(total / args.steps)
+    kmean = {k: statistics.mean(t[k] for t in ktimes) for k in ktimes[0]}
+    kmean["loss+adam"] = max(ms - sum(kmean.values()), 0.0)
+    return st, {"ms": ms, "step_ms_median": max_over_ranks(statistics.median(step_ms)),
+                "value": st.pixels * world / (ms / 1e3) / 1e6, "kmean": kmean,
+                "counts": counts, "launches_per_step": launches_per_step}
+
+
+def plain_leg(args, ctx, dev, sc, off, cams, targets, o, stream, barrier, world):
+    """The plain per-view path (one render_partial per (view, subset), composite, loss and
+    backward per view, one Adam), timed per step with CUDA events on its stream."""
+    import torch
+    from paper_2606_18588_gb300.train import PlainStep
+    with torch.cuda.stream(stream):
+        ps = PlainStep(ctx, dev, off, sc.sh_degree, cams, [torch.from_numpy(t) for t in targets],
+                       o, stream=stream)
+        for _ in range(max(1, min(args.warmup, 3))):
+            ps.run()
+        stream.synchronize()
+        n = args.plain_steps
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+        barrier()
+        torch.cuda.synchronize()
+        for i in range(n):
+            evs[i].record(stream)
+            ps.run()
+        evs[n].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(n)]
+    med = max_over_ranks(statistics.median(step_ms))
+    mean = max_over_ranks(evs[0].elapsed_time(evs[n]) / n)
+    px = ps.pixels * world
+    del ps
+    return {"mpixel_s": px / (med / 1e3) / 1e6, "ms_per_step_median": med,
+            "ms_per_step_mean": mean, "steps": n, "timing": "CUDA events per step, median",
+            "path": "one render_partial per (view, subset) + composite + L1 + backward per "
+                    "view, one Adam; every subset rendered (no saturation skipping)"}
+
+
+def device_peak(local):
+    """FP32 peak derived from the device: SM count (CUDA device properties) x 128 FP32
+    lanes x the maximum SM clock (nvidia-smi clocks.max.sm, else the measured-peaks file)."""
+    import torch
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = None
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(local), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=20).stdout.strip()
+        mhz = float(out.splitlines()[0])
+    except Exception:
+        pass
+    src = "nvidia-smi clocks.max.sm"
+    if not mhz:
+        mhz = peaks()[0].get("sm_max_mhz", 2070.0)
+        src = "MEASURED_PEAKS.json sm_max_mhz"
+    return {"sms": sms, "fp32_lanes_per_sm": FP32_LANES_PER_SM, "sm_max_mhz": mhz,
+            "tflops": sms * FP32_LANES_PER_SM * mhz * 1e6 / 1e12, "clock_source": src}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "train_120m_k32":
         return city_main(args)
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -463,10 +626,14 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     from paper_2606_18588_gb300 import splx as S
-    from paper_2606_18588_gb300.train import BatchedStep, PlainStep, scene_to_device
+    from paper_2606_18588_gb300.train import scene_to_device
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
 
     sc, off, boxes, cams, targets, desc = make_workload(args.workload, args.n, rank=rank,
-                                                 views_override=args.views)
+                                                        views_override=args.views)
     ctx = S.Context(local)
     dev = scene_to_device(sc)
     stream = torch.cuda.Stream()
@@ -483,59 +650,21 @@ def main():
     else:
         tile, ctas = args.tile, args.ctas_per_sm
     o = S.opts(tile=tile)
-    with torch.cuda.stream(stream):
-        st = BatchedStep(ctx, dev, off, sc.sh_degree, cams, [torch.from_numpy(t) for t in targets],
-                         o, stream=stream, order=order)
-        st.batch.set_timing(True)
-        st.batch.set_launch(ctas)
-        st.run()  # eager once: sizes everything, checks status
-        stream.synchronize()
-        code, pairs = st.status()
-        if code != S.OK:
-            raise RuntimeError(f"batched forward status {code}")
-        counts = st.batch.counters(stream)
-        launches0 = ctx.launch_count
-        st.capture()
-        launches_per_step = ctx.launch_count - launches0
-        for _ in range(args.warmup):
-            st.replay()
-        stream.synchronize()
-        code, _ = st.status()
-        if code != S.OK:
-            raise RuntimeError(f"status after warm-up {code}")
+    dpk = device_peak(local)
 
-        def barrier():
-            if world > 1:
-                dist.barrier()
+    # ---- the headline: batched graph with saturation skipping (clocks sampled meanwhile)
+    clocks = Clocks(local)
+    clocks.start()
+    st, head = batched_leg(args, ctx, dev, sc, off, cams, targets, o, ctas, order, stream,
+                           barrier, world)
+    clk = clocks.stop()
+    ms, value, kmean, counts = head["ms"], head["value"], head["kmean"], head["counts"]
+    pixels = st.pixels
 
-        # ---- timed region: K graph replays
-        clocks = Clocks(local)
-        clocks.start()
-        barrier()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ktimes = []
-        e0.record(stream)
-        for _ in range(args.steps):
-            st.replay()
-            ktimes.append(st.batch.kernel_times())  # waits for this replay's last kernel event
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        clk = clocks.stop()
-        ms = e0.elapsed_time(e1) / args.steps
-        code, _ = st.status()
-        if code != S.OK:
-            raise RuntimeError(f"status after timed region {code}")
-        ms = max_over_ranks(ms)
-        pixels = st.pixels
-        value = pixels * world / (ms / 1e3) / 1e6
-        kmean = {k: statistics.mean(t[k] for t in ktimes) for k in ktimes[0]}
-        kmean["loss+adam"] = max(ms - sum(kmean.values()), 0.0)
-
-        # ---- end to end through the public API with host buffers
-        e2e = None
-        if not args.no_e2e:
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        with torch.cuda.stream(stream):
             host_t = torch.cat([torch.from_numpy(t).reshape(-1) for t in targets]).pin_memory()
             host_loss = torch.empty(1).pin_memory()
             barrier()
@@ -549,36 +678,38 @@ def main():
             t1.record(stream)
             torch.cuda.synchronize()
             barrier()
-            ems = max_over_ranks(t0.elapsed_time(t1) / args.steps)
-            e2e = {"value": pixels * world / (ems / 1e3) / 1e6, "unit": UNIT,
-                   "h2d_bytes_per_step": host_t.numel() * 4, "d2h_bytes_per_step": 4,
-                   "ms_per_step": ems}
+        ems = max_over_ranks(t0.elapsed_time(t1) / args.steps)
+        e2e = {"value": pixels * world / (ems / 1e3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": host_t.numel() * 4, "d2h_bytes_per_step": 4,
+               "ms_per_step": ems}
+    st.close()
+    st = None
 
-        # ---- plain per-view path (same work, launched per view and subset)
-        plain = None
-        if not args.no_plain and args.plain_steps > 0:
-            ps = PlainStep(ctx, dev, off, sc.sh_degree, cams, [torch.from_numpy(t) for t in targets],
-                           o, stream=stream)
-            ps.run()
-            stream.synchronize()
-            p0 = time.perf_counter()
-            for _ in range(args.plain_steps):
-                ps.run()
-            stream.synchronize()
-            pms = (time.perf_counter() - p0) / args.plain_steps * 1e3
-            plain = {"mpixel_s": pixels / (pms / 1e3) / 1e6, "ms_per_step": pms,
-                     "steps": args.plain_steps}
+    # ---- like for like: the batched graph without saturation skipping, and the plain
+    # per-view path, both rendering every subset
+    noskip = None
+    if not args.no_plain and order is not None:
+        st0, h0 = batched_leg(args, ctx, dev, sc, off, cams, targets, o, ctas, None, stream,
+                              barrier, world)
+        st0.close()
+        noskip = {"mpixel_s": h0["value"], "ms_per_step": h0["ms"],
+                  "ms_per_step_median": h0["step_ms_median"], "steps": args.steps,
+                  "kernel_ms": h0["kmean"], "timing": "CUDA events, graph replays back to back",
+                  "path": "the batched graph with every subset rendered (no saturation skipping)"}
+    plain = None
+    if not args.no_plain and args.plain_steps > 0:
+        plain = plain_leg(args, ctx, dev, sc, off, cams, targets, o, stream, barrier, world)
 
     # ---- roofline of the dominant kernel
     pk, pk_src = peaks()
     wl = {"V": len(cams), "N": sc.n, "K": len(off) - 1, "nc": (sc.sh_degree + 1) ** 2,
-          "pixels": pixels, "n_tiles": sum(((c.width + tile - 1) // tile) *
-                                           ((c.height + tile - 1) // tile)
-                                           for c in cams) * (len(off) - 1)}
+          "pixels": pixels, "alu_peak": dpk["tflops"]}
     cand = {k: v for k, v in kmean.items() if k != "loss+adam"}
     dom = max(cand, key=cand.get)
     roof = roofline(dom, cand[dom], counts, wl, pk)
-    roof["peak_source"] = f"{pk_src} ({'HBM copy' if roof['bound'] == 'hbm' else 'SMs x FP32 lanes x max SM clock'})"
+    roof["peak_source"] = (f"{pk_src} HBM copy (MEASURED_PEAKS.json)" if roof["bound"] == "hbm"
+                           else "derived: SMs x 128 FP32 lanes x max SM clock, read from the device")
+    roof["device"] = dpk
     roof["share_of_step"] = cand[dom] / ms
     roof["traffic"] = measured_traffic(dom, counts)
     # the other kernels whose algorithmic work the step's counters fix, against their roofs
@@ -589,6 +720,8 @@ def main():
             r = roofline(name, t, counts, wl, pk)
             others[name] = {"bound": r["bound"], "achieved": r["achieved"], "unit": r["unit"],
                             "frac": r["frac"], "ms": t}
+            if "note" in r:
+                others[name]["note"] = r["note"]
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -601,29 +734,38 @@ def main():
                                "fill tile buckets, per-tile depth sort, raster fwd, composite, L1 "
                                "loss, composite bwd, raster bwd, project bwd, Adam)",
                        "saturation_skipping": order is not None,
-                       "plain_path": "one render_partial per (view, subset) + composite + "
-                                     "backward per view, every subset rendered (no skipping)",
+                       "timing": "CUDA events around the back-to-back graph replays (no host "
+                                 "wait between them); per-kernel times from the graph's "
+                                 "timing ring, every replay",
+                       "ms_per_step_median": head["step_ms_median"],
                        "l2": "inputs larger than L2 (2.4 GB parameters, 10 GB projected records)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "plain": plain, "kernel_ms": kmean, "counters": counts,
-                       "kernel_rooflines": others},
+                       "batched_noskip": noskip, "plain": plain, "kernel_ms": kmean,
+                       "counters": counts, "kernel_rooflines": others},
             "roofline": roof, "e2e": e2e, "clocks": clk,
-            "gpu_launches": launches_per_step * args.steps}
-
-    # ---- serving: resident 20M-Gaussian scene, Poisson requests of mixed resolution
-    st.close()
-    st = None
+            "gpu_launches": head["launches_per_step"] * args.steps}
     del dev
     torch.cuda.empty_cache()
+
+    # ---- serving: resident 20M-Gaussian scene, Poisson requests of mixed resolution
     if args.serve_requests > 0:
         line["serve"] = serve_leg(args, ctx, rank, world)
+    ctx.close()
+    torch.cuda.empty_cache()
 
-    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    # ---- the 120M-Gaussian aerial-city training step
+    if args.city_steps > 0:
+        line["train_120m_k32"] = city_leg(args, rank, world, local, args.city_steps,
+                                          args.city_warmup)
+        torch.cuda.empty_cache()
+
+    # ---- CPU oracle baselines (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             full, info, cores = oracle_sample(sc, off, cams[0], args.cpu_tile_fraction)
             line["cpu_baseline"] = {"value": cams[0].width * cams[0].height / full / 1e6,
                                     "unit": UNIT, "cores": cores, "kind": "oracle", "sample": info}
+            line["cpu_baseline"]["other_configs"] = cpu_baseline_small()
         except Exception as ex:  # the baseline is reported, never required
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
                                     "sample": f"failed: {ex}"}
