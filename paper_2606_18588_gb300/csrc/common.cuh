@@ -111,7 +111,7 @@ struct BatchDev {
   int64_t tile_base[kMaxViews + 1];  // view v's image tiles start at tile_base[v]
   int64_t pix_off[kMaxViews + 1];    // view v's pixels start at pix_off[v]
   // [V][N][3]: (sx, sy, sxx, sxy), (syy, go, gr, gg), (gb, 0, 0, 0): sums over pixels of
-  // gp dx, gp dy, gp dx^2, gp dx dy, gp dy^2 (gp = dL/dpower), dL/do, dL/dcolour
+  // ge dx, ge dy, ge dx^2, ge dx dy, ge dy^2 (ge = dL/dpower / o), dL/do, dL/dcolour
   float4* grad2d;
   int* status;                  // device status word
   // work counters (nullable; kept by eager runs): forward [0] thread-entries examined,

@@ -1,7 +1,7 @@
 // Backward of the projection (Sec. 2 step 1) and the parameter update (Sec. 2 step 4).
 //
 // project_bwd: one thread per Gaussian loops over the views of the batch.  For each view
-// where the rasteriser left a nonzero 2-D gradient (the moments of dL/dpower over the
+// where the rasteriser left a nonzero 2-D gradient (the moments of dL/dpower / o over the
 // pixels, dL/do, dL/dcolour) it recomputes the FP32 projection, consumes and clears that gradient, and
 // chains it to the mean (through the 2-D mean, the EWA Jacobian J and the SH viewing
 // direction), the SH coefficients, the opacity logit, and - accumulated over views as
@@ -183,10 +183,11 @@ __global__ void __launch_bounds__(kProjBwdThreads, 4) k_project_bwd(const BatchD
     const float det = d01 * d01 + d02 * d02 + d12 * d12 + 0.3f * (a0 + c0) + 0.09f;
     const float idet = 1.0f / det;
     const float QA = (c0 + 0.3f) * idet, QB = -bb * idet, QC = (a0 + 0.3f) * idet;
-    // the rasteriser's moments -> dL/du, dL/dv and dL/d(A, B, C) of the conic:
-    // power = -(A dx^2 + 2 B dx dy + C dy^2) / 2 with (dx, dy) = pixel - (u, v)
-    const float gu = QA * G0.x + QB * G0.y, gv = QB * G0.x + QC * G0.y;
-    const float gA = -0.5f * G0.z, gB = -G0.w, gCc = -0.5f * G1.x, go = G1.y;
+    // the rasteriser's moments of dL/dpower / o -> dL/du, dL/dv and dL/d(A, B, C) of the
+    // conic: power = -(A dx^2 + 2 B dx dy + C dy^2) / 2 with (dx, dy) = pixel - (u, v)
+    const float mx = o * G0.x, my = o * G0.y;
+    const float gu = QA * mx + QB * my, gv = QB * mx + QC * my;
+    const float gA = -0.5f * o * G0.z, gB = -o * G0.w, gCc = -0.5f * o * G1.x, go = G1.y;
     const float gcol[3] = {G1.z, G1.w, gbl};
     glogit += go * o * (1.0f - o);
     // colour -> SH coefficients and viewing direction

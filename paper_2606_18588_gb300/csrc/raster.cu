@@ -19,9 +19,10 @@
 // Per-Gaussian sums over the tile's pixels are reduced with warp shuffles and added to
 // the per-(view, Gaussian) 2-D gradient with float4 atomics.  With gp = dL/dpower at a
 // pixel, power = -(A dx^2 + 2 B dx dy + C dy^2) / 2 and (dx, dy) = pixel centre - (u, v),
-// the record holds the conic-free moments sum gp dx, gp dy, gp dx^2, gp dx dy, gp dy^2;
-// dL/du = A sum gp dx + B sum gp dy, dL/dA = -sum gp dx^2 / 2 and the rest follow linearly
-// in the projection adjoint, which knows the conic.
+// the record holds the conic-free moments of ge = gp / o = dL/dalpha e^power (0 where
+// alpha is clamped), sum ge dx, ge dy, ge dx^2, ge dx dy, ge dy^2, and dL/do = sum ge;
+// dL/du = o (A sum ge dx + B sum ge dy), dL/dA = -o sum ge dx^2 / 2 and the rest follow
+// linearly in the projection adjoint, which knows the conic and the opacity.
 #include "common.cuh"
 
 namespace splx {
@@ -61,12 +62,11 @@ __device__ __forceinline__ bool pixel_alpha(const ColTerms& c, float ay, float q
                                             float& ex, float& dy, bool& clamped) {
   dy = __fsub_rn(pcy, ay);
   const float p2 = __fmaf_rn(__fmaf_rn(qc, dy, c.bx), dy, c.hx);
-  if (p2 > 0.0f) return false;
-  ex = ex2_approx(p2);
+  ex = ex2_approx(p2);  // finite for the rounding-sized p2 > 0 that the test below rejects
   const float raw = __fmul_rn(o, ex);
   clamped = raw > amax;
   alpha = clamped ? amax : raw;
-  return alpha >= amin;
+  return p2 <= 0.0f && alpha >= amin;
 }
 
 // Adds per-thread counts into counters[slot] with one atomic per warp.
@@ -448,8 +448,9 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
     if (kCount && tlast >= lo) n_evalb += (unsigned)((tlast < top ? tlast : top) - lo + 1);
     for (int jj = 0; jj < cnt; ++jj) {
       const int j = top - jj;
-      // the entry's sums over the warp's pixels: gp dx, gp dy, gp dx^2, gp dx dy, gp dy^2
-      // (gp = dL/dpower), dL/do and dL/dcolour; the projection adjoint applies the conic
+      // the entry's sums over the warp's pixels: ge dx, ge dy, ge dx^2, ge dx dy, ge dy^2
+      // (ge = dL/dpower / o), dL/do and dL/dcolour; the projection adjoint applies the conic
+      // and the opacity
       float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f, go = 0.f, gr = 0.f, gg = 0.f,
             gb = 0.f;
       bool act = false;
@@ -459,15 +460,17 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
         const uint32_t rx = __float_as_uint(Bv.w), ry = __float_as_uint(Cv.w);
         const int x0 = (int)(rx & 0xFFFFu), x1 = (int)(rx >> 16);
         const int y0 = (int)(ry & 0xFFFFu), y1 = (int)(ry >> 16);
+        // inside [x0, x1] as one unsigned compare (a pixel left of x0 wraps to a large value)
+        const unsigned rw = (unsigned)(x1 - x0), rh = (unsigned)(y1 - y0);
         bool cin[kSlotCols<PPT>], rin[kSlotRows<PPT>], anyc = false, anyr = false;
 #pragma unroll
         for (int c = 0; c < kSlotCols<PPT>; ++c) {
-          cin[c] = ti.x + 8 * c >= x0 && ti.x + 8 * c <= x1;
+          cin[c] = (unsigned)(ti.x + 8 * c - x0) <= rw;
           anyc |= cin[c];
         }
 #pragma unroll
         for (int r = 0; r < kSlotRows<PPT>; ++r) {
-          rin[r] = ti.y + 4 * r >= y0 && ti.y + 4 * r <= y1;
+          rin[r] = (unsigned)(ti.y + 4 * r - y0) <= rh;
           anyr |= rin[r];
         }
         if (anyc && anyr) {
@@ -495,16 +498,16 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
             gb = fmaf(q.z, aT, gb);
             const float qc = fmaf(q.z, Cv.z, fmaf(q.y, Cv.y, q.x * Cv.x));  // dL/dC^m . c_i
             const float ga = fmaf(Ti, qc, W[i] * rinv);                      // dL/dalpha_i
-            if (!cl) {
-              go = fmaf(ga, ex, go);
-              const float gp = ga * alpha;  // dL/dpower
-              const float px = gp * ct.dx, py = gp * dy;
-              sx += px;
-              sy += py;
-              sxx = fmaf(px, ct.dx, sxx);
-              sxy = fmaf(px, dy, sxy);
-              syy = fmaf(py, dy, syy);
-            }
+            // dL/do = ga e^power and dL/dpower = o ga e^power where alpha is not clamped,
+            // 0 where it is; the moments are of ga e^power (the projection adjoint applies o)
+            const float ge = cl ? 0.0f : ga * ex;
+            go += ge;
+            const float px = ge * ct.dx, py = ge * dy;
+            sx += px;
+            sy += py;
+            sxx = fmaf(px, ct.dx, sxx);
+            sxy = fmaf(px, dy, sxy);
+            syy = fmaf(py, dy, syy);
             W[i] = fmaf(-qc, aT, W[i]);
             T[i] = Ti;
           }
