@@ -657,8 +657,9 @@ CrossFilter make_filter(const orc_params& p, const int64_t* offsets, int K, cons
   for (int m = 0; m < K; ++m) {
     orc_params q = slice(p, offsets[m], offsets[m + 1]);
     const Subset s = prepare(q, cam, o.tile, (float)o.alpha_min);
-    // Omega (reading 14): the bounding rectangle of the tile rectangles of the subset's
-    // Gaussians that have at least one (Gaussian, tile) pair
+    // Omega (the visible region of Sec. 4.2, read on one GPU as a tile rectangle): the
+    // bounding rectangle of the tile rectangles of the subset's Gaussians that have at
+    // least one (Gaussian, tile) pair
     int* om = &f.omega[(size_t)4 * m];
     om[0] = om[1] = INT_MAX;
     om[2] = om[3] = -1;
