@@ -137,6 +137,31 @@ size_t splx_scratch_bytes(splx_ctx_t ctx);
 int splx_render_partial(splx_ctx_t ctx, const splx_gaussians* subset, const splx_camera* cam,
                         const splx_opts* opts, const splx_partial* out, splx_state_t* state_out,
                         splx_stream_t stream);
+/* Cross-boundary per-ray filtering on the per-view path (Sec. 8.1, appendix "Cross-boundary
+ * Gaussians Handling"; the batch's splx_batch_set_cross_filter per view).  The filter of
+ * one view needs every subset's visible region and depth range in that view:
+ * splx_view_regions projects the K subsets (device pointers, as for a batch) for `cam` and
+ * writes regions_out (host, [K][6] uint32: the visible region's tile rectangle x0, y0,
+ * ~x1, ~y1 and the FP32 depth bits min, ~max of the Gaussians the projection keeps; an
+ * empty subset gives 0xFFFFFFFF throughout).  Synchronises `stream`.  No device memory
+ * outlives the call. */
+int splx_view_regions(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
+                      const splx_camera* cam, const splx_opts* opts, uint32_t* regions_out,
+                      splx_stream_t stream);
+/* splx_render_partial of subset k of K with cross-boundary filtering: cells (host, [K][6]
+ * floats, the k-d boxes lo x, y, z, hi x, y, z, +-INFINITY on open sides; NaN rejected) and
+ * regions (host, [K][6], from splx_view_regions for the same camera and options).  A
+ * Gaussian of subset k whose support box mu +- 3 s_max meets another cell s leaves the rays
+ * of every tile of its own list that lies in s's visible region when its depth lies in the
+ * overlap of the two subsets' depth ranges; its pairs there sort last and stay out of the
+ * tile's range, so the kept state's backward (splx_backward) follows the same lists.  The
+ * partial equals the batch's filtered partial of that subset bit for bit.  K in 1..64,
+ * 0 <= k < K, else SPLX_ERR_INVALID. */
+int splx_render_partial_filtered(splx_ctx_t ctx, const splx_gaussians* subset, int32_t k,
+                                 int32_t K, const float* cells, const uint32_t* regions,
+                                 const splx_camera* cam, const splx_opts* opts,
+                                 const splx_partial* out, splx_state_t* state_out,
+                                 splx_stream_t stream);
 
 /* Global composition (Sec. 4.1, Eq. 5): per pixel, orders the K partials by the
  * normalised depth D^m/(1-T^m) (ties to the lower index, empty subsets last) and

@@ -231,6 +231,12 @@ struct Plan {
   uint32_t* zr = nullptr;                  // [V][K][2] depth ranges (min, ~max bits)
   uint32_t* removed = nullptr;             // [n_tiles] pairs the filter removed per tile
   bool cross_filter = false;               // filter cross-boundary Gaussians per ray
+  bool depth_ranges = false;               // record depth ranges (zr) without filtering
+  // a per-view render's filter: every cell's visible region [ncells][4] and depth range
+  // [ncells][2] in this view (uploaded), and the cell of the plan's one subset
+  uint32_t* omega_x = nullptr;
+  uint32_t* zr_x = nullptr;
+  int ncells = 0, cell_self = -1;
   void* scan_temp = nullptr;
   int64_t capacity = 0, n_tiles = 0, total_pixels = 0;
   splx_opts opts{};
@@ -292,11 +298,18 @@ struct Plan {
     b.persist_grid = persist_grid;
     b.work_ctr = work_ctr;
     b.omega = visibility ? omega : nullptr;
-    const bool cf = cross_filter && visibility && omega && cells_d && cross && zr && removed;
+    // the filter needs the cells' visible regions: the batch's own (visibility on) or, for a
+    // per-view render, the uploaded ones
+    const bool cf = cross_filter && (omega_x || (visibility && omega)) && cells_d && cross &&
+                    zr && removed;
     b.cells = cf ? cells_d : nullptr;
     b.cross = cf ? cross : nullptr;
-    b.zr = cf ? zr : nullptr;
+    b.zr = cf || (depth_ranges && zr) ? zr : nullptr;
     b.removed = cf ? removed : nullptr;
+    b.omega_x = omega_x ? omega_x : omega;
+    b.zr_x = zr_x ? zr_x : zr;
+    b.ncells = ncells > 0 ? ncells : K;
+    b.cell_self = cell_self;
     b.order = nullptr;  // set per launch by the forward's waves
     b.wave = 0;
     b.tpre = tpre;
@@ -318,7 +331,8 @@ struct Plan {
                    (void**)&chunk_count, (void**)&ranges,
                    (void**)&grad2d, (void**)&scan_temp, (void**)&counters, (void**)&work_ctr,
                    (void**)&order_d, (void**)&tpre, (void**)&omega, (void**)&cells_d,
-                   (void**)&cross, (void**)&zr, (void**)&removed};
+                   (void**)&cross, (void**)&zr, (void**)&removed, (void**)&omega_x,
+                   (void**)&zr_x};
     for (void** p : ps) free_ptr(*p, s);
     for (auto& e : ev)
       if (e) { cudaEventDestroy(e); e = nullptr; }
@@ -335,10 +349,9 @@ struct Plan {
     CK(cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(n_tiles, 1), s));
     if (visibility && omega)
       CK(cudaMemsetAsync(omega, 0xFF, sizeof(uint32_t) * 4 * (size_t)V * K, s));
-    if (b.zr) {
-      CK(cudaMemsetAsync(zr, 0xFF, sizeof(uint32_t) * 2 * (size_t)V * K, s));
+    if (b.zr) CK(cudaMemsetAsync(zr, 0xFF, sizeof(uint32_t) * 2 * (size_t)V * K, s));
+    if (b.removed)
       CK(cudaMemsetAsync(removed, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(n_tiles, 1), s));
-    }
     CK(cudaMemsetAsync(big_count, 0, 2 * sizeof(unsigned), s));
     CK(cudaMemsetAsync(chunk_count, 0, sizeof(unsigned), s));
     mark(0, s);
@@ -543,9 +556,18 @@ size_t splx_scratch_bytes(splx_ctx_t c) {
   return c->in_use;
 }
 
-int splx_render_partial(splx_ctx_t ctx, const splx_gaussians* subset, const splx_camera* cam,
-                        const splx_opts* opts, const splx_partial* out, splx_state_t* state_out,
-                        splx_stream_t stream) {
+// The filter of a per-view render (splx_render_partial_filtered): K cells, this subset's
+// cell k, the cells' boxes and their visible regions and depth ranges in the view.
+struct ViewFilter {
+  int K, k;
+  const float* cells;      // host [K][6]
+  const uint32_t* regions; // host [K][6]
+};
+
+static int render_partial_impl(splx_ctx_t ctx, const splx_gaussians* subset,
+                               const splx_camera* cam, const splx_opts* opts,
+                               const splx_partial* out, splx_state_t* state_out,
+                               splx_stream_t stream, const ViewFilter* vf) {
   if (!ctx || !out || !out->rgb || !out->T || !out->depth || !out->last) return SPLX_ERR_INVALID;
   int r;
   if ((r = check_gaussians(subset)) || (r = check_cam(cam)) || (r = check_opts(opts))) return r;
@@ -569,6 +591,31 @@ int splx_render_partial(splx_ctx_t ctx, const splx_gaussians* subset, const splx
     return code;
   };
   if ((r = P.alloc_common(s))) return fail(r);
+  if (vf) {
+    // the batch's filter with this subset as cell k of K, the cells' visible regions and
+    // depth ranges from `regions`; every tile is rendered (tiles outside the subset's own
+    // region have no pairs and come out empty, as the batch's composite reads them)
+    if ((r = ctx_alloc_t(ctx, &P.cells_d, (size_t)6 * vf->K, s))) return fail(r);
+    if ((r = ctx_alloc_t(ctx, &P.cross, (size_t)std::max<int64_t>(P.N, 1), s))) return fail(r);
+    if ((r = ctx_alloc_t(ctx, &P.zr, 2, s))) return fail(r);
+    if ((r = ctx_alloc_t(ctx, &P.removed, (size_t)std::max<int64_t>(P.n_tiles, 1), s)))
+      return fail(r);
+    if ((r = ctx_alloc_t(ctx, &P.omega_x, (size_t)4 * vf->K, s))) return fail(r);
+    if ((r = ctx_alloc_t(ctx, &P.zr_x, (size_t)2 * vf->K, s))) return fail(r);
+    std::vector<uint32_t> om((size_t)4 * vf->K), zr((size_t)2 * vf->K);
+    for (int c = 0; c < vf->K; ++c) {
+      for (int e = 0; e < 4; ++e) om[(size_t)4 * c + e] = vf->regions[(size_t)6 * c + e];
+      for (int e = 0; e < 2; ++e) zr[(size_t)2 * c + e] = vf->regions[(size_t)6 * c + 4 + e];
+    }
+    CK(cudaMemcpyAsync(P.cells_d, vf->cells, sizeof(float) * 6 * vf->K, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(P.omega_x, om.data(), sizeof(uint32_t) * om.size(),
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(P.zr_x, zr.data(), sizeof(uint32_t) * zr.size(), cudaMemcpyHostToDevice,
+                       s));
+    P.cross_filter = true;
+    P.ncells = vf->K;
+    P.cell_self = vf->k;
+  }
   if ((r = P.project_and_count(s))) return fail(r);
   uint64_t total = 0;
   if ((r = P.read_total(&total, s))) return fail(r);
@@ -592,6 +639,76 @@ int splx_render_partial(splx_ctx_t ctx, const splx_gaussians* subset, const splx
   if (!state_out) return fail(SPLX_OK);
   *state_out = st;
   return SPLX_OK;
+}
+
+int splx_render_partial(splx_ctx_t ctx, const splx_gaussians* subset, const splx_camera* cam,
+                        const splx_opts* opts, const splx_partial* out, splx_state_t* state_out,
+                        splx_stream_t stream) {
+  return render_partial_impl(ctx, subset, cam, opts, out, state_out, stream, nullptr);
+}
+
+int splx_render_partial_filtered(splx_ctx_t ctx, const splx_gaussians* subset, int32_t k,
+                                 int32_t K, const float* cells, const uint32_t* regions,
+                                 const splx_camera* cam, const splx_opts* opts,
+                                 const splx_partial* out, splx_state_t* state_out,
+                                 splx_stream_t stream) {
+  if (!cells || !regions || K < 1 || K > 64 || k < 0 || k >= K) return SPLX_ERR_INVALID;
+  for (int i = 0; i < 6 * K; ++i)
+    if (std::isnan(cells[i])) return SPLX_ERR_INVALID;
+  const ViewFilter vf{K, k, cells, regions};
+  return render_partial_impl(ctx, subset, cam, opts, out, state_out, stream, &vf);
+}
+
+int splx_view_regions(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
+                      const splx_camera* cam, const splx_opts* opts, uint32_t* regions_out,
+                      splx_stream_t stream) {
+  if (!ctx || !subsets || !regions_out || K < 1 || K > kMaxK) return SPLX_ERR_INVALID;
+  int r;
+  if ((r = check_cam(cam)) || (r = check_opts(opts))) return r;
+  int64_t N = 0;
+  for (int k = 0; k < K; ++k) {
+    if ((r = check_gaussians(&subsets[k]))) return r;
+    if (subsets[k].sh_degree != subsets[0].sh_degree) return SPLX_ERR_INVALID;
+    N += subsets[k].n;
+  }
+  CtxScope scope(ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Plan P;
+  P.ctx = ctx; P.V = 1; P.K = K; P.deg = subsets[0].sh_degree; P.tile = opts->tile; P.N = N;
+  P.opts = *opts;
+  int64_t goff = 0;
+  for (int k = 0; k < K; ++k) {
+    P.subsets_h.push_back(make_subset(subsets[k], goff));
+    goff += subsets[k].n;
+  }
+  P.views_h.push_back(make_view(*cam, opts->tile));
+  P.layout();
+  for (int k = 0; k < K; ++k) {
+    ImgDev im{};
+    P.imgs_h.push_back(im);
+  }
+  auto done = [&](int code) {
+    P.release(s);
+    return code;
+  };
+  if ((r = P.alloc_common(s))) return done(r);
+  if ((r = ctx_alloc_t(ctx, &P.omega, (size_t)4 * K, s))) return done(r);
+  if ((r = ctx_alloc_t(ctx, &P.zr, (size_t)2 * K, s))) return done(r);
+  P.visibility = true;
+  P.depth_ranges = true;
+  if ((r = P.project_and_count(s))) return done(r);
+  std::vector<uint32_t> om((size_t)4 * K), zr((size_t)2 * K);
+  cudaError_t e = cudaMemcpyAsync(om.data(), P.omega, sizeof(uint32_t) * om.size(),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(zr.data(), P.zr, sizeof(uint32_t) * zr.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return done(cuda_fail(e, "splx_view_regions"));
+  for (int k = 0; k < K; ++k) {
+    for (int i = 0; i < 4; ++i) regions_out[(size_t)6 * k + i] = om[(size_t)4 * k + i];
+    for (int i = 0; i < 2; ++i) regions_out[(size_t)6 * k + 4 + i] = zr[(size_t)2 * k + i];
+  }
+  return done(SPLX_OK);
 }
 
 namespace splx {

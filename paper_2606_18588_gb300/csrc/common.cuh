@@ -135,6 +135,14 @@ struct BatchDev {
   // per image tile, the pairs the filter removed: the fill gives them the largest depth,
   // so they sort last, and the tile's range ends before them (zero between runs)
   uint32_t* removed;
+  // the cells the filter compares against: ncells boxes in `cells`, their visible regions
+  // omega_x [V][ncells][4] and depth ranges zr_x [V][ncells][2] (the batch's own omega and
+  // zr, ncells = K); cell_self >= 0 names the one cell a per-view render's single subset
+  // belongs to (-1: subset k is cell k)
+  const uint32_t* omega_x;
+  const uint32_t* zr_x;
+  int ncells;
+  int cell_self;
   // saturation skipping (order != nullptr): the forward rasteriser runs in K waves; wave r
   // renders subset order[v * K + r] of every view v, and tpre [total pixels] holds the
   // product of the transmittances of the subsets rendered so far
@@ -264,15 +272,16 @@ __device__ __forceinline__ bool item_saturated(const BatchDev& b, int64_t id) {
 __device__ __forceinline__ bool cross_removed(const BatchDev& b, int v, int k,
                                               unsigned long long c, int tx, int ty,
                                               uint32_t dbits) {
-  const uint32_t* zk = b.zr + 2 * ((int64_t)v * b.K + k);
+  const int own = b.cell_self >= 0 ? b.cell_self : k;
+  const uint32_t* zk = b.zr_x + 2 * ((int64_t)v * b.ncells + own);
   const uint32_t kmin = zk[0], kmax = ~zk[1];
   while (c) {
     const int s = __ffsll((long long)c) - 1;
     c &= c - 1ull;
-    const uint4 o = reinterpret_cast<const uint4*>(b.omega)[v * b.K + s];
+    const uint4 o = reinterpret_cast<const uint4*>(b.omega_x)[v * b.ncells + s];
     const uint32_t x = (uint32_t)tx, y = (uint32_t)ty;
     if (x < o.x || y < o.y || x > ~o.z || y > ~o.w) continue;
-    const uint32_t* zs = b.zr + 2 * ((int64_t)v * b.K + s);
+    const uint32_t* zs = b.zr_x + 2 * ((int64_t)v * b.ncells + s);
     const uint32_t lo = max(kmin, zs[0]), hi = min(kmax, ~zs[1]);
     if (dbits >= lo && dbits <= hi) return true;
   }

@@ -100,8 +100,9 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(const BatchDev b) {
     const float lo[3] = {fs(m[0], r3), fs(m[1], r3), fs(m[2], r3)};
     const float hi[3] = {fa(m[0], r3), fa(m[1], r3), fa(m[2], r3)};
     unsigned long long mask = 0ull;
-    for (int c = 0; c < b.K; ++c) {
-      if (c == k) continue;
+    const int own = b.cell_self >= 0 ? b.cell_self : k;
+    for (int c = 0; c < b.ncells; ++c) {
+      if (c == own) continue;
       const float* cb = b.cells + 6 * c;
       if (lo[0] <= cb[3] && hi[0] >= cb[0] && lo[1] <= cb[4] && hi[1] >= cb[1] &&
           lo[2] <= cb[5] && hi[2] >= cb[2])

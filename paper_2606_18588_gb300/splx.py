@@ -107,6 +107,9 @@ _sigs = {
     "splx_graph_begin": (C.c_int, [_P, _P]),
     "splx_graph_end": (C.c_int, [_P, _P, C.POINTER(_P)]),
     "splx_graph_launch": (C.c_int, [_P, _P]),
+    "splx_view_regions": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P, _P]),
+    "splx_render_partial_filtered": (C.c_int, [_P, _P, C.c_int32, C.c_int32, _P, _P, _P, _P,
+                                               _P, _P, _P]),
     "splx_server_request_times": (C.c_int, [_P, C.c_int64, _P]),
     "splx_graph_set_timing_ring": (C.c_int, [_P, C.c_int32]),
     "splx_batch_kernel_times_slot": (C.c_int, [_P, _P, C.c_int32, _P]),
@@ -258,15 +261,41 @@ def _partial_struct(p) -> Partial:
 
 
 # ---------------------------------------------------------------- per-view entry points
+def view_regions(ctx: Context, subsets, cam, o: Opts, stream=None) -> np.ndarray:
+    """Every subset's visible region and depth range in one view ([K, 6] uint32), the input
+    of the per-view cross-boundary filter."""
+    c = cam if isinstance(cam, Camera) else camera(cam)
+    K = len(subsets)
+    sarr = (Gaussians * K)(*subsets)
+    out = np.zeros((K, 6), np.uint32)
+    _check(_lib.splx_view_regions(ctx.h, sarr, K, C.byref(c), C.byref(o),
+                                  out.ctypes.data_as(C.c_void_p), _stream(stream)),
+           "splx_view_regions")
+    return out
+
+
 def render_partial(ctx: Context, subset: Gaussians, cam, o: Opts, out: dict, keep_state=True,
-                   stream=None):
-    """Local render of one subset into `out` (a new_partial dict); returns a State."""
+                   stream=None, cross=None):
+    """Local render of one subset into `out` (a new_partial dict); returns a State.
+    cross = (k, cells [K, 2, 3], regions [K, 6]) turns on cross-boundary filtering with this
+    subset as cell k (regions from view_regions for the same camera)."""
     c = cam if isinstance(cam, Camera) else camera(cam)
     h = C.c_void_p()
     ps = _partial_struct(out)
-    _check(_lib.splx_render_partial(ctx.h, C.byref(subset), C.byref(c), C.byref(o), C.byref(ps),
-                                    C.byref(h) if keep_state else None, _stream(stream)),
-           "splx_render_partial")
+    if cross is None:
+        _check(_lib.splx_render_partial(ctx.h, C.byref(subset), C.byref(c), C.byref(o),
+                                        C.byref(ps), C.byref(h) if keep_state else None,
+                                        _stream(stream)), "splx_render_partial")
+    else:
+        k, cells, regions = cross
+        cl = np.ascontiguousarray(np.asarray(cells, np.float32).reshape(-1, 6))
+        rg = np.ascontiguousarray(np.asarray(regions, np.uint32).reshape(-1, 6))
+        if cl.shape[0] != rg.shape[0]:
+            raise ValueError("cells and regions must describe the same K subsets")
+        _check(_lib.splx_render_partial_filtered(
+            ctx.h, C.byref(subset), int(k), cl.shape[0], cl.ctypes.data_as(C.c_void_p),
+            rg.ctypes.data_as(C.c_void_p), C.byref(c), C.byref(o), C.byref(ps),
+            C.byref(h) if keep_state else None, _stream(stream)), "splx_render_partial_filtered")
     if not keep_state:
         return None
     st = State(ctx, h)

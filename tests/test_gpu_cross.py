@@ -93,3 +93,56 @@ def test_filter_changes_the_image_and_turns_off(ctx, case):
     assert torch.equal(rgb1, rgb0)
     b1.close()
     b0.close()
+
+
+def test_per_view_path_filters_as_the_batch_does(ctx, case):
+    """The per-view entry points with the filter (splx_view_regions, then
+    splx_render_partial_filtered for each subset, splx_composite, splx_backward) render the
+    batch's filtered images bit for bit and its gradients up to the atomics' order, and the
+    oracle's filtered image within the pixel tolerance and flip bounds."""
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import (GRAD_TOL, check_band, params_struct, rel_l2, subset_struct, to_device,
+                          zeros_like_params)
+    sc, off, boxes, cams = case
+    K = len(off) - 1
+    dev = to_device(sc)
+    subs = [subset_struct(dev, int(off[k]), int(off[k + 1]), sc.sh_degree) for k in range(K)]
+    b, rgb = _batch(ctx, dev, off, cams, sc.sh_degree, boxes)
+    rng = np.random.default_rng(11)
+    dL = torch.from_numpy(rng.standard_normal(b.rgb_off[-1]).astype(np.float32)).cuda()
+    g_b = zeros_like_params(dev)
+    b.backward(dL, None, [params_struct(g_b, int(off[k]), int(off[k + 1]), sc.sh_degree)
+                          for k in range(K)])
+    torch.cuda.synchronize()
+    views_b = b.views(rgb)
+    g_v = zeros_like_params(dev)
+    o = S.opts()
+    for v, cam in enumerate(cams):
+        regions = S.view_regions(ctx, subs, cam, o)
+        parts, states = [], []
+        for k in range(K):
+            p = S.new_partial(cam.height, cam.width)
+            states.append(S.render_partial(ctx, subs[k], cam, o, p, cross=(k, boxes, regions)))
+            parts.append(p)
+        img = torch.empty(3, cam.height, cam.width, device="cuda")
+        S.composite(ctx, parts, cam.width, cam.height, o, img)
+        torch.cuda.synchronize()
+        assert torch.equal(img, views_b[v]), v
+        dLv = dL[b.rgb_off[v]:b.rgb_off[v + 1]].view(3, cam.height, cam.width).contiguous()
+        S.backward(ctx, subs, cam, parts, states, dLv, None, o,
+                   [params_struct(g_v, int(off[k]), int(off[k + 1]), sc.sh_degree)
+                    for k in range(K)])
+        torch.cuda.synchronize()
+        for st in states:
+            st.close()
+        ref = O.render_view(sc, off, cam, O.opts(), cells=boxes, bounds=True)
+        check_band(img.cpu().numpy(), ref["image"], ref["amb"], ref["flip"]["image"],
+                   label=f"per-view filtered view {v}")
+    b.close()
+    for k in GROUPS:
+        assert rel_l2(g_v[k].cpu().numpy(), g_b[k].cpu().numpy()) <= 1e-5, k
+    # a regions table that is not the view's is the caller's to get right; a bad index is not
+    with pytest.raises(S.SplxError):
+        S.render_partial(ctx, subs[0], cams[0], o, S.new_partial(cams[0].height, cams[0].width),
+                         cross=(K, boxes, S.view_regions(ctx, subs, cams[0], o)))
+    assert GRAD_TOL > 1e-5
