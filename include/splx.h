@@ -261,7 +261,10 @@ int splx_batch_destroy(splx_batch_t b);
  * each of its kernels; inside a captured graph they become event nodes, so every replay
  * re-records them.  splx_batch_kernel_times waits for the last run's final event and
  * writes 9 durations in ms (host array): project, scan, fill, sort, raster_fwd,
- * composite, composite_bwd, raster_bwd, project_bwd. */
+ * composite, composite_bwd, raster_bwd, project_bwd.  With saturation skipping on and at
+ * least two views, the waves of up to four view groups (about equal pixels each) run side
+ * by side on their own streams; sort and raster_fwd are then the first group's stream's
+ * intervals, which add up to the waves' whole span. */
 int splx_batch_set_timing(splx_batch_t b, int enable);
 /* Launch shape of the batch's rasterisers (the autotuner's second axis beside the tile
  * side; Sec. 4.3's aim of keeping every SM busy).  raster_ctas_per_sm = 0 launches one

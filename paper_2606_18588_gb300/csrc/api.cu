@@ -222,6 +222,16 @@ struct Plan {
   unsigned long long* counters = nullptr;  // [kCounters]: see BatchDev::counters
   unsigned long long* work_ctr = nullptr;  // [2]: persistent rasterisers' work counters
   int persist_grid = 0;                    // persistent raster grid (0: one CTA per item)
+  // saturation-skipping waves of view groups side by side (batches): group g > 0 runs on
+  // side[g - 1] with its own long-segment lists; fork / join events
+  static constexpr int kGroups = 4;
+  bool split_views = false;
+  cudaStream_t side[kGroups - 1] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kGroups - 1] = {};
+  uint32_t* big_list_g[kGroups - 1] = {};
+  unsigned* big_count_g[kGroups - 1] = {};
+  uint2* chunks_g[kGroups - 1] = {};
+  unsigned* chunk_count_g[kGroups - 1] = {};
   int32_t* order_d = nullptr;              // [V][K] front-to-back subset order (skipping on)
   uint32_t* omega = nullptr;               // [V][K][4] visible regions (internal partials only)
   bool visibility = false;                 // use omega (batches and server launches)
@@ -312,6 +322,8 @@ struct Plan {
     b.cell_self = cell_self;
     b.order = nullptr;  // set per launch by the forward's waves
     b.wave = 0;
+    b.item_lo = 0;
+    b.item_n = K > 0 ? n_tiles / K : 0;
     b.tpre = tpre;
     // composite-only plans carry no subsets; their offsets are unused
     for (int k = 0; k <= K; ++k) b.goff[k] = k < (int)subsets_h.size() ? subsets_h[k].goff : N;
@@ -334,6 +346,15 @@ struct Plan {
                    (void**)&cross, (void**)&zr, (void**)&removed, (void**)&omega_x,
                    (void**)&zr_x};
     for (void** p : ps) free_ptr(*p, s);
+    for (int g = 0; g < kGroups - 1; ++g) {
+      free_ptr((void*&)big_list_g[g], s);
+      free_ptr((void*&)big_count_g[g], s);
+      free_ptr((void*&)chunks_g[g], s);
+      free_ptr((void*&)chunk_count_g[g], s);
+      if (side[g]) { cudaStreamSynchronize(side[g]); cudaStreamDestroy(side[g]); side[g] = nullptr; }
+      if (join_ev[g]) { cudaEventDestroy(join_ev[g]); join_ev[g] = nullptr; }
+    }
+    if (fork_ev) { cudaEventDestroy(fork_ev); fork_ev = nullptr; }
     for (auto& e : ev)
       if (e) { cudaEventDestroy(e); e = nullptr; }
     for (auto& e : wev)
@@ -380,20 +401,61 @@ struct Plan {
 
   // Forward rasterisation with saturation skipping: per wave, sort the wave's segments
   // (those of saturated items are left unsorted) and render them.
+  // Saturation skipping: K waves, wave r sorting and rendering subset order[v][r] of every
+  // view v after the waves before it (the prefix transmittance it reads).  With
+  // split_views the views form up to kGroups groups of about equal pixels whose waves run
+  // on their own streams, so that one group's kernels fill the others' wave tails; the
+  // groups share nothing but the read-only inputs.
   int waves(const BatchDev& b, cudaStream_t s) {
+    const int64_t nw = n_tiles / K;
+    // first view of each group; groups[G] = V
+    int G = 1, first[kGroups + 1] = {0};
+    if (split_views && persist_grid == 0 && V >= 2) {
+      G = std::min(kGroups, V);
+      for (int g = 1; g < G; ++g) {
+        // the view whose start is nearest to g / G of the pixels, after the previous group's
+        int v = first[g - 1] + 1;
+        while (v < V - (G - g) && G * (pix_off[v] + pix_off[v + 1]) <= 2 * g * pix_off[V]) ++v;
+        first[g] = v;
+      }
+    }
+    first[G] = V;
+    mark_wave(0, s);
+    if (G > 1) {
+      CK(cudaEventRecord(fork_ev, s));
+      for (int g = 1; g < G; ++g) CK(cudaStreamWaitEvent(side[g - 1], fork_ev, 0));
+    }
     for (int r = 0; r < K; ++r) {
-      BatchDev bw = b;
-      bw.order = order_d;
-      bw.wave = r;
-      mark_wave(2 * r, s);
-      CK(cudaMemsetAsync(big_count, 0, 2 * sizeof(unsigned), s));
-      CK(cudaMemsetAsync(chunk_count, 0, sizeof(unsigned), s));
-      launch_seg_sort(bw, merge_rounds_bound(max_subset()), s);
+      BatchDev bg[kGroups];
+      for (int g = 0; g < G; ++g) {
+        BatchDev& bw = bg[g];
+        bw = b;
+        bw.order = order_d;
+        bw.wave = r;
+        bw.item_lo = tile_base[first[g]] / K;
+        bw.item_n = tile_base[first[g + 1]] / K - bw.item_lo;
+        if (g > 0) {
+          bw.big_list = big_list_g[g - 1]; bw.big_count = big_count_g[g - 1];
+          bw.chunks = chunks_g[g - 1]; bw.chunk_count = chunk_count_g[g - 1];
+        }
+      }
+      if (r > 0) mark_wave(2 * r, s);
+      for (int g = 0; g < G; ++g) {
+        cudaStream_t sg = g ? side[g - 1] : s;
+        CK(cudaMemsetAsync(bg[g].big_count, 0, 2 * sizeof(unsigned), sg));
+        CK(cudaMemsetAsync(bg[g].chunk_count, 0, sizeof(unsigned), sg));
+        launch_seg_sort(bg[g], merge_rounds_bound(max_subset()), sg);
+      }
       mark_wave(2 * r + 1, s);
-      launch_raster_fwd(bw, s);
+      for (int g = 0; g < G; ++g) launch_raster_fwd(bg[g], g ? side[g - 1] : s);
       CK_LAUNCH();
     }
+    for (int g = 1; g < G; ++g) {
+      CK(cudaEventRecord(join_ev[g - 1], side[g - 1]));
+      CK(cudaStreamWaitEvent(s, join_ev[g - 1], 0));
+    }
     mark_wave(2 * K, s);
+    (void)nw;
     return SPLX_OK;
   }
 
@@ -410,6 +472,26 @@ struct Plan {
     if ((r = ctx_alloc_t(ctx, &keys, (size_t)std::max<int64_t>(cap, 1), s))) return r;
     if ((r = ctx_alloc_t(ctx, &keys_alt, (size_t)std::max<int64_t>(cap, 1), s))) return r;
     if ((r = ctx_alloc_t(ctx, &chunks, (size_t)chunk_list_capacity(n_tiles, cap), s))) return r;
+    if (split_views)
+      for (int g = 0; g < kGroups - 1; ++g)
+        if ((r = ctx_alloc_t(ctx, &chunks_g[g], (size_t)chunk_list_capacity(n_tiles, cap), s)))
+          return r;
+    return SPLX_OK;
+  }
+
+  // The other view groups' streams, events and long-segment lists (split_views).
+  int alloc_split(cudaStream_t s) {
+    int r;
+    const size_t nt = (size_t)std::max<int64_t>(n_tiles, 1);
+    for (int g = 0; g < kGroups - 1; ++g) {
+      if ((r = ctx_alloc_t(ctx, &big_list_g[g], nt, s))) return r;
+      if ((r = ctx_alloc_t(ctx, &big_count_g[g], 2, s))) return r;
+      if ((r = ctx_alloc_t(ctx, &chunk_count_g[g], 1, s))) return r;
+      CK(cudaStreamCreateWithFlags(&side[g], cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&join_ev[g], cudaEventDisableTiming));
+    }
+    CK(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+    split_views = true;
     return SPLX_OK;
   }
 
@@ -1013,6 +1095,7 @@ int splx_batch_create(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
     }
   }
   if ((r = P.alloc_common(s))) return fail(r);
+  if (V >= 2 && (r = P.alloc_split(s))) return fail(r);
   if ((r = ctx_alloc_t(ctx, &P.grad2d, (size_t)V * N * 3, s))) return fail(r);
   if ((r = ctx_alloc_t(ctx, &P.counters, kCounters, s))) return fail(r);
   if ((r = ctx_alloc_t(ctx, &P.work_ctr, 2, s))) return fail(r);

@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(kBigThreads) k_merge_fixup(const BatchDev b) {
 
 void launch_seg_sort(const BatchDev& b, int max_rounds, cudaStream_t s) {
   if (b.n_tiles == 0) return;
-  const int64_t items = b.order ? b.n_tiles / b.K : b.n_tiles;
+  const int64_t items = b.order ? b.item_n : b.n_tiles;
   k_seg_sort_small<<<(unsigned)items, kSortThreads, 0, s>>>(b);
   const unsigned grid = (unsigned)device_sm_count() * 4;
   // 72 KB of dynamic shared memory: opted in once per device (a refused opt-in shows as

@@ -148,6 +148,9 @@ struct BatchDev {
   // product of the transmittances of the subsets rendered so far
   const int32_t* order;
   int wave;
+  // a wave launch covers wave items [item_lo, item_lo + item_n) of the n_tiles / K (views
+  // in order), so that groups of views can run their waves side by side
+  int64_t item_lo, item_n;
   float* tpre;
   // persistent rasterisers: grid size (0 = one CTA per work item) and the two work
   // counters they take items from ([0] forward, [1] backward; reset before each launch)
@@ -236,6 +239,7 @@ __device__ __forceinline__ int view_of(const int64_t* base, int V, int64_t x) {
 // tiles of subset order[v][wave] of every view v (n_tiles / K items).
 __device__ __forceinline__ int64_t item_of(const BatchDev& b, int64_t w) {
   if (!b.order) return w;
+  w += b.item_lo;
   const int v = view_of(b.tile_base, b.V, w * b.K);
   const int64_t nt = (b.tile_base[v + 1] - b.tile_base[v]) / b.K;
   const int k = b.order[v * b.K + b.wave];
@@ -243,7 +247,7 @@ __device__ __forceinline__ int64_t item_of(const BatchDev& b, int64_t w) {
 }
 
 __device__ __forceinline__ int64_t items_of_launch(const BatchDev& b) {
-  return b.order ? b.n_tiles / b.K : b.n_tiles;
+  return b.order ? b.item_n : b.n_tiles;
 }
 
 // Saturation skipping test of work item `id` in a wave after the first: true if every pixel

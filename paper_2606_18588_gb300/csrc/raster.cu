@@ -611,7 +611,7 @@ static bool counting(const BatchDev& b, cudaStream_t s) {
 template <int TS, bool kCount, bool kPersist>
 static void launch_fwd_k(const BatchDev& b, cudaStream_t s) {
   constexpr int P = PptFwd<TS>::value;
-  const int64_t items = b.order ? b.n_tiles / b.K : b.n_tiles;
+  const int64_t items = b.order ? b.item_n : b.n_tiles;
   const unsigned grid = kPersist ? (unsigned)std::min<int64_t>(items, (int64_t)b.persist_grid)
                                  : (unsigned)items;
   k_raster_fwd<TS, P, kCount, kPersist><<<grid, TS * TS / P, 0, s>>>(b);
