@@ -246,10 +246,11 @@ def roofline(name, ms, counts, w, pk):
 
 
 # ---------------------------------------------------------------- CPU oracle leg
-def oracle_sample(sc, off, cam, frac, seed=0, reps=1):
+def oracle_sample(sc, off, cam, frac, seed=0, reps=1, fixed_s=None):
     """Times the FP64 oracle's forward (local renders + composite) and backward on one view,
     restricted to a seeded fraction of its tiles, and once with no tiles (the fixed
-    projection / binning cost).  Returns (extrapolated full-view seconds, info)."""
+    projection / binning cost; `fixed_s` reuses an earlier measurement of it).  Returns
+    (extrapolated full-view seconds, info, threads, fixed seconds)."""
     import numpy as np
     from oracle import oracle as O
     o = O.opts()
@@ -267,13 +268,13 @@ def oracle_sample(sc, off, cam, frac, seed=0, reps=1):
         O.render_view(sc, off, cam, o, tile_mask=m)
         O.backward_view(sc, off, cam, dl, None, o, tile_mask=m)
         return time.perf_counter() - t
-    t0 = min(run(empty) for _ in range(reps))
+    t0 = fixed_s if fixed_s is not None else min(run(empty) for _ in range(reps))
     t1 = min(run(mask) for _ in range(reps))
     full = t0 + max(t1 - t0, 0.0) * nt / k
     info = (f"1 view {cam.width}x{cam.height}, all {len(off) - 1} subsets, forward+backward on "
             f"{k}/{nt} seeded tiles ({t1:.1f} s) plus the fixed projection/binning cost "
             f"({t0:.1f} s, no tiles), extrapolated to the full view")
-    return full, info, O.num_threads()
+    return full, info, O.num_threads(), t0
 
 
 def cpu_baseline_small():
@@ -292,7 +293,7 @@ def cpu_baseline_small():
     out["plain_10k_sh0_256"] = {"value": cam.width * cam.height / dt / 1e6, "unit": UNIT,
                                 "pass": "forward", "sample": "whole view", "seconds": dt}
     sc, off, _, cams = I.cluster_case(1_000_000, 2, 4, 1, [(1920, 1080)])
-    full, info, _ = oracle_sample(sc, off, cams[0], 1.0 / 64.0)
+    full, info, _, _ = oracle_sample(sc, off, cams[0], 1.0 / 64.0)
     out["fwdbwd_1m_k4_1080p"] = {"value": cams[0].width * cams[0].height / full / 1e6,
                                  "unit": UNIT, "pass": "forward+backward", "sample": info}
     return out
@@ -308,8 +309,10 @@ def run_reference(args):
     cam = cams[0]
     times = []
     info = ""
+    fixed = None  # the no-tile projection cost, measured once (steps differ in their tiles)
     for i in range(args.warmup + args.steps):
-        full, info, cores = oracle_sample(sc, off, cam, args.cpu_tile_fraction, seed=i)
+        full, info, cores, fixed = oracle_sample(sc, off, cam, args.cpu_tile_fraction, seed=i,
+                                                 fixed_s=fixed)
         if i >= args.warmup:
             times.append(full)
     sec = statistics.mean(times)
@@ -778,7 +781,7 @@ def main():
     # ---- CPU oracle baselines (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            full, info, cores = oracle_sample(sc, off, cams[0], args.cpu_tile_fraction)
+            full, info, cores, _ = oracle_sample(sc, off, cams[0], args.cpu_tile_fraction)
             line["cpu_baseline"] = {"value": cams[0].width * cams[0].height / full / 1e6,
                                     "unit": UNIT, "cores": cores, "kind": "oracle", "sample": info}
             line["cpu_baseline"]["other_configs"] = cpu_baseline_small()

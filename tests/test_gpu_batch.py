@@ -92,6 +92,43 @@ def test_graph_replay_is_identical(ctx, scene):
     b.close()
 
 
+def test_graph_timing_ring_reads_every_replay(ctx, scene):
+    """The timing ring: each back-to-back replay of a captured training step records the
+    batch's kernel events into its own slot, every slot reads back (no host wait between
+    the replays), and once the ring is removed the graph replays and times as before (its
+    event nodes point at the captured events again)."""
+    from paper_2606_18588_gb300 import splx as S
+    from paper_2606_18588_gb300.train import BatchedStep
+    from gpu_util import to_device
+    sc, off, cams = scene
+    dev = to_device(sc)
+    s = torch.cuda.Stream()
+    tg = [torch.from_numpy(I.random_image(c.height, c.width, 5 + i)) for i, c in enumerate(cams)]
+    with torch.cuda.stream(s):
+        st = BatchedStep(ctx, dev, off, sc.sh_degree, cams, tg, S.opts(), stream=s)
+        st.batch.set_timing(True)
+        st.run()
+        s.synchronize()
+        st.capture()
+        for ring in (4, 3):  # a second ring replaces the first
+            st.graph.set_timing_ring(ring)
+            for _ in range(ring):
+                st.replay()
+            s.synchronize()
+            for i in range(ring):
+                t = st.batch.kernel_times(st.graph, i)
+                assert all(v >= 0 for v in t.values())
+                assert t["project"] > 0 and t["raster_fwd"] > 0 and t["raster_bwd"] > 0
+        with pytest.raises(S.SplxError):
+            st.batch.kernel_times(st.graph, ring)  # outside the ring
+        st.graph.set_timing_ring(0)
+        st.replay()
+        s.synchronize()
+        assert st.status()[0] == S.OK
+        assert st.batch.kernel_times()["raster_bwd"] > 0
+    st.close()
+
+
 def test_capacity_overflow_is_reported_not_faulted(ctx, scene):
     from paper_2606_18588_gb300 import splx as S
     from gpu_util import to_device
