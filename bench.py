@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--unfused-adam", action="store_true",
+                    help="backward into gradient arrays and a separate Adam pass")
     ap.add_argument("--no-skip", action="store_true",
                     help="render every (view, subset, tile) item (no saturation skipping)")
     ap.add_argument("--cpu-tile-fraction", type=float, default=1.0 / 48.0)
@@ -224,7 +226,13 @@ def roofline(name, ms, counts, w, pk):
     elif name == "project":
         byts = N * param_bytes + V * N * (64 + 4)
     elif name == "project_bwd":
-        byts = N * (3 * param_bytes) + V * N * 96
+        if w.get("fused_adam"):
+            # gradient from the views' 2-D gradients (read and cleared), then Adam in place:
+            # read p, m, v and write p, m, v once
+            byts = N * (6 * param_bytes) + V * N * 96
+            note = "Adam fused in: read p, m, v; write p, m, v; no gradient array"
+        else:
+            byts = N * (3 * param_bytes) + V * N * 96
     elif name == "fill":
         byts = V * N * (4 + 32) + counts["pairs"] * 8
     elif name in ("composite", "composite_bwd"):
@@ -232,6 +240,9 @@ def roofline(name, ms, counts, w, pk):
         byts = pixels * (16 if name == "composite" else 12) + int(pixels * K * per * inside)
         note = (f"partial planes counted only inside the visible regions ({inside:.3f} of the "
                 "work items)")
+    elif name == "adam" and w.get("fused_adam"):
+        byts = pixels * 3 * 12
+        note = "the L1 loss alone (Adam runs inside project_bwd)"
     elif name == "adam":
         byts = N * param_bytes // 4 * 32 + pixels * 3 * 12
         note = "Adam over every parameter (read p, g, m, v; write p, m, v, g = 0) and the L1 loss"
@@ -420,7 +431,8 @@ def city_leg(args, rank, world, local, steps, warmup):
         del rgb
         cap = int(need * 1.05) + 1024
         st = BatchedStep(ctx, dev, layout.offsets, layout.sh_degree, views[0], None, o,
-                         pair_capacity=cap, stream=stream, order=orders[0])
+                         pair_capacity=cap, stream=stream, order=orders[0],
+                         fused_adam=not args.unfused_adam)
         st.set_targets(tgt[0])
         st.run()
         stream.synchronize()
@@ -530,7 +542,7 @@ def batched_leg(args, ctx, dev, sc, off, cams, targets, o, ctas, order, stream, 
     from paper_2606_18588_gb300.train import BatchedStep
     with torch.cuda.stream(stream):
         st = BatchedStep(ctx, dev, off, sc.sh_degree, cams, [torch.from_numpy(t) for t in targets],
-                         o, stream=stream, order=order)
+                         o, stream=stream, order=order, fused_adam=not args.unfused_adam)
         st.batch.set_timing(True)
         st.batch.set_launch(ctas)
         st.run()  # eager once: sizes everything, checks status
@@ -559,7 +571,8 @@ def batched_leg(args, ctx, dev, sc, off, cams, targets, o, ctas, order, stream, 
     kmean["loss+adam"] = max(ms - sum(kmean.values()), 0.0)
     return st, {"ms": ms, "step_ms_median": max_over_ranks(statistics.median(step_ms)),
                 "value": st.pixels * world / (ms / 1e3) / 1e6, "kmean": kmean,
-                "counts": counts, "launches_per_step": launches_per_step}
+                "counts": counts, "launches_per_step": launches_per_step,
+                "fused_adam": st.fused_adam}
 
 
 def plain_leg(args, ctx, dev, sc, off, cams, targets, o, stream, barrier, world):
@@ -706,7 +719,7 @@ def main():
     # ---- roofline of the dominant kernel
     pk, pk_src = peaks()
     wl = {"V": len(cams), "N": sc.n, "K": len(off) - 1, "nc": (sc.sh_degree + 1) ** 2,
-          "pixels": pixels, "alu_peak": dpk["tflops"]}
+          "pixels": pixels, "alu_peak": dpk["tflops"], "fused_adam": head["fused_adam"]}
     cand = {k: v for k, v in kmean.items() if k != "loss+adam"}
     dom = max(cand, key=cand.get)
     roof = roofline(dom, cand[dom], counts, wl, pk)
@@ -721,7 +734,8 @@ def main():
     # on several streams side by side: only their span together is a kernel time, so the
     # forward's fraction is taken over that span (a lower bound) and the sort gets none
     overlapped = order is not None and len(cams) >= 2
-    for name in ("raster_fwd", "raster_bwd", "sort", "composite", "composite_bwd", "adam"):
+    for name in ("raster_fwd", "raster_bwd", "sort", "composite", "composite_bwd", "project",
+                 "project_bwd", "fill", "adam"):
         t = kmean.get("loss+adam" if name == "adam" else name)
         if overlapped and name == "sort":
             continue
@@ -749,6 +763,8 @@ def main():
                                "fill tile buckets, per-tile depth sort, raster fwd, composite, L1 "
                                "loss, composite bwd, raster bwd, project bwd, Adam)",
                        "saturation_skipping": order is not None,
+                       "adam": ("fused into the projection adjoint (kernel_ms project_bwd)"
+                                if head["fused_adam"] else "separate pass over the gradients"),
                        "waves": ("sort + raster_fwd of up to 4 view groups on their own "
                                  "streams, side by side; kernel_ms sort and raster_fwd are the "
                                  "first group's stream's intervals, their sum the waves' span")

@@ -253,6 +253,23 @@ int splx_batch_forward(splx_batch_t b, float* out_rgb, float* out_T, splx_stream
  * outputs; gradients added into grads[k] (host array of K).  Capturable. */
 int splx_batch_backward(splx_batch_t b, const float* dL_drgb, const float* dL_dT,
                         const splx_params* grads, splx_stream_t stream);
+/* Backward of the last forward with the Adam step fused into the projection adjoint
+ * (Sec. 4.1 step 3): the same result as splx_batch_backward into zeroed gradients followed
+ * by splx_step_device over every subset, but no gradient array exists; each Gaussian's
+ * parameters, first and second moments are updated straight from its gradient of this
+ * backward (Gaussians without one take a zero gradient, as after zero_grad).
+ *   params[k]  device arrays of subset k's Gaussians, the very arrays the batch was
+ *              created on (checked: SPLX_ERR_INVALID otherwise); overwritten in place.
+ *   m[k], v[k] device Adam moments of subset k (same layout), updated in place.
+ *   hp         learning rates, betas, eps (zero_grad is ignored: there is no gradient).
+ *   step_dev   device int64 step counter, incremented first; the update uses the new value.
+ * Host arrays params, m, v hold K entries each; nothing is owned by the call.  Never
+ * synchronises; capturable once the batch exists.  Per-element arithmetic is that of
+ * splx_step, so both routes give bit-identical parameters. */
+int splx_batch_backward_adam(splx_batch_t b, const float* dL_drgb, const float* dL_dT,
+                             const splx_params* params, const splx_params* m,
+                             const splx_params* v, const splx_adam* hp, int64_t* step_dev,
+                             splx_stream_t stream);
 /* Total pairs of the last forward and the device status word (synchronises).  Returns
  * SPLX_ERR_CAPACITY if the pair list overflowed (its forward output is invalid). */
 int splx_batch_status(splx_batch_t b, int64_t* pairs_out, splx_stream_t stream);

@@ -1202,6 +1202,58 @@ int splx_batch_backward(splx_batch_t bt, const float* dL_drgb, const float* dL_d
   return SPLX_OK;
 }
 
+int splx_batch_backward_adam(splx_batch_t bt, const float* dL_drgb, const float* dL_dT,
+                             const splx_params* params, const splx_params* m,
+                             const splx_params* v, const splx_adam* hp, int64_t* step_dev,
+                             splx_stream_t stream) {
+  if (!bt || !dL_drgb || !params || !m || !v || !hp || !step_dev) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  if (!bt->forward_done) return SPLX_ERR_STATE;
+  AdamTable at;
+  std::memset(&at, 0, sizeof(at));
+  for (int k = 0; k < P.K; ++k) {
+    const SubsetDev& S = P.subsets_h[k];
+    if (S.n == 0) continue;
+    const splx_params* t[3] = {&params[k], &m[k], &v[k]};
+    for (int j = 0; j < 3; ++j) {
+      const splx_params& q = *t[j];
+      if (q.n != S.n || q.sh_degree != P.deg || !q.means || !q.log_scales || !q.quats ||
+          !q.opacity_logits || !q.sh)
+        return SPLX_ERR_INVALID;
+    }
+    // the adjoint reads the batch's own parameter arrays, which this call then updates
+    const splx_params& q = params[k];
+    if (q.means != S.means || q.log_scales != S.log_scales || q.quats != S.quats ||
+        q.opacity_logits != S.opacity_logits || q.sh != S.sh)
+      return SPLX_ERR_INVALID;
+    for (int j = 0; j < 3; ++j) {
+      const splx_params& r = *t[j];
+      float** dst = j == 0 ? at.p[k] : j == 1 ? at.m[k] : at.v[k];
+      dst[0] = r.means; dst[1] = r.log_scales; dst[2] = r.quats;
+      dst[3] = r.opacity_logits; dst[4] = r.sh;
+    }
+  }
+  for (int j = 0; j < 6; ++j) at.lr[j] = hp->lr[j];
+  at.b1 = hp->beta1;
+  at.b2 = hp->beta2;
+  at.eps = hp->eps;
+  at.step_dev = step_dev;
+  CtxScope scope(P.ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  BatchDev b = P.dev();
+  b.dL_drgb = dL_drgb;
+  b.dL_dT = dL_dT;
+  P.mark(7, s);
+  launch_composite_bwd(b, P.total_pixels, s);
+  P.mark(8, s);
+  launch_raster_bwd(b, s);
+  P.mark(9, s);
+  launch_project_bwd_adam(b, at, s);
+  P.mark(10, s);
+  CK_LAUNCH();
+  return SPLX_OK;
+}
+
 int splx_batch_set_timing(splx_batch_t bt, int enable) {
   if (!bt) return SPLX_ERR_INVALID;
   Plan& P = bt->plan;

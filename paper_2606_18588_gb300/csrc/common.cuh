@@ -168,6 +168,19 @@ struct GradTable {
   float* p[kMaxK][5];
 };
 
+// Adam state of the K subsets (parameters, first and second moments; arrays in the
+// GradTable order) and its hyperparameters: lr[0..4] per array, lr[5] the SH coefficients
+// above degree 0; the step number is *step_dev if non-NULL, else step.
+struct AdamTable {
+  float* p[kMaxK][5];
+  float* m[kMaxK][5];
+  float* v[kMaxK][5];
+  float lr[6];
+  float b1, b2, eps;
+  int64_t step;
+  const int64_t* step_dev;
+};
+
 __host__ __device__ inline int n_sh(int deg) { return (deg + 1) * (deg + 1); }
 
 // ---- launch wrappers (defined in the .cu files) ------------------------------------
@@ -186,6 +199,10 @@ void launch_raster_bwd(const BatchDev& b, cudaStream_t s);
 // Largest number of persistent rasteriser CTAs that fit on one SM (0 on error).
 int raster_max_ctas_per_sm(int tile, bool bwd);
 void launch_project_bwd(const BatchDev& b, const GradTable& gt, cudaStream_t s);
+// The projection adjoint with Adam fused in: every Gaussian of the batch is updated from its
+// gradient of this backward (zero where it has none) without materialising the gradient.
+// Increments *at.step_dev first when it is set.
+void launch_project_bwd_adam(const BatchDev& b, const AdamTable& at, cudaStream_t s);
 
 // exclusive scan of n u32 values (out has n+1 entries; out[n] = total)
 size_t scan_u32_temp_bytes(int64_t n);

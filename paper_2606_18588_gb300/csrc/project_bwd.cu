@@ -78,11 +78,19 @@ __device__ __forceinline__ void sh_dir_grad(float x, float y, float z, const flo
 }  // namespace
 
 constexpr int kProjBwdThreads = 128;
+// Row stride of the shared gradient columns: one float of padding, so that a warp reading
+// one Gaussian's consecutive elements (the fused Adam epilogue) hits distinct banks, as do
+// the threads writing one element of their own Gaussians.
+constexpr int kGs = kProjBwdThreads + 1;
 
+// The gradient of one Gaussian g over all views: mean, log-scale, quaternion and opacity
+// logit in the outputs, the SH coefficients' in gsh (one column of shared memory, element e
+// at gsh[e * kGs]); false (outputs untouched, gsh zero) where no view left a
+// 2-D gradient.  Consumes and clears the views' 2-D gradients.
 template <int DEG>
-__global__ void __launch_bounds__(kProjBwdThreads, 4) k_project_bwd(const BatchDev b, const GradTable gt) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= b.N) return;
+__device__ __forceinline__ bool proj_grads(const BatchDev& b, const int64_t g, float* gsh,
+                                           float (&out_m)[3], float (&out_ls)[3],
+                                           float (&out_q)[4], float& out_logit) {
   const int k = subset_of(b, g);
   const SubsetDev& S = b.subsets[k];
   const int64_t i = g - b.goff[k];
@@ -108,15 +116,13 @@ __global__ void __launch_bounds__(kProjBwdThreads, 4) k_project_bwd(const BatchD
   // shared memory (one column per thread): 96 fewer registers, so more warps hide the
   // latency of the per-view 2-D gradient loads
   const float* shp = S.sh + i * NC * 3;
-  __shared__ float s_gsh[NC * 3 * kProjBwdThreads];
-  float* gsh = s_gsh + threadIdx.x;  // element e at gsh[e * kProjBwdThreads]
 
   float gm[3] = {0.f, 0.f, 0.f}, gM[9];
 #pragma unroll
   for (int e = 0; e < 9; ++e) gM[e] = 0.f;
   float glogit = 0.f;
 #pragma unroll
-  for (int e = 0; e < NC * 3; ++e) gsh[e * kProjBwdThreads] = 0.f;
+  for (int e = 0; e < NC * 3; ++e) gsh[e * kGs] = 0.f;
   bool any = false;
 
   // the next view's 2-D gradient is loaded while this view's is processed; only views in
@@ -208,9 +214,9 @@ __global__ void __launch_bounds__(kProjBwdThreads, 4) k_project_bwd(const BatchD
     float w[NC];
 #pragma unroll
     for (int kk = 0; kk < NC; ++kk) {
-      gsh[(3 * kk + 0) * kProjBwdThreads] += Y[kk] * gc[0];
-      gsh[(3 * kk + 1) * kProjBwdThreads] += Y[kk] * gc[1];
-      gsh[(3 * kk + 2) * kProjBwdThreads] += Y[kk] * gc[2];
+      gsh[(3 * kk + 0) * kGs] += Y[kk] * gc[0];
+      gsh[(3 * kk + 1) * kGs] += Y[kk] * gc[1];
+      gsh[(3 * kk + 2) * kGs] += Y[kk] * gc[2];
       w[kk] = __ldg(shp + 3 * kk) * gc[0] + __ldg(shp + 3 * kk + 1) * gc[1] +
               __ldg(shp + 3 * kk + 2) * gc[2];
     }
@@ -268,7 +274,7 @@ __global__ void __launch_bounds__(kProjBwdThreads, 4) k_project_bwd(const BatchD
       for (int c = 0; c < 3; ++c)
         gM[3 * r + c] += R[r] * gV[c] + R[3 + r] * gV[3 + c] + R[6 + r] * gV[6 + c];
   }
-  if (!any) return;
+  if (!any) return false;
   // M = Rq diag(s)
   float gR[9], gls[3];
 #pragma unroll
@@ -290,35 +296,260 @@ __global__ void __launch_bounds__(kProjBwdThreads, 4) k_project_bwd(const BatchD
   gx += -4.f * qx * gR[8]; gy += -4.f * qy * gR[8];
   const float dq = qw * gw + qx * gx + qy * gy + qz * gz;
   const float iqn = 1.0f / qn;
-  float* const* P = gt.p[k];
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
-    P[0][3 * i + e] += gm[e];
-    P[1][3 * i + e] += gls[e];
+    out_m[e] = gm[e];
+    out_ls[e] = gls[e];
   }
-  float4* gq4 = reinterpret_cast<float4*>(P[2]) + i;
-  float4 cur = *gq4;
-  cur.x += (gw - qw * dq) * iqn;
-  cur.y += (gx - qx * dq) * iqn;
-  cur.z += (gy - qy * dq) * iqn;
-  cur.w += (gz - qz * dq) * iqn;
-  *gq4 = cur;
-  P[3][i] += glogit;
-#pragma unroll
-  for (int e = 0; e < NC * 3; ++e) P[4][i * NC * 3 + e] += gsh[e * kProjBwdThreads];
+  out_q[0] = (gw - qw * dq) * iqn;
+  out_q[1] = (gx - qx * dq) * iqn;
+  out_q[2] = (gy - qy * dq) * iqn;
+  out_q[3] = (gz - qz * dq) * iqn;
+  out_logit = glogit;
+  return true;
 }
 
-void launch_project_bwd(const BatchDev& b, const GradTable& gt, cudaStream_t s) {
+// One Adam element with torch.optim.Adam semantics (step_lr = lr / (1 - b1^t),
+// bc2_sqrt_inv = 1 / sqrt(1 - b2^t)), each operation rounded as written, so that the
+// stand-alone update and the one fused into the projection adjoint agree bit for bit.
+__device__ __forceinline__ void adam_elem(float& p, const float g, float& m, float& v,
+                                          const float step_lr, const float b1, const float b2,
+                                          const float bc2_sqrt_inv, const float eps) {
+  m = __fadd_rn(__fmul_rn(b1, m), __fmul_rn(__fsub_rn(1.0f, b1), g));
+  v = __fadd_rn(__fmul_rn(b2, v), __fmul_rn(__fmul_rn(__fsub_rn(1.0f, b2), g), g));
+  p = __fsub_rn(p, __fdiv_rn(__fmul_rn(step_lr, m),
+                             __fadd_rn(__fmul_rn(__fsqrt_rn(v), bc2_sqrt_inv), eps)));
+}
+
+// Bias-corrected learning rates of a step, in double precision once per CTA (FP64 is
+// slow on this part): [0] lr_group / bc1 for the 6 groups, [6] 1 / sqrt(bc2).
+__device__ __forceinline__ void adam_scales(const AdamTable& at, float* sc) {
+  if (threadIdx.x == 0) {
+    const int64_t step = at.step_dev ? *at.step_dev : at.step;
+    const double bc1 = 1.0 - pow((double)at.b1, (double)step);
+    const double bc2 = 1.0 - pow((double)at.b2, (double)step);
+    for (int j = 0; j < 6; ++j) sc[j] = (float)(at.lr[j] / bc1);
+    sc[6] = (float)(1.0 / sqrt(bc2));
+  }
+  __syncthreads();
+}
+
+// The fused epilogue's view of one parameter array of the CTA's ng Gaussians (W floats
+// each) when they all lie in one subset: E = ng W contiguous floats of p, m and v, and the
+// gradient of element idx (CTA Gaussian j = idx / W, element e) at rows[e * kGs + j].
+template <int W>
+struct AdamSpan {
+  float* p;
+  float* m;
+  float* v;
+  const float* rows;
+  int E;
+  float lr_lo, lr_hi;  // elements e < 3, e >= 3 (the SH coefficients above degree 0)
+};
+
+template <int W>
+__device__ __forceinline__ AdamSpan<W> adam_span(const AdamTable& at, const int a, const int k,
+                                                 const int64_t i0, const float* rows, const int ng,
+                                                 const float lr_lo, const float lr_hi) {
+  const int64_t o = i0 * W;
+  return AdamSpan<W>{at.p[k][a] + o, at.m[k][a] + o, at.v[k][a] + o, rows, ng * W, lr_lo, lr_hi};
+}
+
+// Loads kU elements of p, m and v per thread (elements base + u * kProjBwdThreads) ...
+template <int W, int kU>
+__device__ __forceinline__ void span_load(const AdamSpan<W>& sp, const int base, float (&pv)[kU],
+                                          float (&mv)[kU], float (&vv)[kU]) {
+#pragma unroll
+  for (int u = 0; u < kU; ++u) {
+    const int idx = base + u * kProjBwdThreads;
+    if (idx < sp.E) {
+      pv[u] = sp.p[idx];
+      mv[u] = sp.m[idx];
+      vv[u] = sp.v[idx];
+    }
+  }
+}
+
+// ... and updates and stores them.
+template <int W, int kU>
+__device__ __forceinline__ void span_update(const AdamSpan<W>& sp, const int base, float (&pv)[kU],
+                                            float (&mv)[kU], float (&vv)[kU], const float b1,
+                                            const float b2, const float bci, const float eps) {
+#pragma unroll
+  for (int u = 0; u < kU; ++u) {
+    const int idx = base + u * kProjBwdThreads;
+    if (idx < sp.E) {
+      const int j = idx / W, e = idx - j * W;
+      adam_elem(pv[u], sp.rows[e * kGs + j], mv[u], vv[u], e < 3 ? sp.lr_lo : sp.lr_hi, b1, b2,
+                bci, eps);
+      sp.p[idx] = pv[u];
+      sp.m[idx] = mv[u];
+      sp.v[idx] = vv[u];
+    }
+  }
+}
+
+// Adam over array a of the CTA's ng Gaussians (W floats each) element by element, for a CTA
+// whose Gaussians straddle a subset boundary: element e of CTA Gaussian j lives in subset
+// s_k[j] at local index s_i[j].
+template <int W>
+__device__ __forceinline__ void adam_rows_split(const AdamTable& at, const int a,
+                                                const float* rows, const int* s_k,
+                                                const int64_t* s_i, const int ng,
+                                                const float lr_lo, const float lr_hi,
+                                                const float b1, const float b2, const float bci,
+                                                const float eps) {
+  for (int idx = threadIdx.x; idx < ng * W; idx += kProjBwdThreads) {
+    const int j = idx / W, e = idx - j * W;
+    const int k = s_k[j];
+    const int64_t off = s_i[j] * W + e;
+    float* pp = at.p[k][a] + off;
+    float* mp = at.m[k][a] + off;
+    float* vp = at.v[k][a] + off;
+    float pv = *pp, mv = *mp, vv = *vp;
+    adam_elem(pv, rows[e * kGs + j], mv, vv, e < 3 ? lr_lo : lr_hi, b1, b2, bci, eps);
+    *pp = pv;
+    *mp = mv;
+    *vp = vv;
+  }
+}
+
+template <int DEG, bool kFuse>
+__global__ void __launch_bounds__(kProjBwdThreads, 4)
+    k_project_bwd(const BatchDev b, const GradTable gt, const AdamTable at) {
+  constexpr int NC = (DEG + 1) * (DEG + 1);
+  // gradient columns, one per thread: with kFuse rows 0-10 hold mean (3), log-scale (3),
+  // quaternion (4) and opacity logit, the SH rows follow
+  constexpr int kHead = kFuse ? 11 : 0;
+  __shared__ float s_grad[(kHead + NC * 3) * kGs];
+  float* gsh = s_grad + kHead * kGs + threadIdx.x;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
+  float glogit = 0.f;
+  bool any = false;
+  if (g < b.N) {
+    any = proj_grads<DEG>(b, g, gsh, gm, gls, gq, glogit);
+  } else if (kFuse) {
+#pragma unroll
+    for (int e = 0; e < NC * 3; ++e) gsh[e * kGs] = 0.f;
+  }
+  if constexpr (!kFuse) {
+    // add into the caller's gradient arrays (one thread owns one Gaussian: no atomics)
+    if (!any) return;
+    const int k = subset_of(b, g);
+    const int64_t i = g - b.goff[k];
+    float* const* P = gt.p[k];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      P[0][3 * i + e] += gm[e];
+      P[1][3 * i + e] += gls[e];
+    }
+    float4* gq4 = reinterpret_cast<float4*>(P[2]) + i;
+    float4 cur = *gq4;
+    cur.x += gq[0];
+    cur.y += gq[1];
+    cur.z += gq[2];
+    cur.w += gq[3];
+    *gq4 = cur;
+    P[3][i] += glogit;
+#pragma unroll
+    for (int e = 0; e < NC * 3; ++e) P[4][i * NC * 3 + e] += gsh[e * kGs];
+  } else {
+    // Adam on every parameter of the CTA's Gaussians straight from these gradients (zero
+    // where a Gaussian has none, as after zero_grad): no gradient array is written or read.
+    // The CTA's Gaussians are contiguous within each subset's arrays, so the threads walk
+    // each array's range with unit stride (coalesced loads and stores), taking the
+    // gradients from the shared columns.
+    __shared__ float s_sc[7];
+    __shared__ int s_k[kProjBwdThreads];
+    __shared__ int64_t s_i[kProjBwdThreads];
+    float* col = s_grad + threadIdx.x;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      col[e * kGs] = gm[e];
+      col[(3 + e) * kGs] = gls[e];
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) col[(6 + e) * kGs] = gq[e];
+    col[10 * kGs] = glogit;
+    if (g < b.N) {
+      const int k = subset_of(b, g);
+      s_k[threadIdx.x] = k;
+      s_i[threadIdx.x] = g - b.goff[k];
+    }
+    adam_scales(at, s_sc);  // (its barrier also publishes the columns above)
+    const int64_t rest = b.N - (int64_t)blockIdx.x * kProjBwdThreads;
+    const int ng = rest < kProjBwdThreads ? (int)rest : kProjBwdThreads;
+    const float b1 = at.b1, b2 = at.b2, eps = at.eps, bci = s_sc[6];
+    if (s_k[0] == s_k[ng - 1]) {
+      // one subset: contiguous ranges.  The four small arrays hold at most 3 + 3 + 4 + 1
+      // elements per thread, all loaded before any update (33 loads in flight per thread);
+      // the SH array follows in batches of 16 elements per thread
+      const int k = s_k[0];
+      const int64_t i0 = s_i[0];
+      const auto sm = adam_span<3>(at, 0, k, i0, s_grad, ng, s_sc[0], s_sc[0]);
+      const auto sl = adam_span<3>(at, 1, k, i0, s_grad + 3 * kGs, ng, s_sc[1], s_sc[1]);
+      const auto sq = adam_span<4>(at, 2, k, i0, s_grad + 6 * kGs, ng, s_sc[2], s_sc[2]);
+      const auto so = adam_span<1>(at, 3, k, i0, s_grad + 10 * kGs, ng, s_sc[3], s_sc[3]);
+      const int t = threadIdx.x;
+      {
+        float p0[3], m0[3], v0[3], p1[3], m1[3], v1[3], p2[4], m2[4], v2[4], p3[1], m3[1], v3[1];
+        span_load<3, 3>(sm, t, p0, m0, v0);
+        span_load<3, 3>(sl, t, p1, m1, v1);
+        span_load<4, 4>(sq, t, p2, m2, v2);
+        span_load<1, 1>(so, t, p3, m3, v3);
+        span_update<3, 3>(sm, t, p0, m0, v0, b1, b2, bci, eps);
+        span_update<3, 3>(sl, t, p1, m1, v1, b1, b2, bci, eps);
+        span_update<4, 4>(sq, t, p2, m2, v2, b1, b2, bci, eps);
+        span_update<1, 1>(so, t, p3, m3, v3, b1, b2, bci, eps);
+      }
+      constexpr int kU = 16;
+      const auto ss = adam_span<NC * 3>(at, 4, k, i0, s_grad + 11 * kGs, ng, s_sc[4], s_sc[5]);
+      for (int base = t; base < ss.E; base += kU * kProjBwdThreads) {
+        float pv[kU], mv[kU], vv[kU];
+        span_load<NC * 3, kU>(ss, base, pv, mv, vv);
+        span_update<NC * 3, kU>(ss, base, pv, mv, vv, b1, b2, bci, eps);
+      }
+    } else {
+      adam_rows_split<3>(at, 0, s_grad, s_k, s_i, ng, s_sc[0], s_sc[0], b1, b2, bci, eps);
+      adam_rows_split<3>(at, 1, s_grad + 3 * kGs, s_k, s_i, ng, s_sc[1], s_sc[1], b1, b2, bci,
+                         eps);
+      adam_rows_split<4>(at, 2, s_grad + 6 * kGs, s_k, s_i, ng, s_sc[2], s_sc[2], b1, b2, bci,
+                         eps);
+      adam_rows_split<1>(at, 3, s_grad + 10 * kGs, s_k, s_i, ng, s_sc[3], s_sc[3], b1, b2, bci,
+                         eps);
+      adam_rows_split<NC * 3>(at, 4, s_grad + 11 * kGs, s_k, s_i, ng, s_sc[4], s_sc[5], b1, b2,
+                              bci, eps);
+    }
+  }
+}
+
+template <bool kFuse>
+static void launch_project_bwd_t(const BatchDev& b, const GradTable& gt, const AdamTable& at,
+                                 cudaStream_t s) {
   const int threads = kProjBwdThreads;
   const int64_t blocks = (b.N + threads - 1) / threads;
   if (blocks == 0) return;
   switch (b.sh_degree) {
-    case 0: k_project_bwd<0><<<(unsigned)blocks, threads, 0, s>>>(b, gt); break;
-    case 1: k_project_bwd<1><<<(unsigned)blocks, threads, 0, s>>>(b, gt); break;
-    case 2: k_project_bwd<2><<<(unsigned)blocks, threads, 0, s>>>(b, gt); break;
-    default: k_project_bwd<3><<<(unsigned)blocks, threads, 0, s>>>(b, gt); break;
+    case 0: k_project_bwd<0, kFuse><<<(unsigned)blocks, threads, 0, s>>>(b, gt, at); break;
+    case 1: k_project_bwd<1, kFuse><<<(unsigned)blocks, threads, 0, s>>>(b, gt, at); break;
+    case 2: k_project_bwd<2, kFuse><<<(unsigned)blocks, threads, 0, s>>>(b, gt, at); break;
+    default: k_project_bwd<3, kFuse><<<(unsigned)blocks, threads, 0, s>>>(b, gt, at); break;
   }
   count_launch();
+}
+
+void launch_project_bwd(const BatchDev& b, const GradTable& gt, cudaStream_t s) {
+  AdamTable at;
+  memset(&at, 0, sizeof(at));
+  launch_project_bwd_t<false>(b, gt, at, s);
+}
+
+void launch_project_bwd_adam(const BatchDev& b, const AdamTable& at, cudaStream_t s) {
+  GradTable gt;
+  memset(&gt, 0, sizeof(gt));
+  if (at.step_dev) launch_step_increment(const_cast<int64_t*>(at.step_dev), s);
+  launch_project_bwd_t<true>(b, gt, at, s);
 }
 
 // ---------------------------------------------------------------- Adam
@@ -346,7 +577,6 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, float* __re
   const float step_lr = s_sc[0], step_lr_rest = s_sc[1], bc2_sqrt_inv = s_sc[2];
   const int64_t n4 = vec4 ? (n >> 2) : 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const float ob1 = 1.0f - b1, ob2 = 1.0f - b2;
   // SH learning rates: element idx takes lr_rest when idx % sh_stride >= 3.  When
   // sh_stride is a multiple of 4 the float4 q starts at (q % (sh_stride / 4)) * 4 within
   // its Gaussian, kept incrementally (no division per element)
@@ -372,9 +602,7 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, float* __re
       } else if (sh_stride > 0 && ((4 * q + e) % sh_stride) >= 3) {
         lr = step_lr_rest;
       }
-      me[e] = b1 * me[e] + ob1 * ge[e];
-      ve[e] = b2 * ve[e] + ob2 * ge[e] * ge[e];
-      pe[e] -= lr * me[e] / (sqrtf(ve[e]) * bc2_sqrt_inv + eps);
+      adam_elem(pe[e], ge[e], me[e], ve[e], lr, b1, b2, bc2_sqrt_inv, eps);
     }
     reinterpret_cast<float4*>(p)[q] = pp;
     reinterpret_cast<float4*>(m)[q] = mm;
@@ -385,12 +613,11 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, float* __re
   }
   for (int64_t idx = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
     const float lr = (sh_stride > 0 && (idx % sh_stride) >= 3) ? step_lr_rest : step_lr;
-    const float gg = g[idx];
-    const float mm = b1 * m[idx] + ob1 * gg;
-    const float vv = b2 * v[idx] + ob2 * gg * gg;
+    float pp = p[idx], mm = m[idx], vv = v[idx];
+    adam_elem(pp, g[idx], mm, vv, lr, b1, b2, bc2_sqrt_inv, eps);
+    p[idx] = pp;
     m[idx] = mm;
     v[idx] = vv;
-    p[idx] -= lr * mm / (sqrtf(vv) * bc2_sqrt_inv + eps);
     if (zero_grad) g[idx] = 0.0f;
   }
 }

@@ -85,6 +85,7 @@ _sigs = {
     "splx_batch_layout": (C.c_int, [_P, _P, _P]),
     "splx_batch_forward": (C.c_int, [_P, _P, _P, _P]),
     "splx_batch_backward": (C.c_int, [_P, _P, _P, _P, _P]),
+    "splx_batch_backward_adam": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "splx_batch_status": (C.c_int, [_P, C.POINTER(C.c_int64), _P]),
     "splx_batch_destroy": (C.c_int, [_P]),
     "splx_batch_set_timing": (C.c_int, [_P, C.c_int]),
@@ -481,6 +482,20 @@ class Batch:
         garr = (Params * self.K)(*grads)
         _check(_lib.splx_batch_backward(self.h, _ptr(dL_drgb), _ptr(dL_dT), garr, _stream(stream)),
                "splx_batch_backward")
+
+    def backward_adam(self, dL_drgb, dL_dT, params, m, v, hp: Adam, step_dev, stream=None):
+        """Backward with Adam fused into the projection adjoint: params[k] (the subsets the
+        batch was created on), m[k] and v[k] are updated in place; step_dev is a CUDA int64
+        tensor of one element, incremented first."""
+        if step_dev.dtype != torch.int64 or not step_dev.is_cuda:
+            raise ValueError("step_dev must be a CUDA int64 tensor")
+        parr = (Params * self.K)(*params)
+        marr = (Params * self.K)(*m)
+        varr = (Params * self.K)(*v)
+        _check(_lib.splx_batch_backward_adam(self.h, _ptr(dL_drgb), _ptr(dL_dT), parr, marr, varr,
+                                             C.byref(hp), C.c_void_p(step_dev.data_ptr()),
+                                             _stream(stream)),
+               "splx_batch_backward_adam")
 
     def status(self, stream=None):
         pairs = C.c_int64()

@@ -61,15 +61,19 @@ class BatchedStep:
 
     def __init__(self, ctx: S.Context, params: dict, offsets, sh_degree: int, cams, targets,
                  opts: S.Opts | None = None, lr=DEFAULT_LR, pair_capacity: int = 0,
-                 stream: torch.cuda.Stream | None = None, order=None, dssim: float = 0.0):
+                 stream: torch.cuda.Stream | None = None, order=None, dssim: float = 0.0,
+                 fused_adam: bool = True):
         """order: optional [V, K] front-to-back subset order per view, which turns on
         saturation skipping (visibility.orders_for_views gives it for k-d cells).
-        dssim: weight lambda of the D-SSIM term (0: plain L1)."""
+        dssim: weight lambda of the D-SSIM term (0: plain L1).
+        fused_adam: Adam runs inside the projection adjoint (no gradient arrays); False
+        runs the backward into gradient arrays and a separate Adam pass (same result)."""
         self.dssim = float(dssim)
+        self.fused_adam = bool(fused_adam)
         self.ctx, self.p, self.off, self.deg = ctx, params, np.asarray(offsets), sh_degree
         self.opts = opts or S.opts()
         self.stream = stream or torch.cuda.current_stream()
-        self.g = {k: torch.zeros_like(v) for k, v in params.items()}
+        self.g = None if self.fused_adam else {k: torch.zeros_like(v) for k, v in params.items()}
         self.m = {k: torch.zeros_like(v) for k, v in params.items()}
         self.v = {k: torch.zeros_like(v) for k, v in params.items()}
         self.hp = S.adam_hp(lr, zero_grad=True)
@@ -84,7 +88,12 @@ class BatchedStep:
         self.target = torch.empty_like(self.rgb)
         if targets is not None:
             self.set_targets(targets)
-        self._grads = _subset_structs(self.g, offsets, sh_degree, mutable=True)
+        if self.fused_adam:
+            self._p_sub = _subset_structs(params, offsets, sh_degree, mutable=True)
+            self._m_sub = _subset_structs(self.m, offsets, sh_degree, mutable=True)
+            self._v_sub = _subset_structs(self.v, offsets, sh_degree, mutable=True)
+        else:
+            self._grads = _subset_structs(self.g, offsets, sh_degree, mutable=True)
         self.graph = None
 
     @property
@@ -119,11 +128,17 @@ class BatchedStep:
         else:
             S.loss_l1(self.ctx, self.rgb, self.target, self.loss, self.dL, stream=s)
         if ev[2] is not None: ev[2].record(s)
-        self.batch.backward(self.dL, None, self._grads, stream=s)
-        if ev[3] is not None: ev[3].record(s)
-        S.step_device(self.ctx, _whole(self.p, self.deg), _whole(self.g, self.deg),
-                      _whole(self.m, self.deg), _whole(self.v, self.deg), self.hp, self.step_dev,
-                      stream=s)
+        if self.fused_adam:
+            # backward and Adam in one pass (the adam interval ev[3] -> ev[4] is then empty)
+            self.batch.backward_adam(self.dL, None, self._p_sub, self._m_sub, self._v_sub,
+                                     self.hp, self.step_dev, stream=s)
+            if ev[3] is not None: ev[3].record(s)
+        else:
+            self.batch.backward(self.dL, None, self._grads, stream=s)
+            if ev[3] is not None: ev[3].record(s)
+            S.step_device(self.ctx, _whole(self.p, self.deg), _whole(self.g, self.deg),
+                          _whole(self.m, self.deg), _whole(self.v, self.deg), self.hp,
+                          self.step_dev, stream=s)
         if ev[4] is not None: ev[4].record(s)
 
     def capture(self, events=None):

@@ -1,0 +1,153 @@
+"""Adam fused into the projection adjoint (splx_batch_backward_adam) against the backward
+into gradient arrays followed by the separate Adam pass (splx_batch_backward +
+splx_step_device): bit-identical parameters and moments where the backward itself is
+deterministic, close agreement on a clustered scene through a captured graph, and the
+argument checks."""
+import numpy as np
+import pytest
+
+from paper_2606_18588_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2606_18588_gb300 import splx as S
+    c = S.Context()
+    yield c
+    c.close()
+
+
+def _tile_bound_case(sizes=(333, 400, 267), deg=3, seed=7):
+    """Gaussians whose footprints lie inside one 16-pixel tile in each of two 128x128 views
+    (the second view's principal point shifted by exactly one tile), so each (view,
+    Gaussian) 2-D gradient is a single atomic add onto zero and the whole backward is
+    deterministic.  Centres sit within 2 px of a tile centre; projected standard deviations
+    are below 0.7 px before the 0.3 px^2 dilation, so 3-sigma footprints stay within 5 px
+    of it.  The three subsets are contiguous with sizes that put subset boundaries inside
+    128-Gaussian blocks."""
+    rng = np.random.default_rng(seed)
+    n = sum(sizes)
+    f, c0 = 100.0, 64.0
+    u = 8.0 + 16.0 * rng.integers(0, 8, n) + rng.uniform(-2.0, 2.0, n)
+    v = 8.0 + 16.0 * rng.integers(0, 8, n) + rng.uniform(-2.0, 2.0, n)
+    z = rng.uniform(4.5, 5.5, n)
+    means = np.stack([(u - c0) * z / f, (v - c0) * z / f, z], 1).astype(np.float32)
+    log_scales = np.log(rng.uniform(0.01, 0.03, (n, 3))).astype(np.float32)
+    q = rng.standard_normal((n, 4)).astype(np.float32)
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    logits = rng.normal(0.5, 1.0, n).astype(np.float32)
+    nc = I.n_sh_coeffs(deg)
+    sh = rng.normal(0.0, 0.5, (n, nc, 3)).astype(np.float32)
+    sc = I.Scene(means, log_scales, q, logits, sh, deg)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    eye3, t0 = np.eye(3, dtype=np.float32), np.zeros(3, np.float32)
+    cams = [I.Camera(eye3, t0, f, f, c0, c0, 128, 128),
+            I.Camera(eye3, t0, f, f, c0 + 16.0, c0, 128, 128)]
+    return sc, off, cams
+
+
+def _train(ctx, sc, off, cams, tg, fused, steps, graph=False):
+    from paper_2606_18588_gb300 import splx as S
+    from paper_2606_18588_gb300.train import BatchedStep
+    dev = {k: torch.from_numpy(np.ascontiguousarray(a)).cuda() for k, a in zip(GROUPS, sc.arrays())}
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        st = BatchedStep(ctx, dev, off, sc.sh_degree, cams, tg, S.opts(), stream=s,
+                         fused_adam=fused)
+        st.run()
+        if graph:
+            s.synchronize()
+            st.capture()
+            for _ in range(steps - 1):
+                st.replay()
+        else:
+            for _ in range(steps - 1):
+                st.run()
+        s.synchronize()
+        assert st.status()[0] == S.OK
+    out = {"p": {k: t.clone() for k, t in dev.items()}, "m": {k: t.clone() for k, t in st.m.items()},
+           "v": {k: t.clone() for k, t in st.v.items()}, "step": int(st.step_dev.item())}
+    st.close()
+    return out
+
+
+def test_fused_adam_is_bit_identical_where_the_backward_is_deterministic(ctx):
+    sc, off, cams = _tile_bound_case()
+    tg = [torch.from_numpy(I.random_image(c.height, c.width, 40 + i)) for i, c in enumerate(cams)]
+    a = _train(ctx, sc, off, cams, tg, fused=False, steps=3)
+    a2 = _train(ctx, sc, off, cams, tg, fused=False, steps=3)
+    for part in ("p", "m", "v"):  # the premise: this case's backward is deterministic
+        for k in GROUPS:
+            assert torch.equal(a[part][k], a2[part][k]), (part, k)
+    b = _train(ctx, sc, off, cams, tg, fused=True, steps=3)
+    assert a["step"] == b["step"] == 3
+    moved = 0
+    for part in ("p", "m", "v"):
+        for k in GROUPS:
+            assert torch.equal(a[part][k], b[part][k]), (part, k)
+    for k in GROUPS:  # the steps did update every group
+        moved += int((a["p"][k].cpu() != torch.from_numpy(getattr(sc, k))).any())
+    assert moved == len(GROUPS)
+
+
+def test_fused_adam_agrees_on_a_clustered_scene_through_a_graph(ctx):
+    sc, off, _, cams = I.cluster_case(30_000, 11, 4, 3, [(200, 120), (96, 64), (131, 77)])
+    tg = [torch.from_numpy(I.random_image(c.height, c.width, 5 + i)) for i, c in enumerate(cams)]
+    a = _train(ctx, sc, off, cams, tg, fused=False, steps=1)
+    b = _train(ctx, sc, off, cams, tg, fused=True, steps=1)
+    for k in GROUPS:
+        p0 = torch.from_numpy(getattr(sc, k)).cuda().double()
+        # the first moment is (1 - beta1) g: gradients equal up to atomic summation order
+        ma, mb = a["m"][k].double(), b["m"][k].double()
+        assert (ma - mb).norm() <= 1e-4 * ma.norm() + 1e-30, k
+        # the first step moves each element by lr * g / (|g| + eps'): compare the moves
+        da, db = a["p"][k].double() - p0, b["p"][k].double() - p0
+        assert (da - db).norm() <= 1e-2 * da.norm(), k
+    # several steps through a captured graph against the same number of eager ones
+    a3 = _train(ctx, sc, off, cams, tg, fused=False, steps=3)
+    b3 = _train(ctx, sc, off, cams, tg, fused=True, steps=3, graph=True)
+    assert b3["step"] == 3
+    for k in GROUPS:
+        p0 = torch.from_numpy(getattr(sc, k)).cuda().double()
+        da, db = a3["p"][k].double() - p0, b3["p"][k].double() - p0
+        assert (da - db).norm() <= 2e-2 * da.norm(), k
+
+
+def test_fused_adam_checks_its_arguments(ctx):
+    from paper_2606_18588_gb300 import splx as S
+    from paper_2606_18588_gb300.train import _subset_structs
+    sc, off, cams = _tile_bound_case(sizes=(300, 200))
+    dev = {k: torch.from_numpy(np.ascontiguousarray(a)).cuda() for k, a in zip(GROUPS, sc.arrays())}
+    m = {k: torch.zeros_like(t) for k, t in dev.items()}
+    v = {k: torch.zeros_like(t) for k, t in dev.items()}
+    b = S.Batch(ctx, _subset_structs(dev, off, sc.sh_degree), cams, S.opts())
+    rgb = torch.empty(b.rgb_off[-1], device="cuda")
+    dL = torch.zeros_like(rgb)
+    hp = S.adam_hp((1e-3,) * 6)
+    step = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ps = _subset_structs(dev, off, sc.sh_degree, mutable=True)
+    ms = _subset_structs(m, off, sc.sh_degree, mutable=True)
+    vs = _subset_structs(v, off, sc.sh_degree, mutable=True)
+    with pytest.raises(S.SplxError) as e:  # before any forward
+        b.backward_adam(dL, None, ps, ms, vs, hp, step)
+    assert e.value.code == S.ERR_STATE
+    b.forward(rgb)
+    with pytest.raises(S.SplxError) as e:  # parameters that are not the batch's own
+        b.backward_adam(dL, None, ms, ms, vs, hp, step)
+    assert e.value.code == S.ERR_INVALID
+    with pytest.raises(S.SplxError) as e:  # moments of the wrong size
+        b.backward_adam(dL, None, ps, list(reversed(ms)), vs, hp, step)
+    assert e.value.code == S.ERR_INVALID
+    b.backward_adam(dL, None, ps, ms, vs, hp, step)
+    torch.cuda.synchronize()
+    assert int(step.item()) == 1
+    # a zero loss gradient: every moment stays zero and no parameter moves
+    for k in GROUPS:
+        assert not m[k].any() and not v[k].any()
+        assert torch.equal(dev[k].cpu(), torch.from_numpy(getattr(sc, k)))
+    b.close()
