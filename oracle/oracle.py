@@ -131,6 +131,9 @@ def _declare(L, P):
     L.orc_render_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P, P, P, P, P,
                                   P, P, P]
     L.orc_backward_view.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P]
+    L.orc_render_view_pruned.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P, P, P, P, P,
+                                         P, P, P, P, P]
+    L.orc_backward_view_pruned.argtypes = [P, P, C.c_int32, P, P, P, P, P, P, P, P, P]
     L.orc_adam.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_double,
                            C.c_double, C.c_int64]
     L.orc_num_threads.restype = C.c_int
@@ -300,8 +303,15 @@ def _cells(cells, K):
     return a
 
 
+def _sat(sat, H, W):
+    a = np.ascontiguousarray(sat, np.uint8)
+    if a.shape != (H, W):
+        raise ValueError("sat must be [H, W] uint8")
+    return a
+
+
 def render_view(scene, offsets, cam, o: Opts | None = None, tile_mask=None, separable=False,
-                order=None, cells=None, bounds=False):
+                order=None, cells=None, bounds=False, sat=None):
     """K contiguous subsets rendered and composited: dict(image, T, Cp, Tp, Dp, amb, sep,
     skip).  With `order` (front-to-back subset order) the partials are rendered in that
     order with saturation skipping (Sec. 4.2): a subset leaves empty the pixels whose prefix
@@ -309,7 +319,13 @@ def render_view(scene, offsets, cam, o: Opts | None = None, tile_mask=None, sepa
     whole (no open pixel).  With
     `cells` (the subsets' k-d boxes [K, 2, 3]) cross-boundary Gaussians are filtered per
     ray as in Sec. 8.1.  With bounds: also "flip", the flip bounds of the ambiguous pixels:
-    image and T of the composite, partC / partT / partD per partial (absolute amounts)."""
+    image and T of the composite, partC / partT / partD per partial (absolute amounts).
+    With `sat` (with `order`; [H, W] uint8, the view's stale saturation state of Sec. 4.2
+    step 2) the subset at rank r leaves pixel p empty exactly when r >= sat[p] (values >= K
+    prune nothing), and the result adds "sat" (the state re-evaluated from this render for
+    the next visit: the first rank after which the prefix transmittance is below eps_comp,
+    255 for none) and "sat_amb" (pixels whose re-evaluation met a prefix within the
+    AMB_SAT band); `separable` is not available then."""
     o = o or opts()
     k = _Keep(scene)
     c = camera(cam)
@@ -327,11 +343,27 @@ def render_view(scene, offsets, cam, o: Opts | None = None, tile_mask=None, sepa
     skip = np.zeros((K, ((H + B - 1) // B) * ((W + B - 1) // B)), np.uint8)
     cl = _cells(cells, K)
     bd, bout = _bounds(H, W, K) if bounds else (None, None)
-    lib().orc_render_view(C.byref(k.p), _ptr(off), K, C.byref(c), C.byref(o), _ptr(tm), _ptr(od),
-                          _ptr(cl), _ptr(out), _ptr(To), _ptr(Cp), _ptr(Tp), _ptr(Dp), _ptr(amb),
-                          _ptr(sep), _ptr(skip), _ptr(st), C.byref(bd) if bd is not None else None)
+    if sat is not None:
+        if od is None or separable:
+            raise ValueError("sat needs order and excludes separable")
+        si = _sat(sat, H, W)
+        so = np.zeros((H, W), np.uint8)
+        sa = np.zeros((H, W), np.uint8)
+        rc = lib().orc_render_view_pruned(
+            C.byref(k.p), _ptr(off), K, C.byref(c), C.byref(o), _ptr(tm), _ptr(od), _ptr(cl),
+            _ptr(out), _ptr(To), _ptr(Cp), _ptr(Tp), _ptr(Dp), _ptr(amb), _ptr(skip), _ptr(st),
+            C.byref(bd) if bd is not None else None, _ptr(si), _ptr(so), _ptr(sa))
+        if rc != 0:
+            raise ValueError("orc_render_view_pruned failed")
+    else:
+        lib().orc_render_view(C.byref(k.p), _ptr(off), K, C.byref(c), C.byref(o), _ptr(tm),
+                              _ptr(od), _ptr(cl), _ptr(out), _ptr(To), _ptr(Cp), _ptr(Tp),
+                              _ptr(Dp), _ptr(amb), _ptr(sep), _ptr(skip), _ptr(st),
+                              C.byref(bd) if bd is not None else None)
     res = dict(image=out, T=To, Cp=Cp, Tp=Tp, Dp=Dp, amb=amb, sep=sep, skip=skip,
                evaluated=int(st[0]))
+    if sat is not None:
+        res["sat"], res["sat_amb"] = so, sa
     if bounds:
         res["flip"] = dict(image=bout["image"], T=bout["T"], partC=bout["partC"] * bd.cmax,
                            partT=bout["partT"], partD=bout["partC"] * bd.dmax, cmax=bd.cmax,
@@ -340,10 +372,11 @@ def render_view(scene, offsets, cam, o: Opts | None = None, tile_mask=None, sepa
 
 
 def backward_view(scene, offsets, cam, dLdC, dLdT=None, o: Opts | None = None, tile_mask=None,
-                  order=None, cells=None):
+                  order=None, cells=None, sat=None):
     """Gradients (float64) of sum(dLdC*C) + sum(dLdT*T) w.r.t. every parameter array
     (restricted to the pixels of tiles where tile_mask is nonzero, if given; with `order`,
-    of the saturation-skipping render)."""
+    of the saturation-skipping render; with `order` and `sat`, of the render with that
+    stale saturation state)."""
     o = o or opts()
     k = _Keep(scene)
     c = camera(cam)
@@ -355,6 +388,16 @@ def backward_view(scene, offsets, cam, dLdC, dLdT=None, o: Opts | None = None, t
     dT = None if dLdT is None else np.ascontiguousarray(dLdT, np.float64)
     tm = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8)
     cl = _cells(cells, K)
+    if sat is not None:
+        od = _order(order, K)
+        if od is None:
+            raise ValueError("sat needs order")
+        rc = lib().orc_backward_view_pruned(C.byref(k.p), _ptr(off), K, C.byref(c), C.byref(o),
+                                            _ptr(dC), _ptr(dT), _ptr(tm), _ptr(od), _ptr(cl),
+                                            C.byref(gr), _ptr(_sat(sat, cam.height, cam.width)))
+        if rc != 0:
+            raise ValueError("orc_backward_view_pruned failed")
+        return g
     lib().orc_backward_view(C.byref(k.p), _ptr(off), K, C.byref(c), C.byref(o), _ptr(dC), _ptr(dT),
                             _ptr(tm), _ptr(_order(order, K)), _ptr(cl), C.byref(gr))
     return g

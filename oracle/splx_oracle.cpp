@@ -876,13 +876,27 @@ namespace {
 // lies within amb_T of eps_comp, widened by the relative change that the flip bounds of the
 // subsets before it allow (sum of fT / (T - fT)); for such pixels sat_alt ([K][H][W])
 // is set and alt ([K][5][H][W]: C rgb, T, D) holds the partial's other outcome.
+//
+// Stale saturation state (Sec. 4.2 step 2: a view's pixels found saturated by the
+// composition of one visit are left out of the next one).  With sat_in ([H][W], used
+// with order) the subset at rank r leaves pixel i empty exactly when r >= sat_in[i] (a
+// value >= K prunes nothing): the decision is the input's, not the current prefix's.
+// With sat_out ([H][W]) each pixel's state for the next visit is re-evaluated from this
+// visit's partials: r + 1 for the first rank r below min(sat_in, K) whose prefix (the
+// product of the transmittances of ranks 0..r in order) is below eps_comp, or 255 (none)
+// if there is no such rank or r + 1 = K.  Pruned ranks are transparent here, so once the
+// prefix stays above eps_comp up to the old state every pruned rank comes back.  sat_amb
+// (nullable) marks pixels where a prefix examined lies within the AMB_SAT band of
+// eps_comp.
 void render_partials(const orc_params& p, const int64_t* offsets, int K, const orc_camera& cam,
                      const orc_opts& o, const uint8_t* tile_mask, const int32_t* order,
                      std::vector<double>& C, std::vector<double>& T, std::vector<double>& D,
                      std::vector<uint8_t>& skip, uint8_t* amb, int64_t* stats,
                      const CrossFilter* f, std::vector<uint8_t>* pskip = nullptr,
                      std::vector<double>* flips = nullptr, double* cdmax = nullptr,
-                     std::vector<uint8_t>* sat_alt = nullptr, std::vector<double>* alt = nullptr) {
+                     std::vector<uint8_t>* sat_alt = nullptr, std::vector<double>* alt = nullptr,
+                     const uint8_t* sat_in = nullptr, uint8_t* sat_out = nullptr,
+                     uint8_t* sat_amb_out = nullptr) {
   const int W = cam.width, H = cam.height, B = o.tile;
   const int64_t HW = (int64_t)W * H;
   const int tw = (W + B - 1) / B, th = (H + B - 1) / B, nt = tw * th;
@@ -900,7 +914,11 @@ void render_partials(const orc_params& p, const int64_t* offsets, int K, const o
   std::vector<double> fl1(flips ? (size_t)4 * HW : 0);
   std::vector<double> prefix(HW, 1.0), prefix_rel(HW, 0.0);
   std::vector<uint8_t> sat_amb(HW, 0);
-  const bool want_alt = flips && order && sat_alt && alt;
+  if (!order) sat_in = nullptr;
+  const bool want_alt = flips && order && sat_alt && alt && !sat_in;
+  std::vector<uint8_t> decided(sat_out ? HW : 0, 0);
+  if (sat_out) std::fill(sat_out, sat_out + HW, (uint8_t)255);
+  if (sat_amb_out) std::fill(sat_amb_out, sat_amb_out + HW, (uint8_t)0);
   if (want_alt) {
     sat_alt->assign((size_t)K * HW, 0);
     alt->assign((size_t)K * 5 * HW, 0.0);
@@ -908,23 +926,29 @@ void render_partials(const orc_params& p, const int64_t* offsets, int K, const o
   std::vector<uint8_t> mask(nt), a1(HW, 0), open(HW, 1);
   for (int r = 0; r < K; ++r) {
     const int m = order ? order[r] : r;
-    if (order && r > 0)
+    const bool skipping = order && (r > 0 || sat_in);
+    if (skipping)
       for (int64_t i = 0; i < HW; ++i) {
-        open[i] = (uint8_t)(prefix[i] >= o.eps_comp);
-        sat_amb[i] = std::fabs(prefix[i] - o.eps_comp) <=
-                     (o.amb_T + prefix_rel[i] * (1.0 + o.amb_T)) * o.eps_comp;
-        if (amb && sat_amb[i]) amb[i] |= AMB_SAT;
+        if (sat_in) {
+          open[i] = (uint8_t)(r < (int)sat_in[i]);
+        } else {
+          open[i] = (uint8_t)(prefix[i] >= o.eps_comp);
+          sat_amb[i] = std::fabs(prefix[i] - o.eps_comp) <=
+                       (o.amb_T + prefix_rel[i] * (1.0 + o.amb_T)) * o.eps_comp;
+          if (amb && sat_amb[i]) amb[i] |= AMB_SAT;
+        }
         if (pskip && !open[i]) (*pskip)[(size_t)m * HW + i] = 1;
       }
     for (int t = 0; t < nt; ++t) {
       mask[t] = (uint8_t)(!tile_mask || tile_mask[t]);
-      if (order && r > 0 && mask[t]) {
+      if (skipping && mask[t]) {
+        // a tile with no open pixel is not rendered
         const int tx = t % tw, ty = t / tw;
-        double mx = 0.0;
+        bool any_open = false;
         for (int py = ty * B; py < std::min(H, (ty + 1) * B); ++py)
           for (int px = tx * B; px < std::min(W, (tx + 1) * B); ++px)
-            mx = std::max(mx, prefix[(int64_t)py * W + px]);
-        if (mx < o.eps_comp) {
+            any_open = any_open || open[(int64_t)py * W + px];
+        if (!any_open) {
           mask[t] = 0;
           skip[(size_t)m * nt + t] = 1;
         }
@@ -934,7 +958,7 @@ void render_partials(const orc_params& p, const int64_t* offsets, int K, const o
     std::fill(a1.begin(), a1.end(), 0);
     render_subset(&q, &cam, &o, mask.data(), C.data() + (size_t)m * 3 * HW,
                   T.data() + (size_t)m * HW, D.data() + (size_t)m * HW, nullptr, nullptr,
-                  a1.data(), stats, f, m, offsets[m], order && r > 0 ? open.data() : nullptr,
+                  a1.data(), stats, f, m, offsets[m], skipping ? open.data() : nullptr,
                   flips ? fl1.data() : nullptr, cdmax,
                   want_alt && r > 0 ? sat_amb.data() : nullptr,
                   want_alt ? alt->data() + (size_t)m * 5 * HW : nullptr);
@@ -955,6 +979,18 @@ void render_partials(const orc_params& p, const int64_t* offsets, int K, const o
           if (want_alt && r > 0 && sat_amb[i])
             dT = std::max(dT, std::fabs(alt->at(((size_t)m * 5 + 3) * HW + i) - Tb));
           prefix_rel[i] += dT > 0.0 ? (Tb - dT > 0.0 ? dT / (Tb - dT) : INFINITY) : 0.0;
+        }
+      }
+    if (order && sat_out)
+      for (int64_t i = 0; i < HW; ++i) {
+        const int lim = sat_in ? std::min((int)sat_in[i], K) : K;
+        if (decided[i] || r >= lim) continue;
+        if (sat_amb_out && std::fabs(prefix[i] - o.eps_comp) <=
+                               (o.amb_T + prefix_rel[i] * (1.0 + o.amb_T)) * o.eps_comp)
+          sat_amb_out[i] = 1;
+        if (prefix[i] < o.eps_comp) {
+          decided[i] = 1;
+          sat_out[i] = r + 1 < K ? (uint8_t)(r + 1) : (uint8_t)255;
         }
       }
   }
@@ -1175,11 +1211,12 @@ int orc_composite(int32_t K, int32_t H, int32_t W, const double* Cp, const doubl
 // separable, i.e. its monolithic contributor list (all Gaussians, no termination) is a
 // concatenation of per-subset runs in composite order (where Eq. 5 equals Eq. 2).
 // bd (nullable): flip bounds of the image and of every partial (orc_bounds).
-int orc_render_view(const orc_params* p, const int64_t* offsets, int32_t K, const orc_camera* cam,
-                    const orc_opts* o, const uint8_t* tile_mask, const int32_t* order,
-                    const float* cells, double* out, double* Tout, double* Cp, double* Tp,
-                    double* Dp, uint8_t* amb, uint8_t* sep, uint8_t* skip_out, int64_t* stats,
-                    orc_bounds* bd) {
+static int render_view_impl(const orc_params* p, const int64_t* offsets, int32_t K,
+                            const orc_camera* cam, const orc_opts* o, const uint8_t* tile_mask,
+                            const int32_t* order, const float* cells, double* out, double* Tout,
+                            double* Cp, double* Tp, double* Dp, uint8_t* amb, uint8_t* sep,
+                            uint8_t* skip_out, int64_t* stats, orc_bounds* bd,
+                            const uint8_t* sat_in, uint8_t* sat_out, uint8_t* sat_amb) {
   const int64_t HW = (int64_t)cam->width * cam->height;
   std::vector<double> C, T, D;
   std::vector<uint8_t> a(HW, 0), skip;
@@ -1189,7 +1226,8 @@ int orc_render_view(const orc_params* p, const int64_t* offsets, int32_t K, cons
   std::vector<uint8_t> sat_alt;
   double cd[2] = {0.0, 0.0};
   render_partials(*p, offsets, K, *cam, *o, tile_mask, order, C, T, D, skip, a.data(), stats,
-                  cells ? &cf : nullptr, nullptr, bd ? flips : nullptr, cd, &sat_alt, &alt);
+                  cells ? &cf : nullptr, nullptr, bd ? flips : nullptr, cd, &sat_alt, &alt,
+                  sat_in, sat_out, sat_amb);
   if (skip_out) std::memcpy(skip_out, skip.data(), skip.size());
   orc_composite(K, cam->height, cam->width, C.data(), T.data(), D.data(), o, out, Tout, nullptr,
                 a.data(), nullptr, nullptr);
@@ -1307,15 +1345,40 @@ int orc_render_view(const orc_params* p, const int64_t* offsets, int32_t K, cons
   return 0;
 }
 
+int orc_render_view(const orc_params* p, const int64_t* offsets, int32_t K, const orc_camera* cam,
+                    const orc_opts* o, const uint8_t* tile_mask, const int32_t* order,
+                    const float* cells, double* out, double* Tout, double* Cp, double* Tp,
+                    double* Dp, uint8_t* amb, uint8_t* sep, uint8_t* skip_out, int64_t* stats,
+                    orc_bounds* bd) {
+  return render_view_impl(p, offsets, K, cam, o, tile_mask, order, cells, out, Tout, Cp, Tp, Dp,
+                          amb, sep, skip_out, stats, bd, nullptr, nullptr, nullptr);
+}
+
+// orc_render_view with the view's stale saturation state (Sec. 4.2 step 2; render_partials
+// gives the rule): sat_in [H][W] (required, with order) prunes ranks >= sat_in at each
+// pixel; sat_out [H][W] receives the state re-evaluated from this render's partials and
+// sat_amb [H][W] (nullable) the pixels whose re-evaluation met a prefix within the AMB_SAT
+// band of eps_comp.
+int orc_render_view_pruned(const orc_params* p, const int64_t* offsets, int32_t K,
+                           const orc_camera* cam, const orc_opts* o, const uint8_t* tile_mask,
+                           const int32_t* order, const float* cells, double* out, double* Tout,
+                           double* Cp, double* Tp, double* Dp, uint8_t* amb, uint8_t* skip_out,
+                           int64_t* stats, orc_bounds* bd, const uint8_t* sat_in,
+                           uint8_t* sat_out, uint8_t* sat_amb) {
+  if (!order || !sat_in) return -1;
+  return render_view_impl(p, offsets, K, cam, o, tile_mask, order, cells, out, Tout, Cp, Tp, Dp,
+                          amb, nullptr, skip_out, stats, bd, sat_in, sat_out, sat_amb);
+}
+
 // Backward of one view [Eq. 6-7 and the chain through Eq. 1-4 and the projection].
 // dLdC [3][H][W] and dLdT [H][W] (nullable) are the loss gradients w.r.t. the composited
 // image and total transmittance.  Gradients are written (not accumulated) to g.
 // tile_mask (nullable) restricts the adjoint to pixels of tiles with a nonzero entry,
 // as if dLdC and dLdT were zero elsewhere.
-int orc_backward_view(const orc_params* p, const int64_t* offsets, int32_t K,
-                      const orc_camera* cam, const orc_opts* o, const double* dLdC,
-                      const double* dLdT, const uint8_t* tile_mask, const int32_t* order,
-                      const float* cells, const orc_grads* gr) {
+static int backward_view_impl(const orc_params* p, const int64_t* offsets, int32_t K,
+                              const orc_camera* cam, const orc_opts* o, const double* dLdC,
+                              const double* dLdT, const uint8_t* tile_mask, const int32_t* order,
+                              const float* cells, const orc_grads* gr, const uint8_t* sat_in) {
   const int W = cam->width, H = cam->height, B = o->tile;
   const int64_t HW = (int64_t)W * H;
   const int nc = (p->sh_degree + 1) * (p->sh_degree + 1);
@@ -1330,7 +1393,7 @@ int orc_backward_view(const orc_params* p, const int64_t* offsets, int32_t K,
   std::vector<double> C, T, D;
   std::vector<uint8_t> skip, pskip;
   render_partials(*p, offsets, K, *cam, *o, tile_mask, order, C, T, D, skip, nullptr, nullptr, fp,
-                  &pskip);
+                  &pskip, nullptr, nullptr, nullptr, nullptr, sat_in);
   // per-Gaussian 2-D gradients: u, v, A, B, C, o, r, g, b (threads add atomically)
   std::vector<double> g2((size_t)p->n * 9, 0.0);
   const int tw = (W + B - 1) / B, th = (H + B - 1) / B;
@@ -1523,6 +1586,25 @@ int orc_backward_view(const orc_params* p, const int64_t* offsets, int32_t K,
     for (int k = 0; k < 4; ++k) gq[k] = (gqh[k] - g.qhat[k] * dq) / g.qnorm;
   }
   return 0;
+}
+
+int orc_backward_view(const orc_params* p, const int64_t* offsets, int32_t K,
+                      const orc_camera* cam, const orc_opts* o, const double* dLdC,
+                      const double* dLdT, const uint8_t* tile_mask, const int32_t* order,
+                      const float* cells, const orc_grads* gr) {
+  return backward_view_impl(p, offsets, K, cam, o, dLdC, dLdT, tile_mask, order, cells, gr,
+                            nullptr);
+}
+
+// orc_backward_view of the render with the stale saturation state sat_in [H][W] (the
+// partials of orc_render_view_pruned).
+int orc_backward_view_pruned(const orc_params* p, const int64_t* offsets, int32_t K,
+                             const orc_camera* cam, const orc_opts* o, const double* dLdC,
+                             const double* dLdT, const uint8_t* tile_mask, const int32_t* order,
+                             const float* cells, const orc_grads* gr, const uint8_t* sat_in) {
+  if (!order || !sat_in) return -1;
+  return backward_view_impl(p, offsets, K, cam, o, dLdC, dLdT, tile_mask, order, cells, gr,
+                            sat_in);
 }
 
 // Which clamp branches of the adjoint one view exercises, so that a finite-difference pin

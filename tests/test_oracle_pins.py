@@ -735,6 +735,114 @@ def test_saturation_skipping_drops_a_front_subset_when_ordered_wrongly():
     assert np.abs(wrong["image"] - full["image"]).max() > 1e-2
 
 
+def _prefix_state(Tp, order, eps, lim=None):
+    """Brute force of the re-evaluated saturation state from the partial transmittances:
+    r + 1 for the first rank r (below lim) whose prefix product is below eps, else 255
+    (also when r + 1 = K)."""
+    K, H, W = Tp.shape
+    lim = np.full((H, W), K) if lim is None else np.minimum(lim.astype(int), K)
+    out = np.full((H, W), 255, np.uint8)
+    done = np.zeros((H, W), bool)
+    prefix = np.ones((H, W))
+    for r, m in enumerate(order):
+        prefix = prefix * Tp[m]
+        hit = ~done & (r < lim) & (prefix < eps)
+        out[hit] = r + 1 if r + 1 < K else 255
+        done |= hit
+    return out
+
+
+def test_stale_state_prunes_exactly_the_ranks_it_names():
+    # Sec. 4.2 step 2: with a view's stale state sat, the subset at rank r leaves pixel p
+    # empty exactly when r >= sat[p]; every other pixel of every partial is the full
+    # render's, and a tile with no open pixel is not rendered.  Random states, including
+    # 0 (even the front subset pruned) and values >= K (nothing pruned)
+    sc, off, boxes = _saturating_slabs(24, half_middle=True)
+    cam = _cam(64, 48)
+    order = O.cell_order(boxes, cam.eye)
+    o = O.opts()
+    K = len(order)
+    full = O.render_view(sc, off, cam, o)
+    rng = np.random.default_rng(3)
+    sat = rng.choice(np.array([0, 1, 2, 3, 200, 255], np.uint8), (cam.height, cam.width))
+    sat[:16, :16] = 1  # one tile where only the front subset is open
+    sat[16:32, 16:32] = 0  # one tile pruned from every subset
+    st = O.render_view(sc, off, cam, o, order=order, sat=sat)
+    B = 16
+    tw, th = (cam.width + B - 1) // B, (cam.height + B - 1) // B
+    for r, m in enumerate(order):
+        shut = r >= sat
+        assert np.all(st["Cp"][m][:, shut] == 0.0)
+        assert np.all(st["Tp"][m][shut] == 1.0) and np.all(st["Dp"][m][shut] == 0.0)
+        np.testing.assert_array_equal(st["Cp"][m][:, ~shut], full["Cp"][m][:, ~shut])
+        np.testing.assert_array_equal(st["Tp"][m][~shut], full["Tp"][m][~shut])
+        pad = np.ones((th * B, tw * B), bool)
+        pad[:cam.height, :cam.width] = shut
+        expect = pad.reshape(th, B, tw, B).all(axis=(1, 3)).reshape(-1)
+        assert np.array_equal(st["skip"][m].astype(bool), expect)
+    assert st["skip"][order[0]][tw + 1] == 1 and st["skip"][order[1]][0] == 1
+    # the image is the composite of these partials; the re-evaluated state follows from
+    # them, examining the ranks below min(sat, K) only
+    np.testing.assert_array_equal(st["sat"], _prefix_state(st["Tp"], order, o.eps_comp, sat))
+    assert K == 3
+
+
+def test_stale_state_of_a_visit_reproduces_the_exact_skip_on_the_next():
+    # a first visit prunes nothing (state 255) and renders the full image; its re-evaluated
+    # state is the first saturated rank of each pixel (brute force from its partials).  The
+    # next visit with that state renders exactly the partials, skip flags, image and
+    # gradients of the exact (same-visit) saturation skip, and re-evaluates to the same state
+    sc, off, boxes = _saturating_slabs(25, half_middle=True)
+    cam = _cam(64, 48)
+    order = O.cell_order(boxes, cam.eye)
+    o = O.opts()
+    none = np.full((cam.height, cam.width), 255, np.uint8)
+    full = O.render_view(sc, off, cam, o)
+    v1 = O.render_view(sc, off, cam, o, order=order, sat=none)
+    for key in ("image", "T", "Cp", "Tp", "Dp"):
+        np.testing.assert_array_equal(v1[key], full[key])
+    assert v1["skip"].sum() == 0
+    s1 = v1["sat"]
+    np.testing.assert_array_equal(s1, _prefix_state(v1["Tp"], order, o.eps_comp))
+    assert (s1 == 2).sum() > 0 and (s1 == 255).sum() > 0  # pruned after two slabs, and open
+    exact = O.render_view(sc, off, cam, o, order=order)
+    v2 = O.render_view(sc, off, cam, o, order=order, sat=s1)
+    for key in ("image", "T", "Cp", "Tp", "Dp", "skip"):
+        np.testing.assert_array_equal(v2[key], exact[key])
+    np.testing.assert_array_equal(v2["sat"], s1)
+    rng = np.random.default_rng(4)
+    dC = rng.standard_normal((3, cam.height, cam.width))
+    g_exact = O.backward_view(sc, off, cam, dC, None, o, order=order)
+    g_stale = O.backward_view(sc, off, cam, dC, None, o, order=order, sat=s1)
+    for a, b in zip(g_exact, g_stale):  # (the oracle adds 2-D gradients in thread order)
+        np.testing.assert_allclose(b, a, atol=1e-12, rtol=1e-10)
+
+
+def test_stale_state_brings_pruned_ranks_back_when_the_front_clears():
+    # the front slab turns nearly transparent after the state was taken: the stale visit
+    # still prunes the back slab (its image misses it: the cost of a stale state), its
+    # re-evaluation finds the prefix above eps_comp up to the old state and brings every
+    # pruned rank back, and the visit after that renders the full image again
+    sc, off, boxes = _saturating_slabs(26)
+    cam = _cam(64, 48)
+    order = O.cell_order(boxes, cam.eye)
+    o = O.opts()
+    none = np.full((cam.height, cam.width), 255, np.uint8)
+    s1 = O.render_view(sc, off, cam, o, order=order, sat=none)["sat"]
+    assert (s1 < 255).sum() > 0
+    logits = sc.opacity_logits.copy()
+    logits[: off[2]] = -6.0  # the front and middle slabs nearly transparent
+    sc2 = I.Scene(sc.means, sc.log_scales, sc.quats, logits, sc.sh, sc.sh_degree)
+    full2 = O.render_view(sc2, off, cam, o)
+    v2 = O.render_view(sc2, off, cam, o, order=order, sat=s1)
+    back = s1 <= 2  # pixels where the back slab was pruned
+    assert np.abs(v2["image"] - full2["image"]).max(axis=0)[back].max() > 1e-2
+    np.testing.assert_array_equal(v2["sat"], _prefix_state(v2["Tp"], order, o.eps_comp, s1))
+    assert np.all(v2["sat"][back] == 255)
+    v3 = O.render_view(sc2, off, cam, o, order=order, sat=v2["sat"])
+    np.testing.assert_allclose(v3["image"], full2["image"], atol=1e-12, rtol=0)
+
+
 # --------------------------------------------------------------------------- D-SSIM loss
 def test_ssim_window_sum_is_the_windowed_sum():
     # brute force: every output pixel sums the 11 x 11 window of weights w_i w_j over the
