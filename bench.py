@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--stale", action="store_true",
+                    help="skip by each view's stale saturation state instead of the waves")
     ap.add_argument("--unfused-adam", action="store_true",
                     help="backward into gradient arrays and a separate Adam pass")
     ap.add_argument("--no-skip", action="store_true",
@@ -542,7 +544,8 @@ def batched_leg(args, ctx, dev, sc, off, cams, targets, o, ctas, order, stream, 
     from paper_2606_18588_gb300.train import BatchedStep
     with torch.cuda.stream(stream):
         st = BatchedStep(ctx, dev, off, sc.sh_degree, cams, [torch.from_numpy(t) for t in targets],
-                         o, stream=stream, order=order, fused_adam=not args.unfused_adam)
+                         o, stream=stream, order=order, fused_adam=not args.unfused_adam,
+                         stale=args.stale and order is not None)
         st.batch.set_timing(True)
         st.batch.set_launch(ctas)
         st.run()  # eager once: sizes everything, checks status
@@ -712,6 +715,19 @@ def main():
                   "ms_per_step_median": h0["step_ms_median"], "steps": args.steps,
                   "kernel_ms": h0["kmean"], "timing": "CUDA events, graph replays back to back",
                   "path": "the batched graph with every subset rendered (no saturation skipping)"}
+    # the same skipping driven by each view's state from its previous visit (the previous
+    # step): one sort and one rasteriser launch per step instead of the waves
+    stale = None
+    if not args.no_plain and order is not None and not args.stale:
+        import argparse
+        st1, h1 = batched_leg(argparse.Namespace(**{**vars(args), "stale": True}), ctx, dev, sc,
+                              off, cams, targets, o, ctas, order, stream, barrier, world)
+        st1.close()
+        stale = {"mpixel_s": h1["value"], "ms_per_step": h1["ms"],
+                 "ms_per_step_median": h1["step_ms_median"], "steps": args.steps,
+                 "kernel_ms": h1["kmean"], "timing": "CUDA events, graph replays back to back",
+                 "path": "saturation skipping by the stale state of each view (set by the "
+                         "previous step's composite), one launch per stage"}
     plain = None
     if not args.no_plain and args.plain_steps > 0:
         plain = plain_leg(args, ctx, dev, sc, off, cams, targets, o, stream, barrier, world)
@@ -733,7 +749,7 @@ def main():
     # with saturation skipping the sort and the forward rasteriser run as waves of view groups
     # on several streams side by side: only their span together is a kernel time, so the
     # forward's fraction is taken over that span (a lower bound) and the sort gets none
-    overlapped = order is not None and len(cams) >= 2
+    overlapped = order is not None and len(cams) >= 2 and not args.stale
     for name in ("raster_fwd", "raster_bwd", "sort", "composite", "composite_bwd", "project",
                  "project_bwd", "fill", "adam"):
         t = kmean.get("loss+adam" if name == "adam" else name)
@@ -768,14 +784,18 @@ def main():
                        "waves": ("sort + raster_fwd of up to 4 view groups on their own "
                                  "streams, side by side; kernel_ms sort and raster_fwd are the "
                                  "first group's stream's intervals, their sum the waves' span")
-                                if order is not None else None,
+                                if order is not None and not args.stale else None,
+                       "stale_state": ("saturation skipping by each view's state from its "
+                                       "previous visit (the previous step), one sort and one "
+                                       "forward rasteriser launch per step"
+                                       if args.stale and order is not None else None),
                        "timing": "CUDA events around the back-to-back graph replays (no host "
                                  "wait between them); per-kernel times from the graph's "
                                  "timing ring, every replay",
                        "ms_per_step_median": head["step_ms_median"],
                        "l2": "inputs larger than L2 (2.4 GB parameters, 10 GB projected records)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "batched_noskip": noskip, "plain": plain, "kernel_ms": kmean,
+                       "batched_noskip": noskip, "batched_stale": stale, "plain": plain, "kernel_ms": kmean,
                        "counters": counts, "kernel_rooflines": others},
             "roofline": roof, "e2e": e2e, "clocks": clk,
             "gpu_launches": head["launches_per_step"] * args.steps}

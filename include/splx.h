@@ -329,6 +329,26 @@ int splx_batch_set_cross_filter(splx_batch_t b, const float* cells);
  * permutation of 0..K-1, else SPLX_ERR_INVALID.  Synchronises; applies to launches
  * issued afterwards. */
 int splx_batch_set_order(splx_batch_t b, const int32_t* order);
+/* Stale saturation state (Sec. 4.2 step 2: the pixels that one visit's composition finds
+ * saturated leave the subsets behind in the view's next visit).  sat (host array of V)
+ * holds one device plane per view, sat[v] of H_v * W_v bytes (row-major, owned by the
+ * caller, kept alive while set).  Value s at a pixel prunes the subsets of rank >= s in
+ * the view's order (splx_batch_set_order): they leave the pixel empty as in the waves
+ * above.  Values >= K prune nothing: fill a plane with 255 for a view's first visit.
+ * While set, each forward renders with one sort and one rasteriser launch (no waves),
+ * leaves out every (view, subset, tile) work item pruned at all its pixels, and after the
+ * composite overwrites each plane with the state re-evaluated from this visit's partials:
+ * the first rank r + 1 whose prefix (FP32 product of the partial transmittances of ranks
+ * 0..r, in order) is below eps_comp, among ranks below the old state, else 255.  Pruned
+ * ranks count as transparent there, so a pixel whose prefix no longer saturates gets all
+ * of them back at the next visit.  A visit after an identical one renders exactly what
+ * the waves render; when the scene changed in between, the pruned pixels miss what the
+ * pruned subsets would now add (the price of a stale state).  The state belongs to the
+ * view's pose and order: reset it (255) when either changes.  NULL turns it off.
+ * SPLX_ERR_STATE without an order, SPLX_ERR_INVALID for a NULL plane.  Synchronises;
+ * applies to launches issued afterwards (a captured graph reads the planes set when it
+ * replays). */
+int splx_batch_set_stale(splx_batch_t b, uint8_t* const* sat);
 /* Largest number of persistent forward / backward rasteriser CTAs resident on one SM at
  * the batch's tile side (host outputs). */
 int splx_batch_max_ctas_per_sm(splx_batch_t b, int32_t* fwd, int32_t* bwd);

@@ -233,6 +233,11 @@ struct Plan {
   uint2* chunks_g[kGroups - 1] = {};
   unsigned* chunk_count_g[kGroups - 1] = {};
   int32_t* order_d = nullptr;              // [V][K] front-to-back subset order (skipping on)
+  int32_t* rank_d = nullptr;               // [V][K] rank of subset k in view v's order
+  // stale saturation state (with order_d): device table of the V views' state planes;
+  // the forward then runs one launch per stage and re-evaluates the states in place
+  uint8_t** sat_d = nullptr;
+  bool stale() const { return sat_d && order_d; }
   uint32_t* omega = nullptr;               // [V][K][4] visible regions (internal partials only)
   bool visibility = false;                 // use omega (batches and server launches)
   float* tpre = nullptr;                   // [total pixels] prefix transmittance of the waves
@@ -325,6 +330,8 @@ struct Plan {
     b.item_lo = 0;
     b.item_n = K > 0 ? n_tiles / K : 0;
     b.tpre = tpre;
+    b.sat = stale() ? sat_d : nullptr;
+    b.rank = rank_d;
     // composite-only plans carry no subsets; their offsets are unused
     for (int k = 0; k <= K; ++k) b.goff[k] = k < (int)subsets_h.size() ? subsets_h[k].goff : N;
     for (int v = 0; v <= V; ++v) { b.tile_base[v] = tile_base[v]; b.pix_off[v] = pix_off[v]; }
@@ -342,7 +349,8 @@ struct Plan {
                    (void**)&keys_alt, (void**)&big_list, (void**)&big_count, (void**)&chunks,
                    (void**)&chunk_count, (void**)&ranges,
                    (void**)&grad2d, (void**)&scan_temp, (void**)&counters, (void**)&work_ctr,
-                   (void**)&order_d, (void**)&tpre, (void**)&omega, (void**)&cells_d,
+                   (void**)&order_d, (void**)&rank_d, (void**)&sat_d, (void**)&tpre,
+                   (void**)&omega, (void**)&cells_d,
                    (void**)&cross, (void**)&zr, (void**)&removed, (void**)&omega_x,
                    (void**)&zr_x};
     for (void** p : ps) free_ptr(*p, s);
@@ -391,7 +399,9 @@ struct Plan {
     launch_fill(b, s);
     CK_LAUNCH();
     mark(3, s);
-    if (!order_d) {  // with saturation skipping each wave sorts its own segments
+    // with saturation-skipping waves each wave sorts its own segments; with a stale state
+    // one sort covers the tiles it leaves open
+    if (!order_d || stale()) {
       launch_seg_sort(b, merge_rounds_bound(max_subset()), s);
       CK_LAUNCH();
     }
@@ -1157,15 +1167,17 @@ int splx_batch_forward(splx_batch_t bt, float* out_rgb, float* out_T, splx_strea
   BatchDev b = P.dev();
   b.out_rgb = out_rgb;
   b.out_T = out_T;
-  if (P.order_d) {
+  if (P.order_d && !P.stale()) {
     // saturation skipping: K waves, each sorting and rendering one subset of every view,
     // front to back
     if ((r = P.waves(b, s))) return r;
   } else {
+    // (with a stale saturation state the rasteriser leaves the pruned pixels empty)
     launch_raster_fwd(b, s);
   }
   P.mark(5, s);
   launch_composite(b, P.total_pixels, s);
+  if (P.stale()) launch_sat_update(b, P.order_d, P.total_pixels, s);
   P.mark(6, s);
   CK_LAUNCH();
   bt->forward_done = true;
@@ -1315,6 +1327,8 @@ int splx_batch_set_order(splx_batch_t bt, const int32_t* order) {
   CtxScope scope(P.ctx);
   if (!order) {
     P.free_ptr((void*&)P.order_d, nullptr);
+    P.free_ptr((void*&)P.rank_d, nullptr);
+    P.free_ptr((void*&)P.sat_d, nullptr);
     P.free_ptr((void*&)P.tpre, nullptr);
     return SPLX_OK;
   }
@@ -1327,12 +1341,38 @@ int splx_batch_set_order(splx_batch_t bt, const int32_t* order) {
   }
   int r;
   if (!P.order_d && (r = ctx_alloc_t(P.ctx, &P.order_d, (size_t)P.V * P.K, nullptr))) return r;
-  if (!P.tpre &&
-      (r = ctx_alloc_t(P.ctx, &P.tpre, (size_t)std::max<int64_t>(P.total_pixels, 1), nullptr))) {
+  if (!P.rank_d && (r = ctx_alloc_t(P.ctx, &P.rank_d, (size_t)P.V * P.K, nullptr))) {
     P.free_ptr((void*&)P.order_d, nullptr);
     return r;
   }
+  if (!P.tpre &&
+      (r = ctx_alloc_t(P.ctx, &P.tpre, (size_t)std::max<int64_t>(P.total_pixels, 1), nullptr))) {
+    P.free_ptr((void*&)P.order_d, nullptr);
+    P.free_ptr((void*&)P.rank_d, nullptr);
+    return r;
+  }
+  std::vector<int32_t> rank((size_t)P.V * P.K);
+  for (int v = 0; v < P.V; ++v)
+    for (int q = 0; q < P.K; ++q) rank[(size_t)v * P.K + order[v * P.K + q]] = q;
   CK(cudaMemcpy(P.order_d, order, sizeof(int32_t) * P.V * P.K, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(P.rank_d, rank.data(), sizeof(int32_t) * P.V * P.K, cudaMemcpyHostToDevice));
+  return SPLX_OK;
+}
+
+int splx_batch_set_stale(splx_batch_t bt, uint8_t* const* sat) {
+  if (!bt) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  CtxScope scope(P.ctx);
+  if (!sat) {
+    P.free_ptr((void*&)P.sat_d, nullptr);
+    return SPLX_OK;
+  }
+  if (!P.order_d) return SPLX_ERR_STATE;
+  for (int v = 0; v < P.V; ++v)
+    if (!sat[v]) return SPLX_ERR_INVALID;
+  int r;
+  if (!P.sat_d && (r = ctx_alloc_t(P.ctx, &P.sat_d, (size_t)P.V, nullptr))) return r;
+  CK(cudaMemcpy(P.sat_d, sat, sizeof(uint8_t*) * P.V, cudaMemcpyHostToDevice));
   return SPLX_OK;
 }
 
@@ -1382,7 +1422,7 @@ static int kernel_times_of(const Plan& P, const splx_graph_s* g, int slot, float
     CK(cudaEventElapsedTime(&ms, E(P.ev[pairs[i][0]]), E(P.ev[pairs[i][1]])));
     ms_out[i] = ms;
   }
-  if (P.order_d && (int)P.wev.size() == 2 * P.K + 1) {
+  if (P.order_d && !P.stale() && (int)P.wev.size() == 2 * P.K + 1) {
     // waves interleave sort and rasteriser: sum each over the waves
     float sort = 0.0f, ras = 0.0f;
     for (int r = 0; r < P.K; ++r) {

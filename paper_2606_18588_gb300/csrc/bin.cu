@@ -319,6 +319,8 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_sort_small(const BatchDev 
   if (n <= 1) return;
   // saturation-skipping waves sort only what the wave's rasteriser will walk
   if (b.order && b.wave > 0 && item_saturated(b, t)) return;
+  // likewise with a stale saturation state: a tile pruned at every pixel stays unsorted
+  if (b.sat && item_pruned(b, t)) return;
   if (n > kChunk) {
     const unsigned nch = (unsigned)((n + kBig - 1) / kBig);
     if (threadIdx.x == 0) {

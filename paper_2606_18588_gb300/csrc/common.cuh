@@ -152,6 +152,12 @@ struct BatchDev {
   // in order), so that groups of views can run their waves side by side
   int64_t item_lo, item_n;
   float* tpre;
+  // stale saturation state (sat != nullptr, one launch per stage instead of waves): view
+  // v's state sat[v] [H_v][W_v] prunes the subsets of rank >= sat[v][p] in its
+  // front-to-back order at pixel p (values >= K prune nothing); rank [V][K] is the rank of
+  // subset k in view v's order
+  uint8_t* const* sat;
+  const int32_t* rank;
   // persistent rasterisers: grid size (0 = one CTA per work item) and the two work
   // counters they take items from ([0] forward, [1] backward; reset before each launch)
   int persist_grid;
@@ -195,6 +201,10 @@ inline int64_t chunk_list_capacity(int64_t n_tiles, int64_t capacity) {
 void launch_raster_fwd(const BatchDev& b, cudaStream_t s);
 void launch_composite(const BatchDev& b, int64_t total_pixels, cudaStream_t s);
 void launch_composite_bwd(const BatchDev& b, int64_t total_pixels, cudaStream_t s);
+// Re-evaluates every view's stale saturation state (b.sat) from the partials just rendered:
+// order [V][K] is each view's front-to-back subset order.
+void launch_sat_update(const BatchDev& b, const int32_t* order, int64_t total_pixels,
+                       cudaStream_t s);
 void launch_raster_bwd(const BatchDev& b, cudaStream_t s);
 // Largest number of persistent rasteriser CTAs that fit on one SM (0 on error).
 int raster_max_ctas_per_sm(int tile, bool bwd);
@@ -307,6 +317,26 @@ __device__ __forceinline__ bool cross_removed(const BatchDev& b, int v, int k,
     if (dbits >= lo && dbits <= hi) return true;
   }
   return false;
+}
+
+// Stale-state test of work item `id` (a whole tile of subset k in view v): true if every
+// pixel of the tile has subset k pruned (its rank >= the pixel's state).  Whole-CTA call;
+// the rasteriser and the segment sort take the same decision.
+__device__ __forceinline__ bool item_pruned(const BatchDev& b, int64_t id) {
+  const int v = view_of(b.tile_base, b.V, id);
+  const ViewDev& cam = b.views[v];
+  const int64_t nt = (int64_t)cam.tiles_x * cam.tiles_y;
+  const int k = (int)((id - b.tile_base[v]) / nt);
+  const int64_t t = (id - b.tile_base[v]) - (int64_t)k * nt;
+  const int x0 = (int)(t % cam.tiles_x) * b.tile, y0 = (int)(t / cam.tiles_x) * b.tile;
+  const uint8_t* sp = b.sat[v];
+  const int rk = b.rank[v * b.K + k];
+  bool open = false;
+  for (int i = threadIdx.x; i < b.tile * b.tile; i += blockDim.x) {
+    const int x = x0 + i % b.tile, y = y0 + i / b.tile;
+    if (x < cam.W && y < cam.H) open |= (int)sp[(int64_t)y * cam.W + x] > rk;
+  }
+  return !__syncthreads_or(open);
 }
 
 // Whether tile (tx, ty) of view v lies in subset k's visible region (always, if off).

@@ -153,6 +153,51 @@ static void dispatch(const BatchDev& b, int64_t total, bool bwd, cudaStream_t s)
 void launch_composite(const BatchDev& b, int64_t total, cudaStream_t s) { dispatch(b, total, false, s); }
 void launch_composite_bwd(const BatchDev& b, int64_t total, cudaStream_t s) { dispatch(b, total, true, s); }
 
+// ---------------------------------------------------------------- stale saturation state
+// Sec. 4.2 step 2: the composition of this visit finds the pixels where the subsets in
+// front have saturated; in the view's next visit the subsets behind leave those pixels.
+// Per pixel: the prefix product of the partial transmittances in the view's front-to-back
+// order (FP32, multiplied in that order, as the exact waves do), over the ranks below the
+// old state (ranks at or beyond it were left empty); the new state is the first rank whose
+// prefix before it is below eps_comp, or 255 (none).  Ranks pruned by the old state count
+// as transparent, so where the prefix no longer saturates they all come back.  Subsets
+// whose visible region leaves the pixel's tile out have no partial there (transparent).
+__global__ void __launch_bounds__(256) k_sat_update(const BatchDev b,
+                                                    const int32_t* __restrict__ order,
+                                                    int64_t total) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int v = view_of(b.pix_off, b.V, q);
+    const int64_t p = q - b.pix_off[v];
+    const ViewDev& cam = b.views[v];
+    const int px = (int)(p % cam.W), py = (int)(p / cam.W);
+    const int tx = px / b.tile, ty = py / b.tile;
+    uint8_t* sp = b.sat[v];
+    const int lim = min((int)sp[p], b.K);
+    float prefix = 1.0f;
+    int out = 255;
+    for (int r = 0; r < lim; ++r) {
+      const int k = order[v * b.K + r];
+      if (!in_omega(b, v, k, tx, ty)) continue;
+      prefix *= b.imgs[v * b.K + k].T[p];
+      if (prefix < b.eps_comp) {
+        out = r + 1 < b.K ? r + 1 : 255;
+        break;
+      }
+    }
+    sp[p] = (uint8_t)out;
+  }
+}
+
+void launch_sat_update(const BatchDev& b, const int32_t* order, int64_t total, cudaStream_t s) {
+  if (total <= 0 || !b.sat) return;
+  int64_t blocks = (total + 255) / 256;
+  const int64_t cap = (int64_t)device_sm_count() * 16;
+  if (blocks > cap) blocks = cap;
+  k_sat_update<<<(unsigned)blocks, 256, 0, s>>>(b, order, total);
+  count_launch();
+}
+
 // ---------------------------------------------------------------- L1 loss
 __global__ void __launch_bounds__(256) k_loss_l1(const float* __restrict__ img, const float* __restrict__ tgt,
                                                  int64_t n, float* loss, float* __restrict__ dL) {

@@ -260,19 +260,31 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
   }
   const ImgDev im = b.imgs[ti.v * b.K + ti.k];
   const int64_t HW = (int64_t)ti.W * ti.H;
-  if (b.order && b.wave > 0) {
+  if ((b.order && b.wave > 0) || b.sat) {
     const unsigned inb = live;  // slots inside the image
     // saturation skipping: a pixel where the subsets rendered before this one took the
     // transmittance below eps_comp leaves this subset's pixel set (the composite would
     // skip this subset there anyway): it stays empty (T = 1, no contributor); a tile with
-    // no open pixel is left empty as a whole
-    const float* tp = b.tpre + b.pix_off[ti.v];
+    // no open pixel is left empty as a whole.  With a stale saturation state the pixel
+    // set is the one the state names (ranks below the pixel's state)
+    if (b.sat) {
+      const uint8_t* sp = b.sat[ti.v];
+      const int rk = b.rank[ti.v * b.K + ti.k];
 #pragma unroll
-    for (int i = 0; i < PPT; ++i)
-      if ((live >> i) & 1u &&
-          !(tp[(int64_t)(ti.y + 4 * slot_row<PPT>(i)) * ti.W + ti.x + 8 * slot_col<PPT>(i)] >=
-            b.eps_comp))
-        live &= ~(1u << i);
+      for (int i = 0; i < PPT; ++i)
+        if ((live >> i) & 1u &&
+            !((int)sp[(int64_t)(ti.y + 4 * slot_row<PPT>(i)) * ti.W + ti.x + 8 * slot_col<PPT>(i)] >
+              rk))
+          live &= ~(1u << i);
+    } else {
+      const float* tp = b.tpre + b.pix_off[ti.v];
+#pragma unroll
+      for (int i = 0; i < PPT; ++i)
+        if ((live >> i) & 1u &&
+            !(tp[(int64_t)(ti.y + 4 * slot_row<PPT>(i)) * ti.W + ti.x + 8 * slot_col<PPT>(i)] >=
+              b.eps_comp))
+          live &= ~(1u << i);
+    }
     if (!__syncthreads_or(live != 0)) {
       if (kCount && threadIdx.x == 0 && b.counters) atomicAdd(b.counters + 6, 1ull);
 #pragma unroll

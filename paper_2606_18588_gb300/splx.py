@@ -93,6 +93,7 @@ _sigs = {
     "splx_batch_counters": (C.c_int, [_P, _P, _P]),
     "splx_batch_set_launch": (C.c_int, [_P, C.c_int32]),
     "splx_batch_set_order": (C.c_int, [_P, _P]),
+    "splx_batch_set_stale": (C.c_int, [_P, _P]),
     "splx_batch_set_visibility": (C.c_int, [_P, C.c_int32]),
     "splx_batch_set_cross_filter": (C.c_int, [_P, _P]),
     "splx_batch_loss_l1_dssim": (C.c_int, [_P, _P, _P, C.c_float, _P, _P, _P]),
@@ -553,6 +554,23 @@ class Batch:
             raise ValueError(f"order must be [{self.V}, {self.K}]")
         _check(_lib.splx_batch_set_order(self.h, a.ctypes.data_as(C.c_void_p)),
                "splx_batch_set_order")
+
+    def set_stale(self, planes):
+        """Stale saturation state: `planes` is a list of V uint8 CUDA tensors, plane v of
+        H_v * W_v elements (255: nothing pruned), kept alive by the caller and rewritten by
+        every forward; None turns it off.  See splx_batch_set_stale."""
+        if planes is None:
+            _check(_lib.splx_batch_set_stale(self.h, None), "splx_batch_set_stale")
+            self._stale = None
+            return
+        if len(planes) != self.V:
+            raise ValueError(f"need {self.V} planes")
+        for t, (h, w) in zip(planes, self.sizes):
+            if t.dtype != torch.uint8 or not t.is_cuda or t.numel() != h * w or not t.is_contiguous():
+                raise ValueError("each plane must be a contiguous CUDA uint8 tensor of H*W")
+        arr = (C.c_void_p * self.V)(*[t.data_ptr() for t in planes])
+        _check(_lib.splx_batch_set_stale(self.h, arr), "splx_batch_set_stale")
+        self._stale = list(planes)
 
     def max_ctas_per_sm(self) -> tuple[int, int]:
         f, b = C.c_int32(0), C.c_int32(0)

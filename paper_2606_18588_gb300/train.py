@@ -62,9 +62,12 @@ class BatchedStep:
     def __init__(self, ctx: S.Context, params: dict, offsets, sh_degree: int, cams, targets,
                  opts: S.Opts | None = None, lr=DEFAULT_LR, pair_capacity: int = 0,
                  stream: torch.cuda.Stream | None = None, order=None, dssim: float = 0.0,
-                 fused_adam: bool = True):
+                 fused_adam: bool = True, stale: bool = False):
         """order: optional [V, K] front-to-back subset order per view, which turns on
         saturation skipping (visibility.orders_for_views gives it for k-d cells).
+        stale: with an order, skip by each view's stale saturation state (Sec. 4.2 step 2)
+        instead of the exact waves: one launch per stage, the state of this batch's views
+        kept on the device and refreshed by every forward (reset by set_views).
         dssim: weight lambda of the D-SSIM term (0: plain L1).
         fused_adam: Adam runs inside the projection adjoint (no gradient arrays); False
         runs the backward into gradient arrays and a separate Adam pass (same result)."""
@@ -80,8 +83,13 @@ class BatchedStep:
         self.step_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
         self.batch = S.Batch(ctx, _subset_structs(params, offsets, sh_degree), cams, self.opts,
                              pair_capacity, stream=self.stream)
+        self.sat = None
         if order is not None:
             self.batch.set_order(order)
+            if stale:
+                self.sat = [torch.full((h * w,), 255, dtype=torch.uint8, device="cuda")
+                            for h, w in self.batch.sizes]
+                self.batch.set_stale(self.sat)
         self.rgb = torch.empty(self.batch.rgb_off[-1], device="cuda")
         self.dL = torch.empty_like(self.rgb)
         self.loss = torch.zeros(1, device="cuda")
@@ -114,6 +122,11 @@ class BatchedStep:
         self.batch.set_cameras(cams, stream=self.stream)
         if order is not None:
             self.batch.set_order(order)
+        if self.sat is not None:  # new poses: the states start over
+            with torch.cuda.stream(self.stream):
+                for t in self.sat:
+                    t.fill_(255)
+            self.batch.set_stale(self.sat)
 
     def run(self, events=None):
         """Forward, loss, backward, Adam on self.stream.  `events`, if given, is a list of
