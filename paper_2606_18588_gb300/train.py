@@ -103,6 +103,7 @@ class BatchedStep:
         else:
             self._grads = _subset_structs(self.g, offsets, sh_degree, mutable=True)
         self.graph = None
+        self.graphs = ()
 
     @property
     def pixels(self) -> int:
@@ -131,11 +132,19 @@ class BatchedStep:
     def run(self, events=None):
         """Forward, loss, backward, Adam on self.stream.  `events`, if given, is a list of
         5 CUDA events recorded around the stages (fwd | loss | bwd | adam)."""
-        s = self.stream
         ev = events or [None] * 5
+        self._forward(ev)
+        self._update(ev)
+
+    def _forward(self, ev):
+        s = self.stream
         if ev[0] is not None: ev[0].record(s)
         self.batch.forward(self.rgb, None, stream=s)
         if ev[1] is not None: ev[1].record(s)
+
+    def _update(self, ev):
+        """Loss against self.target, backward, Adam."""
+        s = self.stream
         if self.dssim > 0.0:
             self.batch.loss_l1_dssim(self.rgb, self.target, self.loss, self.dL, self.dssim, stream=s)
         else:
@@ -168,12 +177,47 @@ class BatchedStep:
     def replay(self):
         self.graph.launch(self.stream)
 
+    def capture_split(self):
+        """Captures the step as two CUDA graphs, the forward and the rest (loss, backward,
+        Adam), for step_from_host (the batch must already have run eagerly once)."""
+        graphs = []
+        for part in (self._forward, self._update):
+            S.graph_begin(self.ctx, self.stream)
+            try:
+                part([None] * 5)
+            finally:
+                graphs.append(S.graph_end(self.ctx, self.stream))
+        self.graphs = tuple(graphs)
+        self._copy_stream = torch.cuda.Stream()
+        self._copy_done = torch.cuda.Event()
+        return self.graphs
+
+    def step_from_host(self, host_target, host_loss=None):
+        """One training step whose target images come from host memory (pinned, flat like
+        self.target): the host-to-device copy runs on its own stream while the forward
+        graph renders (the forward does not read the target), the rest of the step waits
+        for it; the loss is copied back to host_loss (pinned, one float) if given.  Nothing
+        waits on the host.  Needs capture_split()."""
+        s, cs = self.stream, self._copy_stream
+        cs.wait_stream(s)  # the previous step has finished reading self.target
+        with torch.cuda.stream(cs):
+            self.target.copy_(host_target, non_blocking=True)
+            self._copy_done.record(cs)
+        self.graphs[0].launch(s)
+        s.wait_event(self._copy_done)
+        self.graphs[1].launch(s)
+        if host_loss is not None:
+            with torch.cuda.stream(s):
+                host_loss.copy_(self.loss, non_blocking=True)
+
     def status(self):
         return self.batch.status(self.stream)
 
     def close(self):
         if self.graph is not None:
             self.graph.close()
+        for g in self.graphs:
+            g.close()
         self.batch.close()
 
 

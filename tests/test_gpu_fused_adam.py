@@ -151,3 +151,33 @@ def test_fused_adam_checks_its_arguments(ctx):
         assert not m[k].any() and not v[k].any()
         assert torch.equal(dev[k].cpu(), torch.from_numpy(getattr(sc, k)))
     b.close()
+
+
+def test_step_from_host_equals_the_captured_step(ctx):
+    # the public step with host targets (forward graph, target upload on a copy stream,
+    # then the update graph) trains exactly as the one-graph replay with device targets
+    from paper_2606_18588_gb300 import splx as S
+    from paper_2606_18588_gb300.train import BatchedStep
+    sc, off, cams = _tile_bound_case()
+    tg = [torch.from_numpy(I.random_image(c.height, c.width, 60 + i)) for i, c in enumerate(cams)]
+    a = _train(ctx, sc, off, cams, tg, fused=True, steps=4, graph=True)
+    dev = {k: torch.from_numpy(np.ascontiguousarray(x)).cuda() for k, x in zip(GROUPS, sc.arrays())}
+    s = torch.cuda.Stream()
+    host_t = torch.cat([t.reshape(-1) for t in tg]).pin_memory()
+    host_loss = torch.empty(1).pin_memory()
+    with torch.cuda.stream(s):
+        st = BatchedStep(ctx, dev, off, sc.sh_degree, cams, None, S.opts(), stream=s)
+        st.target.copy_(host_t.cuda())  # the first (eager) step's targets
+        st.run()
+        s.synchronize()
+        st.capture_split()
+        for _ in range(3):
+            st.step_from_host(host_t, host_loss)
+        s.synchronize()
+        assert st.status()[0] == S.OK
+    assert int(st.step_dev.item()) == 4
+    for k in GROUPS:
+        assert torch.equal(dev[k], a["p"][k]), k
+        assert torch.equal(st.m[k], a["m"][k]) and torch.equal(st.v[k], a["v"][k]), k
+    assert np.isfinite(host_loss.item()) and host_loss.item() > 0
+    st.close()
