@@ -226,17 +226,23 @@ def roofline(name, ms, counts, w, pk):
     if name == "sort":
         byts = counts["pairs"] * 16  # each tile segment read and written once
     elif name == "project":
-        byts = N * param_bytes + V * N * (64 + 4)
+        # parameters once, a tile count per (view, Gaussian), a record per kept one
+        vis = counts.get("visible", V * N)
+        byts = N * param_bytes + V * N * 4 + vis * 64
     elif name == "project_bwd":
+        # tile counts of every (view, Gaussian); the 2-D gradients (48 B, read and cleared)
+        # of the kept ones
+        vis = counts.get("visible", V * N)
         if w.get("fused_adam"):
-            # gradient from the views' 2-D gradients (read and cleared), then Adam in place:
-            # read p, m, v and write p, m, v once
-            byts = N * (6 * param_bytes) + V * N * 96
+            # gradient from the views' 2-D gradients, then Adam in place: read p, m, v and
+            # write p, m, v once
+            byts = N * (6 * param_bytes) + V * N * 4 + vis * 96
             note = "Adam fused in: read p, m, v; write p, m, v; no gradient array"
         else:
-            byts = N * (3 * param_bytes) + V * N * 96
+            byts = N * (3 * param_bytes) + V * N * 4 + vis * 96
     elif name == "fill":
-        byts = V * N * (4 + 32) + counts["pairs"] * 8
+        vis = counts.get("visible", V * N)
+        byts = V * N * 4 + vis * 32 + counts["pairs"] * 8
     elif name in ("composite", "composite_bwd"):
         per = 20 if name == "composite" else 36
         byts = pixels * (16 if name == "composite" else 12) + int(pixels * K * per * inside)
@@ -554,6 +560,7 @@ def batched_leg(args, ctx, dev, sc, off, cams, targets, o, ctas, order, stream, 
         if code != S.OK:
             raise RuntimeError(f"batched forward status {code}")
         counts = st.batch.counters(stream)
+        counts["visible"] = st.batch.visible(stream)
         counts["items_total"] = (len(off) - 1) * sum(
             ((c.width + o.tile - 1) // o.tile) * ((c.height + o.tile - 1) // o.tile) for c in cams)
         launches0 = ctx.launch_count

@@ -367,6 +367,10 @@ int splx_batch_kernel_times_slot(splx_batch_t b, splx_graph_t g, int32_t slot, f
  * A forward thread owns 2 pixels (8x8, 16x16 tiles) or 4 (32x32); a backward thread 2
  * (8x8), 8 (16x16: one warp per tile) or 4 (32x32). */
 int splx_batch_counters(splx_batch_t b, int64_t* out, splx_stream_t stream);
+/* Number of (view, Gaussian) pairs that the last forward's projection kept (a tile count
+ * above zero: the Gaussians that write a record and may receive a 2-D gradient), for the
+ * kernels' algorithmic byte counts.  Host output; synchronises; not capturable. */
+int splx_batch_visible(splx_batch_t b, int64_t* visible_out, splx_stream_t stream);
 
 /* ---- serving: continuous batching of render requests --------------------------- */
 /* A render server keeps K resident subsets and renders requests (a camera of any

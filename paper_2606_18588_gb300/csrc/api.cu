@@ -1469,6 +1469,28 @@ int splx_batch_counters(splx_batch_t bt, int64_t* out, splx_stream_t stream) {
   return SPLX_OK;
 }
 
+int splx_batch_visible(splx_batch_t bt, int64_t* visible_out, splx_stream_t stream) {
+  if (!bt || !visible_out) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  CtxScope scope(P.ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long* d = nullptr;
+  int r;
+  if ((r = ctx_alloc_t(P.ctx, &d, 1, s))) return r;
+  unsigned long long h = 0;
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(h), s);
+  if (e == cudaSuccess) {
+    count_nonzero_u32(P.counts, (int64_t)P.V * P.N, d, s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  ctx_free(P.ctx, (void*)d, s);
+  if (e != cudaSuccess) return cuda_fail(e, "splx_batch_visible");
+  *visible_out = (int64_t)h;
+  return SPLX_OK;
+}
+
 int splx_batch_status(splx_batch_t bt, int64_t* pairs_out, splx_stream_t stream) {
   if (!bt) return SPLX_ERR_INVALID;
   Plan& P = bt->plan;

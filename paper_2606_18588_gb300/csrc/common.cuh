@@ -217,6 +217,8 @@ void launch_project_bwd_adam(const BatchDev& b, const AdamTable& at, cudaStream_
 // exclusive scan of n u32 values (out has n+1 entries; out[n] = total)
 size_t scan_u32_temp_bytes(int64_t n);
 void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, void* temp, cudaStream_t s);
+// *out += number of nonzero entries of a[0, n)
+void count_nonzero_u32(const uint32_t* a, int64_t n, unsigned long long* out, cudaStream_t s);
 
 // Adam over one parameter array.  The step number is `step` or, if step_dev is non-NULL,
 // *step_dev read on the device.

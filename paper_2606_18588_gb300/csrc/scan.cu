@@ -132,3 +132,29 @@ void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, void* temp, cudaStre
 }
 
 }  // namespace splx
+
+namespace splx {
+
+// Number of nonzero entries of a[0, n) added into *out (a grid-stride count, one atomic
+// per warp).
+__global__ void __launch_bounds__(256) k_count_nonzero(const uint32_t* __restrict__ a, int64_t n,
+                                                       unsigned long long* out) {
+  unsigned long long c = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    c += a[i] != 0u ? 1ull : 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+void count_nonzero_u32(const uint32_t* a, int64_t n, unsigned long long* out, cudaStream_t s) {
+  if (n <= 0) return;
+  int64_t blocks = (n + 255) / 256;
+  const int64_t cap = (int64_t)device_sm_count() * 8;
+  if (blocks > cap) blocks = cap;
+  k_count_nonzero<<<(unsigned)blocks, 256, 0, s>>>(a, n, out);
+  count_launch();
+}
+
+}  // namespace splx

@@ -94,6 +94,7 @@ _sigs = {
     "splx_batch_set_launch": (C.c_int, [_P, C.c_int32]),
     "splx_batch_set_order": (C.c_int, [_P, _P]),
     "splx_batch_set_stale": (C.c_int, [_P, _P]),
+    "splx_batch_visible": (C.c_int, [_P, C.POINTER(C.c_int64), _P]),
     "splx_batch_set_visibility": (C.c_int, [_P, C.c_int32]),
     "splx_batch_set_cross_filter": (C.c_int, [_P, _P]),
     "splx_batch_loss_l1_dssim": (C.c_int, [_P, _P, _P, C.c_float, _P, _P, _P]),
@@ -584,6 +585,12 @@ class Batch:
         return dict(pairs=arr[0], entries_fwd=arr[1], alpha_fwd=arr[2], blended=arr[3],
                     entries_bwd=arr[4], alpha_bwd=arr[5], contrib_bwd=arr[6],
                     skipped_items=arr[7], outside_items=arr[8])
+
+    def visible(self, stream=None) -> int:
+        """(view, Gaussian) pairs the last forward's projection kept (synchronises)."""
+        n = C.c_int64()
+        _check(_lib.splx_batch_visible(self.h, C.byref(n), _stream(stream)), "splx_batch_visible")
+        return int(n.value)
 
     def views(self, flat_rgb):
         """Split a concatenated rgb buffer into per-view [3,H,W] tensors."""

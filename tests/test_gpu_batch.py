@@ -254,3 +254,19 @@ def test_spatial_visibility_changes_nothing(ctx, scene):
     assert torch.equal(out[True][1], out[False][1])
     for k in GROUPS:
         assert rel_l2(out[True][2][k].cpu().numpy(), out[False][2][k].cpu().numpy()) < 1e-5, k
+
+
+def test_visible_pairs_are_the_oracles_kept_gaussians(ctx, scene):
+    # splx_batch_visible counts the (view, Gaussian) pairs the projection kept: the
+    # oracle's binning specification keeps the same Gaussians, bit for bit
+    from paper_2606_18588_gb300 import splx as S
+    from oracle import oracle as O
+    from gpu_util import to_device
+    sc, off, cams = scene
+    dev = to_device(sc)
+    b = S.Batch(ctx, _subsets(dev, off, sc.sh_degree), cams, S.opts())
+    rgb = torch.empty(b.rgb_off[-1], device="cuda")
+    b.forward(rgb)
+    expect = sum(int(O.bin(sc, c)[0].astype(bool).sum()) for c in cams)
+    assert b.visible() == expect > 0
+    b.close()
