@@ -82,13 +82,36 @@ constexpr int kProjBwdThreads = 128;
 // one Gaussian's consecutive elements (the fused Adam epilogue) hits distinct banks, as do
 // the threads writing one element of their own Gaussians.
 constexpr int kGs = kProjBwdThreads + 1;
+// The views' 2-D gradients of a thread's Gaussian stream through a ring of kRing slots of
+// shared memory filled by asynchronous copies (cp.async), kRing - 1 views ahead of the one
+// being processed, without holding registers for them.
+constexpr int kRing = 3;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // The gradient of one Gaussian g over all views: mean, log-scale, quaternion and opacity
 // logit in the outputs, the SH coefficients' in gsh (one column of shared memory, element e
 // at gsh[e * kGs]); false (outputs untouched, gsh zero) where no view left a
-// 2-D gradient.  Consumes and clears the views' 2-D gradients.
+// 2-D gradient.  Consumes and clears the views' 2-D gradients.  ring / ringb: this
+// thread's column of the kRing-slot ring (slot s: float4s at ring[(2 s + k) *
+// kProjBwdThreads], k = 0, 1, and the ninth value at ringb[s * kProjBwdThreads]).
 template <int DEG>
 __device__ __forceinline__ bool proj_grads(const BatchDev& b, const int64_t g, float* gsh,
+                                           float4* ring, float* ringb,
                                            float (&out_m)[3], float (&out_ls)[3],
                                            float (&out_q)[4], float& out_logit) {
   const int k = subset_of(b, g);
@@ -125,154 +148,170 @@ __device__ __forceinline__ bool proj_grads(const BatchDev& b, const int64_t g, f
   for (int e = 0; e < NC * 3; ++e) gsh[e * kGs] = 0.f;
   bool any = false;
 
-  // the next view's 2-D gradient is loaded while this view's is processed; only views in
-  // which the Gaussian was projected (tile count > 0) can hold one
-  // (the count of the view after next is loaded a step ahead, off the loads' critical path)
-  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  // Only views in which the Gaussian was projected (tile count > 0) can hold a 2-D
+  // gradient.  Per chunk of up to 64 views: the counts give the chunk's mask of such views
+  // (all loads in flight together), whose gradients then stream through the ring in view
+  // order; a slot is refilled one view after it was read (its loads have returned: the
+  // zero test below consumed them)
   auto seen_in = [&](int v) { return !b.counts || b.counts[(int64_t)v * b.N + g] != 0u; };
-  float4 nG0 = z4, nG1 = z4;
-  float ngb = 0.f;
-  if (seen_in(0)) {
-    nG0 = b.grad2d[g * 3];
-    nG1 = b.grad2d[g * 3 + 1];
-    ngb = b.grad2d[g * 3 + 2].x;
-  }
-  bool seen_next = b.V > 1 && seen_in(1);
-  for (int v = 0; v < b.V; ++v) {
-    float4* gp = b.grad2d + ((int64_t)v * b.N + g) * 3;
-    const float4 G0 = nG0, G1 = nG1;
-    const float gbl = ngb;
-    if (v + 1 < b.V) {
-      const float4* np = gp + (int64_t)b.N * 3;
-      nG0 = seen_next ? np[0] : z4;
-      nG1 = seen_next ? np[1] : z4;
-      ngb = seen_next ? np[2].x : 0.f;
-      seen_next = v + 2 < b.V && seen_in(v + 2);
+  for (int v0 = 0; v0 < b.V; v0 += 64) {
+    const int vn = b.V - v0 < 64 ? b.V - v0 : 64;
+    uint64_t vm = 0;
+    for (int q = 0; q < vn; ++q)
+      if (seen_in(v0 + q)) vm |= 1ull << q;
+    uint64_t pend = vm;  // views not yet copied
+    auto issue = [&](int s) {
+      if (pend) {
+        const int q = __ffsll((long long)pend) - 1;
+        pend &= pend - 1;
+        const float4* src = b.grad2d + ((int64_t)(v0 + q) * b.N + g) * 3;
+        cp_async16(ring + (2 * s) * kProjBwdThreads, src);
+        cp_async16(ring + (2 * s + 1) * kProjBwdThreads, src + 1);
+        cp_async4(ringb + s * kProjBwdThreads, &src[2].x);
+      }
+      cp_async_commit();  // one group per call, empty or not
+    };
+#pragma unroll
+    for (int s0 = 0; s0 < kRing; ++s0) issue(s0);
+    int slot = 0;
+    bool first = true;
+    while (vm) {
+      const int v = v0 + __ffsll((long long)vm) - 1;
+      vm &= vm - 1;
+      if (!first) issue(slot == 0 ? kRing - 1 : slot - 1);
+      first = false;
+      cp_async_wait<kRing - 1>();  // this view's group, the oldest outstanding, has landed
+      const float4 G0 = ring[(2 * slot) * kProjBwdThreads];
+      const float4 G1 = ring[(2 * slot + 1) * kProjBwdThreads];
+      const float gbl = ringb[slot * kProjBwdThreads];
+      slot = slot + 1 == kRing ? 0 : slot + 1;
+      float4* gp = b.grad2d + ((int64_t)v * b.N + g) * 3;
+      if (G0.x == 0.f && G0.y == 0.f && G0.z == 0.f && G0.w == 0.f && G1.x == 0.f && G1.y == 0.f &&
+          G1.z == 0.f && G1.w == 0.f && gbl == 0.f)
+        continue;
+      any = true;
+      gp[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+      gp[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      gp[2].x = 0.f;
+      const ViewDev& cam = b.views[v];
+      const float* R = cam.R;
+      const float tx = R[0] * m[0] + R[1] * m[1] + R[2] * m[2] + cam.t[0];
+      const float ty = R[3] * m[0] + R[4] * m[1] + R[5] * m[2] + cam.t[1];
+      const float tz = R[6] * m[0] + R[7] * m[1] + R[8] * m[2] + cam.t[2];
+      const float fx = cam.fx, fy = cam.fy;
+      const float itz = 1.0f / tz;
+      const float limx = 1.3f * 0.5f * (float)cam.W / fx, limy = 1.3f * 0.5f * (float)cam.H / fy;
+      const float rx = tx * itz, ry = ty * itz;
+      const bool clx = rx < -limx || rx > limx, cly = ry < -limy || ry > limy;
+      const float rxc = fminf(limx, fmaxf(-limx, rx)), ryc = fminf(limy, fmaxf(-limy, ry));
+      const float j00 = fx * itz, j02 = -fx * rxc * itz, j11 = fy * itz, j12 = -fy * ryc * itz;
+      float V[9];
+  #pragma unroll
+      for (int r = 0; r < 3; ++r)
+  #pragma unroll
+        for (int c = 0; c < 3; ++c)
+          V[3 * r + c] = R[3 * r] * M[c] + R[3 * r + 1] * M[3 + c] + R[3 * r + 2] * M[6 + c];
+      float P0[3], P1[3];
+  #pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        P0[c] = j00 * V[c] + j02 * V[6 + c];
+        P1[c] = j11 * V[3 + c] + j12 * V[6 + c];
+      }
+      const float a0 = P0[0] * P0[0] + P0[1] * P0[1] + P0[2] * P0[2];
+      const float c0 = P1[0] * P1[0] + P1[1] * P1[1] + P1[2] * P1[2];
+      const float bb = P0[0] * P1[0] + P0[1] * P1[1] + P0[2] * P1[2];
+      const float d01 = P0[0] * P1[1] - P0[1] * P1[0];
+      const float d02 = P0[0] * P1[2] - P0[2] * P1[0];
+      const float d12 = P0[1] * P1[2] - P0[2] * P1[1];
+      const float det = d01 * d01 + d02 * d02 + d12 * d12 + 0.3f * (a0 + c0) + 0.09f;
+      const float idet = 1.0f / det;
+      const float QA = (c0 + 0.3f) * idet, QB = -bb * idet, QC = (a0 + 0.3f) * idet;
+      // the rasteriser's moments of dL/dpower / o -> dL/du, dL/dv and dL/d(A, B, C) of the
+      // conic: power = -(A dx^2 + 2 B dx dy + C dy^2) / 2 with (dx, dy) = pixel - (u, v)
+      const float mx = o * G0.x, my = o * G0.y;
+      const float gu = QA * mx + QB * my, gv = QB * mx + QC * my;
+      const float gA = -0.5f * o * G0.z, gB = -o * G0.w, gCc = -0.5f * o * G1.x, go = G1.y;
+      const float gcol[3] = {G1.z, G1.w, gbl};
+      glogit += go * o * (1.0f - o);
+      // colour -> SH coefficients and viewing direction
+      float dx = m[0] - cam.eye[0], dy = m[1] - cam.eye[1], dz = m[2] - cam.eye[2];
+      const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+      const float idist = 1.0f / dist;
+      dx *= idist; dy *= idist; dz *= idist;
+      float Y[NC];
+      sh_basis<DEG>(dx, dy, dz, Y);
+      float gc[3];
+  #pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        float raw = 0.5f;
+  #pragma unroll
+        for (int kk = 0; kk < NC; ++kk) raw = fmaf(Y[kk], __ldg(shp + 3 * kk + ch), raw);
+        gc[ch] = raw < 0.0f ? 0.0f : gcol[ch];
+      }
+      float w[NC];
+  #pragma unroll
+      for (int kk = 0; kk < NC; ++kk) {
+        gsh[(3 * kk + 0) * kGs] += Y[kk] * gc[0];
+        gsh[(3 * kk + 1) * kGs] += Y[kk] * gc[1];
+        gsh[(3 * kk + 2) * kGs] += Y[kk] * gc[2];
+        w[kk] = __ldg(shp + 3 * kk) * gc[0] + __ldg(shp + 3 * kk + 1) * gc[1] +
+                __ldg(shp + 3 * kk + 2) * gc[2];
+      }
+      if (DEG > 0) {
+        float gd[3];
+        sh_dir_grad<DEG>(dx, dy, dz, w, gd);
+        const float dd = dx * gd[0] + dy * gd[1] + dz * gd[2];
+        gm[0] += (gd[0] - dx * dd) * idist;
+        gm[1] += (gd[1] - dy * dd) * idist;
+        gm[2] += (gd[2] - dz * dd) * idist;
+      }
+      // conic -> Sigma2D:  H = -Q Gq Q,  Gq = [[gA, gB/2], [gB/2, gC]]
+      const float hB = 0.5f * gB;
+      const float QG00 = QA * gA + QB * hB, QG01 = QA * hB + QB * gCc;
+      const float QG10 = QB * gA + QC * hB, QG11 = QB * hB + QC * gCc;
+      const float H00 = -(QG00 * QA + QG01 * QB), H01 = -(QG00 * QB + QG01 * QC);
+      const float H10 = -(QG10 * QA + QG11 * QB), H11 = -(QG10 * QB + QG11 * QC);
+      // Sigma2D0 = P P^T  ->  gP = 2 H P
+      float gP0[3], gP1[3];
+  #pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        gP0[c] = 2.f * (H00 * P0[c] + H01 * P1[c]);
+        gP1[c] = 2.f * (H10 * P0[c] + H11 * P1[c]);
+      }
+      // P = J V
+      const float gj00 = gP0[0] * V[0] + gP0[1] * V[1] + gP0[2] * V[2];
+      const float gj02 = gP0[0] * V[6] + gP0[1] * V[7] + gP0[2] * V[8];
+      const float gj11 = gP1[0] * V[3] + gP1[1] * V[4] + gP1[2] * V[5];
+      const float gj12 = gP1[0] * V[6] + gP1[1] * V[7] + gP1[2] * V[8];
+      float gV[9];
+  #pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        gV[c] = j00 * gP0[c];
+        gV[3 + c] = j11 * gP1[c];
+        gV[6 + c] = j02 * gP0[c] + j12 * gP1[c];
+      }
+      // J and the 2-D mean -> camera-space mean
+      const float itz2 = itz * itz;
+      float gtx = 0.f, gty = 0.f, gtz = 0.f;
+      gtz += -fx * itz2 * gj00 - fy * itz2 * gj11;
+      if (!clx) { gtx += -fx * itz2 * gj02; gtz += 2.f * fx * tx * itz2 * itz * gj02; }
+      else { gtz += fx * rxc * itz2 * gj02; }
+      if (!cly) { gty += -fy * itz2 * gj12; gtz += 2.f * fy * ty * itz2 * itz * gj12; }
+      else { gtz += fy * ryc * itz2 * gj12; }
+      gtx += fx * itz * gu;
+      gtz += -fx * tx * itz2 * gu;
+      gty += fy * itz * gv;
+      gtz += -fy * ty * itz2 * gv;
+  #pragma unroll
+      for (int e = 0; e < 3; ++e) gm[e] += R[e] * gtx + R[3 + e] * gty + R[6 + e] * gtz;
+      // V = W M  ->  gM += W^T gV
+  #pragma unroll
+      for (int r = 0; r < 3; ++r)
+  #pragma unroll
+        for (int c = 0; c < 3; ++c)
+          gM[3 * r + c] += R[r] * gV[c] + R[3 + r] * gV[3 + c] + R[6 + r] * gV[6 + c];
     }
-    if (G0.x == 0.f && G0.y == 0.f && G0.z == 0.f && G0.w == 0.f && G1.x == 0.f && G1.y == 0.f &&
-        G1.z == 0.f && G1.w == 0.f && gbl == 0.f)
-      continue;
-    any = true;
-    gp[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-    gp[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-    gp[2].x = 0.f;
-    const ViewDev& cam = b.views[v];
-    const float* R = cam.R;
-    const float tx = R[0] * m[0] + R[1] * m[1] + R[2] * m[2] + cam.t[0];
-    const float ty = R[3] * m[0] + R[4] * m[1] + R[5] * m[2] + cam.t[1];
-    const float tz = R[6] * m[0] + R[7] * m[1] + R[8] * m[2] + cam.t[2];
-    const float fx = cam.fx, fy = cam.fy;
-    const float itz = 1.0f / tz;
-    const float limx = 1.3f * 0.5f * (float)cam.W / fx, limy = 1.3f * 0.5f * (float)cam.H / fy;
-    const float rx = tx * itz, ry = ty * itz;
-    const bool clx = rx < -limx || rx > limx, cly = ry < -limy || ry > limy;
-    const float rxc = fminf(limx, fmaxf(-limx, rx)), ryc = fminf(limy, fmaxf(-limy, ry));
-    const float j00 = fx * itz, j02 = -fx * rxc * itz, j11 = fy * itz, j12 = -fy * ryc * itz;
-    float V[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        V[3 * r + c] = R[3 * r] * M[c] + R[3 * r + 1] * M[3 + c] + R[3 * r + 2] * M[6 + c];
-    float P0[3], P1[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      P0[c] = j00 * V[c] + j02 * V[6 + c];
-      P1[c] = j11 * V[3 + c] + j12 * V[6 + c];
-    }
-    const float a0 = P0[0] * P0[0] + P0[1] * P0[1] + P0[2] * P0[2];
-    const float c0 = P1[0] * P1[0] + P1[1] * P1[1] + P1[2] * P1[2];
-    const float bb = P0[0] * P1[0] + P0[1] * P1[1] + P0[2] * P1[2];
-    const float d01 = P0[0] * P1[1] - P0[1] * P1[0];
-    const float d02 = P0[0] * P1[2] - P0[2] * P1[0];
-    const float d12 = P0[1] * P1[2] - P0[2] * P1[1];
-    const float det = d01 * d01 + d02 * d02 + d12 * d12 + 0.3f * (a0 + c0) + 0.09f;
-    const float idet = 1.0f / det;
-    const float QA = (c0 + 0.3f) * idet, QB = -bb * idet, QC = (a0 + 0.3f) * idet;
-    // the rasteriser's moments of dL/dpower / o -> dL/du, dL/dv and dL/d(A, B, C) of the
-    // conic: power = -(A dx^2 + 2 B dx dy + C dy^2) / 2 with (dx, dy) = pixel - (u, v)
-    const float mx = o * G0.x, my = o * G0.y;
-    const float gu = QA * mx + QB * my, gv = QB * mx + QC * my;
-    const float gA = -0.5f * o * G0.z, gB = -o * G0.w, gCc = -0.5f * o * G1.x, go = G1.y;
-    const float gcol[3] = {G1.z, G1.w, gbl};
-    glogit += go * o * (1.0f - o);
-    // colour -> SH coefficients and viewing direction
-    float dx = m[0] - cam.eye[0], dy = m[1] - cam.eye[1], dz = m[2] - cam.eye[2];
-    const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
-    const float idist = 1.0f / dist;
-    dx *= idist; dy *= idist; dz *= idist;
-    float Y[NC];
-    sh_basis<DEG>(dx, dy, dz, Y);
-    float gc[3];
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      float raw = 0.5f;
-#pragma unroll
-      for (int kk = 0; kk < NC; ++kk) raw = fmaf(Y[kk], __ldg(shp + 3 * kk + ch), raw);
-      gc[ch] = raw < 0.0f ? 0.0f : gcol[ch];
-    }
-    float w[NC];
-#pragma unroll
-    for (int kk = 0; kk < NC; ++kk) {
-      gsh[(3 * kk + 0) * kGs] += Y[kk] * gc[0];
-      gsh[(3 * kk + 1) * kGs] += Y[kk] * gc[1];
-      gsh[(3 * kk + 2) * kGs] += Y[kk] * gc[2];
-      w[kk] = __ldg(shp + 3 * kk) * gc[0] + __ldg(shp + 3 * kk + 1) * gc[1] +
-              __ldg(shp + 3 * kk + 2) * gc[2];
-    }
-    if (DEG > 0) {
-      float gd[3];
-      sh_dir_grad<DEG>(dx, dy, dz, w, gd);
-      const float dd = dx * gd[0] + dy * gd[1] + dz * gd[2];
-      gm[0] += (gd[0] - dx * dd) * idist;
-      gm[1] += (gd[1] - dy * dd) * idist;
-      gm[2] += (gd[2] - dz * dd) * idist;
-    }
-    // conic -> Sigma2D:  H = -Q Gq Q,  Gq = [[gA, gB/2], [gB/2, gC]]
-    const float hB = 0.5f * gB;
-    const float QG00 = QA * gA + QB * hB, QG01 = QA * hB + QB * gCc;
-    const float QG10 = QB * gA + QC * hB, QG11 = QB * hB + QC * gCc;
-    const float H00 = -(QG00 * QA + QG01 * QB), H01 = -(QG00 * QB + QG01 * QC);
-    const float H10 = -(QG10 * QA + QG11 * QB), H11 = -(QG10 * QB + QG11 * QC);
-    // Sigma2D0 = P P^T  ->  gP = 2 H P
-    float gP0[3], gP1[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      gP0[c] = 2.f * (H00 * P0[c] + H01 * P1[c]);
-      gP1[c] = 2.f * (H10 * P0[c] + H11 * P1[c]);
-    }
-    // P = J V
-    const float gj00 = gP0[0] * V[0] + gP0[1] * V[1] + gP0[2] * V[2];
-    const float gj02 = gP0[0] * V[6] + gP0[1] * V[7] + gP0[2] * V[8];
-    const float gj11 = gP1[0] * V[3] + gP1[1] * V[4] + gP1[2] * V[5];
-    const float gj12 = gP1[0] * V[6] + gP1[1] * V[7] + gP1[2] * V[8];
-    float gV[9];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      gV[c] = j00 * gP0[c];
-      gV[3 + c] = j11 * gP1[c];
-      gV[6 + c] = j02 * gP0[c] + j12 * gP1[c];
-    }
-    // J and the 2-D mean -> camera-space mean
-    const float itz2 = itz * itz;
-    float gtx = 0.f, gty = 0.f, gtz = 0.f;
-    gtz += -fx * itz2 * gj00 - fy * itz2 * gj11;
-    if (!clx) { gtx += -fx * itz2 * gj02; gtz += 2.f * fx * tx * itz2 * itz * gj02; }
-    else { gtz += fx * rxc * itz2 * gj02; }
-    if (!cly) { gty += -fy * itz2 * gj12; gtz += 2.f * fy * ty * itz2 * itz * gj12; }
-    else { gtz += fy * ryc * itz2 * gj12; }
-    gtx += fx * itz * gu;
-    gtz += -fx * tx * itz2 * gu;
-    gty += fy * itz * gv;
-    gtz += -fy * ty * itz2 * gv;
-#pragma unroll
-    for (int e = 0; e < 3; ++e) gm[e] += R[e] * gtx + R[3 + e] * gty + R[6 + e] * gtz;
-    // V = W M  ->  gM += W^T gV
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        gM[3 * r + c] += R[r] * gV[c] + R[3 + r] * gV[3 + c] + R[6 + r] * gV[6 + c];
+    cp_async_wait<0>();  // the chunk's ring is idle before the next chunk refills it
   }
   if (!any) return false;
   // M = Rq diag(s)
@@ -422,13 +461,16 @@ __global__ void __launch_bounds__(kProjBwdThreads, 4)
   // quaternion (4) and opacity logit, the SH rows follow
   constexpr int kHead = kFuse ? 11 : 0;
   __shared__ float s_grad[(kHead + NC * 3) * kGs];
+  __shared__ float4 s_ring[kRing * 2 * kProjBwdThreads];
+  __shared__ float s_ringb[kRing * kProjBwdThreads];
   float* gsh = s_grad + kHead * kGs + threadIdx.x;
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
   float glogit = 0.f;
   bool any = false;
   if (g < b.N) {
-    any = proj_grads<DEG>(b, g, gsh, gm, gls, gq, glogit);
+    any = proj_grads<DEG>(b, g, gsh, s_ring + threadIdx.x, s_ringb + threadIdx.x, gm, gls, gq,
+                          glogit);
   } else if (kFuse) {
 #pragma unroll
     for (int e = 0; e < NC * 3; ++e) gsh[e * kGs] = 0.f;
