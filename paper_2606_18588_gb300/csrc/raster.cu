@@ -438,6 +438,17 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
   const int lane = threadIdx.x & 31;
   unsigned n_evalb = 0, n_pixb = 0, n_actb = 0;
 
+  // the thread's keys of the next batch (low halves: the Gaussian indices), loaded one
+  // batch ahead so that staging waits for the records only
+  uint32_t nk[NB / NTH];
+  auto load_keys = [&](int top) {
+#pragma unroll
+    for (int r = 0; r < NB / NTH; ++r) {
+      const int j = top - (r * NTH + (int)threadIdx.x);
+      nk[r] = j >= 0 ? (uint32_t)b.keys[start + j] : 0u;
+    }
+  };
+  load_keys(maxlast);
   for (int top = maxlast; top >= 0; top -= NB) {
     const int lo = top - NB + 1 > 0 ? top - NB + 1 : 0;
     __syncthreads();
@@ -446,7 +457,7 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
       const int slot = r * NTH + (int)threadIdx.x;  // slot s holds entry top - s
       const int j = top - slot;
       if (j >= lo) {
-        uint32_t g = (uint32_t)b.keys[start + j];
+        uint32_t g = nk[r];
         if (g >= (uint32_t)b.N) { atomicOr(b.status, ST_BOUNDS); g = 0; }
         const Rec* rp = rec + g;
         sA[slot] = rp->a;
@@ -455,6 +466,7 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
         sG[slot] = g;
       }
     }
+    load_keys(top - NB);
     __syncthreads();
     const int cnt = top - lo + 1;
     if (kCount && tlast >= lo) n_evalb += (unsigned)((tlast < top ? tlast : top) - lo + 1);
