@@ -341,6 +341,25 @@ __device__ __forceinline__ bool item_pruned(const BatchDev& b, int64_t id) {
   return !__syncthreads_or(open);
 }
 
+// Asynchronous global -> shared copies (cp.async) of 16 or 4 bytes by the calling thread,
+// grouped by commit; wait<N> returns once at most N of the thread's groups are pending, and
+// then the thread's own copies of the older groups are visible to it.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Whether tile (tx, ty) of view v lies in subset k's visible region (always, if off).
 __device__ __forceinline__ bool in_omega(const BatchDev& b, int v, int k, int tx, int ty) {
   if (!b.omega) return true;

@@ -87,21 +87,6 @@ constexpr int kGs = kProjBwdThreads + 1;
 // being processed, without holding registers for them.
 constexpr int kRing = 3;
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
 // The gradient of one Gaussian g over all views: mean, log-scale, quaternion and opacity
 // logit in the outputs, the SH coefficients' in gsh (one column of shared memory, element e
