@@ -76,8 +76,9 @@ def _train(ctx, sc, off, cams, tg, fused, steps, graph=False):
     return out
 
 
-def test_fused_adam_is_bit_identical_where_the_backward_is_deterministic(ctx):
-    sc, off, cams = _tile_bound_case()
+@pytest.mark.parametrize("deg", [0, 1, 2, 3])
+def test_fused_adam_is_bit_identical_where_the_backward_is_deterministic(ctx, deg):
+    sc, off, cams = _tile_bound_case(deg=deg)
     tg = [torch.from_numpy(I.random_image(c.height, c.width, 40 + i)) for i, c in enumerate(cams)]
     a = _train(ctx, sc, off, cams, tg, fused=False, steps=3)
     a2 = _train(ctx, sc, off, cams, tg, fused=False, steps=3)

@@ -24,12 +24,13 @@ def ctx():
     c.close()
 
 
-def _batch(ctx, dev, sc, off, cams, order=None, planes=None):
+def _batch(ctx, dev, sc, off, cams, order=None, planes=None, visibility=True):
     from paper_2606_18588_gb300 import splx as S
     from gpu_util import subset_struct
     subs = [subset_struct(dev, int(off[k]), int(off[k + 1]), sc.sh_degree)
             for k in range(len(off) - 1)]
     b = S.Batch(ctx, subs, cams, S.opts())
+    b.set_visibility(visibility)
     if order is not None:
         b.set_order(order)
     if planes is not None:
@@ -60,16 +61,19 @@ def _planes(cams, fill=255):
     return [torch.full((c.height * c.width,), fill, dtype=torch.uint8, device="cuda") for c in cams]
 
 
-def test_a_visit_after_an_identical_one_renders_what_the_waves_render(ctx):
+@pytest.mark.parametrize("visibility", [True, False])
+def test_a_visit_after_an_identical_one_renders_what_the_waves_render(ctx, visibility):
+    # (with the visible regions on, partial planes outside them are never written and the
+    # re-evaluation must skip them; off, every subset has a plane everywhere)
     from paper_2606_18588_gb300.visibility import orders_for_views
     from gpu_util import rel_l2, to_device
     sc, off, boxes, cams = I.cluster_case(120_000, 9, 8, 3, [(160, 120), (96, 64), (131, 77)])
     orders = orders_for_views(boxes, cams)
     dev = to_device(sc)
-    full = _batch(ctx, dev, sc, off, cams)
+    full = _batch(ctx, dev, sc, off, cams, visibility=visibility)
     rgb_f, T_f = _forward(full)
     full.close()
-    waves = _batch(ctx, dev, sc, off, cams, orders)
+    waves = _batch(ctx, dev, sc, off, cams, orders, visibility=visibility)
     rgb_w, T_w = _forward(waves)
     skipped_w = waves.counters()["skipped_items"]
     npx = int(rgb_w.numel())
@@ -77,7 +81,7 @@ def test_a_visit_after_an_identical_one_renders_what_the_waves_render(ctx):
     g_w = _grads(waves, dev, off, sc.sh_degree, dL)
     waves.close()
     planes = _planes(cams)
-    st = _batch(ctx, dev, sc, off, cams, orders, planes)
+    st = _batch(ctx, dev, sc, off, cams, orders, planes, visibility=visibility)
     # first visit: nothing pruned, so the render without skipping
     rgb_1, T_1 = _forward(st)
     assert torch.equal(rgb_1, rgb_f) and torch.equal(T_1, T_f)
