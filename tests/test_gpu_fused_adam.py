@@ -96,6 +96,18 @@ def test_fused_adam_is_bit_identical_where_the_backward_is_deterministic(ctx, de
     assert moved == len(GROUPS)
 
 
+def test_fused_adam_with_an_empty_subset(ctx):
+    # an empty subset between two others: its Adam entries are never touched, and the
+    # 128-Gaussian blocks across the boundary still find their own subsets
+    sc, off, cams = _tile_bound_case(sizes=(300, 0, 200), deg=2, seed=11)
+    tg = [torch.from_numpy(I.random_image(c.height, c.width, 50 + i)) for i, c in enumerate(cams)]
+    a = _train(ctx, sc, off, cams, tg, fused=False, steps=2)
+    b = _train(ctx, sc, off, cams, tg, fused=True, steps=2)
+    for part in ("p", "m", "v"):
+        for k in GROUPS:
+            assert torch.equal(a[part][k], b[part][k]), (part, k)
+
+
 def test_fused_adam_agrees_on_a_clustered_scene_through_a_graph(ctx):
     sc, off, _, cams = I.cluster_case(30_000, 11, 4, 3, [(200, 120), (96, 64), (131, 77)])
     tg = [torch.from_numpy(I.random_image(c.height, c.width, 5 + i)) for i, c in enumerate(cams)]
