@@ -261,7 +261,10 @@ __global__ void __launch_bounds__(kFillThreads, 8) k_fill(const BatchDev b) {
     f[15][lane] = __uint_as_float((uint32_t)key);
     f[16][lane] = __uint_as_float((uint32_t)(key >> 32));
     f[17][lane] = __uint_as_float(tiles);
-    const WarpWalk walk = warp_walk_begin(lanes, (int)tiles);
+    // a rectangle of at most 32 tiles walks only the tiles its pass bits name (the test is
+    // already taken); a larger one walks them all and takes the test
+    const int cand = tiles <= 32u ? __popc(hits) : (int)tiles;
+    const WarpWalk walk = warp_walk_begin(lanes, cand);
     for (int base = 0; base < walk.total; base += walk.nact) {
       int j;
       const int o = warp_walk_owner(walk, base, s_own[warp], j);
@@ -269,11 +272,15 @@ __global__ void __launch_bounds__(kFillThreads, 8) k_fill(const BatchDev b) {
       uint64_t okey = 0;
       if (o >= 0) {
         int jx, jy;
-        walk_tile(j, __float_as_int(f[11][o]), f[12][o], jx, jy);
         bool pass;
         if (__float_as_uint(f[17][o]) <= 32u) {
-          pass = ((__float_as_uint(f[14][o]) >> j) & 1u) != 0u;
+          // the j-th set pass bit
+          unsigned m = __float_as_uint(f[14][o]);
+          for (int q = 0; q < j; ++q) m &= m - 1u;
+          walk_tile(__ffs(m) - 1, __float_as_int(f[11][o]), f[12][o], jx, jy);
+          pass = true;
         } else {
+          walk_tile(j, __float_as_int(f[11][o]), f[12][o], jx, jy);
           TileCull oc;
           oc.u = f[0][o]; oc.v = f[1][o]; oc.A = f[2][o]; oc.B = f[3][o];
           oc.C = f[4][o]; oc.qmax = f[5][o]; oc.rBC = f[6][o]; oc.rBA = f[7][o];
