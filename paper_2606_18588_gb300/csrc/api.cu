@@ -27,6 +27,7 @@ std::mutex g_dev_mu;
 int g_sm_count[kMaxDev] = {};
 bool g_smem_done[kMaxDev][kSmemSlots] = {};
 cudaError_t g_smem_result[kMaxDev][kSmemSlots] = {};
+int g_ctas[kMaxDev][kSmemSlots] = {};
 int current_device() {
   int d = 0;
   return cudaGetDevice(&d) == cudaSuccess && d >= 0 && d < kMaxDev ? d : 0;
@@ -43,6 +44,20 @@ int device_sm_count() {
     g_sm_count[d] = n;
   }
   return g_sm_count[d];
+}
+
+int resident_ctas(const void* fn, int threads, int smem, int slot) {
+  const int d = current_device();
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (!g_ctas[d][slot]) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, (size_t)smem) !=
+            cudaSuccess ||
+        n <= 0)
+      n = 1;
+    g_ctas[d][slot] = n;
+  }
+  return g_ctas[d][slot];
 }
 
 cudaError_t opt_in_smem(const void* fn, int bytes, int slot) {

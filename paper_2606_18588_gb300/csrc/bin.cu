@@ -452,10 +452,14 @@ void launch_seg_sort(const BatchDev& b, int max_rounds, cudaStream_t s) {
   k_seg_sort_small<<<(unsigned)items, kSortThreads, 0, s>>>(b);
   const unsigned grid = (unsigned)device_sm_count() * 4;
   // 72 KB of dynamic shared memory: opted in once per device (a refused opt-in shows as
-  // the launch's error, which the callers check)
+  // the launch's error, which the callers check).  Its grid-stride loop runs one wave of
+  // resident CTAs (3 per SM at 72 KB), so that no CTA starts after the others have ended
   constexpr int kChunkSmem = 2 * kBigPadded * (int)sizeof(uint64_t);
   (void)opt_in_smem((const void*)k_chunk_sort, kChunkSmem, 0);
-  k_chunk_sort<<<grid, kBigThreads, kChunkSmem, s>>>(b);
+  const unsigned cgrid = (unsigned)device_sm_count() *
+                         (unsigned)resident_ctas((const void*)k_chunk_sort, kBigThreads,
+                                                 kChunkSmem, 0);
+  k_chunk_sort<<<cgrid, kBigThreads, kChunkSmem, s>>>(b);
   for (int r = 0; r < max_rounds; ++r) k_merge_round<<<grid, kBigThreads, 0, s>>>(b, r);
   k_merge_fixup<<<grid, kBigThreads, 0, s>>>(b);
   count_launch(3 + max_rounds);

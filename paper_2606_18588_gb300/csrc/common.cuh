@@ -235,6 +235,9 @@ int device_sm_count();
 // Opts kernel `fn` into `bytes` of dynamic shared memory on the current device, once per
 // device (function attributes belong to a device's context); returns the opt-in's result.
 cudaError_t opt_in_smem(const void* fn, int bytes, int slot);
+// CTAs of kernel fn (threads per CTA, dynamic shared memory bytes) resident on one SM of the
+// current device, looked up once per device and slot (at least 1).
+int resident_ctas(const void* fn, int threads, int smem, int slot);
 
 // Counts kernel launches issued by the library (for reporting).
 extern thread_local int64_t* g_launch_counter;
