@@ -64,15 +64,16 @@ __device__ __forceinline__ int merge_path_smem(const uint64_t* s, int a0, int na
   return lo;
 }
 
-// Sorts keys[0, n) (n <= CH) in place with TH threads: each thread sorts kItems keys in
+// Sorts in[0, n) into out[0, n) (n <= CH; out may be in) with TH threads: each thread sorts kItems keys in
 // registers (odd-even transposition network), then runs of 8, 16, ... are merged pairwise
 // through two shared buffers, every thread producing kItems outputs located by merge path.
 // The array is padded to a power of two P >= 8 with ~0 keys.  sa, sb: CH + CH/8 keys each.
 template <int TH>
-__device__ __forceinline__ void sort_chunk(uint64_t* keys, int n, uint64_t* sa, uint64_t* sb) {
+__device__ __forceinline__ void sort_chunk(const uint64_t* in, uint64_t* out, int n, uint64_t* sa,
+                                           uint64_t* sb) {
   int P = next_pow2(n);
   if (P < kItems) P = kItems;
-  for (int i = threadIdx.x; i < P; i += TH) sa[pad(i)] = i < n ? keys[i] : ~0ull;
+  for (int i = threadIdx.x; i < P; i += TH) sa[pad(i)] = i < n ? in[i] : ~0ull;
   __syncthreads();
   const int active = P / kItems;  // threads holding keys
   const int t = threadIdx.x;
@@ -121,7 +122,7 @@ __device__ __forceinline__ void sort_chunk(uint64_t* keys, int n, uint64_t* sa, 
     src = dst;
     dst = tmp;
   }
-  for (int i = threadIdx.x; i < n; i += TH) keys[i] = src[pad(i)];
+  for (int i = threadIdx.x; i < n; i += TH) out[i] = src[pad(i)];
 }
 
 __device__ __forceinline__ void segment_of(const BatchDev& b, int64_t t, uint32_t& s, uint32_t& e) {
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_sort_small(const BatchDev 
     for (unsigned c = threadIdx.x; c < nch; c += kSortThreads) b.chunks[s_base[1] + c] = make_uint2(i, c);
     return;
   }
-  sort_chunk<kSortThreads>(b.keys + s, n, sk[0], sk[1]);
+  sort_chunk<kSortThreads>(b.keys + s, b.keys + s, n, sk[0], sk[1]);
 }
 
 // Sorts every 4096-key chunk of the long segments (grid-stride over the chunk list); two
@@ -359,14 +360,18 @@ __global__ void __launch_bounds__(kBigThreads) k_chunk_sort(const BatchDev b) {
     const uint32_t c0 = s + ch.y * kBig;
     if (c0 >= e) continue;
     const uint32_t c1 = c0 + kBig < e ? c0 + kBig : e;
-    sort_chunk<kBigThreads>(b.keys + c0, (int)(c1 - c0), sa, sb);
+    // a segment merged in R rounds starts them in keys_alt when R is odd, so that its
+    // last round writes keys
+    uint64_t* out = ((rounds_for(e - s) & 1) ? b.keys_alt : b.keys) + c0;
+    sort_chunk<kBigThreads>(b.keys + c0, out, (int)(c1 - c0), sa, sb);
     __syncthreads();
   }
 }
 
 // Merge round r (run width 4096 << r): each chunk work item produces 4096 outputs of the
-// merge of the two runs its output range falls in.  Data of round r lives in keys when r
-// is even and in keys_alt when r is odd.
+// merge of the two runs its output range falls in.  A segment merged in R rounds holds the
+// input of round r in keys_alt when R - r is odd and in keys otherwise, so its last round
+// writes keys.
 __global__ void __launch_bounds__(kBigThreads) k_merge_round(const BatchDev b, int r) {
   __shared__ uint64_t sm[kBigPadded];
   __shared__ uint32_t s_split[4];
@@ -383,8 +388,11 @@ __global__ void __launch_bounds__(kBigThreads) k_merge_round(const BatchDev b, i
     segment_of(b, t, s, e);
     const uint32_t n = e - s;
     if (n <= w) continue;  // this segment needs no merge at this width
-    const uint64_t* src = ((r & 1) ? b.keys_alt : b.keys) + s;
-    uint64_t* dst = ((r & 1) ? b.keys : b.keys_alt) + s;
+    // round r of a segment merged in R rounds reads keys_alt when R - r is odd (see the
+    // chunk sort), so its last round writes keys
+    const bool from_alt = ((rounds_for(n) - r) & 1) != 0;
+    const uint64_t* src = (from_alt ? b.keys_alt : b.keys) + s;
+    uint64_t* dst = (from_alt ? b.keys : b.keys_alt) + s;
     const uint32_t o0 = ch.y * kBig;
     if (o0 >= n) continue;
     const uint32_t o1 = o0 + kBig < n ? o0 + kBig : n;
@@ -431,21 +439,6 @@ __global__ void __launch_bounds__(kBigThreads) k_merge_round(const BatchDev b, i
   }
 }
 
-// Copies back the segments whose last merge round wrote keys_alt (odd round count).
-__global__ void __launch_bounds__(kBigThreads) k_merge_fixup(const BatchDev b) {
-  const unsigned count = *b.chunk_count;
-  for (unsigned wi = blockIdx.x; wi < count; wi += gridDim.x) {
-    const uint2 ch = b.chunks[wi];
-    const int64_t t = b.big_list[ch.x];
-    uint32_t s, e;
-    segment_of(b, t, s, e);
-    if ((rounds_for(e - s) & 1) == 0) continue;
-    const uint32_t c0 = s + ch.y * kBig;
-    const uint32_t c1 = c0 + kBig < e ? c0 + kBig : e;
-    for (uint32_t i = c0 + threadIdx.x; i < c1; i += kBigThreads) b.keys[i] = b.keys_alt[i];
-  }
-}
-
 void launch_seg_sort(const BatchDev& b, int max_rounds, cudaStream_t s) {
   if (b.n_tiles == 0) return;
   const int64_t items = b.order ? b.item_n : b.n_tiles;
@@ -461,8 +454,7 @@ void launch_seg_sort(const BatchDev& b, int max_rounds, cudaStream_t s) {
                                                  kChunkSmem, 0);
   k_chunk_sort<<<cgrid, kBigThreads, kChunkSmem, s>>>(b);
   for (int r = 0; r < max_rounds; ++r) k_merge_round<<<grid, kBigThreads, 0, s>>>(b, r);
-  k_merge_fixup<<<grid, kBigThreads, 0, s>>>(b);
-  count_launch(3 + max_rounds);
+  count_launch(2 + max_rounds);
 }
 
 // Merge rounds that cover any segment of a batch whose largest subset has max_n Gaussians
