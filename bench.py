@@ -442,6 +442,7 @@ def city_leg(args, rank, world, local, steps, warmup):
                          pair_capacity=cap, stream=stream, order=orders[0],
                          fused_adam=not args.unfused_adam)
         st.set_targets(tgt[0])
+        st.batch.set_timing(True)
         st.run()
         stream.synchronize()
         code, _ = st.status()
@@ -475,6 +476,7 @@ def city_leg(args, rank, world, local, steps, warmup):
         if code != S.OK:
             raise RuntimeError(f"city status after timed region {code}")
         ms = max_over_ranks(e0.elapsed_time(e1) / steps)
+        kms = st.batch.kernel_times()  # the last timed replay's kernels
         st.close()
     ctx.close()
     del dev, tgt
@@ -489,7 +491,8 @@ def city_leg(args, rank, world, local, steps, warmup):
             "scene_gen_s": gen_s, "l2": "inputs larger than L2 (28 GB parameters)",
             "timing": "CUDA events around the timed steps; each step sets its views, orders "
                       "and targets between replays (a host wait for the previous replay)",
-            "clocks": clk, "gpu_launches": launches_per_step * steps}
+            "clocks": clk, "gpu_launches": launches_per_step * steps,
+            "kernel_ms_last_step": kms}
 
 
 def city_main(args):
