@@ -510,7 +510,7 @@ def city_main(args):
             "data": "synthetic",
             "config": {k: r[k] for k in ("workload", "global_batch", "pixels_per_step", "tile",
                                          "pair_capacity", "saturation_skipping", "scene_gen_s",
-                                         "l2", "timing")},
+                                         "l2", "timing", "kernel_ms_last_step")},
             "roofline": None, "e2e": None, "clocks": r["clocks"],
             "gpu_launches": r["gpu_launches"]}
     line["config"]["parallelism"] = "replicas" if world > 1 else "single GPU"
