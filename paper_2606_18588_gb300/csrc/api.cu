@@ -234,6 +234,7 @@ struct Plan {
   unsigned* chunk_count = nullptr;
   uint2* ranges = nullptr;
   float4* grad2d = nullptr;
+  uint8_t* defer = nullptr;  // [ceil(N / 128)]: blocks left to the zero-gradient Adam pass
   unsigned long long* counters = nullptr;  // [kCounters]: see BatchDev::counters
   unsigned long long* work_ctr = nullptr;  // [2]: persistent rasterisers' work counters
   int persist_grid = 0;                    // persistent raster grid (0: one CTA per item)
@@ -363,7 +364,7 @@ struct Plan {
                    (void**)&counts, (void**)&tile_cnt, (void**)&tile_start, (void**)&keys,
                    (void**)&keys_alt, (void**)&big_list, (void**)&big_count, (void**)&chunks,
                    (void**)&chunk_count, (void**)&ranges,
-                   (void**)&grad2d, (void**)&scan_temp, (void**)&counters, (void**)&work_ctr,
+                   (void**)&grad2d, (void**)&defer, (void**)&scan_temp, (void**)&counters, (void**)&work_ctr,
                    (void**)&order_d, (void**)&rank_d, (void**)&sat_d, (void**)&tpre,
                    (void**)&omega, (void**)&cells_d,
                    (void**)&cross, (void**)&zr, (void**)&removed, (void**)&omega_x,
@@ -1267,6 +1268,11 @@ int splx_batch_backward_adam(splx_batch_t bt, const float* dL_drgb, const float*
   at.step_dev = step_dev;
   CtxScope scope(P.ctx);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!P.defer) {
+    int r = ctx_alloc_t(P.ctx, &P.defer, (size_t)std::max<int64_t>((P.N + 127) / 128, 1), s);
+    if (r) return r;
+  }
+  at.defer = P.defer;
   BatchDev b = P.dev();
   b.dL_drgb = dL_drgb;
   b.dL_dT = dL_dT;

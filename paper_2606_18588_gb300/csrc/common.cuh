@@ -185,6 +185,9 @@ struct AdamTable {
   float b1, b2, eps;
   int64_t step;
   const int64_t* step_dev;
+  // optional, [ceil(N / 128)]: the fused projection adjoint leaves to a second, streaming
+  // pass the 128-Gaussian blocks in which no Gaussian has a gradient (flag 1)
+  uint8_t* defer;
 };
 
 __host__ __device__ inline int n_sh(int deg) { return (deg + 1) * (deg + 1); }

@@ -99,10 +99,21 @@ __device__ __forceinline__ bool proj_grads(const BatchDev& b, const int64_t g, f
                                            float4* ring, float* ringb,
                                            float (&out_m)[3], float (&out_ls)[3],
                                            float (&out_q)[4], float& out_logit) {
+  constexpr int NC = (DEG + 1) * (DEG + 1);
+  if (b.counts) {
+    // a Gaussian that no view kept has no 2-D gradient: leave before reading its
+    // parameters (most of a large scene that a few views see); all counts loads in flight
+    uint32_t seen = 0u;
+    for (int v = 0; v < b.V; ++v) seen |= b.counts[(int64_t)v * b.N + g];
+    if (!seen) {
+#pragma unroll
+      for (int e = 0; e < NC * 3; ++e) gsh[e * kGs] = 0.f;
+      return false;
+    }
+  }
   const int k = subset_of(b, g);
   const SubsetDev& S = b.subsets[k];
   const int64_t i = g - b.goff[k];
-  constexpr int NC = (DEG + 1) * (DEG + 1);
   float m[3], ls[3];
 #pragma unroll
   for (int e = 0; e < 3; ++e) { m[e] = S.means[3 * i + e]; ls[e] = S.log_scales[3 * i + e]; }
@@ -490,6 +501,13 @@ __global__ void __launch_bounds__(kProjBwdThreads, 4)
     __shared__ float s_sc[7];
     __shared__ int s_k[kProjBwdThreads];
     __shared__ int64_t s_i[kProjBwdThreads];
+    if (at.defer) {
+      // a block without any gradient (most of a large scene that few views see) is left
+      // to the zero-gradient pass, which streams it at full occupancy
+      const bool cta_any = __syncthreads_or(any) != 0;
+      if (threadIdx.x == 0) at.defer[blockIdx.x] = cta_any ? 0 : 1;
+      if (!cta_any) return;
+    }
     float* col = s_grad + threadIdx.x;
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
@@ -551,6 +569,77 @@ __global__ void __launch_bounds__(kProjBwdThreads, 4)
   }
 }
 
+// Adam with a zero gradient over the 128-Gaussian blocks that the fused projection adjoint
+// deferred (at.defer[blk] = 1): the same element function and bias-corrected rates, so the
+// result is bit for bit that of the fused epilogue.  A grid-stride loop over blocks at full
+// occupancy; each block's ranges are contiguous within its subset (element by element when
+// it straddles two subsets).
+template <int NC3>
+__global__ void __launch_bounds__(256) k_adam_zero(const BatchDev b, const AdamTable at) {
+  __shared__ float s_sc[7];
+  adam_scales(at, s_sc);
+  const float b1 = at.b1, b2 = at.b2, eps = at.eps, bci = s_sc[6];
+  const int64_t nblk = (b.N + kProjBwdThreads - 1) / kProjBwdThreads;
+  constexpr int W[5] = {3, 3, 4, 1, NC3};
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    if (!at.defer[blk]) continue;
+    const int64_t g0 = blk * kProjBwdThreads;
+    const int ng = b.N - g0 < kProjBwdThreads ? (int)(b.N - g0) : kProjBwdThreads;
+    const int k0 = subset_of(b, g0), k1 = subset_of(b, g0 + ng - 1);
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+      const int w = W[a];
+      const float lo = s_sc[a < 4 ? a : 4], hi = s_sc[a < 4 ? a : 5];
+      const int E = ng * w;
+      if (k0 == k1) {
+        const int64_t o = (g0 - b.goff[k0]) * w;
+        float* pb = at.p[k0][a] + o;
+        float* mb = at.m[k0][a] + o;
+        float* vb = at.v[k0][a] + o;
+        constexpr int kU = 4;
+        for (int base = threadIdx.x; base < E; base += kU * 256) {
+          float pv[kU], mv[kU], vv[kU];
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const int idx = base + u * 256;
+            if (idx < E) {
+              pv[u] = pb[idx];
+              mv[u] = mb[idx];
+              vv[u] = vb[idx];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const int idx = base + u * 256;
+            if (idx < E) {
+              const int e = idx % w;
+              adam_elem(pv[u], 0.0f, mv[u], vv[u], e < 3 ? lo : hi, b1, b2, bci, eps);
+              pb[idx] = pv[u];
+              mb[idx] = mv[u];
+              vb[idx] = vv[u];
+            }
+          }
+        }
+      } else {
+        for (int idx = threadIdx.x; idx < E; idx += 256) {
+          const int j = idx / w, e = idx - j * w;
+          const int64_t g = g0 + j;
+          const int k = subset_of(b, g);
+          const int64_t off = (g - b.goff[k]) * w + e;
+          float* pp = at.p[k][a] + off;
+          float* mp = at.m[k][a] + off;
+          float* vp = at.v[k][a] + off;
+          float pv = *pp, mv = *mp, vv = *vp;
+          adam_elem(pv, 0.0f, mv, vv, e < 3 ? lo : hi, b1, b2, bci, eps);
+          *pp = pv;
+          *mp = mv;
+          *vp = vv;
+        }
+      }
+    }
+  }
+}
+
 template <bool kFuse>
 static void launch_project_bwd_t(const BatchDev& b, const GradTable& gt, const AdamTable& at,
                                  cudaStream_t s) {
@@ -577,6 +666,17 @@ void launch_project_bwd_adam(const BatchDev& b, const AdamTable& at, cudaStream_
   memset(&gt, 0, sizeof(gt));
   if (at.step_dev) launch_step_increment(const_cast<int64_t*>(at.step_dev), s);
   launch_project_bwd_t<true>(b, gt, at, s);
+  if (!at.defer || b.N == 0) return;
+  const int64_t nblk = (b.N + kProjBwdThreads - 1) / kProjBwdThreads;
+  int64_t blocks = (int64_t)device_sm_count() * 8;  // one wave of 256-thread CTAs
+  if (blocks > nblk) blocks = nblk;
+  switch (b.sh_degree) {
+    case 0: k_adam_zero<3><<<(unsigned)blocks, 256, 0, s>>>(b, at); break;
+    case 1: k_adam_zero<12><<<(unsigned)blocks, 256, 0, s>>>(b, at); break;
+    case 2: k_adam_zero<27><<<(unsigned)blocks, 256, 0, s>>>(b, at); break;
+    default: k_adam_zero<48><<<(unsigned)blocks, 256, 0, s>>>(b, at); break;
+  }
+  count_launch();
 }
 
 // ---------------------------------------------------------------- Adam

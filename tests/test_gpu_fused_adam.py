@@ -22,14 +22,15 @@ def ctx():
     c.close()
 
 
-def _tile_bound_case(sizes=(333, 400, 267), deg=3, seed=7):
+def _tile_bound_case(sizes=(333, 400, 267), deg=3, seed=7, hidden=0):
     """Gaussians whose footprints lie inside one 16-pixel tile in each of two 128x128 views
     (the second view's principal point shifted by exactly one tile), so each (view,
     Gaussian) 2-D gradient is a single atomic add onto zero and the whole backward is
     deterministic.  Centres sit within 2 px of a tile centre; projected standard deviations
     are below 0.7 px before the 0.3 px^2 dilation, so 3-sigma footprints stay within 5 px
     of it.  The three subsets are contiguous with sizes that put subset boundaries inside
-    128-Gaussian blocks."""
+    128-Gaussian blocks.  The last `hidden` Gaussians lie behind both cameras (no view keeps
+    them, so they have no gradient)."""
     rng = np.random.default_rng(seed)
     n = sum(sizes)
     f, c0 = 100.0, 64.0
@@ -37,6 +38,8 @@ def _tile_bound_case(sizes=(333, 400, 267), deg=3, seed=7):
     v = 8.0 + 16.0 * rng.integers(0, 8, n) + rng.uniform(-2.0, 2.0, n)
     z = rng.uniform(4.5, 5.5, n)
     means = np.stack([(u - c0) * z / f, (v - c0) * z / f, z], 1).astype(np.float32)
+    if hidden:
+        means[n - hidden:, 2] = -means[n - hidden:, 2]
     log_scales = np.log(rng.uniform(0.01, 0.03, (n, 3))).astype(np.float32)
     q = rng.standard_normal((n, 4)).astype(np.float32)
     q /= np.linalg.norm(q, axis=1, keepdims=True)
@@ -94,6 +97,26 @@ def test_fused_adam_is_bit_identical_where_the_backward_is_deterministic(ctx, de
     for k in GROUPS:  # the steps did update every group
         moved += int((a["p"][k].cpu() != torch.from_numpy(getattr(sc, k))).any())
     assert moved == len(GROUPS)
+
+
+def test_fused_adam_defers_blocks_without_gradients(ctx):
+    # the last 300 Gaussians (two subsets) lie behind the cameras: the 128-Gaussian blocks
+    # without any gradient go to the zero-gradient pass (one of them across the boundary of
+    # the two hidden subsets, one partial at the end), the block that mixes visible and
+    # hidden Gaussians stays in the fused epilogue; parameters and moments bit for bit those
+    # of the separate Adam pass
+    sizes = (333, 400, 267, 150, 150)
+    sc, off, cams = _tile_bound_case(sizes=sizes, deg=3, seed=13, hidden=300)
+    tg = [torch.from_numpy(I.random_image(c.height, c.width, 70 + i)) for i, c in enumerate(cams)]
+    a = _train(ctx, sc, off, cams, tg, fused=False, steps=3)
+    b = _train(ctx, sc, off, cams, tg, fused=True, steps=3)
+    for part in ("p", "m", "v"):
+        for k in GROUPS:
+            assert torch.equal(a[part][k], b[part][k]), (part, k)
+    # hidden Gaussians: zero gradient every step, so their moments stay zero and they stay put
+    for k in GROUPS:
+        assert not b["m"][k][1000:].any() and not b["v"][k][1000:].any(), k
+        assert torch.equal(b["p"][k][1000:].cpu(), torch.from_numpy(getattr(sc, k)[1000:])), k
 
 
 def test_fused_adam_with_an_empty_subset(ctx):
