@@ -22,7 +22,7 @@ thread_local int64_t* g_launch_counter = nullptr;
 
 namespace {
 constexpr int kMaxDev = 64;
-constexpr int kSmemSlots = 4;
+constexpr int kSmemSlots = 16;
 std::mutex g_dev_mu;
 int g_sm_count[kMaxDev] = {};
 bool g_smem_done[kMaxDev][kSmemSlots] = {};

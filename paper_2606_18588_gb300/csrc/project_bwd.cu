@@ -640,6 +640,50 @@ __global__ void __launch_bounds__(256) k_adam_zero(const BatchDev b, const AdamT
   }
 }
 
+// The zero-gradient pass over one parameter array of the whole batch when the subsets'
+// arrays are consecutive slices of one allocation (p, m, v of n = N W floats): a flat
+// grid-stride stream of four floats at a time over the deferred blocks only (a 128-Gaussian
+// block is 32 W float4s, so no float4 straddles two blocks).  Same element function and
+// rates as the fused epilogue.
+template <int W>
+__global__ void __launch_bounds__(256) k_adam_zero_flat(const AdamTable at, int a,
+                                                        float* __restrict__ p,
+                                                        float* __restrict__ m,
+                                                        float* __restrict__ v, int64_t n) {
+  __shared__ float s_sc[7];
+  adam_scales(at, s_sc);
+  const float b1 = at.b1, b2 = at.b2, eps = at.eps, bci = s_sc[6];
+  const float lo = s_sc[a < 4 ? a : 4], hi = s_sc[a < 4 ? a : 5];
+  const int64_t n4 = n >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
+    if (!at.defer[q / (32 * W)]) continue;
+    float4 p4 = reinterpret_cast<float4*>(p)[q];
+    float4 m4 = reinterpret_cast<float4*>(m)[q];
+    float4 v4 = reinterpret_cast<float4*>(v)[q];
+    float* pe = &p4.x;
+    float* me = &m4.x;
+    float* ve = &v4.x;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int e = (int)((4 * q + c) % W);
+      adam_elem(pe[c], 0.0f, me[c], ve[c], e < 3 ? lo : hi, b1, b2, bci, eps);
+    }
+    reinterpret_cast<float4*>(p)[q] = p4;
+    reinterpret_cast<float4*>(m)[q] = m4;
+    reinterpret_cast<float4*>(v)[q] = v4;
+  }
+  for (int64_t idx = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += stride) {
+    if (!at.defer[idx / (128 * W)]) continue;
+    float pv = p[idx], mv = m[idx], vv = v[idx];
+    adam_elem(pv, 0.0f, mv, vv, idx % W < 3 ? lo : hi, b1, b2, bci, eps);
+    p[idx] = pv;
+    m[idx] = mv;
+    v[idx] = vv;
+  }
+}
+
 template <bool kFuse>
 static void launch_project_bwd_t(const BatchDev& b, const GradTable& gt, const AdamTable& at,
                                  cudaStream_t s) {
@@ -667,6 +711,42 @@ void launch_project_bwd_adam(const BatchDev& b, const AdamTable& at, cudaStream_
   if (at.step_dev) launch_step_increment(const_cast<int64_t*>(at.step_dev), s);
   launch_project_bwd_t<true>(b, gt, at, s);
   if (!at.defer || b.N == 0) return;
+  // one allocation per array (each subset's slice right after the previous one, 16-byte
+  // aligned): a flat stream per array, one wave of resident CTAs
+  const int width[5] = {3, 3, 4, 1, 3 * n_sh(b.sh_degree)};
+  bool flat = true;
+  for (int a = 0; a < 5 && flat; ++a)
+    for (int t = 0; t < 3 && flat; ++t) {
+      float* const* base = t == 0 ? at.p[0] : t == 1 ? at.m[0] : at.v[0];
+      if ((reinterpret_cast<uintptr_t>(base[a]) & 15) != 0) flat = false;
+      for (int k = 1; k < b.K && flat; ++k) {
+        if (b.goff[k + 1] == b.goff[k]) continue;  // an empty subset has no arrays
+        float* const* tk = t == 0 ? at.p[k] : t == 1 ? at.m[k] : at.v[k];
+        if (tk[a] != base[a] + b.goff[k] * width[a]) flat = false;
+      }
+    }
+  if (flat) {
+    for (int a = 0; a < 5; ++a) {
+      const int64_t n = b.N * width[a];
+      auto go = [&](auto kernel, int slot) {
+        int64_t blocks =
+            (int64_t)device_sm_count() * resident_ctas((const void*)kernel, 256, 0, slot);
+        const int64_t need = ((n >> 2) + 255) / 256;
+        if (blocks > need) blocks = need > 0 ? need : 1;
+        kernel<<<(unsigned)blocks, 256, 0, s>>>(at, a, at.p[0][a], at.m[0][a], at.v[0][a], n);
+      };
+      switch (width[a]) {  // (a cache slot of resident_ctas per kernel)
+        case 3: go(k_adam_zero_flat<3>, 8); break;
+        case 4: go(k_adam_zero_flat<4>, 9); break;
+        case 1: go(k_adam_zero_flat<1>, 10); break;
+        case 12: go(k_adam_zero_flat<12>, 11); break;
+        case 27: go(k_adam_zero_flat<27>, 12); break;
+        default: go(k_adam_zero_flat<48>, 13); break;
+      }
+      count_launch();
+    }
+    return;
+  }
   const int64_t nblk = (b.N + kProjBwdThreads - 1) / kProjBwdThreads;
   int64_t blocks = (int64_t)device_sm_count() * 8;  // one wave of 256-thread CTAs
   if (blocks > nblk) blocks = nblk;

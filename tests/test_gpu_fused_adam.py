@@ -217,3 +217,54 @@ def test_step_from_host_equals_the_captured_step(ctx):
         assert torch.equal(st.m[k], a["m"][k]) and torch.equal(st.v[k], a["v"][k]), k
     assert np.isfinite(host_loss.item()) and host_loss.item() > 0
     st.close()
+
+
+def test_update_step_on_separately_allocated_subsets(ctx):
+    # subsets in arrays of their own (not slices of one allocation): the update step takes
+    # its block-by-block route, deferred blocks included; one step equals the backward into
+    # gradient arrays followed by splx_step on each subset, bit for bit
+    from paper_2606_18588_gb300 import splx as S
+    sizes = (333, 400, 267, 150, 150)
+    sc, off, cams = _tile_bound_case(sizes=sizes, deg=3, seed=17, hidden=300)
+    K = len(sizes)
+    lr = (1e-3, 2e-3, 3e-3, 4e-3, 5e-3, 6e-3)
+
+    def split():
+        return [{k: torch.from_numpy(np.ascontiguousarray(getattr(sc, k)[off[j]:off[j + 1]])).cuda()
+                 for k in GROUPS} for j in range(K)]
+
+    def run(fused):
+        par = split()
+        mom = [{k: torch.zeros_like(t) for k, t in d.items()} for d in par]
+        vel = [{k: torch.zeros_like(t) for k, t in d.items()} for d in par]
+        subs = [S.gaussians(*(d[k] for k in GROUPS), sc.sh_degree) for d in par]
+        b = S.Batch(ctx, subs, cams, S.opts())
+        rgb = torch.empty(b.rgb_off[-1], device="cuda")
+        b.forward(rgb)
+        tgt = torch.from_numpy(np.concatenate([I.random_image(c.height, c.width, 80 + i).reshape(-1)
+                                               for i, c in enumerate(cams)])).cuda()
+        loss = torch.zeros(1, device="cuda")
+        dL = torch.empty_like(rgb)
+        S.loss_l1(ctx, rgb, tgt, loss, dL)
+        ps = [S.params(*(d[k] for k in GROUPS), sc.sh_degree) for d in par]
+        ms = [S.params(*(d[k] for k in GROUPS), sc.sh_degree) for d in mom]
+        vs = [S.params(*(d[k] for k in GROUPS), sc.sh_degree) for d in vel]
+        if fused:
+            step = torch.zeros(1, dtype=torch.int64, device="cuda")
+            b.backward_adam(dL, None, ps, ms, vs, S.adam_hp(lr), step)
+        else:
+            gr = [{k: torch.zeros_like(t) for k, t in d.items()} for d in par]
+            gs = [S.params(*(d[k] for k in GROUPS), sc.sh_degree) for d in gr]
+            b.backward(dL, None, gs)
+            for j in range(K):
+                S.step(ctx, ps[j], gs[j], ms[j], vs[j], lr, 1)
+        torch.cuda.synchronize()
+        assert b.status()[0] == S.OK
+        b.close()
+        return par, mom, vel
+
+    a, b = run(False), run(True)
+    for x, y in zip(a, b):
+        for dx, dy in zip(x, y):
+            for k in GROUPS:
+                assert torch.equal(dx[k], dy[k]), k
