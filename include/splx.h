@@ -263,9 +263,11 @@ int splx_batch_backward(splx_batch_t b, const float* dL_drgb, const float* dL_dT
  *   m[k], v[k] device Adam moments of subset k (same layout), updated in place.
  *   hp         learning rates, betas, eps (zero_grad is ignored: there is no gradient).
  *   step_dev   device int64 step counter, incremented first; the update uses the new value.
- * Host arrays params, m, v hold K entries each; nothing is owned by the call.  Never
- * synchronises; capturable once the batch exists.  Per-element arithmetic is that of
- * splx_step, so both routes give bit-identical parameters. */
+ * Host arrays params, m, v hold K entries each; nothing is owned by the call (the batch
+ * keeps one flag byte per 128 Gaussians, allocated at the first call: blocks without any
+ * gradient are updated by a second, streaming pass).  Never synchronises; capturable once
+ * the batch exists.  Per-element arithmetic is that of splx_step, so both routes give
+ * bit-identical parameters. */
 int splx_batch_backward_adam(splx_batch_t b, const float* dL_drgb, const float* dL_dT,
                              const splx_params* params, const splx_params* m,
                              const splx_params* v, const splx_adam* hp, int64_t* step_dev,
