@@ -90,8 +90,8 @@ constexpr int kRing = 3;
 
 // The gradient of one Gaussian g over all views: mean, log-scale, quaternion and opacity
 // logit in the outputs, the SH coefficients' in gsh (one column of shared memory, element e
-// at gsh[e * kGs]); false (outputs untouched, gsh zero) where no view left a
-// 2-D gradient.  Consumes and clears the views' 2-D gradients.  ring / ringb: this
+// at gsh[e * kGs]); false (outputs untouched) where no view left a 2-D gradient, with gsh
+// zeroed, or untouched when no view kept the Gaussian at all.  Consumes and clears the views' 2-D gradients.  ring / ringb: this
 // thread's column of the kRing-slot ring (slot s: float4s at ring[(2 s + k) *
 // kProjBwdThreads], k = 0, 1, and the ninth value at ringb[s * kProjBwdThreads]).
 template <int DEG>
@@ -105,11 +105,7 @@ __device__ __forceinline__ bool proj_grads(const BatchDev& b, const int64_t g, f
     // parameters (most of a large scene that a few views see); all counts loads in flight
     uint32_t seen = 0u;
     for (int v = 0; v < b.V; ++v) seen |= b.counts[(int64_t)v * b.N + g];
-    if (!seen) {
-#pragma unroll
-      for (int e = 0; e < NC * 3; ++e) gsh[e * kGs] = 0.f;
-      return false;
-    }
+    if (!seen) return false;  // (gsh untouched)
   }
   const int k = subset_of(b, g);
   const SubsetDev& S = b.subsets[k];
@@ -467,9 +463,6 @@ __global__ void __launch_bounds__(kProjBwdThreads, 4)
   if (g < b.N) {
     any = proj_grads<DEG>(b, g, gsh, s_ring + threadIdx.x, s_ringb + threadIdx.x, gm, gls, gq,
                           glogit);
-  } else if (kFuse) {
-#pragma unroll
-    for (int e = 0; e < NC * 3; ++e) gsh[e * kGs] = 0.f;
   }
   if constexpr (!kFuse) {
     // add into the caller's gradient arrays (one thread owns one Gaussian: no atomics)
@@ -507,6 +500,10 @@ __global__ void __launch_bounds__(kProjBwdThreads, 4)
       const bool cta_any = __syncthreads_or(any) != 0;
       if (threadIdx.x == 0) at.defer[blockIdx.x] = cta_any ? 0 : 1;
       if (!cta_any) return;
+    }
+    if (!any) {  // a zero gradient (and a column proj_grads may have left untouched)
+#pragma unroll
+      for (int e = 0; e < NC * 3; ++e) gsh[e * kGs] = 0.f;
     }
     float* col = s_grad + threadIdx.x;
 #pragma unroll
