@@ -6,7 +6,10 @@
 // chains it to the mean (through the 2-D mean, the EWA Jacobian J and the SH viewing
 // direction), the SH coefficients, the opacity logit, and - accumulated over views as
 // dL/dM for M = R(q) diag(s) - the log-scales and the quaternion.  Results are added
-// to the caller's gradient arrays (one thread owns one Gaussian: no atomics).
+// to the caller's gradient arrays (one thread owns one Gaussian: no atomics), or, in the
+// batch's update step, applied at once by Adam from shared memory (k_project_bwd<DEG,
+// true>), the blocks without any gradient being left to a streaming zero-gradient pass.
+// k_adam is the stand-alone Adam over gradient arrays; all routes share adam_elem.
 #include "common.cuh"
 #include "spec.cuh"
 
