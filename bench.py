@@ -26,12 +26,16 @@ sys.path.insert(0, ROOT)
 METRIC = "fwd+bwd Mpixel/s at 10M Gaussians, batched vs plain; serve p50/p99 ms"
 UNIT = "Mpixel/s"
 
-# Algorithmic FP32 operations of the rasterisers per counted (pixel, list entry) event:
-# an alpha evaluation (dx, dy, the conic's quadratic form, exp2, times opacity, clamp,
-# threshold), a forward blend (1 - alpha, T update, stop test, alpha T, rgb and depth
-# accumulation) and a backward contribution (T_i recovery 4, colour gradient 3, the dot
-# product of dL/dC with the colour 3, dL/dalpha 2, opacity 1, dL/dpower 1, its five
-# moments in dx, dy 7, the suffix term 1).
+# Algorithmic FP32 work of the rasterisers per evaluated (pixel, list entry) pair, the unit
+# the roofline counts: about 16 FP32-pipe instructions in the forward and 45 in the backward
+# (plus one exp2 on the special-function unit, outside the FP32 peak).
+OPS_PER_EVAL_FWD = 16
+OPS_PER_EVAL_BWD = 45
+# The bare arithmetic of the same events, reported beside it: an alpha evaluation (dx, dy,
+# the conic's quadratic form, exp2, times opacity, clamp, threshold), a forward blend
+# (1 - alpha, T update, stop test, alpha T, rgb and depth accumulation) and a backward
+# contribution (T_i recovery 4, colour gradient 3, the dot product of dL/dC with the colour
+# 3, dL/dalpha 2, opacity 1, dL/dpower 1, its five moments in dx, dy 7, the suffix term 1).
 OPS_PER_ALPHA = 10
 OPS_PER_BLEND = 8
 OPS_PER_CONTRIB = 22
@@ -208,15 +212,18 @@ def roofline(name, ms, counts, w, pk):
     sec = ms / 1e3
     if name in ("raster_fwd", "raster_bwd"):
         if name == "raster_fwd":
-            ev, more, per = counts["alpha_fwd"], counts["blended"], OPS_PER_BLEND
+            ev, more, per, unit = counts["alpha_fwd"], counts["blended"], OPS_PER_BLEND, OPS_PER_EVAL_FWD
         else:
-            ev, more, per = counts["alpha_bwd"], counts["contrib_bwd"], OPS_PER_CONTRIB
-        ops = ev * OPS_PER_ALPHA + more * per
-        a = ops / sec / 1e12
+            ev, more, per, unit = counts["alpha_bwd"], counts["contrib_bwd"], OPS_PER_CONTRIB, OPS_PER_EVAL_BWD
+        a = ev * unit / sec / 1e12
+        bare = (ev * OPS_PER_ALPHA + more * per) / sec / 1e12
         return {"kernel": name, "bound": "alu", "achieved": a, "peak": alu_peak,
                 "unit": "T FP32 ops/s", "frac": a / alu_peak, "traffic": None,
-                "work": f"{ev} alpha evaluations x {OPS_PER_ALPHA} + {more} "
-                        f"{'blends' if name == 'raster_fwd' else 'contributions'} x {per} FP32 ops"}
+                "work": f"{ev} evaluated (pixel, entry) pairs x {unit} FP32 instructions",
+                "arithmetic": {"achieved": bare, "frac": bare / alu_peak,
+                               "work": f"{ev} alpha evaluations x {OPS_PER_ALPHA} + {more} "
+                                       f"{'blends' if name == 'raster_fwd' else 'contributions'}"
+                                       f" x {per} FP32 ops"}}
     param_bytes = (3 + 3 + 4 + 1 + 3 * nc) * 4
     note = None
     # share of (view, subset, tile) work items inside the subsets' visible regions: the
@@ -777,6 +784,8 @@ def main():
             r = roofline(name, t, counts, wl, pk)
             others[name] = {"bound": r["bound"], "achieved": r["achieved"], "unit": r["unit"],
                             "frac": r["frac"], "ms": t}
+            if "arithmetic" in r:
+                others[name]["frac_arithmetic"] = r["arithmetic"]["frac"]
             if "note" in r:
                 others[name]["note"] = r["note"]
             if overlapped and name == "raster_fwd":
