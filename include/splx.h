@@ -307,6 +307,17 @@ int splx_batch_loss_l1_dssim(splx_batch_t b, const float* rgb, const float* targ
  * their partial planes (treated as empty: C = 0, T = 1).  Results are identical with it on
  * or off.  enable = 0 turns it off for launches issued afterwards. */
 int splx_batch_set_visibility(splx_batch_t b, int32_t enable);
+/* Selected-prefix sort of long tile segments (the per-tile depth sort of Sec. 2 step 2,
+ * restricted to what the forward reaches).  On by default for batches: a segment longer
+ * than 2048 keys gets only its nearest keys (at most 2048, the keys below a depth threshold
+ * read from a two-level histogram of the key's depth bits) sorted, and the forward walks
+ * that prefix; a work item whose pixels are still blending at the prefix's end renders
+ * nothing in that pass, and after its segment is sorted whole it is rendered again, so
+ * images, transmittances and gradients are those of whole-segment sorts.  enable = 0 sorts
+ * every segment whole, for launches issued afterwards (a captured graph keeps the mode it
+ * was captured with).  Off while cross-boundary filtering is on, and for a pair capacity
+ * of 2^31 or more. */
+int splx_batch_set_prefix_sort(splx_batch_t b, int32_t enable);
 /* Cross-boundary per-ray filtering (Sec. 8.1, appendix "Cross-boundary Gaussians
  * Handling").  cells (host, [K][6] floats: lo x, y, z, hi x, y, z of subset k's k-d box,
  * +-INFINITY on open sides; NaN rejected) turns it on for launches issued afterwards (and
@@ -359,13 +370,18 @@ int splx_batch_kernel_times(splx_batch_t b, float* ms_out);
  * splx_graph_set_timing_ring (waits for that replay's final event only).  SPLX_ERR_INVALID
  * for a slot outside the ring. */
 int splx_batch_kernel_times_slot(splx_batch_t b, splx_graph_t g, int32_t slot, float* ms_out);
-/* Work counters (synchronises; host array of 9): out[0] = (Gaussian, tile) pairs of the
+/* Work counters (synchronises; host array of 11): out[0] = (Gaussian, tile) pairs of the
  * last run; then, from the last EAGER run (replays of a captured graph do not count):
  * forward rasteriser out[1] = (thread, list entry) pairs examined, out[2] = (pixel,
  * entry) alpha evaluations, out[3] = (pixel, entry) blends; backward rasteriser out[4] =
  * (thread, entry) pairs, out[5] = alpha evaluations, out[6] = contributions (alpha >=
  * alpha_min); out[7] = (view, subset, tile) work items left empty by saturation skipping
- * (no open pixel); out[8] = work items outside their subset's visible region.
+ * (no open pixel); out[8] = work items outside their subset's visible region; out[9] =
+ * work items whose segment, longer than 2048 keys, the forward walked on its sorted
+ * prefix of the nearest keys (at most 2048), out[10] = those of them (and those with no
+ * prefix) whose pixels were still open at the prefix's end, so that the segment was
+ * sorted whole and the item rendered again (the batch's results are those of whole
+ * sorts either way).
  * A forward thread owns 2 pixels (8x8, 16x16 tiles) or 4 (32x32); a backward thread 2
  * (8x8), 8 (16x16: one warp per tile) or 4 (32x32). */
 int splx_batch_counters(splx_batch_t b, int64_t* out, splx_stream_t stream);

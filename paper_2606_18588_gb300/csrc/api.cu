@@ -248,6 +248,15 @@ struct Plan {
   unsigned* big_count_g[kGroups - 1] = {};
   uint2* chunks_g[kGroups - 1] = {};
   unsigned* chunk_count_g[kGroups - 1] = {};
+  // selected-prefix sort of long segments (batches; see BatchDev::sel): per image tile the
+  // prefix length, and per view group the forward's retry list and its count
+  bool select_prefix = false;
+  bool alt_in_keys = false;  // keys_alt = keys + capacity (one allocation, owned by keys)
+  uint32_t* sel = nullptr;
+  uint32_t* retry = nullptr;
+  unsigned* retry_count = nullptr;
+  uint32_t* retry_g[kGroups - 1] = {};
+  unsigned* retry_count_g[kGroups - 1] = {};
   int32_t* order_d = nullptr;              // [V][K] front-to-back subset order (skipping on)
   int32_t* rank_d = nullptr;               // [V][K] rank of subset k in view v's order
   // stale saturation state (with order_d): device table of the V views' state planes;
@@ -348,6 +357,10 @@ struct Plan {
     b.tpre = tpre;
     b.sat = stale() ? sat_d : nullptr;
     b.rank = rank_d;
+    // (the cross-boundary filter's removed pairs keep the whole-segment sort)
+    b.sel = select_prefix && alt_in_keys && sel && !b.removed ? sel : nullptr;
+    b.retry = retry;
+    b.retry_count = retry_count;
     // composite-only plans carry no subsets; their offsets are unused
     for (int k = 0; k <= K; ++k) b.goff[k] = k < (int)subsets_h.size() ? subsets_h[k].goff : N;
     for (int v = 0; v <= V; ++v) { b.tile_base[v] = tile_base[v]; b.pix_off[v] = pix_off[v]; }
@@ -360,6 +373,10 @@ struct Plan {
   }
 
   void release(cudaStream_t s) {
+    if (alt_in_keys) {
+      keys_alt = nullptr;  // part of keys' allocation
+      alt_in_keys = false;
+    }
     void** ps[] = {(void**)&subsets_d, (void**)&views_d, (void**)&imgs_d, (void**)&rec,
                    (void**)&counts, (void**)&tile_cnt, (void**)&tile_start, (void**)&keys,
                    (void**)&keys_alt, (void**)&big_list, (void**)&big_count, (void**)&chunks,
@@ -368,9 +385,11 @@ struct Plan {
                    (void**)&order_d, (void**)&rank_d, (void**)&sat_d, (void**)&tpre,
                    (void**)&omega, (void**)&cells_d,
                    (void**)&cross, (void**)&zr, (void**)&removed, (void**)&omega_x,
-                   (void**)&zr_x};
+                   (void**)&zr_x, (void**)&sel, (void**)&retry, (void**)&retry_count};
     for (void** p : ps) free_ptr(*p, s);
     for (int g = 0; g < kGroups - 1; ++g) {
+      free_ptr((void*&)retry_g[g], s);
+      free_ptr((void*&)retry_count_g[g], s);
       free_ptr((void*&)big_list_g[g], s);
       free_ptr((void*&)big_count_g[g], s);
       free_ptr((void*&)chunks_g[g], s);
@@ -418,6 +437,7 @@ struct Plan {
     // with saturation-skipping waves each wave sorts its own segments; with a stale state
     // one sort covers the tiles it leaves open
     if (!order_d || stale()) {
+      if (b.sel) CK(cudaMemsetAsync(retry_count, 0, sizeof(unsigned), s));
       launch_seg_sort(b, merge_rounds_bound(max_subset()), s);
       CK_LAUNCH();
     }
@@ -463,17 +483,27 @@ struct Plan {
         if (g > 0) {
           bw.big_list = big_list_g[g - 1]; bw.big_count = big_count_g[g - 1];
           bw.chunks = chunks_g[g - 1]; bw.chunk_count = chunk_count_g[g - 1];
+          bw.retry = retry_g[g - 1]; bw.retry_count = retry_count_g[g - 1];
         }
       }
       if (r > 0) mark_wave(2 * r, s);
+      const int rounds = merge_rounds_bound(max_subset());
       for (int g = 0; g < G; ++g) {
         cudaStream_t sg = g ? side[g - 1] : s;
         CK(cudaMemsetAsync(bg[g].big_count, 0, 2 * sizeof(unsigned), sg));
         CK(cudaMemsetAsync(bg[g].chunk_count, 0, sizeof(unsigned), sg));
-        launch_seg_sort(bg[g], merge_rounds_bound(max_subset()), sg);
+        if (bg[g].sel) CK(cudaMemsetAsync(bg[g].retry_count, 0, sizeof(unsigned), sg));
+        launch_seg_sort(bg[g], rounds, sg);
       }
       mark_wave(2 * r + 1, s);
-      for (int g = 0; g < G; ++g) launch_raster_fwd(bg[g], g ? side[g - 1] : s);
+      for (int g = 0; g < G; ++g) {
+        cudaStream_t sg = g ? side[g - 1] : s;
+        launch_raster_fwd(bg[g], sg);
+        // items whose pixels were still open at the end of their selected prefix: full
+        // sort, second forward
+        launch_sort_retries(bg[g], rounds, sg);
+        launch_raster_fwd_retry(bg[g], sg);
+      }
       CK_LAUNCH();
     }
     for (int g = 1; g < G; ++g) {
@@ -495,8 +525,15 @@ struct Plan {
   int alloc_pairs(int64_t cap, cudaStream_t s) {
     capacity = cap;
     int r;
-    if ((r = ctx_alloc_t(ctx, &keys, (size_t)std::max<int64_t>(cap, 1), s))) return r;
-    if ((r = ctx_alloc_t(ctx, &keys_alt, (size_t)std::max<int64_t>(cap, 1), s))) return r;
+    if (select_prefix && cap > 0 && 2 * cap < (int64_t(1) << 32)) {
+      // selected prefixes are named by ranges into keys_alt through keys: one allocation
+      if ((r = ctx_alloc_t(ctx, &keys, (size_t)(2 * cap), s))) return r;
+      keys_alt = keys + cap;
+      alt_in_keys = true;
+    } else {
+      if ((r = ctx_alloc_t(ctx, &keys, (size_t)std::max<int64_t>(cap, 1), s))) return r;
+      if ((r = ctx_alloc_t(ctx, &keys_alt, (size_t)std::max<int64_t>(cap, 1), s))) return r;
+    }
     if ((r = ctx_alloc_t(ctx, &chunks, (size_t)chunk_list_capacity(n_tiles, cap), s))) return r;
     if (split_views)
       for (int g = 0; g < kGroups - 1; ++g)
@@ -518,6 +555,26 @@ struct Plan {
     }
     CK(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
     split_views = true;
+    return SPLX_OK;
+  }
+
+  // Selected-prefix sort state (batches): per tile prefix lengths, retry lists per group.
+  int alloc_select(cudaStream_t s) {
+    int r;
+    const size_t nt = (size_t)std::max<int64_t>(n_tiles, 1);
+    if ((r = ctx_alloc_t(ctx, &sel, nt, s))) return r;
+    if ((r = ctx_alloc_t(ctx, &retry, nt, s))) return r;
+    if ((r = ctx_alloc_t(ctx, &retry_count, 1, s))) return r;
+    if (split_views)
+      for (int g = 0; g < kGroups - 1; ++g) {
+        if ((r = ctx_alloc_t(ctx, &retry_g[g], nt, s))) return r;
+        if ((r = ctx_alloc_t(ctx, &retry_count_g[g], 1, s))) return r;
+      }
+    CK(cudaMemsetAsync(sel, 0, sizeof(uint32_t) * nt, s));
+    CK(cudaMemsetAsync(retry_count, 0, sizeof(unsigned), s));
+    for (int g = 0; g < kGroups - 1; ++g)
+      if (retry_count_g[g]) CK(cudaMemsetAsync(retry_count_g[g], 0, sizeof(unsigned), s));
+    select_prefix = true;
     return SPLX_OK;
   }
 
@@ -1122,6 +1179,7 @@ int splx_batch_create(splx_ctx_t ctx, const splx_gaussians* subsets, int32_t K,
   }
   if ((r = P.alloc_common(s))) return fail(r);
   if (V >= 2 && (r = P.alloc_split(s))) return fail(r);
+  if ((r = P.alloc_select(s))) return fail(r);
   if ((r = ctx_alloc_t(ctx, &P.grad2d, (size_t)V * N * 3, s))) return fail(r);
   if ((r = ctx_alloc_t(ctx, &P.counters, kCounters, s))) return fail(r);
   if ((r = ctx_alloc_t(ctx, &P.work_ctr, 2, s))) return fail(r);
@@ -1190,6 +1248,8 @@ int splx_batch_forward(splx_batch_t bt, float* out_rgb, float* out_T, splx_strea
   } else {
     // (with a stale saturation state the rasteriser leaves the pruned pixels empty)
     launch_raster_fwd(b, s);
+    launch_sort_retries(b, merge_rounds_bound(P.max_subset()), s);
+    launch_raster_fwd_retry(b, s);
   }
   P.mark(5, s);
   launch_composite(b, P.total_pixels, s);
@@ -1339,6 +1399,12 @@ int splx_batch_loss_l1_dssim(splx_batch_t bt, const float* rgb, const float* tar
 int splx_batch_set_visibility(splx_batch_t bt, int32_t enable) {
   if (!bt || !bt->plan.omega) return SPLX_ERR_INVALID;
   bt->plan.visibility = enable != 0;
+  return SPLX_OK;
+}
+
+int splx_batch_set_prefix_sort(splx_batch_t bt, int32_t enable) {
+  if (!bt || !bt->plan.sel) return SPLX_ERR_INVALID;
+  bt->plan.select_prefix = enable != 0;
   return SPLX_OK;
 }
 

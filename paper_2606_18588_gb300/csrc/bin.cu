@@ -163,6 +163,110 @@ __device__ __forceinline__ uint32_t merge_path_warp(const uint64_t* A, uint32_t 
   return lo;
 }
 
+// ---- selected-prefix sort (BatchDev::sel) ----
+constexpr int kHistBins = 4096;
+constexpr int kHistPer = kHistBins / kSortThreads;  // bins per thread in the boundary scan
+
+// With base + (all keys counted in hist) > cap: the bin j whose keys take the running
+// count base + (keys in bins below j) from at most cap to above it.  Writes j to s_tmp[8]
+// and base + (keys below j) to s_tmp[9]; s_tmp[0..7] hold the warps' totals.  Whole-CTA
+// call; the results are valid after it returns.
+__device__ __forceinline__ void hist_boundary(const unsigned* hist, unsigned base, unsigned cap,
+                                              unsigned* s_tmp) {
+  const int t = (int)threadIdx.x, lane = t & 31, w = t >> 5;
+  if (t == 0) { s_tmp[8] = 0u; s_tmp[9] = base; }  // (always overwritten below)
+  unsigned v[kHistPer];
+  unsigned sum = 0;
+#pragma unroll
+  for (int r = 0; r < kHistPer; ++r) {
+    v[r] = hist[t * kHistPer + r];
+    sum += v[r];
+  }
+  unsigned inc = sum;  // inclusive prefix over the warp's threads
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_tmp[w] = inc;
+  __syncthreads();
+  unsigned before = base + inc - sum;
+  for (int i = 0; i < w; ++i) before += s_tmp[i];
+#pragma unroll
+  for (int r = 0; r < kHistPer; ++r) {
+    if (before <= cap && cap < before + v[r]) {  // true for exactly one bin
+      s_tmp[8] = (unsigned)(t * kHistPer + r);
+      s_tmp[9] = before;
+    }
+    before += v[r];
+  }
+  __syncthreads();
+}
+
+// Sorts the S <= kSelCap smallest keys of the segment [s, e) (n > kChunk keys) into
+// keys_alt[s, s + S) and records S in sel[t] and ranges[t] = [capacity + s, capacity + s +
+// S), which indexes keys_alt through keys (keys_alt = keys + capacity with sel on); keys[s,
+// e) stays as the fill left it.  S is the number of keys below a threshold found from a histogram
+// of key bits 62..51 (the depth's exponent and 4 mantissa bits; bit 63, its sign, is 0),
+// refined by one of bits 50..39 inside the bin the threshold falls in: the keys below the
+// threshold are exactly the S smallest.  If even the nearest bin holds more than kSelCap
+// keys, sel[t] = kSelNone and the forward hands the item straight to the full sort.
+__device__ __forceinline__ void select_prefix(const BatchDev& b, int64_t t, uint32_t s,
+                                              uint32_t e, uint64_t* sa, uint64_t* sb,
+                                              unsigned* s_tmp) {
+  const uint64_t* in = b.keys + s;
+  const int n = (int)(e - s);
+  unsigned* hist = reinterpret_cast<unsigned*>(sa);  // 16 KB of sa's 18 KB
+  for (int i = threadIdx.x; i < kHistBins; i += kSortThreads) hist[i] = 0u;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += kSortThreads)
+    atomicAdd(&hist[(unsigned)(in[i] >> 51) & (kHistBins - 1)], 1u);
+  __syncthreads();
+  hist_boundary(hist, 0u, (unsigned)kSelCap, s_tmp);
+  const unsigned b1 = s_tmp[8];
+  unsigned S = s_tmp[9];
+  uint64_t thr = (uint64_t)b1 << 51;
+  if (8u * ((unsigned)kSelCap - S) > (unsigned)kSelCap) {
+    // more than an eighth of the prefix left: refine inside bin b1
+    for (int i = threadIdx.x; i < kHistBins; i += kSortThreads) hist[i] = 0u;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kSortThreads) {
+      const uint64_t k = in[i];
+      if ((unsigned)(k >> 51) == b1) atomicAdd(&hist[(unsigned)(k >> 39) & (kHistBins - 1)], 1u);
+    }
+    __syncthreads();
+    hist_boundary(hist, S, (unsigned)kSelCap, s_tmp);
+    thr |= (uint64_t)s_tmp[8] << 39;
+    S = s_tmp[9];
+  }
+  if (S == 0) {
+    if (threadIdx.x == 0) b.sel[t] = kSelNone;
+    return;
+  }
+  if (threadIdx.x == 0) s_tmp[10] = 0u;
+  __syncthreads();
+  // the keys below thr, in any order, then sorted (sort_chunk reads them before it
+  // writes sb)
+  for (int i = threadIdx.x; i < n; i += kSortThreads) {
+    const uint64_t k = in[i];
+    if (k < thr) {
+      const unsigned pos = atomicAdd(&s_tmp[10], 1u);
+      if (pos < S) sb[pos] = k;
+    }
+  }
+  __syncthreads();
+  if (s_tmp[10] != S) {  // not reachable for keys of positive depths; kept as a check
+    if (threadIdx.x == 0) { atomicOr(b.status, ST_BOUNDS); b.sel[t] = kSelNone; }
+    return;
+  }
+  sort_chunk<kSortThreads>(sb, b.keys_alt + s, (int)S, sa, sb);
+  if (threadIdx.x == 0) {
+    b.sel[t] = S;
+    const uint32_t off = (uint32_t)b.capacity + s;
+    b.ranges[t] = make_uint2(off, off + S);
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- fill
@@ -315,6 +419,7 @@ void launch_fill(const BatchDev& b, cudaStream_t s) {
 __global__ void __launch_bounds__(kSortThreads) k_seg_sort_small(const BatchDev b) {
   __shared__ uint64_t sk[2][kPadded];
   __shared__ unsigned s_base[2];
+  __shared__ unsigned s_tmp[11];
   const int64_t t = item_of(b, blockIdx.x);
   uint32_t s, e;
   segment_of(b, t, s, e);
@@ -322,6 +427,7 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_sort_small(const BatchDev 
   if (threadIdx.x == 0) {
     const uint32_t cut = b.removed ? min(b.removed[t], e - s) : 0u;
     b.ranges[t] = make_uint2(s, e - cut);
+    if (b.sel) b.sel[t] = 0u;
   }
   const int n = (int)(e - s);
   if (n <= 1) return;
@@ -329,6 +435,10 @@ __global__ void __launch_bounds__(kSortThreads) k_seg_sort_small(const BatchDev 
   if (b.order && b.wave > 0 && item_saturated(b, t)) return;
   // likewise with a stale saturation state: a tile pruned at every pixel stays unsorted
   if (b.sat && item_pruned(b, t)) return;
+  if (n > kChunk && b.sel) {
+    select_prefix(b, t, s, e, sk[0], sk[1], s_tmp);
+    return;
+  }
   if (n > kChunk) {
     const unsigned nch = (unsigned)((n + kBig - 1) / kBig);
     if (threadIdx.x == 0) {
@@ -439,10 +549,27 @@ __global__ void __launch_bounds__(kBigThreads) k_merge_round(const BatchDev b, i
   }
 }
 
-void launch_seg_sort(const BatchDev& b, int max_rounds, cudaStream_t s) {
-  if (b.n_tiles == 0) return;
-  const int64_t items = b.order ? b.item_n : b.n_tiles;
-  k_seg_sort_small<<<(unsigned)items, kSortThreads, 0, s>>>(b);
+// The items the forward handed back (b.retry): full segment ranges, sel = 0, and their
+// segments registered as chunk work items for the long-segment sort.
+__global__ void __launch_bounds__(128) k_retry_prep(const BatchDev b) {
+  const unsigned n = *b.retry_count;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t t = b.retry[i];
+    uint32_t s, e;
+    segment_of(b, t, s, e);
+    b.ranges[t] = make_uint2(s, e);
+    b.sel[t] = 0u;
+    const unsigned nch = (e - s + kBig - 1) / kBig;
+    const unsigned bi = atomicAdd(b.big_count, 1u);
+    const unsigned c0 = atomicAdd(b.chunk_count, nch);
+    atomicMax(b.big_count + 1, nch);
+    b.big_list[bi] = t;
+    for (unsigned c = 0; c < nch; ++c) b.chunks[c0 + c] = make_uint2(bi, c);
+  }
+}
+
+// Chunk sort and merge rounds of the segments registered in big_list / chunks.
+static void launch_long_sort(const BatchDev& b, int max_rounds, cudaStream_t s) {
   const unsigned grid = (unsigned)device_sm_count() * 4;
   // 72 KB of dynamic shared memory: opted in once per device (a refused opt-in shows as
   // the launch's error, which the callers check).  Its grid-stride loop runs one wave of
@@ -454,7 +581,25 @@ void launch_seg_sort(const BatchDev& b, int max_rounds, cudaStream_t s) {
                                                  kChunkSmem, 0);
   k_chunk_sort<<<cgrid, kBigThreads, kChunkSmem, s>>>(b);
   for (int r = 0; r < max_rounds; ++r) k_merge_round<<<grid, kBigThreads, 0, s>>>(b, r);
-  count_launch(2 + max_rounds);
+  count_launch(1 + max_rounds);
+}
+
+void launch_seg_sort(const BatchDev& b, int max_rounds, cudaStream_t s) {
+  if (b.n_tiles == 0) return;
+  const int64_t items = b.order ? b.item_n : b.n_tiles;
+  k_seg_sort_small<<<(unsigned)items, kSortThreads, 0, s>>>(b);
+  count_launch();
+  // with selected prefixes no segment is left to the long-segment sort before the forward
+  if (!b.sel) launch_long_sort(b, max_rounds, s);
+}
+
+void launch_sort_retries(const BatchDev& b, int max_rounds, cudaStream_t s) {
+  if (!b.sel || b.n_tiles == 0) return;
+  cudaMemsetAsync(b.big_count, 0, 2 * sizeof(unsigned), s);
+  cudaMemsetAsync(b.chunk_count, 0, sizeof(unsigned), s);
+  k_retry_prep<<<(unsigned)device_sm_count(), 128, 0, s>>>(b);
+  count_launch();
+  launch_long_sort(b, max_rounds, s);
 }
 
 // Merge rounds that cover any segment of a batch whose largest subset has max_n Gaussians

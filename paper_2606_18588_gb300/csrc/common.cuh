@@ -9,7 +9,7 @@
 namespace splx {
 
 constexpr int kMaxK = 64;        // subsets per view
-constexpr int kCounters = 8;     // work counters of a batch (BatchDev::counters)
+constexpr int kCounters = 10;    // work counters of a batch (BatchDev::counters)
 constexpr int kMaxViews = 256;   // views per batch
 
 // Concatenated views of the D-SSIM loss: view v's [3][H][W] image at 3 * pix_off[v];
@@ -117,8 +117,22 @@ struct BatchDev {
   // work counters (nullable; kept by eager runs): forward [0] thread-entries examined,
   // [1] (pixel, entry) alpha evaluations, [2] blends; backward [3] thread-entries,
   // [4] alpha evaluations, [5] contributions (alpha >= alpha_min); [6] work items left
-  // empty by saturation skipping; [7] work items outside their subset's visible region
+  // empty by saturation skipping; [7] work items outside their subset's visible region;
+  // [8] work items the forward walked on a selected prefix, [9] of those, the ones it
+  // handed to the full sort (see sel)
   unsigned long long* counters;
+  // selected-prefix sort (sel != nullptr; the batched path, with keys_alt = keys +
+  // capacity and 2 capacity < 2^32): a tile segment longer than one sort chunk gets only
+  // its sel[t] smallest keys sorted, into keys_alt at the segment's offset, and ranges[t]
+  // names them as keys[capacity + start, capacity + start + sel[t]) (keys keeps the
+  // segment unsorted).
+  // The forward walks that prefix; if a pixel of the tile is still blending at its end,
+  // it renders nothing and appends the item to retry (retry_count of them), whose segments
+  // are then sorted whole into keys (sel[t] = 0) and rendered again.  sel[t] = 0: the
+  // segment is sorted whole in keys; kSelNone: no prefix was selected (straight to retry)
+  uint32_t* sel;
+  uint32_t* retry;
+  unsigned* retry_count;
   // spatial visibility (nullable): per (view, subset) the bounding tile rectangle of the
   // subset's (Gaussian, tile) pairs as (min tx, min ty, ~max tx, ~max ty), built by the
   // projection with atomicMin (all four start at 0xFFFFFFFF, i.e. empty).  Work items
@@ -192,6 +206,12 @@ struct AdamTable {
 
 __host__ __device__ inline int n_sh(int deg) { return (deg + 1) * (deg + 1); }
 
+// BatchDev::sel value of a long segment with no selected prefix (its nearest depth bin
+// alone holds more keys than a prefix may)
+constexpr uint32_t kSelNone = 0xFFFFFFFFu;
+// largest selected prefix: keys sorted in shared memory by one sort CTA
+constexpr int kSelCap = 2048;
+
 // ---- launch wrappers (defined in the .cu files) ------------------------------------
 void launch_project(const BatchDev& b, cudaStream_t s);
 void launch_fill(const BatchDev& b, cudaStream_t s);
@@ -202,6 +222,10 @@ inline int64_t chunk_list_capacity(int64_t n_tiles, int64_t capacity) {
   return n_tiles + capacity / 2048 + 1;
 }
 void launch_raster_fwd(const BatchDev& b, cudaStream_t s);
+// The full sort of the segments the forward handed back (b.retry) and their second
+// forward: no-ops when the retry list is empty (selected-prefix sort, b.sel != nullptr).
+void launch_sort_retries(const BatchDev& b, int max_rounds, cudaStream_t s);
+void launch_raster_fwd_retry(const BatchDev& b, cudaStream_t s);
 void launch_composite(const BatchDev& b, int64_t total_pixels, cudaStream_t s);
 void launch_composite_bwd(const BatchDev& b, int64_t total_pixels, cudaStream_t s);
 // Re-evaluates every view's stale saturation state (b.sat) from the partials just rendered:

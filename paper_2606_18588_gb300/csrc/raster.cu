@@ -301,6 +301,22 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
       return;
     }
   }
+  // with no selected prefix (kSelNone) the item goes straight to the full sort and its
+  // second forward (a selected prefix needs nothing here: its range points into keys_alt)
+  // The item's id, if its list is a selected prefix, waits in shared memory for the end of
+  // the walk (no register held across it).
+  __shared__ uint32_t s_prefix_item;
+  if (b.sel) {
+    const uint32_t sv = b.sel[id];
+    if (sv == kSelNone) {
+      if (threadIdx.x == 0) {
+        b.retry[atomicAdd(b.retry_count, 1u)] = (uint32_t)id;
+        if (kCount && b.counters) atomicAdd(b.counters + 9, 1ull);
+      }
+      return;
+    }
+    if (threadIdx.x == 0) s_prefix_item = sv ? (uint32_t)id : kSelNone;
+  }
   unsigned n_eval = 0, n_pix = 0, n_blend = 0;
   for (int64_t base = start; base < end; base += NB) {
     if (__syncthreads_count(live == 0) == NTH) break;
@@ -380,8 +396,30 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
     im.T[p] = T[i];
     im.D[p] = D[i];
     im.last[p] = last[i];
-    if (b.order) {
-      float* tp = b.tpre + b.pix_off[ti.v] + p;
+  }
+  if (b.sel) {
+    // a walk that ended inside a sorted prefix is exact unless a pixel is still blending, in
+    // which case the entries after the prefix matter in their sorted order (the barrier
+    // also publishes s_prefix_item)
+    const bool more = __syncthreads_or(live != 0);
+    const uint32_t pid = s_prefix_item;
+    if (pid != kSelNone) {
+      if (threadIdx.x == 0 && kCount && b.counters) atomicAdd(b.counters + 8, 1ull);
+      if (more) {
+        if (threadIdx.x == 0) {
+          b.retry[atomicAdd(b.retry_count, 1u)] = pid;
+          if (kCount && b.counters) atomicAdd(b.counters + 9, 1ull);
+        }
+        return;  // the second forward writes the prefix transmittance (and the planes again)
+      }
+    }
+  }
+  if (b.order) {
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      const int px = ti.x + 8 * slot_col<PPT>(i), py = ti.y + 4 * slot_row<PPT>(i);
+      if (px >= ti.W || py >= ti.H) continue;
+      float* tp = b.tpre + b.pix_off[ti.v] + (int64_t)py * ti.W + px;
       *tp = b.wave == 0 ? T[i] : *tp * T[i];
     }
   }
@@ -396,7 +434,7 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
   const TileInfo ti = decode_tile<TS, PPT>(b, id);
   if (!in_omega(b, ti.v, ti.k, ti.tx, ti.ty)) return;  // nothing written there, nothing to do
   const uint2 rg = b.ranges[id];
-  const int64_t start = rg.x;
+  const int64_t start = rg.x;  // (a selected prefix's range points into keys_alt)
   const ImgDev im = b.imgs[ti.v * b.K + ti.k];
   // composite adjoint of the thread's pixels: (dL/dC^m rgb, -T^m dL/dT^m) per slot, in
   // shared memory (read only where a pixel takes an entry), which keeps registers down
@@ -570,8 +608,12 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
 
 // One CTA per work item, or (kPersist) a grid sized to the SMs whose CTAs take work items
 // in order from a device counter until none is left.
+// (16x16 tiles: 128 threads held to 48 registers, 10 resident CTAs per SM)
+template <int TS>
+constexpr int kMinBlocksFwd = TS == 16 ? 10 : 1;
+
 template <int TS, int PPT, bool kCount, bool kPersist>
-__global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) {
+__global__ void __launch_bounds__(TS * TS / PPT, kMinBlocksFwd<TS>) k_raster_fwd(const BatchDev b) {
   __shared__ float4 sA[kNB], sB[kNB], sC[kNB];
   __shared__ uint32_t sL[(TS * TS / PPT / 32) * kNB];  // per-warp compacted entry lists
   if constexpr (!kPersist) {
@@ -586,6 +628,19 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd(const BatchDev b) 
       if (id >= items_of_launch(b)) return;
       fwd_item<TS, PPT, kCount>(b, item_of(b, id), sA, sB, sC, sL);
     }
+  }
+}
+
+// Second forward of the items the first one handed back (b.retry, after their full sort):
+// a fixed grid whose CTAs take the list's items in a grid-stride loop.
+template <int TS, int PPT, bool kCount>
+__global__ void __launch_bounds__(TS * TS / PPT, kMinBlocksFwd<TS>) k_raster_fwd_retry(const BatchDev b) {
+  __shared__ float4 sA[kNB], sB[kNB], sC[kNB];
+  __shared__ uint32_t sL[(TS * TS / PPT / 32) * kNB];
+  const unsigned n = *b.retry_count;
+  for (unsigned w = blockIdx.x; w < n; w += gridDim.x) {
+    __syncthreads();  // the previous item is done with shared memory
+    fwd_item<TS, PPT, kCount>(b, (int64_t)b.retry[w], sA, sB, sC, sL);
   }
 }
 
@@ -688,6 +743,24 @@ void launch_raster_fwd(const BatchDev& b, cudaStream_t s) {
     case 8: launch_fwd_t<8>(b, s); break;
     case 32: launch_fwd_t<32>(b, s); break;
     default: launch_fwd_t<16>(b, s); break;
+  }
+  count_launch();
+}
+
+template <int TS>
+static void launch_fwd_retry_t(const BatchDev& b, cudaStream_t s) {
+  constexpr int P = PptFwd<TS>::value;
+  const unsigned grid = (unsigned)device_sm_count() * 2;
+  if (counting(b, s)) k_raster_fwd_retry<TS, P, true><<<grid, TS * TS / P, 0, s>>>(b);
+  else k_raster_fwd_retry<TS, P, false><<<grid, TS * TS / P, 0, s>>>(b);
+}
+
+void launch_raster_fwd_retry(const BatchDev& b, cudaStream_t s) {
+  if (!b.sel || b.n_tiles == 0) return;
+  switch (b.tile) {
+    case 8: launch_fwd_retry_t<8>(b, s); break;
+    case 32: launch_fwd_retry_t<32>(b, s); break;
+    default: launch_fwd_retry_t<16>(b, s); break;
   }
   count_launch();
 }

@@ -96,6 +96,7 @@ _sigs = {
     "splx_batch_set_stale": (C.c_int, [_P, _P]),
     "splx_batch_visible": (C.c_int, [_P, C.POINTER(C.c_int64), _P]),
     "splx_batch_set_visibility": (C.c_int, [_P, C.c_int32]),
+    "splx_batch_set_prefix_sort": (C.c_int, [_P, C.c_int32]),
     "splx_batch_set_cross_filter": (C.c_int, [_P, _P]),
     "splx_batch_loss_l1_dssim": (C.c_int, [_P, _P, _P, C.c_float, _P, _P, _P]),
     "splx_loss_l1_dssim": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32, C.c_float, _P, _P, _P]),
@@ -534,6 +535,12 @@ class Batch:
         _check(_lib.splx_batch_set_visibility(self.h, int(bool(enable))),
                "splx_batch_set_visibility")
 
+    def set_prefix_sort(self, enable: bool):
+        """Selected-prefix sort of long tile segments on (default) or off; results are
+        identical."""
+        _check(_lib.splx_batch_set_prefix_sort(self.h, int(bool(enable))),
+               "splx_batch_set_prefix_sort")
+
     def set_cross_filter(self, cells):
         """Cross-boundary per-ray filtering with the subsets' k-d boxes [K, 2, 3] (lo, hi;
         infinite on open sides), or off (None); see splx_batch_set_cross_filter."""
@@ -580,11 +587,12 @@ class Batch:
         return f.value, b.value
 
     def counters(self, stream=None) -> dict:
-        arr = (C.c_int64 * 9)()
+        arr = (C.c_int64 * 11)()
         _check(_lib.splx_batch_counters(self.h, arr, _stream(stream)), "splx_batch_counters")
         return dict(pairs=arr[0], entries_fwd=arr[1], alpha_fwd=arr[2], blended=arr[3],
                     entries_bwd=arr[4], alpha_bwd=arr[5], contrib_bwd=arr[6],
-                    skipped_items=arr[7], outside_items=arr[8])
+                    skipped_items=arr[7], outside_items=arr[8], prefix_items=arr[9],
+                    retried_items=arr[10])
 
     def visible(self, stream=None) -> int:
         """(view, Gaussian) pairs the last forward's projection kept (synchronises)."""
