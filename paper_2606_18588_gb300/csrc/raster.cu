@@ -117,57 +117,50 @@ struct TileInfo {
   int v, k, x, y, W, H, tx, ty;
 };
 
-// Blocks of a warp's region (origin RX, RY) that the rectangle [x0,x1] x [y0,y1] meets:
-// bit i for slot i (PPT = 4: blocks at x offsets 0/8, y offsets 0/4; PPT = 2: y 0/4).
+// Compacts the staged entries [0, cnt) whose rectangle meets the warp's region (origin RX,
+// RY; 8 x 8 pixels for PPT = 2, 16 x 8 for PPT = 4) into list[], in entry order, as
+// entry | (region columns the rectangle spans) << 8 | (region rows it spans) << 24: bit c
+// of the column mask for column RX + c, bit r of the row mask for row RY + r.  A lane's
+// slot test is then two bit extractions (slot_mask).  One lane tests one entry, 32 at a
+// time; returns the number listed.
 template <int PPT>
-__device__ __forceinline__ unsigned block_mask(int x0, int x1, int y0, int y1, int RX, int RY) {
-  const bool xb0 = x0 <= RX + 7 && x1 >= RX;
-  const bool xb1 = PPT == 4 && x0 <= RX + 15 && x1 >= RX + 8;
-  const bool yb0 = y0 <= RY + 3 && y1 >= RY;
-  const bool yb1 = y0 <= RY + 7 && y1 >= RY + 4;
-  if (PPT == 4)
-    return (unsigned)(xb0 && yb0) | ((unsigned)(xb1 && yb0) << 1) |
-           ((unsigned)(xb0 && yb1) << 2) | ((unsigned)(xb1 && yb1) << 3);
-  return (unsigned)(xb0 && yb0) | ((unsigned)(xb0 && yb1) << 1);
-}
-
-// Compacts the staged entries [0, cnt) that meet the warp's region (and pass `keep`) into
-// list[] as (entry | block mask << 16), in entry order; returns their number.  One lane
-// tests one entry, 32 at a time.
-template <int PPT, typename Keep>
 __device__ __forceinline__ int compact_entries(const float4* sB, const float4* sC, int cnt,
-                                               int RX, int RY, int lane, uint32_t* list,
-                                               Keep keep) {
+                                               int RX, int RY, int lane, uint32_t* list) {
+  constexpr int RW = PPT == 4 ? 16 : 8;  // region width
   int nl = 0;
   for (int g0 = 0; g0 < cnt; g0 += 32) {
     const int e = g0 + lane;
-    unsigned m = 0;
-    if (e < cnt && keep(e)) {
+    uint32_t item = 0;
+    if (e < cnt) {
       const uint32_t rx = __float_as_uint(sB[e].w), ry = __float_as_uint(sC[e].w);
-      m = block_mask<PPT>((int)(rx & 0xFFFFu), (int)(rx >> 16), (int)(ry & 0xFFFFu),
-                          (int)(ry >> 16), RX, RY);
+      const int c0 = max((int)(rx & 0xFFFFu) - RX, 0), c1 = min((int)(rx >> 16) - RX, RW - 1);
+      const int r0 = max((int)(ry & 0xFFFFu) - RY, 0), r1 = min((int)(ry >> 16) - RY, 7);
+      if (c0 <= c1 && r0 <= r1) {
+        const uint32_t cm = ((2u << (c1 - c0)) - 1u) << c0;
+        const uint32_t rm = ((2u << (r1 - r0)) - 1u) << r0;
+        item = (uint32_t)e | (cm << 8) | (rm << 24);
+      }
     }
-    const unsigned hit = __ballot_sync(0xffffffffu, m != 0);
-    if (m) list[nl + __popc(hit & ((1u << lane) - 1u))] = (uint32_t)e | (m << 16);
+    const unsigned hit = __ballot_sync(0xffffffffu, item != 0u);
+    if (item) list[nl + __popc(hit & ((1u << lane) - 1u))] = item;
     nl += __popc(hit);
   }
   __syncwarp();
   return nl;
 }
 
-// Slots of a thread whose pixel lies in the rectangle [x0, x1] x [y0, y1]: bit i for slot i
-// (pixel (x + 8 col(i), y + 4 row(i))).  Unsigned differences test both bounds at once (a
-// pixel left of x0 wraps to a large value).
+// Slots of the lane at column lx, row ly of its 8 x 4 blocks whose pixel lies in the
+// rectangle of a compacted list item: bit i for slot i (pixel column lx + 8 col(i), row
+// ly + 4 row(i) of the region).
 template <int PPT>
-__device__ __forceinline__ unsigned rect_slots(int x, int y, int x0, int x1, int y0, int y1) {
-  const unsigned dx = (unsigned)(x - x0), dy = (unsigned)(y - y0);
-  const unsigned w = (unsigned)(x1 - x0), h = (unsigned)(y1 - y0);
-  const unsigned rows = (unsigned)(dy <= h) | ((unsigned)(dy + 4u <= h) << 1);
+__device__ __forceinline__ unsigned slot_mask(uint32_t item, int lx, int ly) {
+  const uint32_t cs = item >> (8 + lx), rs = item >> (24 + ly);
+  const uint32_t c0 = cs & 1u, r0 = rs & 1u, r1 = (rs >> 4) & 1u;
   if (PPT == 4) {
-    const unsigned cols = (unsigned)(dx <= w) | ((unsigned)(dx + 8u <= w) << 1);
-    return ((rows & 1u) ? cols : 0u) | ((rows & 2u) ? cols << 2 : 0u);
+    const uint32_t c1 = (cs >> 8) & 1u;
+    return (c0 & r0) | ((c1 & r0) << 1) | ((c0 & r1) << 2) | ((c1 & r1) << 3);
   }
-  return dx <= w ? rows : 0u;
+  return (c0 & r0) | ((c0 & r1) << 1);
 }
 
 template <int PPT>
@@ -217,6 +210,7 @@ __device__ __forceinline__ TileInfo decode_tile(const BatchDev& b, int64_t id) {
 // kCount variants (eager runs only) also count the work for the roofline: thread-entries
 // examined, (pixel, entry) alpha evaluations and blends / contributions.
 constexpr int kNB = 256;  // list entries staged in shared memory per batch
+static_assert(kNB <= 256, "a compacted list item holds the entry in 8 bits");
 // the backward stages fewer at a time where its threads allow (one entry per thread at
 // least); one-warp CTAs stage 64, which keeps their shared memory at 7.4 KB
 template <int TS, int PPT>
@@ -339,20 +333,13 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
       const int lane = (int)(threadIdx.x & 31);
       uint32_t* list = sL + (threadIdx.x >> 5) * NB;
       const int nl = compact_entries<PPT>(sB, sC, cnt, ti.x - (lane & 7), ti.y - (lane >> 3),
-                                          lane, list, [](int) { return true; });
-      int q = 0;
-      for (; q < nl; ++q) {
-        if (!__any_sync(0xffffffffu, live != 0)) break;
-        const uint32_t item = list[q];
-        const int jj = (int)(item & 0xFFFFu);
-        const unsigned bm = item >> 16;
+                                          lane, list);
+      auto entry = [&](const uint32_t item) {
+        const int jj = (int)(item & 0xFFu);
         const float4 Bv = sB[jj];
         const float4 Cv = sC[jj];
-        const uint32_t rx = __float_as_uint(Bv.w), ry = __float_as_uint(Cv.w);
-        // slots to evaluate: in the warp's blocks (bm), in the rectangle, still blending
-        const unsigned todo = bm & live &
-                              rect_slots<PPT>(ti.x, ti.y, (int)(rx & 0xFFFFu), (int)(rx >> 16),
-                                              (int)(ry & 0xFFFFu), (int)(ry >> 16));
+        // slots to evaluate: in the rectangle, still blending
+        const unsigned todo = live & slot_mask<PPT>(item, lane & 7, lane >> 3);
         const float4 Av = sA[jj];
         const ColTerms ct0 = col_terms(Av, pcx0), ct1 = col_terms(Av, pcx1);
 #pragma unroll
@@ -376,7 +363,18 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
           last[i] = (int)(base - start) + jj;
           if (kCount) ++n_blend;
         }
+      };
+      // four entries per warp-wide test of whether any pixel still blends (entries after
+      // the warp's last pixel has stopped find no slot to evaluate)
+      int q = 0;
+      for (; q < nl; q += 4) {
+        if (!__any_sync(0xffffffffu, live != 0)) break;
+        entry(list[q]);
+        if (q + 1 < nl) entry(list[q + 1]);
+        if (q + 2 < nl) entry(list[q + 2]);
+        if (q + 3 < nl) entry(list[q + 3]);
       }
+      q = q < nl ? q : nl;
       if (kCount && lane == 0) n_eval += (unsigned)q;
     }
   }
@@ -608,9 +606,10 @@ __device__ __forceinline__ void bwd_item(const BatchDev& b, const int64_t id, fl
 
 // One CTA per work item, or (kPersist) a grid sized to the SMs whose CTAs take work items
 // in order from a device counter until none is left.
-// (16x16 tiles: 128 threads held to 48 registers, 10 resident CTAs per SM)
+// (16x16 tiles: 128 threads held to 48 registers, 10 resident CTAs per SM; 32x32 tiles:
+// 256 threads at 64 registers, 4 CTAs)
 template <int TS>
-constexpr int kMinBlocksFwd = TS == 16 ? 10 : 1;
+constexpr int kMinBlocksFwd = TS == 16 ? 10 : (TS == 32 ? 4 : 1);
 
 template <int TS, int PPT, bool kCount, bool kPersist>
 __global__ void __launch_bounds__(TS * TS / PPT, kMinBlocksFwd<TS>) k_raster_fwd(const BatchDev b) {
