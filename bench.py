@@ -65,6 +65,8 @@ def parse():
                     help="backward into gradient arrays and a separate Adam pass")
     ap.add_argument("--no-skip", action="store_true",
                     help="render every (view, subset, tile) item (no saturation skipping)")
+    ap.add_argument("--whole-sort", action="store_true",
+                    help="sort every tile segment whole (no selected prefixes of long ones)")
     ap.add_argument("--cpu-tile-fraction", type=float, default=1.0 / 48.0)
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving run (0: skip it)")
@@ -450,11 +452,14 @@ def city_leg(args, rank, world, local, steps, warmup):
                          fused_adam=not args.unfused_adam)
         st.set_targets(tgt[0])
         st.batch.set_timing(True)
+        if args.whole_sort:
+            st.batch.set_prefix_sort(False)
         st.run()
         stream.synchronize()
         code, _ = st.status()
         if code != S.OK:
             raise RuntimeError(f"city step status {code}")
+        counts = st.batch.counters(stream)  # the eager step's work
         launches0 = ctx.launch_count
         st.capture()
         launches_per_step = ctx.launch_count - launches0
@@ -499,7 +504,11 @@ def city_leg(args, rank, world, local, steps, warmup):
             "timing": "CUDA events around the timed steps; each step sets its views, orders "
                       "and targets between replays (a host wait for the previous replay)",
             "clocks": clk, "gpu_launches": launches_per_step * steps,
-            "kernel_ms_last_step": kms}
+            "kernel_ms_last_step": kms, "counters_first_step": counts,
+            # selected prefixes stay on only if the eager step handed back at most a quarter
+            # of its prefix items (splx_batch_tune_prefix_sort, before the capture)
+            "prefix_sort": (not args.whole_sort) and not (
+                counts["prefix_items"] > 0 and 4 * counts["retried_items"] > counts["prefix_items"])}
 
 
 def city_main(args):
@@ -517,7 +526,8 @@ def city_main(args):
             "data": "synthetic",
             "config": {k: r[k] for k in ("workload", "global_batch", "pixels_per_step", "tile",
                                          "pair_capacity", "saturation_skipping", "scene_gen_s",
-                                         "l2", "timing", "kernel_ms_last_step")},
+                                         "l2", "timing", "kernel_ms_last_step",
+                                         "counters_first_step", "prefix_sort")},
             "roofline": None, "e2e": None, "clocks": r["clocks"],
             "gpu_launches": r["gpu_launches"]}
     line["config"]["parallelism"] = "replicas" if world > 1 else "single GPU"
@@ -564,6 +574,8 @@ def batched_leg(args, ctx, dev, sc, off, cams, targets, o, ctas, order, stream, 
                          stale=args.stale and order is not None)
         st.batch.set_timing(True)
         st.batch.set_launch(ctas)
+        if args.whole_sort:
+            st.batch.set_prefix_sort(False)
         st.run()  # eager once: sizes everything, checks status
         stream.synchronize()
         code, pairs = st.status()
@@ -804,6 +816,9 @@ def main():
                                "fill tile buckets, per-tile depth sort, raster fwd, composite, L1 "
                                "loss, composite bwd, raster bwd, project bwd, Adam)",
                        "saturation_skipping": order is not None,
+                       "prefix_sort": (not args.whole_sort) and not (
+                           counts["prefix_items"] > 0
+                           and 4 * counts["retried_items"] > counts["prefix_items"]),
                        "adam": ("fused into the projection adjoint (kernel_ms project_bwd)"
                                 if head["fused_adam"] else "separate pass over the gradients"),
                        "waves": ("sort + raster_fwd of up to 4 view groups on their own "

@@ -318,6 +318,12 @@ int splx_batch_set_visibility(splx_batch_t b, int32_t enable);
  * was captured with).  Off while cross-boundary filtering is on, and for a pair capacity
  * of 2^31 or more. */
 int splx_batch_set_prefix_sort(splx_batch_t b, int32_t enable);
+/* Keeps the selected-prefix sort on only if the last eager forward handed at most a
+ * quarter of its prefix items back to the whole sort (their pixels still blending at the
+ * prefix's end: tiles with long lists of small or faint Gaussians), and turns it off
+ * otherwise, for launches issued afterwards; call it between an eager forward and a graph
+ * capture.  Synchronises `stream`; not capturable; SPLX_ERR_INVALID without a batch state. */
+int splx_batch_tune_prefix_sort(splx_batch_t b, splx_stream_t stream);
 /* Cross-boundary per-ray filtering (Sec. 8.1, appendix "Cross-boundary Gaussians
  * Handling").  cells (host, [K][6] floats: lo x, y, z, hi x, y, z of subset k's k-d box,
  * +-INFINITY on open sides; NaN rejected) turns it on for launches issued afterwards (and

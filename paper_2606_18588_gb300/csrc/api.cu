@@ -1408,6 +1408,20 @@ int splx_batch_set_prefix_sort(splx_batch_t bt, int32_t enable) {
   return SPLX_OK;
 }
 
+int splx_batch_tune_prefix_sort(splx_batch_t bt, splx_stream_t stream) {
+  if (!bt || !bt->plan.sel) return SPLX_ERR_INVALID;
+  Plan& P = bt->plan;
+  if (!P.select_prefix || !P.counters) return SPLX_OK;
+  CtxScope scope(P.ctx);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long c[kCounters] = {};
+  CK(cudaMemcpyAsync(c, P.counters, sizeof(c), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  // counters[8]: items walked on a selected prefix, [9]: items handed to the whole sort
+  if (c[8] > 0 && 4 * c[9] > c[8]) P.select_prefix = false;
+  return SPLX_OK;
+}
+
 int splx_batch_set_order(splx_batch_t bt, const int32_t* order) {
   if (!bt) return SPLX_ERR_INVALID;
   Plan& P = bt->plan;

@@ -97,6 +97,7 @@ _sigs = {
     "splx_batch_visible": (C.c_int, [_P, C.POINTER(C.c_int64), _P]),
     "splx_batch_set_visibility": (C.c_int, [_P, C.c_int32]),
     "splx_batch_set_prefix_sort": (C.c_int, [_P, C.c_int32]),
+    "splx_batch_tune_prefix_sort": (C.c_int, [_P, _P]),
     "splx_batch_set_cross_filter": (C.c_int, [_P, _P]),
     "splx_batch_loss_l1_dssim": (C.c_int, [_P, _P, _P, C.c_float, _P, _P, _P]),
     "splx_loss_l1_dssim": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32, C.c_float, _P, _P, _P]),
@@ -540,6 +541,12 @@ class Batch:
         identical."""
         _check(_lib.splx_batch_set_prefix_sort(self.h, int(bool(enable))),
                "splx_batch_set_prefix_sort")
+
+    def tune_prefix_sort(self, stream=None):
+        """Keeps the selected-prefix sort only if the last eager forward handed at most a
+        quarter of its prefix items back to the whole sort (synchronises)."""
+        _check(_lib.splx_batch_tune_prefix_sort(self.h, _stream(stream)),
+               "splx_batch_tune_prefix_sort")
 
     def set_cross_filter(self, cells):
         """Cross-boundary per-ray filtering with the subsets' k-d boxes [K, 2, 3] (lo, hi;

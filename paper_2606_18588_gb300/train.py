@@ -165,7 +165,9 @@ class BatchedStep:
 
     def capture(self, events=None):
         """Captures run() as one CUDA graph on self.stream (the batch must already have
-        run eagerly once, so its scratch exists)."""
+        run eagerly once, so its scratch exists; that run's counts decide whether the graph
+        keeps the selected-prefix sort)."""
+        self.batch.tune_prefix_sort(self.stream)
         S.graph_begin(self.ctx, self.stream)
         try:
             self.run(events)
@@ -180,6 +182,7 @@ class BatchedStep:
     def capture_split(self):
         """Captures the step as two CUDA graphs, the forward and the rest (loss, backward,
         Adam), for step_from_host (the batch must already have run eagerly once)."""
+        self.batch.tune_prefix_sort(self.stream)
         graphs = []
         for part in (self._forward, self._update):
             S.graph_begin(self.ctx, self.stream)

@@ -169,3 +169,31 @@ def test_prefix_sort_switch_needs_a_batch_state(ctx):
     b.set_prefix_sort(False)
     b.set_prefix_sort(True)
     b.close()
+
+
+@pytest.mark.parametrize("make", [_dense, _faint, _planar])
+def test_prefix_sort_tuning_follows_the_hand_back_share(ctx, make):
+    # splx_batch_tune_prefix_sort keeps the selected prefixes only if at most a quarter of
+    # the last eager forward's prefix items went back to the whole sort; the images stay
+    # those of whole sorts either way
+    from paper_2606_18588_gb300 import splx as S
+    from gpu_util import subset_struct, to_device
+    sc, off, _ = make()
+    cams = _cams()
+    dev = to_device(sc)
+    b = S.Batch(ctx, [subset_struct(dev, int(off[k]), int(off[k + 1]), sc.sh_degree)
+                      for k in range(len(off) - 1)], cams, S.opts())
+    rgb = torch.empty(b.rgb_off[-1], device="cuda")
+    b.forward(rgb)
+    c1 = b.counters()
+    ref = rgb.clone()
+    b.tune_prefix_sort()
+    keep = not (c1["prefix_items"] > 0 and 4 * c1["retried_items"] > c1["prefix_items"])
+    if make is _faint:
+        assert not keep  # long lists of faint Gaussians: most prefixes are handed back
+    b.forward(rgb)
+    torch.cuda.synchronize()
+    c2 = b.counters()
+    assert (c2["prefix_items"] + c2["retried_items"] > 0) == keep
+    assert torch.equal(rgb, ref)
+    b.close()
