@@ -558,7 +558,10 @@ __global__ void __launch_bounds__(128) k_retry_prep(const BatchDev b) {
     uint32_t s, e;
     segment_of(b, t, s, e);
     b.ranges[t] = make_uint2(s, e);
-    b.sel[t] = 0u;
+    // after a prefix the second forward resumes at the prefix's end (the whole sort puts
+    // the prefix's keys first, in its order); without one it starts at the beginning
+    const uint32_t sv = b.sel[t];
+    b.sel[t] = sv != kSelNone && sv != 0u ? (kSelResume | sv) : 0u;
     const unsigned nch = (e - s + kBig - 1) / kBig;
     const unsigned bi = atomicAdd(b.big_count, 1u);
     const unsigned c0 = atomicAdd(b.chunk_count, nch);

@@ -129,7 +129,9 @@ struct BatchDev {
   // The forward walks that prefix; if a pixel of the tile is still blending at its end,
   // it renders nothing and appends the item to retry (retry_count of them), whose segments
   // are then sorted whole into keys (sel[t] = 0) and rendered again.  sel[t] = 0: the
-  // segment is sorted whole in keys; kSelNone: no prefix was selected (straight to retry)
+  // segment is sorted whole in keys; kSelNone: no prefix was selected (straight to retry);
+  // kSelResume | S: sorted whole after a prefix of S keys, whose forward state the planes
+  // hold
   uint32_t* sel;
   uint32_t* retry;
   unsigned* retry_count;
@@ -209,6 +211,9 @@ __host__ __device__ inline int n_sh(int deg) { return (deg + 1) * (deg + 1); }
 // BatchDev::sel value of a long segment with no selected prefix (its nearest depth bin
 // alone holds more keys than a prefix may)
 constexpr uint32_t kSelNone = 0xFFFFFFFFu;
+// BatchDev::sel bit of a handed-back item whose segment is now sorted whole and whose
+// second forward resumes after its first (sel & ~kSelResume) entries
+constexpr uint32_t kSelResume = 0x80000000u;
 // largest selected prefix: keys sorted in shared memory by one sort CTA
 constexpr int kSelCap = 2048;
 

@@ -301,8 +301,11 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
   // with no selected prefix (kSelNone) the item goes straight to the full sort and its
   // second forward (a selected prefix needs nothing here: its range points into keys_alt)
   // The item's id, if its list is a selected prefix, waits in shared memory for the end of
-  // the walk (no register held across it).
+  // the walk (no register held across it).  A second forward after a prefix (kSelResume)
+  // takes the pixels' state from the planes the first one wrote and walks the whole
+  // sorted list from the prefix's end: its first entries are the prefix's, in its order.
   __shared__ uint32_t s_prefix_item;
+  int64_t walk0 = start;
   if (b.sel) {
     const uint32_t sv = b.sel[id];
     if (sv == kSelNone) {
@@ -312,10 +315,27 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
       }
       return;
     }
-    if (threadIdx.x == 0) s_prefix_item = sv ? (uint32_t)id : kSelNone;
+    if (sv & kSelResume) {
+      walk0 = start + (sv & ~kSelResume);
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) {
+        const int px = ti.x + 8 * slot_col<PPT>(i), py = ti.y + 4 * slot_row<PPT>(i);
+        if (px >= ti.W || py >= ti.H) continue;
+        const int64_t p = (int64_t)py * ti.W + px;
+        c0[i] = im.rgb[p];
+        c1[i] = im.rgb[HW + p];
+        c2[i] = im.rgb[2 * HW + p];
+        T[i] = im.T[p];
+        D[i] = im.D[p];
+        const int l = im.last[p];
+        last[i] = l <= -2 ? -3 - l : l;
+        if (l <= -2) live &= ~(1u << i);  // it had stopped inside the prefix
+      }
+    }
+    if (threadIdx.x == 0) s_prefix_item = sv && !(sv & kSelResume) ? (uint32_t)id : kSelNone;
   }
   unsigned n_eval = 0, n_pix = 0, n_blend = 0;
-  for (int64_t base = start; base < end; base += NB) {
+  for (int64_t base = walk0; base < end; base += NB) {
     if (__syncthreads_count(live == 0) == NTH) break;
 #pragma unroll
     for (int r = 0; r < NB / NTH; ++r) {
@@ -411,7 +431,15 @@ __device__ __forceinline__ void fwd_item(const BatchDev& b, const int64_t id, fl
           b.retry[atomicAdd(b.retry_count, 1u)] = pid;
           if (kCount && b.counters) atomicAdd(b.counters + 9, 1ull);
         }
-        return;  // the second forward writes the prefix transmittance (and the planes again)
+        // the planes hold the state at the prefix's end for the second forward: a pixel
+        // that has stopped keeps its last index as -3 - last
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+          const int px = ti.x + 8 * slot_col<PPT>(i), py = ti.y + 4 * slot_row<PPT>(i);
+          if (px < ti.W && py < ti.H && !((live >> i) & 1u))
+            im.last[(int64_t)py * ti.W + px] = -3 - last[i];
+        }
+        return;  // the second forward writes the prefix transmittance and the planes
       }
     }
   }
@@ -635,9 +663,10 @@ __global__ void __launch_bounds__(TS * TS / PPT, kMinBlocksFwd<TS>) k_raster_fwd
 }
 
 // Second forward of the items the first one handed back (b.retry, after their full sort):
-// a fixed grid whose CTAs take the list's items in a grid-stride loop.
+// a fixed grid whose CTAs take the list's items in a grid-stride loop (few items, each a
+// long walk: no register cap for occupancy).
 template <int TS, int PPT, bool kCount>
-__global__ void __launch_bounds__(TS * TS / PPT, kMinBlocksFwd<TS>) k_raster_fwd_retry(const BatchDev b) {
+__global__ void __launch_bounds__(TS * TS / PPT) k_raster_fwd_retry(const BatchDev b) {
   __shared__ float4 sA[kNB], sB[kNB], sC[kNB];
   __shared__ uint32_t sL[(TS * TS / PPT / 32) * kNB];
   const unsigned n = *b.retry_count;
