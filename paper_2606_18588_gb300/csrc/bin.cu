@@ -204,13 +204,14 @@ __device__ __forceinline__ void hist_boundary(const unsigned* hist, unsigned bas
 }
 
 // Sorts the S <= kSelCap smallest keys of the segment [s, e) (n > kChunk keys) into
-// keys_alt[s, s + S) and records S in sel[t] and ranges[t] = [capacity + s, capacity + s +
-// S), which indexes keys_alt through keys (keys_alt = keys + capacity with sel on); keys[s,
-// e) stays as the fill left it.  S is the number of keys below a threshold found from a histogram
-// of key bits 62..51 (the depth's exponent and 4 mantissa bits; bit 63, its sign, is 0),
-// refined by one of bits 50..39 inside the bin the threshold falls in: the keys below the
-// threshold are exactly the S smallest.  If even the nearest bin holds more than kSelCap
-// keys, sel[t] = kSelNone and the forward hands the item straight to the full sort.
+// keys_alt[s, s + S) and records S in sel[t] and ranges[t] = [capacity + s, capacity + s
+// + S), which indexes keys_alt through keys (keys_alt = keys + capacity with sel on);
+// keys[s, e) stays as the fill left it.  S is the number of keys below a threshold found
+// from a histogram of key bits 62..51 (the depth's exponent and 4 mantissa bits; bit 63,
+// its sign, is 0), refined by one of bits 50..39 inside the bin the threshold falls in:
+// the keys below the threshold are exactly the S smallest.  If even the nearest bin holds
+// more than kSelCap keys, sel[t] = kSelNone and the forward hands the item straight to
+// the full sort.
 __device__ __forceinline__ void select_prefix(const BatchDev& b, int64_t t, uint32_t s,
                                               uint32_t e, uint64_t* sa, uint64_t* sb,
                                               unsigned* s_tmp) {
