@@ -56,13 +56,13 @@ def _cams():
             I.pinhole(80, 48, 50.0, (0.2, -0.1, -3.2), (0, 0, 0))]
 
 
-def _run(ctx, sc, off, cams, order, prefix, dL=None):
+def _run(ctx, sc, off, cams, order, prefix, dL=None, tile=16):
     from paper_2606_18588_gb300 import splx as S
     from gpu_util import params_struct, subset_struct, to_device, zeros_like_params
     dev = to_device(sc)
     K = len(off) - 1
     subs = [subset_struct(dev, int(off[k]), int(off[k + 1]), sc.sh_degree) for k in range(K)]
-    b = S.Batch(ctx, subs, cams, S.opts())
+    b = S.Batch(ctx, subs, cams, S.opts(tile=tile))
     b.set_prefix_sort(prefix)
     if order is not None:
         b.set_order(order)
@@ -110,6 +110,20 @@ def test_prefix_sort_equals_whole_sort(ctx, make, route, waves):
     assert torch.equal(T1, T0)
     for k in GROUPS:
         assert rel_l2(g1[k].cpu().numpy(), g0[k].cpu().numpy()) < 1e-5, k
+
+
+@pytest.mark.parametrize("tile", [8, 32])
+def test_prefix_sort_at_other_tile_sizes(ctx, tile):
+    # the rasterisers' other launch shapes on the prefix and hand-back routes, with waves
+    from paper_2606_18588_gb300.visibility import orders_for_views
+    for make in (_dense, _faint):
+        sc, off, boxes = make()
+        cams = _cams()
+        order = orders_for_views(boxes, cams)
+        rgb1, T1, _, c1, _ = _run(ctx, sc, off, cams, order, True, tile=tile)
+        rgb0, T0, _, _, _ = _run(ctx, sc, off, cams, order, False, tile=tile)
+        assert c1["prefix_items"] + c1["retried_items"] > 0, (make.__name__, tile)
+        assert torch.equal(rgb1, rgb0) and torch.equal(T1, T0), (make.__name__, tile)
 
 
 def test_prefix_sort_equals_plain_path(ctx):
