@@ -1,6 +1,6 @@
 """Host-side logic without a GPU: the autotuner's result cache, the serving request
-generator and latency summary, and the replica harness's max-over-ranks timing on two
-gloo ranks."""
+generator and latency summary, the replica harness's max-over-ranks timing on two gloo
+ranks, and the bench line's roofline accounting."""
 import os
 import sys
 
@@ -86,3 +86,35 @@ def test_replica_timing_is_max_over_two_gloo_ranks():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.max_over_ranks(3.5) == 3.5  # no process group: the value itself
+
+
+def test_roofline_accounting_per_unit():
+    # the bench line's roofline: rasterisers at 16 (forward) and 45 (backward) FP32
+    # instructions per evaluated (pixel, entry) pair, their bare arithmetic beside it, and
+    # HBM kernels by their algorithmic bytes per unit, each divided by the launch time
+    sys.path.insert(0, ROOT)
+    import bench
+    counts = dict(alpha_fwd=4_000_000_000, blended=2_000_000_000, alpha_bwd=3_000_000_000,
+                  contrib_bwd=1_500_000_000, pairs=400_000_000, visible=140_000_000,
+                  items_total=1000, outside_items=600)
+    w = dict(V=16, N=10_000_000, K=8, nc=16, pixels=21_000_000, alu_peak=40.0,
+             fused_adam=True)
+    pk = {"hbm_gbs": 6800.0}
+    r = bench.roofline("raster_bwd", 20.0, counts, w, pk)
+    assert r["bound"] == "alu" and r["achieved"] == pytest.approx(3e9 * 45 / 0.02 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 40.0)
+    assert r["arithmetic"]["achieved"] == pytest.approx((3e9 * 10 + 1.5e9 * 22) / 0.02 / 1e12)
+    r = bench.roofline("raster_fwd", 10.0, counts, w, pk)
+    assert r["achieved"] == pytest.approx(4e9 * 16 / 0.01 / 1e12)
+    assert r["arithmetic"]["achieved"] == pytest.approx((4e9 * 10 + 2e9 * 8) / 0.01 / 1e12)
+    r = bench.roofline("sort", 5.0, counts, w, pk)
+    assert r["bound"] == "hbm" and r["achieved"] == pytest.approx(4e8 * 16 / 0.005 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6800.0)
+    # composites count the partial planes only inside the visible regions (40 % here)
+    r = bench.roofline("composite", 1.0, counts, w, pk)
+    assert r["achieved"] == pytest.approx((21e6 * 16 + int(21e6 * 8 * 20 * 0.4)) / 0.001 / 1e9)
+    # the fused projection adjoint: read and write p, m, v once, plus the kept views' bytes
+    r = bench.roofline("project_bwd", 2.0, counts, w, pk)
+    param_bytes = (3 + 3 + 4 + 1 + 3 * 16) * 4
+    assert r["achieved"] == pytest.approx((1e7 * 6 * param_bytes + 16e7 * 4 + 1.4e8 * 96)
+                                          / 0.002 / 1e9)
